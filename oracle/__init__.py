@@ -1,0 +1,268 @@
+"""Plain FP64 CPU oracle of MIUGKS (arXiv 1704.03151) -- test infrastructure.
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It compiles ``oracle.c`` with the host C
+compiler (no fast-math) and wraps it with ctypes.  It shares no code with the
+CUDA library in ``paper_1704_03151_gb300``.
+"""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lib = None
+
+WALL, SYMMETRY, FARFIELD, OUTFLOW = 0, 1, 2, 3
+
+
+def build(force=False):
+    """Compile the oracle into oracle/_build/liboracle.so (gcc, -O2, no fast-math)."""
+    src = os.path.join(_HERE, "oracle.c")
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= max(
+            os.path.getmtime(src), os.path.getmtime(os.path.join(_HERE, "oracle.h"))):
+        return _LIB
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = _LIB + ".%d.tmp" % os.getpid()
+    subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fno-fast-math",
+                           "-ffp-contract=off", "-o", tmp, src, "-lm"])
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(build())
+        P = ctypes.POINTER
+        d, i, vp = ctypes.c_double, ctypes.c_int, ctypes.c_void_p
+        L.oracle_create.restype = vp
+        L.oracle_create.argtypes = [i, i, vp, vp, vp, vp, i, vp, vp, i, i, d, d, d, d, i,
+                                    d, d, d, i, i, i, i, d, d]
+        L.oracle_last_error.restype = ctypes.c_char_p
+        L.oracle_destroy.argtypes = [vp]
+        L.oracle_init_uniform.argtypes = [vp, d, d, d, d]
+        L.oracle_init_fields.argtypes = [vp, vp, vp, vp, vp]
+        L.oracle_step.argtypes = [vp, i, vp]
+        L.oracle_get_macro.argtypes = [vp] + [vp] * 6
+        L.oracle_get_f.argtypes = [vp, vp]
+        L.oracle_set_f.argtypes = [vp, vp]
+        L.oracle_get_wall.argtypes = [vp, i, P(i), vp, vp, vp]
+        L.oracle_set_bc.argtypes = [vp, i, d, d, d, d]
+        L.oracle_residual.argtypes = [vp, vp]
+        L.oracle_iterations.argtypes = [vp]
+        L.oracle_vgrid.argtypes = [i, d, d, i, vp, vp]
+        L.oracle_time_coeffs.argtypes = [d, d, vp]
+        L.oracle_time_coeffs.restype = None
+        L.oracle_micro_slope.argtypes = [vp, d, d, d, vp]
+        L.oracle_micro_slope.restype = None
+        L.oracle_vanleer.argtypes = [d, d]
+        L.oracle_vanleer.restype = d
+        L.oracle_mu_ref.argtypes = [d, d]
+        L.oracle_mu_ref.restype = d
+        L.oracle_wall_jacobian.argtypes = [vp, d, d, d, vp]
+        L.oracle_wall_jacobian.restype = None
+        L.oracle_wall_ghost.argtypes = [vp, d, d, d, vp]
+        L.oracle_wall_ghost.restype = None
+        L.oracle_stage_flux.argtypes = [vp, vp, vp, vp]
+        L.oracle_stage_sgs_micro.argtypes = [vp, i, vp, vp, vp, i]
+        L.oracle_stage_apply_micro.argtypes = [vp, i, vp, vp, vp]
+        L.oracle_stage_sgs_macro.argtypes = [vp, i, vp, vp, vp, vp, i]
+        L.oracle_stage_resid_macro.argtypes = [vp, i, vp, vp, vp]
+        L.oracle_stage_restrict.argtypes = [vp, i, i, vp, vp]
+        L.oracle_stage_prolong.argtypes = [vp, i, i, vp, vp]
+        L.oracle_level_size.argtypes = [vp, i, P(i), P(i)]
+        L.oracle_nv.argtypes = [vp]
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(st):
+    if st:
+        raise RuntimeError("oracle: " + lib().oracle_last_error().decode())
+
+
+class Oracle:
+    """One MIUGKS problem on the oracle.  ``case`` is a dict from
+    ``paper_1704_03151_gb300.workloads`` (mesh nodes, face BC ids, BC table,
+    velocity grid, gas and multigrid options)."""
+
+    def __init__(self, case):
+        L = lib()
+        self.case = case
+        self.nx, self.ny = case["nx"], case["ny"]
+        self.nc = self.nx * self.ny
+        self._keep = [np.ascontiguousarray(case[k], dtype=np.float64) for k in ("x_nodes", "y_nodes")]
+        self._keep += [np.ascontiguousarray(case[k], dtype=np.int32) for k in ("face_bc_x", "face_bc_y")]
+        bt = np.ascontiguousarray([b["type"] for b in case["bcs"]], dtype=np.int32)
+        bv = np.ascontiguousarray([[b["rho"], b["u"], b["v"], b["t"]] for b in case["bcs"]], dtype=np.float64)
+        self._keep += [bt, bv]
+        vg, gas, mg = case["vgrid"], case["gas"], case["mg"]
+        self.h = L.oracle_create(self.nx, self.ny, _p(self._keep[0]), _p(self._keep[1]), _p(self._keep[2]),
+                                 _p(self._keep[3]), len(bt), _p(bt), _p(bv),
+                                 vg["nu"], vg["nv"], vg["umin"], vg["umax"], vg["vmin"], vg["vmax"], vg["rule"],
+                                 gas["kn"], gas["omega"], gas["pr"],
+                                 mg["levels"], mg["nu1"], mg["nu2"], mg["nuc"], mg["cfl"], mg["dtn_growth"])
+        if not self.h:
+            raise RuntimeError("oracle_create: " + L.oracle_last_error().decode())
+        self.nv = L.oracle_nv(self.h)
+
+    def close(self):
+        if self.h:
+            lib().oracle_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_uniform(self, rho, u, v, t):
+        _check(lib().oracle_init_uniform(self.h, rho, u, v, t))
+
+    def init_fields(self, rho, u, v, t):
+        arrs = [np.ascontiguousarray(a, dtype=np.float64).ravel() for a in (rho, u, v, t)]
+        _check(lib().oracle_init_fields(self.h, *[_p(a) for a in arrs]))
+
+    def step(self, n=1):
+        res = np.zeros(4)
+        _check(lib().oracle_step(self.h, n, _p(res)))
+        return res
+
+    def residual(self):
+        R = np.zeros((self.nc, 4))
+        _check(lib().oracle_residual(self.h, _p(R)))
+        return R
+
+    def macro(self):
+        out = [np.zeros(self.nc) for _ in range(6)]
+        _check(lib().oracle_get_macro(self.h, *[_p(a) for a in out]))
+        return dict(zip(("rho", "u", "v", "t", "qx", "qy"), out))
+
+    def get_f(self):
+        f = np.zeros((2, self.nc, self.nv))
+        _check(lib().oracle_get_f(self.h, _p(f)))
+        return f
+
+    def set_f(self, f):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        _check(lib().oracle_set_f(self.h, _p(f)))
+
+    def set_bc(self, b, rho, u, v, t):
+        _check(lib().oracle_set_bc(self.h, b, rho, u, v, t))
+
+    def wall(self, bc):
+        n = ctypes.c_int(0)
+        lib().oracle_get_wall(self.h, bc, ctypes.byref(n), None, None, None)
+        cap = n.value
+        p, tau, q = np.zeros(cap), np.zeros(cap), np.zeros(cap)
+        n = ctypes.c_int(cap)
+        _check(lib().oracle_get_wall(self.h, bc, ctypes.byref(n), _p(p), _p(tau), _p(q)))
+        return p, tau, q
+
+    def iterations(self):
+        return lib().oracle_iterations(self.h)
+
+    # ---- stages for the pins ----
+    def level_size(self, lev):
+        nx, ny = ctypes.c_int(), ctypes.c_int()
+        _check(lib().oracle_level_size(self.h, lev, ctypes.byref(nx), ctypes.byref(ny)))
+        return nx.value, ny.value
+
+    def stage_flux(self):
+        nfx, nfy = (self.nx + 1) * self.ny, self.nx * (self.ny + 1)
+        R = np.zeros((self.nc, 4))
+        px, py = np.zeros((2, nfx, self.nv)), np.zeros((2, nfy, self.nv))
+        _check(lib().oracle_stage_flux(self.h, _p(R), _p(px), _p(py)))
+        return R, px, py
+
+    def sgs_micro(self, lev, inv_tau, r, order=0):
+        r = np.ascontiguousarray(r, dtype=np.float64)
+        it = np.ascontiguousarray(inv_tau, dtype=np.float64)
+        x = np.zeros_like(r)
+        _check(lib().oracle_stage_sgs_micro(self.h, lev, _p(it), _p(r), _p(x), order))
+        return x
+
+    def apply_micro(self, lev, inv_tau, x):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        it = np.ascontiguousarray(inv_tau, dtype=np.float64)
+        y = np.zeros_like(x)
+        _check(lib().oracle_stage_apply_micro(self.h, lev, _p(it), _p(x), _p(y)))
+        return y
+
+    def sgs_macro(self, lev, W, Wg, R, order=0):
+        W, Wg, R = (np.ascontiguousarray(a, dtype=np.float64) for a in (W, Wg, R))
+        dW = np.zeros_like(W)
+        _check(lib().oracle_stage_sgs_macro(self.h, lev, _p(W), _p(Wg), _p(R), _p(dW), order))
+        return dW
+
+    def resid_macro(self, lev, W, Wg):
+        W, Wg = (np.ascontiguousarray(a, dtype=np.float64) for a in (W, Wg))
+        RE = np.zeros_like(W)
+        _check(lib().oracle_stage_resid_macro(self.h, lev, _p(W), _p(Wg), _p(RE)))
+        return RE
+
+    def restrict(self, lev, fine):
+        fine = np.ascontiguousarray(fine, dtype=np.float64)
+        nx, ny = self.level_size(lev + 1)
+        m = fine.shape[-1]
+        coarse = np.zeros((nx * ny, m))
+        _check(lib().oracle_stage_restrict(self.h, lev, m, _p(fine), _p(coarse)))
+        return coarse
+
+    def prolong(self, lev, coarse):
+        coarse = np.ascontiguousarray(coarse, dtype=np.float64)
+        nx, ny = self.level_size(lev)
+        m = coarse.shape[-1]
+        fine = np.zeros((nx * ny, m))
+        _check(lib().oracle_stage_prolong(self.h, lev, m, _p(coarse), _p(fine)))
+        return fine
+
+
+def vgrid(n, a, b, rule):
+    x, w = np.zeros(n), np.zeros(n)
+    _check(lib().oracle_vgrid(n, a, b, rule, _p(x), _p(w)))
+    return x, w
+
+
+def time_coeffs(dt, tau):
+    q = np.zeros(5)
+    lib().oracle_time_coeffs(dt, tau, _p(q))
+    return q
+
+
+def micro_slope(dw, U, V, lam):
+    dw = np.ascontiguousarray(dw, dtype=np.float64)
+    a = np.zeros(4)
+    lib().oracle_micro_slope(_p(dw), U, V, lam, _p(a))
+    return a
+
+
+def vanleer(s1, s2):
+    return lib().oracle_vanleer(s1, s2)
+
+
+def mu_ref(kn, omega):
+    return lib().oracle_mu_ref(kn, omega)
+
+
+def wall_jacobian(W, Uw, Vw, Tw):
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    M = np.zeros(16)
+    lib().oracle_wall_jacobian(_p(W), Uw, Vw, Tw, _p(M))
+    return M.reshape(4, 4)
+
+
+def wall_ghost(W, Uw, Vw, Tw):
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    G = np.zeros(4)
+    lib().oracle_wall_ghost(_p(W), Uw, Vw, Tw, _p(G))
+    return G

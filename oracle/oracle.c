@@ -1,0 +1,1496 @@
+/*
+ * oracle.c -- plain serial FP64 CPU oracle of MIUGKS (arXiv 1704.03151).
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by the tests, the smoke check and the CPU
+ * baseline leg of the benchmark; never by the product library.  Written for
+ * readability against the paper, not for speed: straightforward loops in the
+ * order the paper states the steps.  Where the paper is silent the reading
+ * taken is stated at the function (and listed in the design notes).
+ *
+ * Parity pins (tests/test_oracle_*.py) cover every function here except the
+ * physical time step rule of face_dt(), which the paper leaves open and which
+ * is therefore "parity unpinned" (both implementations follow the same rule).
+ */
+#include "oracle.h"
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define KINT 1      /* internal (z-translational) degrees of freedom of the 2-D reduced model */
+#define MAXL 8
+#define PI 3.14159265358979323846
+
+static char g_err[512];
+static int fail(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return 1;
+}
+const char *oracle_last_error(void) { return g_err; }
+
+typedef struct { int type; double rho, u, v, t; } obc_t;
+
+typedef struct {
+    int nx, ny, nc, nfx, nfy;
+    double *xn, *yn, *xc, *yc, *dx, *dy;
+    int *fbx, *fby;
+    /* FAS work (nc x 4) and CS work (2 x nc x nv) */
+    double *Wn, *Wc, *Rc, *P, *RE, *dW, *Wtil;
+    double *r, *df, *dl, *Ad, *inv_tau;
+} olev_t;
+
+/* one boundary face of a cell, as seen from that cell */
+typedef struct { int bc, axis, outsign; double S, V; } bface_t;
+
+struct oracle_solver {
+    int L;
+    olev_t lev[MAXL];
+    int nu, nvv, nv;
+    double *u, *v, *w;
+    int *mxk, *myk;
+    double umax_abs, vmax_abs;
+    double kn, omega, pr, mu_ref;
+    int nbc;
+    obc_t *bc;
+    double *Cw; /* per BC: unit-density Maxwellian at the BC state, G part */
+    int nu1, nu2, nuc;
+    double cfl, dtn_growth, dtp_min;
+    int iter;
+    double *f, *W, *q, *R;
+    double *phx, *phy, *Fx, *Fy;
+    double *tmp0, *tmp1, *tmp2; /* per-face / per-cell velocity scratch (2 x nv each) */
+};
+
+/* ------------------------------------------------------------------ */
+/* Gas model and quadrature                                            */
+/* ------------------------------------------------------------------ */
+
+/* VHS reference viscosity for a given Knudsen number (alpha = 1), in units of
+ * rho0*L*sqrt(2RT0).  The paper relates Kn and viscosity through the VHS model
+ * (Sec. 4.1, 4.3) without printing the constant; this is the standard VHS
+ * mean-free-path relation. */
+double oracle_mu_ref(double kn, double omega)
+{
+    return 15.0 * sqrt(PI) * kn / (2.0 * (5.0 - 2.0 * omega) * (7.0 - 2.0 * omega));
+}
+
+/* Discrete velocity nodes and weights on [a, b] (Sec. 4.1: trapezoidal rule;
+ * Sec. 4.3: Newton-Cotes).  rule 0 = trapezoid, rule 1 = composite Boole
+ * (closed Newton-Cotes of degree 4, needs (n-1) % 4 == 0).  Nodes are placed
+ * symmetrically about the centre so that mirrored nodes negate exactly. */
+int oracle_vgrid(int n, double a, double b, int rule, double *x, double *w)
+{
+    if (n < 2 || !(b > a)) return fail("vgrid: need n >= 2 and b > a");
+    double h = (b - a) / (n - 1), c = 0.5 * (a + b);
+    for (int i = 0; i < n; ++i) x[i] = c + (i - 0.5 * (n - 1)) * h;
+    if (rule == 0) {
+        for (int i = 0; i < n; ++i) w[i] = h;
+        w[0] = w[n - 1] = 0.5 * h;
+    } else if (rule == 1) {
+        if ((n - 1) % 4) return fail("vgrid: Boole rule needs (n-1) %% 4 == 0");
+        for (int i = 0; i < n; ++i) w[i] = 0.0;
+        for (int p = 0; p + 4 < n; p += 4) {
+            w[p] += 7.0; w[p + 1] += 32.0; w[p + 2] += 12.0; w[p + 3] += 32.0; w[p + 4] += 7.0;
+        }
+        for (int i = 0; i < n; ++i) w[i] *= 2.0 * h / 45.0;
+    } else {
+        return fail("vgrid: unknown rule %d", rule);
+    }
+    return 0;
+}
+
+/* conservative -> primitive (rho, U, V, lambda); rho*eps = rho|U|^2/2 + (K+2) rho/(4 lambda) */
+static void prim(const double *W, double *rho, double *U, double *V, double *lam)
+{
+    *rho = W[0];
+    *U = W[1] / W[0];
+    *V = W[2] / W[0];
+    double eint = W[3] - 0.5 * (W[1] * W[1] + W[2] * W[2]) / W[0];
+    *lam = (KINT + 2) * W[0] / (4.0 * eint);
+}
+
+/* tau = mu/p with mu = mu_ref T^omega, p = rho T / 2 (Sec. 4.1) */
+static double tau_of(const oracle_solver *s, double rho, double lam)
+{
+    double T = 1.0 / lam;
+    return s->mu_ref * pow(T, s->omega) / (0.5 * rho * T);
+}
+
+/* reduced Maxwellian G at node k (Eq. f_on_wall form with R = 1/2) */
+static double maxw(double rho, double U, double V, double lam, double u, double v)
+{
+    return rho * (lam / PI) * exp(-lam * ((u - U) * (u - U) + (v - V) * (v - V)));
+}
+
+/* ------------------------------------------------------------------ */
+/* UGKS building blocks (the explicit flux is deferred by the paper to  */
+/* its references; these are the standard UGKS forms)                   */
+/* ------------------------------------------------------------------ */
+
+/* Time integrals of the integral solution over [0, dt] with collision time
+ * tau (x = dt/tau, e = exp(-x)):
+ *   q1 = dt - tau(1-e)                 (equilibrium)
+ *   q2 = -tau dt (1+e) + 2 tau^2 (1-e) (equilibrium spatial slope)
+ *   q3 = dt^2/2 - tau dt + tau^2 (1-e) (equilibrium time slope)
+ *   q4 = tau (1-e)                     (initial distribution)
+ *   q5 = tau dt e - tau^2 (1-e)        (initial slope)
+ * For x < 1 the cancelling forms are summed as power series in x. */
+void oracle_time_coeffs(double dt, double tau, double q[5])
+{
+    double x = dt / tau;
+    if (x < 1.0) {
+        double p[27];
+        p[0] = 1.0;
+        for (int n = 1; n < 27; ++n) p[n] = p[n - 1] * x / n; /* x^n / n! */
+        double s1 = 0, s2 = 0, s3 = 0, s4 = 0, s5 = 0;
+        for (int n = 0; n < 26; ++n) {
+            double sg = (n % 2) ? -1.0 : 1.0;      /* (-1)^n */
+            s4 += sg * p[n] / (n + 1);             /* sum_{n>=0} (-1)^n x^n/(n+1)! */
+            if (n >= 1) {
+                s1 += -sg * p[n] / (n + 1);                     /* (-1)^{n+1} x^n/(n+1)! */
+                s3 += -sg * p[n] / ((double)(n + 1) * (n + 2)); /* (-1)^{n+1} x^n/(n+2)! */
+            }
+            int m = n + 1;                                      /* m >= 1 */
+            double sm = (m % 2) ? -1.0 : 1.0;                   /* (-1)^m */
+            s5 += sm * p[m - 1] / (m + 1);                      /* (-1)^m m x^{m-1}/(m+1)! */
+            if (m >= 2) s2 += sm * (1.0 - m) * p[m - 1] / ((double)m * (m + 1));
+        }
+        q[0] = dt * s1;
+        q[1] = dt * dt * s2;
+        q[2] = dt * dt * s3;
+        q[3] = dt * s4;
+        q[4] = dt * dt * s5;
+    } else {
+        double e = exp(-x), E1 = -expm1(-x);
+        q[0] = dt - tau * E1;
+        q[1] = -tau * dt * (1.0 + e) + 2.0 * tau * tau * E1;
+        q[2] = 0.5 * dt * dt - tau * dt + tau * tau * E1;
+        q[3] = tau * E1;
+        q[4] = tau * dt * e - tau * tau * E1;
+    }
+}
+
+/* Micro-slope inversion: given the derivative of W divided by rho, dw, find
+ * a = (a1..a4) such that the (continuous) moments of (a1 + a2 u + a3 v +
+ * a4 (u^2+v^2+xi^2)/2) g reproduce it, g the Maxwellian at (U, V, lam). */
+void oracle_micro_slope(const double dw[4], double U, double V, double lam, double a[4])
+{
+    double Kp2 = KINT + 2.0;
+    double R4 = 2.0 * dw[3] - (U * U + V * V + Kp2 / (2.0 * lam)) * dw[0];
+    double R3 = dw[2] - V * dw[0];
+    double R2 = dw[1] - U * dw[0];
+    a[3] = 4.0 * lam * lam / Kp2 * (R4 - 2.0 * U * R2 - 2.0 * V * R3);
+    a[2] = 2.0 * lam * R3 - V * a[3];
+    a[1] = 2.0 * lam * R2 - U * a[3];
+    a[0] = dw[0] - U * a[1] - V * a[2] - 0.5 * a[3] * (U * U + V * V + Kp2 / (2.0 * lam));
+}
+
+/* van Leer limiter of two one-sided slopes */
+double oracle_vanleer(double s1, double s2)
+{
+    double p = s1 * s2;
+    return p > 0.0 ? 2.0 * p / (s1 + s2) : 0.0;
+}
+
+/* Physical time step of one face: CFL number times the smaller normal cell
+ * width over the largest normal discrete speed (Sec. 2.1: Delta t_p from a CFL
+ * condition with Courant number below 1; the exact rule is not printed). */
+static double face_dt(const oracle_solver *s, int axis, double hL, double hR)
+{
+    double um = axis == 0 ? s->umax_abs : s->vmax_abs;
+    return s->cfl * (hL < hR ? hL : hR) / um;
+}
+
+/* (a . psi) g split into the two reduced components, with
+ * b = a1 + a2 u + a3 v + a4 (u^2+v^2)/2:
+ *   G part: b gM + a4 hM,  H part: b hM + a4 <xi^4>/4 gM */
+static void slope_moments(const double a[4], double u, double v, double gM, double hM,
+                          double lam, double *mG, double *mH)
+{
+    double b = a[0] + a[1] * u + a[2] * v + 0.5 * a[3] * (u * u + v * v);
+    double xi4q = KINT * (KINT + 2.0) / (16.0 * lam * lam);
+    *mG = b * gM + a[3] * hM;
+    *mH = b * hM + a[3] * xi4q * gM;
+}
+
+/* ------------------------------------------------------------------ */
+/* Mesh levels                                                          */
+/* ------------------------------------------------------------------ */
+
+static double *dalloc(size_t n) { return (double *)calloc(n ? n : 1, sizeof(double)); }
+
+static int level_alloc(oracle_solver *s, olev_t *Lv)
+{
+    size_t nc = Lv->nc, nv = s->nv;
+    Lv->Wn = dalloc(4 * nc); Lv->Wc = dalloc(4 * nc); Lv->Rc = dalloc(4 * nc);
+    Lv->P = dalloc(4 * nc); Lv->RE = dalloc(4 * nc); Lv->dW = dalloc(4 * nc); Lv->Wtil = dalloc(4 * nc);
+    Lv->r = dalloc(2 * nc * nv); Lv->df = dalloc(2 * nc * nv); Lv->dl = dalloc(2 * nc * nv);
+    Lv->Ad = dalloc(2 * nc * nv); Lv->inv_tau = dalloc(nc);
+    if (!Lv->Wn || !Lv->Wc || !Lv->Rc || !Lv->P || !Lv->RE || !Lv->dW || !Lv->Wtil || !Lv->r ||
+        !Lv->df || !Lv->dl || !Lv->Ad || !Lv->inv_tau)
+        return fail("out of memory");
+    return 0;
+}
+
+static int level_geom(olev_t *Lv)
+{
+    int nx = Lv->nx, ny = Lv->ny;
+    Lv->xc = dalloc(nx); Lv->dx = dalloc(nx); Lv->yc = dalloc(ny); Lv->dy = dalloc(ny);
+    for (int i = 0; i < nx; ++i) {
+        Lv->dx[i] = Lv->xn[i + 1] - Lv->xn[i];
+        Lv->xc[i] = 0.5 * (Lv->xn[i] + Lv->xn[i + 1]);
+        if (!(Lv->dx[i] > 0)) return fail("x nodes must increase");
+    }
+    for (int j = 0; j < ny; ++j) {
+        Lv->dy[j] = Lv->yn[j + 1] - Lv->yn[j];
+        Lv->yc[j] = 0.5 * (Lv->yn[j] + Lv->yn[j + 1]);
+        if (!(Lv->dy[j] > 0)) return fail("y nodes must increase");
+    }
+    return 0;
+}
+
+/* Coarse grid by deleting every second grid line in each direction (Sec. 3.1). */
+static int coarsen(const olev_t *F, olev_t *C)
+{
+    if (F->nx % 2 || F->ny % 2) return fail("cannot coarsen %dx%d", F->nx, F->ny);
+    C->nx = F->nx / 2; C->ny = F->ny / 2; C->nc = C->nx * C->ny;
+    C->nfx = (C->nx + 1) * C->ny; C->nfy = C->nx * (C->ny + 1);
+    C->xn = dalloc(C->nx + 1); C->yn = dalloc(C->ny + 1);
+    for (int I = 0; I <= C->nx; ++I) C->xn[I] = F->xn[2 * I];
+    for (int J = 0; J <= C->ny; ++J) C->yn[J] = F->yn[2 * J];
+    C->fbx = (int *)calloc(C->nfx, sizeof(int));
+    C->fby = (int *)calloc(C->nfy, sizeof(int));
+    for (int J = 0; J < C->ny; ++J)
+        for (int I = 0; I <= C->nx; ++I) {
+            int a = F->fbx[(2 * J) * (F->nx + 1) + 2 * I], b = F->fbx[(2 * J + 1) * (F->nx + 1) + 2 * I];
+            if (a != b) return fail("coarse x-face (%d,%d) spans two boundary ids", I, J);
+            C->fbx[J * (C->nx + 1) + I] = a;
+        }
+    for (int J = 0; J <= C->ny; ++J)
+        for (int I = 0; I < C->nx; ++I) {
+            int a = F->fby[(2 * J) * F->nx + 2 * I], b = F->fby[(2 * J) * F->nx + 2 * I + 1];
+            if (a != b) return fail("coarse y-face (%d,%d) spans two boundary ids", I, J);
+            C->fby[J * C->nx + I] = a;
+        }
+    return level_geom(C);
+}
+
+/* Boundary faces of cell (i, j) on one sweep side: side 0 = lower (west, south),
+ * side 1 = upper (east, north), side 2 = all. */
+static int cell_bfaces(const olev_t *Lv, int i, int j, int side, bface_t *bf)
+{
+    int n = 0, nx = Lv->nx;
+    double V = Lv->dx[i] * Lv->dy[j];
+    if (side != 1 && i == 0) bf[n++] = (bface_t){Lv->fbx[j * (nx + 1)], 0, -1, Lv->dy[j], V};
+    if (side != 1 && j == 0) bf[n++] = (bface_t){Lv->fby[i], 1, -1, Lv->dx[i], V};
+    if (side != 0 && i == nx - 1) bf[n++] = (bface_t){Lv->fbx[j * (nx + 1) + nx], 0, +1, Lv->dy[j], V};
+    if (side != 0 && j == Lv->ny - 1) bf[n++] = (bface_t){Lv->fby[(Lv->ny) * nx + i], 1, +1, Lv->dx[i], V};
+    return n;
+}
+
+/* ------------------------------------------------------------------ */
+/* Step 1: explicit UGKS fluxes and residuals (Eqs. macroResidualDef,   */
+/* macroResidualCalc, microResidualDef)                                 */
+/* ------------------------------------------------------------------ */
+
+#define FIX(s, comp, c, k) ((s)->f[((size_t)(comp) * (s)->lev[0].nc + (c)) * (s)->nv + (k)])
+
+/* Interior face between cells cL (lower) and cR (upper) along `axis`; cLL /
+ * cRR are the next cells outward (-1 where the neighbour is a boundary ghost:
+ * first order there).  Writes the time-averaged micro flux per velocity
+ * (G, H) and the macro flux F = sum_k w psi flux.  */
+static void interior_face(oracle_solver *s, int axis, int cLL, int cL, int cR, int cRR,
+                          double dLLL, double dLR, double dRRR, double hL, double hR,
+                          double wL, double wR, double *phG, double *phH, double F[4])
+{
+    int nv = s->nv;
+    const double *u = s->u, *v = s->v, *w = s->w;
+    double *f0 = s->tmp0, *sg = s->tmp1; /* [comp][k] */
+    /* reconstruction (van Leer) and upwinding of the initial distribution */
+    for (int k = 0; k < nv; ++k) {
+        double un = axis == 0 ? u[k] : v[k];
+        for (int cp = 0; cp < 2; ++cp) {
+            double fL = FIX(s, cp, cL, k), fR = FIX(s, cp, cR, k);
+            double sL = 0.0, sR = 0.0;
+            if (cLL >= 0) sL = oracle_vanleer((fL - FIX(s, cp, cLL, k)) / dLLL, (fR - fL) / dLR);
+            if (cRR >= 0) sR = oracle_vanleer((fR - fL) / dLR, (FIX(s, cp, cRR, k) - fR) / dRRR);
+            double faceL = fL + sL * hL, faceR = fR - sR * hR;
+            if (un > 0) { f0[cp * nv + k] = faceL; sg[cp * nv + k] = sL; }
+            else if (un < 0) { f0[cp * nv + k] = faceR; sg[cp * nv + k] = sR; }
+            else { f0[cp * nv + k] = 0.5 * (faceL + faceR); sg[cp * nv + k] = 0.5 * (sL + sR); }
+        }
+    }
+    /* interface conservative variables from the upwinded distribution */
+    double W0[4] = {0, 0, 0, 0};
+    for (int k = 0; k < nv; ++k) {
+        double g = f0[k], h = f0[nv + k];
+        W0[0] += w[k] * g;
+        W0[1] += w[k] * u[k] * g;
+        W0[2] += w[k] * v[k] * g;
+        W0[3] += w[k] * (0.5 * (u[k] * u[k] + v[k] * v[k]) * g + h);
+    }
+    double rho0, U0, V0, lam0;
+    prim(W0, &rho0, &U0, &V0, &lam0);
+    double tau0 = tau_of(s, rho0, lam0);
+    double dt = face_dt(s, axis, wL, wR);
+    /* equilibrium slopes on either side from the cell averages */
+    const double *WL = s->W + 4 * cL, *WR = s->W + 4 * cR;
+    double dwl[4], dwr[4], aL[4], aR[4];
+    for (int m = 0; m < 4; ++m) {
+        dwl[m] = (W0[m] - WL[m]) / hL / rho0;
+        dwr[m] = (WR[m] - W0[m]) / hR / rho0;
+    }
+    oracle_micro_slope(dwl, U0, V0, lam0, aL);
+    oracle_micro_slope(dwr, U0, V0, lam0, aR);
+    /* heat flux of the interface distribution (Shakhov) and the time slope A
+     * from compatibility: sum_k w psi (u_n a + A) g0 = 0 */
+    double q0[2] = {0, 0}, Mt[4] = {0, 0, 0, 0};
+    for (int k = 0; k < nv; ++k) {
+        double cx = u[k] - U0, cy = v[k] - V0, c2 = cx * cx + cy * cy;
+        double g = f0[k], h = f0[nv + k];
+        q0[0] += w[k] * cx * (0.5 * c2 * g + h);
+        q0[1] += w[k] * cy * (0.5 * c2 * g + h);
+        double un = axis == 0 ? u[k] : v[k];
+        if (un == 0.0) continue;
+        double gM = maxw(rho0, U0, V0, lam0, u[k], v[k]), hM = gM * KINT / (4.0 * lam0);
+        double mG, mH;
+        slope_moments(un > 0 ? aL : aR, u[k], v[k], gM, hM, lam0, &mG, &mH);
+        Mt[0] += w[k] * un * mG;
+        Mt[1] += w[k] * un * u[k] * mG;
+        Mt[2] += w[k] * un * v[k] * mG;
+        Mt[3] += w[k] * un * (0.5 * (u[k] * u[k] + v[k] * v[k]) * mG + mH);
+    }
+    double dwt[4], A[4];
+    for (int m = 0; m < 4; ++m) dwt[m] = -Mt[m] / rho0;
+    oracle_micro_slope(dwt, U0, V0, lam0, A);
+    double qc[5];
+    oracle_time_coeffs(dt, tau0, qc);
+    double shk = (1.0 - s->pr) * 4.0 * lam0 * lam0 / (5.0 * rho0);
+    for (int m = 0; m < 4; ++m) F[m] = 0.0;
+    for (int k = 0; k < nv; ++k) {
+        double un = axis == 0 ? u[k] : v[k];
+        double cx = u[k] - U0, cy = v[k] - V0, c2 = cx * cx + cy * cy;
+        double gM = maxw(rho0, U0, V0, lam0, u[k], v[k]), hM = gM * KINT / (4.0 * lam0);
+        double Fq = shk * (cx * q0[0] + cy * q0[1]);
+        double gP = gM * (1.0 + Fq * (2.0 * lam0 * c2 - 4.0));
+        double hP = hM * (1.0 + Fq * (2.0 * lam0 * c2 - 2.0));
+        double mGa, mHa, mGA, mHA;
+        slope_moments(un > 0 ? aL : aR, u[k], v[k], gM, hM, lam0, &mGa, &mHa);
+        slope_moments(A, u[k], v[k], gM, hM, lam0, &mGA, &mHA);
+        double PG = un * (qc[0] * gP + qc[1] * un * mGa + qc[2] * mGA + qc[3] * f0[k] + qc[4] * un * sg[k]);
+        double PH = un * (qc[0] * hP + qc[1] * un * mHa + qc[2] * mHA + qc[3] * f0[nv + k] + qc[4] * un * sg[nv + k]);
+        phG[k] = PG / dt;
+        phH[k] = PH / dt;
+        F[0] += w[k] * phG[k];
+        F[1] += w[k] * u[k] * phG[k];
+        F[2] += w[k] * v[k] * phG[k];
+        F[3] += w[k] * (0.5 * (u[k] * u[k] + v[k] * v[k]) * phG[k] + phH[k]);
+    }
+}
+
+/* Distribution on a boundary face as seen from interior cell c (Sec. 3.2):
+ * wall: diffuse reflection, incoming rho_w C_k with rho_w from zero mass flux,
+ * both sums discrete; symmetry: mirrored velocity; farfield: freestream
+ * Maxwellian incoming; outflow: zero gradient.  Outgoing velocities carry the
+ * cell value (first order at boundaries). */
+static void boundary_face_f(const oracle_solver *s, int bcid, int axis, int outsign, int c,
+                            double *fG, double *fH)
+{
+    int nv = s->nv;
+    const obc_t *b = &s->bc[bcid];
+    double rhow = 0.0, lamw = 1.0 / b->t;
+    if (b->type == ORC_BC_WALL) {
+        double num = 0.0, den = 0.0;
+        for (int k = 0; k < nv; ++k) {
+            double uo = outsign * (axis == 0 ? s->u[k] : s->v[k]);
+            if (uo > 0) num += s->w[k] * uo * FIX(s, 0, c, k);
+            else if (uo < 0) den += s->w[k] * uo * s->Cw[(size_t)bcid * nv + k];
+        }
+        rhow = -num / den;
+    }
+    for (int k = 0; k < nv; ++k) {
+        double uo = outsign * (axis == 0 ? s->u[k] : s->v[k]);
+        if (uo >= 0 || b->type == ORC_BC_OUTFLOW) {
+            fG[k] = FIX(s, 0, c, k); fH[k] = FIX(s, 1, c, k);
+        } else if (b->type == ORC_BC_WALL) {
+            double C = s->Cw[(size_t)bcid * nv + k];
+            fG[k] = rhow * C; fH[k] = rhow * C * KINT / (4.0 * lamw);
+        } else if (b->type == ORC_BC_SYMMETRY) {
+            int km = axis == 0 ? s->mxk[k] : s->myk[k];
+            fG[k] = FIX(s, 0, c, km); fH[k] = FIX(s, 1, c, km);
+        } else { /* farfield */
+            double g = maxw(b->rho, b->u, b->v, lamw, s->u[k], s->v[k]);
+            fG[k] = g; fH[k] = g * KINT / (4.0 * lamw);
+        }
+    }
+}
+
+/* Boundary face flux: free transport of the face distribution, time-averaged,
+ * oriented along +axis like the interior faces. */
+static void boundary_face(oracle_solver *s, int bcid, int axis, int outsign, int c,
+                          double *phG, double *phH, double F[4])
+{
+    int nv = s->nv;
+    double *fG = s->tmp2, *fH = s->tmp2 + nv;
+    boundary_face_f(s, bcid, axis, outsign, c, fG, fH);
+    for (int m = 0; m < 4; ++m) F[m] = 0.0;
+    for (int k = 0; k < nv; ++k) {
+        double un = axis == 0 ? s->u[k] : s->v[k];
+        phG[k] = un * fG[k];
+        phH[k] = un * fH[k];
+        F[0] += s->w[k] * phG[k];
+        F[1] += s->w[k] * s->u[k] * phG[k];
+        F[2] += s->w[k] * s->v[k] * phG[k];
+        F[3] += s->w[k] * (0.5 * (s->u[k] * s->u[k] + s->v[k] * s->v[k]) * phG[k] + phH[k]);
+    }
+}
+
+/* All face fluxes on level 0 and the macroscopic residual
+ * R_i = -(1/V_i) sum_j S_ij F_ij (Eq. macroResidualDef). */
+static void flux_stage(oracle_solver *s)
+{
+    olev_t *Lv = &s->lev[0];
+    int nx = Lv->nx, ny = Lv->ny, nv = s->nv;
+    size_t nfx = Lv->nfx, nfy = Lv->nfy;
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i <= nx; ++i) {
+            int fi = j * (nx + 1) + i;
+            double *pG = s->phx + (size_t)fi * nv, *pH = s->phx + (nfx + fi) * (size_t)nv;
+            int bcid = Lv->fbx[fi];
+            if (bcid >= 0) {
+                if (i == 0) boundary_face(s, bcid, 0, -1, j * nx, pG, pH, s->Fx + 4 * fi);
+                else boundary_face(s, bcid, 0, +1, j * nx + nx - 1, pG, pH, s->Fx + 4 * fi);
+                continue;
+            }
+            int cL = j * nx + i - 1, cR = j * nx + i;
+            int hasLL = (i - 1 > 0) && Lv->fbx[fi - 1] < 0;
+            int hasRR = (i + 1 < nx) && Lv->fbx[fi + 1] < 0;
+            interior_face(s, 0, hasLL ? cL - 1 : -1, cL, cR, hasRR ? cR + 1 : -1,
+                          hasLL ? Lv->xc[i - 1] - Lv->xc[i - 2] : 1.0, Lv->xc[i] - Lv->xc[i - 1],
+                          hasRR ? Lv->xc[i + 1] - Lv->xc[i] : 1.0,
+                          Lv->xn[i] - Lv->xc[i - 1], Lv->xc[i] - Lv->xn[i],
+                          Lv->dx[i - 1], Lv->dx[i], pG, pH, s->Fx + 4 * fi);
+        }
+    for (int j = 0; j <= ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            int fi = j * nx + i;
+            double *pG = s->phy + (size_t)fi * nv, *pH = s->phy + (nfy + fi) * (size_t)nv;
+            int bcid = Lv->fby[fi];
+            if (bcid >= 0) {
+                if (j == 0) boundary_face(s, bcid, 1, -1, i, pG, pH, s->Fy + 4 * fi);
+                else boundary_face(s, bcid, 1, +1, (ny - 1) * nx + i, pG, pH, s->Fy + 4 * fi);
+                continue;
+            }
+            int cL = (j - 1) * nx + i, cR = j * nx + i;
+            int hasLL = (j - 1 > 0) && Lv->fby[fi - nx] < 0;
+            int hasRR = (j + 1 < ny) && Lv->fby[fi + nx] < 0;
+            interior_face(s, 1, hasLL ? cL - nx : -1, cL, cR, hasRR ? cR + nx : -1,
+                          hasLL ? Lv->yc[j - 1] - Lv->yc[j - 2] : 1.0, Lv->yc[j] - Lv->yc[j - 1],
+                          hasRR ? Lv->yc[j + 1] - Lv->yc[j] : 1.0,
+                          Lv->yn[j] - Lv->yc[j - 1], Lv->yc[j] - Lv->yn[j],
+                          Lv->dy[j - 1], Lv->dy[j], pG, pH, s->Fy + 4 * fi);
+        }
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            int c = j * nx + i;
+            double V = Lv->dx[i] * Lv->dy[j];
+            const double *FW = s->Fx + 4 * (j * (nx + 1) + i), *FE = FW + 4;
+            const double *FS = s->Fy + 4 * (j * nx + i), *FN = s->Fy + 4 * ((j + 1) * nx + i);
+            for (int m = 0; m < 4; ++m)
+                s->R[4 * c + m] = -(Lv->dy[j] * (FE[m] - FW[m]) + Lv->dx[i] * (FN[m] - FS[m])) / V;
+        }
+}
+
+/* ------------------------------------------------------------------ */
+/* Prediction step: split Euler flux, FAS (Secs. 2.1.1, 2.3, 2.4, 3.2) */
+/* ------------------------------------------------------------------ */
+
+/* Euler flux T(W).n */
+static void euler_flux(const double *W, int axis, double sgn, double T[4])
+{
+    double rho, U, V, lam;
+    prim(W, &rho, &U, &V, &lam);
+    double p = rho / (2.0 * lam);
+    double nx_ = axis == 0 ? sgn : 0.0, ny_ = axis == 1 ? sgn : 0.0;
+    double Un = U * nx_ + V * ny_;
+    T[0] = rho * Un;
+    T[1] = W[1] * Un + p * nx_;
+    T[2] = W[2] * Un + p * ny_;
+    T[3] = (W[3] + p) * Un;
+}
+
+/* Ghost state W_j = B(W_i) of a boundary face and its Jacobian dB/dW
+ * (Eqs. boundaryRelation, boundaryWall, example_results).  Reading of the
+ * garbled wall relation: rho_j V_j = 2 rho_i V_w - rho_i V_i, and U_0, V_0 in
+ * the Jacobian are the wall velocity. */
+void oracle_wall_ghost(const double W[4], double Uw, double Vw, double Tw, double Wg[4])
+{
+    double rho, U, V, lam;
+    prim(W, &rho, &U, &V, &lam);
+    double lamg = 2.0 / Tw - lam, Ug = 2.0 * Uw - U, Vg = 2.0 * Vw - V;
+    Wg[0] = rho;
+    Wg[1] = rho * Ug;
+    Wg[2] = rho * Vg;
+    Wg[3] = 0.5 * rho * (Ug * Ug + Vg * Vg) + (KINT + 2) * rho / (4.0 * lamg);
+}
+
+void oracle_wall_jacobian(const double W[4], double Uw, double Vw, double Tw, double M[16])
+{
+    double rho, U, V, lam;
+    prim(W, &rho, &U, &V, &lam);
+    double lamw = 1.0 / Tw, Y = lam / (lam - 2.0 * lamw), K = KINT + 2.0;
+    memset(M, 0, 16 * sizeof(double));
+    M[0] = 1.0;
+    M[4] = 2.0 * Uw; M[5] = -1.0;
+    M[8] = 2.0 * Vw; M[10] = -1.0;
+    M[12] = 2.0 * (Uw * Uw + Vw * Vw) - 0.5 * (U * U + V * V) * (1.0 + Y * Y) + K / (4.0 * lam) * (Y * Y - Y);
+    M[13] = U - 2.0 * Uw + U * Y * Y;
+    M[14] = V - 2.0 * Vw + V * Y * Y;
+    M[15] = -Y * Y;
+}
+
+static void macro_ghost(const oracle_solver *s, int bcid, int axis, const double *Wi, double Wg[4], double M[16])
+{
+    const obc_t *b = &s->bc[bcid];
+    if (b->type == ORC_BC_WALL) {
+        oracle_wall_ghost(Wi, b->u, b->v, b->t, Wg);
+        if (M) oracle_wall_jacobian(Wi, b->u, b->v, b->t, M);
+    } else if (b->type == ORC_BC_SYMMETRY) {
+        for (int m = 0; m < 4; ++m) Wg[m] = Wi[m];
+        Wg[1 + axis] = -Wi[1 + axis];
+        if (M) {
+            memset(M, 0, 16 * sizeof(double));
+            for (int m = 0; m < 4; ++m) M[5 * m] = 1.0;
+            M[5 * (1 + axis)] = -1.0;
+        }
+    } else if (b->type == ORC_BC_FARFIELD) {
+        double lam = 1.0 / b->t;
+        Wg[0] = b->rho; Wg[1] = b->rho * b->u; Wg[2] = b->rho * b->v;
+        Wg[3] = 0.5 * b->rho * (b->u * b->u + b->v * b->v) + (KINT + 2) * b->rho / (4.0 * lam);
+        if (M) memset(M, 0, 16 * sizeof(double));
+    } else {
+        for (int m = 0; m < 4; ++m) Wg[m] = Wi[m];
+        if (M) {
+            memset(M, 0, 16 * sizeof(double));
+            for (int m = 0; m < 4; ++m) M[5 * m] = 1.0;
+        }
+    }
+}
+
+/* Gamma_ij = |U_ij . n| + a_s + 2 nu / (n . (x_j - x_i)) at the arithmetic mean
+ * of the two conservative states (Eq. predictionSpectralRadius). */
+static double gamma_face(const oracle_solver *s, const double *Wa, const double *Wb, int axis, double dist)
+{
+    double Wm[4], rho, U, V, lam;
+    for (int m = 0; m < 4; ++m) Wm[m] = 0.5 * (Wa[m] + Wb[m]);
+    prim(Wm, &rho, &U, &V, &lam);
+    double gam = (KINT + 4.0) / (KINT + 2.0);
+    double as = sqrt(gam / (2.0 * lam));
+    double nu = s->mu_ref * pow(1.0 / lam, s->omega) / rho;
+    return fabs(axis == 0 ? U : V) + as + 2.0 * nu / dist;
+}
+
+/* split flux 1/2 [T_a + T_b + Gamma (W_a - W_b)] along the normal from a to b (Eq. macroFluxSplitting) */
+static void split_flux(const double *Wa, const double *Wb, int axis, double sgn, double gam, double F[4])
+{
+    double Ta[4], Tb[4];
+    euler_flux(Wa, axis, sgn, Ta);
+    euler_flux(Wb, axis, sgn, Tb);
+    for (int m = 0; m < 4; ++m) F[m] = 0.5 * (Ta[m] + Tb[m] + gam * (Wa[m] - Wb[m]));
+}
+
+/* Gamma of the four faces of cell c on level Lv, from the frozen state Wg */
+static void cell_gammas(const oracle_solver *s, const olev_t *Lv, const double *Wg, int i, int j, double gm[4])
+{
+    int nx = Lv->nx, ny = Lv->ny, c = j * nx + i;
+    double G[4];
+    /* west, east, south, north */
+    for (int f = 0; f < 4; ++f) {
+        int axis = f / 2, up = f % 2;
+        int bcid = axis == 0 ? Lv->fbx[j * (nx + 1) + i + up] : Lv->fby[(j + up) * nx + i];
+        if (bcid >= 0) {
+            macro_ghost(s, bcid, axis, Wg + 4 * c, G, NULL);
+            gm[f] = gamma_face(s, Wg + 4 * c, G, axis, axis == 0 ? Lv->dx[i] : Lv->dy[j]);
+        } else {
+            int nb = axis == 0 ? c + (up ? 1 : -1) : c + (up ? nx : -nx);
+            double dist = axis == 0 ? fabs(Lv->xc[i + (up ? 1 : -1)] - Lv->xc[i])
+                                    : fabs(Lv->yc[j + (up ? 1 : -1)] - Lv->yc[j]);
+            gm[f] = gamma_face(s, Wg + 4 * c, Wg + 4 * nb, axis, dist);
+        }
+    }
+    (void)ny;
+}
+
+/* R_E(W) = -(1/V_i) sum_j S_ij F_split(W_i, W_j), Gamma frozen at Wg (Eq. forcingFunction) */
+static void resid_macro(const oracle_solver *s, const olev_t *Lv, const double *W, const double *Wg, double *RE)
+{
+    int nx = Lv->nx, ny = Lv->ny;
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            int c = j * nx + i;
+            double V = Lv->dx[i] * Lv->dy[j], gm[4], acc[4] = {0, 0, 0, 0};
+            cell_gammas(s, Lv, Wg, i, j, gm);
+            for (int f = 0; f < 4; ++f) {
+                int axis = f / 2, up = f % 2;
+                double sgn = up ? 1.0 : -1.0, S = axis == 0 ? Lv->dy[j] : Lv->dx[i], F[4], G[4];
+                int bcid = axis == 0 ? Lv->fbx[j * (nx + 1) + i + up] : Lv->fby[(j + up) * nx + i];
+                if (bcid >= 0) {
+                    macro_ghost(s, bcid, axis, W + 4 * c, G, NULL);
+                    split_flux(W + 4 * c, G, axis, sgn, gm[f], F);
+                } else {
+                    int nb = axis == 0 ? c + (up ? 1 : -1) : c + (up ? nx : -nx);
+                    split_flux(W + 4 * c, W + 4 * nb, axis, sgn, gm[f], F);
+                }
+                for (int m = 0; m < 4; ++m) acc[m] += S * F[m];
+            }
+            for (int m = 0; m < 4; ++m) RE[4 * c + m] = -acc[m] / V;
+        }
+}
+
+static double dtn_inv(const oracle_solver *s)
+{
+    if (!(s->dtn_growth > 0.0)) return 0.0;
+    return 1.0 / (pow(s->dtn_growth, (double)s->iter) * s->dtp_min);
+}
+
+/* One LU-SGS pass of Eq. macroFinalDefect with the split flux: forward sweep
+ * with the lower neighbours (west, south), backward sweep with the upper ones
+ * (east, north).  Boundary ghosts dW_j = (dB/dW) dW_i take dW_i from the
+ * previous half sweep (zero in the forward sweep).  order 1 runs the same
+ * sweeps over anti-diagonals (identical arithmetic per cell). */
+static void sgs_macro(const oracle_solver *s, const olev_t *Lv, const double *W, const double *Wg,
+                      const double *R, double *dW, int order)
+{
+    int nx = Lv->nx, ny = Lv->ny, nd = nx + ny - 1;
+    double add = dtn_inv(s);
+    for (int pass = 0; pass < 2; ++pass) {
+        int ncell = nx * ny;
+        for (int t = 0; t < ncell; ++t) {
+            int i, j;
+            if (order == 0) {
+                int tt = pass == 0 ? t : ncell - 1 - t;
+                i = tt % nx; j = tt / nx;
+            } else {
+                /* t-th cell in diagonal order */
+                int cnt = 0, found = 0;
+                for (int d0 = 0; d0 < nd && !found; ++d0) {
+                    int d = pass == 0 ? d0 : nd - 1 - d0;
+                    int ilo = d - (ny - 1) > 0 ? d - (ny - 1) : 0, ihi = d < nx - 1 ? d : nx - 1;
+                    if (t < cnt + (ihi - ilo + 1)) {
+                        int off = t - cnt;
+                        i = pass == 0 ? ilo + off : ihi - off;
+                        j = d - i;
+                        found = 1;
+                    }
+                    cnt += ihi - ilo + 1;
+                }
+            }
+            int c = j * nx + i;
+            double V = Lv->dx[i] * Lv->dy[j], gm[4];
+            cell_gammas(s, Lv, Wg, i, j, gm);
+            double diag = 0.0;
+            for (int f = 0; f < 4; ++f) diag += (f / 2 == 0 ? Lv->dy[j] : Lv->dx[i]) * gm[f];
+            diag = diag / (2.0 * V) + add;
+            double acc[4] = {0, 0, 0, 0};
+            for (int f = 0; f < 4; ++f) {
+                int axis = f / 2, up = f % 2;
+                if (up != pass) continue; /* forward: lower faces, backward: upper faces */
+                double sgn = up ? 1.0 : -1.0, S = axis == 0 ? Lv->dy[j] : Lv->dx[i];
+                int bcid = axis == 0 ? Lv->fbx[j * (nx + 1) + i + up] : Lv->fby[(j + up) * nx + i];
+                double Wn[4], dWn[4], Wp[4], T1[4], T0[4];
+                if (bcid >= 0) {
+                    double M[16];
+                    macro_ghost(s, bcid, axis, W + 4 * c, Wn, M);
+                    for (int m = 0; m < 4; ++m) {
+                        dWn[m] = 0.0;
+                        if (pass == 1)
+                            for (int q = 0; q < 4; ++q) dWn[m] += M[4 * m + q] * dW[4 * c + q];
+                    }
+                } else {
+                    int nb = axis == 0 ? c + (up ? 1 : -1) : c + (up ? nx : -nx);
+                    for (int m = 0; m < 4; ++m) { Wn[m] = W[4 * nb + m]; dWn[m] = dW[4 * nb + m]; }
+                }
+                for (int m = 0; m < 4; ++m) Wp[m] = Wn[m] + dWn[m];
+                euler_flux(Wp, axis, sgn, T1);
+                euler_flux(Wn, axis, sgn, T0);
+                for (int m = 0; m < 4; ++m) acc[m] += S * ((T1[m] - T0[m]) - gm[f] * dWn[m]);
+            }
+            if (pass == 0)
+                for (int m = 0; m < 4; ++m) dW[4 * c + m] = (R[4 * c + m] - acc[m] / (2.0 * V)) / diag;
+            else
+                for (int m = 0; m < 4; ++m) dW[4 * c + m] = dW[4 * c + m] - acc[m] / (2.0 * V * diag);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Transfer operators (Secs. 2.3.1, 2.3.3)                             */
+/* ------------------------------------------------------------------ */
+
+/* Volume-weighted restriction of an [cell][m] array from level l to l+1 */
+static void restrict_lv(const olev_t *F, const olev_t *C, int m, const double *fine, double *coarse)
+{
+    for (int J = 0; J < C->ny; ++J)
+        for (int I = 0; I < C->nx; ++I) {
+            double *out = coarse + (size_t)(J * C->nx + I) * m;
+            double vs = 0.0;
+            for (int q = 0; q < m; ++q) out[q] = 0.0;
+            for (int b = 0; b < 2; ++b)
+                for (int a = 0; a < 2; ++a) {
+                    int i = 2 * I + a, j = 2 * J + b;
+                    double V = F->dx[i] * F->dy[j];
+                    const double *in = fine + (size_t)(j * F->nx + i) * m;
+                    for (int q = 0; q < m; ++q) out[q] += in[q] * V;
+                    vs += V;
+                }
+            for (int q = 0; q < m; ++q) out[q] /= vs;
+        }
+}
+
+/* 1-D linear weights for a fine centre x in coarse cell I: the second coarse
+ * cell is the neighbour on the side of x, or the one on the other side when
+ * that neighbour does not exist (extrapolation, signed weights). */
+static void lin1d(const double *Xc, int n, int I, double x, int *N, double *wA, double *wN)
+{
+    int nb = x < Xc[I] ? I - 1 : I + 1;
+    if (nb < 0 || nb >= n) nb = x < Xc[I] ? I + 1 : I - 1;
+    if (nb < 0 || nb >= n) { *N = I; *wA = 1.0; *wN = 0.0; return; }
+    *N = nb;
+    *wA = (Xc[nb] - x) / (Xc[nb] - Xc[I]);
+    *wN = (x - Xc[I]) / (Xc[nb] - Xc[I]);
+}
+
+/* Bilinear prolongation from level l+1 to l (Eqs. prolongation, prolongationWeight):
+ * on a rectilinear mesh the weights h_BC h_CD / S_ABCD etc. are the products of
+ * the 1-D linear weights in each direction. */
+static void prolong_lv(const olev_t *F, const olev_t *C, int m, const double *coarse, double *fine)
+{
+    for (int j = 0; j < F->ny; ++j)
+        for (int i = 0; i < F->nx; ++i) {
+            int I = i / 2, J = j / 2, IN, JN;
+            double ax, bx, ay, by;
+            lin1d(C->xc, C->nx, I, F->xc[i], &IN, &ax, &bx);
+            lin1d(C->yc, C->ny, J, F->yc[j], &JN, &ay, &by);
+            const double *A = coarse + (size_t)(J * C->nx + I) * m, *B = coarse + (size_t)(J * C->nx + IN) * m;
+            const double *D = coarse + (size_t)(JN * C->nx + I) * m, *Cc = coarse + (size_t)(JN * C->nx + IN) * m;
+            double *out = fine + (size_t)(j * F->nx + i) * m;
+            for (int q = 0; q < m; ++q)
+                out[q] = ax * ay * A[q] + bx * ay * B[q] + ax * by * D[q] + bx * by * Cc[q];
+        }
+}
+
+/* FAS cycle (Eq. FASCYC): W_l <- FAS(l, W_l^n, R_l); lv->Wn holds W_l^n and
+ * lv->Rc the restricted (or UGKS) residual on entry; the result is left in lv->Wc. */
+static void fas(oracle_solver *s, int l)
+{
+    olev_t *Lv = &s->lev[l];
+    size_t n4 = 4 * (size_t)Lv->nc;
+    resid_macro(s, Lv, Lv->Wn, Lv->Wn, Lv->RE);
+    for (size_t q = 0; q < n4; ++q) Lv->P[q] = Lv->Rc[q] - Lv->RE[q]; /* forcing function */
+    memcpy(Lv->Wc, Lv->Wn, n4 * sizeof(double));
+    double *R = (double *)malloc(n4 * sizeof(double));
+    memcpy(R, Lv->Rc, n4 * sizeof(double));
+    int coarsest = (l == s->L - 1);
+    int npre = coarsest ? (s->L == 1 ? 1 : s->nuc) : s->nu1;
+    for (int m = 0; m < npre; ++m) {
+        sgs_macro(s, Lv, Lv->Wc, Lv->Wn, R, Lv->dW, 0);
+        for (size_t q = 0; q < n4; ++q) Lv->Wc[q] += Lv->dW[q];
+        if (coarsest && m == npre - 1) break;
+        resid_macro(s, Lv, Lv->Wc, Lv->Wn, Lv->RE); /* renewal, Eq. renewResiduals */
+        for (size_t q = 0; q < n4; ++q) R[q] = Lv->P[q] + Lv->RE[q];
+    }
+    if (!coarsest) {
+        olev_t *Cv = &s->lev[l + 1];
+        restrict_lv(Lv, Cv, 4, Lv->Wc, Cv->Wn);
+        restrict_lv(Lv, Cv, 4, R, Cv->Rc);
+        fas(s, l + 1);
+        size_t c4 = 4 * (size_t)Cv->nc;
+        for (size_t q = 0; q < c4; ++q) Cv->dW[q] = Cv->Wc[q] - Cv->Wn[q];
+        double *corr = (double *)malloc(n4 * sizeof(double));
+        prolong_lv(Lv, Cv, 4, Cv->dW, corr);
+        for (size_t q = 0; q < n4; ++q) Lv->Wc[q] += corr[q];
+        free(corr);
+        for (int m = 0; m < s->nu2; ++m) {
+            resid_macro(s, Lv, Lv->Wc, Lv->Wn, Lv->RE);
+            for (size_t q = 0; q < n4; ++q) R[q] = Lv->P[q] + Lv->RE[q];
+            sgs_macro(s, Lv, Lv->Wc, Lv->Wn, R, Lv->dW, 0);
+            for (size_t q = 0; q < n4; ++q) Lv->Wc[q] += Lv->dW[q];
+        }
+    }
+    free(R);
+}
+
+/* ------------------------------------------------------------------ */
+/* Evolution step: upwind micro system, LU-SGS, CS cycle (Secs. 2.1.2,  */
+/* 2.3, 2.4, 3.2)                                                       */
+/* ------------------------------------------------------------------ */
+
+/* D_{i,k} = 1/tau_i (+1/dt_n) + (1/V_i) sum_{u_n > 0} u_n S_ij (Eq. evolutionCoefficients) */
+static double Dii(const oracle_solver *s, const olev_t *Lv, int i, int j, double inv_tau, int k)
+{
+    double V = Lv->dx[i] * Lv->dy[j];
+    return inv_tau + (fabs(s->u[k]) * Lv->dy[j] + fabs(s->v[k]) * Lv->dx[i]) / V;
+}
+
+/* D_{j,k} = (1/V_i) u_n S_ij for u_n < 0 through a face with outward normal outsign*axis */
+static double Dij(const oracle_solver *s, int axis, int outsign, double S, double V, int k)
+{
+    double un = outsign * (axis == 0 ? s->u[k] : s->v[k]);
+    return un < 0 ? un * S / V : 0.0;
+}
+
+static double wallC(const oracle_solver *s, int bcid, int comp, int k)
+{
+    double C = s->Cw[(size_t)bcid * s->nv + k];
+    return comp == 0 ? C : C * KINT * s->bc[bcid].t / 4.0;
+}
+
+/* Solve one cell's own equations for one sweep side given base_k:
+ *   D_k x_k + sum_{b: k incoming at b} D_bk ghost_bk(x) = base_k
+ * Ghosts (Sec. 3.2): wall  rho_b C_k with rho_b = -sum_{out} w u_n x_k,G / sum_{in} w u_n C_k;
+ * symmetry x_{k'} (mirror); farfield 0; outflow x_k.  Two walls on the same
+ * side (a corner) couple through a 2x2 system for the two densities; every
+ * other combination is resolved exactly by three substitution rounds. */
+static void cell_solve(const oracle_solver *s, int c, int nb, const bface_t *bf, const double *D,
+                       const double *base, double *x)
+{
+    int nv = s->nv;
+    size_t nc = s->lev[0].nc; (void)nc;
+    double *den = s->tmp0, *xo = s->tmp1;
+    for (int k = 0; k < nv; ++k) {
+        den[k] = D[k];
+        for (int b = 0; b < nb; ++b)
+            if (s->bc[bf[b].bc].type == ORC_BC_OUTFLOW) den[k] += Dij(s, bf[b].axis, bf[b].outsign, bf[b].S, bf[b].V, k);
+    }
+    int nwall = 0;
+    for (int b = 0; b < nb; ++b) nwall += s->bc[bf[b].bc].type == ORC_BC_WALL;
+    double Z[4], rho[4];
+    for (int b = 0; b < nb; ++b) {
+        Z[b] = 0.0;
+        if (s->bc[bf[b].bc].type != ORC_BC_WALL) continue;
+        for (int k = 0; k < nv; ++k) {
+            double uo = bf[b].outsign * (bf[b].axis == 0 ? s->u[k] : s->v[k]);
+            if (uo < 0) Z[b] += s->w[k] * uo * wallC(s, bf[b].bc, 0, k);
+        }
+    }
+    if (nwall == 2 && nb == 2) {
+        double cc[2] = {0, 0}, mm[2] = {0, 0}; /* mm[b] couples b to the other wall */
+        for (int b = 0; b < 2; ++b) {
+            int o = 1 - b;
+            for (int k = 0; k < nv; ++k) {
+                double uo = bf[b].outsign * (bf[b].axis == 0 ? s->u[k] : s->v[k]);
+                if (!(uo > 0)) continue;
+                cc[b] += s->w[k] * uo * base[k] / den[k];
+                double Do = Dij(s, bf[o].axis, bf[o].outsign, bf[o].S, bf[o].V, k);
+                if (Do != 0.0) mm[b] += s->w[k] * uo * Do * wallC(s, bf[o].bc, 0, k) / den[k];
+            }
+            cc[b] = -cc[b] / Z[b];
+            mm[b] = mm[b] / Z[b];
+        }
+        rho[0] = (cc[0] + mm[0] * cc[1]) / (1.0 - mm[0] * mm[1]);
+        rho[1] = cc[1] + mm[1] * rho[0];
+        for (int cp = 0; cp < 2; ++cp)
+            for (int k = 0; k < nv; ++k) {
+                double acc = base[cp * nv + k];
+                for (int b = 0; b < 2; ++b) {
+                    double Db = Dij(s, bf[b].axis, bf[b].outsign, bf[b].S, bf[b].V, k);
+                    if (Db != 0.0) acc -= Db * wallC(s, bf[b].bc, cp, k) * rho[b];
+                }
+                x[cp * nv + k] = acc / den[k];
+            }
+        return;
+    }
+    for (int cp = 0; cp < 2; ++cp)
+        for (int k = 0; k < nv; ++k) x[cp * nv + k] = base[cp * nv + k] / den[k];
+    double *xs = (double *)malloc(2 * (size_t)nv * sizeof(double));
+    for (int round = 0; round < 3; ++round) {
+        memcpy(xs, x, 2 * (size_t)nv * sizeof(double));
+        for (int b = 0; b < nb; ++b) {
+            if (s->bc[bf[b].bc].type != ORC_BC_WALL) continue;
+            double num = 0.0;
+            for (int k = 0; k < nv; ++k) {
+                double uo = bf[b].outsign * (bf[b].axis == 0 ? s->u[k] : s->v[k]);
+                if (uo > 0) num += s->w[k] * uo * xs[k];
+            }
+            rho[b] = -num / Z[b];
+        }
+        for (int cp = 0; cp < 2; ++cp)
+            for (int k = 0; k < nv; ++k) {
+                double acc = base[cp * nv + k];
+                for (int b = 0; b < nb; ++b) {
+                    double Db = Dij(s, bf[b].axis, bf[b].outsign, bf[b].S, bf[b].V, k);
+                    if (Db == 0.0) continue;
+                    int t = s->bc[bf[b].bc].type;
+                    if (t == ORC_BC_WALL) acc -= Db * wallC(s, bf[b].bc, cp, k) * rho[b];
+                    else if (t == ORC_BC_SYMMETRY) {
+                        int km = bf[b].axis == 0 ? s->mxk[k] : s->myk[k];
+                        acc -= Db * xs[cp * nv + km];
+                    }
+                }
+                x[cp * nv + k] = acc / den[k];
+            }
+    }
+    free(xs);
+    (void)xo; (void)c;
+}
+
+#define AT(arr, nc_, nv_, cp, c, k) ((arr)[((size_t)(cp) * (nc_) + (c)) * (nv_) + (k)])
+
+/* One symmetric Gauss-Seidel pass (LU-SGS) on Eq. microFinalDefect:
+ * forward  (D + L) x* = r, backward (D + U) x = D x*, lower = west/south
+ * neighbours and ghosts, upper = east/north.  order 1 = anti-diagonal
+ * wavefront order (same arithmetic per cell). */
+static void sgs_micro(oracle_solver *s, const olev_t *Lv, const double *inv_tau, const double *r, double *x, int order)
+{
+    int nx = Lv->nx, ny = Lv->ny, nv = s->nv, nd = nx + ny - 1;
+    size_t nc = Lv->nc;
+    double *D = dalloc(nv), *base = dalloc(2 * (size_t)nv), *xc = dalloc(2 * (size_t)nv);
+    for (int pass = 0; pass < 2; ++pass) {
+        int ncell = nx * ny;
+        for (int t = 0; t < ncell; ++t) {
+            int i = 0, j = 0;
+            if (order == 0) {
+                int tt = pass == 0 ? t : ncell - 1 - t;
+                i = tt % nx; j = tt / nx;
+            } else {
+                int cnt = 0, found = 0;
+                for (int d0 = 0; d0 < nd && !found; ++d0) {
+                    int d = pass == 0 ? d0 : nd - 1 - d0;
+                    int ilo = d - (ny - 1) > 0 ? d - (ny - 1) : 0, ihi = d < nx - 1 ? d : nx - 1;
+                    if (t < cnt + (ihi - ilo + 1)) {
+                        int off = t - cnt;
+                        i = pass == 0 ? ilo + off : ihi - off;
+                        j = d - i;
+                        found = 1;
+                    }
+                    cnt += ihi - ilo + 1;
+                }
+            }
+            int c = j * nx + i;
+            double V = Lv->dx[i] * Lv->dy[j];
+            for (int k = 0; k < nv; ++k) D[k] = Dii(s, Lv, i, j, inv_tau[c], k);
+            for (int cp = 0; cp < 2; ++cp)
+                for (int k = 0; k < nv; ++k) {
+                    double y = 0.0;
+                    if (pass == 0) {
+                        if (i > 0 && Lv->fbx[j * (nx + 1) + i] < 0)
+                            y += Dij(s, 0, -1, Lv->dy[j], V, k) * AT(x, nc, nv, cp, c - 1, k);
+                        if (j > 0 && Lv->fby[j * nx + i] < 0)
+                            y += Dij(s, 1, -1, Lv->dx[i], V, k) * AT(x, nc, nv, cp, c - nx, k);
+                        base[cp * nv + k] = AT(r, nc, nv, cp, c, k) - y;
+                    } else {
+                        if (i < nx - 1 && Lv->fbx[j * (nx + 1) + i + 1] < 0)
+                            y += Dij(s, 0, +1, Lv->dy[j], V, k) * AT(x, nc, nv, cp, c + 1, k);
+                        if (j < ny - 1 && Lv->fby[(j + 1) * nx + i] < 0)
+                            y += Dij(s, 1, +1, Lv->dx[i], V, k) * AT(x, nc, nv, cp, c + nx, k);
+                        base[cp * nv + k] = D[k] * AT(x, nc, nv, cp, c, k) - y;
+                    }
+                }
+            bface_t bf[4];
+            int nb = cell_bfaces(Lv, i, j, pass, bf);
+            if (nb == 0) {
+                for (int cp = 0; cp < 2; ++cp)
+                    for (int k = 0; k < nv; ++k) AT(x, nc, nv, cp, c, k) = base[cp * nv + k] / D[k];
+            } else {
+                cell_solve(s, c, nb, bf, D, base, xc);
+                for (int cp = 0; cp < 2; ++cp)
+                    for (int k = 0; k < nv; ++k) AT(x, nc, nv, cp, c, k) = xc[cp * nv + k];
+            }
+        }
+    }
+    free(D); free(base); free(xc);
+}
+
+/* y = A x, the full evolution operator of Eq. microFinalDefect with every
+ * neighbour and every boundary ghost (used to renew residuals, Eq. renewResidualMicro). */
+static void apply_micro(const oracle_solver *s, const olev_t *Lv, const double *inv_tau, const double *x, double *y)
+{
+    int nx = Lv->nx, ny = Lv->ny, nv = s->nv;
+    size_t nc = Lv->nc;
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            int c = j * nx + i;
+            double V = Lv->dx[i] * Lv->dy[j];
+            bface_t bf[4];
+            int nb = cell_bfaces(Lv, i, j, 2, bf);
+            double rho[4];
+            for (int b = 0; b < nb; ++b) {
+                if (s->bc[bf[b].bc].type != ORC_BC_WALL) continue;
+                double num = 0.0, Z = 0.0;
+                for (int k = 0; k < nv; ++k) {
+                    double uo = bf[b].outsign * (bf[b].axis == 0 ? s->u[k] : s->v[k]);
+                    if (uo > 0) num += s->w[k] * uo * AT(x, nc, nv, 0, c, k);
+                    else if (uo < 0) Z += s->w[k] * uo * wallC(s, bf[b].bc, 0, k);
+                }
+                rho[b] = -num / Z;
+            }
+            for (int cp = 0; cp < 2; ++cp)
+                for (int k = 0; k < nv; ++k) {
+                    double acc = Dii(s, Lv, i, j, inv_tau[c], k) * AT(x, nc, nv, cp, c, k);
+                    if (i > 0 && Lv->fbx[j * (nx + 1) + i] < 0)
+                        acc += Dij(s, 0, -1, Lv->dy[j], V, k) * AT(x, nc, nv, cp, c - 1, k);
+                    if (i < nx - 1 && Lv->fbx[j * (nx + 1) + i + 1] < 0)
+                        acc += Dij(s, 0, +1, Lv->dy[j], V, k) * AT(x, nc, nv, cp, c + 1, k);
+                    if (j > 0 && Lv->fby[j * nx + i] < 0)
+                        acc += Dij(s, 1, -1, Lv->dx[i], V, k) * AT(x, nc, nv, cp, c - nx, k);
+                    if (j < ny - 1 && Lv->fby[(j + 1) * nx + i] < 0)
+                        acc += Dij(s, 1, +1, Lv->dx[i], V, k) * AT(x, nc, nv, cp, c + nx, k);
+                    for (int b = 0; b < nb; ++b) {
+                        double Db = Dij(s, bf[b].axis, bf[b].outsign, bf[b].S, bf[b].V, k);
+                        if (Db == 0.0) continue;
+                        int t = s->bc[bf[b].bc].type;
+                        if (t == ORC_BC_WALL) acc += Db * wallC(s, bf[b].bc, cp, k) * rho[b];
+                        else if (t == ORC_BC_SYMMETRY) {
+                            int km = bf[b].axis == 0 ? s->mxk[k] : s->myk[k];
+                            acc += Db * AT(x, nc, nv, cp, c, km);
+                        } else if (t == ORC_BC_OUTFLOW) acc += Db * AT(x, nc, nv, cp, c, k);
+                    }
+                    AT(y, nc, nv, cp, c, k) = acc;
+                }
+        }
+}
+
+/* CS cycle (Eq. CSCYC): on entry lv->r holds the residual of level l (it is
+ * renewed in place); on exit lv->df holds the total correction. */
+static void cs(oracle_solver *s, int l)
+{
+    olev_t *Lv = &s->lev[l];
+    size_t n = 2 * (size_t)Lv->nc * s->nv;
+    memset(Lv->df, 0, n * sizeof(double));
+    int coarsest = (l == s->L - 1);
+    int npre = coarsest ? (s->L == 1 ? 1 : s->nuc) : s->nu1;
+    for (int m = 0; m < npre; ++m) {
+        sgs_micro(s, Lv, Lv->inv_tau, Lv->r, Lv->dl, 0);
+        for (size_t q = 0; q < n; ++q) Lv->df[q] += Lv->dl[q];
+        if (coarsest && m == npre - 1) return;
+        apply_micro(s, Lv, Lv->inv_tau, Lv->dl, Lv->Ad); /* Eq. renewResidualMicro */
+        for (size_t q = 0; q < n; ++q) Lv->r[q] -= Lv->Ad[q];
+    }
+    olev_t *Cv = &s->lev[l + 1];
+    for (int cp = 0; cp < 2; ++cp)
+        restrict_lv(Lv, Cv, s->nv, Lv->r + (size_t)cp * Lv->nc * s->nv, Cv->r + (size_t)cp * Cv->nc * s->nv);
+    cs(s, l + 1);
+    for (int cp = 0; cp < 2; ++cp)
+        prolong_lv(Lv, Cv, s->nv, Cv->df + (size_t)cp * Cv->nc * s->nv, Lv->dl + (size_t)cp * Lv->nc * s->nv);
+    for (size_t q = 0; q < n; ++q) Lv->df[q] += Lv->dl[q];
+    for (int m = 0; m < s->nu2; ++m) {
+        apply_micro(s, Lv, Lv->inv_tau, Lv->dl, Lv->Ad);
+        for (size_t q = 0; q < n; ++q) Lv->r[q] -= Lv->Ad[q];
+        sgs_micro(s, Lv, Lv->inv_tau, Lv->r, Lv->dl, 0);
+        for (size_t q = 0; q < n; ++q) Lv->df[q] += Lv->dl[q];
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Outer iteration (Steps 1-8)                                          */
+/* ------------------------------------------------------------------ */
+
+/* Step 7: W = sum_k w psi f and the heat flux q = sum_k w c (c^2 G/2 + H) */
+static void moments(oracle_solver *s)
+{
+    int nv = s->nv;
+    size_t nc = s->lev[0].nc;
+    for (size_t c = 0; c < nc; ++c) {
+        double W[4] = {0, 0, 0, 0};
+        for (int k = 0; k < nv; ++k) {
+            double g = FIX(s, 0, c, k), h = FIX(s, 1, c, k);
+            W[0] += s->w[k] * g;
+            W[1] += s->w[k] * s->u[k] * g;
+            W[2] += s->w[k] * s->v[k] * g;
+            W[3] += s->w[k] * (0.5 * (s->u[k] * s->u[k] + s->v[k] * s->v[k]) * g + h);
+        }
+        double rho, U, V, lam, qx = 0.0, qy = 0.0;
+        prim(W, &rho, &U, &V, &lam);
+        for (int k = 0; k < nv; ++k) {
+            double cx = s->u[k] - U, cy = s->v[k] - V, c2 = cx * cx + cy * cy;
+            double e = 0.5 * c2 * FIX(s, 0, c, k) + FIX(s, 1, c, k);
+            qx += s->w[k] * cx * e;
+            qy += s->w[k] * cy * e;
+        }
+        for (int m = 0; m < 4; ++m) s->W[4 * c + m] = W[m];
+        s->q[2 * c] = qx;
+        s->q[2 * c + 1] = qy;
+    }
+}
+
+static void rms(const oracle_solver *s, double res[4])
+{
+    size_t nc = s->lev[0].nc;
+    for (int m = 0; m < 4; ++m) {
+        double a = 0.0;
+        for (size_t c = 0; c < nc; ++c) a += s->R[4 * c + m] * s->R[4 * c + m];
+        res[m] = sqrt(a / nc);
+    }
+}
+
+static void one_iteration(oracle_solver *s, double res[4])
+{
+    olev_t *L0 = &s->lev[0];
+    int nx = L0->nx, ny = L0->ny, nv = s->nv;
+    size_t nc = L0->nc;
+    /* Step 1 */
+    flux_stage(s);
+    rms(s, res);
+    /* Step 2: predicted conservative variables by FAS */
+    memcpy(L0->Wn, s->W, 4 * nc * sizeof(double));
+    memcpy(L0->Rc, s->R, 4 * nc * sizeof(double));
+    fas(s, 0);
+    memcpy(L0->Wtil, L0->Wc, 4 * nc * sizeof(double));
+    /* Step 3: predicted equilibrium and collision time; coarse tau from the
+     * volume-restricted predicted state */
+    double add = dtn_inv(s);
+    for (int l = 0; l < s->L; ++l) {
+        olev_t *Lv = &s->lev[l];
+        if (l > 0) restrict_lv(&s->lev[l - 1], Lv, 4, s->lev[l - 1].Wtil, Lv->Wtil);
+        for (int c = 0; c < Lv->nc; ++c) {
+            double rho, U, V, lam;
+            prim(Lv->Wtil + 4 * c, &rho, &U, &V, &lam);
+            Lv->inv_tau[c] = 1.0 / tau_of(s, rho, lam) + add;
+        }
+    }
+    /* Step 4: r = (g~ - f)/tau~ - (1/V) sum S u_n f~ (Eq. microResidualDef) */
+    double shk0 = (1.0 - s->pr) * 4.0 / 5.0;
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            int c = j * nx + i;
+            double rho, U, V, lam;
+            prim(L0->Wtil + 4 * c, &rho, &U, &V, &lam);
+            double itau = 1.0 / tau_of(s, rho, lam);
+            double Vol = L0->dx[i] * L0->dy[j];
+            double qx = s->q[2 * c], qy = s->q[2 * c + 1];
+            int fW = j * (nx + 1) + i, fE = fW + 1, fS = j * nx + i, fN = (j + 1) * nx + i;
+            for (int k = 0; k < nv; ++k) {
+                double cx = s->u[k] - U, cy = s->v[k] - V, c2 = cx * cx + cy * cy;
+                double gM = maxw(rho, U, V, lam, s->u[k], s->v[k]), hM = gM * KINT / (4.0 * lam);
+                double Fq = shk0 * lam * lam / rho * (cx * qx + cy * qy);
+                double gt[2] = {gM * (1.0 + Fq * (2.0 * lam * c2 - 4.0)), hM * (1.0 + Fq * (2.0 * lam * c2 - 2.0))};
+                for (int cp = 0; cp < 2; ++cp) {
+                    const double *px = s->phx + (size_t)cp * L0->nfx * nv, *py = s->phy + (size_t)cp * L0->nfy * nv;
+                    double div = (L0->dy[j] * (px[(size_t)fE * nv + k] - px[(size_t)fW * nv + k]) +
+                                  L0->dx[i] * (py[(size_t)fN * nv + k] - py[(size_t)fS * nv + k])) / Vol;
+                    AT(L0->r, nc, nv, cp, c, k) = (gt[cp] - FIX(s, cp, c, k)) * itau - div;
+                }
+            }
+        }
+    /* Step 5: total correction by the CS cycle */
+    cs(s, 0);
+    /* Steps 6-7 */
+    size_t n = 2 * nc * nv;
+    for (size_t q = 0; q < n; ++q) s->f[q] += L0->df[q];
+    moments(s);
+    s->iter++;
+}
+
+/* ------------------------------------------------------------------ */
+/* Public API                                                           */
+/* ------------------------------------------------------------------ */
+
+oracle_solver *oracle_create(int nx, int ny, const double *xn, const double *yn,
+                             const int *face_bc_x, const int *face_bc_y,
+                             int nbc, const int *bc_type, const double *bc_vals,
+                             int nu, int nv, double umin, double umax,
+                             double vmin, double vmax, int rule,
+                             double kn, double omega, double pr,
+                             int levels, int nu1, int nu2, int nuc,
+                             double cfl, double dtn_growth)
+{
+    if (nx < 1 || ny < 1 || levels < 1 || levels > MAXL || nbc < 1 || nu < 2 || nv < 2) {
+        fail("bad sizes");
+        return NULL;
+    }
+    oracle_solver *s = (oracle_solver *)calloc(1, sizeof *s);
+    s->L = levels;
+    s->nu = nu; s->nvv = nv; s->nv = nu * nv;
+    s->kn = kn; s->omega = omega; s->pr = pr; s->mu_ref = oracle_mu_ref(kn, omega);
+    s->nu1 = nu1; s->nu2 = nu2; s->nuc = nuc; s->cfl = cfl; s->dtn_growth = dtn_growth;
+    double *ux = dalloc(nu), *wu = dalloc(nu), *vy = dalloc(nv), *wv = dalloc(nv);
+    if (oracle_vgrid(nu, umin, umax, rule, ux, wu) || oracle_vgrid(nv, vmin, vmax, rule, vy, wv)) {
+        free(ux); free(wu); free(vy); free(wv); free(s);
+        return NULL;
+    }
+    int NV = s->nv;
+    s->u = dalloc(NV); s->v = dalloc(NV); s->w = dalloc(NV);
+    s->mxk = (int *)calloc(NV, sizeof(int)); s->myk = (int *)calloc(NV, sizeof(int));
+    int symu = (umin == -umax), symv = (vmin == -vmax);
+    for (int a = 0; a < nu; ++a)
+        for (int b = 0; b < nv; ++b) {
+            int k = a * nv + b;
+            s->u[k] = ux[a]; s->v[k] = vy[b]; s->w[k] = wu[a] * wv[b];
+            s->mxk[k] = symu ? (nu - 1 - a) * nv + b : -1;
+            s->myk[k] = symv ? a * nv + (nv - 1 - b) : -1;
+        }
+    s->umax_abs = fmax(fabs(umin), fabs(umax));
+    s->vmax_abs = fmax(fabs(vmin), fabs(vmax));
+    free(ux); free(wu); free(vy); free(wv);
+    s->nbc = nbc;
+    s->bc = (obc_t *)calloc(nbc, sizeof(obc_t));
+    s->Cw = dalloc((size_t)nbc * NV);
+    for (int b = 0; b < nbc; ++b) {
+        s->bc[b] = (obc_t){bc_type[b], bc_vals[4 * b], bc_vals[4 * b + 1], bc_vals[4 * b + 2], bc_vals[4 * b + 3]};
+        if (bc_type[b] < 0 || bc_type[b] > 3 || !(bc_vals[4 * b + 3] > 0)) {
+            fail("bad BC %d", b);
+            oracle_destroy(s);
+            return NULL;
+        }
+        if (bc_type[b] == ORC_BC_SYMMETRY && (!symu || !symv)) {
+            fail("symmetry BC needs a velocity grid symmetric about zero");
+            oracle_destroy(s);
+            return NULL;
+        }
+        for (int k = 0; k < NV; ++k)
+            s->Cw[(size_t)b * NV + k] = maxw(1.0, s->bc[b].u, s->bc[b].v, 1.0 / s->bc[b].t, s->u[k], s->v[k]);
+    }
+    olev_t *L0 = &s->lev[0];
+    L0->nx = nx; L0->ny = ny; L0->nc = nx * ny; L0->nfx = (nx + 1) * ny; L0->nfy = nx * (ny + 1);
+    L0->xn = dalloc(nx + 1); L0->yn = dalloc(ny + 1);
+    memcpy(L0->xn, xn, (nx + 1) * sizeof(double));
+    memcpy(L0->yn, yn, (ny + 1) * sizeof(double));
+    L0->fbx = (int *)malloc(L0->nfx * sizeof(int));
+    L0->fby = (int *)malloc(L0->nfy * sizeof(int));
+    memcpy(L0->fbx, face_bc_x, L0->nfx * sizeof(int));
+    memcpy(L0->fby, face_bc_y, L0->nfy * sizeof(int));
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i <= nx; ++i) {
+            int b = L0->fbx[j * (nx + 1) + i], bnd = (i == 0 || i == nx);
+            if (bnd ? (b < 0 || b >= nbc) : (b != -1)) {
+                fail("x-face (%d,%d): boundary faces need a BC id, interior faces -1", i, j);
+                oracle_destroy(s);
+                return NULL;
+            }
+        }
+    for (int j = 0; j <= ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            int b = L0->fby[j * nx + i], bnd = (j == 0 || j == ny);
+            if (bnd ? (b < 0 || b >= nbc) : (b != -1)) {
+                fail("y-face (%d,%d): boundary faces need a BC id, interior faces -1", i, j);
+                oracle_destroy(s);
+                return NULL;
+            }
+        }
+    if (level_geom(L0)) { oracle_destroy(s); return NULL; }
+    for (int l = 1; l < levels; ++l)
+        if (coarsen(&s->lev[l - 1], &s->lev[l])) { oracle_destroy(s); return NULL; }
+    for (int l = 0; l < levels; ++l)
+        if (level_alloc(s, &s->lev[l])) { oracle_destroy(s); return NULL; }
+    size_t nc = L0->nc;
+    s->f = dalloc(2 * nc * NV); s->W = dalloc(4 * nc); s->q = dalloc(2 * nc); s->R = dalloc(4 * nc);
+    s->phx = dalloc(2 * (size_t)L0->nfx * NV); s->phy = dalloc(2 * (size_t)L0->nfy * NV);
+    s->Fx = dalloc(4 * (size_t)L0->nfx); s->Fy = dalloc(4 * (size_t)L0->nfy);
+    s->tmp0 = dalloc(2 * (size_t)NV); s->tmp1 = dalloc(2 * (size_t)NV); s->tmp2 = dalloc(2 * (size_t)NV);
+    if (!s->f || !s->phx || !s->phy) { fail("out of memory"); oracle_destroy(s); return NULL; }
+    /* minimum physical time step over the interior faces (for dt_n) */
+    s->dtp_min = 1e300;
+    for (int i = 1; i < nx; ++i) s->dtp_min = fmin(s->dtp_min, face_dt(s, 0, L0->dx[i - 1], L0->dx[i]));
+    for (int j = 1; j < ny; ++j) s->dtp_min = fmin(s->dtp_min, face_dt(s, 1, L0->dy[j - 1], L0->dy[j]));
+    return s;
+}
+
+void oracle_destroy(oracle_solver *s)
+{
+    if (!s) return;
+    for (int l = 0; l < MAXL; ++l) {
+        olev_t *Lv = &s->lev[l];
+        free(Lv->xn); free(Lv->yn); free(Lv->xc); free(Lv->yc); free(Lv->dx); free(Lv->dy);
+        free(Lv->fbx); free(Lv->fby);
+        free(Lv->Wn); free(Lv->Wc); free(Lv->Rc); free(Lv->P); free(Lv->RE); free(Lv->dW); free(Lv->Wtil);
+        free(Lv->r); free(Lv->df); free(Lv->dl); free(Lv->Ad); free(Lv->inv_tau);
+    }
+    free(s->u); free(s->v); free(s->w); free(s->mxk); free(s->myk); free(s->bc); free(s->Cw);
+    free(s->f); free(s->W); free(s->q); free(s->R); free(s->phx); free(s->phy); free(s->Fx); free(s->Fy);
+    free(s->tmp0); free(s->tmp1); free(s->tmp2);
+    free(s);
+}
+
+int oracle_init_fields(oracle_solver *s, const double *rho, const double *u, const double *v, const double *t)
+{
+    size_t nc = s->lev[0].nc;
+    for (size_t c = 0; c < nc; ++c) {
+        if (!(rho[c] > 0) || !(t[c] > 0)) return fail("init: rho and T must be positive");
+        double lam = 1.0 / t[c];
+        for (int k = 0; k < s->nv; ++k) {
+            double g = maxw(rho[c], u[c], v[c], lam, s->u[k], s->v[k]);
+            FIX(s, 0, c, k) = g;
+            FIX(s, 1, c, k) = g * KINT / (4.0 * lam);
+        }
+    }
+    moments(s);
+    s->iter = 0;
+    return 0;
+}
+
+int oracle_init_uniform(oracle_solver *s, double rho, double u, double v, double t)
+{
+    size_t nc = s->lev[0].nc;
+    double *a = dalloc(4 * nc);
+    for (size_t c = 0; c < nc; ++c) { a[c] = rho; a[nc + c] = u; a[2 * nc + c] = v; a[3 * nc + c] = t; }
+    int st = oracle_init_fields(s, a, a + nc, a + 2 * nc, a + 3 * nc);
+    free(a);
+    return st;
+}
+
+int oracle_step(oracle_solver *s, int n, double res[4])
+{
+    double r[4] = {0, 0, 0, 0};
+    for (int it = 0; it < n; ++it) {
+        one_iteration(s, r);
+        for (size_t c = 0; c < (size_t)s->lev[0].nc; ++c) {
+            const double *W = s->W + 4 * c;
+            double eint = W[3] - 0.5 * (W[1] * W[1] + W[2] * W[2]) / W[0];
+            if (!(W[0] > 0) || !(eint > 0)) return fail("diverged at iteration %d", s->iter);
+        }
+    }
+    if (res) memcpy(res, r, sizeof r);
+    return 0;
+}
+
+int oracle_residual(oracle_solver *s, double *R)
+{
+    flux_stage(s);
+    memcpy(R, s->R, 4 * (size_t)s->lev[0].nc * sizeof(double));
+    return 0;
+}
+
+int oracle_get_macro(const oracle_solver *s, double *rho, double *u, double *v, double *t, double *qx, double *qy)
+{
+    for (int c = 0; c < s->lev[0].nc; ++c) {
+        double r, U, V, lam;
+        prim(s->W + 4 * c, &r, &U, &V, &lam);
+        if (rho) rho[c] = r;
+        if (u) u[c] = U;
+        if (v) v[c] = V;
+        if (t) t[c] = 1.0 / lam;
+        if (qx) qx[c] = s->q[2 * c];
+        if (qy) qy[c] = s->q[2 * c + 1];
+    }
+    return 0;
+}
+
+int oracle_get_f(const oracle_solver *s, double *f)
+{
+    memcpy(f, s->f, 2 * (size_t)s->lev[0].nc * s->nv * sizeof(double));
+    return 0;
+}
+
+int oracle_set_f(oracle_solver *s, const double *f)
+{
+    memcpy(s->f, f, 2 * (size_t)s->lev[0].nc * s->nv * sizeof(double));
+    moments(s);
+    return 0;
+}
+
+int oracle_set_bc(oracle_solver *s, int b, double rho, double u, double v, double t)
+{
+    if (b < 0 || b >= s->nbc || !(t > 0)) return fail("set_bc: bad arguments");
+    s->bc[b].rho = rho; s->bc[b].u = u; s->bc[b].v = v; s->bc[b].t = t;
+    for (int k = 0; k < s->nv; ++k) s->Cw[(size_t)b * s->nv + k] = maxw(1.0, u, v, 1.0 / t, s->u[k], s->v[k]);
+    return 0;
+}
+
+/* Wall pressure, shear stress and heat flux (Secs. 4.2, 4.3): momentum and
+ * energy carried into the wall per unit area and time by the face
+ * distribution, in the frame of the wall; normal n points from the gas into
+ * the wall, the tangent is the other axis. */
+int oracle_get_wall(const oracle_solver *s, int bc, int *nf, double *p, double *tau, double *q)
+{
+    const olev_t *L0 = &s->lev[0];
+    int nx = L0->nx, ny = L0->ny, nv = s->nv, cnt = 0, cap = *nf;
+    if (bc < 0 || bc >= s->nbc) return fail("get_wall: bad BC id");
+    double *fG = dalloc(nv), *fH = dalloc(nv);
+    const obc_t *B = &s->bc[bc];
+    for (int pass = 0; pass < 2; ++pass) {
+        int nfc = pass == 0 ? L0->nfx : L0->nfy;
+        for (int fi = 0; fi < nfc; ++fi) {
+            int b = pass == 0 ? L0->fbx[fi] : L0->fby[fi];
+            if (b != bc) continue;
+            int axis = pass, outsign, c;
+            if (axis == 0) {
+                int i = fi % (nx + 1), j = fi / (nx + 1);
+                outsign = i == 0 ? -1 : 1; c = j * nx + (i == 0 ? 0 : nx - 1);
+            } else {
+                int i = fi % nx, j = fi / nx;
+                outsign = j == 0 ? -1 : 1; c = (j == 0 ? 0 : ny - 1) * nx + i;
+            }
+            boundary_face_f(s, bc, axis, outsign, c, fG, fH);
+            double P = 0, T = 0, Q = 0, Uwt = axis == 0 ? B->v : B->u;
+            for (int k = 0; k < nv; ++k) {
+                double uo = outsign * (axis == 0 ? s->u[k] : s->v[k]);
+                double ut = axis == 0 ? s->v[k] : s->u[k];
+                double du = s->u[k] - B->u, dv = s->v[k] - B->v;
+                P += s->w[k] * uo * uo * fG[k];
+                T += s->w[k] * uo * (ut - Uwt) * fG[k];
+                Q += s->w[k] * uo * (0.5 * (du * du + dv * dv) * fG[k] + fH[k]);
+            }
+            if (cnt < cap) { p[cnt] = P; tau[cnt] = T; q[cnt] = Q; }
+            cnt++;
+        }
+    }
+    free(fG); free(fH);
+    *nf = cnt;
+    return cnt > cap ? fail("get_wall: capacity %d < %d faces", cap, cnt) : 0;
+}
+
+int oracle_iterations(const oracle_solver *s) { return s->iter; }
+int oracle_nv(const oracle_solver *s) { return s->nv; }
+int oracle_level_size(const oracle_solver *s, int lev, int *nx, int *ny)
+{
+    if (lev < 0 || lev >= s->L) return fail("bad level");
+    *nx = s->lev[lev].nx; *ny = s->lev[lev].ny;
+    return 0;
+}
+
+int oracle_stage_flux(oracle_solver *s, double *R, double *phx, double *phy)
+{
+    flux_stage(s);
+    const olev_t *L0 = &s->lev[0];
+    if (R) memcpy(R, s->R, 4 * (size_t)L0->nc * sizeof(double));
+    if (phx) memcpy(phx, s->phx, 2 * (size_t)L0->nfx * s->nv * sizeof(double));
+    if (phy) memcpy(phy, s->phy, 2 * (size_t)L0->nfy * s->nv * sizeof(double));
+    return 0;
+}
+
+int oracle_stage_sgs_micro(oracle_solver *s, int lev, const double *inv_tau, const double *r, double *x, int order)
+{
+    if (lev < 0 || lev >= s->L) return fail("bad level");
+    sgs_micro(s, &s->lev[lev], inv_tau, r, x, order);
+    return 0;
+}
+
+int oracle_stage_apply_micro(oracle_solver *s, int lev, const double *inv_tau, const double *x, double *y)
+{
+    if (lev < 0 || lev >= s->L) return fail("bad level");
+    apply_micro(s, &s->lev[lev], inv_tau, x, y);
+    return 0;
+}
+
+int oracle_stage_sgs_macro(oracle_solver *s, int lev, const double *W, const double *Wg, const double *R, double *dW, int order)
+{
+    if (lev < 0 || lev >= s->L) return fail("bad level");
+    sgs_macro(s, &s->lev[lev], W, Wg, R, dW, order);
+    return 0;
+}
+
+int oracle_stage_resid_macro(oracle_solver *s, int lev, const double *W, const double *Wg, double *RE)
+{
+    if (lev < 0 || lev >= s->L) return fail("bad level");
+    resid_macro(s, &s->lev[lev], W, Wg, RE);
+    return 0;
+}
+
+int oracle_stage_restrict(oracle_solver *s, int lev, int m, const double *fine, double *coarse)
+{
+    if (lev < 0 || lev + 1 >= s->L) return fail("bad level");
+    restrict_lv(&s->lev[lev], &s->lev[lev + 1], m, fine, coarse);
+    return 0;
+}
+
+int oracle_stage_prolong(oracle_solver *s, int lev, int m, const double *coarse, double *fine)
+{
+    if (lev < 0 || lev + 1 >= s->L) return fail("bad level");
+    prolong_lv(&s->lev[lev], &s->lev[lev + 1], m, coarse, fine);
+    return 0;
+}

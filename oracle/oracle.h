@@ -1,0 +1,101 @@
+/*
+ * oracle.h -- plain, serial, FP64 CPU oracle of the multigrid implicit unified
+ * gas-kinetic scheme (MIUGKS) of Zhu, Zhong & Xu, "Unified Gas-kinetic Scheme
+ * with Multigrid Convergence for Rarefied Flow Study" (arXiv 1704.03151).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the CPU
+ * baseline leg of the benchmark may load this library.  It shares no code,
+ * header, table or constant with the CUDA library under
+ * paper_1704_03151_gb300/csrc, and the CUDA library never calls it.
+ *
+ * Conventions (all nondimensional): gas constant R = 1/2, reference density,
+ * temperature and length 1, so lambda = 1/(2RT) = 1/T and p = rho*T/2.
+ * Monatomic gas in 2-D with one internal (z-translational) degree of freedom:
+ * two reduced distributions per (cell, velocity), G = int f dxi_z and
+ * H = int xi_z^2/2 f dxi_z.
+ *
+ * Layouts: cell c = j*nx + i; f[(comp*nc + c)*nv + k] with comp 0 = G, 1 = H;
+ * velocity k = a*nv_v + b with u_k = u_a, v_k = v_b.  x-faces indexed
+ * j*(nx+1) + i (face between cells i-1 and i), y-faces j*nx + i (between
+ * rows j-1 and j).  A face BC id of -1 marks an interior face.
+ *
+ * Every function returns 0 on success and a nonzero status on error, with a
+ * message available from oracle_last_error().
+ */
+#ifndef MIUGKS_ORACLE_H
+#define MIUGKS_ORACLE_H
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORC_BC_WALL = 0, ORC_BC_SYMMETRY = 1, ORC_BC_FARFIELD = 2, ORC_BC_OUTFLOW = 3 };
+
+typedef struct oracle_solver oracle_solver;
+
+/* Build the solver: mesh (rectilinear nodes), face boundary ids, BC table
+ * (bc_vals = nbc x {rho, u, v, T}), velocity grid, gas and multigrid options.
+ * levels = 1 is the single-grid implicit UGKS (one smoothing per step). */
+oracle_solver *oracle_create(int nx, int ny, const double *xn, const double *yn,
+                             const int *face_bc_x, const int *face_bc_y,
+                             int nbc, const int *bc_type, const double *bc_vals,
+                             int nu, int nv, double umin, double umax,
+                             double vmin, double vmax, int rule,
+                             double kn, double omega, double pr,
+                             int levels, int nu1, int nu2, int nuc,
+                             double cfl, double dtn_growth);
+const char *oracle_last_error(void);
+void oracle_destroy(oracle_solver *s);
+
+int oracle_init_uniform(oracle_solver *s, double rho, double u, double v, double t);
+int oracle_init_fields(oracle_solver *s, const double *rho, const double *u,
+                       const double *v, const double *t);
+/* n outer iterations (Steps 1-8); res = RMS residual of the last Step 1. */
+int oracle_step(oracle_solver *s, int n, double res[4]);
+int oracle_get_macro(const oracle_solver *s, double *rho, double *u, double *v,
+                     double *t, double *qx, double *qy);
+int oracle_get_f(const oracle_solver *s, double *f);
+int oracle_set_f(oracle_solver *s, const double *f);
+/* wall quantities along the faces carrying BC id bc (in face-index order:
+ * x-faces first, then y-faces); *nf in: capacity, out: count. */
+int oracle_get_wall(const oracle_solver *s, int bc, int *nf, double *p,
+                    double *tau, double *q);
+int oracle_set_bc(oracle_solver *s, int bc, double rho, double u, double v, double t);
+/* Step 1 alone: the macroscopic residual R (nc x 4) of the current state. */
+int oracle_residual(oracle_solver *s, double *R);
+int oracle_iterations(const oracle_solver *s);
+
+/* ---- building blocks exposed for the pins (tests/test_oracle_*.py) ---- */
+int oracle_vgrid(int n, double a, double b, int rule, double *x, double *w);
+void oracle_time_coeffs(double dt, double tau, double q[5]);
+void oracle_micro_slope(const double dw[4], double U, double V, double lam, double a[4]);
+double oracle_vanleer(double s1, double s2);
+double oracle_mu_ref(double kn, double omega);
+void oracle_wall_jacobian(const double W[4], double Uw, double Vw, double Tw, double M[16]);
+void oracle_wall_ghost(const double W[4], double Uw, double Vw, double Tw, double Wg[4]);
+/* Internal stages on level 0 of an existing solver (f, W already set):
+ *  flux   : Step 1 -> R (nc x 4) and the time-averaged micro face fluxes
+ *           phx (2 x nfx x nv), phy (2 x nfy x nv)                            */
+int oracle_stage_flux(oracle_solver *s, double *R, double *phx, double *phy);
+/*  sgs_micro : one symmetric Gauss-Seidel pass on level lev for residual r
+ *              (2 x nc_l x nv), collision frequency 1/tau per cell (inv_tau),
+ *              order 0 = lexicographic, 1 = anti-diagonal wavefront.          */
+int oracle_stage_sgs_micro(oracle_solver *s, int lev, const double *inv_tau,
+                           const double *r, double *dx_out, int order);
+/*  apply_micro : y = A x with the full evolution operator (all ghosts).       */
+int oracle_stage_apply_micro(oracle_solver *s, int lev, const double *inv_tau,
+                             const double *x, double *y);
+/*  sgs_macro : one LU-SGS pass of the prediction smoother on level lev.       */
+int oracle_stage_sgs_macro(oracle_solver *s, int lev, const double *W,
+                           const double *Wn_gamma, const double *R, double *dW, int order);
+/*  resid_macro : split-Euler residual R_E(W) on level lev (Gamma from Wg).    */
+int oracle_stage_resid_macro(oracle_solver *s, int lev, const double *W,
+                             const double *Wg, double *RE);
+int oracle_stage_restrict(oracle_solver *s, int lev, int ncomp, const double *fine, double *coarse);
+int oracle_stage_prolong(oracle_solver *s, int lev, int ncomp, const double *coarse, double *fine);
+int oracle_level_size(const oracle_solver *s, int lev, int *nx, int *ny);
+int oracle_nv(const oracle_solver *s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
