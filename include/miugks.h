@@ -1,0 +1,159 @@
+/*
+ * miugks.h -- C ABI of the GB300 (sm_103a) multigrid implicit unified
+ * gas-kinetic scheme (MIUGKS) library.
+ *
+ * Method: Zhu, Zhong & Xu, "Unified Gas-kinetic Scheme with Multigrid
+ * Convergence for Rarefied Flow Study", arXiv 1704.03151.  One call of
+ * miugks_step() performs Steps 1-8 of Sec. 2.4 once per iteration: explicit
+ * UGKS fluxes and residuals (Sec. 2.1, Eqs. macroResidualDef,
+ * macroResidualCalc, microResidualDef), the FAS prediction of the conservative
+ * variables (Eq. FASCYC), the predicted equilibrium, the CS evolution of the
+ * distribution function (Eq. CSCYC), its update and the moments.
+ *
+ * Units (nondimensional): gas constant R = 1/2, reference density,
+ * temperature and length 1 -- so lambda = 1/(2RT) = 1/T, p = rho T / 2 and
+ * the most probable speed is 1.  2-D monatomic gas with one internal degree
+ * of freedom: two reduced distributions per (cell, velocity).
+ *
+ * Layouts.  Cells are row-major, c = j*nx + i.  The distribution function is
+ * f[(comp*nc + c)*nv + k] (comp 0: G = int f dxi_z, comp 1: H = int xi_z^2/2
+ * f dxi_z) with discrete velocity k = a*nv_v + b, u_k = u_a, v_k = v_b.
+ * x-faces are indexed j*(nx+1) + i (between cells i-1 and i), y-faces
+ * j*nx + i (between rows j-1 and j); a face BC id of -1 marks an interior face.
+ * Only the outer edges of the rectangle may carry boundary ids.
+ *
+ * Ownership and errors.  The library owns all device memory of a solver; it
+ * allocates through the caller's callbacks when given (the Python binding
+ * passes PyTorch's caching allocator), else with cudaMalloc, and works on the
+ * caller's CUDA stream (or the legacy default stream).  Arrays passed in or
+ * out are HOST arrays owned by the caller unless a name says _dev.  Every
+ * call returns a status and never aborts; miugks_last_error() gives the
+ * message of the last failure of that solver (valid until its next call).
+ * A solver must not be used by two threads at once.
+ */
+#ifndef MIUGKS_H
+#define MIUGKS_H
+#include <stddef.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct miugks_solver miugks_solver;
+
+typedef enum {
+    MIUGKS_OK = 0,
+    MIUGKS_EINVAL = 1,         /* invalid argument or unsupported configuration   */
+    MIUGKS_ENOMEM = 2,         /* device or host allocation failed                */
+    MIUGKS_ECUDA = 3,          /* CUDA runtime error (message has the details)    */
+    MIUGKS_EDIVERGED = 4,      /* non-positive density or temperature, or NaN     */
+    MIUGKS_ETIMEOUT = 5,       /* reserved: a bounded device wait gave up         */
+    MIUGKS_ENOTCONVERGED = 6,  /* miugks_run reached max_iter above tolerance    */
+    MIUGKS_ESTATE = 7          /* call order (e.g. step before init)              */
+} miugks_status;
+
+typedef enum { MIUGKS_BC_WALL = 0, MIUGKS_BC_SYMMETRY = 1, MIUGKS_BC_FARFIELD = 2, MIUGKS_BC_OUTFLOW = 3 } miugks_bc_type;
+typedef enum { MIUGKS_FP64 = 0 } miugks_precision;
+
+/* rectilinear mesh: x_nodes[nx+1], y_nodes[ny+1] increasing; face ids as above */
+typedef struct {
+    int nx, ny;
+    const double *x_nodes, *y_nodes;
+    const int *face_bc_x;      /* (nx+1)*ny */
+    const int *face_bc_y;      /* nx*(ny+1) */
+} miugks_mesh;
+
+/* discrete velocities: nu x nv nodes, placed symmetrically on [umin,umax] x
+ * [vmin,vmax]; rule 0 trapezoid (Sec. 4.1), 1 composite Boole, closed
+ * Newton-Cotes of degree 4, needing (n-1) % 4 == 0 (Sec. 4.3) */
+typedef struct { int nu, nv; double umin, umax, vmin, vmax; int rule; } miugks_vgrid;
+
+/* Kn (VHS, alpha = 1), viscosity index omega (mu ~ T^omega), Prandtl number
+ * of the Shakhov equilibrium (Sec. 2.1) */
+typedef struct { double kn, omega, pr; } miugks_gas;
+
+/* boundary condition (Sec. 3.2): wall = diffuse isothermal wall moving with
+ * (u, v) at temperature t; symmetry = specular plane (needs a velocity grid
+ * symmetric about 0); farfield = Maxwellian (rho, u, v, t) entering;
+ * outflow = zero gradient */
+typedef struct { int type; double rho, u, v, t; } miugks_bc;
+
+/* multigrid options (Secs. 2.4, 3.4): levels (1 = single-grid implicit UGKS
+ * with one smoothing per step), pre/post smoothings nu1/nu2 (2/1 in the
+ * paper), smoothings on the coarsest level, CFL number of the physical time
+ * step, growth factor a of the numerical time step dt_n = a^n dt_p (0 = off). */
+typedef struct {
+    int levels, nu1, nu2, nu_coarse;
+    double cfl, dtn_growth;
+    int precision;                                   /* miugks_precision */
+    void *cuda_stream;                               /* cudaStream_t or NULL */
+    void *(*dev_alloc)(size_t bytes, void *ctx);     /* NULL: cudaMalloc */
+    void (*dev_free)(void *ptr, void *ctx);
+    void *alloc_ctx;
+} miugks_opts;
+
+/* Build a solver (host mesh hierarchy by 2x2 agglomeration, Sec. 3.1; device
+ * state).  nx and ny must be divisible by 2^(levels-1).  On error *out is NULL. */
+miugks_status miugks_create(const miugks_mesh *mesh, const miugks_vgrid *vgrid, const miugks_gas *gas,
+                            const miugks_bc *bcs, int n_bcs, const miugks_opts *opts, miugks_solver **out);
+void miugks_destroy(miugks_solver *s);
+const char *miugks_last_error(const miugks_solver *s);
+
+/* Initial state: discrete Maxwellian of (rho, u, v, t), uniform or per cell (host arrays of nc). */
+miugks_status miugks_init_uniform(miugks_solver *s, double rho, double u, double v, double t);
+miugks_status miugks_init_fields(miugks_solver *s, const double *rho, const double *u, const double *v,
+                                 const double *t);
+
+/* n outer iterations (Steps 1-8).  res_out (may be NULL): RMS of the
+ * macroscopic residual per component (rho, rho U, rho V, rho eps) evaluated in
+ * Step 1 of the last iteration (Eq. Residual_Def).  Returns MIUGKS_EDIVERGED
+ * when the state became unphysical. */
+miugks_status miugks_step(miugks_solver *s, int n_iter, double res_out[4]);
+/* iterate until every RMS component is below tol (Sec. 4.1) or max_iter */
+miugks_status miugks_run(miugks_solver *s, double tol, int max_iter, int *iters_out, double res_out[4]);
+/* RMS residual of the current state (Step 1 only) */
+miugks_status miugks_residual(miugks_solver *s, double res_out[4]);
+int miugks_iterations(const miugks_solver *s);
+
+/* Macroscopic fields (host, nc each; NULL skips) and the distribution function
+ * (host, 2*nc*nv doubles in the layout above). */
+miugks_status miugks_get_macro(miugks_solver *s, double *rho, double *u, double *v, double *t, double *qx,
+                               double *qy);
+miugks_status miugks_get_f(miugks_solver *s, double *f);
+miugks_status miugks_set_f(miugks_solver *s, const double *f);
+/* Wall pressure, shear stress and heat flux (Secs. 4.2, 4.3: momentum and
+ * energy carried into the wall per unit area and time, in the wall frame)
+ * for the faces with BC id bc, x-faces first, each in face-index order.
+ * *n_faces: in capacity, out count (call with capacity 0 to size). */
+miugks_status miugks_get_wall(miugks_solver *s, int bc, int *n_faces, double *p, double *tau, double *q);
+miugks_status miugks_set_bc(miugks_solver *s, int bc, const miugks_bc *value);
+
+/* Stages of one iteration on explicit host data, for kernel-level checks.
+ *  flux: Step 1 at the current state -> R (nc x 4), time-averaged micro face
+ *        fluxes phx (2 x nfx x nv) and phy (2 x nfy x nv); any may be NULL.
+ *  sgs_micro: one LU-SGS pass of the evolution smoother on level lev with
+ *        collision frequency inv_tau (nc_l) for residual r (2 x nc_l x nv).
+ *  apply_micro: y = A x with the full evolution operator of level lev.
+ *  sgs_macro: one LU-SGS pass of the prediction smoother at state W with
+ *        Gamma frozen at Wg, residual R; returns dW (all nc_l x 4).
+ *  resid_macro: split-Euler residual R_E(W) with Gamma frozen at Wg.
+ *  restrict / prolong: transfer of an [nc][m] array between lev and lev+1. */
+miugks_status miugks_stage_flux(miugks_solver *s, double *R, double *phx, double *phy);
+miugks_status miugks_stage_sgs_micro(miugks_solver *s, int lev, const double *inv_tau, const double *r, double *x);
+miugks_status miugks_stage_apply_micro(miugks_solver *s, int lev, const double *inv_tau, const double *x, double *y);
+miugks_status miugks_stage_sgs_macro(miugks_solver *s, int lev, const double *W, const double *Wg, const double *R,
+                                     double *dW);
+miugks_status miugks_stage_resid_macro(miugks_solver *s, int lev, const double *W, const double *Wg, double *RE);
+miugks_status miugks_stage_restrict(miugks_solver *s, int lev, int m, const double *fine, double *coarse);
+miugks_status miugks_stage_prolong(miugks_solver *s, int lev, int m, const double *coarse, double *fine);
+
+/* Sizes and the CUDA events bracketing the last Step-1 flux launch (for
+ * roofline timing): elapsed milliseconds of the flux kernels of the last
+ * iteration, or -1 when timing is off.  miugks_set_timing(s, 1) enables it. */
+miugks_status miugks_sizes(const miugks_solver *s, int *nx, int *ny, int *nv, int *levels);
+miugks_status miugks_set_timing(miugks_solver *s, int on);
+miugks_status miugks_kernel_times(miugks_solver *s, double *flux_ms, double *sweep_ms, double *total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,143 @@
+// common.cuh -- device-side model functions and shared types of the MIUGKS
+// CUDA library (arXiv 1704.03151).  Units: R = 1/2, lambda = 1/T, p = rho T / 2;
+// 2-D monatomic gas with one internal degree of freedom carried by the reduced
+// distributions G (comp 0) and H (comp 1).
+#pragma once
+#include <cuda_runtime.h>
+#include <cooperative_groups.h>
+#include <stdint.h>
+
+namespace miugks {
+
+constexpr int kKint = 1;                       // internal degrees of freedom
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kMaxLevels = 8;
+
+enum BcType { BC_WALL = 0, BC_SYMMETRY = 1, BC_FARFIELD = 2, BC_OUTFLOW = 3 };
+
+struct BcDev { int type; double rho, u, v, t; };
+
+// velocity space: k = a * nvv + b, u_k = ua[a], v_k = vb[b]
+struct VelDev {
+    int nu, nvv, nv;
+    const double *u, *v, *w;     // per discrete velocity
+    const double *ua, *vb;       // per-axis nodes
+    double umax, vmax;           // largest |u|, |v|
+};
+
+// one grid level (all device pointers)
+struct LevelDev {
+    int nx, ny, nc, nfx, nfy;
+    const double *xn, *yn, *xc, *yc, *dx, *dy;
+    const int *fbx, *fby;        // face BC id, -1 interior
+};
+
+struct GasDev { double mu_ref, omega, pr; };
+
+// ---------------------------------------------------------------------------
+// gas model
+__device__ __forceinline__ void prim4(const double* W, double& rho, double& U, double& V, double& lam)
+{
+    rho = W[0];
+    double ir = 1.0 / W[0];
+    U = W[1] * ir;
+    V = W[2] * ir;
+    double eint = W[3] - 0.5 * (W[1] * U + W[2] * V);
+    lam = (kKint + 2) * rho / (4.0 * eint);
+}
+
+__device__ __forceinline__ double tau_of(const GasDev& g, double rho, double lam)
+{
+    double T = 1.0 / lam;
+    return g.mu_ref * pow(T, g.omega) / (0.5 * rho * T);
+}
+
+// Time integrals of the UGKS integral solution over [0, dt] (x = dt/tau):
+// q[0..4] multiply g0, u_n a g0, A g0, f0, u_n sigma.  Series in x below 1.
+__device__ __forceinline__ void time_coeffs(double dt, double tau, double q[5])
+{
+    double x = dt / tau;
+    if (x < 1.0) {
+        // Horner-free explicit sums of the power series, terms x^n / n!
+        double pn = 1.0;             // x^n / n!
+        double s1 = 0, s2 = 0, s3 = 0, s4 = 0, s5 = 0;
+        #pragma unroll 1
+        for (int n = 0; n < 26; ++n) {
+            double sg = (n & 1) ? -1.0 : 1.0;
+            s4 += sg * pn / (n + 1);                      // (-1)^n x^n/(n+1)!
+            // m = n + 1 terms use x^{m-1}/(m-1)! = pn
+            int m = n + 1;
+            s5 += -sg * pn / (m + 1);                     // (-1)^m m x^{m-1}/(m+1)! = (-1)^m x^{m-1}/((m+1) (m-1)!)
+            if (m >= 2) s2 += -sg * (1.0 - m) * pn / ((double)m * (m + 1));
+            double pn1 = pn * x / (n + 1);                // x^{n+1}/(n+1)!
+            // n+1 >= 1 terms of q1, q3
+            s1 += sg * pn1 / (n + 2);                     // (-1)^{n+2} x^{n+1}/(n+2)!
+            s3 += sg * pn1 / ((double)(n + 2) * (n + 3));
+            pn = pn1;
+        }
+        q[0] = dt * s1;
+        q[1] = dt * dt * s2;
+        q[2] = dt * dt * s3;
+        q[3] = dt * s4;
+        q[4] = dt * dt * s5;
+    } else {
+        double e = exp(-x), E1 = -expm1(-x);
+        q[0] = dt - tau * E1;
+        q[1] = -tau * dt * (1.0 + e) + 2.0 * tau * tau * E1;
+        q[2] = 0.5 * dt * dt - tau * dt + tau * tau * E1;
+        q[3] = tau * E1;
+        q[4] = tau * dt * e - tau * tau * E1;
+    }
+}
+
+// moments dw (already divided by rho) -> slope coefficients of a Maxwellian at (U, V, lam)
+__device__ __forceinline__ void micro_slope(const double dw[4], double U, double V, double lam, double a[4])
+{
+    const double Kp2 = kKint + 2.0;
+    double c = U * U + V * V + Kp2 / (2.0 * lam);
+    double R4 = 2.0 * dw[3] - c * dw[0];
+    double R3 = dw[2] - V * dw[0];
+    double R2 = dw[1] - U * dw[0];
+    a[3] = 4.0 * lam * lam / Kp2 * (R4 - 2.0 * U * R2 - 2.0 * V * R3);
+    a[2] = 2.0 * lam * R3 - V * a[3];
+    a[1] = 2.0 * lam * R2 - U * a[3];
+    a[0] = dw[0] - U * a[1] - V * a[2] - 0.5 * a[3] * c;
+}
+
+template <typename T>
+__device__ __forceinline__ T van_leer(T s1, T s2)
+{
+    T p = s1 * s2;
+    return p > T(0) ? T(2) * p / (s1 + s2) : T(0);
+}
+
+// ---------------------------------------------------------------------------
+// deterministic block reduction of N doubles (fixed tree order); every thread
+// receives the result.  scratch: at least 32 * N doubles of shared memory.
+template <int N>
+__device__ __forceinline__ void block_sum(double (&v)[N], double* scratch)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    #pragma unroll
+    for (int q = 0; q < N; ++q) {
+        double x = v[q];
+        #pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        v[q] = x;
+    }
+    __syncthreads();
+    if (lane == 0) {
+        #pragma unroll
+        for (int q = 0; q < N; ++q) scratch[warp * N + q] = v[q];
+    }
+    __syncthreads();
+    #pragma unroll
+    for (int q = 0; q < N; ++q) {
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += scratch[w * N + q];
+        v[q] = s;
+    }
+    __syncthreads();
+}
+
+} // namespace miugks

@@ -1,0 +1,354 @@
+// flux.cu -- Step 1 of the MIUGKS iteration (arXiv 1704.03151, Sec. 2.1):
+// time-averaged UGKS interface fluxes of every discrete velocity (Eqs.
+// macroResidualCalc, microResidualDef) and the macroscopic residual R
+// (Eq. macroResidualDef), plus its RMS (Eq. Residual_Def).
+//
+// One CTA per face; threads stride over the discrete velocities, which are
+// contiguous in memory ([comp][cell][k]), so every load of f is coalesced.
+// The three velocity reductions a face needs (interface state W0; heat flux
+// and time slope; macroscopic flux) are deterministic block reductions.  The
+// equilibrium at the face is evaluated from separable per-axis exponential
+// tables (Nu + Nv exponentials per face instead of Nu * Nv).
+#include "kernels.cuh"
+
+namespace miugks {
+
+__constant__ double c_series[5][28];   // power-series coefficients of the time integrals
+
+void upload_series_coefficients()
+{
+    // q1/dt  = sum_{n>=1} (-1)^{n+1} x^n/(n+1)!
+    // q2/dt2 = sum_{n>=1} (-1)^n n x^n/(n+2)!
+    // q3/dt2 = sum_{n>=1} (-1)^{n+1} x^n/(n+2)!
+    // q4/dt  = sum_{n>=0} (-1)^n x^n/(n+1)!
+    // q5/dt2 = sum_{n>=0} (-1)^{n+1} (n+1) x^n/(n+2)!
+    double c[5][28] = {};
+    double fact[32];
+    fact[0] = 1.0;
+    for (int n = 1; n < 32; ++n) fact[n] = fact[n - 1] * n;
+    for (int n = 0; n < 28; ++n) {
+        double s = (n % 2) ? -1.0 : 1.0;                 // (-1)^n
+        c[0][n] = n >= 1 ? -s / fact[n + 1] : 0.0;
+        c[1][n] = n >= 1 ? s * n / fact[n + 2] : 0.0;
+        c[2][n] = n >= 1 ? -s / fact[n + 2] : 0.0;
+        c[3][n] = s / fact[n + 1];
+        c[4][n] = -s * (n + 1) / fact[n + 2];
+    }
+    cudaMemcpyToSymbol(c_series, c, sizeof c);
+}
+
+__device__ __forceinline__ void time_coeffs_fast(double dt, double tau, double q[5])
+{
+    double x = dt / tau;
+    if (x < 1.0) {
+        double s[5];
+        #pragma unroll
+        for (int m = 0; m < 5; ++m) {
+            double acc = c_series[m][27];
+            #pragma unroll
+            for (int n = 26; n >= 0; --n) acc = fma(acc, x, c_series[m][n]);
+            s[m] = acc;
+        }
+        q[0] = dt * s[0];
+        q[1] = dt * dt * s[1];
+        q[2] = dt * dt * s[2];
+        q[3] = dt * s[3];
+        q[4] = dt * dt * s[4];
+    } else {
+        time_coeffs(dt, tau, q);
+    }
+}
+
+// (a . psi) g split into the reduced components: b gM + a4 hM and b hM + a4 <xi^4>/4 gM
+__device__ __forceinline__ void slope_mom(const double* a, double u, double v, double gM, double hM,
+                                          double xi4q, double& mG, double& mH)
+{
+    double b = a[0] + a[1] * u + a[2] * v + 0.5 * a[3] * (u * u + v * v);
+    mG = b * gM + a[3] * hM;
+    mH = b * hM + a[3] * xi4q * gM;
+}
+
+template <typename F>
+__global__ void __launch_bounds__(256) k_face_flux(FaceFluxArgs<F> A)
+{
+    extern __shared__ double sm[];
+    const LevelDev& L = A.L;
+    const VelDev& Vg = A.V;
+    const int nv = Vg.nv, tid = threadIdx.x, bs = blockDim.x;
+    const int axis = A.axis, fi = blockIdx.x;
+    const int nx = L.nx, ny = L.ny;
+    const size_t nc = L.nc, nf = axis == 0 ? L.nfx : L.nfy;
+    double* red = sm;                       // 32 * 8
+    double* par = red + 256;                // face scalars
+    double* f0s = par + 64;                 // [2][nv]
+    double* sgs = f0s + 2 * nv;             // [2][nv]
+    double* Eu = sgs + 2 * nv;              // [nu]
+    double* Ev = Eu + Vg.nu;                // [nvv]
+    const int i = axis == 0 ? fi % (nx + 1) : fi % nx;
+    const int j = axis == 0 ? fi / (nx + 1) : fi / nx;
+    const int bcid = (axis == 0 ? L.fbx : L.fby)[fi];
+    const F* __restrict__ fG = A.f;
+    const F* __restrict__ fH = A.f + nc * nv;
+    F* __restrict__ phG = A.ph + (size_t)fi * nv;
+    F* __restrict__ phH = A.ph + (nf + fi) * (size_t)nv;
+
+    if (bcid >= 0) {
+        // ---------------- boundary face: free transport of the face distribution
+        const int outsign = (axis == 0 ? i == 0 : j == 0) ? -1 : 1;
+        const int c = axis == 0 ? j * nx + (i == 0 ? 0 : nx - 1) : (j == 0 ? 0 : ny - 1) * nx + i;
+        const BcDev B = A.bc[bcid];
+        const double* Cb = A.Cw + (size_t)bcid * nv;
+        const double Hfac = kKint * B.t / 4.0;   // K / (4 lambda_b)
+        double rhow = B.rho;
+        if (B.type == BC_WALL) {
+            double s[2] = {0.0, 0.0};
+            for (int k = tid; k < nv; k += bs) {
+                double uo = outsign * (axis == 0 ? Vg.u[k] : Vg.v[k]);
+                if (uo > 0) s[0] += Vg.w[k] * uo * (double)fG[c * (size_t)nv + k];
+                else if (uo < 0) s[1] += Vg.w[k] * uo * Cb[k];
+            }
+            block_sum<2>(s, red);
+            rhow = -s[0] / s[1];
+        }
+        double Fm[4] = {0, 0, 0, 0};
+        for (int k = tid; k < nv; k += bs) {
+            double un = axis == 0 ? Vg.u[k] : Vg.v[k];
+            double uo = outsign * un;
+            double g, h;
+            if (uo >= 0 || B.type == BC_OUTFLOW) {
+                g = fG[c * (size_t)nv + k]; h = fH[c * (size_t)nv + k];
+            } else if (B.type == BC_SYMMETRY) {
+                int a = k / Vg.nvv, b = k - a * Vg.nvv;
+                int km = axis == 0 ? (Vg.nu - 1 - a) * Vg.nvv + b : a * Vg.nvv + (Vg.nvv - 1 - b);
+                g = fG[c * (size_t)nv + km]; h = fH[c * (size_t)nv + km];
+            } else {   // wall (rho_w C) or farfield (rho_inf C)
+                g = rhow * Cb[k]; h = g * Hfac;
+            }
+            double pg = un * g, ph = un * h;
+            phG[k] = (F)pg; phH[k] = (F)ph;
+            double u = Vg.u[k], v = Vg.v[k], w = Vg.w[k];
+            Fm[0] += w * pg; Fm[1] += w * u * pg; Fm[2] += w * v * pg;
+            Fm[3] += w * (0.5 * (u * u + v * v) * pg + ph);
+        }
+        block_sum<4>(Fm, red);
+        if (tid == 0)
+            for (int m = 0; m < 4; ++m) A.Fm[4 * (size_t)fi + m] = Fm[m];
+        return;
+    }
+
+    // ---------------- interior face between cL (lower) and cR (upper)
+    int cL, cR, cLL = -1, cRR = -1;
+    double dLLL = 1, dLR, dRRR = 1, hL, hR, wL, wR;
+    if (axis == 0) {
+        cL = j * nx + i - 1; cR = cL + 1;
+        if (i - 1 > 0 && L.fbx[fi - 1] < 0) { cLL = cL - 1; dLLL = L.xc[i - 1] - L.xc[i - 2]; }
+        if (i + 1 < nx && L.fbx[fi + 1] < 0) { cRR = cR + 1; dRRR = L.xc[i + 1] - L.xc[i]; }
+        dLR = L.xc[i] - L.xc[i - 1];
+        hL = L.xn[i] - L.xc[i - 1]; hR = L.xc[i] - L.xn[i];
+        wL = L.dx[i - 1]; wR = L.dx[i];
+    } else {
+        cL = (j - 1) * nx + i; cR = cL + nx;
+        if (j - 1 > 0 && L.fby[fi - nx] < 0) { cLL = cL - nx; dLLL = L.yc[j - 1] - L.yc[j - 2]; }
+        if (j + 1 < ny && L.fby[fi + nx] < 0) { cRR = cR + nx; dRRR = L.yc[j + 1] - L.yc[j]; }
+        dLR = L.yc[j] - L.yc[j - 1];
+        hL = L.yn[j] - L.yc[j - 1]; hR = L.yc[j] - L.yn[j];
+        wL = L.dy[j - 1]; wR = L.dy[j];
+    }
+    const F r1 = (F)(1.0 / dLLL), r2 = (F)(1.0 / dLR), r3 = (F)(1.0 / dRRR);
+    const F fhL = (F)hL, fhR = (F)hR;
+
+    // pass 1: reconstruction, upwinding, interface conservative variables
+    double W0[4] = {0, 0, 0, 0};
+    for (int k = tid; k < nv; k += bs) {
+        double un = axis == 0 ? Vg.u[k] : Vg.v[k];
+        #pragma unroll
+        for (int cp = 0; cp < 2; ++cp) {
+            const F* fc = cp == 0 ? fG : fH;
+            F fL = fc[cL * (size_t)nv + k], fR = fc[cR * (size_t)nv + k];
+            F d2 = (fR - fL) * r2;
+            F sL = cLL >= 0 ? van_leer<F>((fL - fc[cLL * (size_t)nv + k]) * r1, d2) : F(0);
+            F sR = cRR >= 0 ? van_leer<F>(d2, (fc[cRR * (size_t)nv + k] - fR) * r3) : F(0);
+            F faceL = fL + sL * fhL, faceR = fR - sR * fhR;
+            double f0, sg;
+            if (un > 0) { f0 = faceL; sg = sL; }
+            else if (un < 0) { f0 = faceR; sg = sR; }
+            else { f0 = 0.5 * ((double)faceL + (double)faceR); sg = 0.5 * ((double)sL + (double)sR); }
+            f0s[cp * nv + k] = f0;
+            sgs[cp * nv + k] = sg;
+        }
+        double w = Vg.w[k], u = Vg.u[k], v = Vg.v[k], g = f0s[k];
+        W0[0] += w * g; W0[1] += w * u * g; W0[2] += w * v * g;
+        W0[3] += w * (0.5 * (u * u + v * v) * g + f0s[nv + k]);
+    }
+    block_sum<4>(W0, red);
+    // face scalars (one thread), broadcast through shared memory
+    if (tid == 0) {
+        double rho, U, V, lam;
+        prim4(W0, rho, U, V, lam);
+        double tau0 = tau_of(A.gas, rho, lam);
+        double um = axis == 0 ? Vg.umax : Vg.vmax;
+        double dt = A.cfl * fmin(wL, wR) / um;
+        const double* WL = A.W + 4 * (size_t)cL;
+        const double* WR = A.W + 4 * (size_t)cR;
+        double dwl[4], dwr[4], ir = 1.0 / rho;
+        for (int m = 0; m < 4; ++m) {
+            dwl[m] = (W0[m] - WL[m]) / hL * ir;
+            dwr[m] = (WR[m] - W0[m]) / hR * ir;
+        }
+        micro_slope(dwl, U, V, lam, par + 8);
+        micro_slope(dwr, U, V, lam, par + 12);
+        par[0] = rho; par[1] = U; par[2] = V; par[3] = lam; par[4] = tau0; par[5] = dt;
+    }
+    __syncthreads();
+    const double rho0 = par[0], U0 = par[1], V0 = par[2], lam0 = par[3];
+    for (int a = tid; a < Vg.nu; a += bs) { double d = Vg.ua[a] - U0; Eu[a] = exp(-lam0 * d * d); }
+    for (int b = tid; b < Vg.nvv; b += bs) { double d = Vg.vb[b] - V0; Ev[b] = exp(-lam0 * d * d); }
+    __syncthreads();
+    const double gnorm = rho0 * lam0 / kPi, hfac = kKint / (4.0 * lam0);
+    const double xi4q = kKint * (kKint + 2.0) / (16.0 * lam0 * lam0);
+    const double* aL = par + 8;
+    const double* aR = par + 12;
+
+    // pass 2: heat flux of the interface distribution, compatibility moments for A
+    double s6[6] = {0, 0, 0, 0, 0, 0};
+    for (int k = tid; k < nv; k += bs) {
+        int a = k / Vg.nvv, b = k - a * Vg.nvv;
+        double u = Vg.u[k], v = Vg.v[k], w = Vg.w[k];
+        double cx = u - U0, cy = v - V0, c2 = cx * cx + cy * cy;
+        double e = 0.5 * c2 * f0s[k] + f0s[nv + k];
+        s6[0] += w * cx * e;
+        s6[1] += w * cy * e;
+        double un = axis == 0 ? u : v;
+        if (un != 0.0) {
+            double gM = gnorm * Eu[a] * Ev[b], hM = gM * hfac, mG, mH;
+            slope_mom(un > 0 ? aL : aR, u, v, gM, hM, xi4q, mG, mH);
+            double wu = w * un;
+            s6[2] += wu * mG; s6[3] += wu * u * mG; s6[4] += wu * v * mG;
+            s6[5] += wu * (0.5 * (u * u + v * v) * mG + mH);
+        }
+    }
+    block_sum<6>(s6, red);
+    if (tid == 0) {
+        double dwt[4], ir = 1.0 / rho0;
+        for (int m = 0; m < 4; ++m) dwt[m] = -s6[2 + m] * ir;
+        micro_slope(dwt, U0, V0, lam0, par + 16);
+        time_coeffs_fast(par[5], par[4], par + 20);
+        par[6] = s6[0]; par[7] = s6[1];
+    }
+    __syncthreads();
+    const double* Aslope = par + 16;
+    const double q1 = par[20], q2 = par[21], q3 = par[22], q4 = par[23], q5 = par[24];
+    const double idt = 1.0 / par[5];
+    const double shk = (1.0 - A.gas.pr) * 4.0 * lam0 * lam0 / (5.0 * rho0);
+    const double qx = par[6], qy = par[7];
+
+    // pass 3: time-averaged flux of every discrete velocity and its moments
+    double Fm[4] = {0, 0, 0, 0};
+    for (int k = tid; k < nv; k += bs) {
+        int a = k / Vg.nvv, b = k - a * Vg.nvv;
+        double u = Vg.u[k], v = Vg.v[k], w = Vg.w[k];
+        double un = axis == 0 ? u : v;
+        double cx = u - U0, cy = v - V0, c2 = cx * cx + cy * cy;
+        double gM = gnorm * Eu[a] * Ev[b], hM = gM * hfac;
+        double Fq = shk * (cx * qx + cy * qy);
+        double gP = gM * (1.0 + Fq * (2.0 * lam0 * c2 - 4.0));
+        double hP = hM * (1.0 + Fq * (2.0 * lam0 * c2 - 2.0));
+        double mGa, mHa, mGA, mHA;
+        slope_mom(un > 0 ? aL : aR, u, v, gM, hM, xi4q, mGa, mHa);
+        slope_mom(Aslope, u, v, gM, hM, xi4q, mGA, mHA);
+        double pg = un * (q1 * gP + q2 * un * mGa + q3 * mGA + q4 * f0s[k] + q5 * un * sgs[k]) * idt;
+        double ph = un * (q1 * hP + q2 * un * mHa + q3 * mHA + q4 * f0s[nv + k] + q5 * un * sgs[nv + k]) * idt;
+        phG[k] = (F)pg; phH[k] = (F)ph;
+        Fm[0] += w * pg; Fm[1] += w * u * pg; Fm[2] += w * v * pg;
+        Fm[3] += w * (0.5 * (u * u + v * v) * pg + ph);
+    }
+    block_sum<4>(Fm, red);
+    if (tid == 0)
+        for (int m = 0; m < 4; ++m) A.Fm[4 * (size_t)fi + m] = Fm[m];
+}
+
+size_t face_flux_smem(const VelDev& V)
+{
+    return sizeof(double) * (256 + 64 + 4 * (size_t)V.nv + V.nu + V.nvv);
+}
+
+template <typename F>
+cudaError_t launch_face_flux(const FaceFluxArgs<F>& a, cudaStream_t st)
+{
+    size_t smem = face_flux_smem(a.V);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_face_flux<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    int nf = a.axis == 0 ? a.L.nfx : a.L.nfy;
+    int threads = a.V.nv >= 256 ? 256 : 128;
+    k_face_flux<F><<<nf, threads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+template cudaError_t launch_face_flux<double>(const FaceFluxArgs<double>&, cudaStream_t);
+
+// R_i = -(1/V_i) sum_j S_ij F_ij
+__global__ void k_cell_residual(LevelDev L, const double* __restrict__ Fx, const double* __restrict__ Fy,
+                                double* __restrict__ R)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= L.nc) return;
+    int i = c % L.nx, j = c / L.nx;
+    double V = L.dx[i] * L.dy[j];
+    const double* FW = Fx + 4 * (size_t)(j * (L.nx + 1) + i);
+    const double* FE = FW + 4;
+    const double* FS = Fy + 4 * (size_t)(j * L.nx + i);
+    const double* FN = Fy + 4 * (size_t)((j + 1) * L.nx + i);
+    for (int m = 0; m < 4; ++m)
+        R[4 * (size_t)c + m] = -(L.dy[j] * (FE[m] - FW[m]) + L.dx[i] * (FN[m] - FS[m])) / V;
+}
+
+cudaError_t launch_cell_residual(const LevelDev& L, const double* Fx, const double* Fy, double* R, cudaStream_t st)
+{
+    k_cell_residual<<<(L.nc + 127) / 128, 128, 0, st>>>(L, Fx, Fy, R);
+    return cudaGetLastError();
+}
+
+// sum of squares of R per component: per-block partials, then one block
+__global__ void k_rms_partial(const double* __restrict__ R, int nc, double* __restrict__ part)
+{
+    __shared__ double red[32 * 4];
+    double s[4] = {0, 0, 0, 0};
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x)
+        for (int m = 0; m < 4; ++m) s[m] += R[4 * (size_t)c + m] * R[4 * (size_t)c + m];
+    block_sum<4>(s, red);
+    if (threadIdx.x == 0)
+        for (int m = 0; m < 4; ++m) part[4 * blockIdx.x + m] = s[m];
+}
+
+__global__ void k_rms_final(const double* __restrict__ part, int nblk, int nc, const double* __restrict__ W,
+                            double* __restrict__ out)
+{
+    __shared__ double red[32 * 5];
+    double s[5] = {0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x)
+        for (int m = 0; m < 4; ++m) s[m] += part[4 * b + m];
+    // health of the state: count cells with non-positive density or internal energy (or NaN)
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+        const double* w = W + 4 * (size_t)c;
+        double eint = w[3] - 0.5 * (w[1] * w[1] + w[2] * w[2]) / w[0];
+        if (!(w[0] > 0.0) || !(eint > 0.0)) s[4] += 1.0;
+    }
+    block_sum<5>(s, red);
+    if (threadIdx.x == 0) {
+        for (int m = 0; m < 4; ++m) out[m] = sqrt(s[m] / nc);
+        out[4] = s[4];
+    }
+}
+
+cudaError_t launch_rms(const double* R, const double* W, int nc, double* part, double* out, cudaStream_t st)
+{
+    int nblk = 64;
+    k_rms_partial<<<nblk, 256, 0, st>>>(R, nc, part);
+    k_rms_final<<<1, 256, 0, st>>>(part, nblk, nc, W, out);
+    return cudaGetLastError();
+}
+
+} // namespace miugks

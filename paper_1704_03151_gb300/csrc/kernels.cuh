@@ -1,0 +1,84 @@
+// kernels.cuh -- argument structs and launchers of the MIUGKS kernels.
+#pragma once
+#include "common.cuh"
+
+namespace miugks {
+
+template <typename F>
+struct FaceFluxArgs {
+    LevelDev L; VelDev V; GasDev gas;
+    const BcDev* bc; const double* Cw;     // Cw[b * nv + k]: unit-density Maxwellian of BC b
+    const F* f;                            // [2][nc][nv]
+    const double* W;                       // [nc][4]
+    F* ph;                                 // [2][nf][nv] time-averaged micro flux, along +axis
+    double* Fm;                            // [nf][4] macro flux
+    int axis; double cfl;
+};
+
+void upload_series_coefficients();
+template <typename F> cudaError_t launch_face_flux(const FaceFluxArgs<F>& a, cudaStream_t st);
+cudaError_t launch_cell_residual(const LevelDev& L, const double* Fx, const double* Fy, double* R, cudaStream_t st);
+cudaError_t launch_rms(const double* R, const double* W, int nc, double* part, double* out, cudaStream_t st);
+
+// ---- prediction step (macroscopic, FP64) ----
+struct MacroArgs {
+    LevelDev L; GasDev gas; const BcDev* bc;
+    double dtn_inv;                        // 1/dt_n (0 when off)
+};
+// Gamma of every face from the frozen state Wg
+cudaError_t launch_macro_gamma(const MacroArgs& a, const double* Wg, double* gx, double* gy, cudaStream_t st);
+// mode 0: out = Rin - R_E(W)  (forcing);  mode 1: out = Rin + R_E(W)  (renewal P + R_E)
+cudaError_t launch_macro_resid(const MacroArgs& a, const double* W, const double* gx, const double* gy,
+                               const double* Rin, double* out, int mode, cudaStream_t st);
+// one LU-SGS pass: dW from R at state W; then W += dW
+cudaError_t launch_macro_sgs(const MacroArgs& a, double* W, const double* gx, const double* gy,
+                             const double* R, double* dW, int* err, cudaStream_t st);
+cudaError_t launch_restrict(const LevelDev& F, const LevelDev& C, int m, int nblk, const double* fine, double* coarse,
+                            cudaStream_t st);
+// fine += prolong(coarse) (m components per cell, nblk blocks of [nc][m]); also writes the
+// prolongated values into out_pro when it is not null
+// idx4/w4: per fine cell the four coarse stencil cells and their bilinear weights
+cudaError_t launch_prolong_add(const LevelDev& F, const LevelDev& C, int m, int nblk, const int* idx4,
+                               const double* w4, const double* coarse, double* fine, double* out_pro,
+                               cudaStream_t st);
+cudaError_t launch_axpy(double* y, const double* x, double a, size_t n, cudaStream_t st);
+cudaError_t launch_sub(double* out, const double* a, const double* b, size_t n, cudaStream_t st);
+
+// ---- evolution step (microscopic) ----
+struct MicroArgs {
+    LevelDev L; VelDev V; const BcDev* bc; const double* Cw;
+    const double* inv_tau;                 // [nc] collision frequency (+ 1/dt_n)
+};
+// Step 3-4: r = (g~ - f)/tau~ - div(ph) on level 0; also inv_tau (with dtn_inv) and invD
+template <typename F>
+cudaError_t launch_micro_residual(const MicroArgs& m, GasDev gas, const double* Wt, const double* q,
+                                  const F* f, const F* phx, const F* phy, double dtn_inv,
+                                  double* inv_tau, F* invD, F* r, cudaStream_t st);
+// inv_tau and invD of a coarse level from its restricted predicted state
+template <typename F>
+cudaError_t launch_coarse_coeffs(const MicroArgs& m, GasDev gas, const double* Wt, double dtn_inv,
+                                 double* inv_tau, F* invD, cudaStream_t st);
+// one symmetric Gauss-Seidel pass: x = SGS(r).  Zw[b*4 + axis*2 + (outsign>0)] = sum over the
+// incoming velocities of w u_n C_k of wall BC b; xcorner: scratch of 2*nv values
+template <typename F>
+cudaError_t launch_micro_sgs(const MicroArgs& m, const double* Zw, const F* invD, const F* r, F* x, F* xcorner,
+                             cudaStream_t st);
+// r -= A x (when renew) and acc += x (when acc != null)
+template <typename F>
+cudaError_t launch_micro_renew(const MicroArgs& m, const double* Zw, const F* x, F* r, F* acc, int renew,
+                               cudaStream_t st);
+// Steps 6-7: f += df; W, q from moments
+template <typename F>
+cudaError_t launch_update_moments(const LevelDev& L, const VelDev& V, F* f, const F* df, double* W, double* q,
+                                  cudaStream_t st);
+template <typename F>
+cudaError_t launch_moments(const LevelDev& L, const VelDev& V, const F* f, double* W, double* q, cudaStream_t st);
+template <typename F>
+cudaError_t launch_init_maxwell(const LevelDev& L, const VelDev& V, const double* prim, F* f, cudaStream_t st);
+// per wall face p, tau, q (one block per face of BC bc, in face order)
+template <typename F>
+cudaError_t launch_wall_quantities(const LevelDev& L, const VelDev& V, const BcDev* bc, const double* Cw,
+                                   const F* f, int bcid, const int* faces, int nfaces, double* out,
+                                   cudaStream_t st);
+
+} // namespace miugks

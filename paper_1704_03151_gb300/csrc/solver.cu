@@ -1,0 +1,850 @@
+// solver.cu -- host side of the MIUGKS library: the C ABI of include/miugks.h,
+// the mesh hierarchy (Sec. 3.1), device memory, and the multigrid cycles of
+// Sec. 2.4 (Eq. FASCYC for the prediction, Eq. CSCYC for the evolution)
+// driving the kernels of flux.cu, macro.cu and micro.cu on one CUDA stream.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/miugks.h"
+#include "kernels.cuh"
+
+using namespace miugks;
+
+namespace {
+
+struct HLevel {
+    int nx = 0, ny = 0, nc = 0, nfx = 0, nfy = 0;
+    std::vector<double> xn, yn, xc, yc, dx, dy;
+    std::vector<int> fbx, fby;
+    LevelDev dev{};
+    int* pidx = nullptr;      // prolongation stencil from the next coarser level
+    double* pw = nullptr;
+    // prediction work, [nc][4]
+    double *Wn = nullptr, *Wc = nullptr, *Rc = nullptr, *P = nullptr, *R = nullptr, *dW = nullptr, *gx = nullptr,
+           *gy = nullptr, *Wt = nullptr;
+    // evolution work, [2][nc][nv] (invD [nc][nv])
+    double *r = nullptr, *df = nullptr, *dl = nullptr, *invD = nullptr, *inv_tau = nullptr;
+};
+
+} // namespace
+
+struct miugks_solver {
+    std::string err;
+    miugks_opts opts{};
+    cudaStream_t st = nullptr;
+    std::vector<void*> allocs;
+    int L = 1, nu = 0, nvv = 0, nv = 0, nbc = 0;
+    double umax = 0, vmax = 0;
+    GasDev gas{};
+    std::vector<BcDev> bch;
+    std::vector<double> uh, vh, wh, uah, vbh;
+    VelDev vel{};
+    BcDev* bc = nullptr;
+    double *Cw = nullptr, *Zw = nullptr;
+    std::vector<double> Cwh;
+    HLevel lev[kMaxLevels];
+    // finest-level state
+    double *f = nullptr, *W = nullptr, *q = nullptr, *R = nullptr, *phx = nullptr, *phy = nullptr, *Fx = nullptr,
+           *Fy = nullptr;
+    double *rms_part = nullptr, *rms_out = nullptr, *xcorner = nullptr;
+    double dtp_min = 0;
+    int iter = 0;
+    bool initialised = false;
+    bool timing = false;
+    cudaEvent_t ev[6] = {};
+    double t_flux = 0, t_sweep = 0, t_total = 0;
+};
+
+namespace {
+
+miugks_status fail(miugks_solver* s, miugks_status code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (s) s->err = buf;
+    return code;
+}
+
+#define CK(expr)                                                                                     \
+    do {                                                                                             \
+        cudaError_t e_ = (expr);                                                                     \
+        if (e_ != cudaSuccess) return fail(s, MIUGKS_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+    } while (0)
+#define ST(expr)                                  \
+    do {                                          \
+        miugks_status st_ = (expr);               \
+        if (st_ != MIUGKS_OK) return st_;         \
+    } while (0)
+
+template <typename T>
+miugks_status dalloc(miugks_solver* s, T** p, size_t count)
+{
+    size_t bytes = count * sizeof(T);
+    if (bytes == 0) bytes = 16;
+    void* ptr = nullptr;
+    if (s->opts.dev_alloc) {
+        ptr = s->opts.dev_alloc(bytes, s->opts.alloc_ctx);
+        if (!ptr) return fail(s, MIUGKS_ENOMEM, "device allocation of %zu bytes failed", bytes);
+    } else {
+        cudaError_t e = cudaMalloc(&ptr, bytes);
+        if (e != cudaSuccess) return fail(s, MIUGKS_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    }
+    s->allocs.push_back(ptr);
+    *p = (T*)ptr;
+    return MIUGKS_OK;
+}
+
+template <typename T>
+miugks_status upload(miugks_solver* s, T** p, const std::vector<T>& h)
+{
+    ST(dalloc(s, p, h.size()));
+    CK(cudaMemcpyAsync(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s->st));
+    return MIUGKS_OK;
+}
+
+// discrete velocity nodes and weights of one axis (symmetric placement)
+bool axis_grid(int n, double a, double b, int rule, std::vector<double>& x, std::vector<double>& w)
+{
+    if (n < 2 || !(b > a)) return false;
+    x.resize(n);
+    w.assign(n, 0.0);
+    double h = (b - a) / (n - 1), c = 0.5 * (a + b);
+    for (int i = 0; i < n; ++i) x[i] = c + (i - 0.5 * (n - 1)) * h;
+    if (rule == 0) {
+        for (int i = 0; i < n; ++i) w[i] = h;
+        w[0] = w[n - 1] = 0.5 * h;
+    } else if (rule == 1) {
+        if ((n - 1) % 4) return false;
+        static const double pan[5] = {7, 32, 12, 32, 7};
+        for (int p = 0; p + 4 < n; p += 4)
+            for (int q = 0; q < 5; ++q) w[p + q] += pan[q];
+        for (int i = 0; i < n; ++i) w[i] *= 2.0 * h / 45.0;
+    } else {
+        return false;
+    }
+    return true;
+}
+
+double maxwell_unit(double U, double V, double T, double u, double v)
+{
+    double lam = 1.0 / T;
+    return lam / kPi * std::exp(-lam * ((u - U) * (u - U) + (v - V) * (v - V)));
+}
+
+// unit-density Maxwellian of BC b at every discrete velocity (wall C_k, Eq. f_on_wall)
+void refresh_bc_tables(miugks_solver* s, int b)
+{
+    const BcDev& B = s->bch[b];
+    for (int k = 0; k < s->nv; ++k) s->Cwh[(size_t)b * s->nv + k] = maxwell_unit(B.u, B.v, B.t, s->uh[k], s->vh[k]);
+}
+
+std::vector<double> wall_norms(miugks_solver* s)
+{
+    std::vector<double> Zh((size_t)s->nbc * 4, 0.0);
+    for (int b = 0; b < s->nbc; ++b)
+        for (int k = 0; k < s->nv; ++k) {
+            double C = s->Cwh[(size_t)b * s->nv + k];
+            for (int axis = 0; axis < 2; ++axis)
+                for (int pos = 0; pos < 2; ++pos) {
+                    double uo = (pos ? 1.0 : -1.0) * (axis == 0 ? s->uh[k] : s->vh[k]);
+                    if (uo < 0) Zh[(size_t)b * 4 + axis * 2 + pos] += s->wh[k] * uo * C;
+                }
+        }
+    return Zh;
+}
+
+void level_geometry(HLevel& Lv)
+{
+    Lv.xc.resize(Lv.nx); Lv.dx.resize(Lv.nx); Lv.yc.resize(Lv.ny); Lv.dy.resize(Lv.ny);
+    for (int i = 0; i < Lv.nx; ++i) { Lv.dx[i] = Lv.xn[i + 1] - Lv.xn[i]; Lv.xc[i] = 0.5 * (Lv.xn[i] + Lv.xn[i + 1]); }
+    for (int j = 0; j < Lv.ny; ++j) { Lv.dy[j] = Lv.yn[j + 1] - Lv.yn[j]; Lv.yc[j] = 0.5 * (Lv.yn[j] + Lv.yn[j + 1]); }
+}
+
+// linear weights in one direction for a fine centre x inside coarse cell I
+void lin_weights(const std::vector<double>& Xc, int I, double x, int& N, double& wA, double& wN)
+{
+    int n = (int)Xc.size();
+    int nb = x < Xc[I] ? I - 1 : I + 1;
+    if (nb < 0 || nb >= n) nb = x < Xc[I] ? I + 1 : I - 1;
+    if (nb < 0 || nb >= n) { N = I; wA = 1.0; wN = 0.0; return; }
+    N = nb;
+    double span = Xc[nb] - Xc[I];
+    wA = (Xc[nb] - x) / span;
+    wN = (x - Xc[I]) / span;
+}
+
+miugks_status upload_level(miugks_solver* s, HLevel& Lv)
+{
+    double *xn, *yn, *xc, *yc, *dx, *dy;
+    int *fbx, *fby;
+    ST(upload(s, &xn, Lv.xn)); ST(upload(s, &yn, Lv.yn)); ST(upload(s, &xc, Lv.xc)); ST(upload(s, &yc, Lv.yc));
+    ST(upload(s, &dx, Lv.dx)); ST(upload(s, &dy, Lv.dy)); ST(upload(s, &fbx, Lv.fbx)); ST(upload(s, &fby, Lv.fby));
+    Lv.dev = LevelDev{Lv.nx, Lv.ny, Lv.nc, Lv.nfx, Lv.nfy, xn, yn, xc, yc, dx, dy, fbx, fby};
+    size_t n4 = 4 * (size_t)Lv.nc, nf = 2 * (size_t)Lv.nc * s->nv;
+    ST(dalloc(s, &Lv.Wn, n4)); ST(dalloc(s, &Lv.Wc, n4)); ST(dalloc(s, &Lv.Rc, n4)); ST(dalloc(s, &Lv.P, n4));
+    ST(dalloc(s, &Lv.R, n4)); ST(dalloc(s, &Lv.dW, n4)); ST(dalloc(s, &Lv.Wt, n4));
+    ST(dalloc(s, &Lv.gx, (size_t)Lv.nfx)); ST(dalloc(s, &Lv.gy, (size_t)Lv.nfy));
+    ST(dalloc(s, &Lv.r, nf)); ST(dalloc(s, &Lv.df, nf)); ST(dalloc(s, &Lv.dl, nf));
+    ST(dalloc(s, &Lv.invD, (size_t)Lv.nc * s->nv)); ST(dalloc(s, &Lv.inv_tau, (size_t)Lv.nc));
+    return MIUGKS_OK;
+}
+
+MicroArgs micro_args(miugks_solver* s, int l)
+{
+    return MicroArgs{s->lev[l].dev, s->vel, s->bc, s->Cw, s->lev[l].inv_tau};
+}
+
+MacroArgs macro_args(miugks_solver* s, int l, double dtn_inv)
+{
+    return MacroArgs{s->lev[l].dev, s->gas, s->bc, dtn_inv};
+}
+
+double dtn_inv(miugks_solver* s)
+{
+    if (!(s->opts.dtn_growth > 0.0)) return 0.0;
+    return 1.0 / (std::pow(s->opts.dtn_growth, (double)s->iter) * s->dtp_min);
+}
+
+// ---------------------------------------------------------------- cycles
+miugks_status fas(miugks_solver* s, int l, double dti)
+{
+    HLevel& Lv = s->lev[l];
+    MacroArgs ma = macro_args(s, l, dti);
+    size_t n4 = 4 * (size_t)Lv.nc;
+    CK(launch_macro_gamma(ma, Lv.Wn, Lv.gx, Lv.gy, s->st));
+    CK(launch_macro_resid(ma, Lv.Wn, Lv.gx, Lv.gy, Lv.Rc, Lv.P, 0, s->st));     // forcing function
+    CK(cudaMemcpyAsync(Lv.Wc, Lv.Wn, n4 * sizeof(double), cudaMemcpyDeviceToDevice, s->st));
+    CK(cudaMemcpyAsync(Lv.R, Lv.Rc, n4 * sizeof(double), cudaMemcpyDeviceToDevice, s->st));
+    const bool coarsest = l == s->L - 1;
+    const int npre = coarsest ? (s->L == 1 ? 1 : s->opts.nu_coarse) : s->opts.nu1;
+    for (int m = 0; m < npre; ++m) {
+        CK(launch_macro_sgs(ma, Lv.Wc, Lv.gx, Lv.gy, Lv.R, Lv.dW, nullptr, s->st));
+        if (coarsest && m == npre - 1) break;
+        CK(launch_macro_resid(ma, Lv.Wc, Lv.gx, Lv.gy, Lv.P, Lv.R, 1, s->st));  // renewal P + R_E(W)
+    }
+    if (coarsest) return MIUGKS_OK;
+    HLevel& Cv = s->lev[l + 1];
+    CK(launch_restrict(Lv.dev, Cv.dev, 4, 1, Lv.Wc, Cv.Wn, s->st));
+    CK(launch_restrict(Lv.dev, Cv.dev, 4, 1, Lv.R, Cv.Rc, s->st));
+    ST(fas(s, l + 1, dti));
+    CK(launch_sub(Cv.dW, Cv.Wc, Cv.Wn, 4 * (size_t)Cv.nc, s->st));
+    CK(launch_prolong_add(Lv.dev, Cv.dev, 4, 1, Lv.pidx, Lv.pw, Cv.dW, Lv.Wc, nullptr, s->st));
+    for (int m = 0; m < s->opts.nu2; ++m) {
+        CK(launch_macro_resid(ma, Lv.Wc, Lv.gx, Lv.gy, Lv.P, Lv.R, 1, s->st));
+        CK(launch_macro_sgs(ma, Lv.Wc, Lv.gx, Lv.gy, Lv.R, Lv.dW, nullptr, s->st));
+    }
+    return MIUGKS_OK;
+}
+
+miugks_status cs(miugks_solver* s, int l)
+{
+    HLevel& Lv = s->lev[l];
+    MicroArgs mi = micro_args(s, l);
+    size_t n = 2 * (size_t)Lv.nc * s->nv;
+    CK(cudaMemsetAsync(Lv.df, 0, n * sizeof(double), s->st));
+    const bool coarsest = l == s->L - 1;
+    const int npre = coarsest ? (s->L == 1 ? 1 : s->opts.nu_coarse) : s->opts.nu1;
+    for (int m = 0; m < npre; ++m) {
+        CK(launch_micro_sgs<double>(mi, s->Zw, Lv.invD, Lv.r, Lv.dl, s->xcorner, s->st));
+        bool last = coarsest && m == npre - 1;
+        CK(launch_micro_renew<double>(mi, s->Zw, Lv.dl, Lv.r, Lv.df, last ? 0 : 1, s->st));
+        if (last) return MIUGKS_OK;
+    }
+    HLevel& Cv = s->lev[l + 1];
+    CK(launch_restrict(Lv.dev, Cv.dev, s->nv, 2, Lv.r, Cv.r, s->st));
+    ST(cs(s, l + 1));
+    CK(launch_prolong_add(Lv.dev, Cv.dev, s->nv, 2, Lv.pidx, Lv.pw, Cv.df, Lv.df, Lv.dl, s->st));
+    for (int m = 0; m < s->opts.nu2; ++m) {
+        CK(launch_micro_renew<double>(mi, s->Zw, Lv.dl, Lv.r, nullptr, 1, s->st));
+        CK(launch_micro_sgs<double>(mi, s->Zw, Lv.invD, Lv.r, Lv.dl, s->xcorner, s->st));
+        CK(launch_micro_renew<double>(mi, s->Zw, Lv.dl, Lv.r, Lv.df, 0, s->st));
+    }
+    return MIUGKS_OK;
+}
+
+miugks_status flux_stage(miugks_solver* s)
+{
+    HLevel& L0 = s->lev[0];
+    FaceFluxArgs<double> fa{L0.dev, s->vel, s->gas, s->bc, s->Cw, s->f, s->W, s->phx, s->Fx, 0, s->opts.cfl};
+    CK(launch_face_flux<double>(fa, s->st));
+    fa.axis = 1; fa.ph = s->phy; fa.Fm = s->Fy;
+    CK(launch_face_flux<double>(fa, s->st));
+    CK(launch_cell_residual(L0.dev, s->Fx, s->Fy, s->R, s->st));
+    return MIUGKS_OK;
+}
+
+miugks_status one_iteration(miugks_solver* s)
+{
+    HLevel& L0 = s->lev[0];
+    const double dti = dtn_inv(s);
+    if (s->timing) CK(cudaEventRecord(s->ev[0], s->st));
+    ST(flux_stage(s));                                                       // Step 1
+    if (s->timing) CK(cudaEventRecord(s->ev[1], s->st));
+    CK(launch_rms(s->R, s->W, L0.nc, s->rms_part, s->rms_out, s->st));
+    size_t n4 = 4 * (size_t)L0.nc;
+    CK(cudaMemcpyAsync(L0.Wn, s->W, n4 * sizeof(double), cudaMemcpyDeviceToDevice, s->st));
+    CK(cudaMemcpyAsync(L0.Rc, s->R, n4 * sizeof(double), cudaMemcpyDeviceToDevice, s->st));
+    ST(fas(s, 0, dti));                                                      // Step 2
+    CK(cudaMemcpyAsync(L0.Wt, L0.Wc, n4 * sizeof(double), cudaMemcpyDeviceToDevice, s->st));
+    MicroArgs m0 = micro_args(s, 0);                                         // Steps 3-4
+    CK(launch_micro_residual<double>(m0, s->gas, L0.Wt, s->q, s->f, s->phx, s->phy, dti, L0.inv_tau, L0.invD,
+                                     L0.r, s->st));
+    for (int l = 1; l < s->L; ++l) {
+        CK(launch_restrict(s->lev[l - 1].dev, s->lev[l].dev, 4, 1, s->lev[l - 1].Wt, s->lev[l].Wt, s->st));
+        CK(launch_coarse_coeffs<double>(micro_args(s, l), s->gas, s->lev[l].Wt, dti, s->lev[l].inv_tau,
+                                        s->lev[l].invD, s->st));
+    }
+    if (s->timing) CK(cudaEventRecord(s->ev[2], s->st));
+    ST(cs(s, 0));                                                            // Step 5
+    if (s->timing) CK(cudaEventRecord(s->ev[3], s->st));
+    CK(launch_update_moments<double>(L0.dev, s->vel, s->f, L0.df, s->W, s->q, s->st));   // Steps 6-7
+    if (s->timing) CK(cudaEventRecord(s->ev[4], s->st));
+    s->iter++;
+    return MIUGKS_OK;
+}
+
+miugks_status read_residual(miugks_solver* s, double res_out[4])
+{
+    double h[5];
+    CK(cudaMemcpyAsync(h, s->rms_out, sizeof h, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    if (res_out) memcpy(res_out, h, 4 * sizeof(double));
+    bool bad = h[4] > 0;
+    for (int m = 0; m < 4; ++m) bad = bad || !std::isfinite(h[m]);
+    if (bad) return fail(s, MIUGKS_EDIVERGED, "diverged at iteration %d (%.0f unphysical cells)", s->iter, h[4]);
+    return MIUGKS_OK;
+}
+
+miugks_status check_level(miugks_solver* s, int lev)
+{
+    if (!s) return MIUGKS_EINVAL;
+    if (lev < 0 || lev >= s->L) return fail(s, MIUGKS_EINVAL, "level %d out of range", lev);
+    return MIUGKS_OK;
+}
+
+} // namespace
+
+// =========================================================================== C ABI
+extern "C" {
+
+static thread_local std::string g_create_err;
+
+const char* miugks_last_error(const miugks_solver* s) { return s ? s->err.c_str() : g_create_err.c_str(); }
+
+void miugks_destroy(miugks_solver* s)
+{
+    if (!s) return;
+    if (s->st) cudaStreamSynchronize(s->st);
+    else cudaDeviceSynchronize();
+    for (void* p : s->allocs) {
+        if (s->opts.dev_free) s->opts.dev_free(p, s->opts.alloc_ctx);
+        else cudaFree(p);
+    }
+    for (auto& e : s->ev)
+        if (e) cudaEventDestroy(e);
+    delete s;
+}
+
+miugks_status miugks_create(const miugks_mesh* mesh, const miugks_vgrid* vg, const miugks_gas* gas,
+                            const miugks_bc* bcs, int n_bcs, const miugks_opts* opts, miugks_solver** out)
+{
+    if (!out) return MIUGKS_EINVAL;
+    *out = nullptr;
+    if (!mesh || !vg || !gas || !bcs || !opts || n_bcs < 1) return MIUGKS_EINVAL;
+    miugks_solver* s = new miugks_solver();
+    s->opts = *opts;
+    s->st = (cudaStream_t)opts->cuda_stream;
+    auto bad = [&](const char* fmt, auto... a) {
+        fail(s, MIUGKS_EINVAL, fmt, a...);
+        return MIUGKS_EINVAL;
+    };
+    miugks_status st = MIUGKS_OK;
+    do {
+        if (opts->precision != MIUGKS_FP64) { st = bad("unsupported precision %d", opts->precision); break; }
+        if (opts->levels < 1 || opts->levels > kMaxLevels) { st = bad("levels must be 1..%d", kMaxLevels); break; }
+        if (opts->nu1 < 1 || opts->nu2 < 1 || opts->nu_coarse < 1) { st = bad("smoothing counts must be >= 1"); break; }
+        if (!(opts->cfl > 0.0)) { st = bad("cfl must be positive"); break; }
+        if (mesh->nx < 1 || mesh->ny < 1) { st = bad("empty mesh"); break; }
+        int div = 1 << (opts->levels - 1);
+        if (mesh->nx % div || mesh->ny % div) { st = bad("nx, ny must be divisible by 2^(levels-1) = %d", div); break; }
+        s->L = opts->levels;
+        std::vector<double> ua, wa, vb, wb;
+        if (!axis_grid(vg->nu, vg->umin, vg->umax, vg->rule, ua, wa) ||
+            !axis_grid(vg->nv, vg->vmin, vg->vmax, vg->rule, vb, wb)) {
+            st = bad("bad velocity grid (n >= 2, max > min, rule 0, or rule 1 with (n-1) %% 4 == 0)");
+            break;
+        }
+        s->nu = vg->nu; s->nvv = vg->nv; s->nv = vg->nu * vg->nv;
+        s->uah = ua; s->vbh = vb;
+        s->uh.resize(s->nv); s->vh.resize(s->nv); s->wh.resize(s->nv);
+        for (int a = 0; a < s->nu; ++a)
+            for (int b = 0; b < s->nvv; ++b) {
+                int k = a * s->nvv + b;
+                s->uh[k] = ua[a]; s->vh[k] = vb[b]; s->wh[k] = wa[a] * wb[b];
+            }
+        s->umax = std::fmax(std::fabs(vg->umin), std::fabs(vg->umax));
+        s->vmax = std::fmax(std::fabs(vg->vmin), std::fabs(vg->vmax));
+        bool symgrid = vg->umin == -vg->umax && vg->vmin == -vg->vmax;
+        if (!(gas->kn > 0) || !(gas->pr > 0)) { st = bad("Kn and Pr must be positive"); break; }
+        s->gas = GasDev{15.0 * std::sqrt(kPi) * gas->kn / (2.0 * (5.0 - 2.0 * gas->omega) * (7.0 - 2.0 * gas->omega)),
+                        gas->omega, gas->pr};
+        s->nbc = n_bcs;
+        s->bch.resize(n_bcs);
+        for (int b = 0; b < n_bcs; ++b) {
+            const miugks_bc& B = bcs[b];
+            if (B.type < 0 || B.type > 3 || !(B.t > 0)) { st = bad("bad BC %d", b); break; }
+            if (B.type == MIUGKS_BC_SYMMETRY && !symgrid) { st = bad("symmetry BC needs a velocity grid symmetric about 0"); break; }
+            if (B.type == MIUGKS_BC_FARFIELD && !(B.rho > 0)) { st = bad("farfield BC %d needs rho > 0", b); break; }
+            s->bch[b] = BcDev{B.type, B.rho, B.u, B.v, B.t};
+        }
+        if (st != MIUGKS_OK) break;
+        // level 0
+        HLevel& L0 = s->lev[0];
+        L0.nx = mesh->nx; L0.ny = mesh->ny; L0.nc = L0.nx * L0.ny;
+        L0.nfx = (L0.nx + 1) * L0.ny; L0.nfy = L0.nx * (L0.ny + 1);
+        L0.xn.assign(mesh->x_nodes, mesh->x_nodes + L0.nx + 1);
+        L0.yn.assign(mesh->y_nodes, mesh->y_nodes + L0.ny + 1);
+        L0.fbx.assign(mesh->face_bc_x, mesh->face_bc_x + L0.nfx);
+        L0.fby.assign(mesh->face_bc_y, mesh->face_bc_y + L0.nfy);
+        for (int i = 0; i < L0.nx && st == MIUGKS_OK; ++i)
+            if (!(L0.xn[i + 1] > L0.xn[i])) st = bad("x nodes must increase");
+        for (int j = 0; j < L0.ny && st == MIUGKS_OK; ++j)
+            if (!(L0.yn[j + 1] > L0.yn[j])) st = bad("y nodes must increase");
+        for (int j = 0; j < L0.ny && st == MIUGKS_OK; ++j)
+            for (int i = 0; i <= L0.nx; ++i) {
+                int b = L0.fbx[j * (L0.nx + 1) + i];
+                bool edge = i == 0 || i == L0.nx;
+                if (edge ? (b < 0 || b >= n_bcs) : b != -1) { st = bad("x-face (%d,%d): edge faces need a BC id, interior faces -1", i, j); break; }
+            }
+        for (int j = 0; j <= L0.ny && st == MIUGKS_OK; ++j)
+            for (int i = 0; i < L0.nx; ++i) {
+                int b = L0.fby[j * L0.nx + i];
+                bool edge = j == 0 || j == L0.ny;
+                if (edge ? (b < 0 || b >= n_bcs) : b != -1) { st = bad("y-face (%d,%d): edge faces need a BC id, interior faces -1", i, j); break; }
+            }
+        if (st != MIUGKS_OK) break;
+        level_geometry(L0);
+        for (int l = 1; l < s->L && st == MIUGKS_OK; ++l) {
+            HLevel& F = s->lev[l - 1];
+            HLevel& C = s->lev[l];
+            C.nx = F.nx / 2; C.ny = F.ny / 2; C.nc = C.nx * C.ny;
+            C.nfx = (C.nx + 1) * C.ny; C.nfy = C.nx * (C.ny + 1);
+            for (int I = 0; I <= C.nx; ++I) C.xn.push_back(F.xn[2 * I]);
+            for (int J = 0; J <= C.ny; ++J) C.yn.push_back(F.yn[2 * J]);
+            C.fbx.resize(C.nfx); C.fby.resize(C.nfy);
+            for (int J = 0; J < C.ny && st == MIUGKS_OK; ++J)
+                for (int I = 0; I <= C.nx; ++I) {
+                    int a = F.fbx[(2 * J) * (F.nx + 1) + 2 * I], b = F.fbx[(2 * J + 1) * (F.nx + 1) + 2 * I];
+                    if (a != b) { st = bad("level %d x-face (%d,%d) spans two boundary ids", l, I, J); break; }
+                    C.fbx[J * (C.nx + 1) + I] = a;
+                }
+            for (int J = 0; J <= C.ny && st == MIUGKS_OK; ++J)
+                for (int I = 0; I < C.nx; ++I) {
+                    int a = F.fby[(2 * J) * F.nx + 2 * I], b = F.fby[(2 * J) * F.nx + 2 * I + 1];
+                    if (a != b) { st = bad("level %d y-face (%d,%d) spans two boundary ids", l, I, J); break; }
+                    C.fby[J * C.nx + I] = a;
+                }
+            level_geometry(C);
+        }
+        if (st != MIUGKS_OK) break;
+        // chain kernel capacity: velocities per CTA of the 8-CTA cluster
+        int nloc = (((s->nu + 1) / 2 + 7) / 8) * 2 * s->nvv;
+        if (nloc > 8 * 256) { st = bad("velocity grid too large for the boundary-line kernel (%d local > 2048)", nloc); break; }
+        // device data (on the caller's stream, or the legacy default stream when none is given)
+        upload_series_coefficients();
+        if ((st = upload(s, (double**)&s->vel.u, s->uh)) != MIUGKS_OK) break;
+        if ((st = upload(s, (double**)&s->vel.v, s->vh)) != MIUGKS_OK) break;
+        if ((st = upload(s, (double**)&s->vel.w, s->wh)) != MIUGKS_OK) break;
+        if ((st = upload(s, (double**)&s->vel.ua, s->uah)) != MIUGKS_OK) break;
+        if ((st = upload(s, (double**)&s->vel.vb, s->vbh)) != MIUGKS_OK) break;
+        s->vel.nu = s->nu; s->vel.nvv = s->nvv; s->vel.nv = s->nv; s->vel.umax = s->umax; s->vel.vmax = s->vmax;
+        if ((st = upload(s, &s->bc, s->bch)) != MIUGKS_OK) break;
+        s->Cwh.assign((size_t)n_bcs * s->nv, 0.0);
+        for (int b = 0; b < n_bcs; ++b) refresh_bc_tables(s, b);
+        if ((st = upload(s, &s->Cw, s->Cwh)) != MIUGKS_OK) break;
+        if ((st = upload(s, &s->Zw, wall_norms(s))) != MIUGKS_OK) break;
+        for (int l = 0; l < s->L && st == MIUGKS_OK; ++l) st = upload_level(s, s->lev[l]);
+        if (st != MIUGKS_OK) break;
+        for (int l = 0; l + 1 < s->L && st == MIUGKS_OK; ++l) {
+            HLevel& F = s->lev[l];
+            HLevel& C = s->lev[l + 1];
+            std::vector<int> idx(4 * (size_t)F.nc);
+            std::vector<double> w(4 * (size_t)F.nc);
+            for (int j = 0; j < F.ny; ++j)
+                for (int i = 0; i < F.nx; ++i) {
+                    int I = i / 2, J = j / 2, IN, JN;
+                    double ax, bx, ay, by;
+                    lin_weights(C.xc, I, F.xc[i], IN, ax, bx);
+                    lin_weights(C.yc, J, F.yc[j], JN, ay, by);
+                    size_t c = (size_t)j * F.nx + i;
+                    idx[4 * c + 0] = J * C.nx + I;   w[4 * c + 0] = ax * ay;
+                    idx[4 * c + 1] = J * C.nx + IN;  w[4 * c + 1] = bx * ay;
+                    idx[4 * c + 2] = JN * C.nx + I;  w[4 * c + 2] = ax * by;
+                    idx[4 * c + 3] = JN * C.nx + IN; w[4 * c + 3] = bx * by;
+                }
+            if ((st = upload(s, &F.pidx, idx)) != MIUGKS_OK) break;
+            st = upload(s, &F.pw, w);
+        }
+        if (st != MIUGKS_OK) break;
+        size_t nc = L0.nc, nv = s->nv;
+        if ((st = dalloc(s, &s->f, 2 * nc * nv)) != MIUGKS_OK) break;
+        if ((st = dalloc(s, &s->W, 4 * nc)) != MIUGKS_OK) break;
+        if ((st = dalloc(s, &s->q, 2 * nc)) != MIUGKS_OK) break;
+        if ((st = dalloc(s, &s->R, 4 * nc)) != MIUGKS_OK) break;
+        if ((st = dalloc(s, &s->phx, 2 * (size_t)L0.nfx * nv)) != MIUGKS_OK) break;
+        if ((st = dalloc(s, &s->phy, 2 * (size_t)L0.nfy * nv)) != MIUGKS_OK) break;
+        if ((st = dalloc(s, &s->Fx, 4 * (size_t)L0.nfx)) != MIUGKS_OK) break;
+        if ((st = dalloc(s, &s->Fy, 4 * (size_t)L0.nfy)) != MIUGKS_OK) break;
+        if ((st = dalloc(s, &s->rms_part, 64 * 4)) != MIUGKS_OK) break;
+        if ((st = dalloc(s, &s->rms_out, 8)) != MIUGKS_OK) break;
+        if ((st = dalloc(s, &s->xcorner, 2 * nv)) != MIUGKS_OK) break;
+        // smallest interior physical time step (for the numerical time step)
+        s->dtp_min = 1e300;
+        for (int i = 1; i < L0.nx; ++i) s->dtp_min = std::fmin(s->dtp_min, opts->cfl * std::fmin(L0.dx[i - 1], L0.dx[i]) / s->umax);
+        for (int j = 1; j < L0.ny; ++j) s->dtp_min = std::fmin(s->dtp_min, opts->cfl * std::fmin(L0.dy[j - 1], L0.dy[j]) / s->vmax);
+        for (auto& e : s->ev) {
+            cudaError_t ce = cudaEventCreate(&e);
+            if (ce != cudaSuccess) { st = fail(s, MIUGKS_ECUDA, "cudaEventCreate: %s", cudaGetErrorString(ce)); break; }
+        }
+        if (st != MIUGKS_OK) break;
+        cudaError_t ce = cudaStreamSynchronize(s->st);
+        if (ce != cudaSuccess) { st = fail(s, MIUGKS_ECUDA, "create: %s", cudaGetErrorString(ce)); break; }
+    } while (0);
+    if (st != MIUGKS_OK) {
+        g_create_err = s->err;   // readable through miugks_last_error(NULL)
+        miugks_destroy(s);
+        return st;
+    }
+    *out = s;
+    return MIUGKS_OK;
+}
+
+miugks_status miugks_init_fields(miugks_solver* s, const double* rho, const double* u, const double* v, const double* t)
+{
+    if (!s || !rho || !u || !v || !t) return MIUGKS_EINVAL;
+    size_t nc = s->lev[0].nc;
+    std::vector<double> prim(4 * nc);
+    for (size_t c = 0; c < nc; ++c) {
+        if (!(rho[c] > 0) || !(t[c] > 0)) return fail(s, MIUGKS_EINVAL, "initial rho and T must be positive");
+        prim[4 * c] = rho[c]; prim[4 * c + 1] = u[c]; prim[4 * c + 2] = v[c]; prim[4 * c + 3] = t[c];
+    }
+    CK(cudaMemcpyAsync(s->lev[0].Wn, prim.data(), prim.size() * sizeof(double), cudaMemcpyHostToDevice, s->st));
+    CK(launch_init_maxwell<double>(s->lev[0].dev, s->vel, s->lev[0].Wn, s->f, s->st));
+    CK(launch_moments<double>(s->lev[0].dev, s->vel, s->f, s->W, s->q, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    s->iter = 0;
+    s->initialised = true;
+    return MIUGKS_OK;
+}
+
+miugks_status miugks_init_uniform(miugks_solver* s, double rho, double u, double v, double t)
+{
+    if (!s) return MIUGKS_EINVAL;
+    size_t nc = s->lev[0].nc;
+    std::vector<double> a(nc, rho), b(nc, u), c(nc, v), d(nc, t);
+    return miugks_init_fields(s, a.data(), b.data(), c.data(), d.data());
+}
+
+miugks_status miugks_step(miugks_solver* s, int n_iter, double res_out[4])
+{
+    if (!s) return MIUGKS_EINVAL;
+    if (!s->initialised) return fail(s, MIUGKS_ESTATE, "step before init");
+    if (n_iter < 0) return fail(s, MIUGKS_EINVAL, "n_iter < 0");
+    for (int it = 0; it < n_iter; ++it) {
+        ST(one_iteration(s));
+        if (s->timing) {
+            CK(cudaEventSynchronize(s->ev[4]));
+            float a = 0, b = 0, c = 0;
+            CK(cudaEventElapsedTime(&a, s->ev[0], s->ev[1]));
+            CK(cudaEventElapsedTime(&b, s->ev[2], s->ev[3]));
+            CK(cudaEventElapsedTime(&c, s->ev[0], s->ev[4]));
+            s->t_flux += a; s->t_sweep += b; s->t_total += c;
+        }
+    }
+    if (n_iter > 0) return read_residual(s, res_out);
+    return MIUGKS_OK;
+}
+
+miugks_status miugks_run(miugks_solver* s, double tol, int max_iter, int* iters_out, double res_out[4])
+{
+    if (!s) return MIUGKS_EINVAL;
+    double res[4] = {1e300, 1e300, 1e300, 1e300};
+    int it = 0;
+    miugks_status st = MIUGKS_OK;
+    for (; it < max_iter; ++it) {
+        st = miugks_step(s, 1, res);
+        if (st != MIUGKS_OK) break;
+        if (res[0] < tol && res[1] < tol && res[2] < tol && res[3] < tol) { ++it; break; }
+    }
+    if (iters_out) *iters_out = it;
+    if (res_out) memcpy(res_out, res, sizeof res);
+    if (st != MIUGKS_OK) return st;
+    if (!(res[0] < tol && res[1] < tol && res[2] < tol && res[3] < tol))
+        return fail(s, MIUGKS_ENOTCONVERGED, "not converged after %d iterations", it);
+    return MIUGKS_OK;
+}
+
+miugks_status miugks_residual(miugks_solver* s, double res_out[4])
+{
+    if (!s) return MIUGKS_EINVAL;
+    if (!s->initialised) return fail(s, MIUGKS_ESTATE, "residual before init");
+    ST(flux_stage(s));
+    CK(launch_rms(s->R, s->W, s->lev[0].nc, s->rms_part, s->rms_out, s->st));
+    return read_residual(s, res_out);
+}
+
+int miugks_iterations(const miugks_solver* s) { return s ? s->iter : -1; }
+
+miugks_status miugks_get_macro(miugks_solver* s, double* rho, double* u, double* v, double* t, double* qx, double* qy)
+{
+    if (!s) return MIUGKS_EINVAL;
+    size_t nc = s->lev[0].nc;
+    std::vector<double> W(4 * nc), q(2 * nc);
+    CK(cudaMemcpyAsync(W.data(), s->W, W.size() * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaMemcpyAsync(q.data(), s->q, q.size() * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    for (size_t c = 0; c < nc; ++c) {
+        double r = W[4 * c], U = W[4 * c + 1] / r, V = W[4 * c + 2] / r;
+        double eint = W[4 * c + 3] - 0.5 * r * (U * U + V * V);
+        double lam = (kKint + 2) * r / (4.0 * eint);
+        if (rho) rho[c] = r;
+        if (u) u[c] = U;
+        if (v) v[c] = V;
+        if (t) t[c] = 1.0 / lam;
+        if (qx) qx[c] = q[2 * c];
+        if (qy) qy[c] = q[2 * c + 1];
+    }
+    return MIUGKS_OK;
+}
+
+miugks_status miugks_get_f(miugks_solver* s, double* f)
+{
+    if (!s || !f) return MIUGKS_EINVAL;
+    CK(cudaMemcpyAsync(f, s->f, 2 * (size_t)s->lev[0].nc * s->nv * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    return MIUGKS_OK;
+}
+
+miugks_status miugks_set_f(miugks_solver* s, const double* f)
+{
+    if (!s || !f) return MIUGKS_EINVAL;
+    CK(cudaMemcpyAsync(s->f, f, 2 * (size_t)s->lev[0].nc * s->nv * sizeof(double), cudaMemcpyHostToDevice, s->st));
+    CK(launch_moments<double>(s->lev[0].dev, s->vel, s->f, s->W, s->q, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    s->initialised = true;
+    return MIUGKS_OK;
+}
+
+miugks_status miugks_set_bc(miugks_solver* s, int bc, const miugks_bc* value)
+{
+    if (!s || !value) return MIUGKS_EINVAL;
+    if (bc < 0 || bc >= s->nbc) return fail(s, MIUGKS_EINVAL, "BC id %d out of range", bc);
+    if (value->type != s->bch[bc].type) return fail(s, MIUGKS_EINVAL, "BC type cannot change");
+    if (!(value->t > 0)) return fail(s, MIUGKS_EINVAL, "BC temperature must be positive");
+    s->bch[bc] = BcDev{value->type, value->rho, value->u, value->v, value->t};
+    refresh_bc_tables(s, bc);
+    std::vector<double> Zh = wall_norms(s);
+    CK(cudaMemcpyAsync(s->bc + bc, &s->bch[bc], sizeof(BcDev), cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemcpyAsync(s->Cw + (size_t)bc * s->nv, s->Cwh.data() + (size_t)bc * s->nv, s->nv * sizeof(double),
+                       cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemcpyAsync(s->Zw, Zh.data(), Zh.size() * sizeof(double), cudaMemcpyHostToDevice, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    return MIUGKS_OK;
+}
+
+miugks_status miugks_get_wall(miugks_solver* s, int bc, int* n_faces, double* p, double* tau, double* q)
+{
+    if (!s || !n_faces) return MIUGKS_EINVAL;
+    if (bc < 0 || bc >= s->nbc) return fail(s, MIUGKS_EINVAL, "BC id %d out of range", bc);
+    if (s->bch[bc].type != MIUGKS_BC_WALL) return fail(s, MIUGKS_EINVAL, "BC %d is not a wall", bc);
+    HLevel& L0 = s->lev[0];
+    std::vector<int> faces;
+    for (int fi = 0; fi < L0.nfx; ++fi) if (L0.fbx[fi] == bc) faces.push_back(fi);
+    for (int fi = 0; fi < L0.nfy; ++fi) if (L0.fby[fi] == bc) faces.push_back((1 << 30) | fi);
+    int cap = *n_faces, n = (int)faces.size();
+    *n_faces = n;
+    if (cap == 0) return MIUGKS_OK;
+    if (cap < n) return fail(s, MIUGKS_EINVAL, "capacity %d < %d faces", cap, n);
+    int* dfaces;
+    double* dout;
+    cudaError_t e = cudaMalloc(&dfaces, n * sizeof(int));
+    if (e != cudaSuccess) return fail(s, MIUGKS_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e));
+    e = cudaMalloc(&dout, 3 * n * sizeof(double));
+    if (e != cudaSuccess) { cudaFree(dfaces); return fail(s, MIUGKS_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e)); }
+    std::vector<double> h(3 * (size_t)n);
+    e = cudaMemcpyAsync(dfaces, faces.data(), n * sizeof(int), cudaMemcpyHostToDevice, s->st);
+    if (e == cudaSuccess) e = launch_wall_quantities<double>(L0.dev, s->vel, s->bc, s->Cw, s->f, bc, dfaces, n, dout, s->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), dout, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+    cudaFree(dfaces);
+    cudaFree(dout);
+    if (e != cudaSuccess) return fail(s, MIUGKS_ECUDA, "get_wall: %s", cudaGetErrorString(e));
+    for (int m = 0; m < n; ++m) {
+        if (p) p[m] = h[3 * m];
+        if (tau) tau[m] = h[3 * m + 1];
+        if (q) q[m] = h[3 * m + 2];
+    }
+    return MIUGKS_OK;
+}
+
+miugks_status miugks_sizes(const miugks_solver* s, int* nx, int* ny, int* nv, int* levels)
+{
+    if (!s) return MIUGKS_EINVAL;
+    if (nx) *nx = s->lev[0].nx;
+    if (ny) *ny = s->lev[0].ny;
+    if (nv) *nv = s->nv;
+    if (levels) *levels = s->L;
+    return MIUGKS_OK;
+}
+
+miugks_status miugks_set_timing(miugks_solver* s, int on)
+{
+    if (!s) return MIUGKS_EINVAL;
+    s->timing = on != 0;
+    s->t_flux = s->t_sweep = s->t_total = 0;
+    return MIUGKS_OK;
+}
+
+miugks_status miugks_kernel_times(miugks_solver* s, double* flux_ms, double* sweep_ms, double* total_ms)
+{
+    if (!s) return MIUGKS_EINVAL;
+    if (flux_ms) *flux_ms = s->timing ? s->t_flux : -1.0;
+    if (sweep_ms) *sweep_ms = s->timing ? s->t_sweep : -1.0;
+    if (total_ms) *total_ms = s->timing ? s->t_total : -1.0;
+    s->t_flux = s->t_sweep = s->t_total = 0;
+    return MIUGKS_OK;
+}
+
+// ---------------------------------------------------------------- stages
+miugks_status miugks_stage_flux(miugks_solver* s, double* R, double* phx, double* phy)
+{
+    if (!s) return MIUGKS_EINVAL;
+    if (!s->initialised) return fail(s, MIUGKS_ESTATE, "stage before init");
+    ST(flux_stage(s));
+    HLevel& L0 = s->lev[0];
+    if (R) CK(cudaMemcpyAsync(R, s->R, 4 * (size_t)L0.nc * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    if (phx) CK(cudaMemcpyAsync(phx, s->phx, 2 * (size_t)L0.nfx * s->nv * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    if (phy) CK(cudaMemcpyAsync(phy, s->phy, 2 * (size_t)L0.nfy * s->nv * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    return MIUGKS_OK;
+}
+
+namespace {
+__global__ void k_invD_from_itau(LevelDev L, VelDev Vg, const double* it, double* invD)
+{
+    int c = blockIdx.x, i = c % L.nx, j = c / L.nx;
+    for (int k = threadIdx.x; k < Vg.nv; k += blockDim.x) {
+        double g = (fabs(Vg.u[k]) * L.dy[j] + fabs(Vg.v[k]) * L.dx[i]) / (L.dx[i] * L.dy[j]);
+        invD[(size_t)c * Vg.nv + k] = 1.0 / (it[c] + g);
+    }
+}
+} // namespace
+
+miugks_status miugks_stage_sgs_micro(miugks_solver* s, int lev, const double* inv_tau, const double* r, double* x)
+{
+    ST(check_level(s, lev));
+    HLevel& Lv = s->lev[lev];
+    size_t n = 2 * (size_t)Lv.nc * s->nv;
+    CK(cudaMemcpyAsync(Lv.inv_tau, inv_tau, Lv.nc * sizeof(double), cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemcpyAsync(Lv.r, r, n * sizeof(double), cudaMemcpyHostToDevice, s->st));
+    k_invD_from_itau<<<Lv.nc, 128, 0, s->st>>>(Lv.dev, s->vel, Lv.inv_tau, Lv.invD);
+    CK(cudaGetLastError());
+    CK(launch_micro_sgs<double>(micro_args(s, lev), s->Zw, Lv.invD, Lv.r, Lv.dl, s->xcorner, s->st));
+    CK(cudaMemcpyAsync(x, Lv.dl, n * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    return MIUGKS_OK;
+}
+
+miugks_status miugks_stage_apply_micro(miugks_solver* s, int lev, const double* inv_tau, const double* x, double* y)
+{
+    ST(check_level(s, lev));
+    HLevel& Lv = s->lev[lev];
+    size_t n = 2 * (size_t)Lv.nc * s->nv;
+    CK(cudaMemcpyAsync(Lv.inv_tau, inv_tau, Lv.nc * sizeof(double), cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemcpyAsync(Lv.dl, x, n * sizeof(double), cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemsetAsync(Lv.r, 0, n * sizeof(double), s->st));
+    CK(launch_micro_renew<double>(micro_args(s, lev), s->Zw, Lv.dl, Lv.r, nullptr, 1, s->st));
+    std::vector<double> h(n);
+    CK(cudaMemcpyAsync(h.data(), Lv.r, n * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    for (size_t q = 0; q < n; ++q) y[q] = -h[q];
+    return MIUGKS_OK;
+}
+
+miugks_status miugks_stage_sgs_macro(miugks_solver* s, int lev, const double* W, const double* Wg, const double* R,
+                                     double* dW)
+{
+    ST(check_level(s, lev));
+    HLevel& Lv = s->lev[lev];
+    size_t n4 = 4 * (size_t)Lv.nc;
+    CK(cudaMemcpyAsync(Lv.Wc, W, n4 * sizeof(double), cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemcpyAsync(Lv.Wn, Wg, n4 * sizeof(double), cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemcpyAsync(Lv.R, R, n4 * sizeof(double), cudaMemcpyHostToDevice, s->st));
+    MacroArgs ma = macro_args(s, lev, 0.0);
+    CK(launch_macro_gamma(ma, Lv.Wn, Lv.gx, Lv.gy, s->st));
+    CK(launch_macro_sgs(ma, Lv.Wc, Lv.gx, Lv.gy, Lv.R, Lv.dW, nullptr, s->st));
+    CK(cudaMemcpyAsync(dW, Lv.dW, n4 * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    return MIUGKS_OK;
+}
+
+miugks_status miugks_stage_resid_macro(miugks_solver* s, int lev, const double* W, const double* Wg, double* RE)
+{
+    ST(check_level(s, lev));
+    HLevel& Lv = s->lev[lev];
+    size_t n4 = 4 * (size_t)Lv.nc;
+    CK(cudaMemcpyAsync(Lv.Wc, W, n4 * sizeof(double), cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemcpyAsync(Lv.Wn, Wg, n4 * sizeof(double), cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemsetAsync(Lv.P, 0, n4 * sizeof(double), s->st));
+    MacroArgs ma = macro_args(s, lev, 0.0);
+    CK(launch_macro_gamma(ma, Lv.Wn, Lv.gx, Lv.gy, s->st));
+    CK(launch_macro_resid(ma, Lv.Wc, Lv.gx, Lv.gy, Lv.P, Lv.R, 1, s->st));
+    CK(cudaMemcpyAsync(RE, Lv.R, n4 * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    return MIUGKS_OK;
+}
+
+static miugks_status transfer(miugks_solver* s, int lev, int m, const double* in, double* out, bool up)
+{
+    ST(check_level(s, lev));
+    if (lev + 1 >= s->L) return fail(s, MIUGKS_EINVAL, "no coarser level below %d", lev);
+    if (m < 1) return fail(s, MIUGKS_EINVAL, "m must be positive");
+    HLevel& F = s->lev[lev];
+    HLevel& C = s->lev[lev + 1];
+    size_t nin = (size_t)(up ? F.nc : C.nc) * m, nout = (size_t)(up ? C.nc : F.nc) * m;
+    double *din, *dout;
+    cudaError_t e = cudaMalloc(&din, nin * sizeof(double));
+    if (e != cudaSuccess) return fail(s, MIUGKS_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e));
+    e = cudaMalloc(&dout, nout * sizeof(double));
+    if (e != cudaSuccess) { cudaFree(din); return fail(s, MIUGKS_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e)); }
+    e = cudaMemcpyAsync(din, in, nin * sizeof(double), cudaMemcpyHostToDevice, s->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dout, 0, nout * sizeof(double), s->st);
+    if (e == cudaSuccess)
+        e = up ? launch_restrict(F.dev, C.dev, m, 1, din, dout, s->st)
+               : launch_prolong_add(F.dev, C.dev, m, 1, F.pidx, F.pw, din, dout, nullptr, s->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, nout * sizeof(double), cudaMemcpyDeviceToHost, s->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+    cudaFree(din);
+    cudaFree(dout);
+    if (e != cudaSuccess) return fail(s, MIUGKS_ECUDA, "transfer: %s", cudaGetErrorString(e));
+    return MIUGKS_OK;
+}
+
+miugks_status miugks_stage_restrict(miugks_solver* s, int lev, int m, const double* fine, double* coarse)
+{
+    return transfer(s, lev, m, fine, coarse, true);
+}
+
+miugks_status miugks_stage_prolong(miugks_solver* s, int lev, int m, const double* coarse, double* fine)
+{
+    return transfer(s, lev, m, coarse, fine, false);
+}
+
+} // extern "C"

@@ -1,0 +1,293 @@
+"""Python binding of the MIUGKS CUDA library (include/miugks.h).
+
+Argument marshalling only: every step of the method runs in the CUDA kernels
+of libmiugks.so.  PyTorch provides the device memory (through the library's
+allocator callbacks, backed by PyTorch's caching allocator) and the CUDA
+stream.  There is no CPU fallback: without the built library, or without a
+CUDA device, creating a solver raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MIUGKS_OK, MIUGKS_EINVAL, MIUGKS_ENOMEM, MIUGKS_ECUDA, MIUGKS_EDIVERGED, MIUGKS_ETIMEOUT, \
+    MIUGKS_ENOTCONVERGED, MIUGKS_ESTATE = range(8)
+WALL, SYMMETRY, FARFIELD, OUTFLOW = 0, 1, 2, 3
+
+_d, _i, _vp, _P = ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.POINTER
+
+
+class miugks_mesh(ctypes.Structure):
+    _fields_ = [("nx", _i), ("ny", _i), ("x_nodes", _vp), ("y_nodes", _vp), ("face_bc_x", _vp), ("face_bc_y", _vp)]
+
+
+class miugks_vgrid(ctypes.Structure):
+    _fields_ = [("nu", _i), ("nv", _i), ("umin", _d), ("umax", _d), ("vmin", _d), ("vmax", _d), ("rule", _i)]
+
+
+class miugks_gas(ctypes.Structure):
+    _fields_ = [("kn", _d), ("omega", _d), ("pr", _d)]
+
+
+class miugks_bc(ctypes.Structure):
+    _fields_ = [("type", _i), ("rho", _d), ("u", _d), ("v", _d), ("t", _d)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(_vp, ctypes.c_size_t, _vp)
+FREE_FN = ctypes.CFUNCTYPE(None, _vp, _vp)
+
+
+class miugks_opts(ctypes.Structure):
+    _fields_ = [("levels", _i), ("nu1", _i), ("nu2", _i), ("nu_coarse", _i), ("cfl", _d), ("dtn_growth", _d),
+                ("precision", _i), ("cuda_stream", _vp), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
+                ("alloc_ctx", _vp)]
+
+
+class MiugksError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("miugks status %d: %s" % (status, msg))
+        self.status = status
+
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def load():
+    """Load libmiugks.so (it must have been built; see __graft_entry__.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        raise ImportError("libmiugks.so is not built (%s); run __graft_entry__.build()" % _build.LIB)
+    L = ctypes.CDLL(_build.LIB)
+    vp = _vp
+    sig = {
+        "miugks_create": [_P(miugks_mesh), _P(miugks_vgrid), _P(miugks_gas), _P(miugks_bc), _i, _P(miugks_opts),
+                          _P(vp)],
+        "miugks_destroy": [vp], "miugks_last_error": [vp],
+        "miugks_init_uniform": [vp, _d, _d, _d, _d], "miugks_init_fields": [vp, vp, vp, vp, vp],
+        "miugks_step": [vp, _i, vp], "miugks_run": [vp, _d, _i, _P(_i), vp], "miugks_residual": [vp, vp],
+        "miugks_iterations": [vp], "miugks_get_macro": [vp] + [vp] * 6, "miugks_get_f": [vp, vp],
+        "miugks_set_f": [vp, vp], "miugks_get_wall": [vp, _i, _P(_i), vp, vp, vp],
+        "miugks_set_bc": [vp, _i, _P(miugks_bc)],
+        "miugks_stage_flux": [vp, vp, vp, vp], "miugks_stage_sgs_micro": [vp, _i, vp, vp, vp],
+        "miugks_stage_apply_micro": [vp, _i, vp, vp, vp], "miugks_stage_sgs_macro": [vp, _i, vp, vp, vp, vp],
+        "miugks_stage_resid_macro": [vp, _i, vp, vp, vp], "miugks_stage_restrict": [vp, _i, _i, vp, vp],
+        "miugks_stage_prolong": [vp, _i, _i, vp, vp], "miugks_sizes": [vp, _P(_i), _P(_i), _P(_i), _P(_i)],
+        "miugks_set_timing": [vp, _i], "miugks_kernel_times": [vp, _P(_d), _P(_d), _P(_d)],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = _i
+    L.miugks_destroy.restype = None
+    L.miugks_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def exported_symbols():
+    return ["miugks_create", "miugks_destroy", "miugks_last_error", "miugks_init_uniform", "miugks_init_fields",
+            "miugks_step", "miugks_run", "miugks_residual", "miugks_iterations", "miugks_get_macro",
+            "miugks_get_f", "miugks_set_f", "miugks_get_wall", "miugks_set_bc", "miugks_stage_flux",
+            "miugks_stage_sgs_micro", "miugks_stage_apply_micro", "miugks_stage_sgs_macro",
+            "miugks_stage_resid_macro", "miugks_stage_restrict", "miugks_stage_prolong", "miugks_sizes",
+            "miugks_set_timing", "miugks_kernel_times"]
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_vp)
+
+
+class _TorchAllocator:
+    """Device memory for the library from PyTorch's caching allocator."""
+
+    def __init__(self, torch, device):
+        self.torch, self.device, self.live = torch, device, {}
+        self.alloc_fn = ALLOC_FN(self._alloc)
+        self.free_fn = FREE_FN(self._free)
+
+    def _alloc(self, nbytes, ctx):
+        try:
+            t = self.torch.empty(int(nbytes), dtype=self.torch.uint8, device=self.device)
+        except Exception:
+            return None
+        p = t.data_ptr()
+        self.live[p] = t
+        return p
+
+    def _free(self, ptr, ctx):
+        self.live.pop(ptr, None)
+
+
+class Solver:
+    """One MIUGKS problem.  ``case`` is a dict as produced by
+    ``paper_1704_03151_gb300.workloads`` (mesh nodes, face BC ids, BC table,
+    velocity grid, gas, multigrid options)."""
+
+    def __init__(self, case, use_torch=True, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise MiugksError(MIUGKS_ECUDA, "no CUDA device: the MIUGKS library has no CPU path")
+        self._lib = L = load()
+        self.case = case
+        self.nx, self.ny = int(case["nx"]), int(case["ny"])
+        self.nc = self.nx * self.ny
+        self._arrays = [np.ascontiguousarray(case["x_nodes"], dtype=np.float64),
+                        np.ascontiguousarray(case["y_nodes"], dtype=np.float64),
+                        np.ascontiguousarray(case["face_bc_x"], dtype=np.int32),
+                        np.ascontiguousarray(case["face_bc_y"], dtype=np.int32)]
+        mesh = miugks_mesh(self.nx, self.ny, *[_ptr(a) for a in self._arrays])
+        vg = case["vgrid"]
+        vgrid = miugks_vgrid(vg["nu"], vg["nv"], vg["umin"], vg["umax"], vg["vmin"], vg["vmax"], vg["rule"])
+        gas = miugks_gas(case["gas"]["kn"], case["gas"]["omega"], case["gas"]["pr"])
+        bcs = (miugks_bc * len(case["bcs"]))(*[miugks_bc(b["type"], b["rho"], b["u"], b["v"], b["t"])
+                                               for b in case["bcs"]])
+        mg = case["mg"]
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self._stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        self._alloc = _TorchAllocator(torch, dev) if use_torch else None
+        opts = miugks_opts(mg["levels"], mg["nu1"], mg["nu2"], mg["nuc"], mg["cfl"], mg["dtn_growth"], 0,
+                           _vp(self._stream.cuda_stream),
+                           self._alloc.alloc_fn if self._alloc else ALLOC_FN(),
+                           self._alloc.free_fn if self._alloc else FREE_FN(), None)
+        h = _vp()
+        st = L.miugks_create(ctypes.byref(mesh), ctypes.byref(vgrid), ctypes.byref(gas), bcs, len(case["bcs"]),
+                             ctypes.byref(opts), ctypes.byref(h))
+        if st != MIUGKS_OK:
+            raise MiugksError(st, L.miugks_last_error(None).decode())
+        self.h = h
+        nx, ny, nv, lv = _i(), _i(), _i(), _i()
+        L.miugks_sizes(h, ctypes.byref(nx), ctypes.byref(ny), ctypes.byref(nv), ctypes.byref(lv))
+        self.nv, self.levels = nv.value, lv.value
+
+    def _check(self, st):
+        if st != MIUGKS_OK:
+            raise MiugksError(st, self._lib.miugks_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.miugks_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- C ABI, same names without the prefix
+    def init_uniform(self, rho, u, v, t):
+        self._check(self._lib.miugks_init_uniform(self.h, rho, u, v, t))
+
+    def init_fields(self, rho, u, v, t):
+        a = [np.ascontiguousarray(x, dtype=np.float64).ravel() for x in (rho, u, v, t)]
+        self._check(self._lib.miugks_init_fields(self.h, *[_ptr(x) for x in a]))
+
+    def step(self, n=1):
+        res = np.zeros(4)
+        self._check(self._lib.miugks_step(self.h, n, _ptr(res)))
+        return res
+
+    def run(self, tol, max_iter):
+        res = np.zeros(4)
+        it = _i()
+        st = self._lib.miugks_run(self.h, tol, max_iter, ctypes.byref(it), _ptr(res))
+        if st not in (MIUGKS_OK, MIUGKS_ENOTCONVERGED):
+            self._check(st)
+        return it.value, res, st == MIUGKS_OK
+
+    def residual(self):
+        res = np.zeros(4)
+        self._check(self._lib.miugks_residual(self.h, _ptr(res)))
+        return res
+
+    def iterations(self):
+        return self._lib.miugks_iterations(self.h)
+
+    def macro(self):
+        out = [np.zeros(self.nc) for _ in range(6)]
+        self._check(self._lib.miugks_get_macro(self.h, *[_ptr(a) for a in out]))
+        return dict(zip(("rho", "u", "v", "t", "qx", "qy"), out))
+
+    def get_f(self):
+        f = np.zeros((2, self.nc, self.nv))
+        self._check(self._lib.miugks_get_f(self.h, _ptr(f)))
+        return f
+
+    def set_f(self, f):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        self._check(self._lib.miugks_set_f(self.h, _ptr(f)))
+
+    def set_bc(self, b, type_, rho, u, v, t):
+        self._check(self._lib.miugks_set_bc(self.h, b, ctypes.byref(miugks_bc(type_, rho, u, v, t))))
+
+    def wall(self, bc):
+        n = _i(0)
+        self._check(self._lib.miugks_get_wall(self.h, bc, ctypes.byref(n), None, None, None))
+        p, tau, q = np.zeros(n.value), np.zeros(n.value), np.zeros(n.value)
+        self._check(self._lib.miugks_get_wall(self.h, bc, ctypes.byref(n), _ptr(p), _ptr(tau), _ptr(q)))
+        return p, tau, q
+
+    def set_timing(self, on):
+        self._check(self._lib.miugks_set_timing(self.h, 1 if on else 0))
+
+    def kernel_times(self):
+        a, b, c = _d(), _d(), _d()
+        self._check(self._lib.miugks_kernel_times(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return a.value, b.value, c.value
+
+    # ---- stages
+    def stage_flux(self):
+        nfx, nfy = (self.nx + 1) * self.ny, self.nx * (self.ny + 1)
+        R = np.zeros((self.nc, 4))
+        px, py = np.zeros((2, nfx, self.nv)), np.zeros((2, nfy, self.nv))
+        self._check(self._lib.miugks_stage_flux(self.h, _ptr(R), _ptr(px), _ptr(py)))
+        return R, px, py
+
+    def sgs_micro(self, lev, inv_tau, r):
+        r = np.ascontiguousarray(r, dtype=np.float64)
+        it = np.ascontiguousarray(inv_tau, dtype=np.float64)
+        x = np.zeros_like(r)
+        self._check(self._lib.miugks_stage_sgs_micro(self.h, lev, _ptr(it), _ptr(r), _ptr(x)))
+        return x
+
+    def apply_micro(self, lev, inv_tau, x):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        it = np.ascontiguousarray(inv_tau, dtype=np.float64)
+        y = np.zeros_like(x)
+        self._check(self._lib.miugks_stage_apply_micro(self.h, lev, _ptr(it), _ptr(x), _ptr(y)))
+        return y
+
+    def sgs_macro(self, lev, W, Wg, R):
+        W, Wg, R = (np.ascontiguousarray(a, dtype=np.float64) for a in (W, Wg, R))
+        dW = np.zeros_like(W)
+        self._check(self._lib.miugks_stage_sgs_macro(self.h, lev, _ptr(W), _ptr(Wg), _ptr(R), _ptr(dW)))
+        return dW
+
+    def resid_macro(self, lev, W, Wg):
+        W, Wg = (np.ascontiguousarray(a, dtype=np.float64) for a in (W, Wg))
+        RE = np.zeros_like(W)
+        self._check(self._lib.miugks_stage_resid_macro(self.h, lev, _ptr(W), _ptr(Wg), _ptr(RE)))
+        return RE
+
+    def restrict(self, lev, fine):
+        fine = np.ascontiguousarray(fine, dtype=np.float64)
+        m = fine.shape[-1]
+        coarse = np.zeros((self.nc // 4 ** (lev + 1), m))
+        self._check(self._lib.miugks_stage_restrict(self.h, lev, m, _ptr(fine), _ptr(coarse)))
+        return coarse
+
+    def prolong(self, lev, coarse):
+        coarse = np.ascontiguousarray(coarse, dtype=np.float64)
+        m = coarse.shape[-1]
+        fine = np.zeros((self.nc // 4 ** lev, m))
+        self._check(self._lib.miugks_stage_prolong(self.h, lev, m, _ptr(coarse), _ptr(fine)))
+        return fine
