@@ -153,6 +153,30 @@ miugks_status miugks_sizes(const miugks_solver *s, int *nx, int *ny, int *nv, in
 miugks_status miugks_set_timing(miugks_solver *s, int on);
 miugks_status miugks_kernel_times(miugks_solver *s, double *flux_ms, double *sweep_ms, double *total_ms);
 
+/* Residual norm of caller-owned device arrays without allocating anything.
+ * The paper has no counterpart: this serves callers that cannot allocate at
+ * the point where they need the convergence measure -- code running during a
+ * CUDA graph capture (an allocation there breaks the capture), frameworks that
+ * only hand out their own pre-sized pools, and latency-critical loops that
+ * must not enter the allocator.
+ *   R_dev:   nc x 4 residuals (device, [cell][component]);
+ *   W_dev:   nc x 4 conservative variables (device), used for a health count;
+ *   out_dev: 5 doubles (device): RMS of each component over the cells
+ *            (Eq. Residual_Def) and the number of cells with non-positive
+ *            density or internal energy (or NaN);
+ *   cuda_stream: cudaStream_t or NULL (legacy default stream).
+ * The partial sums live in a fixed scratch array inside the library (one
+ * __device__ array of 4096 rows of 5 doubles per GPU that loads it, kept until
+ * process exit): nc is limited to 1,048,576 cells, and larger nc returns
+ * MIUGKS_EINVAL.  The first call on a device resolves the scratch address with
+ * that device current; make that first call before any stream capture.  Every
+ * call overwrites the rows it reads, so nothing needs clearing, but all calls
+ * share the one array: calls whose kernels overlap on the GPU race and must be
+ * serialised by the caller.  Asynchronous on cuda_stream; the error message of
+ * a failed call is returned by miugks_last_error(NULL). */
+miugks_status miugks_residual_rms_noalloc(const double *R_dev, const double *W_dev, int nc, double *out_dev,
+                                          void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -336,6 +336,9 @@ extern "C" {
 
 static thread_local std::string g_create_err;
 
+// message for miugks_last_error(NULL) from entry points that have no solver
+extern "C" void miugks_set_thread_error(const char* msg) { g_create_err = msg; }
+
 const char* miugks_last_error(const miugks_solver* s) { return s ? s->err.c_str() : g_create_err.c_str(); }
 
 void miugks_destroy(miugks_solver* s)
