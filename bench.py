@@ -3,7 +3,9 @@
 A step is one outer iteration (Steps 1-8 of arXiv 1704.03151, Sec. 2.4) of the
 64x64-cell lid-driven cavity with 32x32 discrete velocities on [-4,4]^2,
 Kn = 1, lid speed 0.16, 3-level V-cycle (nu1 = 2, nu2 = 1, 4 coarsest
-smoothings), FP64.  value = cell-velocity updates per second
+smoothings).  The headline is the mixed form (FP32 per-velocity arithmetic,
+FP64 moments, prediction and residual); the same run also measures the FP64
+form (key "fp64").  value = cell-velocity updates per second
 (64*64*32*32 per step) with the state resident in HBM; e2e = the same through
 the C ABI with host arrays each step (initial fields in, macroscopic fields and
 residual out); time_to_residual = wall time to RMS residual 1e-6 from rest.
@@ -40,6 +42,8 @@ WORKLOAD = "cavity64x64_v32x32_kn1_lid0.16_3level_Vcycle"
 # FP64 FMA throughput of a GB300 (FMA-chain kernel, no MEASURED_PEAKS.json entry)
 FLUX_FLOPS_PER_FACE_VELOCITY = 175.0
 FP64_PEAK_TFLOPS = 1.20
+FP32_PEAK_TFLOPS = 70.0
+HBM_PEAK_GBS = 6500.0
 
 
 def case():
@@ -153,83 +157,114 @@ def run_reference(args):
     return 0
 
 
+def measure(precision, steps, warmup, world, rank, dev, with_e2e=True, with_ttr=True, clocks=True):
+    import torch
+    from paper_1704_03151_gb300 import miugks, workloads
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        s = miugks.Solver(case(), stream=stream, precision=precision)
+    s.init_uniform(1.0, 0.0, 0.0, 1.0)
+    cv = NX * NY * NVEL * NVEL
+    s.step(warmup)
+    barrier(world)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(dev) if clocks else None
+    if sampler:
+        sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    res = s.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = sampler.stop() if sampler else None
+    ms = max_over_ranks(e0.elapsed_time(e1), world)
+    # stage breakdown in a separate pass (per-stage events synchronise the host every iteration)
+    s.set_timing(True)
+    s.kernel_times()
+    nst = max(3, steps // 5)
+    s.step(nst)
+    flux_ms, sweep_ms, total_ms = s.kernel_times()
+    s.set_timing(False)
+    out = {"value": cv * steps * world / (ms * 1e-3), "ms_per_step": ms / steps, "clocks": clk,
+           "flux_ms_per_launch": flux_ms / nst / 2.0,
+           "stage_ms_per_step": {"flux": flux_ms / nst, "evolution_cs": sweep_ms / nst, "total": total_ms / nst},
+           "residual_last": [float(x) for x in res]}
+    if with_e2e:
+        c = case()
+        fields = workloads.random_fields(c, 0, amp=0.0)
+        n = max(3, steps // 5)
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(n):
+            s.init_fields(*fields)
+            s.step(1)
+            s.macro()
+        torch.cuda.synchronize()
+        sec = max_over_ranks(time.perf_counter() - t0, world)
+        out["e2e"] = {"value": cv * n * world / sec, "unit": UNIT, "h2d_bytes_per_step": 4 * NX * NY * 8,
+                      "d2h_bytes_per_step": 6 * NX * NY * 8 + 4 * 8}
+    if with_ttr and rank == 0:
+        s.init_uniform(1.0, 0.0, 0.0, 1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        iters, rr, ok = s.run(1e-6, 3000)
+        out["time_to_residual"] = {"seconds": time.perf_counter() - t0, "iterations": iters, "converged": bool(ok),
+                                   "residual": [float(x) for x in rr]}
+    s.close()
+    return out
+
+
+def flux_roofline(m, precision):
+    """Roofline of the face-flux kernel: algorithmic flops per (face, velocity)
+    in the arithmetic type against that type's measured peak, and algorithmic
+    bytes (f read once, fluxes written once) against the measured copy rate."""
+    nfx, nfy = (NX + 1) * NY, NX * (NY + 1)
+    fv = (nfx + nfy) * NVEL * NVEL / 2.0                      # (face, velocity) pairs per launch
+    t = m["flux_ms_per_launch"] * 1e-3
+    size = 4 if precision == "mixed" else 8
+    flops = FLUX_FLOPS_PER_FACE_VELOCITY * fv / t / 1e12
+    bytes_ = (2 * NX * NY * NVEL * NVEL + 2 * fv) * size / t / 1e9
+    fpeak = FP32_PEAK_TFLOPS if precision == "mixed" else FP64_PEAK_TFLOPS
+    if flops / fpeak >= bytes_ / HBM_PEAK_GBS:
+        return {"bound": "alu", "kernel": "k_face_flux", "achieved": flops, "peak": fpeak, "unit": "TFLOP/s",
+                "frac": flops / fpeak, "traffic": None,
+                "peak_source": "measured %s FMA chain on GB300 (no MEASURED_PEAKS.json)" %
+                               ("FP32" if precision == "mixed" else "FP64"),
+                "hbm_frac": bytes_ / HBM_PEAK_GBS}
+    return {"bound": "hbm", "kernel": "k_face_flux", "achieved": bytes_, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+            "frac": bytes_ / HBM_PEAK_GBS, "traffic": None,
+            "peak_source": "measured copy kernel on GB300 (no MEASURED_PEAKS.json)", "alu_frac": flops / fpeak}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttr", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     args.warmup = max(args.warmup, 3)
     import torch
     rank, world = dist_setup(args.gpus)
-    from paper_1704_03151_gb300 import build, miugks
+    from paper_1704_03151_gb300 import build
     build.build()
     dev = torch.cuda.current_device()
-    stream = torch.cuda.Stream()
-    with torch.cuda.stream(stream):
-        s = miugks.Solver(case(), stream=stream)
-    s.init_uniform(1.0, 0.0, 0.0, 1.0)
-    cv = NX * NY * NVEL * NVEL
-    launches_per_step = count_launches()
-
-    # ---- device-resident timed region
-    s.step(args.warmup)
-    s.set_timing(True)
-    s.kernel_times()
-    barrier(world)
-    torch.cuda.synchronize()
-    clocks = ClockSampler(dev)
-    clocks.start()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    res = s.step(args.steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier(world)
-    clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    flux_ms, sweep_ms, total_ms = s.kernel_times()
-    s.set_timing(False)
-    ms = max_over_ranks(ms, world)
-    value = cv * args.steps * world / (ms * 1e-3)
-
-    # ---- end to end through the C ABI with host arrays every step
-    from paper_1704_03151_gb300 import workloads
-    c = case()
-    fields = workloads.random_fields(c, 0, amp=0.0)
-    e2e_steps = max(3, args.steps // 5)
-    barrier(world)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        s.init_fields(*fields)
-        s.step(1)
-        s.macro()
-    torch.cuda.synchronize()
-    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
-    e2e_value = cv * e2e_steps * world / e2e_s
-
-    # ---- time to residual 1e-6 from rest
-    ttr = None
-    if not args.no_ttr and rank == 0:
-        s.init_uniform(1.0, 0.0, 0.0, 1.0)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        iters, rr, ok = s.run(1e-6, 3000)
-        ttr = {"seconds": time.perf_counter() - t0, "iterations": iters, "converged": bool(ok),
-               "residual": [float(x) for x in rr]}
-
+    head = measure(args.precision, args.steps, args.warmup, world, rank, dev, with_ttr=not args.no_ttr)
+    other = None
+    if not args.no_fp64 and args.precision == "mixed":
+        other = measure("fp64", max(3, args.steps // 3), args.warmup, world, rank, dev, with_e2e=False,
+                        with_ttr=not args.no_ttr, clocks=False)
     if rank != 0:
         return 0
-    nfx, nfy = (NX + 1) * NY, NX * (NY + 1)
-    flux_flops = FLUX_FLOPS_PER_FACE_VELOCITY * (nfx + nfy) * NVEL * NVEL
-    flux_launch_ms = flux_ms / args.steps / 2.0          # two launches (x and y faces) per step
-    achieved = flux_flops / 2.0 / (flux_launch_ms * 1e-3) / 1e12
+    cv = NX * NY * NVEL * NVEL
     cpu = None
     if not args.no_cpu_baseline:
         n_iter = 4
@@ -238,25 +273,27 @@ def main():
                "sample": "%d outer iterations of the same workload (%.1f s), serial C oracle on the host" %
                          (n_iter, secs)}
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32/f64" if args.precision == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, "nvel": NVEL, "levels": LEVELS, "kn": KN,
-                   "l2": "working set (f, face fluxes, level arrays, ~0.6 GB) larger than L2",
+                   "precision": args.precision,
+                   "l2": "working set (f, face fluxes, level arrays, 0.3-0.6 GB) larger than L2",
                    "parallelism": "replicas" if world > 1 else "single"},
-        "gpu_launches": launches_per_step * args.steps,
-        "clocks": clk,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * NX * NY * 8,
-                "d2h_bytes_per_step": 6 * NX * NY * 8 + 4 * 8},
-        "roofline": {"bound": "alu", "kernel": "k_face_flux (FP64 pipe)", "achieved": achieved,
-                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                     "traffic": None, "peak_source": "measured FP64 FMA chain on GB300 (no MEASURED_PEAKS.json)"},
-        "stage_ms_per_step": {"flux": flux_ms / args.steps, "evolution_cs": sweep_ms / args.steps,
-                              "total": total_ms / args.steps},
-        "residual_last": [float(x) for x in res],
-        "time_to_residual": ttr,
+        "gpu_launches": count_launches() * args.steps,
+        "clocks": head["clocks"],
+        "e2e": head["e2e"],
+        "roofline": flux_roofline(head, args.precision),
+        "stage_ms_per_step": head["stage_ms_per_step"],
+        "residual_last": head["residual_last"],
+        "time_to_residual": head.get("time_to_residual"),
         "cpu_baseline": cpu,
     }
+    if other:
+        line["fp64"] = {"value": other["value"], "ms_per_step": other["ms_per_step"],
+                        "stage_ms_per_step": other["stage_ms_per_step"],
+                        "time_to_residual": other.get("time_to_residual"),
+                        "roofline": flux_roofline(other, "fp64")}
     print(json.dumps(line))
     return 0
 

@@ -52,7 +52,12 @@ typedef enum {
 } miugks_status;
 
 typedef enum { MIUGKS_BC_WALL = 0, MIUGKS_BC_SYMMETRY = 1, MIUGKS_BC_FARFIELD = 2, MIUGKS_BC_OUTFLOW = 3 } miugks_bc_type;
-typedef enum { MIUGKS_FP64 = 0 } miugks_precision;
+/* FP64: every step in double precision.  MIXED: f, fluxes, residuals and the
+ * evolution smoother in single precision (per-velocity arithmetic), with the
+ * velocity sums Kahan-compensated and combined in double; the conservative
+ * variables, per-face scalars, moments, the FAS prediction and the macroscopic
+ * residual stay in double. */
+typedef enum { MIUGKS_FP64 = 0, MIUGKS_MIXED = 1 } miugks_precision;
 
 /* rectilinear mesh: x_nodes[nx+1], y_nodes[ny+1] increasing; face ids as above */
 typedef struct {

@@ -30,6 +30,7 @@ struct LevelDev {
     int nx, ny, nc, nfx, nfy;
     const double *xn, *yn, *xc, *yc, *dx, *dy;
     const int *fbx, *fby;        // face BC id, -1 interior
+    const double *rdx, *rdy;     // 1/dx, 1/dy
 };
 
 struct GasDev { double mu_ref, omega, pr; };
@@ -104,12 +105,48 @@ __device__ __forceinline__ void micro_slope(const double dw[4], double U, double
     a[0] = dw[0] - U * a[1] - V * a[2] - 0.5 * a[3] * c;
 }
 
+// Reciprocal by the Newton-Raphson iteration y <- y + y (1 - x y) (quadratic
+// convergence) from a single-precision seed: two steps take the 24-bit seed to
+// double precision (within 1 ulp of 1/x).  Outside the seed's exponent range
+// the IEEE division is used.
+__device__ __forceinline__ double rcp64(double x)
+{
+    double ax = fabs(x);
+    if (!(ax > 1e-30 && ax < 1e30)) return 1.0 / x;
+    double y = (double)__frcp_rn((float)x);
+    double e = fma(-x, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-x, y, 1.0);
+    return fma(y, e, y);
+}
+
 template <typename T>
 __device__ __forceinline__ T van_leer(T s1, T s2)
 {
     T p = s1 * s2;
     return p > T(0) ? T(2) * p / (s1 + s2) : T(0);
 }
+
+// ---------------------------------------------------------------------------
+// Per-thread accumulator of velocity sums: plain FP64 in the FP64 form, a
+// Kahan-compensated FP32 sum in the mixed form (its value is taken in FP64).
+template <typename T> struct Acc;
+template <> struct Acc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct Acc<float> {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float x)
+    {
+        float y = x - c;
+        float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
 
 // ---------------------------------------------------------------------------
 // deterministic block reduction of N doubles (fixed tree order); every thread

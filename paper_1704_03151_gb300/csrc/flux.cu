@@ -59,15 +59,30 @@ __device__ __forceinline__ void time_coeffs_fast(double dt, double tau, double q
     }
 }
 
-// (a . psi) g split into the reduced components: b gM + a4 hM and b hM + a4 <xi^4>/4 gM
-__device__ __forceinline__ void slope_mom(const double* a, double u, double v, double gM, double hM,
-                                          double xi4q, double& mG, double& mH)
+// van Leer limited slope 2 s1 s2 / (s1 + s2) when s1 s2 > 0, else 0
+__device__ __forceinline__ double vl_limited(double s1, double s2)
 {
-    double b = a[0] + a[1] * u + a[2] * v + 0.5 * a[3] * (u * u + v * v);
+    double p = s1 * s2;
+    return p > 0.0 ? 2.0 * p * rcp64(s1 + s2) : 0.0;
+}
+__device__ __forceinline__ float vl_limited(float s1, float s2)
+{
+    float p = s1 * s2;
+    return p > 0.0f ? 2.0f * p / (s1 + s2) : 0.0f;
+}
+
+// (a . psi) g split into the reduced components: b gM + a4 hM and b hM + a4 <xi^4>/4 gM
+template <typename F>
+__device__ __forceinline__ void slope_mom(const F* a, F u, F v, F gM, F hM, F xi4q, F& mG, F& mH)
+{
+    F b = a[0] + a[1] * u + a[2] * v + F(0.5) * a[3] * (u * u + v * v);
     mG = b * gM + a[3] * hM;
     mH = b * hM + a[3] * xi4q * gM;
 }
 
+// Per-velocity arithmetic runs in F (FP64, or FP32 in the mixed form); the
+// velocity sums are FP64 (or Kahan-compensated FP32) per thread and combined in
+// FP64; the per-face scalars (interface state, slopes, time integrals) are FP64.
 template <typename F>
 __global__ void __launch_bounds__(256) k_face_flux(FaceFluxArgs<F> A)
 {
@@ -79,11 +94,11 @@ __global__ void __launch_bounds__(256) k_face_flux(FaceFluxArgs<F> A)
     const int nx = L.nx, ny = L.ny;
     const size_t nc = L.nc, nf = axis == 0 ? L.nfx : L.nfy;
     double* red = sm;                       // 32 * 8
-    double* par = red + 256;                // face scalars
-    double* f0s = par + 64;                 // [2][nv]
-    double* sgs = f0s + 2 * nv;             // [2][nv]
-    double* Eu = sgs + 2 * nv;              // [nu]
-    double* Ev = Eu + Vg.nu;                // [nvv]
+    double* par = red + 256;                // face scalars (FP64)
+    F* f0s = reinterpret_cast<F*>(par + 64);  // [2][nv]
+    F* sgs = f0s + 2 * nv;                  // [2][nv]
+    F* Eu = sgs + 2 * nv;                   // [nu]
+    F* Ev = Eu + Vg.nu;                     // [nvv]
     const int i = axis == 0 ? fi % (nx + 1) : fi % nx;
     const int j = axis == 0 ? fi / (nx + 1) : fi / nx;
     const int bcid = (axis == 0 ? L.fbx : L.fby)[fi];
@@ -158,28 +173,29 @@ __global__ void __launch_bounds__(256) k_face_flux(FaceFluxArgs<F> A)
     const F fhL = (F)hL, fhR = (F)hR;
 
     // pass 1: reconstruction, upwinding, interface conservative variables
-    double W0[4] = {0, 0, 0, 0};
+    Acc<F> W0a[4];
     for (int k = tid; k < nv; k += bs) {
-        double un = axis == 0 ? Vg.u[k] : Vg.v[k];
+        const F un = (F)(axis == 0 ? Vg.u[k] : Vg.v[k]);
         #pragma unroll
         for (int cp = 0; cp < 2; ++cp) {
             const F* fc = cp == 0 ? fG : fH;
             F fL = fc[cL * (size_t)nv + k], fR = fc[cR * (size_t)nv + k];
             F d2 = (fR - fL) * r2;
-            F sL = cLL >= 0 ? van_leer<F>((fL - fc[cLL * (size_t)nv + k]) * r1, d2) : F(0);
-            F sR = cRR >= 0 ? van_leer<F>(d2, (fc[cRR * (size_t)nv + k] - fR) * r3) : F(0);
+            F sL = cLL >= 0 ? vl_limited((fL - fc[cLL * (size_t)nv + k]) * r1, d2) : F(0);
+            F sR = cRR >= 0 ? vl_limited(d2, (fc[cRR * (size_t)nv + k] - fR) * r3) : F(0);
             F faceL = fL + sL * fhL, faceR = fR - sR * fhR;
-            double f0, sg;
-            if (un > 0) { f0 = faceL; sg = sL; }
-            else if (un < 0) { f0 = faceR; sg = sR; }
-            else { f0 = 0.5 * ((double)faceL + (double)faceR); sg = 0.5 * ((double)sL + (double)sR); }
+            F f0, sg;
+            if (un > F(0)) { f0 = faceL; sg = sL; }
+            else if (un < F(0)) { f0 = faceR; sg = sR; }
+            else { f0 = F(0.5) * (faceL + faceR); sg = F(0.5) * (sL + sR); }
             f0s[cp * nv + k] = f0;
             sgs[cp * nv + k] = sg;
         }
-        double w = Vg.w[k], u = Vg.u[k], v = Vg.v[k], g = f0s[k];
-        W0[0] += w * g; W0[1] += w * u * g; W0[2] += w * v * g;
-        W0[3] += w * (0.5 * (u * u + v * v) * g + f0s[nv + k]);
+        const F w = (F)Vg.w[k], u = (F)Vg.u[k], v = (F)Vg.v[k], g = f0s[k];
+        W0a[0].add(w * g); W0a[1].add(w * u * g); W0a[2].add(w * v * g);
+        W0a[3].add(w * (F(0.5) * (u * u + v * v) * g + f0s[nv + k]));
     }
+    double W0[4] = {W0a[0].value(), W0a[1].value(), W0a[2].value(), W0a[3].value()};
     block_sum<4>(W0, red);
     // face scalars (one thread), broadcast through shared memory
     if (tid == 0) {
@@ -201,32 +217,37 @@ __global__ void __launch_bounds__(256) k_face_flux(FaceFluxArgs<F> A)
     }
     __syncthreads();
     const double rho0 = par[0], U0 = par[1], V0 = par[2], lam0 = par[3];
-    for (int a = tid; a < Vg.nu; a += bs) { double d = Vg.ua[a] - U0; Eu[a] = exp(-lam0 * d * d); }
-    for (int b = tid; b < Vg.nvv; b += bs) { double d = Vg.vb[b] - V0; Ev[b] = exp(-lam0 * d * d); }
+    for (int a = tid; a < Vg.nu; a += bs) { double d = Vg.ua[a] - U0; Eu[a] = (F)exp(-lam0 * d * d); }
+    for (int b = tid; b < Vg.nvv; b += bs) { double d = Vg.vb[b] - V0; Ev[b] = (F)exp(-lam0 * d * d); }
     __syncthreads();
-    const double gnorm = rho0 * lam0 / kPi, hfac = kKint / (4.0 * lam0);
-    const double xi4q = kKint * (kKint + 2.0) / (16.0 * lam0 * lam0);
-    const double* aL = par + 8;
-    const double* aR = par + 12;
+    const F gnorm = (F)(rho0 * lam0 / kPi), hfac = (F)(kKint / (4.0 * lam0));
+    const F xi4q = (F)(kKint * (kKint + 2.0) / (16.0 * lam0 * lam0));
+    const F fU0 = (F)U0, fV0 = (F)V0;
+    F aL[4], aR[4];
+    #pragma unroll
+    for (int m = 0; m < 4; ++m) { aL[m] = (F)par[8 + m]; aR[m] = (F)par[12 + m]; }
 
     // pass 2: heat flux of the interface distribution, compatibility moments for A
-    double s6[6] = {0, 0, 0, 0, 0, 0};
+    Acc<F> s6a[6];
     for (int k = tid; k < nv; k += bs) {
         int a = k / Vg.nvv, b = k - a * Vg.nvv;
-        double u = Vg.u[k], v = Vg.v[k], w = Vg.w[k];
-        double cx = u - U0, cy = v - V0, c2 = cx * cx + cy * cy;
-        double e = 0.5 * c2 * f0s[k] + f0s[nv + k];
-        s6[0] += w * cx * e;
-        s6[1] += w * cy * e;
-        double un = axis == 0 ? u : v;
-        if (un != 0.0) {
-            double gM = gnorm * Eu[a] * Ev[b], hM = gM * hfac, mG, mH;
-            slope_mom(un > 0 ? aL : aR, u, v, gM, hM, xi4q, mG, mH);
-            double wu = w * un;
-            s6[2] += wu * mG; s6[3] += wu * u * mG; s6[4] += wu * v * mG;
-            s6[5] += wu * (0.5 * (u * u + v * v) * mG + mH);
+        const F u = (F)Vg.u[k], v = (F)Vg.v[k], w = (F)Vg.w[k];
+        F cx = u - fU0, cy = v - fV0, c2 = cx * cx + cy * cy;
+        F e = F(0.5) * c2 * f0s[k] + f0s[nv + k];
+        s6a[0].add(w * cx * e);
+        s6a[1].add(w * cy * e);
+        F un = axis == 0 ? u : v;
+        if (un != F(0)) {
+            F gM = gnorm * Eu[a] * Ev[b], hM = gM * hfac, mG, mH;
+            slope_mom<F>(un > F(0) ? aL : aR, u, v, gM, hM, xi4q, mG, mH);
+            F wu = w * un;
+            s6a[2].add(wu * mG); s6a[3].add(wu * u * mG); s6a[4].add(wu * v * mG);
+            s6a[5].add(wu * (F(0.5) * (u * u + v * v) * mG + mH));
         }
     }
+    double s6[6];
+    #pragma unroll
+    for (int q = 0; q < 6; ++q) s6[q] = s6a[q].value();
     block_sum<6>(s6, red);
     if (tid == 0) {
         double dwt[4], ir = 1.0 / rho0;
@@ -236,46 +257,51 @@ __global__ void __launch_bounds__(256) k_face_flux(FaceFluxArgs<F> A)
         par[6] = s6[0]; par[7] = s6[1];
     }
     __syncthreads();
-    const double* Aslope = par + 16;
-    const double q1 = par[20], q2 = par[21], q3 = par[22], q4 = par[23], q5 = par[24];
+    F As[4];
+    #pragma unroll
+    for (int m = 0; m < 4; ++m) As[m] = (F)par[16 + m];
     const double idt = 1.0 / par[5];
-    const double shk = (1.0 - A.gas.pr) * 4.0 * lam0 * lam0 / (5.0 * rho0);
-    const double qx = par[6], qy = par[7];
+    const F q1 = (F)(par[20] * idt), q2 = (F)(par[21] * idt), q3 = (F)(par[22] * idt), q4 = (F)(par[23] * idt),
+            q5 = (F)(par[24] * idt);
+    const F shk = (F)((1.0 - A.gas.pr) * 4.0 * lam0 * lam0 / (5.0 * rho0));
+    const F qx = (F)par[6], qy = (F)par[7], flam2 = (F)(2.0 * lam0);
 
     // pass 3: time-averaged flux of every discrete velocity and its moments
-    double Fm[4] = {0, 0, 0, 0};
+    Acc<F> Fa[4];
     for (int k = tid; k < nv; k += bs) {
         int a = k / Vg.nvv, b = k - a * Vg.nvv;
-        double u = Vg.u[k], v = Vg.v[k], w = Vg.w[k];
-        double un = axis == 0 ? u : v;
-        double cx = u - U0, cy = v - V0, c2 = cx * cx + cy * cy;
-        double gM = gnorm * Eu[a] * Ev[b], hM = gM * hfac;
-        double Fq = shk * (cx * qx + cy * qy);
-        double gP = gM * (1.0 + Fq * (2.0 * lam0 * c2 - 4.0));
-        double hP = hM * (1.0 + Fq * (2.0 * lam0 * c2 - 2.0));
-        double mGa, mHa, mGA, mHA;
-        slope_mom(un > 0 ? aL : aR, u, v, gM, hM, xi4q, mGa, mHa);
-        slope_mom(Aslope, u, v, gM, hM, xi4q, mGA, mHA);
-        double pg = un * (q1 * gP + q2 * un * mGa + q3 * mGA + q4 * f0s[k] + q5 * un * sgs[k]) * idt;
-        double ph = un * (q1 * hP + q2 * un * mHa + q3 * mHA + q4 * f0s[nv + k] + q5 * un * sgs[nv + k]) * idt;
-        phG[k] = (F)pg; phH[k] = (F)ph;
-        Fm[0] += w * pg; Fm[1] += w * u * pg; Fm[2] += w * v * pg;
-        Fm[3] += w * (0.5 * (u * u + v * v) * pg + ph);
+        const F u = (F)Vg.u[k], v = (F)Vg.v[k], w = (F)Vg.w[k];
+        const F un = axis == 0 ? u : v;
+        F cx = u - fU0, cy = v - fV0, c2 = cx * cx + cy * cy;
+        F gM = gnorm * Eu[a] * Ev[b], hM = gM * hfac;
+        F Fq = shk * (cx * qx + cy * qy);
+        F gP = gM * (F(1) + Fq * (flam2 * c2 - F(4)));
+        F hP = hM * (F(1) + Fq * (flam2 * c2 - F(2)));
+        F mGa, mHa, mGA, mHA;
+        slope_mom<F>(un > F(0) ? aL : aR, u, v, gM, hM, xi4q, mGa, mHa);
+        slope_mom<F>(As, u, v, gM, hM, xi4q, mGA, mHA);
+        F pg = un * (q1 * gP + q2 * un * mGa + q3 * mGA + q4 * f0s[k] + q5 * un * sgs[k]);
+        F ph = un * (q1 * hP + q2 * un * mHa + q3 * mHA + q4 * f0s[nv + k] + q5 * un * sgs[nv + k]);
+        phG[k] = pg; phH[k] = ph;
+        Fa[0].add(w * pg); Fa[1].add(w * u * pg); Fa[2].add(w * v * pg);
+        Fa[3].add(w * (F(0.5) * (u * u + v * v) * pg + ph));
     }
+    double Fm[4] = {Fa[0].value(), Fa[1].value(), Fa[2].value(), Fa[3].value()};
     block_sum<4>(Fm, red);
     if (tid == 0)
         for (int m = 0; m < 4; ++m) A.Fm[4 * (size_t)fi + m] = Fm[m];
 }
 
+template <typename F>
 size_t face_flux_smem(const VelDev& V)
 {
-    return sizeof(double) * (256 + 64 + 4 * (size_t)V.nv + V.nu + V.nvv);
+    return sizeof(double) * (256 + 64) + sizeof(F) * (4 * (size_t)V.nv + V.nu + V.nvv);
 }
 
 template <typename F>
 cudaError_t launch_face_flux(const FaceFluxArgs<F>& a, cudaStream_t st)
 {
-    size_t smem = face_flux_smem(a.V);
+    size_t smem = face_flux_smem<F>(a.V);
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k_face_flux<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
@@ -288,6 +314,7 @@ cudaError_t launch_face_flux(const FaceFluxArgs<F>& a, cudaStream_t st)
     return cudaGetLastError();
 }
 template cudaError_t launch_face_flux<double>(const FaceFluxArgs<double>&, cudaStream_t);
+template cudaError_t launch_face_flux<float>(const FaceFluxArgs<float>&, cudaStream_t);
 
 // R_i = -(1/V_i) sum_j S_ij F_ij
 __global__ void k_cell_residual(LevelDev L, const double* __restrict__ Fx, const double* __restrict__ Fy,

@@ -26,21 +26,24 @@ struct MacroArgs {
     double dtn_inv;                        // 1/dt_n (0 when off)
 };
 // Gamma of every face from the frozen state Wg
-cudaError_t launch_macro_gamma(const MacroArgs& a, const double* Wg, double* gx, double* gy, cudaStream_t st);
+// (and the inverse diagonal of the smoother per cell)
+cudaError_t launch_macro_gamma(const MacroArgs& a, const double* Wg, double* gx, double* gy, double* idiag,
+                               cudaStream_t st);
 // mode 0: out = Rin - R_E(W)  (forcing);  mode 1: out = Rin + R_E(W)  (renewal P + R_E)
 cudaError_t launch_macro_resid(const MacroArgs& a, const double* W, const double* gx, const double* gy,
                                const double* Rin, double* out, int mode, cudaStream_t st);
-// one LU-SGS pass: dW from R at state W; then W += dW
-cudaError_t launch_macro_sgs(const MacroArgs& a, double* W, const double* gx, const double* gy,
-                             const double* R, double* dW, int* err, cudaStream_t st);
-cudaError_t launch_restrict(const LevelDev& F, const LevelDev& C, int m, int nblk, const double* fine, double* coarse,
+// one LU-SGS pass: dW from R at state W; then W += dW (T: [nc][20] scratch for fluxes and ghost terms)
+cudaError_t launch_macro_sgs(const MacroArgs& a, double* W, const double* gx, const double* gy, const double* idiag,
+                             double* T, const double* R, double* dW, cudaStream_t st);
+template <typename T>
+cudaError_t launch_restrict(const LevelDev& F, const LevelDev& C, int m, int nblk, const T* fine, T* coarse,
                             cudaStream_t st);
 // fine += prolong(coarse) (m components per cell, nblk blocks of [nc][m]); also writes the
 // prolongated values into out_pro when it is not null
 // idx4/w4: per fine cell the four coarse stencil cells and their bilinear weights
+template <typename T>
 cudaError_t launch_prolong_add(const LevelDev& F, const LevelDev& C, int m, int nblk, const int* idx4,
-                               const double* w4, const double* coarse, double* fine, double* out_pro,
-                               cudaStream_t st);
+                               const double* w4, const T* coarse, T* fine, T* out_pro, cudaStream_t st);
 cudaError_t launch_axpy(double* y, const double* x, double a, size_t n, cudaStream_t st);
 cudaError_t launch_sub(double* out, const double* a, const double* b, size_t n, cudaStream_t st);
 

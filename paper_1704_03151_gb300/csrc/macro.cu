@@ -31,6 +31,20 @@ __device__ __forceinline__ void euler_flux(const double* W, int axis, double sgn
     T[3] = (W[3] + p) * Un;
 }
 
+// Euler flux along +e_axis: (m_a, m_x U_a + p d_xa, m_y U_a + p d_ya, (E + p) U_a),
+// with p = 2 e_int / (K + 2)
+__device__ __forceinline__ void euler_axis(const double* W, int axis, double T[4])
+{
+    double ir = rcp64(W[0]);
+    double U = W[1] * ir, V = W[2] * ir;
+    double p = (2.0 / (kKint + 2)) * (W[3] - 0.5 * (W[1] * U + W[2] * V));
+    double Ua = axis == 0 ? U : V;
+    T[0] = W[1 + axis];
+    T[1] = W[1] * Ua + (axis == 0 ? p : 0.0);
+    T[2] = W[2] * Ua + (axis == 1 ? p : 0.0);
+    T[3] = (W[3] + p) * Ua;
+}
+
 // ghost state of a boundary face (Eqs. boundaryRelation, boundaryWall) and, when
 // M != null, its Jacobian dB/dW (Eq. example_results, with the wall velocity
 // in place of U_0, V_0)
@@ -122,11 +136,36 @@ __global__ void k_macro_gamma(MacroArgs a, const double* __restrict__ Wg, double
     }
 }
 
-cudaError_t launch_macro_gamma(const MacroArgs& a, const double* Wg, double* gx, double* gy, cudaStream_t st)
+// 1 / ((1/2V) sum_faces S Gamma + 1/dt_n): the inverse diagonal of the smoother
+__global__ void k_macro_idiag(MacroArgs a, const double* __restrict__ gx, const double* __restrict__ gy,
+                              double* __restrict__ idiag)
+{
+    const LevelDev& L = a.L;
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= L.nc) return;
+    int i = c % L.nx, j = c / L.nx;
+    double sx = gx[j * (L.nx + 1) + i] + gx[j * (L.nx + 1) + i + 1];
+    double sy = gy[j * L.nx + i] + gy[(j + 1) * L.nx + i];
+    double V = L.dx[i] * L.dy[j];
+    idiag[c] = 1.0 / ((L.dy[j] * sx + L.dx[i] * sy) / (2.0 * V) + a.dtn_inv);
+}
+
+cudaError_t launch_macro_gamma(const MacroArgs& a, const double* Wg, double* gx, double* gy, double* idiag,
+                               cudaStream_t st)
 {
     int n = a.L.nfx + a.L.nfy;
     k_macro_gamma<<<(n + 127) / 128, 128, 0, st>>>(a, Wg, gx, gy);
+    k_macro_idiag<<<(a.L.nc + 127) / 128, 128, 0, st>>>(a, gx, gy, idiag);
     return cudaGetLastError();
+}
+
+// Euler fluxes of every cell along +x and +y, [nc][8]
+__global__ void k_macro_prep(LevelDev L, const double* __restrict__ W, double* __restrict__ T)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= L.nc) return;
+    euler_axis(W + 4 * (size_t)c, 0, T + 8 * (size_t)c);
+    euler_axis(W + 4 * (size_t)c, 1, T + 8 * (size_t)c + 4);
 }
 
 // face f of cell (i, j): 0 west, 1 east, 2 south, 3 north
@@ -196,84 +235,159 @@ cudaError_t launch_macro_resid(const MacroArgs& a, const double* W, const double
     return cudaGetLastError();
 }
 
-// one cell of the LU-SGS pass (pass 0 forward with west/south, pass 1 backward with east/north)
-__device__ void macro_sgs_cell(const MacroArgs& a, const double* W, const double* gx, const double* gy,
-                               const double* R, double* dW, int i, int j, int pass)
+// LU-SGS pass of Eq. macroFinalDefect, one lane per (cell, component).
+//
+// On GB300 an FP64 warp instruction occupies its SM sub-partition for 64 cycles
+// however many lanes are active, so the sweep minimises FP64 instructions per
+// lane rather than lanes: each lane updates one component of one cell of the
+// current diagonal (about eight FP64 instructions), and the four lanes of a
+// cell then evaluate the Euler fluxes of the new state W + dW along x and y,
+// which the cell's successors on the next diagonal need.  Boundary ghosts
+// enter only the backward sweep (they use dW_i of the forward sweep), so their
+// contribution is computed for all boundary cells in parallel between the two
+// half sweeps.  Arrays: T0 = T(W) [nc][8] (from k_macro_prep), T1 = T(W + dW)
+// [nc][8], G = upper-side ghost terms [nc][4].
+
+// Euler flux component m of W along +e_axis, given 1/rho, U_a and p
+__device__ __forceinline__ double euler_comp(const double* W, int m, int axis, double Ua, double p)
+{
+    if (m == 0) return W[1 + axis];
+    if (m == 3) return (W[3] + p) * Ua;
+    double v = W[m] * Ua;
+    return (m == 1 + axis) ? v + p : v;
+}
+
+__device__ __forceinline__ void producer_fluxes(const double wp, int m, int g0, double* T1c)
+{
+    // gather the four components of W + dW of this cell (lanes g0..g0+3)
+    double Wp[4];
+    #pragma unroll
+    for (int q = 0; q < 4; ++q) Wp[q] = __shfl_sync(0xffffffffu, wp, g0 + q);
+    double ir = rcp64(Wp[0]);
+    double U = Wp[1] * ir, V = Wp[2] * ir;
+    double p = (2.0 / (kKint + 2)) * fma(-0.5, fma(Wp[2], V, Wp[1] * U), Wp[3]);
+    T1c[m] = euler_comp(Wp, m, 0, U, p);
+    T1c[4 + m] = euler_comp(Wp, m, 1, V, p);
+}
+
+// ghost term of the upper-side boundary faces of cell (i, j) for the backward sweep
+__device__ void macro_ghost_terms(const MacroArgs& a, const double* W, const double* gx, const double* gy,
+                                  const double* dW, int i, int j, double Gc[4])
 {
     const LevelDev& L = a.L;
-    int c = j * L.nx + i;
-    double V = L.dx[i] * L.dy[j];
-    double diag = 0.0;
-    #pragma unroll
-    for (int f = 0; f < 4; ++f) diag += ((f >> 1) == 0 ? L.dy[j] : L.dx[i]) * face_gamma(L, gx, gy, i, j, f);
-    diag = diag / (2.0 * V) + a.dtn_inv;
-    double acc[4] = {0, 0, 0, 0};
-    const double* Wi = W + 4 * (size_t)c;
-    for (int f = pass; f < 4; f += 2) {
-        int axis = f >> 1;
-        double sgn = pass ? 1.0 : -1.0, S = axis == 0 ? L.dy[j] : L.dx[i];
-        int bcid, nb; double dum = 0;
-        face_of(L, i, j, f, bcid, nb, dum);
-        double Wn[4], dWn[4], Wp[4], T1[4], T0[4];
-        if (bcid >= 0) {
-            double M[16];
-            macro_ghost(a.bc[bcid], axis, Wi, Wn, M);
-            for (int m = 0; m < 4; ++m) {
-                double s = 0.0;
-                if (pass == 1)
-                    for (int q = 0; q < 4; ++q) s += M[4 * m + q] * dW[4 * (size_t)c + q];
-                dWn[m] = s;
-            }
-        } else {
-            for (int m = 0; m < 4; ++m) { Wn[m] = W[4 * (size_t)nb + m]; dWn[m] = dW[4 * (size_t)nb + m]; }
+    const int c = j * L.nx + i;
+    for (int m = 0; m < 4; ++m) Gc[m] = 0.0;
+    for (int axis = 0; axis < 2; ++axis) {
+        int bcid = axis == 0 ? (i == L.nx - 1 ? L.fbx[j * (L.nx + 1) + L.nx] : -1)
+                             : (j == L.ny - 1 ? L.fby[L.ny * L.nx + i] : -1);
+        if (bcid < 0) continue;
+        double Wn[4], dWn[4], Wp[4], T1[4], T0[4], M[16];
+        macro_ghost(a.bc[bcid], axis, W + 4 * (size_t)c, Wn, M);
+        for (int m = 0; m < 4; ++m) {
+            double s2 = 0.0;
+            for (int q = 0; q < 4; ++q) s2 += M[4 * m + q] * dW[4 * (size_t)c + q];
+            dWn[m] = s2;
+            Wp[m] = Wn[m] + dWn[m];
         }
-        for (int m = 0; m < 4; ++m) Wp[m] = Wn[m] + dWn[m];
-        euler_flux(Wp, axis, sgn, T1);
-        euler_flux(Wn, axis, sgn, T0);
-        double gm = face_gamma(L, gx, gy, i, j, f);
-        for (int m = 0; m < 4; ++m) acc[m] += S * ((T1[m] - T0[m]) - gm * dWn[m]);
+        euler_axis(Wp, axis, T1);
+        euler_axis(Wn, axis, T0);
+        double S = axis == 0 ? L.dy[j] : L.dx[i];
+        double gm = axis == 0 ? gx[j * (L.nx + 1) + i + 1] : gy[(j + 1) * L.nx + i];
+        for (int m = 0; m < 4; ++m) Gc[m] += S * ((T1[m] - T0[m]) - gm * dWn[m]);
     }
-    if (pass == 0)
-        for (int m = 0; m < 4; ++m) dW[4 * (size_t)c + m] = (R[4 * (size_t)c + m] - acc[m] / (2.0 * V)) / diag;
-    else
-        for (int m = 0; m < 4; ++m) dW[4 * (size_t)c + m] = dW[4 * (size_t)c + m] - acc[m] / (2.0 * V * diag);
 }
 
 __global__ void __cluster_dims__(kMacroCluster, 1, 1) __launch_bounds__(kMacroThreads)
-k_macro_sgs(MacroArgs a, double* __restrict__ W, const double* __restrict__ gx, const double* __restrict__ gy,
-            const double* __restrict__ R, double* __restrict__ dW)
+k_macro_sgs(MacroArgs a, double* __restrict__ W, const double* __restrict__ T0, double* __restrict__ T1,
+            double* __restrict__ Gt, const double* __restrict__ gx, const double* __restrict__ gy,
+            const double* __restrict__ idiag, const double* __restrict__ R, double* __restrict__ dW)
 {
     cg::cluster_group cl = cg::this_cluster();
     const LevelDev& L = a.L;
     const int nx = L.nx, ny = L.ny, nd = nx + ny - 1;
-    const int g = cl.block_rank() * blockDim.x + threadIdx.x, G = kMacroCluster * blockDim.x;
+    const int t = cl.block_rank() * blockDim.x + threadIdx.x;
+    const int m = t & 3, g0 = threadIdx.x & 28;        // component; first lane of the cell's group
+    const int ncell_pass = kMacroCluster * blockDim.x / 4;
     for (int pass = 0; pass < 2; ++pass) {
+        if (pass == 1) {
+            // upper-side ghost terms of the last column and row, from the forward dW (one thread per cell)
+            for (int b = t; b < nx + ny - 1; b += kMacroCluster * blockDim.x) {
+                int i = b < ny ? nx - 1 : b - ny, j = b < ny ? b : ny - 1;
+                macro_ghost_terms(a, W, gx, gy, dW, i, j, Gt + 4 * (size_t)(j * nx + i));
+            }
+            cl.sync();
+        }
+        const double sgn = pass ? 1.0 : -1.0;
         for (int d0 = 0; d0 < nd; ++d0) {
             int d = pass == 0 ? d0 : nd - 1 - d0;
             int ilo = d - (ny - 1) > 0 ? d - (ny - 1) : 0, ihi = d < nx - 1 ? d : nx - 1;
-            for (int t = g; t <= ihi - ilo; t += G) {
-                int i = ilo + t;
-                macro_sgs_cell(a, W, gx, gy, R, dW, i, d - i, pass);
+            for (int base = 0; base <= ihi - ilo; base += ncell_pass) {
+                int slot = base + (t >> 2);
+                bool on = slot <= ihi - ilo;
+                int i = ilo + slot, j = d - i, c = j * nx + i;
+                double wp = 0.0;
+                if (on) {
+                    double acc = 0.0;
+                    #pragma unroll
+                    for (int axis = 0; axis < 2; ++axis) {
+                        int nb, fidx;
+                        bool interior;
+                        if (axis == 0) {
+                            fidx = j * (nx + 1) + i + pass;
+                            interior = L.fbx[fidx] < 0;
+                            nb = c + (pass ? 1 : -1);
+                        } else {
+                            fidx = (j + pass) * nx + i;
+                            interior = L.fby[fidx] < 0;
+                            nb = c + (pass ? nx : -nx);
+                        }
+                        if (!interior) continue;
+                        double gm = axis == 0 ? gx[fidx] : gy[fidx];
+                        double S = axis == 0 ? L.dy[j] : L.dx[i];
+                        double dT = T1[8 * (size_t)nb + 4 * axis + m] - T0[8 * (size_t)nb + 4 * axis + m];
+                        acc = fma(S, fma(-gm, dW[4 * (size_t)nb + m], sgn * dT), acc);
+                    }
+                    const double hv = 0.5 * L.rdx[i] * L.rdy[j], id = idiag[c];
+                    double dw;
+                    if (pass == 0) {
+                        dw = fma(-acc, hv, R[4 * (size_t)c + m]) * id;
+                    } else {
+                        if (i == nx - 1 || j == ny - 1) acc += Gt[4 * (size_t)c + m];
+                        dw = fma(-acc * hv, id, dW[4 * (size_t)c + m]);
+                    }
+                    dW[4 * (size_t)c + m] = dw;
+                    wp = W[4 * (size_t)c + m] + dw;
+                }
+                double T1c[8];
+                producer_fluxes(wp, m, g0, T1c);
+                if (on) {
+                    T1[8 * (size_t)c + m] = T1c[m];
+                    T1[8 * (size_t)c + 4 + m] = T1c[4 + m];
+                }
             }
             cl.sync();   // release/acquire at cluster scope: the diagonal is visible to the next one
         }
     }
-    for (int c = g; c < L.nc; c += G)
-        for (int m = 0; m < 4; ++m) W[4 * (size_t)c + m] += dW[4 * (size_t)c + m];
+    for (int c = t; c < 4 * L.nc; c += kMacroCluster * blockDim.x) W[c] += dW[c];
 }
 
-cudaError_t launch_macro_sgs(const MacroArgs& a, double* W, const double* gx, const double* gy, const double* R,
-                             double* dW, int* err, cudaStream_t st)
+cudaError_t launch_macro_sgs(const MacroArgs& a, double* W, const double* gx, const double* gy, const double* idiag,
+                             double* T, const double* R, double* dW, cudaStream_t st)
 {
-    (void)err;
-    k_macro_sgs<<<kMacroCluster, kMacroThreads, 0, st>>>(a, W, gx, gy, R, dW);
+    // T: [nc][8] T(W), then [nc][8] T(W + dW), then [nc][4] ghost terms
+    double* T0 = T;
+    double* T1 = T + 8 * (size_t)a.L.nc;
+    double* Gt = T + 16 * (size_t)a.L.nc;
+    k_macro_prep<<<(a.L.nc + 127) / 128, 128, 0, st>>>(a.L, W, T0);
+    k_macro_sgs<<<kMacroCluster, kMacroThreads, 0, st>>>(a, W, T0, T1, Gt, gx, gy, idiag, R, dW);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
 // volume-weighted restriction (nblk blocks of [nc][m])
-__global__ void k_restrict(LevelDev F, LevelDev C, int m, int nblk, const double* __restrict__ fine,
-                           double* __restrict__ coarse)
+template <typename T>
+__global__ void k_restrict(LevelDev F, LevelDev C, int m, int nblk, const T* __restrict__ fine,
+                           T* __restrict__ coarse)
 {
     size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     size_t per = (size_t)C.nc * m;
@@ -282,7 +396,7 @@ __global__ void k_restrict(LevelDev F, LevelDev C, int m, int nblk, const double
     size_t rem = t - blk * per;
     int cc = (int)(rem / m), q = (int)(rem - (size_t)cc * m);
     int I = cc % C.nx, J = cc / C.nx;
-    const double* fb = fine + (size_t)blk * F.nc * m;
+    const T* fb = fine + (size_t)blk * F.nc * m;
     double s = 0.0, vs = 0.0;
     #pragma unroll
     for (int b = 0; b < 2; ++b)
@@ -290,23 +404,29 @@ __global__ void k_restrict(LevelDev F, LevelDev C, int m, int nblk, const double
         for (int a2 = 0; a2 < 2; ++a2) {
             int i = 2 * I + a2, j = 2 * J + b;
             double V = F.dx[i] * F.dy[j];
-            s += fb[(size_t)(j * F.nx + i) * m + q] * V;
+            s += (double)fb[(size_t)(j * F.nx + i) * m + q] * V;
             vs += V;
         }
-    coarse[(size_t)blk * per + rem] = s / vs;
+    coarse[(size_t)blk * per + rem] = (T)(s / vs);
 }
 
-cudaError_t launch_restrict(const LevelDev& F, const LevelDev& C, int m, int nblk, const double* fine, double* coarse,
+template <typename T>
+cudaError_t launch_restrict(const LevelDev& F, const LevelDev& C, int m, int nblk, const T* fine, T* coarse,
                             cudaStream_t st)
 {
     size_t n = (size_t)C.nc * m * nblk;
-    k_restrict<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(F, C, m, nblk, fine, coarse);
+    k_restrict<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(F, C, m, nblk, fine, coarse);
     return cudaGetLastError();
 }
+template cudaError_t launch_restrict<double>(const LevelDev&, const LevelDev&, int, int, const double*, double*,
+                                             cudaStream_t);
+template cudaError_t launch_restrict<float>(const LevelDev&, const LevelDev&, int, int, const float*, float*,
+                                            cudaStream_t);
 
+template <typename T>
 __global__ void k_prolong_add(LevelDev F, LevelDev C, int m, int nblk, const int* __restrict__ idx4,
-                              const double* __restrict__ w4, const double* __restrict__ coarse,
-                              double* __restrict__ fine, double* __restrict__ out_pro)
+                              const double* __restrict__ w4, const T* __restrict__ coarse,
+                              T* __restrict__ fine, T* __restrict__ out_pro)
 {
     size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     size_t per = (size_t)F.nc * m;
@@ -314,22 +434,26 @@ __global__ void k_prolong_add(LevelDev F, LevelDev C, int m, int nblk, const int
     int blk = (int)(t / per);
     size_t rem = t - blk * per;
     int c = (int)(rem / m), q = (int)(rem - (size_t)c * m);
-    const double* cb = coarse + (size_t)blk * C.nc * m;
+    const T* cb = coarse + (size_t)blk * C.nc * m;
     double v = 0.0;
     #pragma unroll
-    for (int s = 0; s < 4; ++s) v += w4[4 * c + s] * cb[(size_t)idx4[4 * c + s] * m + q];
-    fine[t] += v;
-    if (out_pro) out_pro[t] = v;
+    for (int s = 0; s < 4; ++s) v += w4[4 * c + s] * (double)cb[(size_t)idx4[4 * c + s] * m + q];
+    fine[t] = (T)((double)fine[t] + v);
+    if (out_pro) out_pro[t] = (T)v;
 }
 
+template <typename T>
 cudaError_t launch_prolong_add(const LevelDev& F, const LevelDev& C, int m, int nblk, const int* idx4,
-                               const double* w4, const double* coarse, double* fine, double* out_pro,
-                               cudaStream_t st)
+                               const double* w4, const T* coarse, T* fine, T* out_pro, cudaStream_t st)
 {
     size_t n = (size_t)F.nc * m * nblk;
-    k_prolong_add<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(F, C, m, nblk, idx4, w4, coarse, fine, out_pro);
+    k_prolong_add<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(F, C, m, nblk, idx4, w4, coarse, fine, out_pro);
     return cudaGetLastError();
 }
+template cudaError_t launch_prolong_add<double>(const LevelDev&, const LevelDev&, int, int, const int*,
+                                                const double*, const double*, double*, double*, cudaStream_t);
+template cudaError_t launch_prolong_add<float>(const LevelDev&, const LevelDev&, int, int, const int*,
+                                               const double*, const float*, float*, float*, cudaStream_t);
 
 __global__ void k_axpy(double* __restrict__ y, const double* __restrict__ x, double a, size_t n)
 {

@@ -28,21 +28,29 @@ namespace cg = cooperative_groups;
 namespace miugks {
 
 constexpr int kChainCluster = 8;
-constexpr int kChainThreads = 256;
-constexpr int kChainKpt = 8;          // local velocities per thread in the chain kernel
+constexpr int kChainThreads = 128;    // 4 warps: one per SM sub-partition
+constexpr int kChainKptMax = 16;      // local velocities per thread in the chain kernel (at most)
 constexpr int kInteriorKc = 4;        // velocities per CTA in the interior kernel
 
-__device__ __forceinline__ double geomD(const LevelDev& L, int i, int j, double u, double v)
+// (1/V) sum over the faces with u_n > 0 of u_n S = |u|/dx + |v|/dy
+template <typename F>
+__device__ __forceinline__ F geomD(const LevelDev& L, int i, int j, F u, F v)
 {
-    return (fabs(u) * L.dy[j] + fabs(v) * L.dx[i]) / (L.dx[i] * L.dy[j]);
+    return fabs(u) * (F)L.rdx[i] + fabs(v) * (F)L.rdy[j];
 }
 
-// coefficient of a neighbour (or ghost) through the face with outward normal outsign * e_axis
-__device__ __forceinline__ double Dface(int axis, int outsign, double S, double V, double u, double v)
+// coefficient (1/V) u_n S of a neighbour (or ghost) through the face with outward normal
+// outsign * e_axis, zero unless u_n < 0; rS = S/V = 1/dx (x-faces) or 1/dy (y-faces)
+template <typename F>
+__device__ __forceinline__ F Dface(int axis, int outsign, F rS, F u, F v)
 {
-    double un = outsign * (axis == 0 ? u : v);
-    return un < 0 ? un * S / V : 0.0;
+    F un = (axis == 0 ? u : v);
+    un = outsign < 0 ? -un : un;
+    return un < F(0) ? un * rS : F(0);
 }
+
+__device__ __forceinline__ double recip(double x) { return rcp64(x); }
+__device__ __forceinline__ float recip(float x) { return 1.0f / x; }
 
 // ---------------------------------------------------------------------------
 // Steps 3-4 on the finest level
@@ -59,37 +67,36 @@ __global__ void __launch_bounds__(256) k_micro_residual(MicroArgs M, GasDev gas,
     const int c = blockIdx.x, nv = Vg.nv, nx = L.nx;
     const int i = c % nx, j = c / nx;
     const size_t nc = L.nc;
-    double* Eu = sm;
-    double* Ev = sm + Vg.nu;
+    F* Eu = reinterpret_cast<F*>(sm);
+    F* Ev = Eu + Vg.nu;
     double rho, U, V, lam;
     prim4(Wt + 4 * (size_t)c, rho, U, V, lam);
     const double itau = 1.0 / tau_of(gas, rho, lam);
-    for (int a = threadIdx.x; a < Vg.nu; a += blockDim.x) { double d = Vg.ua[a] - U; Eu[a] = exp(-lam * d * d); }
-    for (int b = threadIdx.x; b < Vg.nvv; b += blockDim.x) { double d = Vg.vb[b] - V; Ev[b] = exp(-lam * d * d); }
+    for (int a = threadIdx.x; a < Vg.nu; a += blockDim.x) { double d = Vg.ua[a] - U; Eu[a] = (F)exp(-lam * d * d); }
+    for (int b = threadIdx.x; b < Vg.nvv; b += blockDim.x) { double d = Vg.vb[b] - V; Ev[b] = (F)exp(-lam * d * d); }
     if (threadIdx.x == 0) inv_tau[c] = itau + dtn_inv;
     __syncthreads();
-    const double gnorm = rho * lam / kPi, hfac = kKint / (4.0 * lam);
-    const double shk = (1.0 - gas.pr) * 4.0 * lam * lam / (5.0 * rho);
-    const double qx = q[2 * (size_t)c], qy = q[2 * (size_t)c + 1];
-    const double Vol = L.dx[i] * L.dy[j], dxi = L.dx[i], dyj = L.dy[j];
+    const F gnorm = (F)(rho * lam / kPi), hfac = (F)(kKint / (4.0 * lam)), flam2 = (F)(2.0 * lam);
+    const F shk = (F)((1.0 - gas.pr) * 4.0 * lam * lam / (5.0 * rho));
+    const F qx = (F)q[2 * (size_t)c], qy = (F)q[2 * (size_t)c + 1], fU = (F)U, fV = (F)V;
+    const F rdxi = (F)L.rdx[i], rdyj = (F)L.rdy[j], fitau = (F)itau, fdiag = (F)(itau + dtn_inv);
     const size_t nfx = L.nfx, nfy = L.nfy;
     const size_t fW = (size_t)j * (nx + 1) + i, fE = fW + 1, fS = (size_t)j * nx + i, fN = (size_t)(j + 1) * nx + i;
     for (int k = threadIdx.x; k < nv; k += blockDim.x) {
         int a = k / Vg.nvv, b = k - a * Vg.nvv;
-        double u = Vg.u[k], v = Vg.v[k];
-        double cx = u - U, cy = v - V, c2 = cx * cx + cy * cy;
-        double gM = gnorm * Eu[a] * Ev[b], hM = gM * hfac;
-        double Fq = shk * (cx * qx + cy * qy);
-        double gt[2] = {gM * (1.0 + Fq * (2.0 * lam * c2 - 4.0)), hM * (1.0 + Fq * (2.0 * lam * c2 - 2.0))};
+        const F u = (F)Vg.u[k], v = (F)Vg.v[k];
+        F cx = u - fU, cy = v - fV, c2 = cx * cx + cy * cy;
+        F gM = gnorm * Eu[a] * Ev[b], hM = gM * hfac;
+        F Fq = shk * (cx * qx + cy * qy);
+        F gt[2] = {gM * (F(1) + Fq * (flam2 * c2 - F(4))), hM * (F(1) + Fq * (flam2 * c2 - F(2)))};
         #pragma unroll
         for (int cp = 0; cp < 2; ++cp) {
             const F* px = phx + cp * nfx * nv;
             const F* py = phy + cp * nfy * nv;
-            double div = (dyj * ((double)px[fE * nv + k] - (double)px[fW * nv + k]) +
-                          dxi * ((double)py[fN * nv + k] - (double)py[fS * nv + k])) / Vol;
-            r[(cp * nc + c) * nv + k] = (F)((gt[cp] - (double)f[(cp * nc + c) * nv + k]) * itau - div);
+            F div = (px[fE * nv + k] - px[fW * nv + k]) * rdxi + (py[fN * nv + k] - py[fS * nv + k]) * rdyj;
+            r[(cp * nc + c) * nv + k] = (gt[cp] - f[(cp * nc + c) * nv + k]) * fitau - div;
         }
-        invD[(size_t)c * nv + k] = (F)(1.0 / (itau + dtn_inv + geomD(L, i, j, u, v)));
+        invD[(size_t)c * nv + k] = recip(fdiag + geomD<F>(L, i, j, u, v));
     }
 }
 
@@ -98,7 +105,7 @@ cudaError_t launch_micro_residual(const MicroArgs& m, GasDev gas, const double* 
                                   const F* phx, const F* phy, double dtn_inv, double* inv_tau, F* invD, F* r,
                                   cudaStream_t st)
 {
-    size_t smem = sizeof(double) * (m.V.nu + m.V.nvv);
+    size_t smem = sizeof(F) * (m.V.nu + m.V.nvv);
     k_micro_residual<F><<<m.L.nc, m.V.nv >= 256 ? 256 : 128, smem, st>>>(m, gas, Wt, q, f, phx, phy, dtn_inv,
                                                                           inv_tau, invD, r);
     return cudaGetLastError();
@@ -106,6 +113,9 @@ cudaError_t launch_micro_residual(const MicroArgs& m, GasDev gas, const double* 
 template cudaError_t launch_micro_residual<double>(const MicroArgs&, GasDev, const double*, const double*,
                                                    const double*, const double*, const double*, double, double*,
                                                    double*, double*, cudaStream_t);
+template cudaError_t launch_micro_residual<float>(const MicroArgs&, GasDev, const double*, const double*,
+                                                  const float*, const float*, const float*, double, double*, float*,
+                                                  float*, cudaStream_t);
 
 template <typename F>
 __global__ void k_coarse_coeffs(MicroArgs M, GasDev gas, const double* __restrict__ Wt, double dtn_inv,
@@ -118,7 +128,7 @@ __global__ void k_coarse_coeffs(MicroArgs M, GasDev gas, const double* __restric
     double it = 1.0 / tau_of(gas, rho, lam) + dtn_inv;
     if (threadIdx.x == 0) inv_tau[c] = it;
     for (int k = threadIdx.x; k < M.V.nv; k += blockDim.x)
-        invD[(size_t)c * M.V.nv + k] = (F)(1.0 / (it + geomD(L, i, j, M.V.u[k], M.V.v[k])));
+        invD[(size_t)c * M.V.nv + k] = recip((F)it + geomD<F>(L, i, j, (F)M.V.u[k], (F)M.V.v[k]));
 }
 
 template <typename F>
@@ -130,18 +140,20 @@ cudaError_t launch_coarse_coeffs(const MicroArgs& m, GasDev gas, const double* W
 }
 template cudaError_t launch_coarse_coeffs<double>(const MicroArgs&, GasDev, const double*, double, double*, double*,
                                                   cudaStream_t);
+template cudaError_t launch_coarse_coeffs<float>(const MicroArgs&, GasDev, const double*, double, double*, float*,
+                                                 cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // boundary faces of a cell on one sweep side (0 lower = west/south, 1 upper = east/north)
-struct BFace { int bc, axis, outsign; double S; };
+struct BFace { int bc, axis, outsign; double rS; };   // rS = face area / cell volume
 
 __device__ __forceinline__ int side_faces(const LevelDev& L, int i, int j, int side, BFace* bf)
 {
     int n = 0, nx = L.nx, ny = L.ny;
-    if (side != 1 && i == 0) bf[n++] = {L.fbx[j * (nx + 1)], 0, -1, L.dy[j]};
-    if (side != 1 && j == 0) bf[n++] = {L.fby[i], 1, -1, L.dx[i]};
-    if (side != 0 && i == nx - 1) bf[n++] = {L.fbx[j * (nx + 1) + nx], 0, 1, L.dy[j]};
-    if (side != 0 && j == ny - 1) bf[n++] = {L.fby[ny * nx + i], 1, 1, L.dx[i]};
+    if (side != 1 && i == 0) bf[n++] = {L.fbx[j * (nx + 1)], 0, -1, L.rdx[i]};
+    if (side != 1 && j == 0) bf[n++] = {L.fby[i], 1, -1, L.rdy[j]};
+    if (side != 0 && i == nx - 1) bf[n++] = {L.fbx[j * (nx + 1) + nx], 0, 1, L.rdx[i]};
+    if (side != 0 && j == ny - 1) bf[n++] = {L.fby[ny * nx + i], 1, 1, L.rdy[j]};
     return n;
 }
 
@@ -161,33 +173,44 @@ __device__ __forceinline__ int chain_k(const VelDev& Vg, int rank, int m, int* m
     return a * nvv + b;
 }
 
-// cluster-wide deterministic sum of NR values: block reduce, publish in own
-// shared slot, cluster barrier, read every rank's slot in rank order.
-template <int NR>
-__device__ __forceinline__ void cluster_sum(cg::cluster_group& cl, double (&v)[NR], double* red, double* slots,
-                                            int& ev)
+// Cluster-wide deterministic sum of NR values with a fixed summation tree:
+// each warp reduces its lanes with xor shuffles, lane 0 publishes the warp's
+// partial in this CTA's shared slot, one cluster barrier, then every warp
+// loads the 32 partials of the cluster (8 CTAs x 4 warps, one per lane, read
+// through distributed shared memory) and reduces them with xor shuffles.
+// Every thread ends with the same sum.  Slots are double-buffered by event.
+template <typename T, int NR>
+__device__ __forceinline__ void cluster_sum(cg::cluster_group& cl, T (&v)[NR], T* slots, int& ev)
 {
-    block_sum<NR>(v, red);
-    double* my = slots + (ev & 1) * 8;
-    if (threadIdx.x == 0)
-        for (int q = 0; q < NR; ++q) my[q] = v[q];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    #pragma unroll
+    for (int q = 0; q < NR; ++q)
+        #pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+    T* my = slots + (ev & 1) * (4 * 4);                // [warp][q]
+    if (lane == 0)
+        #pragma unroll
+        for (int q = 0; q < NR; ++q) my[warp * 4 + q] = v[q];
     cl.sync();
-    for (int q = 0; q < NR; ++q) v[q] = 0.0;
-    for (int rk = 0; rk < kChainCluster; ++rk) {
-        const double* other = cl.map_shared_rank(my, rk);
-        for (int q = 0; q < NR; ++q) v[q] += other[q];
+    const T* src = cl.map_shared_rank(my, lane >> 2);
+    #pragma unroll
+    for (int q = 0; q < NR; ++q) {
+        T x = src[(lane & 3) * 4 + q];
+        #pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        v[q] = x;
     }
     ++ev;
 }
 
-template <typename F>
+template <typename F, int kChainKpt>
 __global__ void __cluster_dims__(kChainCluster, 1, 1) __launch_bounds__(kChainThreads)
-k_sgs_chain(MicroArgs M, const double* __restrict__ Zw, const F* __restrict__ r, F* __restrict__ x,
-            const F* __restrict__ xcorner, int pass)
+k_sgs_chain(MicroArgs M, const double* __restrict__ Zw, const F* __restrict__ invD, const F* __restrict__ r,
+            F* __restrict__ x, const F* __restrict__ xcorner, int pass)
 {
-    __shared__ double red[32 * 4];
-    __shared__ double slots[16];
-    extern __shared__ double xsm[];          // [2][nloc] current cell values of this CTA's velocities
+    __shared__ F slots[2 * 4 * 4];
+    extern __shared__ double xsm_raw[];
+    F* xsm = reinterpret_cast<F*>(xsm_raw);  // [2][nloc] current cell values of this CTA's velocities
     cg::cluster_group cl = cg::this_cluster();
     const LevelDev& L = M.L;
     const VelDev& Vg = M.V;
@@ -203,7 +226,7 @@ k_sgs_chain(MicroArgs M, const double* __restrict__ Zw, const F* __restrict__ r,
         int m = threadIdx.x + t * blockDim.x;
         kk[t] = m < nloc ? chain_k(Vg, rank, m, &mu[t], &mvv[t]) : -1;
     }
-    double xprev[kChainKpt][2];
+    F xprev[kChainKpt][2];
     const int len = line == 0 ? ny : nx;
     for (int s = 0; s < len; ++s) {
         // cell of this step
@@ -211,83 +234,95 @@ k_sgs_chain(MicroArgs M, const double* __restrict__ Zw, const F* __restrict__ r,
         if (pass == 0) { i = line == 0 ? 0 : s; j = line == 0 ? s : 0; }
         else { i = line == 0 ? nx - 1 : nx - 1 - s; j = line == 0 ? ny - 1 - s : ny - 1; }
         const int c = j * nx + i;
-        const double Vol = L.dx[i] * L.dy[j], itau = M.inv_tau[c];
+        const F itau = (F)M.inv_tau[c];
         // interior neighbour along the line (the previous cell), if any
         int nb_axis = line == 0 ? 1 : 0, nb_sign = pass == 0 ? -1 : 1;
-        double nbS = nb_axis == 0 ? L.dy[j] : L.dx[i];
+        const F nbS = (F)(nb_axis == 0 ? L.rdx[i] : L.rdy[j]);
         BFace bf[2];
         int nb = side_faces(L, i, j, pass, bf);
         int nwall = 0, nsym = 0;
+        bool has_out = false;
         for (int b = 0; b < nb; ++b) {
             int t = M.bc[bf[b].bc].type;
             nwall += t == BC_WALL;
             nsym += t == BC_SYMMETRY;
+            has_out = has_out || t == BC_OUTFLOW;
         }
-        double base[kChainKpt][2], den[kChainKpt], xc[kChainKpt][2];
+        F base[kChainKpt][2], den[kChainKpt], xc[kChainKpt][2];   // den holds 1/denominator
         #pragma unroll
         for (int t = 0; t < kChainKpt; ++t) {
             int k = kk[t];
             if (k < 0) continue;
-            double u = Vg.u[k], v = Vg.v[k];
-            double D = itau + geomD(L, i, j, u, v);
-            double Dn = s > 0 ? Dface(nb_axis, nb_sign, nbS, Vol, u, v) : 0.0;
-            den[t] = D;
-            for (int b = 0; b < nb; ++b)
-                if (M.bc[bf[b].bc].type == BC_OUTFLOW) den[t] += Dface(bf[b].axis, bf[b].outsign, bf[b].S, Vol, u, v);
+            const F u = (F)Vg.u[k], v = (F)Vg.v[k];
+            const F Dn = s > 0 ? Dface<F>(nb_axis, nb_sign, nbS, u, v) : F(0);
+            // 1/D from the precomputed table unless an outflow face adds to the diagonal
+            F D = F(0);
+            if (has_out || pass == 1) D = itau + geomD<F>(L, i, j, u, v);
+            if (has_out) {
+                F dd = D;
+                for (int b = 0; b < nb; ++b)
+                    if (M.bc[bf[b].bc].type == BC_OUTFLOW) dd += Dface<F>(bf[b].axis, bf[b].outsign, (F)bf[b].rS, u, v);
+                den[t] = recip(dd);
+            } else {
+                den[t] = invD[(size_t)c * nv + k];
+            }
             #pragma unroll
             for (int cp = 0; cp < 2; ++cp) {
-                double y = s > 0 ? Dn * xprev[t][cp] : 0.0;
+                F y = s > 0 ? Dn * xprev[t][cp] : F(0);
                 size_t id = (cp * nc + c) * nv + k;
                 // backward: the corner's forward value comes from a copy taken before the
                 // launch, because the column line overwrites the corner while the row line reads it
-                double xs = pass == 0 ? 0.0 : (s == 0 ? (double)xcorner[cp * nv + k] : (double)x[id]);
-                base[t][cp] = pass == 0 ? (double)r[id] - y : D * xs - y;
-                xc[t][cp] = base[t][cp] / den[t];
+                F xs = pass == 0 ? F(0) : (s == 0 ? xcorner[cp * nv + k] : x[id]);
+                base[t][cp] = pass == 0 ? r[id] - y : D * xs - y;
+                xc[t][cp] = base[t][cp] * den[t];
             }
         }
         if (nwall == 2 && nb == 2) {
             // two walls at a corner: 2x2 system for the two ghost densities
-            double z[2], acc[4] = {0, 0, 0, 0};
+            double z[2];
+            F acc[4] = {0, 0, 0, 0};
             for (int b = 0; b < 2; ++b) z[b] = Zw[bf[b].bc * 4 + bf[b].axis * 2 + (bf[b].outsign > 0)];
             #pragma unroll
             for (int t = 0; t < kChainKpt; ++t) {
                 int k = kk[t];
                 if (k < 0) continue;
-                double u = Vg.u[k], v = Vg.v[k], w = Vg.w[k];
+                const F u = (F)Vg.u[k], v = (F)Vg.v[k], w = (F)Vg.w[k];
                 for (int b = 0; b < 2; ++b) {
-                    double uo = bf[b].outsign * (bf[b].axis == 0 ? u : v);
-                    if (!(uo > 0)) continue;
-                    acc[b] += w * uo * base[t][0] / den[t];
+                    F uo = bf[b].axis == 0 ? u : v;
+                    uo = bf[b].outsign < 0 ? -uo : uo;
+                    if (!(uo > F(0))) continue;
+                    acc[b] += w * uo * base[t][0] * den[t];
                     int o = 1 - b;
-                    double Do = Dface(bf[o].axis, bf[o].outsign, bf[o].S, Vol, u, v);
-                    if (Do != 0.0) acc[2 + b] += w * uo * Do * M.Cw[(size_t)bf[o].bc * nv + k] / den[t];
+                    F Do = Dface<F>(bf[o].axis, bf[o].outsign, (F)bf[o].rS, u, v);
+                    if (Do != F(0)) acc[2 + b] += w * uo * Do * (F)M.Cw[(size_t)bf[o].bc * nv + k] * den[t];
                 }
             }
-            cluster_sum<4>(cl, acc, red, slots, ev);
+            cluster_sum<F, 4>(cl, acc, slots, ev);
             double cc0 = -acc[0] / z[0], cc1 = -acc[1] / z[1], mm0 = acc[2] / z[0], mm1 = acc[3] / z[1];
-            double rho[2];
-            rho[0] = (cc0 + mm0 * cc1) / (1.0 - mm0 * mm1);
-            rho[1] = cc1 + mm1 * rho[0];
+            double rho2[2];
+            rho2[0] = (cc0 + mm0 * cc1) / (1.0 - mm0 * mm1);
+            rho2[1] = cc1 + mm1 * rho2[0];
+            const F rho[2] = {(F)rho2[0], (F)rho2[1]};
             #pragma unroll
             for (int t = 0; t < kChainKpt; ++t) {
                 int k = kk[t];
                 if (k < 0) continue;
-                double u = Vg.u[k], v = Vg.v[k];
+                const F u = (F)Vg.u[k], v = (F)Vg.v[k];
                 for (int cp = 0; cp < 2; ++cp) {
-                    double a = base[t][cp];
+                    F a = base[t][cp];
                     for (int b = 0; b < 2; ++b) {
-                        double Db = Dface(bf[b].axis, bf[b].outsign, bf[b].S, Vol, u, v);
-                        double C = M.Cw[(size_t)bf[b].bc * nv + k] * (cp == 0 ? 1.0 : kKint * M.bc[bf[b].bc].t / 4.0);
-                        if (Db != 0.0) a -= Db * C * rho[b];
+                        F Db = Dface<F>(bf[b].axis, bf[b].outsign, (F)bf[b].rS, u, v);
+                        F C = (F)(M.Cw[(size_t)bf[b].bc * nv + k] * (cp == 0 ? 1.0 : kKint * M.bc[bf[b].bc].t / 4.0));
+                        if (Db != F(0)) a -= Db * C * rho[b];
                     }
-                    xc[t][cp] = a / den[t];
+                    xc[t][cp] = a * den[t];
                 }
             }
         } else if (nwall + nsym > 0) {
             // substitution rounds (exact for every other combination; one round without symmetry)
             int rounds = nsym > 0 ? 3 : 1;
             for (int rd = 0; rd < rounds; ++rd) {
-                double rho = 0.0;
+                F rho = F(0);
                 int wb = -1;
                 for (int b = 0; b < nb; ++b) if (M.bc[bf[b].bc].type == BC_WALL) wb = b;
                 if (nsym > 0) {
@@ -299,36 +334,37 @@ k_sgs_chain(MicroArgs M, const double* __restrict__ Zw, const F* __restrict__ r,
                     __syncthreads();
                 }
                 if (wb >= 0) {
-                    double acc[1] = {0.0};
+                    F acc[1] = {F(0)};
                     #pragma unroll
                     for (int t = 0; t < kChainKpt; ++t) {
                         int k = kk[t];
                         if (k < 0) continue;
-                        double uo = bf[wb].outsign * (bf[wb].axis == 0 ? Vg.u[k] : Vg.v[k]);
-                        if (uo > 0) acc[0] += Vg.w[k] * uo * xc[t][0];
+                        F uo = (F)(bf[wb].axis == 0 ? Vg.u[k] : Vg.v[k]);
+                        uo = bf[wb].outsign < 0 ? -uo : uo;
+                        if (uo > F(0)) acc[0] += (F)Vg.w[k] * uo * xc[t][0];
                     }
-                    cluster_sum<1>(cl, acc, red, slots, ev);
-                    rho = -acc[0] / Zw[bf[wb].bc * 4 + bf[wb].axis * 2 + (bf[wb].outsign > 0)];
+                    cluster_sum<F, 1>(cl, acc, slots, ev);
+                    rho = (F)(-(double)acc[0] / Zw[bf[wb].bc * 4 + bf[wb].axis * 2 + (bf[wb].outsign > 0)]);
                 }
-                double xn[kChainKpt][2];
+                F xn[kChainKpt][2];
                 #pragma unroll
                 for (int t = 0; t < kChainKpt; ++t) {
                     int k = kk[t];
                     if (k < 0) continue;
-                    double u = Vg.u[k], v = Vg.v[k];
+                    const F u = (F)Vg.u[k], v = (F)Vg.v[k];
                     for (int cp = 0; cp < 2; ++cp) {
-                        double a = base[t][cp];
+                        F a = base[t][cp];
                         for (int b = 0; b < nb; ++b) {
-                            double Db = Dface(bf[b].axis, bf[b].outsign, bf[b].S, Vol, u, v);
-                            if (Db == 0.0) continue;
+                            F Db = Dface<F>(bf[b].axis, bf[b].outsign, (F)bf[b].rS, u, v);
+                            if (Db == F(0)) continue;
                             int ty = M.bc[bf[b].bc].type;
                             if (ty == BC_WALL)
-                                a -= Db * M.Cw[(size_t)bf[b].bc * nv + k] *
-                                     (cp == 0 ? 1.0 : kKint * M.bc[bf[b].bc].t / 4.0) * rho;
+                                a -= Db * (F)(M.Cw[(size_t)bf[b].bc * nv + k] *
+                                              (cp == 0 ? 1.0 : kKint * M.bc[bf[b].bc].t / 4.0)) * rho;
                             else if (ty == BC_SYMMETRY)
                                 a -= Db * xsm[cp * nloc + (bf[b].axis == 0 ? mu[t] : mvv[t])];
                         }
-                        xn[t][cp] = a / den[t];
+                        xn[t][cp] = a * den[t];
                     }
                 }
                 if (nsym > 0) __syncthreads();
@@ -346,8 +382,8 @@ k_sgs_chain(MicroArgs M, const double* __restrict__ Zw, const F* __restrict__ r,
             xprev[t][0] = xc[t][0];
             xprev[t][1] = xc[t][1];
             if (write) {
-                x[c * (size_t)nv + k] = (F)xc[t][0];
-                x[(nc + c) * (size_t)nv + k] = (F)xc[t][1];
+                x[c * (size_t)nv + k] = xc[t][0];
+                x[(nc + c) * (size_t)nv + k] = xc[t][1];
             }
         }
     }
@@ -378,18 +414,18 @@ __global__ void __launch_bounds__(128) k_sgs_interior(MicroArgs M, const F* __re
             if (k >= nv) continue;
             int i = ilo + slot, j = d - i;
             int c = j * nx + i;
-            double u = Vg.u[k], v = Vg.v[k];
-            double idx = 1.0 / L.dx[i], idy = 1.0 / L.dy[j];
+            const F u = (F)Vg.u[k], v = (F)Vg.v[k];
+            const F idx = (F)L.rdx[i], idy = (F)L.rdy[j];
             F* xb = x + cp * nc * nv;
             size_t id = (size_t)c * nv + k;
             if (pass == 0) {
-                double dW = u > 0 ? -u * idx : 0.0, dS = v > 0 ? -v * idy : 0.0;
-                double base = (double)r[cp * nc * nv + id] - dW * (double)xb[id - nv] - dS * (double)xb[id - (size_t)nx * nv];
-                xb[id] = (F)(base * (double)invD[id]);
+                F dW = u > F(0) ? -u * idx : F(0), dS = v > F(0) ? -v * idy : F(0);
+                F base = r[cp * nc * nv + id] - dW * xb[id - nv] - dS * xb[id - (size_t)nx * nv];
+                xb[id] = base * invD[id];
             } else {
-                double dE = u < 0 ? u * idx : 0.0, dN = v < 0 ? v * idy : 0.0;
-                double y = dE * (double)xb[id + nv] + dN * (double)xb[id + (size_t)nx * nv];
-                xb[id] = (F)((double)xb[id] - y * (double)invD[id]);
+                F dE = u < F(0) ? u * idx : F(0), dN = v < F(0) ? v * idy : F(0);
+                F y = dE * xb[id + nv] + dN * xb[id + (size_t)nx * nv];
+                xb[id] = xb[id] - y * invD[id];
             }
         }
         __syncthreads();
@@ -402,13 +438,15 @@ cudaError_t launch_micro_sgs(const MicroArgs& m, const double* Zw, const F* invD
 {
     const int ngroups = (m.V.nu + 1) / 2;
     const int nloc = ((ngroups + kChainCluster - 1) / kChainCluster) * 2 * m.V.nvv;
-    if (nloc > kChainKpt * kChainThreads) return cudaErrorInvalidValue;
-    size_t smem = sizeof(double) * 2 * nloc;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_sgs_chain<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    if (nloc > kChainKptMax * kChainThreads) return cudaErrorInvalidValue;
+    size_t smem = sizeof(F) * 2 * nloc;
+    const int kpt = (nloc + kChainThreads - 1) / kChainThreads;
+    void (*chain)(MicroArgs, const double*, const F*, const F*, F*, const F*, int) =
+        kpt <= 1 ? k_sgs_chain<F, 1> : kpt <= 2 ? k_sgs_chain<F, 2> : kpt <= 4 ? k_sgs_chain<F, 4>
+                 : kpt <= 8 ? k_sgs_chain<F, 8> : k_sgs_chain<F, 16>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(chain, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     int nblk_int = (m.V.nv + kInteriorKc - 1) / kInteriorKc;
     const size_t nc = m.L.nc, nv = m.V.nv, corner = (size_t)m.L.nc - 1;
@@ -419,7 +457,7 @@ cudaError_t launch_micro_sgs(const MicroArgs& m, const double* Zw, const F* invD
                                                 cudaMemcpyDeviceToDevice, st);
                 if (e != cudaSuccess) return e;
             }
-        k_sgs_chain<F><<<2 * kChainCluster, kChainThreads, smem, st>>>(m, Zw, r, x, xcorner, pass);
+        chain<<<2 * kChainCluster, kChainThreads, smem, st>>>(m, Zw, invD, r, x, xcorner, pass);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         k_sgs_interior<F><<<nblk_int, 128, 0, st>>>(m, invD, r, x, pass);
@@ -430,6 +468,8 @@ cudaError_t launch_micro_sgs(const MicroArgs& m, const double* Zw, const F* invD
 }
 template cudaError_t launch_micro_sgs<double>(const MicroArgs&, const double*, const double*, const double*, double*,
                                               double*, cudaStream_t);
+template cudaError_t launch_micro_sgs<float>(const MicroArgs&, const double*, const float*, const float*, float*,
+                                             float*, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // r -= A x (full operator with every neighbour and ghost), acc += x
@@ -446,52 +486,55 @@ __global__ void __launch_bounds__(256) k_micro_renew(MicroArgs M, const double* 
         for (int e = threadIdx.x; e < 2 * nv; e += blockDim.x) {
             int cp = e / nv, k = e - cp * nv;
             size_t id = (cp * nc + c) * nv + k;
-            acc[id] = (F)((double)acc[id] + (double)x[id]);
+            acc[id] = acc[id] + x[id];
         }
     if (!renew) return;
     BFace bf[4];
     int nb = side_faces(L, i, j, 2, bf);
-    double rho[4] = {0, 0, 0, 0};
+    F rho[4] = {0, 0, 0, 0};
     int nwall = 0;
     for (int b = 0; b < nb; ++b) nwall += M.bc[bf[b].bc].type == BC_WALL;
     if (nwall > 0) {
-        double s[4] = {0, 0, 0, 0};
+        Acc<F> sa[4];
         for (int k = threadIdx.x; k < nv; k += blockDim.x)
             for (int b = 0; b < nb; ++b) {
                 if (M.bc[bf[b].bc].type != BC_WALL) continue;
-                double uo = bf[b].outsign * (bf[b].axis == 0 ? Vg.u[k] : Vg.v[k]);
-                if (uo > 0) s[b] += Vg.w[k] * uo * (double)x[c * (size_t)nv + k];
+                F uo = (F)(bf[b].axis == 0 ? Vg.u[k] : Vg.v[k]);
+                uo = bf[b].outsign < 0 ? -uo : uo;
+                if (uo > F(0)) sa[b].add((F)Vg.w[k] * uo * x[c * (size_t)nv + k]);
             }
-        block_sum<4>(s, red);
+        double sd[4] = {sa[0].value(), sa[1].value(), sa[2].value(), sa[3].value()};
+        block_sum<4>(sd, red);
         for (int b = 0; b < nb; ++b)
-            if (M.bc[bf[b].bc].type == BC_WALL) rho[b] = -s[b] / Zw[bf[b].bc * 4 + bf[b].axis * 2 + (bf[b].outsign > 0)];
+            if (M.bc[bf[b].bc].type == BC_WALL)
+                rho[b] = (F)(-sd[b] / Zw[bf[b].bc * 4 + bf[b].axis * 2 + (bf[b].outsign > 0)]);
     }
-    const double Vol = L.dx[i] * L.dy[j], itau = M.inv_tau[c];
+    const F itau = (F)M.inv_tau[c], rdxi = (F)L.rdx[i], rdyj = (F)L.rdy[j];
     for (int e = threadIdx.x; e < 2 * nv; e += blockDim.x) {
         int cp = e / nv, k = e - cp * nv;
-        double u = Vg.u[k], v = Vg.v[k];
+        const F u = (F)Vg.u[k], v = (F)Vg.v[k];
         const F* xb = x + cp * nc * nv;
         size_t id = (size_t)c * nv + k;
-        double a = (itau + geomD(L, i, j, u, v)) * (double)xb[id];
-        if (i > 0) a += Dface(0, -1, L.dy[j], Vol, u, v) * (double)xb[id - nv];
-        if (i < nx - 1) a += Dface(0, 1, L.dy[j], Vol, u, v) * (double)xb[id + nv];
-        if (j > 0) a += Dface(1, -1, L.dx[i], Vol, u, v) * (double)xb[id - (size_t)nx * nv];
-        if (j < ny - 1) a += Dface(1, 1, L.dx[i], Vol, u, v) * (double)xb[id + (size_t)nx * nv];
+        F a = (itau + geomD<F>(L, i, j, u, v)) * xb[id];
+        if (i > 0) a += Dface<F>(0, -1, rdxi, u, v) * xb[id - nv];
+        if (i < nx - 1) a += Dface<F>(0, 1, rdxi, u, v) * xb[id + nv];
+        if (j > 0) a += Dface<F>(1, -1, rdyj, u, v) * xb[id - (size_t)nx * nv];
+        if (j < ny - 1) a += Dface<F>(1, 1, rdyj, u, v) * xb[id + (size_t)nx * nv];
         for (int b = 0; b < nb; ++b) {
-            double Db = Dface(bf[b].axis, bf[b].outsign, bf[b].S, Vol, u, v);
-            if (Db == 0.0) continue;
+            F Db = Dface<F>(bf[b].axis, bf[b].outsign, (F)bf[b].rS, u, v);
+            if (Db == F(0)) continue;
             int ty = M.bc[bf[b].bc].type;
             if (ty == BC_WALL)
-                a += Db * M.Cw[(size_t)bf[b].bc * nv + k] * (cp == 0 ? 1.0 : kKint * M.bc[bf[b].bc].t / 4.0) * rho[b];
+                a += Db * (F)(M.Cw[(size_t)bf[b].bc * nv + k] * (cp == 0 ? 1.0 : kKint * M.bc[bf[b].bc].t / 4.0)) * rho[b];
             else if (ty == BC_SYMMETRY) {
                 int aa = k / Vg.nvv, bb = k - aa * Vg.nvv;
                 int km = bf[b].axis == 0 ? (Vg.nu - 1 - aa) * Vg.nvv + bb : aa * Vg.nvv + (Vg.nvv - 1 - bb);
-                a += Db * (double)xb[(size_t)c * nv + km];
+                a += Db * xb[(size_t)c * nv + km];
             } else if (ty == BC_OUTFLOW) {
-                a += Db * (double)xb[id];
+                a += Db * xb[id];
             }
         }
-        r[cp * nc * nv + id] = (F)((double)r[cp * nc * nv + id] - a);
+        r[cp * nc * nv + id] = r[cp * nc * nv + id] - a;
     }
 }
 
@@ -504,6 +547,8 @@ cudaError_t launch_micro_renew(const MicroArgs& m, const double* Zw, const F* x,
 }
 template cudaError_t launch_micro_renew<double>(const MicroArgs&, const double*, const double*, double*, double*,
                                                 int, cudaStream_t);
+template cudaError_t launch_micro_renew<float>(const MicroArgs&, const double*, const float*, float*, float*, int,
+                                               cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // Steps 6-7: f += df (when df != null), then W = sum w psi f and q = sum w c (c^2 G/2 + H)
@@ -516,27 +561,31 @@ __global__ void __launch_bounds__(256) k_update_moments(LevelDev L, VelDev Vg, F
     const size_t nc = L.nc;
     F* fG = f + (size_t)c * nv;
     F* fH = f + (nc + c) * (size_t)nv;
-    double s[4] = {0, 0, 0, 0};
+    Acc<F> sa[4];
     for (int k = threadIdx.x; k < nv; k += blockDim.x) {
-        double g = fG[k], h = fH[k];
+        F g = fG[k], h = fH[k];
         if (df) {
-            g = (double)(F)(g + (double)df[(size_t)c * nv + k]);
-            h = (double)(F)(h + (double)df[(nc + c) * (size_t)nv + k]);
-            fG[k] = (F)g; fH[k] = (F)h;
+            g = g + df[(size_t)c * nv + k];
+            h = h + df[(nc + c) * (size_t)nv + k];
+            fG[k] = g; fH[k] = h;
         }
-        double u = Vg.u[k], v = Vg.v[k], w = Vg.w[k];
-        s[0] += w * g; s[1] += w * u * g; s[2] += w * v * g; s[3] += w * (0.5 * (u * u + v * v) * g + h);
+        const F u = (F)Vg.u[k], v = (F)Vg.v[k], w = (F)Vg.w[k];
+        sa[0].add(w * g); sa[1].add(w * u * g); sa[2].add(w * v * g);
+        sa[3].add(w * (F(0.5) * (u * u + v * v) * g + h));
     }
+    double s[4] = {sa[0].value(), sa[1].value(), sa[2].value(), sa[3].value()};
     block_sum<4>(s, red);
     double rho, U, V, lam;
     prim4(s, rho, U, V, lam);
-    double t[2] = {0, 0};
+    Acc<F> ta[2];
+    const F fU = (F)U, fV = (F)V;
     for (int k = threadIdx.x; k < nv; k += blockDim.x) {
-        double cx = Vg.u[k] - U, cy = Vg.v[k] - V;
-        double e = 0.5 * (cx * cx + cy * cy) * (double)fG[k] + (double)fH[k];
-        t[0] += Vg.w[k] * cx * e;
-        t[1] += Vg.w[k] * cy * e;
+        F cx = (F)Vg.u[k] - fU, cy = (F)Vg.v[k] - fV;
+        F e = F(0.5) * (cx * cx + cy * cy) * fG[k] + fH[k];
+        ta[0].add((F)Vg.w[k] * cx * e);
+        ta[1].add((F)Vg.w[k] * cy * e);
     }
+    double t[2] = {ta[0].value(), ta[1].value()};
     block_sum<2>(t, red);
     if (threadIdx.x == 0) {
         for (int m = 0; m < 4; ++m) W[4 * (size_t)c + m] = s[m];
@@ -561,6 +610,10 @@ template cudaError_t launch_update_moments<double>(const LevelDev&, const VelDev
                                                    double*, cudaStream_t);
 template cudaError_t launch_moments<double>(const LevelDev&, const VelDev&, const double*, double*, double*,
                                             cudaStream_t);
+template cudaError_t launch_update_moments<float>(const LevelDev&, const VelDev&, float*, const float*, double*,
+                                                  double*, cudaStream_t);
+template cudaError_t launch_moments<float>(const LevelDev&, const VelDev&, const float*, double*, double*,
+                                           cudaStream_t);
 
 // discrete Maxwellian of (rho, U, V, T) per cell
 template <typename F>
@@ -583,6 +636,7 @@ cudaError_t launch_init_maxwell(const LevelDev& L, const VelDev& V, const double
     return cudaGetLastError();
 }
 template cudaError_t launch_init_maxwell<double>(const LevelDev&, const VelDev&, const double*, double*, cudaStream_t);
+template cudaError_t launch_init_maxwell<float>(const LevelDev&, const VelDev&, const double*, float*, cudaStream_t);
 
 // wall pressure, shear and heat flux of the faces in `faces` (axis * 2^30 + face index)
 template <typename F>
@@ -635,5 +689,7 @@ cudaError_t launch_wall_quantities(const LevelDev& L, const VelDev& V, const BcD
 }
 template cudaError_t launch_wall_quantities<double>(const LevelDev&, const VelDev&, const BcDev*, const double*,
                                                     const double*, int, const int*, int, double*, cudaStream_t);
+template cudaError_t launch_wall_quantities<float>(const LevelDev&, const VelDev&, const BcDev*, const double*,
+                                                   const float*, int, const int*, int, double*, cudaStream_t);
 
 } // namespace miugks

@@ -25,9 +25,10 @@ struct HLevel {
     double* pw = nullptr;
     // prediction work, [nc][4]
     double *Wn = nullptr, *Wc = nullptr, *Rc = nullptr, *P = nullptr, *R = nullptr, *dW = nullptr, *gx = nullptr,
-           *gy = nullptr, *Wt = nullptr;
-    // evolution work, [2][nc][nv] (invD [nc][nv])
-    double *r = nullptr, *df = nullptr, *dl = nullptr, *invD = nullptr, *inv_tau = nullptr;
+           *gy = nullptr, *Wt = nullptr, *idiag = nullptr, *T = nullptr;
+    // evolution work, [2][nc][nv] (invD [nc][nv]); element type double, or float in the mixed form
+    void *r = nullptr, *df = nullptr, *dl = nullptr, *invD = nullptr;
+    double* inv_tau = nullptr;
 };
 
 } // namespace
@@ -47,10 +48,12 @@ struct miugks_solver {
     double *Cw = nullptr, *Zw = nullptr;
     std::vector<double> Cwh;
     HLevel lev[kMaxLevels];
-    // finest-level state
-    double *f = nullptr, *W = nullptr, *q = nullptr, *R = nullptr, *phx = nullptr, *phy = nullptr, *Fx = nullptr,
-           *Fy = nullptr;
-    double *rms_part = nullptr, *rms_out = nullptr, *xcorner = nullptr;
+    // finest-level state (f, face fluxes and the corner scratch in the per-velocity type)
+    bool mixed = false;
+    size_t fsz = sizeof(double);
+    void *f = nullptr, *phx = nullptr, *phy = nullptr, *xcorner = nullptr;
+    double *W = nullptr, *q = nullptr, *R = nullptr, *Fx = nullptr, *Fy = nullptr;
+    double *rms_part = nullptr, *rms_out = nullptr;
     double dtp_min = 0;
     int iter = 0;
     bool initialised = false;
@@ -99,6 +102,13 @@ miugks_status dalloc(miugks_solver* s, T** p, size_t count)
     s->allocs.push_back(ptr);
     *p = (T*)ptr;
     return MIUGKS_OK;
+}
+
+// per-velocity array of count elements of the solver's storage type
+miugks_status falloc(miugks_solver* s, void** p, size_t count)
+{
+    if (s->mixed) return dalloc(s, (float**)p, count);
+    return dalloc(s, (double**)p, count);
 }
 
 template <typename T>
@@ -182,17 +192,22 @@ void lin_weights(const std::vector<double>& Xc, int I, double x, int& N, double&
 
 miugks_status upload_level(miugks_solver* s, HLevel& Lv)
 {
-    double *xn, *yn, *xc, *yc, *dx, *dy;
+    double *xn, *yn, *xc, *yc, *dx, *dy, *rdx, *rdy;
     int *fbx, *fby;
+    std::vector<double> rdxh(Lv.nx), rdyh(Lv.ny);
+    for (int i = 0; i < Lv.nx; ++i) rdxh[i] = 1.0 / Lv.dx[i];
+    for (int j = 0; j < Lv.ny; ++j) rdyh[j] = 1.0 / Lv.dy[j];
     ST(upload(s, &xn, Lv.xn)); ST(upload(s, &yn, Lv.yn)); ST(upload(s, &xc, Lv.xc)); ST(upload(s, &yc, Lv.yc));
     ST(upload(s, &dx, Lv.dx)); ST(upload(s, &dy, Lv.dy)); ST(upload(s, &fbx, Lv.fbx)); ST(upload(s, &fby, Lv.fby));
-    Lv.dev = LevelDev{Lv.nx, Lv.ny, Lv.nc, Lv.nfx, Lv.nfy, xn, yn, xc, yc, dx, dy, fbx, fby};
+    ST(upload(s, &rdx, rdxh)); ST(upload(s, &rdy, rdyh));
+    Lv.dev = LevelDev{Lv.nx, Lv.ny, Lv.nc, Lv.nfx, Lv.nfy, xn, yn, xc, yc, dx, dy, fbx, fby, rdx, rdy};
     size_t n4 = 4 * (size_t)Lv.nc, nf = 2 * (size_t)Lv.nc * s->nv;
     ST(dalloc(s, &Lv.Wn, n4)); ST(dalloc(s, &Lv.Wc, n4)); ST(dalloc(s, &Lv.Rc, n4)); ST(dalloc(s, &Lv.P, n4));
     ST(dalloc(s, &Lv.R, n4)); ST(dalloc(s, &Lv.dW, n4)); ST(dalloc(s, &Lv.Wt, n4));
     ST(dalloc(s, &Lv.gx, (size_t)Lv.nfx)); ST(dalloc(s, &Lv.gy, (size_t)Lv.nfy));
-    ST(dalloc(s, &Lv.r, nf)); ST(dalloc(s, &Lv.df, nf)); ST(dalloc(s, &Lv.dl, nf));
-    ST(dalloc(s, &Lv.invD, (size_t)Lv.nc * s->nv)); ST(dalloc(s, &Lv.inv_tau, (size_t)Lv.nc));
+    ST(dalloc(s, &Lv.idiag, (size_t)Lv.nc)); ST(dalloc(s, &Lv.T, 20 * (size_t)Lv.nc));
+    ST(falloc(s, &Lv.r, nf)); ST(falloc(s, &Lv.df, nf)); ST(falloc(s, &Lv.dl, nf));
+    ST(falloc(s, &Lv.invD, (size_t)Lv.nc * s->nv)); ST(dalloc(s, &Lv.inv_tau, (size_t)Lv.nc));
     return MIUGKS_OK;
 }
 
@@ -218,69 +233,78 @@ miugks_status fas(miugks_solver* s, int l, double dti)
     HLevel& Lv = s->lev[l];
     MacroArgs ma = macro_args(s, l, dti);
     size_t n4 = 4 * (size_t)Lv.nc;
-    CK(launch_macro_gamma(ma, Lv.Wn, Lv.gx, Lv.gy, s->st));
+    CK(launch_macro_gamma(ma, Lv.Wn, Lv.gx, Lv.gy, Lv.idiag, s->st));
     CK(launch_macro_resid(ma, Lv.Wn, Lv.gx, Lv.gy, Lv.Rc, Lv.P, 0, s->st));     // forcing function
     CK(cudaMemcpyAsync(Lv.Wc, Lv.Wn, n4 * sizeof(double), cudaMemcpyDeviceToDevice, s->st));
     CK(cudaMemcpyAsync(Lv.R, Lv.Rc, n4 * sizeof(double), cudaMemcpyDeviceToDevice, s->st));
     const bool coarsest = l == s->L - 1;
     const int npre = coarsest ? (s->L == 1 ? 1 : s->opts.nu_coarse) : s->opts.nu1;
     for (int m = 0; m < npre; ++m) {
-        CK(launch_macro_sgs(ma, Lv.Wc, Lv.gx, Lv.gy, Lv.R, Lv.dW, nullptr, s->st));
+        CK(launch_macro_sgs(ma, Lv.Wc, Lv.gx, Lv.gy, Lv.idiag, Lv.T, Lv.R, Lv.dW, s->st));
         if (coarsest && m == npre - 1) break;
         CK(launch_macro_resid(ma, Lv.Wc, Lv.gx, Lv.gy, Lv.P, Lv.R, 1, s->st));  // renewal P + R_E(W)
     }
     if (coarsest) return MIUGKS_OK;
     HLevel& Cv = s->lev[l + 1];
-    CK(launch_restrict(Lv.dev, Cv.dev, 4, 1, Lv.Wc, Cv.Wn, s->st));
-    CK(launch_restrict(Lv.dev, Cv.dev, 4, 1, Lv.R, Cv.Rc, s->st));
+    CK(launch_restrict<double>(Lv.dev, Cv.dev, 4, 1, Lv.Wc, Cv.Wn, s->st));
+    CK(launch_restrict<double>(Lv.dev, Cv.dev, 4, 1, Lv.R, Cv.Rc, s->st));
     ST(fas(s, l + 1, dti));
     CK(launch_sub(Cv.dW, Cv.Wc, Cv.Wn, 4 * (size_t)Cv.nc, s->st));
-    CK(launch_prolong_add(Lv.dev, Cv.dev, 4, 1, Lv.pidx, Lv.pw, Cv.dW, Lv.Wc, nullptr, s->st));
+    CK(launch_prolong_add<double>(Lv.dev, Cv.dev, 4, 1, Lv.pidx, Lv.pw, Cv.dW, Lv.Wc, (double*)nullptr, s->st));
     for (int m = 0; m < s->opts.nu2; ++m) {
         CK(launch_macro_resid(ma, Lv.Wc, Lv.gx, Lv.gy, Lv.P, Lv.R, 1, s->st));
-        CK(launch_macro_sgs(ma, Lv.Wc, Lv.gx, Lv.gy, Lv.R, Lv.dW, nullptr, s->st));
+        CK(launch_macro_sgs(ma, Lv.Wc, Lv.gx, Lv.gy, Lv.idiag, Lv.T, Lv.R, Lv.dW, s->st));
     }
     return MIUGKS_OK;
 }
 
+template <typename F>
 miugks_status cs(miugks_solver* s, int l)
 {
     HLevel& Lv = s->lev[l];
     MicroArgs mi = micro_args(s, l);
     size_t n = 2 * (size_t)Lv.nc * s->nv;
-    CK(cudaMemsetAsync(Lv.df, 0, n * sizeof(double), s->st));
+    F *r = (F*)Lv.r, *df = (F*)Lv.df, *dl = (F*)Lv.dl, *invD = (F*)Lv.invD, *xc = (F*)s->xcorner;
+    CK(cudaMemsetAsync(df, 0, n * sizeof(F), s->st));
     const bool coarsest = l == s->L - 1;
     const int npre = coarsest ? (s->L == 1 ? 1 : s->opts.nu_coarse) : s->opts.nu1;
     for (int m = 0; m < npre; ++m) {
-        CK(launch_micro_sgs<double>(mi, s->Zw, Lv.invD, Lv.r, Lv.dl, s->xcorner, s->st));
+        CK(launch_micro_sgs<F>(mi, s->Zw, invD, r, dl, xc, s->st));
         bool last = coarsest && m == npre - 1;
-        CK(launch_micro_renew<double>(mi, s->Zw, Lv.dl, Lv.r, Lv.df, last ? 0 : 1, s->st));
+        CK(launch_micro_renew<F>(mi, s->Zw, dl, r, df, last ? 0 : 1, s->st));
         if (last) return MIUGKS_OK;
     }
     HLevel& Cv = s->lev[l + 1];
-    CK(launch_restrict(Lv.dev, Cv.dev, s->nv, 2, Lv.r, Cv.r, s->st));
-    ST(cs(s, l + 1));
-    CK(launch_prolong_add(Lv.dev, Cv.dev, s->nv, 2, Lv.pidx, Lv.pw, Cv.df, Lv.df, Lv.dl, s->st));
+    CK(launch_restrict<F>(Lv.dev, Cv.dev, s->nv, 2, r, (F*)Cv.r, s->st));
+    ST(cs<F>(s, l + 1));
+    CK(launch_prolong_add<F>(Lv.dev, Cv.dev, s->nv, 2, Lv.pidx, Lv.pw, (F*)Cv.df, df, dl, s->st));
     for (int m = 0; m < s->opts.nu2; ++m) {
-        CK(launch_micro_renew<double>(mi, s->Zw, Lv.dl, Lv.r, nullptr, 1, s->st));
-        CK(launch_micro_sgs<double>(mi, s->Zw, Lv.invD, Lv.r, Lv.dl, s->xcorner, s->st));
-        CK(launch_micro_renew<double>(mi, s->Zw, Lv.dl, Lv.r, Lv.df, 0, s->st));
+        CK(launch_micro_renew<F>(mi, s->Zw, dl, r, nullptr, 1, s->st));
+        CK(launch_micro_sgs<F>(mi, s->Zw, invD, r, dl, xc, s->st));
+        CK(launch_micro_renew<F>(mi, s->Zw, dl, r, df, 0, s->st));
     }
+    return MIUGKS_OK;
+}
+
+template <typename F>
+miugks_status flux_stage_t(miugks_solver* s)
+{
+    HLevel& L0 = s->lev[0];
+    FaceFluxArgs<F> fa{L0.dev, s->vel, s->gas, s->bc, s->Cw, (const F*)s->f, s->W, (F*)s->phx, s->Fx, 0, s->opts.cfl};
+    CK(launch_face_flux<F>(fa, s->st));
+    fa.axis = 1; fa.ph = (F*)s->phy; fa.Fm = s->Fy;
+    CK(launch_face_flux<F>(fa, s->st));
+    CK(launch_cell_residual(L0.dev, s->Fx, s->Fy, s->R, s->st));
     return MIUGKS_OK;
 }
 
 miugks_status flux_stage(miugks_solver* s)
 {
-    HLevel& L0 = s->lev[0];
-    FaceFluxArgs<double> fa{L0.dev, s->vel, s->gas, s->bc, s->Cw, s->f, s->W, s->phx, s->Fx, 0, s->opts.cfl};
-    CK(launch_face_flux<double>(fa, s->st));
-    fa.axis = 1; fa.ph = s->phy; fa.Fm = s->Fy;
-    CK(launch_face_flux<double>(fa, s->st));
-    CK(launch_cell_residual(L0.dev, s->Fx, s->Fy, s->R, s->st));
-    return MIUGKS_OK;
+    return s->mixed ? flux_stage_t<float>(s) : flux_stage_t<double>(s);
 }
 
-miugks_status one_iteration(miugks_solver* s)
+template <typename F>
+miugks_status one_iteration_t(miugks_solver* s)
 {
     HLevel& L0 = s->lev[0];
     const double dti = dtn_inv(s);
@@ -294,20 +318,25 @@ miugks_status one_iteration(miugks_solver* s)
     ST(fas(s, 0, dti));                                                      // Step 2
     CK(cudaMemcpyAsync(L0.Wt, L0.Wc, n4 * sizeof(double), cudaMemcpyDeviceToDevice, s->st));
     MicroArgs m0 = micro_args(s, 0);                                         // Steps 3-4
-    CK(launch_micro_residual<double>(m0, s->gas, L0.Wt, s->q, s->f, s->phx, s->phy, dti, L0.inv_tau, L0.invD,
-                                     L0.r, s->st));
+    CK(launch_micro_residual<F>(m0, s->gas, L0.Wt, s->q, (const F*)s->f, (const F*)s->phx, (const F*)s->phy, dti,
+                                L0.inv_tau, (F*)L0.invD, (F*)L0.r, s->st));
     for (int l = 1; l < s->L; ++l) {
-        CK(launch_restrict(s->lev[l - 1].dev, s->lev[l].dev, 4, 1, s->lev[l - 1].Wt, s->lev[l].Wt, s->st));
-        CK(launch_coarse_coeffs<double>(micro_args(s, l), s->gas, s->lev[l].Wt, dti, s->lev[l].inv_tau,
-                                        s->lev[l].invD, s->st));
+        CK(launch_restrict<double>(s->lev[l - 1].dev, s->lev[l].dev, 4, 1, s->lev[l - 1].Wt, s->lev[l].Wt, s->st));
+        CK(launch_coarse_coeffs<F>(micro_args(s, l), s->gas, s->lev[l].Wt, dti, s->lev[l].inv_tau,
+                                   (F*)s->lev[l].invD, s->st));
     }
     if (s->timing) CK(cudaEventRecord(s->ev[2], s->st));
-    ST(cs(s, 0));                                                            // Step 5
+    ST(cs<F>(s, 0));                                                            // Step 5
     if (s->timing) CK(cudaEventRecord(s->ev[3], s->st));
-    CK(launch_update_moments<double>(L0.dev, s->vel, s->f, L0.df, s->W, s->q, s->st));   // Steps 6-7
+    CK(launch_update_moments<F>(L0.dev, s->vel, (F*)s->f, (const F*)L0.df, s->W, s->q, s->st));   // Steps 6-7
     if (s->timing) CK(cudaEventRecord(s->ev[4], s->st));
     s->iter++;
     return MIUGKS_OK;
+}
+
+miugks_status one_iteration(miugks_solver* s)
+{
+    return s->mixed ? one_iteration_t<float>(s) : one_iteration_t<double>(s);
 }
 
 miugks_status read_residual(miugks_solver* s, double res_out[4])
@@ -322,6 +351,41 @@ miugks_status read_residual(miugks_solver* s, double res_out[4])
     return MIUGKS_OK;
 }
 
+// copy n per-velocity values between a host double array and a device array of the storage type
+miugks_status to_device(miugks_solver* s, void* dst, const double* src, size_t n)
+{
+    if (!s->mixed) {
+        CK(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyHostToDevice, s->st));
+        return cudaStreamSynchronize(s->st) == cudaSuccess ? MIUGKS_OK : fail(s, MIUGKS_ECUDA, "to_device");
+    }
+    std::vector<float> h(n);
+    for (size_t q = 0; q < n; ++q) h[q] = (float)src[q];
+    CK(cudaMemcpyAsync(dst, h.data(), n * sizeof(float), cudaMemcpyHostToDevice, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    return MIUGKS_OK;
+}
+
+miugks_status to_host(miugks_solver* s, double* dst, const void* src, size_t n)
+{
+    if (!s->mixed) {
+        CK(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+        CK(cudaStreamSynchronize(s->st));
+        return MIUGKS_OK;
+    }
+    std::vector<float> h(n);
+    CK(cudaMemcpyAsync(h.data(), src, n * sizeof(float), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    for (size_t q = 0; q < n; ++q) dst[q] = h[q];
+    return MIUGKS_OK;
+}
+
+miugks_status moments_now(miugks_solver* s)
+{
+    if (s->mixed) CK(launch_moments<float>(s->lev[0].dev, s->vel, (const float*)s->f, s->W, s->q, s->st));
+    else CK(launch_moments<double>(s->lev[0].dev, s->vel, (const double*)s->f, s->W, s->q, s->st));
+    return MIUGKS_OK;
+}
+
 miugks_status check_level(miugks_solver* s, int lev)
 {
     if (!s) return MIUGKS_EINVAL;
@@ -329,6 +393,18 @@ miugks_status check_level(miugks_solver* s, int lev)
     return MIUGKS_OK;
 }
 
+} // namespace
+
+namespace {
+template <typename F>
+__global__ void k_invD_from_itau(LevelDev L, VelDev Vg, const double* it, F* invD)
+{
+    int c = blockIdx.x, i = c % L.nx, j = c / L.nx;
+    for (int k = threadIdx.x; k < Vg.nv; k += blockDim.x) {
+        double g = fabs(Vg.u[k]) * L.rdx[i] + fabs(Vg.v[k]) * L.rdy[j];
+        invD[(size_t)c * Vg.nv + k] = (F)(1.0 / (it[c] + g));
+    }
+}
 } // namespace
 
 // =========================================================================== C ABI
@@ -370,7 +446,12 @@ miugks_status miugks_create(const miugks_mesh* mesh, const miugks_vgrid* vg, con
     };
     miugks_status st = MIUGKS_OK;
     do {
-        if (opts->precision != MIUGKS_FP64) { st = bad("unsupported precision %d", opts->precision); break; }
+        if (opts->precision != MIUGKS_FP64 && opts->precision != MIUGKS_MIXED) {
+            st = bad("unsupported precision %d", opts->precision);
+            break;
+        }
+        s->mixed = opts->precision == MIUGKS_MIXED;
+        s->fsz = s->mixed ? sizeof(float) : sizeof(double);
         if (opts->levels < 1 || opts->levels > kMaxLevels) { st = bad("levels must be 1..%d", kMaxLevels); break; }
         if (opts->nu1 < 1 || opts->nu2 < 1 || opts->nu_coarse < 1) { st = bad("smoothing counts must be >= 1"); break; }
         if (!(opts->cfl > 0.0)) { st = bad("cfl must be positive"); break; }
@@ -497,17 +578,17 @@ miugks_status miugks_create(const miugks_mesh* mesh, const miugks_vgrid* vg, con
         }
         if (st != MIUGKS_OK) break;
         size_t nc = L0.nc, nv = s->nv;
-        if ((st = dalloc(s, &s->f, 2 * nc * nv)) != MIUGKS_OK) break;
+        if ((st = falloc(s, &s->f, 2 * nc * nv)) != MIUGKS_OK) break;
         if ((st = dalloc(s, &s->W, 4 * nc)) != MIUGKS_OK) break;
         if ((st = dalloc(s, &s->q, 2 * nc)) != MIUGKS_OK) break;
         if ((st = dalloc(s, &s->R, 4 * nc)) != MIUGKS_OK) break;
-        if ((st = dalloc(s, &s->phx, 2 * (size_t)L0.nfx * nv)) != MIUGKS_OK) break;
-        if ((st = dalloc(s, &s->phy, 2 * (size_t)L0.nfy * nv)) != MIUGKS_OK) break;
+        if ((st = falloc(s, &s->phx, 2 * (size_t)L0.nfx * nv)) != MIUGKS_OK) break;
+        if ((st = falloc(s, &s->phy, 2 * (size_t)L0.nfy * nv)) != MIUGKS_OK) break;
         if ((st = dalloc(s, &s->Fx, 4 * (size_t)L0.nfx)) != MIUGKS_OK) break;
         if ((st = dalloc(s, &s->Fy, 4 * (size_t)L0.nfy)) != MIUGKS_OK) break;
         if ((st = dalloc(s, &s->rms_part, 64 * 4)) != MIUGKS_OK) break;
         if ((st = dalloc(s, &s->rms_out, 8)) != MIUGKS_OK) break;
-        if ((st = dalloc(s, &s->xcorner, 2 * nv)) != MIUGKS_OK) break;
+        if ((st = falloc(s, &s->xcorner, 2 * nv)) != MIUGKS_OK) break;
         // smallest interior physical time step (for the numerical time step)
         s->dtp_min = 1e300;
         for (int i = 1; i < L0.nx; ++i) s->dtp_min = std::fmin(s->dtp_min, opts->cfl * std::fmin(L0.dx[i - 1], L0.dx[i]) / s->umax);
@@ -539,8 +620,13 @@ miugks_status miugks_init_fields(miugks_solver* s, const double* rho, const doub
         prim[4 * c] = rho[c]; prim[4 * c + 1] = u[c]; prim[4 * c + 2] = v[c]; prim[4 * c + 3] = t[c];
     }
     CK(cudaMemcpyAsync(s->lev[0].Wn, prim.data(), prim.size() * sizeof(double), cudaMemcpyHostToDevice, s->st));
-    CK(launch_init_maxwell<double>(s->lev[0].dev, s->vel, s->lev[0].Wn, s->f, s->st));
-    CK(launch_moments<double>(s->lev[0].dev, s->vel, s->f, s->W, s->q, s->st));
+    if (s->mixed) {
+        CK(launch_init_maxwell<float>(s->lev[0].dev, s->vel, s->lev[0].Wn, (float*)s->f, s->st));
+        CK(launch_moments<float>(s->lev[0].dev, s->vel, (const float*)s->f, s->W, s->q, s->st));
+    } else {
+        CK(launch_init_maxwell<double>(s->lev[0].dev, s->vel, s->lev[0].Wn, (double*)s->f, s->st));
+        CK(launch_moments<double>(s->lev[0].dev, s->vel, (const double*)s->f, s->W, s->q, s->st));
+    }
     CK(cudaStreamSynchronize(s->st));
     s->iter = 0;
     s->initialised = true;
@@ -630,16 +716,14 @@ miugks_status miugks_get_macro(miugks_solver* s, double* rho, double* u, double*
 miugks_status miugks_get_f(miugks_solver* s, double* f)
 {
     if (!s || !f) return MIUGKS_EINVAL;
-    CK(cudaMemcpyAsync(f, s->f, 2 * (size_t)s->lev[0].nc * s->nv * sizeof(double), cudaMemcpyDeviceToHost, s->st));
-    CK(cudaStreamSynchronize(s->st));
-    return MIUGKS_OK;
+    return to_host(s, f, s->f, 2 * (size_t)s->lev[0].nc * s->nv);
 }
 
 miugks_status miugks_set_f(miugks_solver* s, const double* f)
 {
     if (!s || !f) return MIUGKS_EINVAL;
-    CK(cudaMemcpyAsync(s->f, f, 2 * (size_t)s->lev[0].nc * s->nv * sizeof(double), cudaMemcpyHostToDevice, s->st));
-    CK(launch_moments<double>(s->lev[0].dev, s->vel, s->f, s->W, s->q, s->st));
+    ST(to_device(s, s->f, f, 2 * (size_t)s->lev[0].nc * s->nv));
+    ST(moments_now(s));
     CK(cudaStreamSynchronize(s->st));
     s->initialised = true;
     return MIUGKS_OK;
@@ -683,7 +767,11 @@ miugks_status miugks_get_wall(miugks_solver* s, int bc, int* n_faces, double* p,
     if (e != cudaSuccess) { cudaFree(dfaces); return fail(s, MIUGKS_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e)); }
     std::vector<double> h(3 * (size_t)n);
     e = cudaMemcpyAsync(dfaces, faces.data(), n * sizeof(int), cudaMemcpyHostToDevice, s->st);
-    if (e == cudaSuccess) e = launch_wall_quantities<double>(L0.dev, s->vel, s->bc, s->Cw, s->f, bc, dfaces, n, dout, s->st);
+    if (e == cudaSuccess)
+        e = s->mixed ? launch_wall_quantities<float>(L0.dev, s->vel, s->bc, s->Cw, (const float*)s->f, bc, dfaces, n,
+                                                      dout, s->st)
+                     : launch_wall_quantities<double>(L0.dev, s->vel, s->bc, s->Cw, (const double*)s->f, bc, dfaces, n,
+                                                       dout, s->st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), dout, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
     cudaFree(dfaces);
@@ -733,22 +821,12 @@ miugks_status miugks_stage_flux(miugks_solver* s, double* R, double* phx, double
     ST(flux_stage(s));
     HLevel& L0 = s->lev[0];
     if (R) CK(cudaMemcpyAsync(R, s->R, 4 * (size_t)L0.nc * sizeof(double), cudaMemcpyDeviceToHost, s->st));
-    if (phx) CK(cudaMemcpyAsync(phx, s->phx, 2 * (size_t)L0.nfx * s->nv * sizeof(double), cudaMemcpyDeviceToHost, s->st));
-    if (phy) CK(cudaMemcpyAsync(phy, s->phy, 2 * (size_t)L0.nfy * s->nv * sizeof(double), cudaMemcpyDeviceToHost, s->st));
     CK(cudaStreamSynchronize(s->st));
+    if (phx) ST(to_host(s, phx, s->phx, 2 * (size_t)L0.nfx * s->nv));
+    if (phy) ST(to_host(s, phy, s->phy, 2 * (size_t)L0.nfy * s->nv));
     return MIUGKS_OK;
 }
 
-namespace {
-__global__ void k_invD_from_itau(LevelDev L, VelDev Vg, const double* it, double* invD)
-{
-    int c = blockIdx.x, i = c % L.nx, j = c / L.nx;
-    for (int k = threadIdx.x; k < Vg.nv; k += blockDim.x) {
-        double g = (fabs(Vg.u[k]) * L.dy[j] + fabs(Vg.v[k]) * L.dx[i]) / (L.dx[i] * L.dy[j]);
-        invD[(size_t)c * Vg.nv + k] = 1.0 / (it[c] + g);
-    }
-}
-} // namespace
 
 miugks_status miugks_stage_sgs_micro(miugks_solver* s, int lev, const double* inv_tau, const double* r, double* x)
 {
@@ -756,13 +834,19 @@ miugks_status miugks_stage_sgs_micro(miugks_solver* s, int lev, const double* in
     HLevel& Lv = s->lev[lev];
     size_t n = 2 * (size_t)Lv.nc * s->nv;
     CK(cudaMemcpyAsync(Lv.inv_tau, inv_tau, Lv.nc * sizeof(double), cudaMemcpyHostToDevice, s->st));
-    CK(cudaMemcpyAsync(Lv.r, r, n * sizeof(double), cudaMemcpyHostToDevice, s->st));
-    k_invD_from_itau<<<Lv.nc, 128, 0, s->st>>>(Lv.dev, s->vel, Lv.inv_tau, Lv.invD);
-    CK(cudaGetLastError());
-    CK(launch_micro_sgs<double>(micro_args(s, lev), s->Zw, Lv.invD, Lv.r, Lv.dl, s->xcorner, s->st));
-    CK(cudaMemcpyAsync(x, Lv.dl, n * sizeof(double), cudaMemcpyDeviceToHost, s->st));
-    CK(cudaStreamSynchronize(s->st));
-    return MIUGKS_OK;
+    ST(to_device(s, Lv.r, r, n));
+    MicroArgs mi = micro_args(s, lev);
+    if (s->mixed) {
+        k_invD_from_itau<float><<<Lv.nc, 128, 0, s->st>>>(Lv.dev, s->vel, Lv.inv_tau, (float*)Lv.invD);
+        CK(cudaGetLastError());
+        CK(launch_micro_sgs<float>(mi, s->Zw, (float*)Lv.invD, (float*)Lv.r, (float*)Lv.dl, (float*)s->xcorner, s->st));
+    } else {
+        k_invD_from_itau<double><<<Lv.nc, 128, 0, s->st>>>(Lv.dev, s->vel, Lv.inv_tau, (double*)Lv.invD);
+        CK(cudaGetLastError());
+        CK(launch_micro_sgs<double>(mi, s->Zw, (double*)Lv.invD, (double*)Lv.r, (double*)Lv.dl, (double*)s->xcorner,
+                                    s->st));
+    }
+    return to_host(s, x, Lv.dl, n);
 }
 
 miugks_status miugks_stage_apply_micro(miugks_solver* s, int lev, const double* inv_tau, const double* x, double* y)
@@ -771,12 +855,13 @@ miugks_status miugks_stage_apply_micro(miugks_solver* s, int lev, const double* 
     HLevel& Lv = s->lev[lev];
     size_t n = 2 * (size_t)Lv.nc * s->nv;
     CK(cudaMemcpyAsync(Lv.inv_tau, inv_tau, Lv.nc * sizeof(double), cudaMemcpyHostToDevice, s->st));
-    CK(cudaMemcpyAsync(Lv.dl, x, n * sizeof(double), cudaMemcpyHostToDevice, s->st));
-    CK(cudaMemsetAsync(Lv.r, 0, n * sizeof(double), s->st));
-    CK(launch_micro_renew<double>(micro_args(s, lev), s->Zw, Lv.dl, Lv.r, nullptr, 1, s->st));
+    ST(to_device(s, Lv.dl, x, n));
+    CK(cudaMemsetAsync(Lv.r, 0, n * s->fsz, s->st));
+    MicroArgs mi = micro_args(s, lev);
+    if (s->mixed) CK(launch_micro_renew<float>(mi, s->Zw, (float*)Lv.dl, (float*)Lv.r, nullptr, 1, s->st));
+    else CK(launch_micro_renew<double>(mi, s->Zw, (double*)Lv.dl, (double*)Lv.r, nullptr, 1, s->st));
     std::vector<double> h(n);
-    CK(cudaMemcpyAsync(h.data(), Lv.r, n * sizeof(double), cudaMemcpyDeviceToHost, s->st));
-    CK(cudaStreamSynchronize(s->st));
+    ST(to_host(s, h.data(), Lv.r, n));
     for (size_t q = 0; q < n; ++q) y[q] = -h[q];
     return MIUGKS_OK;
 }
@@ -791,8 +876,8 @@ miugks_status miugks_stage_sgs_macro(miugks_solver* s, int lev, const double* W,
     CK(cudaMemcpyAsync(Lv.Wn, Wg, n4 * sizeof(double), cudaMemcpyHostToDevice, s->st));
     CK(cudaMemcpyAsync(Lv.R, R, n4 * sizeof(double), cudaMemcpyHostToDevice, s->st));
     MacroArgs ma = macro_args(s, lev, 0.0);
-    CK(launch_macro_gamma(ma, Lv.Wn, Lv.gx, Lv.gy, s->st));
-    CK(launch_macro_sgs(ma, Lv.Wc, Lv.gx, Lv.gy, Lv.R, Lv.dW, nullptr, s->st));
+    CK(launch_macro_gamma(ma, Lv.Wn, Lv.gx, Lv.gy, Lv.idiag, s->st));
+    CK(launch_macro_sgs(ma, Lv.Wc, Lv.gx, Lv.gy, Lv.idiag, Lv.T, Lv.R, Lv.dW, s->st));
     CK(cudaMemcpyAsync(dW, Lv.dW, n4 * sizeof(double), cudaMemcpyDeviceToHost, s->st));
     CK(cudaStreamSynchronize(s->st));
     return MIUGKS_OK;
@@ -807,7 +892,7 @@ miugks_status miugks_stage_resid_macro(miugks_solver* s, int lev, const double* 
     CK(cudaMemcpyAsync(Lv.Wn, Wg, n4 * sizeof(double), cudaMemcpyHostToDevice, s->st));
     CK(cudaMemsetAsync(Lv.P, 0, n4 * sizeof(double), s->st));
     MacroArgs ma = macro_args(s, lev, 0.0);
-    CK(launch_macro_gamma(ma, Lv.Wn, Lv.gx, Lv.gy, s->st));
+    CK(launch_macro_gamma(ma, Lv.Wn, Lv.gx, Lv.gy, Lv.idiag, s->st));
     CK(launch_macro_resid(ma, Lv.Wc, Lv.gx, Lv.gy, Lv.P, Lv.R, 1, s->st));
     CK(cudaMemcpyAsync(RE, Lv.R, n4 * sizeof(double), cudaMemcpyDeviceToHost, s->st));
     CK(cudaStreamSynchronize(s->st));
@@ -830,8 +915,8 @@ static miugks_status transfer(miugks_solver* s, int lev, int m, const double* in
     e = cudaMemcpyAsync(din, in, nin * sizeof(double), cudaMemcpyHostToDevice, s->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(dout, 0, nout * sizeof(double), s->st);
     if (e == cudaSuccess)
-        e = up ? launch_restrict(F.dev, C.dev, m, 1, din, dout, s->st)
-               : launch_prolong_add(F.dev, C.dev, m, 1, F.pidx, F.pw, din, dout, nullptr, s->st);
+        e = up ? launch_restrict<double>(F.dev, C.dev, m, 1, din, dout, s->st)
+               : launch_prolong_add<double>(F.dev, C.dev, m, 1, F.pidx, F.pw, din, dout, nullptr, s->st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, nout * sizeof(double), cudaMemcpyDeviceToHost, s->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
     cudaFree(din);

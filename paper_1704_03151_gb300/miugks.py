@@ -16,6 +16,7 @@ from . import build as _build
 MIUGKS_OK, MIUGKS_EINVAL, MIUGKS_ENOMEM, MIUGKS_ECUDA, MIUGKS_EDIVERGED, MIUGKS_ETIMEOUT, \
     MIUGKS_ENOTCONVERGED, MIUGKS_ESTATE = range(8)
 WALL, SYMMETRY, FARFIELD, OUTFLOW = 0, 1, 2, 3
+PRECISIONS = {"fp64": 0, "mixed": 1}
 
 _d, _i, _vp, _P = ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.POINTER
 
@@ -134,7 +135,7 @@ class Solver:
     ``paper_1704_03151_gb300.workloads`` (mesh nodes, face BC ids, BC table,
     velocity grid, gas, multigrid options)."""
 
-    def __init__(self, case, use_torch=True, stream=None):
+    def __init__(self, case, use_torch=True, stream=None, precision=None):
         import torch
         if not torch.cuda.is_available():
             raise MiugksError(MIUGKS_ECUDA, "no CUDA device: the MIUGKS library has no CPU path")
@@ -156,7 +157,12 @@ class Solver:
         dev = torch.device("cuda", torch.cuda.current_device())
         self._stream = stream if stream is not None else torch.cuda.current_stream(dev)
         self._alloc = _TorchAllocator(torch, dev) if use_torch else None
-        opts = miugks_opts(mg["levels"], mg["nu1"], mg["nu2"], mg["nuc"], mg["cfl"], mg["dtn_growth"], 0,
+        precision = precision or mg.get("precision", "fp64")
+        if precision not in PRECISIONS:
+            raise MiugksError(MIUGKS_EINVAL, "precision must be one of %s" % sorted(PRECISIONS))
+        self.precision = precision
+        opts = miugks_opts(mg["levels"], mg["nu1"], mg["nu2"], mg["nuc"], mg["cfl"], mg["dtn_growth"],
+                           PRECISIONS[precision],
                            _vp(self._stream.cuda_stream),
                            self._alloc.alloc_fn if self._alloc else ALLOC_FN(),
                            self._alloc.free_fn if self._alloc else FREE_FN(), None)

@@ -1,0 +1,81 @@
+"""Mixed-precision form (FP32 per-velocity arithmetic and storage, FP64
+moments, per-face scalars, prediction and residual) against the FP64 oracle
+and the FP64 GPU solver.  The paper gives no bound for this form; the bounds
+asserted here are measured on GB300 (see the design notes) with a margin.
+
+Reading of the errors: FP32 rounding of f is about 6e-8 relative per
+operation, so the per-iteration state differs at the 1e-6 level; the
+converged states differ by the FP32 residual floor.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1704_03151_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1704_03151_gb300 import miugks
+    miugks.load()
+    return miugks
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def report(name, errs):
+    print("\nMIXED %s %s" % (name, " ".join("%s=%.2e" % kv for kv in errs.items())))
+
+
+@pytest.mark.parametrize("name,case", [
+    ("cavity16_L3", wl.cavity(n=16, nvel=12, kn=0.5, lid=0.2, levels=3)),
+    ("couette_sym", wl.couette(n=10, nvel=12, kn=0.3, t_bottom=1.0, t_top=1.3, u_top=0.2, nx=6)),
+    ("plate_small", wl.flat_plate(kn=0.2, nvel=12, levels=2, n_up=4, n_plate=8, n_down=4, ny=12)),
+])
+def test_mixed_iterations_close_to_oracle(lib, name, case):
+    o = oracle.Oracle(case)
+    g = lib.Solver(case, precision="mixed")
+    fields = wl.random_fields(case, 3, amp=0.08)
+    o.init_fields(*fields)
+    g.init_fields(*fields)
+    errs = {}
+    for n in (1, 4):
+        ro, rg = o.step(n), g.step(n)
+        errs["f@%d" % n] = rel(g.get_f(), o.get_f())
+        mo, mg = o.macro(), g.macro()
+        for k in ("rho", "u", "v", "t"):
+            errs["%s@%d" % (k, n)] = rel(mg[k], mo[k])
+        errs["res@%d" % n] = rel(rg, ro)
+    report(name, errs)
+    assert all(v < 2e-5 for k, v in errs.items() if not k.startswith("res")), errs
+    assert errs["res@4"] < 1e-3, errs
+
+
+def test_mixed_converges_to_fp64_steady_state(lib):
+    """64x64 cavity, 32x32 velocities, 3 levels, Kn 1: both forms run to the
+    paper's convergence criterion (RMS residual 1e-6); the converged fields
+    and wall quantities agree within the measured mixed-precision bound."""
+    case = wl.CONFIGS["c2"](kn=1.0)
+    out = {}
+    for prec in ("fp64", "mixed"):
+        g = lib.Solver(case, precision=prec)
+        g.init_uniform(1.0, 0.0, 0.0, 1.0)
+        it, res, ok = g.run(1e-6, 400)
+        assert ok, (prec, it, res)
+        out[prec] = (g.macro(), g.wall(2), it)
+    m64, w64, it64 = out["fp64"]
+    m32, w32, it32 = out["mixed"]
+    errs = {k: rel(m32[k], m64[k]) for k in ("rho", "u", "v", "t")}
+    errs["lid_shear"] = rel(w32[1], w64[1])
+    errs["lid_heat"] = rel(w32[2], w64[2])
+    report("c2_converged it64=%d it32=%d" % (it64, it32), errs)
+    assert abs(it32 - it64) <= max(3, it64 // 5)
+    assert all(v < 1e-4 for v in errs.values()), errs
