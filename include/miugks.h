@@ -113,6 +113,14 @@ miugks_status miugks_init_fields(miugks_solver *s, const double *rho, const doub
  * Step 1 of the last iteration (Eq. Residual_Def).  Returns MIUGKS_EDIVERGED
  * when the state became unphysical. */
 miugks_status miugks_step(miugks_solver *s, int n_iter, double res_out[4]);
+/* Enqueue n outer iterations on the solver's stream and return without waiting;
+ * miugks_wait() then waits for them and returns the RMS residual of the last
+ * one (and MIUGKS_EDIVERGED as miugks_step does).  Lets one host thread keep
+ * many solvers, each on its own stream, running concurrently.  On a stream other
+ * than the legacy default stream, iterations after the first are replayed from
+ * a captured CUDA graph. */
+miugks_status miugks_step_async(miugks_solver *s, int n_iter);
+miugks_status miugks_wait(miugks_solver *s, double res_out[4]);
 /* iterate until every RMS component is below tol (Sec. 4.1) or max_iter */
 miugks_status miugks_run(miugks_solver *s, double tol, int max_iter, int *iters_out, double res_out[4]);
 /* RMS residual of the current state (Step 1 only) */

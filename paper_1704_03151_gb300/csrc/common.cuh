@@ -12,6 +12,7 @@ namespace miugks {
 constexpr int kKint = 1;                       // internal degrees of freedom
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kMaxLevels = 8;
+constexpr int kMaxBcs = 64;                    // boundary conditions per solver
 
 enum BcType { BC_WALL = 0, BC_SYMMETRY = 1, BC_FARFIELD = 2, BC_OUTFLOW = 3 };
 
@@ -175,6 +176,58 @@ __device__ __forceinline__ void block_sum(double (&v)[N], double* scratch)
         v[q] = s;
     }
     __syncthreads();
+}
+
+// Block reduction of per-thread velocity sums into FP64 totals, broadcast to
+// every thread.  FP64 form: FP64 shuffle tree per warp.  Mixed form: each warp
+// reduces its Kahan pairs as float-float numbers (error-free TwoSum in FP32),
+// then warp 0 alone adds the per-warp totals in FP64.  scratch: 32 * N doubles.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = a + b;
+    float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+template <int N>
+__device__ __forceinline__ void block_total(Acc<float> (&a)[N], double* scratch, double (&out)[N])
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    #pragma unroll
+    for (int q = 0; q < N; ++q) {
+        float hi = a[q].s, lo = -a[q].c;
+        #pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            float h2 = __shfl_xor_sync(0xffffffffu, hi, o), l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+            float s, e;
+            two_sum(hi, h2, s, e);
+            lo = lo + l2 + e;
+            hi = s;
+        }
+        if (lane == 0) scratch[warp * N + q] = (double)hi + (double)lo;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        #pragma unroll
+        for (int q = 0; q < N; ++q) {
+            double x = lane < nw ? scratch[lane * N + q] : 0.0;
+            #pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            if (lane == 0) scratch[32 * N - N + q] = x;
+        }
+    }
+    __syncthreads();
+    #pragma unroll
+    for (int q = 0; q < N; ++q) out[q] = scratch[32 * N - N + q];
+    __syncthreads();
+}
+
+template <int N>
+__device__ __forceinline__ void block_total(Acc<double> (&a)[N], double* scratch, double (&out)[N])
+{
+    #pragma unroll
+    for (int q = 0; q < N; ++q) out[q] = a[q].s;
+    block_sum<N>(out, scratch);
 }
 
 } // namespace miugks

@@ -59,6 +59,26 @@ __device__ __forceinline__ void time_coeffs_fast(double dt, double tau, double q
     }
 }
 
+// one of the five time integrals (series below x = dt/tau = 1, closed form above)
+__device__ __forceinline__ double time_coeff_one(double dt, double tau, int m)
+{
+    double x = dt / tau;
+    if (x < 1.0) {
+        double acc = c_series[m][27];
+        #pragma unroll
+        for (int n = 26; n >= 0; --n) acc = fma(acc, x, c_series[m][n]);
+        return (m == 0 || m == 3) ? dt * acc : dt * dt * acc;
+    }
+    double e = exp(-x), E1 = -expm1(-x);
+    switch (m) {
+    case 0: return dt - tau * E1;
+    case 1: return -tau * dt * (1.0 + e) + 2.0 * tau * tau * E1;
+    case 2: return 0.5 * dt * dt - tau * dt + tau * tau * E1;
+    case 3: return tau * E1;
+    default: return tau * dt * e - tau * tau * E1;
+    }
+}
+
 // van Leer limited slope 2 s1 s2 / (s1 + s2) when s1 s2 > 0, else 0
 __device__ __forceinline__ double vl_limited(double s1, double s2)
 {
@@ -195,25 +215,25 @@ __global__ void __launch_bounds__(256) k_face_flux(FaceFluxArgs<F> A)
         W0a[0].add(w * g); W0a[1].add(w * u * g); W0a[2].add(w * v * g);
         W0a[3].add(w * (F(0.5) * (u * u + v * v) * g + f0s[nv + k]));
     }
-    double W0[4] = {W0a[0].value(), W0a[1].value(), W0a[2].value(), W0a[3].value()};
-    block_sum<4>(W0, red);
-    // face scalars (one thread), broadcast through shared memory
-    if (tid == 0) {
-        double rho, U, V, lam;
-        prim4(W0, rho, U, V, lam);
-        double tau0 = tau_of(A.gas, rho, lam);
-        double um = axis == 0 ? Vg.umax : Vg.vmax;
-        double dt = A.cfl * fmin(wL, wR) / um;
-        const double* WL = A.W + 4 * (size_t)cL;
-        const double* WR = A.W + 4 * (size_t)cR;
-        double dwl[4], dwr[4], ir = 1.0 / rho;
-        for (int m = 0; m < 4; ++m) {
-            dwl[m] = (W0[m] - WL[m]) / hL * ir;
-            dwr[m] = (WR[m] - W0[m]) / hR * ir;
+    double W0[4];
+    block_total<4>(W0a, red, W0);
+    // face scalars, spread over the lanes of warp 0 (an FP64 instruction costs the
+    // same for one lane as for thirty-two): lane 0 the collision time and time
+    // step, lanes 1 and 2 the left and right equilibrium slopes
+    if (tid < 3) {
+        double rho = W0[0], ir = rcp64(rho);
+        double U = W0[1] * ir, V = W0[2] * ir;
+        double lam = (kKint + 2) * rho * rcp64(4.0 * (W0[3] - 0.5 * (W0[1] * U + W0[2] * V)));
+        if (tid == 0) {
+            par[0] = rho; par[1] = U; par[2] = V; par[3] = lam;
+            par[4] = tau_of(A.gas, rho, lam);
+            par[5] = A.cfl * fmin(wL, wR) / (axis == 0 ? Vg.umax : Vg.vmax);
+        } else {
+            const double* Wc = A.W + 4 * (size_t)(tid == 1 ? cL : cR);
+            double hf = (tid == 1 ? 1.0 : -1.0) * ir * rcp64(tid == 1 ? hL : hR), dw[4];
+            for (int m = 0; m < 4; ++m) dw[m] = (W0[m] - Wc[m]) * hf;
+            micro_slope(dw, U, V, lam, par + (tid == 1 ? 8 : 12));
         }
-        micro_slope(dwl, U, V, lam, par + 8);
-        micro_slope(dwr, U, V, lam, par + 12);
-        par[0] = rho; par[1] = U; par[2] = V; par[3] = lam; par[4] = tau0; par[5] = dt;
     }
     __syncthreads();
     const double rho0 = par[0], U0 = par[1], V0 = par[2], lam0 = par[3];
@@ -246,15 +266,17 @@ __global__ void __launch_bounds__(256) k_face_flux(FaceFluxArgs<F> A)
         }
     }
     double s6[6];
-    #pragma unroll
-    for (int q = 0; q < 6; ++q) s6[q] = s6a[q].value();
-    block_sum<6>(s6, red);
-    if (tid == 0) {
-        double dwt[4], ir = 1.0 / rho0;
-        for (int m = 0; m < 4; ++m) dwt[m] = -s6[2 + m] * ir;
-        micro_slope(dwt, U0, V0, lam0, par + 16);
-        time_coeffs_fast(par[5], par[4], par + 20);
-        par[6] = s6[0]; par[7] = s6[1];
+    block_total<6>(s6a, red, s6);
+    // lane 0: time slope A from compatibility; lanes 1-5: one time integral each
+    if (tid < 6) {
+        if (tid == 0) {
+            double dwt[4], ir = -rcp64(rho0);
+            for (int m = 0; m < 4; ++m) dwt[m] = s6[2 + m] * ir;
+            micro_slope(dwt, U0, V0, lam0, par + 16);
+            par[6] = s6[0]; par[7] = s6[1];
+        } else {
+            par[20 + tid - 1] = time_coeff_one(par[5], par[4], tid - 1);
+        }
     }
     __syncthreads();
     F As[4];
@@ -286,8 +308,8 @@ __global__ void __launch_bounds__(256) k_face_flux(FaceFluxArgs<F> A)
         Fa[0].add(w * pg); Fa[1].add(w * u * pg); Fa[2].add(w * v * pg);
         Fa[3].add(w * (F(0.5) * (u * u + v * v) * pg + ph));
     }
-    double Fm[4] = {Fa[0].value(), Fa[1].value(), Fa[2].value(), Fa[3].value()};
-    block_sum<4>(Fm, red);
+    double Fm[4];
+    block_total<4>(Fa, red, Fm);
     if (tid == 0)
         for (int m = 0; m < 4; ++m) A.Fm[4 * (size_t)fi + m] = Fm[m];
 }

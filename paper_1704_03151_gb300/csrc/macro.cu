@@ -297,6 +297,13 @@ __device__ void macro_ghost_terms(const MacroArgs& a, const double* W, const dou
     }
 }
 
+// inputs of one lane for one diagonal that do not depend on the previous diagonal
+struct MacroLane {
+    int c, nb[2];
+    bool on, inter[2];
+    double gm[2], S[2], T0[2], own, id, hv, W, G;
+};
+
 __global__ void __cluster_dims__(kMacroCluster, 1, 1) __launch_bounds__(kMacroThreads)
 k_macro_sgs(MacroArgs a, double* __restrict__ W, const double* __restrict__ T0, double* __restrict__ T1,
             double* __restrict__ Gt, const double* __restrict__ gx, const double* __restrict__ gy,
@@ -307,7 +314,28 @@ k_macro_sgs(MacroArgs a, double* __restrict__ W, const double* __restrict__ T0, 
     const int nx = L.nx, ny = L.ny, nd = nx + ny - 1;
     const int t = cl.block_rank() * blockDim.x + threadIdx.x;
     const int m = t & 3, g0 = threadIdx.x & 28;        // component; first lane of the cell's group
-    const int ncell_pass = kMacroCluster * blockDim.x / 4;
+    const int slot = t >> 2;                            // one cell of a diagonal per four lanes
+    auto prepare = [&](int pass, int d, MacroLane& p) {
+        int ilo = d - (ny - 1) > 0 ? d - (ny - 1) : 0, ihi = d < nx - 1 ? d : nx - 1;
+        p.on = slot <= ihi - ilo;
+        if (!p.on) return;
+        int i = ilo + slot, j = d - i, c = j * nx + i;
+        p.c = c;
+        #pragma unroll
+        for (int axis = 0; axis < 2; ++axis) {
+            int fidx = axis == 0 ? j * (nx + 1) + i + pass : (j + pass) * nx + i;
+            p.inter[axis] = (axis == 0 ? L.fbx[fidx] : L.fby[fidx]) < 0;
+            p.nb[axis] = axis == 0 ? c + (pass ? 1 : -1) : c + (pass ? nx : -nx);
+            p.gm[axis] = axis == 0 ? gx[fidx] : gy[fidx];
+            p.S[axis] = axis == 0 ? L.dy[j] : L.dx[i];
+            p.T0[axis] = p.inter[axis] ? T0[8 * (size_t)p.nb[axis] + 4 * axis + m] : 0.0;
+        }
+        p.own = pass == 0 ? R[4 * (size_t)c + m] : dW[4 * (size_t)c + m];
+        p.id = idiag[c];
+        p.hv = 0.5 * L.rdx[i] * L.rdy[j];
+        p.W = W[4 * (size_t)c + m];
+        p.G = (pass == 1 && (i == nx - 1 || j == ny - 1)) ? Gt[4 * (size_t)c + m] : 0.0;
+    };
     for (int pass = 0; pass < 2; ++pass) {
         if (pass == 1) {
             // upper-side ghost terms of the last column and row, from the forward dW (one thread per cell)
@@ -318,54 +346,32 @@ k_macro_sgs(MacroArgs a, double* __restrict__ W, const double* __restrict__ T0, 
             cl.sync();
         }
         const double sgn = pass ? 1.0 : -1.0;
+        MacroLane cur, nxt;
+        prepare(pass, pass == 0 ? 0 : nd - 1, cur);
         for (int d0 = 0; d0 < nd; ++d0) {
-            int d = pass == 0 ? d0 : nd - 1 - d0;
-            int ilo = d - (ny - 1) > 0 ? d - (ny - 1) : 0, ihi = d < nx - 1 ? d : nx - 1;
-            for (int base = 0; base <= ihi - ilo; base += ncell_pass) {
-                int slot = base + (t >> 2);
-                bool on = slot <= ihi - ilo;
-                int i = ilo + slot, j = d - i, c = j * nx + i;
-                double wp = 0.0;
-                if (on) {
-                    double acc = 0.0;
-                    #pragma unroll
-                    for (int axis = 0; axis < 2; ++axis) {
-                        int nb, fidx;
-                        bool interior;
-                        if (axis == 0) {
-                            fidx = j * (nx + 1) + i + pass;
-                            interior = L.fbx[fidx] < 0;
-                            nb = c + (pass ? 1 : -1);
-                        } else {
-                            fidx = (j + pass) * nx + i;
-                            interior = L.fby[fidx] < 0;
-                            nb = c + (pass ? nx : -nx);
-                        }
-                        if (!interior) continue;
-                        double gm = axis == 0 ? gx[fidx] : gy[fidx];
-                        double S = axis == 0 ? L.dy[j] : L.dx[i];
-                        double dT = T1[8 * (size_t)nb + 4 * axis + m] - T0[8 * (size_t)nb + 4 * axis + m];
-                        acc = fma(S, fma(-gm, dW[4 * (size_t)nb + m], sgn * dT), acc);
-                    }
-                    const double hv = 0.5 * L.rdx[i] * L.rdy[j], id = idiag[c];
-                    double dw;
-                    if (pass == 0) {
-                        dw = fma(-acc, hv, R[4 * (size_t)c + m]) * id;
-                    } else {
-                        if (i == nx - 1 || j == ny - 1) acc += Gt[4 * (size_t)c + m];
-                        dw = fma(-acc * hv, id, dW[4 * (size_t)c + m]);
-                    }
-                    dW[4 * (size_t)c + m] = dw;
-                    wp = W[4 * (size_t)c + m] + dw;
+            double wp = 0.0;
+            if (cur.on) {
+                double acc = cur.G;
+                #pragma unroll
+                for (int axis = 0; axis < 2; ++axis) {
+                    if (!cur.inter[axis]) continue;
+                    const size_t nb = cur.nb[axis];
+                    double dT = T1[8 * nb + 4 * axis + m] - cur.T0[axis];
+                    acc = fma(cur.S[axis], fma(-cur.gm[axis], dW[4 * nb + m], sgn * dT), acc);
                 }
-                double T1c[8];
-                producer_fluxes(wp, m, g0, T1c);
-                if (on) {
-                    T1[8 * (size_t)c + m] = T1c[m];
-                    T1[8 * (size_t)c + 4 + m] = T1c[4 + m];
-                }
+                double dw = pass == 0 ? fma(-acc, cur.hv, cur.own) * cur.id : fma(-acc * cur.hv, cur.id, cur.own);
+                dW[4 * (size_t)cur.c + m] = dw;
+                wp = cur.W + dw;
             }
+            double T1c[8];
+            producer_fluxes(wp, m, g0, T1c);
+            if (cur.on) {
+                T1[8 * (size_t)cur.c + m] = T1c[m];
+                T1[8 * (size_t)cur.c + 4 + m] = T1c[4 + m];
+            }
+            if (d0 + 1 < nd) prepare(pass, pass == 0 ? d0 + 1 : nd - 2 - d0, nxt);
             cl.sync();   // release/acquire at cluster scope: the diagonal is visible to the next one
+            cur = nxt;
         }
     }
     for (int c = t; c < 4 * L.nc; c += kMacroCluster * blockDim.x) W[c] += dW[c];
@@ -378,6 +384,9 @@ cudaError_t launch_macro_sgs(const MacroArgs& a, double* W, const double* gx, co
     double* T0 = T;
     double* T1 = T + 8 * (size_t)a.L.nc;
     double* Gt = T + 16 * (size_t)a.L.nc;
+    // one cell of a diagonal per four lanes of the cluster
+    const int maxdiag = a.L.nx < a.L.ny ? a.L.nx : a.L.ny;
+    if (4 * maxdiag > kMacroCluster * kMacroThreads) return cudaErrorInvalidValue;
     k_macro_prep<<<(a.L.nc + 127) / 128, 128, 0, st>>>(a.L, W, T0);
     k_macro_sgs<<<kMacroCluster, kMacroThreads, 0, st>>>(a, W, T0, T1, Gt, gx, gy, idiag, R, dW);
     return cudaGetLastError();

@@ -67,14 +67,20 @@ __global__ void __launch_bounds__(256) k_micro_residual(MicroArgs M, GasDev gas,
     const int c = blockIdx.x, nv = Vg.nv, nx = L.nx;
     const int i = c % nx, j = c / nx;
     const size_t nc = L.nc;
-    F* Eu = reinterpret_cast<F*>(sm);
+    double* cs = sm;                            // cell scalars
+    F* Eu = reinterpret_cast<F*>(sm + 8);
     F* Ev = Eu + Vg.nu;
-    double rho, U, V, lam;
-    prim4(Wt + 4 * (size_t)c, rho, U, V, lam);
-    const double itau = 1.0 / tau_of(gas, rho, lam);
+    if (threadIdx.x == 0) {
+        double rho, U, V, lam;
+        prim4(Wt + 4 * (size_t)c, rho, U, V, lam);
+        double it = 1.0 / tau_of(gas, rho, lam);
+        cs[0] = rho; cs[1] = U; cs[2] = V; cs[3] = lam; cs[4] = it;
+        inv_tau[c] = it + dtn_inv;
+    }
+    __syncthreads();
+    const double rho = cs[0], U = cs[1], V = cs[2], lam = cs[3], itau = cs[4];
     for (int a = threadIdx.x; a < Vg.nu; a += blockDim.x) { double d = Vg.ua[a] - U; Eu[a] = (F)exp(-lam * d * d); }
     for (int b = threadIdx.x; b < Vg.nvv; b += blockDim.x) { double d = Vg.vb[b] - V; Ev[b] = (F)exp(-lam * d * d); }
-    if (threadIdx.x == 0) inv_tau[c] = itau + dtn_inv;
     __syncthreads();
     const F gnorm = (F)(rho * lam / kPi), hfac = (F)(kKint / (4.0 * lam)), flam2 = (F)(2.0 * lam);
     const F shk = (F)((1.0 - gas.pr) * 4.0 * lam * lam / (5.0 * rho));
@@ -105,7 +111,7 @@ cudaError_t launch_micro_residual(const MicroArgs& m, GasDev gas, const double* 
                                   const F* phx, const F* phy, double dtn_inv, double* inv_tau, F* invD, F* r,
                                   cudaStream_t st)
 {
-    size_t smem = sizeof(F) * (m.V.nu + m.V.nvv);
+    size_t smem = sizeof(double) * 8 + sizeof(F) * (m.V.nu + m.V.nvv);
     k_micro_residual<F><<<m.L.nc, m.V.nv >= 256 ? 256 : 128, smem, st>>>(m, gas, Wt, q, f, phx, phy, dtn_inv,
                                                                           inv_tau, invD, r);
     return cudaGetLastError();
@@ -123,10 +129,15 @@ __global__ void k_coarse_coeffs(MicroArgs M, GasDev gas, const double* __restric
 {
     const LevelDev& L = M.L;
     const int c = blockIdx.x, i = c % L.nx, j = c / L.nx;
-    double rho, U, V, lam;
-    prim4(Wt + 4 * (size_t)c, rho, U, V, lam);
-    double it = 1.0 / tau_of(gas, rho, lam) + dtn_inv;
-    if (threadIdx.x == 0) inv_tau[c] = it;
+    __shared__ double sit;
+    if (threadIdx.x == 0) {
+        double rho, U, V, lam;
+        prim4(Wt + 4 * (size_t)c, rho, U, V, lam);
+        sit = 1.0 / tau_of(gas, rho, lam) + dtn_inv;
+        inv_tau[c] = sit;
+    }
+    __syncthreads();
+    const double it = sit;
     for (int k = threadIdx.x; k < M.V.nv; k += blockDim.x)
         invD[(size_t)c * M.V.nv + k] = recip((F)it + geomD<F>(L, i, j, (F)M.V.u[k], (F)M.V.v[k]));
 }
@@ -208,6 +219,7 @@ __global__ void __cluster_dims__(kChainCluster, 1, 1) __launch_bounds__(kChainTh
 k_sgs_chain(MicroArgs M, const double* __restrict__ Zw, const F* __restrict__ invD, const F* __restrict__ r,
             F* __restrict__ x, const F* __restrict__ xcorner, int pass)
 {
+    const double* __restrict__ iZw = Zw + 4 * kMaxBcs;          // reciprocals of the wall normalisations
     __shared__ F slots[2 * 4 * 4];
     extern __shared__ double xsm_raw[];
     F* xsm = reinterpret_cast<F*>(xsm_raw);  // [2][nloc] current cell values of this CTA's velocities
@@ -228,13 +240,40 @@ k_sgs_chain(MicroArgs M, const double* __restrict__ Zw, const F* __restrict__ in
     }
     F xprev[kChainKpt][2];
     const int len = line == 0 ? ny : nx;
+    auto cell_of = [&](int st, int& ci, int& cj) {
+        if (pass == 0) { ci = line == 0 ? 0 : st; cj = line == 0 ? st : 0; }
+        else { ci = line == 0 ? nx - 1 : nx - 1 - st; cj = line == 0 ? ny - 1 - st : ny - 1; }
+    };
+    // per-velocity inputs of the current and the next cell (prefetched one step ahead)
+    F cin[kChainKpt][2], cdi[kChainKpt], nin[kChainKpt][2], ndi[kChainKpt];
+    double citau = 0.0, nitau = 0.0;
+    auto load = [&](int st, F (&in)[kChainKpt][2], F (&di)[kChainKpt], double& it) {
+        int ci, cj;
+        cell_of(st, ci, cj);
+        const int cc = cj * nx + ci;
+        it = M.inv_tau[cc];
+        #pragma unroll
+        for (int t = 0; t < kChainKpt; ++t) {
+            int k = kk[t];
+            if (k < 0) continue;
+            di[t] = invD[(size_t)cc * nv + k];
+            #pragma unroll
+            for (int cp = 0; cp < 2; ++cp) {
+                size_t id = (cp * nc + cc) * nv + k;
+                // backward: the corner's forward value comes from a copy taken before the
+                // launch, because the column line overwrites the corner while the row line reads it
+                in[t][cp] = pass == 0 ? r[id] : (st == 0 ? xcorner[cp * nv + k] : x[id]);
+            }
+        }
+    };
+    load(0, cin, cdi, citau);
     for (int s = 0; s < len; ++s) {
+        if (s + 1 < len) load(s + 1, nin, ndi, nitau);
         // cell of this step
         int i, j;
-        if (pass == 0) { i = line == 0 ? 0 : s; j = line == 0 ? s : 0; }
-        else { i = line == 0 ? nx - 1 : nx - 1 - s; j = line == 0 ? ny - 1 - s : ny - 1; }
+        cell_of(s, i, j);
         const int c = j * nx + i;
-        const F itau = (F)M.inv_tau[c];
+        const F itau = (F)citau;
         // interior neighbour along the line (the previous cell), if any
         int nb_axis = line == 0 ? 1 : 0, nb_sign = pass == 0 ? -1 : 1;
         const F nbS = (F)(nb_axis == 0 ? L.rdx[i] : L.rdy[j]);
@@ -264,16 +303,12 @@ k_sgs_chain(MicroArgs M, const double* __restrict__ Zw, const F* __restrict__ in
                     if (M.bc[bf[b].bc].type == BC_OUTFLOW) dd += Dface<F>(bf[b].axis, bf[b].outsign, (F)bf[b].rS, u, v);
                 den[t] = recip(dd);
             } else {
-                den[t] = invD[(size_t)c * nv + k];
+                den[t] = cdi[t];
             }
             #pragma unroll
             for (int cp = 0; cp < 2; ++cp) {
                 F y = s > 0 ? Dn * xprev[t][cp] : F(0);
-                size_t id = (cp * nc + c) * nv + k;
-                // backward: the corner's forward value comes from a copy taken before the
-                // launch, because the column line overwrites the corner while the row line reads it
-                F xs = pass == 0 ? F(0) : (s == 0 ? xcorner[cp * nv + k] : x[id]);
-                base[t][cp] = pass == 0 ? r[id] - y : D * xs - y;
+                base[t][cp] = pass == 0 ? cin[t][cp] - y : D * cin[t][cp] - y;
                 xc[t][cp] = base[t][cp] * den[t];
             }
         }
@@ -344,7 +379,7 @@ k_sgs_chain(MicroArgs M, const double* __restrict__ Zw, const F* __restrict__ in
                         if (uo > F(0)) acc[0] += (F)Vg.w[k] * uo * xc[t][0];
                     }
                     cluster_sum<F, 1>(cl, acc, slots, ev);
-                    rho = (F)(-(double)acc[0] / Zw[bf[wb].bc * 4 + bf[wb].axis * 2 + (bf[wb].outsign > 0)]);
+                    rho = -acc[0] * (F)iZw[bf[wb].bc * 4 + bf[wb].axis * 2 + (bf[wb].outsign > 0)];
                 }
                 F xn[kChainKpt][2];
                 #pragma unroll
@@ -385,50 +420,105 @@ k_sgs_chain(MicroArgs M, const double* __restrict__ Zw, const F* __restrict__ in
                 x[c * (size_t)nv + k] = xc[t][0];
                 x[(nc + c) * (size_t)nv + k] = xc[t][1];
             }
+            cin[t][0] = nin[t][0];
+            cin[t][1] = nin[t][1];
+            cdi[t] = ndi[t];
         }
+        citau = nitau;
     }
     cl.sync();   // keep every CTA's shared memory alive until all remote reads are done
 }
 
-template <typename F>
+// Interior cells of one sweep for the kInteriorKc velocities of this CTA, in
+// anti-diagonal order.  Values of the previous diagonal stay in shared memory
+// (indexed by the x-index of the cell); the residual (forward) or forward
+// value (backward) and 1/D of the next diagonal are loaded while the current
+// one is computed.  EPT: elements (cell, component, velocity) per thread and
+// diagonal.
+template <typename F, int EPT>
 __global__ void __launch_bounds__(128) k_sgs_interior(MicroArgs M, const F* __restrict__ invD,
                                                       const F* __restrict__ r, F* __restrict__ x, int pass)
 {
+    extern __shared__ double sraw[];
     const LevelDev& L = M.L;
     const VelDev& Vg = M.V;
     const int nx = L.nx, ny = L.ny, nv = Vg.nv;
     const size_t nc = L.nc;
     const int k0 = blockIdx.x * kInteriorKc;
-    // interior region: forward i >= 1, j >= 1; backward i <= nx-2, j <= ny-2
+    constexpr int W = 2 * kInteriorKc;                  // elements per cell
+    F* sx = reinterpret_cast<F*>(sraw);                 // [2][nx][W] values of the previous diagonal
+    F* scol = sx + 2 * (size_t)nx * W;                  // [ny][W] boundary column next to the region
+    F* srow = scol + (size_t)ny * W;                    // [nx][W] boundary row next to the region
     const int ilo0 = pass == 0 ? 1 : 0, ihi0 = pass == 0 ? nx - 1 : nx - 2;
     const int jlo0 = pass == 0 ? 1 : 0, jhi0 = pass == 0 ? ny - 1 : ny - 2;
     if (ihi0 < ilo0 || jhi0 < jlo0) return;
-    const int dlo = ilo0 + jlo0, dhi = ihi0 + jhi0;
-    for (int dd = 0; dd <= dhi - dlo; ++dd) {
-        int d = pass == 0 ? dlo + dd : dhi - dd;
-        int ilo = max(ilo0, d - jhi0), ihi = min(ihi0, d - jlo0);
-        int nel = (ihi - ilo + 1) * kInteriorKc * 2;
-        for (int e = threadIdx.x; e < nel; e += blockDim.x) {
-            int slot = e / (2 * kInteriorKc), rem = e - slot * 2 * kInteriorKc;
-            int cp = rem / kInteriorKc, k = k0 + rem - cp * kInteriorKc;
+    const int dlo = ilo0 + jlo0, dhi = ihi0 + jhi0, nd = dhi - dlo + 1;
+    {   // the boundary lines were finished by the chain kernel: stage them once
+        const int ib = pass == 0 ? 0 : nx - 1, jb = pass == 0 ? 0 : ny - 1;
+        for (int e = threadIdx.x; e < (nx + ny) * W; e += blockDim.x) {
+            int cellk = e / W, rem = e - cellk * W, cp = rem / kInteriorKc, k = k0 + rem - cp * kInteriorKc;
             if (k >= nv) continue;
-            int i = ilo + slot, j = d - i;
-            int c = j * nx + i;
+            if (cellk < ny) scol[cellk * W + rem] = x[(cp * nc + (size_t)cellk * nx + ib) * nv + k];
+            else srow[(cellk - ny) * W + rem] = x[(cp * nc + (size_t)jb * nx + (cellk - ny)) * nv + k];
+        }
+        __syncthreads();
+    }
+    auto diag = [&](int dd) { return pass == 0 ? dlo + dd : dhi - dd; };
+    auto bounds = [&](int d, int& ilo, int& ihi) { ilo = max(ilo0, d - jhi0); ihi = min(ihi0, d - jlo0); };
+    F cr[EPT], ci[EPT], nr[EPT], ni[EPT];
+    auto load = [&](int dd, F (&rv)[EPT], F (&iv)[EPT]) {
+        int d = diag(dd), ilo, ihi;
+        bounds(d, ilo, ihi);
+        const int nel = (ihi - ilo + 1) * W;
+        #pragma unroll
+        for (int m = 0; m < EPT; ++m) {
+            int e = threadIdx.x + m * blockDim.x;
+            int slot = e / W, rem = e - slot * W, cp = rem / kInteriorKc, k = k0 + rem - cp * kInteriorKc;
+            if (e < nel && k < nv) {
+                int i = ilo + slot, c = (d - i) * nx + i;
+                size_t id = (size_t)c * nv + k;
+                rv[m] = pass == 0 ? r[cp * nc * nv + id] : x[cp * nc * nv + id];
+                iv[m] = invD[id];
+            }
+        }
+    };
+    load(0, cr, ci);
+    for (int dd = 0; dd < nd; ++dd) {
+        if (dd + 1 < nd) load(dd + 1, nr, ni);
+        const int d = diag(dd);
+        int ilo, ihi;
+        bounds(d, ilo, ihi);
+        const int nel = (ihi - ilo + 1) * W;
+        F* prev = sx + (size_t)((dd + 1) & 1) * nx * W;
+        F* cur = sx + (size_t)(dd & 1) * nx * W;
+        #pragma unroll
+        for (int m = 0; m < EPT; ++m) {
+            int e = threadIdx.x + m * blockDim.x;
+            int slot = e / W, rem = e - slot * W, cp = rem / kInteriorKc, kk = rem - cp * kInteriorKc, k = k0 + kk;
+            if (e >= nel || k >= nv) continue;
+            int i = ilo + slot, j = d - i, c = j * nx + i;
             const F u = (F)Vg.u[k], v = (F)Vg.v[k];
             const F idx = (F)L.rdx[i], idy = (F)L.rdy[j];
             F* xb = x + cp * nc * nv;
             size_t id = (size_t)c * nv + k;
+            F res;
             if (pass == 0) {
                 F dW = u > F(0) ? -u * idx : F(0), dS = v > F(0) ? -v * idy : F(0);
-                F base = r[cp * nc * nv + id] - dW * xb[id - nv] - dS * xb[id - (size_t)nx * nv];
-                xb[id] = base * invD[id];
+                F xW = (i - 1 >= ilo0) ? prev[(i - 1) * W + cp * kInteriorKc + kk] : scol[j * W + cp * kInteriorKc + kk];
+                F xS = (j - 1 >= jlo0) ? prev[i * W + cp * kInteriorKc + kk] : srow[i * W + cp * kInteriorKc + kk];
+                res = (cr[m] - dW * xW - dS * xS) * ci[m];
             } else {
                 F dE = u < F(0) ? u * idx : F(0), dN = v < F(0) ? v * idy : F(0);
-                F y = dE * xb[id + nv] + dN * xb[id + (size_t)nx * nv];
-                xb[id] = xb[id] - y * invD[id];
+                F xE = (i + 1 <= ihi0) ? prev[(i + 1) * W + cp * kInteriorKc + kk] : scol[j * W + cp * kInteriorKc + kk];
+                F xN = (j + 1 <= jhi0) ? prev[i * W + cp * kInteriorKc + kk] : srow[i * W + cp * kInteriorKc + kk];
+                res = cr[m] - (dE * xE + dN * xN) * ci[m];
             }
+            xb[id] = res;
+            cur[i * W + cp * kInteriorKc + kk] = res;
         }
         __syncthreads();
+        #pragma unroll
+        for (int m = 0; m < EPT; ++m) { cr[m] = nr[m]; ci[m] = ni[m]; }
     }
 }
 
@@ -460,7 +550,13 @@ cudaError_t launch_micro_sgs(const MicroArgs& m, const double* Zw, const F* invD
         chain<<<2 * kChainCluster, kChainThreads, smem, st>>>(m, Zw, invD, r, x, xcorner, pass);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        k_sgs_interior<F><<<nblk_int, 128, 0, st>>>(m, invD, r, x, pass);
+        const int maxdiag = m.L.nx < m.L.ny ? m.L.nx : m.L.ny;
+        const int ept = (maxdiag * 2 * kInteriorKc + 127) / 128;
+        const size_t ismem = sizeof(F) * (2 * (size_t)m.L.nx + m.L.nx + m.L.ny) * 2 * kInteriorKc;
+        if (ept <= 4) k_sgs_interior<F, 4><<<nblk_int, 128, ismem, st>>>(m, invD, r, x, pass);
+        else if (ept <= 8) k_sgs_interior<F, 8><<<nblk_int, 128, ismem, st>>>(m, invD, r, x, pass);
+        else if (ept <= 16) k_sgs_interior<F, 16><<<nblk_int, 128, ismem, st>>>(m, invD, r, x, pass);
+        else return cudaErrorInvalidValue;
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -573,20 +669,19 @@ __global__ void __launch_bounds__(256) k_update_moments(LevelDev L, VelDev Vg, F
         sa[0].add(w * g); sa[1].add(w * u * g); sa[2].add(w * v * g);
         sa[3].add(w * (F(0.5) * (u * u + v * v) * g + h));
     }
-    double s[4] = {sa[0].value(), sa[1].value(), sa[2].value(), sa[3].value()};
-    block_sum<4>(s, red);
-    double rho, U, V, lam;
-    prim4(s, rho, U, V, lam);
+    double s[4];
+    block_total<4>(sa, red, s);
+    const double ir = rcp64(s[0]);
+    const F fU = (F)(s[1] * ir), fV = (F)(s[2] * ir);
     Acc<F> ta[2];
-    const F fU = (F)U, fV = (F)V;
     for (int k = threadIdx.x; k < nv; k += blockDim.x) {
         F cx = (F)Vg.u[k] - fU, cy = (F)Vg.v[k] - fV;
         F e = F(0.5) * (cx * cx + cy * cy) * fG[k] + fH[k];
         ta[0].add((F)Vg.w[k] * cx * e);
         ta[1].add((F)Vg.w[k] * cy * e);
     }
-    double t[2] = {ta[0].value(), ta[1].value()};
-    block_sum<2>(t, red);
+    double t[2];
+    block_total<2>(ta, red, t);
     if (threadIdx.x == 0) {
         for (int m = 0; m < 4; ++m) W[4 * (size_t)c + m] = s[m];
         q[2 * (size_t)c] = t[0];

@@ -59,6 +59,12 @@ struct miugks_solver {
     bool initialised = false;
     bool timing = false;
     cudaEvent_t ev[6] = {};
+    // one outer iteration captured as a CUDA graph (replayed while the launch
+    // sequence and its arguments do not change)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    bool graph_ok = true;
+    int eager_done = 0;
     double t_flux = 0, t_sweep = 0, t_total = 0;
 };
 
@@ -155,9 +161,11 @@ void refresh_bc_tables(miugks_solver* s, int b)
     for (int k = 0; k < s->nv; ++k) s->Cwh[(size_t)b * s->nv + k] = maxwell_unit(B.u, B.v, B.t, s->uh[k], s->vh[k]);
 }
 
+// Z[b*4 + axis*2 + (outward normal positive)] = sum over incoming velocities of w u_n C_k,
+// followed by the reciprocals (at offset 4 * kMaxBcs)
 std::vector<double> wall_norms(miugks_solver* s)
 {
-    std::vector<double> Zh((size_t)s->nbc * 4, 0.0);
+    std::vector<double> Zh((size_t)kMaxBcs * 8, 0.0);
     for (int b = 0; b < s->nbc; ++b)
         for (int k = 0; k < s->nv; ++k) {
             double C = s->Cwh[(size_t)b * s->nv + k];
@@ -167,6 +175,7 @@ std::vector<double> wall_norms(miugks_solver* s)
                     if (uo < 0) Zh[(size_t)b * 4 + axis * 2 + pos] += s->wh[k] * uo * C;
                 }
         }
+    for (int q = 0; q < 4 * s->nbc; ++q) Zh[4 * kMaxBcs + q] = Zh[q] != 0.0 ? 1.0 / Zh[q] : 0.0;
     return Zh;
 }
 
@@ -330,7 +339,6 @@ miugks_status one_iteration_t(miugks_solver* s)
     if (s->timing) CK(cudaEventRecord(s->ev[3], s->st));
     CK(launch_update_moments<F>(L0.dev, s->vel, (F*)s->f, (const F*)L0.df, s->W, s->q, s->st));   // Steps 6-7
     if (s->timing) CK(cudaEventRecord(s->ev[4], s->st));
-    s->iter++;
     return MIUGKS_OK;
 }
 
@@ -428,6 +436,8 @@ void miugks_destroy(miugks_solver* s)
     }
     for (auto& e : s->ev)
         if (e) cudaEventDestroy(e);
+    if (s->gexec) cudaGraphExecDestroy(s->gexec);
+    if (s->graph) cudaGraphDestroy(s->graph);
     delete s;
 }
 
@@ -479,6 +489,7 @@ miugks_status miugks_create(const miugks_mesh* mesh, const miugks_vgrid* vg, con
         if (!(gas->kn > 0) || !(gas->pr > 0)) { st = bad("Kn and Pr must be positive"); break; }
         s->gas = GasDev{15.0 * std::sqrt(kPi) * gas->kn / (2.0 * (5.0 - 2.0 * gas->omega) * (7.0 - 2.0 * gas->omega)),
                         gas->omega, gas->pr};
+        if (n_bcs > kMaxBcs) { st = bad("at most %d boundary conditions", kMaxBcs); break; }
         s->nbc = n_bcs;
         s->bch.resize(n_bcs);
         for (int b = 0; b < n_bcs; ++b) {
@@ -641,24 +652,75 @@ miugks_status miugks_init_uniform(miugks_solver* s, double rho, double u, double
     return miugks_init_fields(s, a.data(), b.data(), c.data(), d.data());
 }
 
+// Enqueue n outer iterations on the solver's stream without waiting.  After one
+// eager iteration (which also performs the one-time kernel attribute set-up)
+// an iteration is captured into a CUDA graph and replayed: one graph launch per
+// iteration instead of a hundred kernel launches.  Stage timing, the numerical
+// time step (whose value changes every iteration) and the legacy default
+// stream (which cannot be captured) keep the eager path.
+static miugks_status enqueue_iterations(miugks_solver* s, int n_iter)
+{
+    for (int it = 0; it < n_iter; ++it) {
+        bool graphable = s->graph_ok && !s->timing && s->st != nullptr && !(s->opts.dtn_growth > 0.0) &&
+                         s->eager_done > 0;
+        if (graphable && !s->gexec) {
+            cudaError_t e = cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal);
+            miugks_status st = e == cudaSuccess ? one_iteration(s) : MIUGKS_ECUDA;
+            cudaGraph_t g = nullptr;
+            cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(s->st, &g) : e;
+            if (st == MIUGKS_OK && e2 == cudaSuccess && g &&
+                cudaGraphInstantiate(&s->gexec, g, 0) == cudaSuccess) {
+                s->graph = g;
+            } else {
+                // capture unsupported here: run eagerly from now on
+                if (g) cudaGraphDestroy(g);
+                s->gexec = nullptr;
+                s->graph_ok = false;
+                cudaGetLastError();
+                graphable = false;
+            }
+        }
+        if (graphable) {
+            CK(cudaGraphLaunch(s->gexec, s->st));
+        } else {
+            ST(one_iteration(s));
+            s->eager_done++;
+            if (s->timing) {
+                CK(cudaEventSynchronize(s->ev[4]));
+                float a = 0, b = 0, c = 0;
+                CK(cudaEventElapsedTime(&a, s->ev[0], s->ev[1]));
+                CK(cudaEventElapsedTime(&b, s->ev[2], s->ev[3]));
+                CK(cudaEventElapsedTime(&c, s->ev[0], s->ev[4]));
+                s->t_flux += a; s->t_sweep += b; s->t_total += c;
+            }
+        }
+        s->iter++;
+    }
+    return MIUGKS_OK;
+}
+
 miugks_status miugks_step(miugks_solver* s, int n_iter, double res_out[4])
 {
     if (!s) return MIUGKS_EINVAL;
     if (!s->initialised) return fail(s, MIUGKS_ESTATE, "step before init");
     if (n_iter < 0) return fail(s, MIUGKS_EINVAL, "n_iter < 0");
-    for (int it = 0; it < n_iter; ++it) {
-        ST(one_iteration(s));
-        if (s->timing) {
-            CK(cudaEventSynchronize(s->ev[4]));
-            float a = 0, b = 0, c = 0;
-            CK(cudaEventElapsedTime(&a, s->ev[0], s->ev[1]));
-            CK(cudaEventElapsedTime(&b, s->ev[2], s->ev[3]));
-            CK(cudaEventElapsedTime(&c, s->ev[0], s->ev[4]));
-            s->t_flux += a; s->t_sweep += b; s->t_total += c;
-        }
-    }
+    ST(enqueue_iterations(s, n_iter));
     if (n_iter > 0) return read_residual(s, res_out);
     return MIUGKS_OK;
+}
+
+miugks_status miugks_step_async(miugks_solver* s, int n_iter)
+{
+    if (!s) return MIUGKS_EINVAL;
+    if (!s->initialised) return fail(s, MIUGKS_ESTATE, "step before init");
+    if (n_iter < 0) return fail(s, MIUGKS_EINVAL, "n_iter < 0");
+    return enqueue_iterations(s, n_iter);
+}
+
+miugks_status miugks_wait(miugks_solver* s, double res_out[4])
+{
+    if (!s) return MIUGKS_EINVAL;
+    return read_residual(s, res_out);
 }
 
 miugks_status miugks_run(miugks_solver* s, double tol, int max_iter, int* iters_out, double res_out[4])

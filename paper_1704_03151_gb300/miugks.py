@@ -83,6 +83,7 @@ def load():
         "miugks_stage_resid_macro": [vp, _i, vp, vp, vp], "miugks_stage_restrict": [vp, _i, _i, vp, vp],
         "miugks_stage_prolong": [vp, _i, _i, vp, vp], "miugks_sizes": [vp, _P(_i), _P(_i), _P(_i), _P(_i)],
         "miugks_set_timing": [vp, _i], "miugks_kernel_times": [vp, _P(_d), _P(_d), _P(_d)],
+        "miugks_step_async": [vp, _i], "miugks_wait": [vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -102,7 +103,7 @@ def exported_symbols():
             "miugks_get_f", "miugks_set_f", "miugks_get_wall", "miugks_set_bc", "miugks_stage_flux",
             "miugks_stage_sgs_micro", "miugks_stage_apply_micro", "miugks_stage_sgs_macro",
             "miugks_stage_resid_macro", "miugks_stage_restrict", "miugks_stage_prolong", "miugks_sizes",
-            "miugks_set_timing", "miugks_kernel_times"]
+            "miugks_set_timing", "miugks_kernel_times", "miugks_step_async", "miugks_wait"]
 
 
 def _ptr(a):
@@ -202,6 +203,14 @@ class Solver:
     def step(self, n=1):
         res = np.zeros(4)
         self._check(self._lib.miugks_step(self.h, n, _ptr(res)))
+        return res
+
+    def step_async(self, n=1):
+        self._check(self._lib.miugks_step_async(self.h, n))
+
+    def wait(self):
+        res = np.zeros(4)
+        self._check(self._lib.miugks_wait(self.h, _ptr(res)))
         return res
 
     def run(self, tol, max_iter):
