@@ -214,6 +214,147 @@ __device__ __forceinline__ void cluster_sum(cg::cluster_group& cl, T (&v)[NR], T
     ++ev;
 }
 
+constexpr int kMaxLine = 512;          // longest boundary line (cells) of the chain kernel
+
+// Cells 1.. of a boundary line (after the corner), given the corner values in
+// xprev.  Every such cell has one boundary face on the sweep side, with a
+// fixed orientation along the line, so velocities split into
+//   outgoing (u_n >= 0 at that face): no ghost term, a recurrence along the
+//     line per velocity (phase A; their wall sums are reduced per cell inside
+//     each warp as they are produced);
+//   incoming (u_n < 0): the ghost term needs the cell's wall density, i.e. a
+//     sum over its outgoing velocities (phase B: all cells at once, one
+//     cluster exchange), or the mirrored outgoing value (symmetry); then the
+//     recurrence along the line (phase C).
+// The arithmetic per cell is that of the serial sweep; only the order in which
+// independent velocities are visited changes.
+template <typename F, int kChainKpt>
+__device__ void chain_rest(cg::cluster_group& cl, const MicroArgs& M, const double* __restrict__ iZw,
+                           const F* __restrict__ invD, const F* __restrict__ r, F* __restrict__ x, int pass,
+                           int line, int len, const int (&kk)[kChainKpt], const int (&mu)[kChainKpt],
+                           F (&xprev)[kChainKpt][2])
+{
+    __shared__ F part[kMaxLine * 4];          // [cell][warp] partial wall sums of this CTA
+    __shared__ F rho_s[kMaxLine];
+    const LevelDev& L = M.L;
+    const VelDev& Vg = M.V;
+    const int nx = L.nx, ny = L.ny, nv = Vg.nv;
+    const size_t nc = L.nc;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nb_axis = line == 0 ? 1 : 0, nb_sign = pass == 0 ? -1 : 1;
+    // orientation of the line's boundary face (column lines: x-faces, row lines: y-faces)
+    const int f_axis = line == 0 ? 0 : 1, f_out = pass == 0 ? -1 : 1;
+    auto cell = [&](int st, int& i, int& j) {
+        if (pass == 0) { i = line == 0 ? 0 : st; j = line == 0 ? st : 0; }
+        else { i = line == 0 ? nx - 1 : nx - 1 - st; j = line == 0 ? ny - 1 - st : ny - 1; }
+    };
+    auto face_bc = [&](int i, int j) {
+        return f_axis == 0 ? L.fbx[j * (nx + 1) + (f_out < 0 ? 0 : nx)] : L.fby[(f_out < 0 ? 0 : ny) * nx + i];
+    };
+    F uo_t[kChainKpt];
+    #pragma unroll
+    for (int t = 0; t < kChainKpt; ++t) {
+        int k = kk[t];
+        F un = k < 0 ? F(0) : (F)(f_axis == 0 ? Vg.u[k] : Vg.v[k]);
+        uo_t[t] = f_out < 0 ? -un : un;
+    }
+    // ---- phase A: outgoing velocities
+    {
+        F xp[kChainKpt][2];
+        #pragma unroll
+        for (int t = 0; t < kChainKpt; ++t) { xp[t][0] = xprev[t][0]; xp[t][1] = xprev[t][1]; }
+        for (int st = 1; st < len; ++st) {
+            int i, j;
+            cell(st, i, j);
+            const int c = j * nx + i;
+            const int bc = face_bc(i, j);
+            const int bt = M.bc[bc].type;
+            const F nbS = (F)(nb_axis == 0 ? L.rdx[i] : L.rdy[j]);
+            const F itau = (F)M.inv_tau[c];
+            F part_w = F(0);
+            #pragma unroll
+            for (int t = 0; t < kChainKpt; ++t) {
+                int k = kk[t];
+                if (k < 0 || uo_t[t] < F(0)) continue;
+                const F u = (F)Vg.u[k], v = (F)Vg.v[k];
+                const F Dn = Dface<F>(nb_axis, nb_sign, nbS, u, v);
+                const F id = invD[(size_t)c * nv + k];
+                const F D = pass == 1 ? itau + geomD<F>(L, i, j, u, v) : F(0);
+                #pragma unroll
+                for (int cp = 0; cp < 2; ++cp) {
+                    size_t idx = (cp * nc + c) * nv + k;
+                    F base = pass == 0 ? r[idx] - Dn * xp[t][cp] : D * x[idx] - Dn * xp[t][cp];
+                    F xv = base * id;
+                    x[idx] = xv;
+                    xp[t][cp] = xv;
+                }
+                if (bt == BC_WALL && uo_t[t] > F(0)) part_w += (F)Vg.w[k] * uo_t[t] * xp[t][0];
+            }
+            #pragma unroll
+            for (int o = 16; o > 0; o >>= 1) part_w += __shfl_xor_sync(0xffffffffu, part_w, o);
+            if (lane == 0) part[st * 4 + warp] = part_w;
+        }
+    }
+    cl.sync();
+    // ---- phase B: wall density of every cell of the line (fixed summation order)
+    for (int st = 1 + threadIdx.x; st < len; st += blockDim.x) {
+        int i, j;
+        cell(st, i, j);
+        const int bc = face_bc(i, j);
+        F rho = F(0);
+        if (M.bc[bc].type == BC_WALL) {
+            F sum = F(0);
+            for (int rk = 0; rk < kChainCluster; ++rk) {
+                const F* pr = cl.map_shared_rank(part, rk);
+                for (int w = 0; w < 4; ++w) sum += pr[st * 4 + w];
+            }
+            rho = -sum * (F)iZw[bc * 4 + f_axis * 2 + (f_out > 0)];
+        }
+        rho_s[st] = rho;
+    }
+    __syncthreads();
+    // ---- phase C: incoming velocities
+    for (int st = 1; st < len; ++st) {
+        int i, j;
+        cell(st, i, j);
+        const int c = j * nx + i;
+        const int bc = face_bc(i, j);
+        const BcDev B = M.bc[bc];
+        const F nbS = (F)(nb_axis == 0 ? L.rdx[i] : L.rdy[j]);
+        const F fS = (F)(f_axis == 0 ? L.rdx[i] : L.rdy[j]);
+        const F itau = (F)M.inv_tau[c];
+        const F rho = rho_s[st];
+        #pragma unroll
+        for (int t = 0; t < kChainKpt; ++t) {
+            int k = kk[t];
+            if (k < 0 || !(uo_t[t] < F(0))) continue;
+            const F u = (F)Vg.u[k], v = (F)Vg.v[k];
+            const F Dn = Dface<F>(nb_axis, nb_sign, nbS, u, v);
+            const F Db = uo_t[t] * fS;                               // (1/V) u_n S, u_n < 0
+            F D = F(0);
+            if (pass == 1 || B.type == BC_OUTFLOW) D = itau + geomD<F>(L, i, j, u, v);
+            const F id = B.type == BC_OUTFLOW ? recip(D + Db) : invD[(size_t)c * nv + k];
+            const int km = f_axis == 0 ? mu[t] : -1;
+            #pragma unroll
+            for (int cp = 0; cp < 2; ++cp) {
+                size_t idx = (cp * nc + c) * nv + k;
+                F base = pass == 0 ? r[idx] - Dn * xprev[t][cp] : D * x[idx] - Dn * xprev[t][cp];
+                if (B.type == BC_WALL) {
+                    base -= Db * (F)(M.Cw[(size_t)bc * nv + k] * (cp == 0 ? 1.0 : kKint * B.t / 4.0)) * rho;
+                } else if (B.type == BC_SYMMETRY) {
+                    int a2 = k / Vg.nvv, b2 = k - a2 * Vg.nvv;
+                    int kmir = f_axis == 0 ? (Vg.nu - 1 - a2) * Vg.nvv + b2 : a2 * Vg.nvv + (Vg.nvv - 1 - b2);
+                    base -= Db * x[(cp * nc + c) * nv + kmir];
+                }
+                (void)km;
+                F xv = base * id;
+                x[idx] = xv;
+                xprev[t][cp] = xv;
+            }
+        }
+    }
+}
+
 template <typename F, int kChainKpt>
 __global__ void __cluster_dims__(kChainCluster, 1, 1) __launch_bounds__(kChainThreads)
 k_sgs_chain(MicroArgs M, const double* __restrict__ Zw, const F* __restrict__ invD, const F* __restrict__ r,
@@ -267,8 +408,8 @@ k_sgs_chain(MicroArgs M, const double* __restrict__ Zw, const F* __restrict__ in
         }
     };
     load(0, cin, cdi, citau);
-    for (int s = 0; s < len; ++s) {
-        if (s + 1 < len) load(s + 1, nin, ndi, nitau);
+    for (int s = 0; s < 1; ++s) {   // the corner cell; the rest of the line follows in three phases
+        (void)nin; (void)ndi; (void)nitau;
         // cell of this step
         int i, j;
         cell_of(s, i, j);
@@ -420,12 +561,9 @@ k_sgs_chain(MicroArgs M, const double* __restrict__ Zw, const F* __restrict__ in
                 x[c * (size_t)nv + k] = xc[t][0];
                 x[(nc + c) * (size_t)nv + k] = xc[t][1];
             }
-            cin[t][0] = nin[t][0];
-            cin[t][1] = nin[t][1];
-            cdi[t] = ndi[t];
         }
-        citau = nitau;
     }
+    if (len > 1) chain_rest<F, kChainKpt>(cl, M, iZw, invD, r, x, pass, line, len, kk, mu, xprev);
     cl.sync();   // keep every CTA's shared memory alive until all remote reads are done
 }
 
@@ -529,6 +667,7 @@ cudaError_t launch_micro_sgs(const MicroArgs& m, const double* Zw, const F* invD
     const int ngroups = (m.V.nu + 1) / 2;
     const int nloc = ((ngroups + kChainCluster - 1) / kChainCluster) * 2 * m.V.nvv;
     if (nloc > kChainKptMax * kChainThreads) return cudaErrorInvalidValue;
+    if (m.L.nx > kMaxLine || m.L.ny > kMaxLine) return cudaErrorInvalidValue;
     size_t smem = sizeof(F) * 2 * nloc;
     const int kpt = (nloc + kChainThreads - 1) / kChainThreads;
     void (*chain)(MicroArgs, const double*, const F*, const F*, F*, const F*, int) =

@@ -549,6 +549,8 @@ miugks_status miugks_create(const miugks_mesh* mesh, const miugks_vgrid* vg, con
             level_geometry(C);
         }
         if (st != MIUGKS_OK) break;
+        if (mesh->nx > 512 || mesh->ny > 512) { st = bad("nx and ny are limited to 512"); break; }
+        if (mesh->nx > 512 || mesh->ny > 512) { st = bad("nx and ny are limited to 512"); break; }
         // chain kernel capacity: velocities per CTA of the 8-CTA cluster
         int nloc = (((s->nu + 1) / 2 + 7) / 8) * 2 * s->nvv;
         if (nloc > 8 * 256) { st = bad("velocity grid too large for the boundary-line kernel (%d local > 2048)", nloc); break; }
