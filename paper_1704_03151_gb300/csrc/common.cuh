@@ -13,6 +13,7 @@ constexpr int kKint = 1;                       // internal degrees of freedom
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kMaxLevels = 8;
 constexpr int kMaxBcs = 64;                    // boundary conditions per solver
+constexpr int kMaxLine = 512;                  // longest grid line (cells) of the micro sweep kernels
 
 enum BcType { BC_WALL = 0, BC_SYMMETRY = 1, BC_FARFIELD = 2, BC_OUTFLOW = 3 };
 

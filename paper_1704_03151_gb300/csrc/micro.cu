@@ -12,15 +12,18 @@
 // couples the incoming velocities of a cell to a sum over its outgoing ones.
 // On the lower side (forward sweep) the boundary cells form two lines, the
 // first column and the first row, and each line only depends on itself; the
-// same holds for the last column and row in the backward sweep.  Each sweep is
-// therefore two launches:
-//   * k_sgs_chain: one thread-block cluster per boundary line walks the line
-//     cell by cell; the velocities of a cell are spread over the CTAs of the
-//     cluster and the wall sums are combined through distributed shared
-//     memory with a hardware cluster barrier;
-//   * k_sgs_interior: every CTA owns a contiguous chunk of discrete
-//     velocities and sweeps the remaining cells diagonal by diagonal, with only
-//     __syncthreads between diagonals (no grid-wide synchronisation).
+// same holds for the last column and row in the backward sweep.  At a line
+// cell, the velocities leaving through the boundary face (outgoing) need no
+// ghost, and the incoming ones need only the cell's wall density, a sum over
+// the outgoing ones.  Each sweep is therefore two launches:
+//   * k_sgs_chain: one thread-block cluster per boundary line solves the
+//     corner cell, then every outgoing velocity along the line, then the wall
+//     density of every line cell (partial sums combined through distributed
+//     shared memory with one hardware cluster barrier);
+//   * k_sgs_wave: every CTA owns a contiguous chunk of discrete velocities and
+//     sweeps all cells diagonal by diagonal, with only __syncthreads between
+//     diagonals (no grid-wide synchronisation); the incoming velocities of
+//     line cells are ordinary updates there, their ghost term being known.
 #include "kernels.cuh"
 
 namespace cg = cooperative_groups;
@@ -30,7 +33,7 @@ namespace miugks {
 constexpr int kChainCluster = 8;
 constexpr int kChainThreads = 128;    // 4 warps: one per SM sub-partition
 constexpr int kChainKptMax = 16;      // local velocities per thread in the chain kernel (at most)
-constexpr int kInteriorKc = 4;        // velocities per CTA in the interior kernel
+constexpr int kInteriorKc = 4;        // velocities per CTA in the wavefront kernel
 
 // (1/V) sum over the faces with u_n > 0 of u_n S = |u|/dx + |v|/dy
 template <typename F>
@@ -214,7 +217,6 @@ __device__ __forceinline__ void cluster_sum(cg::cluster_group& cl, T (&v)[NR], T
     ++ev;
 }
 
-constexpr int kMaxLine = 512;          // longest boundary line (cells) of the chain kernel
 
 // Cells 1.. of a boundary line (after the corner), given the corner values in
 // xprev.  Every such cell has one boundary face on the sweep side, with a
@@ -222,17 +224,18 @@ constexpr int kMaxLine = 512;          // longest boundary line (cells) of the c
 //   outgoing (u_n >= 0 at that face): no ghost term, a recurrence along the
 //     line per velocity (phase A; their wall sums are reduced per cell inside
 //     each warp as they are produced);
-//   incoming (u_n < 0): the ghost term needs the cell's wall density, i.e. a
-//     sum over its outgoing velocities (phase B: all cells at once, one
-//     cluster exchange), or the mirrored outgoing value (symmetry); then the
-//     recurrence along the line (phase C).
+//   incoming (u_n < 0): the ghost term needs the cell's wall density, a sum
+//     over its outgoing velocities (phase B: all cells at once, one cluster
+//     exchange, published in rho_out), or the mirrored outgoing value
+//     (symmetry).  With the ghost known, an incoming velocity of a line cell
+//     is an ordinary cell update, done by the wavefront kernel.
 // The arithmetic per cell is that of the serial sweep; only the order in which
 // independent velocities are visited changes.
 template <typename F, int kChainKpt>
 __device__ void chain_rest(cg::cluster_group& cl, const MicroArgs& M, const double* __restrict__ iZw,
                            const F* __restrict__ invD, const F* __restrict__ r, F* __restrict__ x, int pass,
                            int line, int len, const int (&kk)[kChainKpt], const int (&mu)[kChainKpt],
-                           F (&xprev)[kChainKpt][2])
+                           F (&xprev)[kChainKpt][2], F* __restrict__ rho_out)
 {
     __shared__ F part[kMaxLine * 4];          // [cell][warp] partial wall sums of this CTA
     __shared__ F rho_s[kMaxLine];
@@ -313,52 +316,15 @@ __device__ void chain_rest(cg::cluster_group& cl, const MicroArgs& M, const doub
         rho_s[st] = rho;
     }
     __syncthreads();
-    // ---- phase C: incoming velocities
-    for (int st = 1; st < len; ++st) {
-        int i, j;
-        cell(st, i, j);
-        const int c = j * nx + i;
-        const int bc = face_bc(i, j);
-        const BcDev B = M.bc[bc];
-        const F nbS = (F)(nb_axis == 0 ? L.rdx[i] : L.rdy[j]);
-        const F fS = (F)(f_axis == 0 ? L.rdx[i] : L.rdy[j]);
-        const F itau = (F)M.inv_tau[c];
-        const F rho = rho_s[st];
-        #pragma unroll
-        for (int t = 0; t < kChainKpt; ++t) {
-            int k = kk[t];
-            if (k < 0 || !(uo_t[t] < F(0))) continue;
-            const F u = (F)Vg.u[k], v = (F)Vg.v[k];
-            const F Dn = Dface<F>(nb_axis, nb_sign, nbS, u, v);
-            const F Db = uo_t[t] * fS;                               // (1/V) u_n S, u_n < 0
-            F D = F(0);
-            if (pass == 1 || B.type == BC_OUTFLOW) D = itau + geomD<F>(L, i, j, u, v);
-            const F id = B.type == BC_OUTFLOW ? recip(D + Db) : invD[(size_t)c * nv + k];
-            const int km = f_axis == 0 ? mu[t] : -1;
-            #pragma unroll
-            for (int cp = 0; cp < 2; ++cp) {
-                size_t idx = (cp * nc + c) * nv + k;
-                F base = pass == 0 ? r[idx] - Dn * xprev[t][cp] : D * x[idx] - Dn * xprev[t][cp];
-                if (B.type == BC_WALL) {
-                    base -= Db * (F)(M.Cw[(size_t)bc * nv + k] * (cp == 0 ? 1.0 : kKint * B.t / 4.0)) * rho;
-                } else if (B.type == BC_SYMMETRY) {
-                    int a2 = k / Vg.nvv, b2 = k - a2 * Vg.nvv;
-                    int kmir = f_axis == 0 ? (Vg.nu - 1 - a2) * Vg.nvv + b2 : a2 * Vg.nvv + (Vg.nvv - 1 - b2);
-                    base -= Db * x[(cp * nc + c) * nv + kmir];
-                }
-                (void)km;
-                F xv = base * id;
-                x[idx] = xv;
-                xprev[t][cp] = xv;
-            }
-        }
-    }
+    // the incoming velocities of cells 1.. are finished by the wavefront kernel
+    if (cl.block_rank() == 0)
+        for (int st = threadIdx.x; st < len; st += blockDim.x) rho_out[st] = st == 0 ? F(0) : rho_s[st];
 }
 
 template <typename F, int kChainKpt>
 __global__ void __cluster_dims__(kChainCluster, 1, 1) __launch_bounds__(kChainThreads)
 k_sgs_chain(MicroArgs M, const double* __restrict__ Zw, const F* __restrict__ invD, const F* __restrict__ r,
-            F* __restrict__ x, const F* __restrict__ xcorner, int pass)
+            F* __restrict__ x, const F* __restrict__ xcorner, F* __restrict__ rho_lines, int pass)
 {
     const double* __restrict__ iZw = Zw + 4 * kMaxBcs;          // reciprocals of the wall normalisations
     __shared__ F slots[2 * 4 * 4];
@@ -563,19 +529,53 @@ k_sgs_chain(MicroArgs M, const double* __restrict__ Zw, const F* __restrict__ in
             }
         }
     }
-    if (len > 1) chain_rest<F, kChainKpt>(cl, M, iZw, invD, r, x, pass, line, len, kk, mu, xprev);
+    if (len > 1) chain_rest<F, kChainKpt>(cl, M, iZw, invD, r, x, pass, line, len, kk, mu, xprev,
+                                          rho_lines + line * kMaxLine);
     cl.sync();   // keep every CTA's shared memory alive until all remote reads are done
 }
 
-// Interior cells of one sweep for the kInteriorKc velocities of this CTA, in
-// anti-diagonal order.  Values of the previous diagonal stay in shared memory
-// (indexed by the x-index of the cell); the residual (forward) or forward
-// value (backward) and 1/D of the next diagonal are loaded while the current
-// one is computed.  EPT: elements (cell, component, velocity) per thread and
-// diagonal.
+// asynchronous 4- or 8-byte global -> shared copies (LDGSTS), completed per commit group
+template <typename F>
+__device__ __forceinline__ void cp_async_elem(F* sdst, const F* gsrc)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    if constexpr (sizeof(F) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gsrc) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// wait until at most n (0..7) of this thread's most recent groups are pending
+__device__ __forceinline__ void cp_async_wait(int n)
+{
+    switch (n) {
+    case 0: asm volatile("cp.async.wait_group 0;\n" ::: "memory"); break;
+    case 1: asm volatile("cp.async.wait_group 1;\n" ::: "memory"); break;
+    case 2: asm volatile("cp.async.wait_group 2;\n" ::: "memory"); break;
+    case 3: asm volatile("cp.async.wait_group 3;\n" ::: "memory"); break;
+    case 4: asm volatile("cp.async.wait_group 4;\n" ::: "memory"); break;
+    case 5: asm volatile("cp.async.wait_group 5;\n" ::: "memory"); break;
+    case 6: asm volatile("cp.async.wait_group 6;\n" ::: "memory"); break;
+    default: asm volatile("cp.async.wait_group 7;\n" ::: "memory"); break;
+    }
+}
+
+constexpr int kWaveRingMax = 8;       // diagonals in flight in the wavefront kernel (at most)
+
+// One sweep over every cell for the kInteriorKc velocities of this CTA, in
+// anti-diagonal order.  The corner cell and the outgoing velocities of the
+// boundary-line cells were finished by k_sgs_chain (their values are read);
+// every other update is (forward) x = (b - D_W x_W - D_S x_S) / D, with b the
+// residual minus the known ghost term, or (backward) x = b - (D_E x_E + D_N
+// x_N) / D, with b the forward value (minus the ghost term over D).  Values of
+// the previous diagonal stay in shared memory.  The inputs of the next R - 1
+// diagonals are in flight as asynchronous copies into a ring of R shared
+// buffers, so the per-diagonal path only touches shared memory; the ghost data
+// of the two boundary lines (wall coefficient times wall density, or the
+// mirrored value) is gathered once at the start.
 template <typename F, int EPT>
-__global__ void __launch_bounds__(128) k_sgs_interior(MicroArgs M, const F* __restrict__ invD,
-                                                      const F* __restrict__ r, F* __restrict__ x, int pass)
+__global__ void __launch_bounds__(256) k_sgs_wave(MicroArgs M, const F* __restrict__ invD, const F* __restrict__ r,
+                                                  F* __restrict__ x, const F* __restrict__ rho_lines, int pass, int R)
 {
     extern __shared__ double sraw[];
     const LevelDev& L = M.L;
@@ -584,100 +584,167 @@ __global__ void __launch_bounds__(128) k_sgs_interior(MicroArgs M, const F* __re
     const size_t nc = L.nc;
     const int k0 = blockIdx.x * kInteriorKc;
     constexpr int W = 2 * kInteriorKc;                  // elements per cell
+    const int nd = nx + ny - 1, nl = nx + ny;
+    const int per = EPT * blockDim.x;                   // element slots of one diagonal
     F* sx = reinterpret_cast<F*>(sraw);                 // [2][nx][W] values of the previous diagonal
-    F* scol = sx + 2 * (size_t)nx * W;                  // [ny][W] boundary column next to the region
-    F* srow = scol + (size_t)ny * W;                    // [nx][W] boundary row next to the region
-    const int ilo0 = pass == 0 ? 1 : 0, ihi0 = pass == 0 ? nx - 1 : nx - 2;
-    const int jlo0 = pass == 0 ? 1 : 0, jhi0 = pass == 0 ? ny - 1 : ny - 2;
-    if (ihi0 < ilo0 || jhi0 < jlo0) return;
-    const int dlo = ilo0 + jlo0, dhi = ihi0 + jhi0, nd = dhi - dlo + 1;
-    {   // the boundary lines were finished by the chain kernel: stage them once
-        const int ib = pass == 0 ? 0 : nx - 1, jb = pass == 0 ? 0 : ny - 1;
-        for (int e = threadIdx.x; e < (nx + ny) * W; e += blockDim.x) {
-            int cellk = e / W, rem = e - cellk * W, cp = rem / kInteriorKc, k = k0 + rem - cp * kInteriorKc;
-            if (k >= nv) continue;
-            if (cellk < ny) scol[cellk * W + rem] = x[(cp * nc + (size_t)cellk * nx + ib) * nv + k];
-            else srow[(cellk - ny) * W + rem] = x[(cp * nc + (size_t)jb * nx + (cellk - ny)) * nv + k];
-        }
-        __syncthreads();
-    }
-    auto diag = [&](int dd) { return pass == 0 ? dlo + dd : dhi - dd; };
-    auto bounds = [&](int d, int& ilo, int& ihi) { ilo = max(ilo0, d - jhi0); ihi = min(ihi0, d - jlo0); };
-    F cr[EPT], ci[EPT], nr[EPT], ni[EPT];
-    auto load = [&](int dd, F (&rv)[EPT], F (&iv)[EPT]) {
-        int d = diag(dd), ilo, ihi;
-        bounds(d, ilo, ihi);
-        const int nel = (ihi - ilo + 1) * W;
-        #pragma unroll
-        for (int m = 0; m < EPT; ++m) {
-            int e = threadIdx.x + m * blockDim.x;
-            int slot = e / W, rem = e - slot * W, cp = rem / kInteriorKc, k = k0 + rem - cp * kInteriorKc;
-            if (e < nel && k < nv) {
-                int i = ilo + slot, c = (d - i) * nx + i;
-                size_t id = (size_t)c * nv + k;
-                rv[m] = pass == 0 ? r[cp * nc * nv + id] : x[cp * nc * nv + id];
-                iv[m] = invD[id];
+    F* ring = sx + 2 * (size_t)nx * W;                  // [R][2][per] inputs (value, 1/D) of upcoming diagonals
+    F* gtab = ring + (size_t)R * 2 * per;               // [nl][W] ghost data of the line cells (times Db)
+    F* litau = gtab + (size_t)nl * W;                   // [nl] their collision frequencies
+    F* srdx = litau + nl;                               // [nx] 1/dx
+    F* srdy = srdx + nx;                                // [ny] 1/dy
+    int* lty = reinterpret_cast<int*>(srdy + ny);       // [nl] boundary types of the line cells
+    const int ib = pass == 0 ? 0 : nx - 1, jb = pass == 0 ? 0 : ny - 1;   // boundary column and row of the sweep
+    const int fout = pass == 0 ? -1 : 1;
+    const F* src = pass == 0 ? r : x;
+    // per thread: fixed component and velocity (the element index modulo W)
+    const int rem = threadIdx.x % W, cp = rem / kInteriorKc, kk = rem - cp * kInteriorKc, k = k0 + kk;
+    const bool kok = k < nv;
+    const F u = kok ? (F)Vg.u[k] : F(0), v = kok ? (F)Vg.v[k] : F(0);
+    const F au = fabs(u), av = fabs(v);
+    const F uo_col = fout < 0 ? -u : u, uo_row = fout < 0 ? -v : v;    // u_n at the line faces
+    auto loaded = [&](int i, int j) {                   // finished by the boundary-line kernel
+        const bool on_col = i == ib, on_row = j == jb;
+        return (on_col && on_row) || (on_col && uo_col >= F(0)) || (on_row && uo_row >= F(0));
+    };
+    auto issue = [&](int dd) {
+        if (dd < nd) {
+            const int d = pass == 0 ? dd : nd - 1 - dd;
+            const int ilo = max(0, d - (ny - 1)), ihi = min(nx - 1, d), ncell = ihi - ilo + 1;
+            F* ra = ring + (size_t)(dd % R) * 2 * per;
+            #pragma unroll
+            for (int m = 0; m < EPT; ++m) {
+                const int q = threadIdx.x + m * blockDim.x, slot = q / W;
+                if (slot >= ncell || !kok) continue;
+                const int i = ilo + slot, j = d - i;
+                const size_t id = (size_t)(j * nx + i) * nv + k, xid = cp * nc * nv + id;
+                if (loaded(i, j)) {
+                    cp_async_elem(ra + q, x + xid);
+                } else {
+                    cp_async_elem(ra + q, src + xid);
+                    cp_async_elem(ra + per + q, invD + id);
+                }
             }
         }
+        cp_async_commit();
     };
-    load(0, cr, ci);
+    for (int dd = 0; dd < R - 1; ++dd) issue(dd);
+    // boundary data of the two lines (column: e = st, row: e = ny + st)
+    for (int e = threadIdx.x; e < nl; e += blockDim.x) {
+        const int line = e < ny ? 0 : 1, st = line == 0 ? e : e - ny;
+        const int i = line == 0 ? ib : (pass == 0 ? st : nx - 1 - st);
+        const int j = line == 0 ? (pass == 0 ? st : ny - 1 - st) : jb;
+        const int c = j * nx + i;
+        const int bc = line == 0 ? L.fbx[j * (nx + 1) + (fout < 0 ? 0 : nx)] : L.fby[(fout < 0 ? 0 : ny) * nx + i];
+        const BcDev B = M.bc[bc];
+        const F rho = rho_lines[line * kMaxLine + st];
+        lty[e] = B.type;
+        litau[e] = (F)M.inv_tau[c];
+        for (int q = 0; q < W; ++q) {
+            const int qc = q / kInteriorKc, kq = k0 + q - qc * kInteriorKc;
+            F g = F(0);
+            const F un = kq < nv ? (F)(line == 0 ? Vg.u[kq] : Vg.v[kq]) : F(0);
+            const bool incoming = kq < nv && (fout < 0 ? -un : un) < F(0);
+            if (incoming && B.type == BC_WALL) {
+                g = (F)(M.Cw[(size_t)bc * nv + kq] * (qc == 0 ? 1.0 : kKint * B.t / 4.0)) * rho;
+            } else if (incoming && B.type == BC_SYMMETRY) {
+                const int a2 = kq / Vg.nvv, b2 = kq - a2 * Vg.nvv;
+                const int km = line == 0 ? (Vg.nu - 1 - a2) * Vg.nvv + b2 : a2 * Vg.nvv + (Vg.nvv - 1 - b2);
+                g = x[(qc * nc + c) * nv + km];         // an outgoing velocity: already final
+            }
+            gtab[(size_t)e * W + q] = g;
+        }
+    }
+    for (int e = threadIdx.x; e < nx; e += blockDim.x) srdx[e] = (F)L.rdx[e];
+    for (int e = threadIdx.x; e < ny; e += blockDim.x) srdy[e] = (F)L.rdy[e];
+    __syncthreads();
     for (int dd = 0; dd < nd; ++dd) {
-        if (dd + 1 < nd) load(dd + 1, nr, ni);
-        const int d = diag(dd);
-        int ilo, ihi;
-        bounds(d, ilo, ihi);
-        const int nel = (ihi - ilo + 1) * W;
+        issue(dd + R - 1);
+        cp_async_wait(R - 1);
+        const int d = pass == 0 ? dd : nd - 1 - dd;
+        const int ilo = max(0, d - (ny - 1)), ihi = min(nx - 1, d);
+        const int ncell = ihi - ilo + 1;
+        const F* ra = ring + (size_t)(dd % R) * 2 * per;
         F* prev = sx + (size_t)((dd + 1) & 1) * nx * W;
         F* cur = sx + (size_t)(dd & 1) * nx * W;
         #pragma unroll
         for (int m = 0; m < EPT; ++m) {
-            int e = threadIdx.x + m * blockDim.x;
-            int slot = e / W, rem = e - slot * W, cp = rem / kInteriorKc, kk = rem - cp * kInteriorKc, k = k0 + kk;
-            if (e >= nel || k >= nv) continue;
-            int i = ilo + slot, j = d - i, c = j * nx + i;
-            const F u = (F)Vg.u[k], v = (F)Vg.v[k];
-            const F idx = (F)L.rdx[i], idy = (F)L.rdy[j];
-            F* xb = x + cp * nc * nv;
-            size_t id = (size_t)c * nv + k;
+            const int q = threadIdx.x + m * blockDim.x, slot = q / W;
+            if (slot >= ncell || !kok) continue;
+            const int i = ilo + slot, j = d - i;
+            const bool on_col = i == ib, on_row = j == jb;
             F res;
-            if (pass == 0) {
-                F dW = u > F(0) ? -u * idx : F(0), dS = v > F(0) ? -v * idy : F(0);
-                F xW = (i - 1 >= ilo0) ? prev[(i - 1) * W + cp * kInteriorKc + kk] : scol[j * W + cp * kInteriorKc + kk];
-                F xS = (j - 1 >= jlo0) ? prev[i * W + cp * kInteriorKc + kk] : srow[i * W + cp * kInteriorKc + kk];
-                res = (cr[m] - dW * xW - dS * xS) * ci[m];
+            if (loaded(i, j)) {
+                res = ra[q];
             } else {
-                F dE = u < F(0) ? u * idx : F(0), dN = v < F(0) ? v * idy : F(0);
-                F xE = (i + 1 <= ihi0) ? prev[(i + 1) * W + cp * kInteriorKc + kk] : scol[j * W + cp * kInteriorKc + kk];
-                F xN = (j + 1 <= jhi0) ? prev[i * W + cp * kInteriorKc + kk] : srow[i * W + cp * kInteriorKc + kk];
-                res = cr[m] - (dE * xE + dN * xN) * ci[m];
+                F bv = ra[q], iv = ra[per + q];
+                if (on_col || on_row) {
+                    // incoming velocity at the line face: known ghost term
+                    const int e = on_col ? (pass == 0 ? j : ny - 1 - j) : ny + (pass == 0 ? i : nx - 1 - i);
+                    const int ty = lty[e];
+                    const F Db = on_col ? uo_col * srdx[i] : uo_row * srdy[j];
+                    const F g = Db * gtab[(size_t)e * W + rem];
+                    const F D = litau[e] + (au * srdx[i] + av * srdy[j]);
+                    if (ty == BC_OUTFLOW) iv = recip(D + Db);
+                    bv = pass == 0 ? bv - g : (D * bv - g) * iv;
+                }
+                F y = F(0);
+                if (pass == 0) {
+                    if (i > 0 && u > F(0)) y += -u * srdx[i] * prev[(i - 1) * W + rem];
+                    if (j > 0 && v > F(0)) y += -v * srdy[j] * prev[i * W + rem];
+                    res = (bv - y) * iv;
+                } else {
+                    if (i < nx - 1 && u < F(0)) y += u * srdx[i] * prev[(i + 1) * W + rem];
+                    if (j < ny - 1 && v < F(0)) y += v * srdy[j] * prev[i * W + rem];
+                    res = bv - y * iv;
+                }
+                x[cp * nc * nv + (size_t)(j * nx + i) * nv + k] = res;
             }
-            xb[id] = res;
-            cur[i * W + cp * kInteriorKc + kk] = res;
+            cur[i * W + rem] = res;
         }
         __syncthreads();
-        #pragma unroll
-        for (int m = 0; m < EPT; ++m) { cr[m] = nr[m]; ci[m] = ni[m]; }
     }
+    cp_async_wait(0);
 }
 
 template <typename F>
 cudaError_t launch_micro_sgs(const MicroArgs& m, const double* Zw, const F* invD, const F* r, F* x, F* xcorner,
                              cudaStream_t st)
 {
+    F* rho_lines = xcorner + 2 * (size_t)m.V.nv;       // 2 x kMaxLine wall densities after the corner copy
     const int ngroups = (m.V.nu + 1) / 2;
     const int nloc = ((ngroups + kChainCluster - 1) / kChainCluster) * 2 * m.V.nvv;
     if (nloc > kChainKptMax * kChainThreads) return cudaErrorInvalidValue;
     if (m.L.nx > kMaxLine || m.L.ny > kMaxLine) return cudaErrorInvalidValue;
     size_t smem = sizeof(F) * 2 * nloc;
     const int kpt = (nloc + kChainThreads - 1) / kChainThreads;
-    void (*chain)(MicroArgs, const double*, const F*, const F*, F*, const F*, int) =
+    void (*chain)(MicroArgs, const double*, const F*, const F*, F*, const F*, F*, int) =
         kpt <= 1 ? k_sgs_chain<F, 1> : kpt <= 2 ? k_sgs_chain<F, 2> : kpt <= 4 ? k_sgs_chain<F, 4>
                  : kpt <= 8 ? k_sgs_chain<F, 8> : k_sgs_chain<F, 16>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(chain, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
         if (e != cudaSuccess) return e;
     }
-    int nblk_int = (m.V.nv + kInteriorKc - 1) / kInteriorKc;
+    const int nblk = (m.V.nv + kInteriorKc - 1) / kInteriorKc;
+    const int maxdiag = m.L.nx < m.L.ny ? m.L.nx : m.L.ny;
+    const int nthr = maxdiag * 2 * kInteriorKc <= 128 * 16 ? 128 : 256;
+    const int ept = (maxdiag * 2 * kInteriorKc + nthr - 1) / nthr;
+    if (ept > 16) return cudaErrorInvalidValue;
+    void (*wave)(MicroArgs, const F*, const F*, F*, const F*, int, int) =
+        ept <= 4 ? k_sgs_wave<F, 4> : ept <= 8 ? k_sgs_wave<F, 8> : k_sgs_wave<F, 16>;
+    const size_t nl = (size_t)m.L.nx + m.L.ny;
+    const size_t fixed = sizeof(F) * (2 * (size_t)m.L.nx * 2 * kInteriorKc + nl * (2 * kInteriorKc + 1) + nl)
+                       + sizeof(int) * nl;
+    const int ept_t = ept <= 4 ? 4 : ept <= 8 ? 8 : 16;      // the instantiated elements per thread
+    const size_t slot = sizeof(F) * 2 * (size_t)ept_t * nthr;
+    constexpr size_t kSmemMax = 227 * 1024;
+    if (fixed + slot > kSmemMax) return cudaErrorInvalidValue;
+    const size_t rfit = (kSmemMax - fixed) / slot;
+    const int R = rfit < (size_t)kWaveRingMax ? (int)rfit : kWaveRingMax;
+    const size_t wsmem = fixed + slot * R;
+    if (wsmem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(wave, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem);
+        if (e != cudaSuccess) return e;
+    }
     const size_t nc = m.L.nc, nv = m.V.nv, corner = (size_t)m.L.nc - 1;
     for (int pass = 0; pass < 2; ++pass) {
         if (pass == 1)
@@ -686,16 +753,10 @@ cudaError_t launch_micro_sgs(const MicroArgs& m, const double* Zw, const F* invD
                                                 cudaMemcpyDeviceToDevice, st);
                 if (e != cudaSuccess) return e;
             }
-        chain<<<2 * kChainCluster, kChainThreads, smem, st>>>(m, Zw, invD, r, x, xcorner, pass);
+        chain<<<2 * kChainCluster, kChainThreads, smem, st>>>(m, Zw, invD, r, x, xcorner, rho_lines, pass);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        const int maxdiag = m.L.nx < m.L.ny ? m.L.nx : m.L.ny;
-        const int ept = (maxdiag * 2 * kInteriorKc + 127) / 128;
-        const size_t ismem = sizeof(F) * (2 * (size_t)m.L.nx + m.L.nx + m.L.ny) * 2 * kInteriorKc;
-        if (ept <= 4) k_sgs_interior<F, 4><<<nblk_int, 128, ismem, st>>>(m, invD, r, x, pass);
-        else if (ept <= 8) k_sgs_interior<F, 8><<<nblk_int, 128, ismem, st>>>(m, invD, r, x, pass);
-        else if (ept <= 16) k_sgs_interior<F, 16><<<nblk_int, 128, ismem, st>>>(m, invD, r, x, pass);
-        else return cudaErrorInvalidValue;
+        wave<<<nblk, nthr, wsmem, st>>>(m, invD, r, x, rho_lines, pass, R);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

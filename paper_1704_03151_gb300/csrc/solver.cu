@@ -549,8 +549,7 @@ miugks_status miugks_create(const miugks_mesh* mesh, const miugks_vgrid* vg, con
             level_geometry(C);
         }
         if (st != MIUGKS_OK) break;
-        if (mesh->nx > 512 || mesh->ny > 512) { st = bad("nx and ny are limited to 512"); break; }
-        if (mesh->nx > 512 || mesh->ny > 512) { st = bad("nx and ny are limited to 512"); break; }
+        if (mesh->nx > kMaxLine || mesh->ny > kMaxLine) { st = bad("nx and ny are limited to 512"); break; }
         // chain kernel capacity: velocities per CTA of the 8-CTA cluster
         int nloc = (((s->nu + 1) / 2 + 7) / 8) * 2 * s->nvv;
         if (nloc > 8 * 256) { st = bad("velocity grid too large for the boundary-line kernel (%d local > 2048)", nloc); break; }
@@ -601,7 +600,7 @@ miugks_status miugks_create(const miugks_mesh* mesh, const miugks_vgrid* vg, con
         if ((st = dalloc(s, &s->Fy, 4 * (size_t)L0.nfy)) != MIUGKS_OK) break;
         if ((st = dalloc(s, &s->rms_part, 64 * 4)) != MIUGKS_OK) break;
         if ((st = dalloc(s, &s->rms_out, 8)) != MIUGKS_OK) break;
-        if ((st = falloc(s, &s->xcorner, 2 * nv)) != MIUGKS_OK) break;
+        if ((st = falloc(s, &s->xcorner, 2 * nv + 2 * kMaxLine)) != MIUGKS_OK) break;
         // smallest interior physical time step (for the numerical time step)
         s->dtp_min = 1e300;
         for (int i = 1; i < L0.nx; ++i) s->dtp_min = std::fmin(s->dtp_min, opts->cfl * std::fmin(L0.dx[i - 1], L0.dx[i]) / s->umax);
