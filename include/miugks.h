@@ -46,7 +46,7 @@ typedef enum {
     MIUGKS_ENOMEM = 2,         /* device or host allocation failed                */
     MIUGKS_ECUDA = 3,          /* CUDA runtime error (message has the details)    */
     MIUGKS_EDIVERGED = 4,      /* non-positive density or temperature, or NaN     */
-    MIUGKS_ETIMEOUT = 5,       /* reserved: a bounded device wait gave up         */
+    MIUGKS_ETIMEOUT = 5,       /* a bounded device wait gave up (sticky)          */
     MIUGKS_ENOTCONVERGED = 6,  /* miugks_run reached max_iter above tolerance    */
     MIUGKS_ESTATE = 7          /* call order (e.g. step before init)              */
 } miugks_status;

@@ -20,10 +20,11 @@ template <typename F> cudaError_t launch_face_flux(const FaceFluxArgs<F>& a, cud
 cudaError_t launch_cell_residual(const LevelDev& L, const double* Fx, const double* Fy, double* R, cudaStream_t st);
 cudaError_t launch_rms(const double* R, const double* W, int nc, double* part, double* out, cudaStream_t st);
 
-// ---- prediction step (macroscopic, FP64) ----
+// ---- prediction step (macroscopic state in FP64) ----
 struct MacroArgs {
     LevelDev L; GasDev gas; const BcDev* bc;
     double dtn_inv;                        // 1/dt_n (0 when off)
+    double* flag;                          // set to 1 when a bounded device wait gave up
 };
 // Gamma of every face from the frozen state Wg
 // (and the inverse diagonal of the smoother per cell)
@@ -32,9 +33,12 @@ cudaError_t launch_macro_gamma(const MacroArgs& a, const double* Wg, double* gx,
 // mode 0: out = Rin - R_E(W)  (forcing);  mode 1: out = Rin + R_E(W)  (renewal P + R_E)
 cudaError_t launch_macro_resid(const MacroArgs& a, const double* W, const double* gx, const double* gy,
                                const double* Rin, double* out, int mode, cudaStream_t st);
-// one LU-SGS pass: dW from R at state W; then W += dW (T: [nc][20] scratch for fluxes and ghost terms)
+// one LU-SGS pass: dW from R at state W; then W += dW.  F: arithmetic of the sweep
+// (double, or float with increments); rec: macro_rec_bytes(nx, ny, F == float) of scratch
+template <typename F>
 cudaError_t launch_macro_sgs(const MacroArgs& a, double* W, const double* gx, const double* gy, const double* idiag,
-                             double* T, const double* R, double* dW, cudaStream_t st);
+                             void* rec, const double* R, double* dW, cudaStream_t st);
+size_t macro_rec_bytes(int nx, int ny, bool mixed);
 template <typename T>
 cudaError_t launch_restrict(const LevelDev& F, const LevelDev& C, int m, int nblk, const T* fine, T* coarse,
                             cudaStream_t st);

@@ -6,10 +6,12 @@
 // (Eqs. macroRestriction, microRestriction, prolongation).
 //
 // The LU-SGS sweep runs as an anti-diagonal wavefront inside one thread-block
-// cluster: the cells of a diagonal are spread over the cluster's CTAs and a
-// hardware cluster barrier separates consecutive diagonals, so the serial
-// sweep order is kept without grid-wide synchronisation.
+// cluster: the cells of a diagonal are spread over the cluster's CTAs, which
+// pass the edge cells of each diagonal to their neighbours through
+// distributed shared memory, so the serial sweep order is kept without
+// grid-wide synchronisation.
 #include "kernels.cuh"
+#include "async.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -159,15 +161,6 @@ cudaError_t launch_macro_gamma(const MacroArgs& a, const double* Wg, double* gx,
     return cudaGetLastError();
 }
 
-// Euler fluxes of every cell along +x and +y, [nc][8]
-__global__ void k_macro_prep(LevelDev L, const double* __restrict__ W, double* __restrict__ T)
-{
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= L.nc) return;
-    euler_axis(W + 4 * (size_t)c, 0, T + 8 * (size_t)c);
-    euler_axis(W + 4 * (size_t)c, 1, T + 8 * (size_t)c + 4);
-}
-
 // face f of cell (i, j): 0 west, 1 east, 2 south, 3 north
 __device__ __forceinline__ void face_of(const LevelDev& L, int i, int j, int f, int& bcid, int& nb, double& gidx_dummy)
 {
@@ -237,16 +230,95 @@ cudaError_t launch_macro_resid(const MacroArgs& a, const double* W, const double
 
 // LU-SGS pass of Eq. macroFinalDefect, one lane per (cell, component).
 //
-// On GB300 an FP64 warp instruction occupies its SM sub-partition for 64 cycles
-// however many lanes are active, so the sweep minimises FP64 instructions per
-// lane rather than lanes: each lane updates one component of one cell of the
-// current diagonal (about eight FP64 instructions), and the four lanes of a
-// cell then evaluate the Euler fluxes of the new state W + dW along x and y,
-// which the cell's successors on the next diagonal need.  Boundary ghosts
-// enter only the backward sweep (they use dW_i of the forward sweep), so their
-// contribution is computed for all boundary cells in parallel between the two
-// half sweeps.  Arrays: T0 = T(W) [nc][8] (from k_macro_prep), T1 = T(W + dW)
-// [nc][8], G = upper-side ghost terms [nc][4].
+// The cells of an anti-diagonal are spread over the CTAs of one cluster, 32
+// cells (128 lanes) per CTA; cell s of a diagonal only needs cells s-1, s and
+// s+1 of the previous one.  So a diagonal's results -- dW and the flux terms X
+// along x and y that its successors need -- go to shared memory, and only the
+// two edge cells of each CTA are pushed into the neighbouring CTAs' shared
+// memory (st.async on their mbarrier).  A CTA waits for its two neighbours
+// only: no cluster-wide barrier and no global-memory round trip per diagonal.
+//
+// Everything a lane needs that does not depend on the sweep (own defect times
+// 1/D, face coefficients, the base state) is packed by k_macro_rec into a
+// record of kRec values per (pass, diagonal, slot, component), diagonal-major,
+// so that the records of upcoming diagonals stream into a ring in shared
+// memory with one bulk copy per CTA and diagonal.
+//
+// Flux terms.  FP64: X = T(W + dW), and the record carries
+// c0 = -sum sgn S T(W_nb), so the coupling term is c0 + sum (sgn S X_nb -
+// S Gamma dW_nb).  Mixed: X = T(W + dW) - T(W) written through the increments
+// (dU = (dm_x - U drho) / (rho + drho), dp, ... -- exact identities), which
+// FP32 evaluates to a relative error of the increments themselves, with no
+// cancellation against T(W).
+//
+// Boundary ghosts enter only the backward sweep (they use dW of the forward
+// sweep); their term is folded into that sweep's own value between the passes.
+// The backward sweep adds dW to W as it goes.
+
+constexpr int kRec = 12;                         // values per record
+constexpr int kMacroRing = 8;                    // diagonals of records in flight
+constexpr int kMacroSlots = kMacroThreads / 4;   // cells of a diagonal per CTA
+constexpr int kMsg = 3;                          // values per lane and message: dW, X_x, X_y
+
+__host__ __device__ inline int diag_lo(int d, int ny) { return d - (ny - 1) > 0 ? d - (ny - 1) : 0; }
+__host__ __device__ inline int diag_len(int d, int nx, int ny)
+{
+    return (d < nx - 1 ? d : nx - 1) - diag_lo(d, ny) + 1;
+}
+
+// record layout: rec[((pass * nd + d) * maxdiag + slot) * 4 + m][kRec]
+//   0 own value (pass 0: R / D; pass 1: forward dW minus the ghost term / D)
+//   1 base: W_m (FP64) or Q_m = (rho, m_x, m_y, E + p)_m (mixed)
+//   2 c0 (FP64; 0 in mixed)           3 hv / D, hv = 1 / (2V)
+//   4, 5 sgn S of the x and y neighbour faces (0 at a boundary face)
+//   6, 7 S Gamma of those faces        8, 9, 10 U, V, rho (mixed)
+template <typename F>
+__global__ void k_macro_rec(MacroArgs a, const double* __restrict__ W, const double* __restrict__ gx,
+                            const double* __restrict__ gy, const double* __restrict__ idiag,
+                            const double* __restrict__ R, F* __restrict__ rec, int maxdiag)
+{
+    const LevelDev& L = a.L;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 4 * L.nc) return;
+    const int c = t >> 2, m = t & 3, nx = L.nx, ny = L.ny, nd = nx + ny - 1;
+    const int i = c % nx, j = c / nx, d = i + j, slot = i - diag_lo(d, ny);
+    const double* Wc = W + 4 * (size_t)c;
+    const double id = idiag[c];
+    const double ir = rcp64(Wc[0]), U = Wc[1] * ir, V = Wc[2] * ir;
+    const double p = (2.0 / (kKint + 2)) * (Wc[3] - 0.5 * (Wc[1] * U + Wc[2] * V));
+    for (int pass = 0; pass < 2; ++pass) {
+        F* o = rec + ((((size_t)pass * nd + d) * maxdiag + slot) * 4 + m) * kRec;
+        const double sgn = pass ? 1.0 : -1.0;
+        double sS[2] = {0.0, 0.0}, Sgm[2] = {0.0, 0.0}, c0 = 0.0;
+        for (int axis = 0; axis < 2; ++axis) {
+            const int fidx = axis == 0 ? j * (nx + 1) + i + pass : (j + pass) * nx + i;
+            if ((axis == 0 ? L.fbx[fidx] : L.fby[fidx]) >= 0) continue;
+            const double S = axis == 0 ? L.dy[j] : L.dx[i];
+            sS[axis] = sgn * S;
+            Sgm[axis] = S * (axis == 0 ? gx[fidx] : gy[fidx]);
+            if constexpr (sizeof(F) == 8) {
+                const int nb = axis == 0 ? c + (pass ? 1 : -1) : c + (pass ? nx : -nx);
+                double T0[4];
+                euler_axis(W + 4 * (size_t)nb, axis, T0);
+                c0 -= sS[axis] * T0[m];
+            }
+        }
+        double base = Wc[m];
+        if constexpr (sizeof(F) == 4) base = m == 3 ? Wc[3] + p : Wc[m];
+        o[0] = pass == 0 ? (F)(R[4 * (size_t)c + m] * id) : F(0);
+        o[1] = (F)base;
+        o[2] = (F)c0;
+        o[3] = (F)(0.5 * L.rdx[i] * L.rdy[j] * id);
+        o[4] = (F)sS[0];
+        o[5] = (F)sS[1];
+        o[6] = (F)Sgm[0];
+        o[7] = (F)Sgm[1];
+        o[8] = (F)U;
+        o[9] = (F)V;
+        o[10] = (F)Wc[0];
+        o[11] = F(0);
+    }
+}
 
 // Euler flux component m of W along +e_axis, given 1/rho, U_a and p
 __device__ __forceinline__ double euler_comp(const double* W, int m, int axis, double Ua, double p)
@@ -297,99 +369,187 @@ __device__ void macro_ghost_terms(const MacroArgs& a, const double* W, const dou
     }
 }
 
-// inputs of one lane for one diagonal that do not depend on the previous diagonal
-struct MacroLane {
-    int c, nb[2];
-    bool on, inter[2];
-    double gm[2], S[2], T0[2], own, id, hv, W, G;
-};
-
-__global__ void __cluster_dims__(kMacroCluster, 1, 1) __launch_bounds__(kMacroThreads)
-k_macro_sgs(MacroArgs a, double* __restrict__ W, const double* __restrict__ T0, double* __restrict__ T1,
-            double* __restrict__ Gt, const double* __restrict__ gx, const double* __restrict__ gy,
-            const double* __restrict__ idiag, const double* __restrict__ R, double* __restrict__ dW)
+// flux terms X_x, X_y of lane m (component m) of a cell updated by dw
+__device__ __forceinline__ void macro_x(double dw, const double* rc, int m, int g0, double& Xx, double& Xy)
 {
+    double T1c[8];
+    producer_fluxes(rc[1] + dw, m, g0, T1c);             // X = T(W + dW)
+    Xx = T1c[m];
+    Xy = T1c[4 + m];
+}
+__device__ __forceinline__ void macro_x(float dw, const float* rc, int m, int g0, float& Xx, float& Xy)
+{
+    float dq[4];                                         // increments of the four components
+    #pragma unroll
+    for (int q = 0; q < 4; ++q) dq[q] = __shfl_sync(0xffffffffu, dw, g0 + q);
+    const float Q = rc[1], U = rc[8], V = rc[9], rho = rc[10];
+    const float ir = 1.0f / (rho + dq[0]);
+    const float dU = (dq[1] - U * dq[0]) * ir, dV = (dq[2] - V * dq[0]) * ir;
+    const float Up = U + dU, Vp = V + dV;
+    const float dp = (2.0f / (kKint + 2)) * (dq[3] - 0.5f * (rho * U * dU + dq[1] * Up + rho * V * dV + dq[2] * Vp));
+    const float dm = m == 3 ? dq[3] + dp : dq[m];
+    Xx = Q * dU + dm * Up + (m == 1 ? dp : 0.0f);       // X = T(W + dW) - T(W)
+    Xy = Q * dV + dm * Vp + (m == 2 ? dp : 0.0f);
+}
+
+template <typename F>
+__global__ void __cluster_dims__(kMacroCluster, 1, 1) __launch_bounds__(kMacroThreads)
+k_macro_sgs(MacroArgs a, double* __restrict__ W, F* __restrict__ rec, double* __restrict__ dW,
+            const double* __restrict__ gx, const double* __restrict__ gy, int maxdiag, int nact)
+{
+    extern __shared__ __align__(128) unsigned char smraw[];
+    constexpr int per = kMacroSlots * 4 * kRec;          // record values of one CTA and diagonal
+    constexpr int xper = (kMacroSlots + 2) * 4 * kMsg;   // message values of one diagonal
+    F* ring = reinterpret_cast<F*>(smraw);               // [kMacroRing][per]
+    F* xb = ring + kMacroRing * per;                     // [2][kMacroSlots + 2][4][kMsg], halo at 0 and kMacroSlots + 1
+    uint64_t* rb = reinterpret_cast<uint64_t*>(xb + 2 * xper);   // [kMacroRing] record arrivals
+    uint64_t* xm = rb + kMacroRing;                      // [2] halo arrivals
+
     cg::cluster_group cl = cg::this_cluster();
     const LevelDev& L = a.L;
     const int nx = L.nx, ny = L.ny, nd = nx + ny - 1;
-    const int t = cl.block_rank() * blockDim.x + threadIdx.x;
-    const int m = t & 3, g0 = threadIdx.x & 28;        // component; first lane of the cell's group
-    const int slot = t >> 2;                            // one cell of a diagonal per four lanes
-    auto prepare = [&](int pass, int d, MacroLane& p) {
-        int ilo = d - (ny - 1) > 0 ? d - (ny - 1) : 0, ihi = d < nx - 1 ? d : nx - 1;
-        p.on = slot <= ihi - ilo;
-        if (!p.on) return;
-        int i = ilo + slot, j = d - i, c = j * nx + i;
-        p.c = c;
-        #pragma unroll
-        for (int axis = 0; axis < 2; ++axis) {
-            int fidx = axis == 0 ? j * (nx + 1) + i + pass : (j + pass) * nx + i;
-            p.inter[axis] = (axis == 0 ? L.fbx[fidx] : L.fby[fidx]) < 0;
-            p.nb[axis] = axis == 0 ? c + (pass ? 1 : -1) : c + (pass ? nx : -nx);
-            p.gm[axis] = axis == 0 ? gx[fidx] : gy[fidx];
-            p.S[axis] = axis == 0 ? L.dy[j] : L.dx[i];
-            p.T0[axis] = p.inter[axis] ? T0[8 * (size_t)p.nb[axis] + 4 * axis + m] : 0.0;
-        }
-        p.own = pass == 0 ? R[4 * (size_t)c + m] : dW[4 * (size_t)c + m];
-        p.id = idiag[c];
-        p.hv = 0.5 * L.rdx[i] * L.rdy[j];
-        p.W = W[4 * (size_t)c + m];
-        p.G = (pass == 1 && (i == nx - 1 || j == ny - 1)) ? Gt[4 * (size_t)c + m] : 0.0;
+    const int rank = (int)cl.block_rank(), tid = threadIdx.x;
+    const int m = tid & 3, g0 = tid & 28, ls = tid >> 2;  // component, first lane of the cell, local slot
+    const int gs0 = rank * kMacroSlots;                   // first slot of this CTA
+    const bool active = rank < nact;
+    const int nbrs = active ? (rank > 0) + (rank + 1 < nact) : 0;
+    if (tid == 0) {
+        for (int q = 0; q < kMacroRing; ++q) mbar_init(&rb[q], 1);
+        mbar_init(&xm[0], 1);
+        mbar_init(&xm[1], 1);
+        mbar_init_fence();
+    }
+    for (int e = tid; e < 2 * xper; e += blockDim.x) xb[e] = F(0);
+    cl.sync();
+
+    auto issue = [&](int g) {                            // records of step g into ring slot g % kMacroRing
+        const int pass = g / nd, dd = g - pass * nd, d = pass == 0 ? dd : nd - 1 - dd;
+        int nloc = diag_len(d, nx, ny) - gs0;
+        nloc = nloc < 0 ? 0 : (nloc > kMacroSlots ? kMacroSlots : nloc);
+        const unsigned bytes = (unsigned)(nloc * 4 * kRec * sizeof(F));
+        uint64_t* mb = &rb[g % kMacroRing];
+        mbar_arrive_tx(mb, bytes);
+        if (bytes) bulk_g2s(ring + (g % kMacroRing) * per, rec + (((size_t)pass * nd + d) * maxdiag + gs0) * 4 * kRec,
+                            bytes, mb);
     };
+    bool ok = true;
+    int issued = -1, consumed = -1;                      // last step issued / waited for (thread 0)
     for (int pass = 0; pass < 2; ++pass) {
         if (pass == 1) {
-            // upper-side ghost terms of the last column and row, from the forward dW (one thread per cell)
-            for (int b = t; b < nx + ny - 1; b += kMacroCluster * blockDim.x) {
-                int i = b < ny ? nx - 1 : b - ny, j = b < ny ? b : ny - 1;
-                macro_ghost_terms(a, W, gx, gy, dW, i, j, Gt + 4 * (size_t)(j * nx + i));
+            cl.sync();                                   // forward dW and records visible in the cluster
+            // upper-side ghost terms of the last column and row, from the forward dW, folded
+            // into the backward sweep's own values (one thread per cell)
+            for (int b = rank * blockDim.x + tid; ok && b < nx + ny - 1; b += kMacroCluster * blockDim.x) {
+                const int i = b < ny ? nx - 1 : b - ny, j = b < ny ? b : ny - 1, d = i + j;
+                double Gc[4];
+                macro_ghost_terms(a, W, gx, gy, dW, i, j, Gc);
+                F* o = rec + (((size_t)nd + d) * maxdiag + (i - diag_lo(d, ny))) * 4 * kRec;
+                for (int q = 0; q < 4; ++q)
+                    o[q * kRec] = (F)((double)o[q * kRec] - Gc[q] * (double)o[q * kRec + 3]);
             }
+            fence_proxy_async();
             cl.sync();
         }
-        const double sgn = pass ? 1.0 : -1.0;
-        MacroLane cur, nxt;
-        prepare(pass, pass == 0 ? 0 : nd - 1, cur);
-        for (int d0 = 0; d0 < nd; ++d0) {
-            double wp = 0.0;
-            if (cur.on) {
-                double acc = cur.G;
-                #pragma unroll
-                for (int axis = 0; axis < 2; ++axis) {
-                    if (!cur.inter[axis]) continue;
-                    const size_t nb = cur.nb[axis];
-                    double dT = T1[8 * nb + 4 * axis + m] - cur.T0[axis];
-                    acc = fma(cur.S[axis], fma(-cur.gm[axis], dW[4 * nb + m], sgn * dT), acc);
+        if (!active || !ok) continue;
+        const int gbase = pass * nd;
+        if (tid == 0)
+            for (int g = gbase; g < gbase + kMacroRing - 1 && g < gbase + nd; ++g) issue(issued = g);
+        for (int dd = 0; dd < nd; ++dd) {
+            const int g = gbase + dd, d = pass == 0 ? dd : nd - 1 - dd;
+            if (tid == 0) {
+                if (dd + kMacroRing - 1 < nd) issue(issued = g + kMacroRing - 1);
+                mbar_arrive_tx(&xm[g & 1], nbrs * 4 * kMsg * (unsigned)sizeof(F));   // this step's halo
+            }
+            bool got = mbar_wait(&rb[g % kMacroRing], (g / kMacroRing) & 1);
+            if (tid == 0 && got) consumed = g;
+            if (g > 0) got = mbar_wait(&xm[(g - 1) & 1], ((g - 1) >> 1) & 1) && got;
+            const int ilo = diag_lo(d, ny), ncell = diag_len(d, nx, ny);
+            const bool on = gs0 + ls < ncell;
+            const F* rc = ring + (g % kMacroRing) * per + (ls * 4 + m) * kRec;
+            F dw = F(0);
+            if (on) {
+                // local indices (halo offset 1) of the x and y neighbours on the previous diagonal
+                int nbx, nby;
+                if (pass == 0) {
+                    const bool same = diag_lo(d - 1, ny) == ilo;
+                    nbx = ls + (same ? 0 : 1);
+                    nby = ls + (same ? 1 : 2);
+                } else {
+                    const bool same = diag_lo(d + 1, ny) == ilo;
+                    nbx = ls + (same ? 2 : 1);
+                    nby = ls + (same ? 1 : 0);
                 }
-                double dw = pass == 0 ? fma(-acc, cur.hv, cur.own) * cur.id : fma(-acc * cur.hv, cur.id, cur.own);
-                dW[4 * (size_t)cur.c + m] = dw;
-                wp = cur.W + dw;
+                const F* pb = xb + ((g - 1) & 1) * xper;
+                F acc = rc[2];
+                if (rc[4] != F(0)) acc = fma(rc[4], pb[(nbx * 4 + m) * kMsg + 1], fma(-rc[6], pb[(nbx * 4 + m) * kMsg], acc));
+                if (rc[5] != F(0)) acc = fma(rc[5], pb[(nby * 4 + m) * kMsg + 2], fma(-rc[7], pb[(nby * 4 + m) * kMsg], acc));
+                dw = fma(-acc, rc[3], rc[0]);
             }
-            double T1c[8];
-            producer_fluxes(wp, m, g0, T1c);
-            if (cur.on) {
-                T1[8 * (size_t)cur.c + m] = T1c[m];
-                T1[8 * (size_t)cur.c + 4 + m] = T1c[4 + m];
+            F Xx, Xy;
+            macro_x(dw, rc, m, g0, Xx, Xy);              // all lanes (warp shuffles)
+            if (!on) Xx = Xy = F(0);
+            F* cb = xb + (g & 1) * xper;
+            cb[((ls + 1) * 4 + m) * kMsg] = dw;
+            cb[((ls + 1) * 4 + m) * kMsg + 1] = Xx;
+            cb[((ls + 1) * 4 + m) * kMsg + 2] = Xy;
+            // edge cells to the neighbouring CTAs' halos
+            int peer = -1, hs = 0;
+            if (ls == 0 && rank > 0) { peer = rank - 1; hs = kMacroSlots + 1; }
+            if (ls == kMacroSlots - 1 && rank + 1 < nact) { peer = rank + 1; hs = 0; }
+            if (peer >= 0) {
+                const unsigned rmb = peer_addr(&xm[g & 1], peer);
+                F* hl = cb + (hs * 4 + m) * kMsg;
+                st_async(peer_addr(hl, peer), dw, rmb);
+                st_async(peer_addr(hl + 1, peer), Xx, rmb);
+                st_async(peer_addr(hl + 2, peer), Xy, rmb);
             }
-            if (d0 + 1 < nd) prepare(pass, pass == 0 ? d0 + 1 : nd - 2 - d0, nxt);
-            cl.sync();   // release/acquire at cluster scope: the diagonal is visible to the next one
-            cur = nxt;
+            if (on) {
+                const int i = ilo + gs0 + ls, c = (d - i) * nx + i;
+                dW[4 * (size_t)c + m] = (double)dw;
+                if (pass == 0)
+                    rec[((((size_t)nd + d) * maxdiag + gs0 + ls) * 4 + m) * kRec] = dw;   // backward own value
+                else
+                    W[4 * (size_t)c + m] += (double)dw;
+            }
+            if (!__syncthreads_and(got)) { ok = false; break; }
         }
+        fence_proxy_async();
     }
-    for (int c = t; c < 4 * L.nc; c += kMacroCluster * blockDim.x) W[c] += dW[c];
+    if (active) {
+        if (ok && tid == 0 && !mbar_wait(&xm[(2 * nd - 1) & 1], ((2 * nd - 1) >> 1) & 1)) ok = false;
+        if (tid == 0)                                    // no bulk copy may still target this CTA
+            for (int g = consumed + 1; g <= issued; ++g) mbar_wait(&rb[g % kMacroRing], (g / kMacroRing) & 1);
+        if (!ok && tid == 0) *a.flag = 1.0;
+    }
+    cl.sync();                                           // no peer writes into this CTA after this point
 }
 
+template <typename F>
 cudaError_t launch_macro_sgs(const MacroArgs& a, double* W, const double* gx, const double* gy, const double* idiag,
-                             double* T, const double* R, double* dW, cudaStream_t st)
+                             void* rec, const double* R, double* dW, cudaStream_t st)
 {
-    // T: [nc][8] T(W), then [nc][8] T(W + dW), then [nc][4] ghost terms
-    double* T0 = T;
-    double* T1 = T + 8 * (size_t)a.L.nc;
-    double* Gt = T + 16 * (size_t)a.L.nc;
-    // one cell of a diagonal per four lanes of the cluster
     const int maxdiag = a.L.nx < a.L.ny ? a.L.nx : a.L.ny;
-    if (4 * maxdiag > kMacroCluster * kMacroThreads) return cudaErrorInvalidValue;
-    k_macro_prep<<<(a.L.nc + 127) / 128, 128, 0, st>>>(a.L, W, T0);
-    k_macro_sgs<<<kMacroCluster, kMacroThreads, 0, st>>>(a, W, T0, T1, Gt, gx, gy, idiag, R, dW);
+    const int nact = (maxdiag + kMacroSlots - 1) / kMacroSlots;
+    if (nact > kMacroCluster) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(F) * ((size_t)kMacroRing * kMacroSlots * 4 * kRec + 2 * (kMacroSlots + 2) * 4 * kMsg) +
+                        sizeof(uint64_t) * (kMacroRing + 2);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_macro_sgs<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_macro_rec<F><<<(4 * a.L.nc + 127) / 128, 128, 0, st>>>(a, W, gx, gy, idiag, R, (F*)rec, maxdiag);
+    k_macro_sgs<F><<<kMacroCluster, kMacroThreads, smem, st>>>(a, W, (F*)rec, dW, gx, gy, maxdiag, nact);
     return cudaGetLastError();
+}
+template cudaError_t launch_macro_sgs<double>(const MacroArgs&, double*, const double*, const double*, const double*,
+                                              void*, const double*, double*, cudaStream_t);
+template cudaError_t launch_macro_sgs<float>(const MacroArgs&, double*, const double*, const double*, const double*,
+                                             void*, const double*, double*, cudaStream_t);
+
+size_t macro_rec_bytes(int nx, int ny, bool mixed)
+{
+    const size_t maxdiag = nx < ny ? nx : ny, nd = (size_t)nx + ny - 1;
+    return 2 * nd * maxdiag * 4 * kRec * (mixed ? sizeof(float) : sizeof(double));
 }
 
 // ---------------------------------------------------------------------------

@@ -214,7 +214,7 @@ miugks_status upload_level(miugks_solver* s, HLevel& Lv)
     ST(dalloc(s, &Lv.Wn, n4)); ST(dalloc(s, &Lv.Wc, n4)); ST(dalloc(s, &Lv.Rc, n4)); ST(dalloc(s, &Lv.P, n4));
     ST(dalloc(s, &Lv.R, n4)); ST(dalloc(s, &Lv.dW, n4)); ST(dalloc(s, &Lv.Wt, n4));
     ST(dalloc(s, &Lv.gx, (size_t)Lv.nfx)); ST(dalloc(s, &Lv.gy, (size_t)Lv.nfy));
-    ST(dalloc(s, &Lv.idiag, (size_t)Lv.nc)); ST(dalloc(s, &Lv.T, 20 * (size_t)Lv.nc));
+    ST(dalloc(s, &Lv.idiag, (size_t)Lv.nc)); ST(dalloc(s, &Lv.T, (macro_rec_bytes(Lv.nx, Lv.ny, s->mixed) + 7) / 8));
     ST(falloc(s, &Lv.r, nf)); ST(falloc(s, &Lv.df, nf)); ST(falloc(s, &Lv.dl, nf));
     ST(falloc(s, &Lv.invD, (size_t)Lv.nc * s->nv)); ST(dalloc(s, &Lv.inv_tau, (size_t)Lv.nc));
     return MIUGKS_OK;
@@ -227,7 +227,7 @@ MicroArgs micro_args(miugks_solver* s, int l)
 
 MacroArgs macro_args(miugks_solver* s, int l, double dtn_inv)
 {
-    return MacroArgs{s->lev[l].dev, s->gas, s->bc, dtn_inv};
+    return MacroArgs{s->lev[l].dev, s->gas, s->bc, dtn_inv, s->rms_out + 5};
 }
 
 double dtn_inv(miugks_solver* s)
@@ -237,6 +237,12 @@ double dtn_inv(miugks_solver* s)
 }
 
 // ---------------------------------------------------------------- cycles
+cudaError_t macro_sgs(miugks_solver* s, const MacroArgs& ma, HLevel& Lv)
+{
+    if (s->mixed) return launch_macro_sgs<float>(ma, Lv.Wc, Lv.gx, Lv.gy, Lv.idiag, Lv.T, Lv.R, Lv.dW, s->st);
+    return launch_macro_sgs<double>(ma, Lv.Wc, Lv.gx, Lv.gy, Lv.idiag, Lv.T, Lv.R, Lv.dW, s->st);
+}
+
 miugks_status fas(miugks_solver* s, int l, double dti)
 {
     HLevel& Lv = s->lev[l];
@@ -249,7 +255,7 @@ miugks_status fas(miugks_solver* s, int l, double dti)
     const bool coarsest = l == s->L - 1;
     const int npre = coarsest ? (s->L == 1 ? 1 : s->opts.nu_coarse) : s->opts.nu1;
     for (int m = 0; m < npre; ++m) {
-        CK(launch_macro_sgs(ma, Lv.Wc, Lv.gx, Lv.gy, Lv.idiag, Lv.T, Lv.R, Lv.dW, s->st));
+        CK(macro_sgs(s, ma, Lv));
         if (coarsest && m == npre - 1) break;
         CK(launch_macro_resid(ma, Lv.Wc, Lv.gx, Lv.gy, Lv.P, Lv.R, 1, s->st));  // renewal P + R_E(W)
     }
@@ -262,7 +268,7 @@ miugks_status fas(miugks_solver* s, int l, double dti)
     CK(launch_prolong_add<double>(Lv.dev, Cv.dev, 4, 1, Lv.pidx, Lv.pw, Cv.dW, Lv.Wc, (double*)nullptr, s->st));
     for (int m = 0; m < s->opts.nu2; ++m) {
         CK(launch_macro_resid(ma, Lv.Wc, Lv.gx, Lv.gy, Lv.P, Lv.R, 1, s->st));
-        CK(launch_macro_sgs(ma, Lv.Wc, Lv.gx, Lv.gy, Lv.idiag, Lv.T, Lv.R, Lv.dW, s->st));
+        CK(macro_sgs(s, ma, Lv));
     }
     return MIUGKS_OK;
 }
@@ -349,10 +355,11 @@ miugks_status one_iteration(miugks_solver* s)
 
 miugks_status read_residual(miugks_solver* s, double res_out[4])
 {
-    double h[5];
+    double h[6];
     CK(cudaMemcpyAsync(h, s->rms_out, sizeof h, cudaMemcpyDeviceToHost, s->st));
     CK(cudaStreamSynchronize(s->st));
     if (res_out) memcpy(res_out, h, 4 * sizeof(double));
+    if (h[5] != 0.0) return fail(s, MIUGKS_ETIMEOUT, "a bounded wait of the macro sweep gave up at iteration %d", s->iter);
     bool bad = h[4] > 0;
     for (int m = 0; m < 4; ++m) bad = bad || !std::isfinite(h[m]);
     if (bad) return fail(s, MIUGKS_EDIVERGED, "diverged at iteration %d (%.0f unphysical cells)", s->iter, h[4]);
@@ -600,6 +607,7 @@ miugks_status miugks_create(const miugks_mesh* mesh, const miugks_vgrid* vg, con
         if ((st = dalloc(s, &s->Fy, 4 * (size_t)L0.nfy)) != MIUGKS_OK) break;
         if ((st = dalloc(s, &s->rms_part, 64 * 4)) != MIUGKS_OK) break;
         if ((st = dalloc(s, &s->rms_out, 8)) != MIUGKS_OK) break;
+        if (cudaMemset(s->rms_out, 0, 8 * sizeof(double)) != cudaSuccess) { st = fail(s, MIUGKS_ECUDA, "cudaMemset"); break; }
         if ((st = falloc(s, &s->xcorner, 2 * nv + 2 * kMaxLine)) != MIUGKS_OK) break;
         // smallest interior physical time step (for the numerical time step)
         s->dtp_min = 1e300;
@@ -940,9 +948,12 @@ miugks_status miugks_stage_sgs_macro(miugks_solver* s, int lev, const double* W,
     CK(cudaMemcpyAsync(Lv.R, R, n4 * sizeof(double), cudaMemcpyHostToDevice, s->st));
     MacroArgs ma = macro_args(s, lev, 0.0);
     CK(launch_macro_gamma(ma, Lv.Wn, Lv.gx, Lv.gy, Lv.idiag, s->st));
-    CK(launch_macro_sgs(ma, Lv.Wc, Lv.gx, Lv.gy, Lv.idiag, Lv.T, Lv.R, Lv.dW, s->st));
+    CK(macro_sgs(s, ma, Lv));
     CK(cudaMemcpyAsync(dW, Lv.dW, n4 * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    double flag = 0.0;
+    CK(cudaMemcpyAsync(&flag, s->rms_out + 5, sizeof flag, cudaMemcpyDeviceToHost, s->st));
     CK(cudaStreamSynchronize(s->st));
+    if (flag != 0.0) return fail(s, MIUGKS_ETIMEOUT, "a bounded wait of the macro sweep gave up");
     return MIUGKS_OK;
 }
 
