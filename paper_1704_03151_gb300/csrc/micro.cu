@@ -35,6 +35,34 @@ constexpr int kChainThreads = 128;    // 4 warps: one per SM sub-partition
 constexpr int kChainKptMax = 16;      // local velocities per thread in the chain kernel (at most)
 constexpr int kInteriorKc = 4;        // velocities per CTA in the wavefront kernel
 
+// asynchronous 4- or 8-byte global -> shared copies (LDGSTS), completed per commit group
+template <typename F>
+__device__ __forceinline__ void cp_async_elem(F* sdst, const F* gsrc)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    if constexpr (sizeof(F) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gsrc) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// wait until at most n (0..7) of this thread's most recent groups are pending
+__device__ __forceinline__ void cp_async_wait(int n)
+{
+    switch (n) {
+    case 0: asm volatile("cp.async.wait_group 0;\n" ::: "memory"); break;
+    case 1: asm volatile("cp.async.wait_group 1;\n" ::: "memory"); break;
+    case 2: asm volatile("cp.async.wait_group 2;\n" ::: "memory"); break;
+    case 3: asm volatile("cp.async.wait_group 3;\n" ::: "memory"); break;
+    case 4: asm volatile("cp.async.wait_group 4;\n" ::: "memory"); break;
+    case 5: asm volatile("cp.async.wait_group 5;\n" ::: "memory"); break;
+    case 6: asm volatile("cp.async.wait_group 6;\n" ::: "memory"); break;
+    default: asm volatile("cp.async.wait_group 7;\n" ::: "memory"); break;
+    }
+}
+
+constexpr int kWaveRingMax = 8;       // cells or diagonals of inputs in flight in the sweep kernels (at most)
+
 // (1/V) sum over the faces with u_n > 0 of u_n S = |u|/dx + |v|/dy
 template <typename F>
 __device__ __forceinline__ F geomD(const LevelDev& L, int i, int j, F u, F v)
@@ -222,28 +250,31 @@ __device__ __forceinline__ void cluster_sum(cg::cluster_group& cl, T (&v)[NR], T
 // xprev.  Every such cell has one boundary face on the sweep side, with a
 // fixed orientation along the line, so velocities split into
 //   outgoing (u_n >= 0 at that face): no ghost term, a recurrence along the
-//     line per velocity (phase A; their wall sums are reduced per cell inside
-//     each warp as they are produced);
+//     line per velocity (phase A, inputs streamed RA cells ahead through a
+//     ring of asynchronous shared-memory copies);
 //   incoming (u_n < 0): the ghost term needs the cell's wall density, a sum
-//     over its outgoing velocities (phase B: all cells at once, one cluster
-//     exchange, published in rho_out), or the mirrored outgoing value
-//     (symmetry).  With the ghost known, an incoming velocity of a line cell
-//     is an ordinary cell update, done by the wavefront kernel.
+//     over its outgoing velocities (phase A': per CTA, P threads per cell;
+//     phase B: over the cluster, one exchange; published in rho_out), or the
+//     mirrored outgoing value (symmetry).  With the ghost known, an incoming
+//     velocity of a line cell is an ordinary cell update, done by the
+//     wavefront kernel.
 // The arithmetic per cell is that of the serial sweep; only the order in which
 // independent velocities are visited changes.
 template <typename F, int kChainKpt>
 __device__ void chain_rest(cg::cluster_group& cl, const MicroArgs& M, const double* __restrict__ iZw,
                            const F* __restrict__ invD, const F* __restrict__ r, F* __restrict__ x, int pass,
-                           int line, int len, const int (&kk)[kChainKpt], const int (&mu)[kChainKpt],
-                           F (&xprev)[kChainKpt][2], F* __restrict__ rho_out)
+                           int line, int len, const int (&kk)[kChainKpt], F (&xprev)[kChainKpt][2],
+                           F* __restrict__ rho_out, F* ring, int RA, const int* lk, const F* lw, int nloc)
 {
-    __shared__ F part[kMaxLine * 4];          // [cell][warp] partial wall sums of this CTA
+    __shared__ F part[kMaxLine];              // wall sum of this CTA's velocities per cell
     __shared__ F rho_s[kMaxLine];
+    __shared__ F lm_nbS[kMaxLine], lm_itau[kMaxLine];
+    __shared__ F psum[kChainThreads];
     const LevelDev& L = M.L;
     const VelDev& Vg = M.V;
     const int nx = L.nx, ny = L.ny, nv = Vg.nv;
     const size_t nc = L.nc;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tid = threadIdx.x, B = blockDim.x;
     const int nb_axis = line == 0 ? 1 : 0, nb_sign = pass == 0 ? -1 : 1;
     // orientation of the line's boundary face (column lines: x-faces, row lines: y-faces)
     const int f_axis = line == 0 ? 0 : 1, f_out = pass == 0 ? -1 : 1;
@@ -254,63 +285,123 @@ __device__ void chain_rest(cg::cluster_group& cl, const MicroArgs& M, const doub
     auto face_bc = [&](int i, int j) {
         return f_axis == 0 ? L.fbx[j * (nx + 1) + (f_out < 0 ? 0 : nx)] : L.fby[(f_out < 0 ? 0 : ny) * nx + i];
     };
-    F uo_t[kChainKpt];
+    for (int st = tid; st < len; st += B) {
+        int i, j;
+        cell(st, i, j);
+        lm_nbS[st] = (F)(nb_axis == 0 ? L.rdx[i] : L.rdy[j]);
+        lm_itau[st] = (F)M.inv_tau[j * nx + i];
+    }
+    // per velocity: Dn = an * nbS (the neighbour along the line) and
+    // D = itau + gfix + gvar * nbS (|u|/dx + |v|/dy with the line's fixed spacing in gfix)
+    int ifx, jfx;
+    cell(0, ifx, jfx);
+    F an[kChainKpt], gfix[kChainKpt], gvar[kChainKpt];
+    bool outg[kChainKpt];
     #pragma unroll
     for (int t = 0; t < kChainKpt; ++t) {
-        int k = kk[t];
-        F un = k < 0 ? F(0) : (F)(f_axis == 0 ? Vg.u[k] : Vg.v[k]);
-        uo_t[t] = f_out < 0 ? -un : un;
+        const int k = kk[t];
+        const F u = k < 0 ? F(0) : (F)Vg.u[k], v = k < 0 ? F(0) : (F)Vg.v[k];
+        const F uo = f_out < 0 ? -(f_axis == 0 ? u : v) : (f_axis == 0 ? u : v);
+        outg[t] = k >= 0 && uo >= F(0);
+        const F un = nb_sign < 0 ? -(nb_axis == 0 ? u : v) : (nb_axis == 0 ? u : v);
+        an[t] = un < F(0) ? un : F(0);
+        gfix[t] = line == 0 ? fabs(u) * (F)L.rdx[ifx] : fabs(v) * (F)L.rdy[jfx];
+        gvar[t] = line == 0 ? fabs(v) : fabs(u);
     }
+    __syncthreads();
     // ---- phase A: outgoing velocities
     {
         F xp[kChainKpt][2];
         #pragma unroll
         for (int t = 0; t < kChainKpt; ++t) { xp[t][0] = xprev[t][0]; xp[t][1] = xprev[t][1]; }
+        const F* src = pass == 0 ? r : x;
+        const size_t rstride = (size_t)kChainKpt * 3 * B;
+        auto issue = [&](int st) {
+            if (st < len) {
+                int i, j;
+                cell(st, i, j);
+                const size_t c = (size_t)j * nx + i;
+                F* rs = ring + (size_t)(st % RA) * rstride;
+                #pragma unroll
+                for (int t = 0; t < kChainKpt; ++t) {
+                    if (!outg[t]) continue;
+                    const int k = kk[t];
+                    cp_async_elem(rs + (t * 3 + 0) * B + tid, invD + c * nv + k);
+                    cp_async_elem(rs + (t * 3 + 1) * B + tid, src + c * nv + k);
+                    cp_async_elem(rs + (t * 3 + 2) * B + tid, src + (nc + c) * nv + k);
+                }
+            }
+            cp_async_commit();
+        };
+        for (int q = 1; q < RA; ++q) issue(q);
         for (int st = 1; st < len; ++st) {
+            issue(st + RA - 1);
+            cp_async_wait(RA - 1);
+            const F* rs = ring + (size_t)(st % RA) * rstride;
             int i, j;
             cell(st, i, j);
-            const int c = j * nx + i;
-            const int bc = face_bc(i, j);
-            const int bt = M.bc[bc].type;
-            const F nbS = (F)(nb_axis == 0 ? L.rdx[i] : L.rdy[j]);
-            const F itau = (F)M.inv_tau[c];
-            F part_w = F(0);
+            const size_t c = (size_t)j * nx + i;
+            const F nbS = lm_nbS[st], itau = lm_itau[st];
             #pragma unroll
             for (int t = 0; t < kChainKpt; ++t) {
-                int k = kk[t];
-                if (k < 0 || uo_t[t] < F(0)) continue;
-                const F u = (F)Vg.u[k], v = (F)Vg.v[k];
-                const F Dn = Dface<F>(nb_axis, nb_sign, nbS, u, v);
-                const F id = invD[(size_t)c * nv + k];
-                const F D = pass == 1 ? itau + geomD<F>(L, i, j, u, v) : F(0);
+                if (!outg[t]) continue;
+                const int k = kk[t];
+                const F Dn = an[t] * nbS, id = rs[(t * 3) * B + tid];
+                const F D = pass == 1 ? itau + (gfix[t] + gvar[t] * nbS) : F(0);
                 #pragma unroll
                 for (int cp = 0; cp < 2; ++cp) {
-                    size_t idx = (cp * nc + c) * nv + k;
-                    F base = pass == 0 ? r[idx] - Dn * xp[t][cp] : D * x[idx] - Dn * xp[t][cp];
-                    F xv = base * id;
-                    x[idx] = xv;
+                    const F in = rs[(t * 3 + 1 + cp) * B + tid];
+                    const F base = pass == 0 ? in - Dn * xp[t][cp] : D * in - Dn * xp[t][cp];
+                    const F xv = base * id;
+                    x[(cp * nc + c) * nv + k] = xv;
                     xp[t][cp] = xv;
                 }
-                if (bt == BC_WALL && uo_t[t] > F(0)) part_w += (F)Vg.w[k] * uo_t[t] * xp[t][0];
             }
-            #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) part_w += __shfl_xor_sync(0xffffffffu, part_w, o);
-            if (lane == 0) part[st * 4 + warp] = part_w;
+        }
+        cp_async_wait(0);
+    }
+    __syncthreads();   // this CTA's outgoing values along the line are in x
+    // ---- phase A': wall sum over this CTA's outgoing velocities, P threads per cell
+    {
+        const int ncell = len - 1;
+        const int P = ncell >= B ? 1 : B / ncell, per = B / P;
+        for (int s0 = 0; s0 < ncell; s0 += per) {
+            const int st = 1 + s0 + tid / P, p = tid % P;
+            const bool mine = tid / P < per && st < len;
+            F sum = F(0);
+            if (mine) {
+                int i, j;
+                cell(st, i, j);
+                if (M.bc[face_bc(i, j)].type == BC_WALL) {
+                    const size_t c0 = (size_t)(j * nx + i) * nv;
+                    for (int q = p; q < nloc; q += P)
+                        if (lw[q] != F(0)) sum += lw[q] * x[c0 + lk[q]];
+                }
+            }
+            if (P == 1) {
+                if (mine) part[st] = sum;
+            } else {
+                psum[tid] = sum;
+                __syncthreads();
+                if (mine && p == 0) {
+                    F t = F(0);
+                    for (int q = 0; q < P; ++q) t += psum[tid + q];
+                    part[st] = t;
+                }
+                __syncthreads();
+            }
         }
     }
     cl.sync();
     // ---- phase B: wall density of every cell of the line (fixed summation order)
-    for (int st = 1 + threadIdx.x; st < len; st += blockDim.x) {
+    for (int st = 1 + tid; st < len; st += B) {
         int i, j;
         cell(st, i, j);
         const int bc = face_bc(i, j);
         F rho = F(0);
         if (M.bc[bc].type == BC_WALL) {
             F sum = F(0);
-            for (int rk = 0; rk < kChainCluster; ++rk) {
-                const F* pr = cl.map_shared_rank(part, rk);
-                for (int w = 0; w < 4; ++w) sum += pr[st * 4 + w];
-            }
+            for (int rk = 0; rk < kChainCluster; ++rk) sum += cl.map_shared_rank(part, rk)[st];
             rho = -sum * (F)iZw[bc * 4 + f_axis * 2 + (f_out > 0)];
         }
         rho_s[st] = rho;
@@ -318,13 +409,13 @@ __device__ void chain_rest(cg::cluster_group& cl, const MicroArgs& M, const doub
     __syncthreads();
     // the incoming velocities of cells 1.. are finished by the wavefront kernel
     if (cl.block_rank() == 0)
-        for (int st = threadIdx.x; st < len; st += blockDim.x) rho_out[st] = st == 0 ? F(0) : rho_s[st];
+        for (int st = tid; st < len; st += B) rho_out[st] = st == 0 ? F(0) : rho_s[st];
 }
 
 template <typename F, int kChainKpt>
 __global__ void __cluster_dims__(kChainCluster, 1, 1) __launch_bounds__(kChainThreads)
 k_sgs_chain(MicroArgs M, const double* __restrict__ Zw, const F* __restrict__ invD, const F* __restrict__ r,
-            F* __restrict__ x, const F* __restrict__ xcorner, F* __restrict__ rho_lines, int pass)
+            F* __restrict__ x, const F* __restrict__ xcorner, F* __restrict__ rho_lines, int pass, int RA)
 {
     const double* __restrict__ iZw = Zw + 4 * kMaxBcs;          // reciprocals of the wall normalisations
     __shared__ F slots[2 * 4 * 4];
@@ -529,38 +620,31 @@ k_sgs_chain(MicroArgs M, const double* __restrict__ Zw, const F* __restrict__ in
             }
         }
     }
-    if (len > 1) chain_rest<F, kChainKpt>(cl, M, iZw, invD, r, x, pass, line, len, kk, mu, xprev,
-                                          rho_lines + line * kMaxLine);
+    if (len > 1) {
+        // this CTA's velocities with their outgoing wall weights w u_n (0 when not outgoing)
+        F* lw = xsm + 2 * nloc;
+        F* ring = lw + nloc;
+        int* lk = reinterpret_cast<int*>(ring + (size_t)RA * kChainKpt * 3 * blockDim.x);
+        const int f_axis = line == 0 ? 0 : 1;
+        #pragma unroll
+        for (int t = 0; t < kChainKpt; ++t) {
+            const int m = threadIdx.x + t * blockDim.x;
+            if (m >= nloc) continue;
+            const int k = kk[t];
+            F wuo = F(0);
+            if (k >= 0) {
+                const F un = (F)(f_axis == 0 ? Vg.u[k] : Vg.v[k]), uo = pass == 0 ? -un : un;
+                wuo = uo > F(0) ? (F)Vg.w[k] * uo : F(0);
+            }
+            lk[m] = k;
+            lw[m] = wuo;
+        }
+        chain_rest<F, kChainKpt>(cl, M, iZw, invD, r, x, pass, line, len, kk, xprev, rho_lines + line * kMaxLine,
+                                 ring, RA, lk, lw, nloc);
+    }
     cl.sync();   // keep every CTA's shared memory alive until all remote reads are done
 }
 
-// asynchronous 4- or 8-byte global -> shared copies (LDGSTS), completed per commit group
-template <typename F>
-__device__ __forceinline__ void cp_async_elem(F* sdst, const F* gsrc)
-{
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
-    if constexpr (sizeof(F) == 8)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gsrc) : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-// wait until at most n (0..7) of this thread's most recent groups are pending
-__device__ __forceinline__ void cp_async_wait(int n)
-{
-    switch (n) {
-    case 0: asm volatile("cp.async.wait_group 0;\n" ::: "memory"); break;
-    case 1: asm volatile("cp.async.wait_group 1;\n" ::: "memory"); break;
-    case 2: asm volatile("cp.async.wait_group 2;\n" ::: "memory"); break;
-    case 3: asm volatile("cp.async.wait_group 3;\n" ::: "memory"); break;
-    case 4: asm volatile("cp.async.wait_group 4;\n" ::: "memory"); break;
-    case 5: asm volatile("cp.async.wait_group 5;\n" ::: "memory"); break;
-    case 6: asm volatile("cp.async.wait_group 6;\n" ::: "memory"); break;
-    default: asm volatile("cp.async.wait_group 7;\n" ::: "memory"); break;
-    }
-}
-
-constexpr int kWaveRingMax = 8;       // diagonals in flight in the wavefront kernel (at most)
 
 // One sweep over every cell for the kInteriorKc velocities of this CTA, in
 // anti-diagonal order.  The corner cell and the outgoing velocities of the
@@ -715,13 +799,17 @@ cudaError_t launch_micro_sgs(const MicroArgs& m, const double* Zw, const F* invD
     const int nloc = ((ngroups + kChainCluster - 1) / kChainCluster) * 2 * m.V.nvv;
     if (nloc > kChainKptMax * kChainThreads) return cudaErrorInvalidValue;
     if (m.L.nx > kMaxLine || m.L.ny > kMaxLine) return cudaErrorInvalidValue;
-    size_t smem = sizeof(F) * 2 * nloc;
     const int kpt = (nloc + kChainThreads - 1) / kChainThreads;
-    void (*chain)(MicroArgs, const double*, const F*, const F*, F*, const F*, F*, int) =
+    const int kpt_t = kpt <= 1 ? 1 : kpt <= 2 ? 2 : kpt <= 4 ? 4 : kpt <= 8 ? 8 : 16;   // instantiated
+    const size_t rslot = sizeof(F) * (size_t)kpt_t * 3 * kChainThreads;
+    int RA = (int)((96 * 1024) / rslot);
+    RA = RA < 1 ? 1 : (RA > kWaveRingMax ? kWaveRingMax : RA);
+    size_t smem = sizeof(F) * 2 * nloc + (sizeof(F) + sizeof(int)) * (size_t)nloc + rslot * RA;
+    void (*chain)(MicroArgs, const double*, const F*, const F*, F*, const F*, F*, int, int) =
         kpt <= 1 ? k_sgs_chain<F, 1> : kpt <= 2 ? k_sgs_chain<F, 2> : kpt <= 4 ? k_sgs_chain<F, 4>
                  : kpt <= 8 ? k_sgs_chain<F, 8> : k_sgs_chain<F, 16>;
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(chain, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+        cudaError_t e = cudaFuncSetAttribute(chain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     const int nblk = (m.V.nv + kInteriorKc - 1) / kInteriorKc;
@@ -753,7 +841,7 @@ cudaError_t launch_micro_sgs(const MicroArgs& m, const double* Zw, const F* invD
                                                 cudaMemcpyDeviceToDevice, st);
                 if (e != cudaSuccess) return e;
             }
-        chain<<<2 * kChainCluster, kChainThreads, smem, st>>>(m, Zw, invD, r, x, xcorner, rho_lines, pass);
+        chain<<<2 * kChainCluster, kChainThreads, smem, st>>>(m, Zw, invD, r, x, xcorner, rho_lines, pass, RA);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         wave<<<nblk, nthr, wsmem, st>>>(m, invD, r, x, rho_lines, pass, R);
