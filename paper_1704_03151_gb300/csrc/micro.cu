@@ -646,148 +646,224 @@ k_sgs_chain(MicroArgs M, const double* __restrict__ Zw, const F* __restrict__ in
 }
 
 
-// One sweep over every cell for the kInteriorKc velocities of this CTA, in
-// anti-diagonal order.  The corner cell and the outgoing velocities of the
-// boundary-line cells were finished by k_sgs_chain (their values are read);
-// every other update is (forward) x = (b - D_W x_W - D_S x_S) / D, with b the
-// residual minus the known ghost term, or (backward) x = b - (D_E x_E + D_N
-// x_N) / D, with b the forward value (minus the ghost term over D).  Values of
-// the previous diagonal stay in shared memory.  The inputs of the next R - 1
-// diagonals are in flight as asynchronous copies into a ring of R shared
-// buffers, so the per-diagonal path only touches shared memory; the ghost data
-// of the two boundary lines (wall coefficient times wall density, or the
-// mirrored value) is gathered once at the start.
-template <typename F, int EPT>
-__global__ void __launch_bounds__(256) k_sgs_wave(MicroArgs M, const F* __restrict__ invD, const F* __restrict__ r,
-                                                  F* __restrict__ x, const F* __restrict__ rho_lines, int pass, int R)
+// asynchronous 16-byte copy (both addresses 16-byte aligned)
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc)
 {
-    extern __shared__ double sraw[];
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gsrc) : "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait_n()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// four consecutive values through 16-byte accesses (16-byte aligned for float, 32 for double)
+__device__ __forceinline__ void ld4(const float* p, float (&v)[4])
+{
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&v)[4])
+{
+    const double2 t0 = *reinterpret_cast<const double2*>(p), t1 = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = t0.x; v[1] = t0.y; v[2] = t1.x; v[3] = t1.y;
+}
+__device__ __forceinline__ void st4(float* p, const float (&v)[4])
+{
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double* p, const double (&v)[4])
+{
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+    *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
+}
+
+// the kInteriorKc values of consecutive velocities at gsrc (nk of them exist) into sdst
+template <typename F, bool VEC>
+__device__ __forceinline__ void cp_async_k4(F* sdst, const F* gsrc, int nk)
+{
+    if constexpr (VEC) {
+        cp_async16(sdst, gsrc);
+        if constexpr (sizeof(F) == 8)
+            if (nk > 2) cp_async16(sdst + 2, gsrc + 2);
+    } else {
+        #pragma unroll
+        for (int q = 0; q < kInteriorKc; ++q)
+            if (q < nk) cp_async_elem(sdst + q, gsrc + q);
+    }
+}
+
+// One sweep over every cell for the kInteriorKc velocities of this CTA, in
+// anti-diagonal order, one thread per cell of the diagonal handling the
+// 2 x kInteriorKc values (G and H, consecutive velocities) of its cell.
+// Ordinary update: (forward) x = (b - D_W x_W - D_S x_S) / D with b the
+// residual, (backward) x = b - (D_E x_E + D_N x_N) / D with b the forward
+// value.  The corner cell and the outgoing velocities of the boundary-line
+// cells were finished by k_sgs_chain; for the incoming ones the ghost term is
+// known, so it is folded into b (and, at an outflow face, 1/D) once, at the
+// start.  Values of the previous diagonal stay in shared memory; the inputs of
+// the next R - 1 diagonals are in flight as asynchronous copies into a ring of
+// R shared buffers, so the per-diagonal path only touches shared memory.
+template <typename F, int R, bool VEC>
+__global__ void __launch_bounds__(512) k_sgs_wave(MicroArgs M, const F* __restrict__ invD, const F* __restrict__ r,
+                                                  F* __restrict__ x, const F* __restrict__ rho_lines, int pass)
+{
+    extern __shared__ __align__(16) double sraw[];
+    constexpr int K = kInteriorKc, W = 2 * K;
     const LevelDev& L = M.L;
     const VelDev& Vg = M.V;
     const int nx = L.nx, ny = L.ny, nv = Vg.nv;
     const size_t nc = L.nc;
-    const int k0 = blockIdx.x * kInteriorKc;
-    constexpr int W = 2 * kInteriorKc;                  // elements per cell
+    const int B = blockDim.x, tid = threadIdx.x;
+    const int k0 = blockIdx.x * K, nk = min(K, nv - k0);
     const int nd = nx + ny - 1, nl = nx + ny;
-    const int per = EPT * blockDim.x;                   // element slots of one diagonal
     F* sx = reinterpret_cast<F*>(sraw);                 // [2][nx][W] values of the previous diagonal
-    F* ring = sx + 2 * (size_t)nx * W;                  // [R][2][per] inputs (value, 1/D) of upcoming diagonals
-    F* gtab = ring + (size_t)R * 2 * per;               // [nl][W] ghost data of the line cells (times Db)
-    F* litau = gtab + (size_t)nl * W;                   // [nl] their collision frequencies
-    F* srdx = litau + nl;                               // [nx] 1/dx
+    F* ring = sx + 2 * (size_t)nx * W;                  // [R][3][B][K] b (G, H) and 1/D of upcoming diagonals
+    F* lineb = ring + (size_t)R * 3 * B * K;            // [nl][W] folded b of the line cells
+    F* liv = lineb + (size_t)nl * W;                    // [nl][K] their 1/D
+    F* srdx = liv + (size_t)nl * K;                     // [nx] 1/dx
     F* srdy = srdx + nx;                                // [ny] 1/dy
-    int* lty = reinterpret_cast<int*>(srdy + ny);       // [nl] boundary types of the line cells
     const int ib = pass == 0 ? 0 : nx - 1, jb = pass == 0 ? 0 : ny - 1;   // boundary column and row of the sweep
     const int fout = pass == 0 ? -1 : 1;
     const F* src = pass == 0 ? r : x;
-    // per thread: fixed component and velocity (the element index modulo W)
-    const int rem = threadIdx.x % W, cp = rem / kInteriorKc, kk = rem - cp * kInteriorKc, k = k0 + kk;
-    const bool kok = k < nv;
-    const F u = kok ? (F)Vg.u[k] : F(0), v = kok ? (F)Vg.v[k] : F(0);
-    const F au = fabs(u), av = fabs(v);
-    const F uo_col = fout < 0 ? -u : u, uo_row = fout < 0 ? -v : v;    // u_n at the line faces
-    auto loaded = [&](int i, int j) {                   // finished by the boundary-line kernel
-        const bool on_col = i == ib, on_row = j == jb;
-        return (on_col && on_row) || (on_col && uo_col >= F(0)) || (on_row && uo_row >= F(0));
-    };
     auto issue = [&](int dd) {
         if (dd < nd) {
             const int d = pass == 0 ? dd : nd - 1 - dd;
-            const int ilo = max(0, d - (ny - 1)), ihi = min(nx - 1, d), ncell = ihi - ilo + 1;
-            F* ra = ring + (size_t)(dd % R) * 2 * per;
-            #pragma unroll
-            for (int m = 0; m < EPT; ++m) {
-                const int q = threadIdx.x + m * blockDim.x, slot = q / W;
-                if (slot >= ncell || !kok) continue;
-                const int i = ilo + slot, j = d - i;
-                const size_t id = (size_t)(j * nx + i) * nv + k, xid = cp * nc * nv + id;
-                if (loaded(i, j)) {
-                    cp_async_elem(ra + q, x + xid);
-                } else {
-                    cp_async_elem(ra + q, src + xid);
-                    cp_async_elem(ra + per + q, invD + id);
-                }
+            const int ilo = max(0, d - (ny - 1)), ncell = min(nx - 1, d) - ilo + 1;
+            if (tid < ncell) {
+                const int i = ilo + tid, j = d - i;
+                const size_t e = ((size_t)j * nx + i) * nv + k0;
+                F* ra = ring + ((size_t)(dd % R) * 3 * B + tid) * K;
+                cp_async_k4<F, VEC>(ra, src + e, nk);
+                cp_async_k4<F, VEC>(ra + (size_t)B * K, src + nc * nv + e, nk);
+                cp_async_k4<F, VEC>(ra + (size_t)2 * B * K, invD + e, nk);
             }
         }
         cp_async_commit();
     };
-    for (int dd = 0; dd < R - 1; ++dd) issue(dd);
-    // boundary data of the two lines (column: e = st, row: e = ny + st)
-    for (int e = threadIdx.x; e < nl; e += blockDim.x) {
+    if constexpr (R > 1)
+        for (int dd = 0; dd < R - 1; ++dd) issue(dd);
+    // prologue: diagonal buffers, spacings, and the folded inputs of the two lines
+    // (column: e = st, row: e = ny + st)
+    for (int q = tid; q < 2 * nx * W; q += B) sx[q] = F(0);
+    for (int q = tid; q < nx; q += B) srdx[q] = (F)L.rdx[q];
+    for (int q = tid; q < ny; q += B) srdy[q] = (F)L.rdy[q];
+    for (int q = tid; q < nl * W; q += B) {
+        const int e = q / W, rem = q - e * W, cp = rem / K, kk = rem - cp * K, kq = k0 + kk;
         const int line = e < ny ? 0 : 1, st = line == 0 ? e : e - ny;
         const int i = line == 0 ? ib : (pass == 0 ? st : nx - 1 - st);
         const int j = line == 0 ? (pass == 0 ? st : ny - 1 - st) : jb;
-        const int c = j * nx + i;
-        const int bc = line == 0 ? L.fbx[j * (nx + 1) + (fout < 0 ? 0 : nx)] : L.fby[(fout < 0 ? 0 : ny) * nx + i];
-        const BcDev B = M.bc[bc];
-        const F rho = rho_lines[line * kMaxLine + st];
-        lty[e] = B.type;
-        litau[e] = (F)M.inv_tau[c];
-        for (int q = 0; q < W; ++q) {
-            const int qc = q / kInteriorKc, kq = k0 + q - qc * kInteriorKc;
-            F g = F(0);
-            const F un = kq < nv ? (F)(line == 0 ? Vg.u[kq] : Vg.v[kq]) : F(0);
-            const bool incoming = kq < nv && (fout < 0 ? -un : un) < F(0);
-            if (incoming && B.type == BC_WALL) {
-                g = (F)(M.Cw[(size_t)bc * nv + kq] * (qc == 0 ? 1.0 : kKint * B.t / 4.0)) * rho;
-            } else if (incoming && B.type == BC_SYMMETRY) {
-                const int a2 = kq / Vg.nvv, b2 = kq - a2 * Vg.nvv;
-                const int km = line == 0 ? (Vg.nu - 1 - a2) * Vg.nvv + b2 : a2 * Vg.nvv + (Vg.nvv - 1 - b2);
-                g = x[(qc * nc + c) * nv + km];         // an outgoing velocity: already final
+        F val = F(0), iv = F(1);
+        if (kq < nv) {
+            const int c = j * nx + i;
+            const size_t id = (size_t)c * nv + kq, xid = cp * nc * nv + id;
+            const F u = (F)Vg.u[kq], v = (F)Vg.v[kq];
+            const F uo = fout < 0 ? -(line == 0 ? u : v) : (line == 0 ? u : v);   // u_n at the line face
+            if (st == 0 || uo >= F(0)) {
+                val = x[xid];                           // finished by the boundary-line kernel
+            } else {
+                const int bc = line == 0 ? L.fbx[j * (nx + 1) + (fout < 0 ? 0 : nx)] : L.fby[(fout < 0 ? 0 : ny) * nx + i];
+                const BcDev Bc = M.bc[bc];
+                const F Db = uo * (line == 0 ? (F)L.rdx[i] : (F)L.rdy[j]);
+                F g = F(0);
+                if (Bc.type == BC_WALL) {
+                    g = Db * ((F)(M.Cw[(size_t)bc * nv + kq] * (cp == 0 ? 1.0 : kKint * Bc.t / 4.0)) *
+                              rho_lines[line * kMaxLine + st]);
+                } else if (Bc.type == BC_SYMMETRY) {
+                    const int a2 = kq / Vg.nvv, b2 = kq - a2 * Vg.nvv;
+                    const int km = line == 0 ? (Vg.nu - 1 - a2) * Vg.nvv + b2 : a2 * Vg.nvv + (Vg.nvv - 1 - b2);
+                    g = Db * x[cp * nc * nv + (size_t)c * nv + km];   // an outgoing velocity: final
+                }
+                const F D = (F)M.inv_tau[c] + geomD<F>(L, i, j, u, v);
+                iv = Bc.type == BC_OUTFLOW ? recip(D + Db) : invD[id];
+                val = pass == 0 ? r[xid] - g : (D * x[xid] - g) * iv;
             }
-            gtab[(size_t)e * W + q] = g;
         }
+        lineb[q] = val;
+        if (cp == 0) liv[e * K + kk] = iv;
     }
-    for (int e = threadIdx.x; e < nx; e += blockDim.x) srdx[e] = (F)L.rdx[e];
-    for (int e = threadIdx.x; e < ny; e += blockDim.x) srdy[e] = (F)L.rdy[e];
+    // per velocity: neighbour coefficients (zero where the upwind neighbour is on the other side)
+    // and which velocities leave through the column / row line faces
+    F cu[K], cv[K];
+    unsigned outc = 0, outr = 0;
+    #pragma unroll
+    for (int kk = 0; kk < K; ++kk) {
+        const int kq = k0 + kk;
+        const F u = kq < nv ? (F)Vg.u[kq] : F(0), v = kq < nv ? (F)Vg.v[kq] : F(0);
+        cu[kk] = pass == 0 ? (u > F(0) ? -u : F(0)) : (u < F(0) ? u : F(0));
+        cv[kk] = pass == 0 ? (v > F(0) ? -v : F(0)) : (v < F(0) ? v : F(0));
+        if ((fout < 0 ? -u : u) >= F(0)) outc |= 1u << kk;
+        if ((fout < 0 ? -v : v) >= F(0)) outr |= 1u << kk;
+    }
+    const int xo = pass == 0 ? -1 : 1;                  // x neighbour: i - 1 (forward) or i + 1
     __syncthreads();
     for (int dd = 0; dd < nd; ++dd) {
-        issue(dd + R - 1);
-        cp_async_wait(R - 1);
-        const int d = pass == 0 ? dd : nd - 1 - dd;
-        const int ilo = max(0, d - (ny - 1)), ihi = min(nx - 1, d);
-        const int ncell = ihi - ilo + 1;
-        const F* ra = ring + (size_t)(dd % R) * 2 * per;
-        F* prev = sx + (size_t)((dd + 1) & 1) * nx * W;
-        F* cur = sx + (size_t)(dd & 1) * nx * W;
-        #pragma unroll
-        for (int m = 0; m < EPT; ++m) {
-            const int q = threadIdx.x + m * blockDim.x, slot = q / W;
-            if (slot >= ncell || !kok) continue;
-            const int i = ilo + slot, j = d - i;
-            const bool on_col = i == ib, on_row = j == jb;
-            F res;
-            if (loaded(i, j)) {
-                res = ra[q];
-            } else {
-                F bv = ra[q], iv = ra[per + q];
-                if (on_col || on_row) {
-                    // incoming velocity at the line face: known ghost term
-                    const int e = on_col ? (pass == 0 ? j : ny - 1 - j) : ny + (pass == 0 ? i : nx - 1 - i);
-                    const int ty = lty[e];
-                    const F Db = on_col ? uo_col * srdx[i] : uo_row * srdy[j];
-                    const F g = Db * gtab[(size_t)e * W + rem];
-                    const F D = litau[e] + (au * srdx[i] + av * srdy[j]);
-                    if (ty == BC_OUTFLOW) iv = recip(D + Db);
-                    bv = pass == 0 ? bv - g : (D * bv - g) * iv;
-                }
-                F y = F(0);
-                if (pass == 0) {
-                    if (i > 0 && u > F(0)) y += -u * srdx[i] * prev[(i - 1) * W + rem];
-                    if (j > 0 && v > F(0)) y += -v * srdy[j] * prev[i * W + rem];
-                    res = (bv - y) * iv;
-                } else {
-                    if (i < nx - 1 && u < F(0)) y += u * srdx[i] * prev[(i + 1) * W + rem];
-                    if (j < ny - 1 && v < F(0)) y += v * srdy[j] * prev[i * W + rem];
-                    res = bv - y * iv;
-                }
-                x[cp * nc * nv + (size_t)(j * nx + i) * nv + k] = res;
-            }
-            cur[i * W + rem] = res;
+        if constexpr (R == 1) {
+            issue(dd);
+            cp_async_wait_n<0>();
+        } else {
+            cp_async_wait_n<R - 2>();
         }
+        const int d = pass == 0 ? dd : nd - 1 - dd;
+        const int ilo = max(0, d - (ny - 1)), ncell = min(nx - 1, d) - ilo + 1;
+        const F* prev = sx + (size_t)((dd + 1) & 1) * nx * W;
+        F* cur = sx + (size_t)(dd & 1) * nx * W;
+        if (tid < ncell) {
+            const int i = ilo + tid, j = d - i;
+            const F* ra = ring + ((size_t)(dd % R) * 3 * B + tid) * K;
+            static_assert(K == 4, "vector accesses assume four velocities per CTA");
+            F a[2][K], iv[K], pwv[2][K], psv[2][K];
+            ld4(ra, a[0]);
+            ld4(ra + (size_t)B * K, a[1]);
+            ld4(ra + (size_t)2 * B * K, iv);
+            const bool hx = i != ib, hy = j != jb;
+            const F fx = hx ? srdx[i] : F(0), fy = hy ? srdy[j] : F(0);
+            const F* pw = prev + (size_t)(hx ? i + xo : i) * W;
+            const F* ps = prev + (size_t)i * W;
+            ld4(pw, pwv[0]);
+            ld4(pw + K, pwv[1]);
+            ld4(ps, psv[0]);
+            ld4(ps + K, psv[1]);
+            unsigned ld = 0;
+            if (!(hx && hy)) {                          // a boundary-line cell
+                const int e = !hx ? (pass == 0 ? j : ny - 1 - j) : ny + (pass == 0 ? i : nx - 1 - i);
+                ld = !hx && !hy ? 0xFu : (!hx ? outc : outr);
+                ld4(lineb + (size_t)e * W, a[0]);
+                ld4(lineb + (size_t)e * W + K, a[1]);
+                ld4(liv + (size_t)e * K, iv);
+            }
+            F res[2][K];
+            #pragma unroll
+            for (int cp = 0; cp < 2; ++cp)
+                #pragma unroll
+                for (int kk = 0; kk < K; ++kk) {
+                    const F y = cu[kk] * fx * pwv[cp][kk] + cv[kk] * fy * psv[cp][kk];
+                    const F rv = pass == 0 ? (a[cp][kk] - y) * iv[kk] : a[cp][kk] - y * iv[kk];
+                    res[cp][kk] = (ld >> kk) & 1u ? a[cp][kk] : rv;
+                }
+            #pragma unroll
+            for (int cp = 0; cp < 2; ++cp) {
+                F* xd = x + (cp * nc + (size_t)j * nx + i) * nv + k0;
+                st4(cur + (size_t)i * W + cp * K, res[cp]);
+                if constexpr (VEC) {
+                    if (nk == K) {
+                        st4(xd, res[cp]);
+                    } else {                            // double, nv = 2 mod 4: the last two values do not exist
+                        xd[0] = res[cp][0];
+                        xd[1] = res[cp][1];
+                    }
+                } else {
+                    #pragma unroll
+                    for (int kk = 0; kk < K; ++kk)
+                        if (kk < nk) xd[kk] = res[cp][kk];
+                }
+            }
+        }
+        if constexpr (R > 1) issue(dd + R - 1);
         __syncthreads();
     }
-    cp_async_wait(0);
+    cp_async_wait_n<0>();
 }
 
 template <typename F>
@@ -814,20 +890,18 @@ cudaError_t launch_micro_sgs(const MicroArgs& m, const double* Zw, const F* invD
     }
     const int nblk = (m.V.nv + kInteriorKc - 1) / kInteriorKc;
     const int maxdiag = m.L.nx < m.L.ny ? m.L.nx : m.L.ny;
-    const int nthr = maxdiag * 2 * kInteriorKc <= 128 * 16 ? 128 : 256;
-    const int ept = (maxdiag * 2 * kInteriorKc + nthr - 1) / nthr;
-    if (ept > 16) return cudaErrorInvalidValue;
-    void (*wave)(MicroArgs, const F*, const F*, F*, const F*, int, int) =
-        ept <= 4 ? k_sgs_wave<F, 4> : ept <= 8 ? k_sgs_wave<F, 8> : k_sgs_wave<F, 16>;
+    const int nthr = ((maxdiag + 31) / 32) * 32;       // one thread per cell of the longest diagonal
+    const bool vec = (m.V.nv * sizeof(F)) % 16 == 0;
     const size_t nl = (size_t)m.L.nx + m.L.ny;
-    const size_t fixed = sizeof(F) * (2 * (size_t)m.L.nx * 2 * kInteriorKc + nl * (2 * kInteriorKc + 1) + nl)
-                       + sizeof(int) * nl;
-    const int ept_t = ept <= 4 ? 4 : ept <= 8 ? 8 : 16;      // the instantiated elements per thread
-    const size_t slot = sizeof(F) * 2 * (size_t)ept_t * nthr;
+    const size_t fixed = sizeof(F) * (2 * (size_t)m.L.nx * 2 * kInteriorKc + nl * 3 * kInteriorKc + nl);
+    const size_t slot = sizeof(F) * 3 * (size_t)nthr * kInteriorKc;
     constexpr size_t kSmemMax = 227 * 1024;
     if (fixed + slot > kSmemMax) return cudaErrorInvalidValue;
     const size_t rfit = (kSmemMax - fixed) / slot;
-    const int R = rfit < (size_t)kWaveRingMax ? (int)rfit : kWaveRingMax;
+    const int R = rfit >= 8 ? 8 : rfit >= 4 ? 4 : rfit >= 2 ? 2 : 1;
+    void (*wave)(MicroArgs, const F*, const F*, F*, const F*, int);
+    if (vec) wave = R == 8 ? k_sgs_wave<F, 8, true> : R == 4 ? k_sgs_wave<F, 4, true> : R == 2 ? k_sgs_wave<F, 2, true> : k_sgs_wave<F, 1, true>;
+    else wave = R == 8 ? k_sgs_wave<F, 8, false> : R == 4 ? k_sgs_wave<F, 4, false> : R == 2 ? k_sgs_wave<F, 2, false> : k_sgs_wave<F, 1, false>;
     const size_t wsmem = fixed + slot * R;
     if (wsmem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(wave, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem);
@@ -844,7 +918,7 @@ cudaError_t launch_micro_sgs(const MicroArgs& m, const double* Zw, const F* invD
         chain<<<2 * kChainCluster, kChainThreads, smem, st>>>(m, Zw, invD, r, x, xcorner, rho_lines, pass, RA);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        wave<<<nblk, nthr, wsmem, st>>>(m, invD, r, x, rho_lines, pass, R);
+        wave<<<nblk, nthr, wsmem, st>>>(m, invD, r, x, rho_lines, pass);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
