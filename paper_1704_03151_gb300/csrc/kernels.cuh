@@ -66,7 +66,9 @@ template <typename F>
 cudaError_t launch_coarse_coeffs(const MicroArgs& m, GasDev gas, const double* Wt, double dtn_inv,
                                  double* inv_tau, F* invD, cudaStream_t st);
 // one symmetric Gauss-Seidel pass: x = SGS(r).  Zw[b*4 + axis*2 + (outsign>0)] = sum over the
-// incoming velocities of w u_n C_k of wall BC b; xcorner: scratch of 2*nv values
+// incoming velocities of w u_n C_k of wall BC b; xcorner: scratch of micro_scratch_elems(nv, nx + ny)
+// values (nx + ny of the finest level)
+size_t micro_scratch_elems(int nv, int nl);
 template <typename F>
 cudaError_t launch_micro_sgs(const MicroArgs& m, const double* Zw, const F* invD, const F* r, F* x, F* xcorner,
                              cudaStream_t st);

@@ -694,20 +694,81 @@ __device__ __forceinline__ void cp_async_k4(F* sdst, const F* gsrc, int nk)
     }
 }
 
+// Inputs of the boundary-line cells for k_sgs_wave, after k_sgs_chain: per
+// cell of the two lines (column: e = st, row: e = ny + st) and velocity, the
+// right-hand side b of G and H and 1/D, laid out as the wavefront's ring
+// entries, fold[blk][e][3][kInteriorKc] (blk = k / kInteriorKc).  Outgoing
+// velocities and the corner carry their final value (applied as is).
+// Incoming ones carry the ghost term folded in: forward b = r - g, backward
+// b = (D x - g) / D, with g = Db C rho_s (wall) or Db x_mirror (symmetry), and
+// 1/(D + Db) in place of 1/D at an outflow face.
+template <typename F>
+__global__ void k_line_fold(MicroArgs M, const F* __restrict__ invD, const F* __restrict__ r,
+                            const F* __restrict__ x, const F* __restrict__ rho_lines, F* __restrict__ fold, int pass)
+{
+    constexpr int K = kInteriorKc;
+    const LevelDev& L = M.L;
+    const VelDev& Vg = M.V;
+    const int nx = L.nx, ny = L.ny, nv = Vg.nv, nl = nx + ny;
+    const size_t nc = L.nc;
+    const int nblk = (nv + K - 1) / K;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nblk * nl * K) return;
+    const int kk = t % K, e = (t / K) % nl, blk = t / (K * nl), kq = blk * K + kk;
+    const int ib = pass == 0 ? 0 : nx - 1, jb = pass == 0 ? 0 : ny - 1, fout = pass == 0 ? -1 : 1;
+    const int line = e < ny ? 0 : 1, st = line == 0 ? e : e - ny;
+    const int i = line == 0 ? ib : (pass == 0 ? st : nx - 1 - st);
+    const int j = line == 0 ? (pass == 0 ? st : ny - 1 - st) : jb;
+    F b[2] = {F(0), F(0)}, iv = F(1);
+    if (kq < nv) {
+        const int c = j * nx + i;
+        const size_t id = (size_t)c * nv + kq;
+        const F u = (F)Vg.u[kq], v = (F)Vg.v[kq];
+        const F uo = fout < 0 ? -(line == 0 ? u : v) : (line == 0 ? u : v);   // u_n at the line face
+        if (st == 0 || uo >= F(0)) {
+            b[0] = x[id];
+            b[1] = x[nc * nv + id];
+        } else {
+            const int bc = line == 0 ? L.fbx[j * (nx + 1) + (fout < 0 ? 0 : nx)] : L.fby[(fout < 0 ? 0 : ny) * nx + i];
+            const BcDev Bc = M.bc[bc];
+            const F Db = uo * (line == 0 ? (F)L.rdx[i] : (F)L.rdy[j]);
+            const F D = (F)M.inv_tau[c] + geomD<F>(L, i, j, u, v);
+            iv = Bc.type == BC_OUTFLOW ? recip(D + Db) : invD[id];
+            int km = 0;
+            if (Bc.type == BC_SYMMETRY) {
+                const int a2 = kq / Vg.nvv, b2 = kq - a2 * Vg.nvv;
+                km = line == 0 ? (Vg.nu - 1 - a2) * Vg.nvv + b2 : a2 * Vg.nvv + (Vg.nvv - 1 - b2);
+            }
+            #pragma unroll
+            for (int cp = 0; cp < 2; ++cp) {
+                F g = F(0);
+                if (Bc.type == BC_WALL)
+                    g = Db * ((F)(M.Cw[(size_t)bc * nv + kq] * (cp == 0 ? 1.0 : kKint * Bc.t / 4.0)) *
+                              rho_lines[line * kMaxLine + st]);
+                else if (Bc.type == BC_SYMMETRY)
+                    g = Db * x[cp * nc * nv + (size_t)c * nv + km];   // an outgoing velocity: final
+                b[cp] = pass == 0 ? r[cp * nc * nv + id] - g : (D * x[cp * nc * nv + id] - g) * iv;
+            }
+        }
+    }
+    F* o = fold + ((size_t)(blk * nl + e) * 3) * K + kk;
+    o[0] = b[0];
+    o[K] = b[1];
+    o[2 * K] = iv;
+}
+
 // One sweep over every cell for the kInteriorKc velocities of this CTA, in
 // anti-diagonal order, one thread per cell of the diagonal handling the
 // 2 x kInteriorKc values (G and H, consecutive velocities) of its cell.
 // Ordinary update: (forward) x = (b - D_W x_W - D_S x_S) / D with b the
 // residual, (backward) x = b - (D_E x_E + D_N x_N) / D with b the forward
-// value.  The corner cell and the outgoing velocities of the boundary-line
-// cells were finished by k_sgs_chain; for the incoming ones the ghost term is
-// known, so it is folded into b (and, at an outflow face, 1/D) once, at the
-// start.  Values of the previous diagonal stay in shared memory; the inputs of
-// the next R - 1 diagonals are in flight as asynchronous copies into a ring of
-// R shared buffers, so the per-diagonal path only touches shared memory.
+// value.  Boundary-line cells take b and 1/D from k_line_fold.  Values of the
+// previous diagonal stay in shared memory; the inputs of the next R - 1
+// diagonals are in flight as asynchronous copies into a ring of R shared
+// buffers, so the per-diagonal path only touches shared memory.
 template <typename F, int R, bool VEC>
 __global__ void __launch_bounds__(512) k_sgs_wave(MicroArgs M, const F* __restrict__ invD, const F* __restrict__ r,
-                                                  F* __restrict__ x, const F* __restrict__ rho_lines, int pass)
+                                                  F* __restrict__ x, const F* __restrict__ fold, int pass)
 {
     extern __shared__ __align__(16) double sraw[];
     constexpr int K = kInteriorKc, W = 2 * K;
@@ -720,9 +781,7 @@ __global__ void __launch_bounds__(512) k_sgs_wave(MicroArgs M, const F* __restri
     const int nd = nx + ny - 1, nl = nx + ny;
     F* sx = reinterpret_cast<F*>(sraw);                 // [2][nx][W] values of the previous diagonal
     F* ring = sx + 2 * (size_t)nx * W;                  // [R][3][B][K] b (G, H) and 1/D of upcoming diagonals
-    F* lineb = ring + (size_t)R * 3 * B * K;            // [nl][W] folded b of the line cells
-    F* liv = lineb + (size_t)nl * W;                    // [nl][K] their 1/D
-    F* srdx = liv + (size_t)nl * K;                     // [nx] 1/dx
+    F* srdx = ring + (size_t)R * 3 * B * K;             // [nx] 1/dx
     F* srdy = srdx + nx;                                // [ny] 1/dy
     const int ib = pass == 0 ? 0 : nx - 1, jb = pass == 0 ? 0 : ny - 1;   // boundary column and row of the sweep
     const int fout = pass == 0 ? -1 : 1;
@@ -733,56 +792,29 @@ __global__ void __launch_bounds__(512) k_sgs_wave(MicroArgs M, const F* __restri
             const int ilo = max(0, d - (ny - 1)), ncell = min(nx - 1, d) - ilo + 1;
             if (tid < ncell) {
                 const int i = ilo + tid, j = d - i;
-                const size_t e = ((size_t)j * nx + i) * nv + k0;
                 F* ra = ring + ((size_t)(dd % R) * 3 * B + tid) * K;
-                cp_async_k4<F, VEC>(ra, src + e, nk);
-                cp_async_k4<F, VEC>(ra + (size_t)B * K, src + nc * nv + e, nk);
-                cp_async_k4<F, VEC>(ra + (size_t)2 * B * K, invD + e, nk);
+                if (i != ib && j != jb) {
+                    const size_t e = ((size_t)j * nx + i) * nv + k0;
+                    cp_async_k4<F, VEC>(ra, src + e, nk);
+                    cp_async_k4<F, VEC>(ra + (size_t)B * K, src + nc * nv + e, nk);
+                    cp_async_k4<F, VEC>(ra + (size_t)2 * B * K, invD + e, nk);
+                } else {                                // a boundary-line cell: its folded inputs
+                    const int e = i == ib ? (pass == 0 ? j : ny - 1 - j) : ny + (pass == 0 ? i : nx - 1 - i);
+                    const F* fo = fold + ((size_t)(blockIdx.x * nl + e) * 3) * K;
+                    cp_async_k4<F, true>(ra, fo, K);
+                    cp_async_k4<F, true>(ra + (size_t)B * K, fo + K, K);
+                    cp_async_k4<F, true>(ra + (size_t)2 * B * K, fo + 2 * K, K);
+                }
             }
         }
         cp_async_commit();
     };
     if constexpr (R > 1)
         for (int dd = 0; dd < R - 1; ++dd) issue(dd);
-    // prologue: diagonal buffers, spacings, and the folded inputs of the two lines
-    // (column: e = st, row: e = ny + st)
+    // prologue: diagonal buffers and spacings
     for (int q = tid; q < 2 * nx * W; q += B) sx[q] = F(0);
     for (int q = tid; q < nx; q += B) srdx[q] = (F)L.rdx[q];
     for (int q = tid; q < ny; q += B) srdy[q] = (F)L.rdy[q];
-    for (int q = tid; q < nl * W; q += B) {
-        const int e = q / W, rem = q - e * W, cp = rem / K, kk = rem - cp * K, kq = k0 + kk;
-        const int line = e < ny ? 0 : 1, st = line == 0 ? e : e - ny;
-        const int i = line == 0 ? ib : (pass == 0 ? st : nx - 1 - st);
-        const int j = line == 0 ? (pass == 0 ? st : ny - 1 - st) : jb;
-        F val = F(0), iv = F(1);
-        if (kq < nv) {
-            const int c = j * nx + i;
-            const size_t id = (size_t)c * nv + kq, xid = cp * nc * nv + id;
-            const F u = (F)Vg.u[kq], v = (F)Vg.v[kq];
-            const F uo = fout < 0 ? -(line == 0 ? u : v) : (line == 0 ? u : v);   // u_n at the line face
-            if (st == 0 || uo >= F(0)) {
-                val = x[xid];                           // finished by the boundary-line kernel
-            } else {
-                const int bc = line == 0 ? L.fbx[j * (nx + 1) + (fout < 0 ? 0 : nx)] : L.fby[(fout < 0 ? 0 : ny) * nx + i];
-                const BcDev Bc = M.bc[bc];
-                const F Db = uo * (line == 0 ? (F)L.rdx[i] : (F)L.rdy[j]);
-                F g = F(0);
-                if (Bc.type == BC_WALL) {
-                    g = Db * ((F)(M.Cw[(size_t)bc * nv + kq] * (cp == 0 ? 1.0 : kKint * Bc.t / 4.0)) *
-                              rho_lines[line * kMaxLine + st]);
-                } else if (Bc.type == BC_SYMMETRY) {
-                    const int a2 = kq / Vg.nvv, b2 = kq - a2 * Vg.nvv;
-                    const int km = line == 0 ? (Vg.nu - 1 - a2) * Vg.nvv + b2 : a2 * Vg.nvv + (Vg.nvv - 1 - b2);
-                    g = Db * x[cp * nc * nv + (size_t)c * nv + km];   // an outgoing velocity: final
-                }
-                const F D = (F)M.inv_tau[c] + geomD<F>(L, i, j, u, v);
-                iv = Bc.type == BC_OUTFLOW ? recip(D + Db) : invD[id];
-                val = pass == 0 ? r[xid] - g : (D * x[xid] - g) * iv;
-            }
-        }
-        lineb[q] = val;
-        if (cp == 0) liv[e * K + kk] = iv;
-    }
     // per velocity: neighbour coefficients (zero where the upwind neighbour is on the other side)
     // and which velocities leave through the column / row line faces
     F cu[K], cv[K];
@@ -825,14 +857,8 @@ __global__ void __launch_bounds__(512) k_sgs_wave(MicroArgs M, const F* __restri
             ld4(pw + K, pwv[1]);
             ld4(ps, psv[0]);
             ld4(ps + K, psv[1]);
-            unsigned ld = 0;
-            if (!(hx && hy)) {                          // a boundary-line cell
-                const int e = !hx ? (pass == 0 ? j : ny - 1 - j) : ny + (pass == 0 ? i : nx - 1 - i);
-                ld = !hx && !hy ? 0xFu : (!hx ? outc : outr);
-                ld4(lineb + (size_t)e * W, a[0]);
-                ld4(lineb + (size_t)e * W + K, a[1]);
-                ld4(liv + (size_t)e * K, iv);
-            }
+            // boundary-line cell: the final values (corner, outgoing velocities) are applied as is
+            const unsigned ld = hx && hy ? 0u : (!hx && !hy ? 0xFu : (!hx ? outc : outr));
             F res[2][K];
             #pragma unroll
             for (int cp = 0; cp < 2; ++cp)
@@ -866,11 +892,19 @@ __global__ void __launch_bounds__(512) k_sgs_wave(MicroArgs M, const F* __restri
     cp_async_wait_n<0>();
 }
 
+// sweep scratch (elements of the storage type): corner copy, line wall densities, folded line inputs
+size_t micro_fold_offset(int nv) { return ((2 * (size_t)nv + 2 * kMaxLine + 3) / 4) * 4; }
+size_t micro_scratch_elems(int nv, int nl)
+{
+    return micro_fold_offset(nv) + (size_t)((nv + kInteriorKc - 1) / kInteriorKc) * nl * 3 * kInteriorKc;
+}
+
 template <typename F>
 cudaError_t launch_micro_sgs(const MicroArgs& m, const double* Zw, const F* invD, const F* r, F* x, F* xcorner,
                              cudaStream_t st)
 {
     F* rho_lines = xcorner + 2 * (size_t)m.V.nv;       // 2 x kMaxLine wall densities after the corner copy
+    F* fold = xcorner + micro_fold_offset(m.V.nv);      // k_line_fold output
     const int ngroups = (m.V.nu + 1) / 2;
     const int nloc = ((ngroups + kChainCluster - 1) / kChainCluster) * 2 * m.V.nvv;
     if (nloc > kChainKptMax * kChainThreads) return cudaErrorInvalidValue;
@@ -893,13 +927,14 @@ cudaError_t launch_micro_sgs(const MicroArgs& m, const double* Zw, const F* invD
     const int nthr = ((maxdiag + 31) / 32) * 32;       // one thread per cell of the longest diagonal
     const bool vec = (m.V.nv * sizeof(F)) % 16 == 0;
     const size_t nl = (size_t)m.L.nx + m.L.ny;
-    const size_t fixed = sizeof(F) * (2 * (size_t)m.L.nx * 2 * kInteriorKc + nl * 3 * kInteriorKc + nl);
+    const size_t fixed = sizeof(F) * (2 * (size_t)m.L.nx * 2 * kInteriorKc + nl);
     const size_t slot = sizeof(F) * 3 * (size_t)nthr * kInteriorKc;
     constexpr size_t kSmemMax = 227 * 1024;
     if (fixed + slot > kSmemMax) return cudaErrorInvalidValue;
     const size_t rfit = (kSmemMax - fixed) / slot;
     const int R = rfit >= 8 ? 8 : rfit >= 4 ? 4 : rfit >= 2 ? 2 : 1;
     void (*wave)(MicroArgs, const F*, const F*, F*, const F*, int);
+    const int nfold = ((m.V.nv + kInteriorKc - 1) / kInteriorKc) * (int)nl * kInteriorKc;
     if (vec) wave = R == 8 ? k_sgs_wave<F, 8, true> : R == 4 ? k_sgs_wave<F, 4, true> : R == 2 ? k_sgs_wave<F, 2, true> : k_sgs_wave<F, 1, true>;
     else wave = R == 8 ? k_sgs_wave<F, 8, false> : R == 4 ? k_sgs_wave<F, 4, false> : R == 2 ? k_sgs_wave<F, 2, false> : k_sgs_wave<F, 1, false>;
     const size_t wsmem = fixed + slot * R;
@@ -918,7 +953,10 @@ cudaError_t launch_micro_sgs(const MicroArgs& m, const double* Zw, const F* invD
         chain<<<2 * kChainCluster, kChainThreads, smem, st>>>(m, Zw, invD, r, x, xcorner, rho_lines, pass, RA);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        wave<<<nblk, nthr, wsmem, st>>>(m, invD, r, x, rho_lines, pass);
+        k_line_fold<F><<<(nfold + 255) / 256, 256, 0, st>>>(m, invD, r, x, rho_lines, fold, pass);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        wave<<<nblk, nthr, wsmem, st>>>(m, invD, r, x, fold, pass);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

@@ -608,7 +608,7 @@ miugks_status miugks_create(const miugks_mesh* mesh, const miugks_vgrid* vg, con
         if ((st = dalloc(s, &s->rms_part, 64 * 4)) != MIUGKS_OK) break;
         if ((st = dalloc(s, &s->rms_out, 8)) != MIUGKS_OK) break;
         if (cudaMemset(s->rms_out, 0, 8 * sizeof(double)) != cudaSuccess) { st = fail(s, MIUGKS_ECUDA, "cudaMemset"); break; }
-        if ((st = falloc(s, &s->xcorner, 2 * nv + 2 * kMaxLine)) != MIUGKS_OK) break;
+        if ((st = falloc(s, &s->xcorner, micro_scratch_elems(nv, mesh->nx + mesh->ny))) != MIUGKS_OK) break;
         // smallest interior physical time step (for the numerical time step)
         s->dtp_min = 1e300;
         for (int i = 1; i < L0.nx; ++i) s->dtp_min = std::fmin(s->dtp_min, opts->cfl * std::fmin(L0.dx[i - 1], L0.dx[i]) / s->umax);
