@@ -253,7 +253,7 @@ cudaError_t launch_macro_resid(const MacroArgs& a, const double* W, const double
 //
 // Boundary ghosts enter only the backward sweep (they use dW of the forward
 // sweep); their term is folded into that sweep's own value between the passes.
-// The backward sweep adds dW to W as it goes.
+// W += dW closes the kernel.
 
 constexpr int kRec = 12;                         // values per record
 constexpr int kMacroRing = 8;                    // diagonals of records in flight
@@ -369,6 +369,18 @@ __device__ void macro_ghost_terms(const MacroArgs& a, const double* W, const dou
     }
 }
 
+// four consecutive record values (16-byte aligned for float, 32 for double)
+__device__ __forceinline__ void ld4v(const float* p, float* v)
+{
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void ld4v(const double* p, double* v)
+{
+    const double2 t0 = *reinterpret_cast<const double2*>(p), t1 = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = t0.x; v[1] = t0.y; v[2] = t1.x; v[3] = t1.y;
+}
+
 // flux terms X_x, X_y of lane m (component m) of a cell updated by dw
 __device__ __forceinline__ void macro_x(double dw, const double* rc, int m, int g0, double& Xx, double& Xy)
 {
@@ -383,7 +395,7 @@ __device__ __forceinline__ void macro_x(float dw, const float* rc, int m, int g0
     #pragma unroll
     for (int q = 0; q < 4; ++q) dq[q] = __shfl_sync(0xffffffffu, dw, g0 + q);
     const float Q = rc[1], U = rc[8], V = rc[9], rho = rc[10];
-    const float ir = 1.0f / (rho + dq[0]);
+    const float ir = __frcp_rn(rho + dq[0]);
     const float dU = (dq[1] - U * dq[0]) * ir, dV = (dq[2] - V * dq[0]) * ir;
     const float Up = U + dU, Vp = V + dV;
     const float dp = (2.0f / (kKint + 2)) * (dq[3] - 0.5f * (rho * U * dU + dq[1] * Up + rho * V * dV + dq[2] * Vp));
@@ -456,16 +468,18 @@ k_macro_sgs(MacroArgs a, double* __restrict__ W, F* __restrict__ rec, double* __
             for (int g = gbase; g < gbase + kMacroRing - 1 && g < gbase + nd; ++g) issue(issued = g);
         for (int dd = 0; dd < nd; ++dd) {
             const int g = gbase + dd, d = pass == 0 ? dd : nd - 1 - dd;
-            if (tid == 0) {
-                if (dd + kMacroRing - 1 < nd) issue(issued = g + kMacroRing - 1);
-                mbar_arrive_tx(&xm[g & 1], nbrs * 4 * kMsg * (unsigned)sizeof(F));   // this step's halo
-            }
+            if (tid == 0) mbar_arrive_tx(&xm[g & 1], nbrs * 4 * kMsg * (unsigned)sizeof(F));   // this step's halo
             bool got = mbar_wait(&rb[g % kMacroRing], (g / kMacroRing) & 1);
             if (tid == 0 && got) consumed = g;
             if (g > 0) got = mbar_wait(&xm[(g - 1) & 1], ((g - 1) >> 1) & 1) && got;
             const int ilo = diag_lo(d, ny), ncell = diag_len(d, nx, ny);
             const bool on = gs0 + ls < ncell;
-            const F* rc = ring + (g % kMacroRing) * per + (ls * 4 + m) * kRec;
+            F rc[kRec];                                  // this lane's record
+            {
+                const F* rp = ring + (g % kMacroRing) * per + (ls * 4 + m) * kRec;
+                #pragma unroll
+                for (int q = 0; q < kRec; q += 4) ld4v(rp + q, rc + q);
+            }
             F dw = F(0);
             if (on) {
                 // local indices (halo offset 1) of the x and y neighbours on the previous diagonal
@@ -508,9 +522,8 @@ k_macro_sgs(MacroArgs a, double* __restrict__ W, F* __restrict__ rec, double* __
                 dW[4 * (size_t)c + m] = (double)dw;
                 if (pass == 0)
                     rec[((((size_t)nd + d) * maxdiag + gs0 + ls) * 4 + m) * kRec] = dw;   // backward own value
-                else
-                    W[4 * (size_t)c + m] += (double)dw;
             }
+            if (tid == 0 && dd + kMacroRing - 1 < nd) issue(issued = g + kMacroRing - 1);
             if (!__syncthreads_and(got)) { ok = false; break; }
         }
         fence_proxy_async();
@@ -522,6 +535,7 @@ k_macro_sgs(MacroArgs a, double* __restrict__ W, F* __restrict__ rec, double* __
         if (!ok && tid == 0) *a.flag = 1.0;
     }
     cl.sync();                                           // no peer writes into this CTA after this point
+    for (int q = rank * blockDim.x + tid; q < 4 * L.nc; q += kMacroCluster * blockDim.x) W[q] += dW[q];
 }
 
 template <typename F>
