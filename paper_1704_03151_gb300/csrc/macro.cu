@@ -404,8 +404,14 @@ __device__ __forceinline__ void macro_x(float dw, const float* rc, int m, int g0
     Xy = Q * dV + dm * Vp + (m == 2 ? dp : 0.0f);
 }
 
+constexpr int kMacroBlock = kMacroThreads + 32;   // four sweep warps and one producer warp
+
+// The producer warp (lane 0) keeps the record ring kMacroRing - 1 diagonals
+// ahead.  Each ring slot's mbarrier also counts the halo bytes the neighbours
+// push for that step (the edge cells of the previous diagonal), so one wait
+// per step covers both.
 template <typename F>
-__global__ void __cluster_dims__(kMacroCluster, 1, 1) __launch_bounds__(kMacroThreads)
+__global__ void __cluster_dims__(kMacroCluster, 1, 1) __launch_bounds__(kMacroBlock)
 k_macro_sgs(MacroArgs a, double* __restrict__ W, F* __restrict__ rec, double* __restrict__ dW,
             const double* __restrict__ gx, const double* __restrict__ gy, int maxdiag, int nact)
 {
@@ -414,38 +420,48 @@ k_macro_sgs(MacroArgs a, double* __restrict__ W, F* __restrict__ rec, double* __
     constexpr int xper = (kMacroSlots + 2) * 4 * kMsg;   // message values of one diagonal
     F* ring = reinterpret_cast<F*>(smraw);               // [kMacroRing][per]
     F* xb = ring + kMacroRing * per;                     // [2][kMacroSlots + 2][4][kMsg], halo at 0 and kMacroSlots + 1
-    uint64_t* rb = reinterpret_cast<uint64_t*>(xb + 2 * xper);   // [kMacroRing] record arrivals
-    uint64_t* xm = rb + kMacroRing;                      // [2] halo arrivals
+    uint64_t* rb = reinterpret_cast<uint64_t*>(xb + 2 * xper);   // [kMacroRing] records + halo of a step
 
     cg::cluster_group cl = cg::this_cluster();
     const LevelDev& L = a.L;
     const int nx = L.nx, ny = L.ny, nd = nx + ny - 1;
     const int rank = (int)cl.block_rank(), tid = threadIdx.x;
+    const bool prod = tid >= kMacroThreads;              // the producer warp
     const int m = tid & 3, g0 = tid & 28, ls = tid >> 2;  // component, first lane of the cell, local slot
     const int gs0 = rank * kMacroSlots;                   // first slot of this CTA
     const bool active = rank < nact;
     const int nbrs = active ? (rank > 0) + (rank + 1 < nact) : 0;
+    const unsigned halo_bytes = nbrs * 4 * kMsg * (unsigned)sizeof(F);
     if (tid == 0) {
         for (int q = 0; q < kMacroRing; ++q) mbar_init(&rb[q], 1);
-        mbar_init(&xm[0], 1);
-        mbar_init(&xm[1], 1);
         mbar_init_fence();
     }
     for (int e = tid; e < 2 * xper; e += blockDim.x) xb[e] = F(0);
+    // edge lanes: the peer CTA and the cluster addresses of its halo buffer and mbarriers
+    int peer = -1, hs = 0;
+    if (!prod && ls == 0 && rank > 0) { peer = rank - 1; hs = kMacroSlots + 1; }
+    if (!prod && ls == kMacroSlots - 1 && rank + 1 < nact) { peer = rank + 1; hs = 0; }
+    const unsigned r_xb = peer >= 0 ? peer_addr(xb, peer) : 0u, r_rb = peer >= 0 ? peer_addr(rb, peer) : 0u;
     cl.sync();
 
-    auto issue = [&](int g) {                            // records of step g into ring slot g % kMacroRing
+    const int nsteps = 2 * nd;
+    // producer: arm ring slot g % kMacroRing for step g (records, plus the halo of step g - 1)
+    // and start the records' bulk copy; step nsteps only collects the last halo
+    auto issue = [&](int g) {
+        uint64_t* mb = &rb[g % kMacroRing];
+        const unsigned hb = g > 0 ? halo_bytes : 0u;
+        if (g >= nsteps) { mbar_arrive_tx(mb, hb); return; }
         const int pass = g / nd, dd = g - pass * nd, d = pass == 0 ? dd : nd - 1 - dd;
         int nloc = diag_len(d, nx, ny) - gs0;
         nloc = nloc < 0 ? 0 : (nloc > kMacroSlots ? kMacroSlots : nloc);
         const unsigned bytes = (unsigned)(nloc * 4 * kRec * sizeof(F));
-        uint64_t* mb = &rb[g % kMacroRing];
-        mbar_arrive_tx(mb, bytes);
+        mbar_arrive_tx(mb, bytes + hb);
         if (bytes) bulk_g2s(ring + (g % kMacroRing) * per, rec + (((size_t)pass * nd + d) * maxdiag + gs0) * 4 * kRec,
                             bytes, mb);
     };
+    const bool issuer = prod && (tid & 31) == 0;
     bool ok = true;
-    int issued = -1, consumed = -1;                      // last step issued / waited for (thread 0)
+    int issued = -1;                                     // last step armed (producer)
     for (int pass = 0; pass < 2; ++pass) {
         if (pass == 1) {
             cl.sync();                                   // forward dW and records visible in the cluster
@@ -464,75 +480,79 @@ k_macro_sgs(MacroArgs a, double* __restrict__ W, F* __restrict__ rec, double* __
         }
         if (!active || !ok) continue;
         const int gbase = pass * nd;
-        if (tid == 0)
+        if (issuer)
             for (int g = gbase; g < gbase + kMacroRing - 1 && g < gbase + nd; ++g) issue(issued = g);
         for (int dd = 0; dd < nd; ++dd) {
             const int g = gbase + dd, d = pass == 0 ? dd : nd - 1 - dd;
-            if (tid == 0) mbar_arrive_tx(&xm[g & 1], nbrs * 4 * kMsg * (unsigned)sizeof(F));   // this step's halo
-            bool got = mbar_wait(&rb[g % kMacroRing], (g / kMacroRing) & 1);
-            if (tid == 0 && got) consumed = g;
-            if (g > 0) got = mbar_wait(&xm[(g - 1) & 1], ((g - 1) >> 1) & 1) && got;
-            const int ilo = diag_lo(d, ny), ncell = diag_len(d, nx, ny);
-            const bool on = gs0 + ls < ncell;
-            F rc[kRec];                                  // this lane's record
-            {
-                const F* rp = ring + (g % kMacroRing) * per + (ls * 4 + m) * kRec;
-                #pragma unroll
-                for (int q = 0; q < kRec; q += 4) ld4v(rp + q, rc + q);
-            }
-            F dw = F(0);
-            if (on) {
-                // local indices (halo offset 1) of the x and y neighbours on the previous diagonal
-                int nbx, nby;
-                if (pass == 0) {
-                    const bool same = diag_lo(d - 1, ny) == ilo;
-                    nbx = ls + (same ? 0 : 1);
-                    nby = ls + (same ? 1 : 2);
-                } else {
-                    const bool same = diag_lo(d + 1, ny) == ilo;
-                    nbx = ls + (same ? 2 : 1);
-                    nby = ls + (same ? 1 : 0);
+            bool got = true;
+            if (prod) {
+                if (issuer && dd + kMacroRing - 1 < nd) issue(issued = g + kMacroRing - 1);
+            } else {
+                got = mbar_wait(&rb[g % kMacroRing], (g / kMacroRing) & 1);
+                const int ilo = diag_lo(d, ny), ncell = diag_len(d, nx, ny);
+                const bool on = gs0 + ls < ncell;
+                F rc[kRec];                              // this lane's record
+                {
+                    const F* rp = ring + (g % kMacroRing) * per + (ls * 4 + m) * kRec;
+                    #pragma unroll
+                    for (int q = 0; q < kRec; q += 4) ld4v(rp + q, rc + q);
                 }
-                const F* pb = xb + ((g - 1) & 1) * xper;
-                F acc = rc[2];
-                if (rc[4] != F(0)) acc = fma(rc[4], pb[(nbx * 4 + m) * kMsg + 1], fma(-rc[6], pb[(nbx * 4 + m) * kMsg], acc));
-                if (rc[5] != F(0)) acc = fma(rc[5], pb[(nby * 4 + m) * kMsg + 2], fma(-rc[7], pb[(nby * 4 + m) * kMsg], acc));
-                dw = fma(-acc, rc[3], rc[0]);
+                F dw = F(0);
+                if (on) {
+                    // local indices (halo offset 1) of the x and y neighbours on the previous diagonal
+                    int nbx, nby;
+                    if (pass == 0) {
+                        const bool same = diag_lo(d - 1, ny) == ilo;
+                        nbx = ls + (same ? 0 : 1);
+                        nby = ls + (same ? 1 : 2);
+                    } else {
+                        const bool same = diag_lo(d + 1, ny) == ilo;
+                        nbx = ls + (same ? 2 : 1);
+                        nby = ls + (same ? 1 : 0);
+                    }
+                    const F* pb = xb + ((g - 1) & 1) * xper;
+                    F acc = rc[2];
+                    if (rc[4] != F(0)) acc = fma(rc[4], pb[(nbx * 4 + m) * kMsg + 1], fma(-rc[6], pb[(nbx * 4 + m) * kMsg], acc));
+                    if (rc[5] != F(0)) acc = fma(rc[5], pb[(nby * 4 + m) * kMsg + 2], fma(-rc[7], pb[(nby * 4 + m) * kMsg], acc));
+                    dw = fma(-acc, rc[3], rc[0]);
+                }
+                F Xx, Xy;
+                macro_x(dw, rc, m, g0, Xx, Xy);          // all lanes of the warp (shuffles)
+                if (!on) Xx = Xy = F(0);
+                F* cb = xb + (g & 1) * xper;
+                cb[((ls + 1) * 4 + m) * kMsg] = dw;
+                cb[((ls + 1) * 4 + m) * kMsg + 1] = Xx;
+                cb[((ls + 1) * 4 + m) * kMsg + 2] = Xy;
+                if (peer >= 0) {                         // edge cell: into the neighbour's halo for step g + 1
+                    const unsigned rmb = r_rb + (unsigned)(((g + 1) % kMacroRing) * sizeof(uint64_t));
+                    const unsigned hl = r_xb + (unsigned)((((g & 1) * xper) + (hs * 4 + m) * kMsg) * sizeof(F));
+                    st_async(hl, dw, rmb);
+                    st_async(hl + (unsigned)sizeof(F), Xx, rmb);
+                    st_async(hl + 2u * (unsigned)sizeof(F), Xy, rmb);
+                }
+                if (on) {
+                    const int i = ilo + gs0 + ls, c = (d - i) * nx + i;
+                    dW[4 * (size_t)c + m] = (double)dw;
+                    if (pass == 0)
+                        rec[((((size_t)nd + d) * maxdiag + gs0 + ls) * 4 + m) * kRec] = dw;   // backward own value
+                }
             }
-            F Xx, Xy;
-            macro_x(dw, rc, m, g0, Xx, Xy);              // all lanes (warp shuffles)
-            if (!on) Xx = Xy = F(0);
-            F* cb = xb + (g & 1) * xper;
-            cb[((ls + 1) * 4 + m) * kMsg] = dw;
-            cb[((ls + 1) * 4 + m) * kMsg + 1] = Xx;
-            cb[((ls + 1) * 4 + m) * kMsg + 2] = Xy;
-            // edge cells to the neighbouring CTAs' halos
-            int peer = -1, hs = 0;
-            if (ls == 0 && rank > 0) { peer = rank - 1; hs = kMacroSlots + 1; }
-            if (ls == kMacroSlots - 1 && rank + 1 < nact) { peer = rank + 1; hs = 0; }
-            if (peer >= 0) {
-                const unsigned rmb = peer_addr(&xm[g & 1], peer);
-                F* hl = cb + (hs * 4 + m) * kMsg;
-                st_async(peer_addr(hl, peer), dw, rmb);
-                st_async(peer_addr(hl + 1, peer), Xx, rmb);
-                st_async(peer_addr(hl + 2, peer), Xy, rmb);
-            }
-            if (on) {
-                const int i = ilo + gs0 + ls, c = (d - i) * nx + i;
-                dW[4 * (size_t)c + m] = (double)dw;
-                if (pass == 0)
-                    rec[((((size_t)nd + d) * maxdiag + gs0 + ls) * 4 + m) * kRec] = dw;   // backward own value
-            }
-            if (tid == 0 && dd + kMacroRing - 1 < nd) issue(issued = g + kMacroRing - 1);
             if (!__syncthreads_and(got)) { ok = false; break; }
         }
         fence_proxy_async();
     }
-    if (active) {
-        if (ok && tid == 0 && !mbar_wait(&xm[(2 * nd - 1) & 1], ((2 * nd - 1) >> 1) & 1)) ok = false;
-        if (tid == 0)                                    // no bulk copy may still target this CTA
-            for (int g = consumed + 1; g <= issued; ++g) mbar_wait(&rb[g % kMacroRing], (g / kMacroRing) & 1);
-        if (!ok && tid == 0) *a.flag = 1.0;
+    if (active && issuer) {
+        if (ok) {                                        // the halo of the last step
+            issue(issued = nsteps);
+            if (!mbar_wait(&rb[nsteps % kMacroRing], (nsteps / kMacroRing) & 1)) ok = false;
+        }
+        if (!ok) {
+            // after a timeout: the latest armed phase of every slot, so that no bulk copy
+            // still targets this CTA (bounded waits), then report
+            for (int g = issued - kMacroRing + 1 > 0 ? issued - kMacroRing + 1 : 0; g <= issued; ++g)
+                mbar_wait(&rb[g % kMacroRing], (g / kMacroRing) & 1);
+            *a.flag = 1.0;
+        }
     }
     cl.sync();                                           // no peer writes into this CTA after this point
     for (int q = rank * blockDim.x + tid; q < 4 * L.nc; q += kMacroCluster * blockDim.x) W[q] += dW[q];
@@ -546,13 +566,13 @@ cudaError_t launch_macro_sgs(const MacroArgs& a, double* W, const double* gx, co
     const int nact = (maxdiag + kMacroSlots - 1) / kMacroSlots;
     if (nact > kMacroCluster) return cudaErrorInvalidValue;
     const size_t smem = sizeof(F) * ((size_t)kMacroRing * kMacroSlots * 4 * kRec + 2 * (kMacroSlots + 2) * 4 * kMsg) +
-                        sizeof(uint64_t) * (kMacroRing + 2);
+                        sizeof(uint64_t) * kMacroRing;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_macro_sgs<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     k_macro_rec<F><<<(4 * a.L.nc + 127) / 128, 128, 0, st>>>(a, W, gx, gy, idiag, R, (F*)rec, maxdiag);
-    k_macro_sgs<F><<<kMacroCluster, kMacroThreads, smem, st>>>(a, W, (F*)rec, dW, gx, gy, maxdiag, nact);
+    k_macro_sgs<F><<<kMacroCluster, kMacroBlock, smem, st>>>(a, W, (F*)rec, dW, gx, gy, maxdiag, nact);
     return cudaGetLastError();
 }
 template cudaError_t launch_macro_sgs<double>(const MacroArgs&, double*, const double*, const double*, const double*,
