@@ -24,6 +24,7 @@ struct VelDev {
     int nu, nvv, nv;
     const double *u, *v, *w;     // per discrete velocity
     const double *ua, *vb;       // per-axis nodes
+    const float *uf, *vf, *wf;   // u, v, w rounded to FP32 (for the mixed-precision kernels)
     double umax, vmax;           // largest |u|, |v|
 };
 
@@ -53,6 +54,12 @@ __device__ __forceinline__ double tau_of(const GasDev& g, double rho, double lam
 {
     double T = 1.0 / lam;
     return g.mu_ref * pow(T, g.omega) / (0.5 * rho * T);
+}
+// the same in FP32 (mixed-precision face scalars)
+__device__ __forceinline__ float tau_of_f(const GasDev& g, float rho, float lam)
+{
+    float T = 1.0f / lam;
+    return (float)g.mu_ref * powf(T, (float)g.omega) / (0.5f * rho * T);
 }
 
 // Time integrals of the UGKS integral solution over [0, dt] (x = dt/tau):
@@ -94,17 +101,22 @@ __device__ __forceinline__ void time_coeffs(double dt, double tau, double q[5])
 }
 
 // moments dw (already divided by rho) -> slope coefficients of a Maxwellian at (U, V, lam)
+template <typename T>
+__device__ __forceinline__ void micro_slope_t(const T dw[4], T U, T V, T lam, T a[4])
+{
+    const T Kp2 = T(kKint + 2.0);
+    T c = U * U + V * V + Kp2 / (T(2) * lam);
+    T R4 = T(2) * dw[3] - c * dw[0];
+    T R3 = dw[2] - V * dw[0];
+    T R2 = dw[1] - U * dw[0];
+    a[3] = T(4) * lam * lam / Kp2 * (R4 - T(2) * U * R2 - T(2) * V * R3);
+    a[2] = T(2) * lam * R3 - V * a[3];
+    a[1] = T(2) * lam * R2 - U * a[3];
+    a[0] = dw[0] - U * a[1] - V * a[2] - T(0.5) * a[3] * c;
+}
 __device__ __forceinline__ void micro_slope(const double dw[4], double U, double V, double lam, double a[4])
 {
-    const double Kp2 = kKint + 2.0;
-    double c = U * U + V * V + Kp2 / (2.0 * lam);
-    double R4 = 2.0 * dw[3] - c * dw[0];
-    double R3 = dw[2] - V * dw[0];
-    double R2 = dw[1] - U * dw[0];
-    a[3] = 4.0 * lam * lam / Kp2 * (R4 - 2.0 * U * R2 - 2.0 * V * R3);
-    a[2] = 2.0 * lam * R3 - V * a[3];
-    a[1] = 2.0 * lam * R2 - U * a[3];
-    a[0] = dw[0] - U * a[1] - V * a[2] - 0.5 * a[3] * c;
+    micro_slope_t<double>(dw, U, V, lam, a);
 }
 
 // Reciprocal by the Newton-Raphson iteration y <- y + y (1 - x y) (quadratic
@@ -193,7 +205,10 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
 template <int N>
 __device__ __forceinline__ void block_total(Acc<float> (&a)[N], double* scratch, double (&out)[N])
 {
+    // float-float pairs all the way; one conversion to FP64 per value at the end
+    // (an FP64 instruction costs a warp as much as thirty-two lanes of it)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    float* fs = reinterpret_cast<float*>(scratch);    // [32][N][2] per-warp pairs
     #pragma unroll
     for (int q = 0; q < N; ++q) {
         float hi = a[q].s, lo = -a[q].c;
@@ -205,16 +220,22 @@ __device__ __forceinline__ void block_total(Acc<float> (&a)[N], double* scratch,
             lo = lo + l2 + e;
             hi = s;
         }
-        if (lane == 0) scratch[warp * N + q] = (double)hi + (double)lo;
+        if (lane == 0) { fs[(warp * N + q) * 2] = hi; fs[(warp * N + q) * 2 + 1] = lo; }
     }
     __syncthreads();
     if (warp == 0) {
         #pragma unroll
         for (int q = 0; q < N; ++q) {
-            double x = lane < nw ? scratch[lane * N + q] : 0.0;
+            float hi = lane < nw ? fs[(lane * N + q) * 2] : 0.0f, lo = lane < nw ? fs[(lane * N + q) * 2 + 1] : 0.0f;
             #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-            if (lane == 0) scratch[32 * N - N + q] = x;
+            for (int o = 16; o > 0; o >>= 1) {
+                float h2 = __shfl_xor_sync(0xffffffffu, hi, o), l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+                float s, e;
+                two_sum(hi, h2, s, e);
+                lo = lo + l2 + e;
+                hi = s;
+            }
+            if (lane == q) scratch[32 * N - N + q] = (double)hi + (double)lo;
         }
     }
     __syncthreads();

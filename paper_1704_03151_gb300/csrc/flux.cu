@@ -14,6 +14,7 @@
 namespace miugks {
 
 __constant__ double c_series[5][28];   // power-series coefficients of the time integrals
+__constant__ float c_series_f[5][28];  // the same rounded to FP32
 
 void upload_series_coefficients()
 {
@@ -35,6 +36,10 @@ void upload_series_coefficients()
         c[4][n] = -s * (n + 1) / fact[n + 2];
     }
     cudaMemcpyToSymbol(c_series, c, sizeof c);
+    float cf[5][28];
+    for (int m = 0; m < 5; ++m)
+        for (int n = 0; n < 28; ++n) cf[m][n] = (float)c[m][n];
+    cudaMemcpyToSymbol(c_series_f, cf, sizeof cf);
 }
 
 __device__ __forceinline__ void time_coeffs_fast(double dt, double tau, double q[5])
@@ -79,6 +84,39 @@ __device__ __forceinline__ double time_coeff_one(double dt, double tau, int m)
     }
 }
 
+// FP32 form of time_coeff_one (mixed-precision face scalars)
+__device__ __forceinline__ float time_coeff_one_f(float dt, float tau, int m)
+{
+    float x = dt / tau;
+    if (x < 1.0f) {
+        float acc = c_series_f[m][27];
+        #pragma unroll
+        for (int n = 26; n >= 0; --n) acc = fmaf(acc, x, c_series_f[m][n]);
+        return (m == 0 || m == 3) ? dt * acc : dt * dt * acc;
+    }
+    float e = expf(-x), E1 = -expm1f(-x);
+    switch (m) {
+    case 0: return dt - tau * E1;
+    case 1: return -tau * dt * (1.0f + e) + 2.0f * tau * tau * E1;
+    case 2: return 0.5f * dt * dt - tau * dt + tau * tau * E1;
+    case 3: return tau * E1;
+    default: return tau * dt * e - tau * tau * E1;
+    }
+}
+
+// per-velocity nodes and weights in the arithmetic type
+template <typename F> struct VelT;
+template <> struct VelT<double> {
+    static __device__ __forceinline__ const double* u(const VelDev& V) { return V.u; }
+    static __device__ __forceinline__ const double* v(const VelDev& V) { return V.v; }
+    static __device__ __forceinline__ const double* w(const VelDev& V) { return V.w; }
+};
+template <> struct VelT<float> {
+    static __device__ __forceinline__ const float* u(const VelDev& V) { return V.uf; }
+    static __device__ __forceinline__ const float* v(const VelDev& V) { return V.vf; }
+    static __device__ __forceinline__ const float* w(const VelDev& V) { return V.wf; }
+};
+
 // van Leer limited slope 2 s1 s2 / (s1 + s2) when s1 s2 > 0, else 0
 __device__ __forceinline__ double vl_limited(double s1, double s2)
 {
@@ -114,8 +152,9 @@ __global__ void __launch_bounds__(256) k_face_flux(FaceFluxArgs<F> A)
     const int nx = L.nx, ny = L.ny;
     const size_t nc = L.nc, nf = axis == 0 ? L.nfx : L.nfy;
     double* red = sm;                       // 32 * 8
-    double* par = red + 256;                // face scalars (FP64)
-    F* f0s = reinterpret_cast<F*>(par + 64);  // [2][nv]
+    double* par = red + 256;                // face scalars (FP64), [64]
+    F* pf = reinterpret_cast<F*>(par + 64); // face constants in F, [64]
+    F* f0s = reinterpret_cast<F*>(par + 128);  // [2][nv]
     F* sgs = f0s + 2 * nv;                  // [2][nv]
     F* Eu = sgs + 2 * nv;                   // [nu]
     F* Ev = Eu + Vg.nu;                     // [nvv]
@@ -172,30 +211,48 @@ __global__ void __launch_bounds__(256) k_face_flux(FaceFluxArgs<F> A)
     }
 
     // ---------------- interior face between cL (lower) and cR (upper)
+    // Face constants are computed once (by one thread or one lane each) and
+    // broadcast through shared memory as F: an FP64 instruction occupies a
+    // GB300 SM sub-partition for as long for one lane as for thirty-two.
+    const F* __restrict__ vu = VelT<F>::u(Vg);
+    const F* __restrict__ vv = VelT<F>::v(Vg);
+    const F* __restrict__ vw = VelT<F>::w(Vg);
     int cL, cR, cLL = -1, cRR = -1;
-    double dLLL = 1, dLR, dRRR = 1, hL, hR, wL, wR;
     if (axis == 0) {
         cL = j * nx + i - 1; cR = cL + 1;
-        if (i - 1 > 0 && L.fbx[fi - 1] < 0) { cLL = cL - 1; dLLL = L.xc[i - 1] - L.xc[i - 2]; }
-        if (i + 1 < nx && L.fbx[fi + 1] < 0) { cRR = cR + 1; dRRR = L.xc[i + 1] - L.xc[i]; }
-        dLR = L.xc[i] - L.xc[i - 1];
-        hL = L.xn[i] - L.xc[i - 1]; hR = L.xc[i] - L.xn[i];
-        wL = L.dx[i - 1]; wR = L.dx[i];
+        if (i - 1 > 0 && L.fbx[fi - 1] < 0) cLL = cL - 1;
+        if (i + 1 < nx && L.fbx[fi + 1] < 0) cRR = cR + 1;
     } else {
         cL = (j - 1) * nx + i; cR = cL + nx;
-        if (j - 1 > 0 && L.fby[fi - nx] < 0) { cLL = cL - nx; dLLL = L.yc[j - 1] - L.yc[j - 2]; }
-        if (j + 1 < ny && L.fby[fi + nx] < 0) { cRR = cR + nx; dRRR = L.yc[j + 1] - L.yc[j]; }
-        dLR = L.yc[j] - L.yc[j - 1];
-        hL = L.yn[j] - L.yc[j - 1]; hR = L.yc[j] - L.yn[j];
-        wL = L.dy[j - 1]; wR = L.dy[j];
+        if (j - 1 > 0 && L.fby[fi - nx] < 0) cLL = cL - nx;
+        if (j + 1 < ny && L.fby[fi + nx] < 0) cRR = cR + nx;
     }
-    const F r1 = (F)(1.0 / dLLL), r2 = (F)(1.0 / dLR), r3 = (F)(1.0 / dRRR);
-    const F fhL = (F)hL, fhR = (F)hR;
+    if (tid == 0) {
+        double dLLL = 1, dLR, dRRR = 1, hL, hR, wL, wR;
+        if (axis == 0) {
+            if (cLL >= 0) dLLL = L.xc[i - 1] - L.xc[i - 2];
+            if (cRR >= 0) dRRR = L.xc[i + 1] - L.xc[i];
+            dLR = L.xc[i] - L.xc[i - 1];
+            hL = L.xn[i] - L.xc[i - 1]; hR = L.xc[i] - L.xn[i];
+            wL = L.dx[i - 1]; wR = L.dx[i];
+        } else {
+            if (cLL >= 0) dLLL = L.yc[j - 1] - L.yc[j - 2];
+            if (cRR >= 0) dRRR = L.yc[j + 1] - L.yc[j];
+            dLR = L.yc[j] - L.yc[j - 1];
+            hL = L.yn[j] - L.yc[j - 1]; hR = L.yc[j] - L.yn[j];
+            wL = L.dy[j - 1]; wR = L.dy[j];
+        }
+        pf[0] = (F)(1.0 / dLLL); pf[1] = (F)(1.0 / dLR); pf[2] = (F)(1.0 / dRRR);
+        pf[3] = (F)hL; pf[4] = (F)hR;
+        par[26] = hL; par[27] = hR; par[28] = wL; par[29] = wR;
+    }
+    __syncthreads();
+    const F r1 = pf[0], r2 = pf[1], r3 = pf[2], fhL = pf[3], fhR = pf[4];
 
     // pass 1: reconstruction, upwinding, interface conservative variables
     Acc<F> W0a[4];
     for (int k = tid; k < nv; k += bs) {
-        const F un = (F)(axis == 0 ? Vg.u[k] : Vg.v[k]);
+        const F un = axis == 0 ? vu[k] : vv[k];
         #pragma unroll
         for (int cp = 0; cp < 2; ++cp) {
             const F* fc = cp == 0 ? fG : fH;
@@ -211,47 +268,71 @@ __global__ void __launch_bounds__(256) k_face_flux(FaceFluxArgs<F> A)
             f0s[cp * nv + k] = f0;
             sgs[cp * nv + k] = sg;
         }
-        const F w = (F)Vg.w[k], u = (F)Vg.u[k], v = (F)Vg.v[k], g = f0s[k];
+        const F w = vw[k], u = vu[k], v = vv[k], g = f0s[k];
         W0a[0].add(w * g); W0a[1].add(w * u * g); W0a[2].add(w * v * g);
         W0a[3].add(w * (F(0.5) * (u * u + v * v) * g + f0s[nv + k]));
     }
     double W0[4];
     block_total<4>(W0a, red, W0);
-    // face scalars, spread over the lanes of warp 0 (an FP64 instruction costs the
-    // same for one lane as for thirty-two): lane 0 the collision time and time
-    // step, lanes 1 and 2 the left and right equilibrium slopes
+    // face scalars, spread over the lanes of warp 0: lane 0 the collision time and
+    // time step, lanes 1 and 2 the left and right equilibrium slopes
     if (tid < 3) {
         double rho = W0[0], ir = rcp64(rho);
         double U = W0[1] * ir, V = W0[2] * ir;
         double lam = (kKint + 2) * rho * rcp64(4.0 * (W0[3] - 0.5 * (W0[1] * U + W0[2] * V)));
         if (tid == 0) {
             par[0] = rho; par[1] = U; par[2] = V; par[3] = lam;
-            par[4] = tau_of(A.gas, rho, lam);
-            par[5] = A.cfl * fmin(wL, wR) / (axis == 0 ? Vg.umax : Vg.vmax);
+            if constexpr (sizeof(F) == 8) par[4] = tau_of(A.gas, rho, lam);
+            else par[4] = (double)tau_of_f(A.gas, (float)rho, (float)lam);
+            par[5] = A.cfl * fmin(par[28], par[29]) / (axis == 0 ? Vg.umax : Vg.vmax);
         } else {
             const double* Wc = A.W + 4 * (size_t)(tid == 1 ? cL : cR);
-            double hf = (tid == 1 ? 1.0 : -1.0) * ir * rcp64(tid == 1 ? hL : hR), dw[4];
+            double hf = (tid == 1 ? 1.0 : -1.0) * ir * rcp64(tid == 1 ? par[26] : par[27]), dw[4];
             for (int m = 0; m < 4; ++m) dw[m] = (W0[m] - Wc[m]) * hf;
-            micro_slope(dw, U, V, lam, par + (tid == 1 ? 8 : 12));
+            if constexpr (sizeof(F) == 8) {
+                micro_slope(dw, U, V, lam, par + (tid == 1 ? 8 : 12));
+            } else {
+                float dwf[4] = {(float)dw[0], (float)dw[1], (float)dw[2], (float)dw[3]}, af[4];
+                micro_slope_t<float>(dwf, (float)U, (float)V, (float)lam, af);
+                for (int m = 0; m < 4; ++m) par[(tid == 1 ? 8 : 12) + m] = af[m];
+            }
         }
     }
     __syncthreads();
-    const double rho0 = par[0], U0 = par[1], V0 = par[2], lam0 = par[3];
-    for (int a = tid; a < Vg.nu; a += bs) { double d = Vg.ua[a] - U0; Eu[a] = (F)exp(-lam0 * d * d); }
-    for (int b = tid; b < Vg.nvv; b += bs) { double d = Vg.vb[b] - V0; Ev[b] = (F)exp(-lam0 * d * d); }
+    {
+        // warp 0: constants of the equilibrium in F; the other warps: the per-axis exponentials
+        const double rho0 = par[0], U0 = par[1], V0 = par[2], lam0 = par[3];
+        if (tid < 32) {
+            F val = F(0);
+            if (tid < 8) val = (F)par[8 + tid];          // aL, aR
+            else if (tid == 8) val = (F)U0;
+            else if (tid == 9) val = (F)V0;
+            else if (tid == 10) val = (F)(rho0 * lam0 / kPi);
+            else if (tid == 11) val = (F)(kKint / (4.0 * lam0));
+            else if (tid == 12) val = (F)(kKint * (kKint + 2.0) / (16.0 * lam0 * lam0));
+            if (tid < 13) pf[8 + tid] = val;
+        } else {
+            for (int e = tid - 32; e < Vg.nu + Vg.nvv; e += bs - 32) {
+                const bool isu = e < Vg.nu;
+                const double d = isu ? Vg.ua[e] - U0 : Vg.vb[e - Vg.nu] - V0;
+                F ex;
+                if constexpr (sizeof(F) == 8) ex = exp(-lam0 * d * d);
+                else ex = expf((float)(-lam0 * d * d));
+                (isu ? Eu[e] : Ev[e - Vg.nu]) = ex;
+            }
+        }
+    }
     __syncthreads();
-    const F gnorm = (F)(rho0 * lam0 / kPi), hfac = (F)(kKint / (4.0 * lam0));
-    const F xi4q = (F)(kKint * (kKint + 2.0) / (16.0 * lam0 * lam0));
-    const F fU0 = (F)U0, fV0 = (F)V0;
+    const F fU0 = pf[16], fV0 = pf[17], gnorm = pf[18], hfac = pf[19], xi4q = pf[20];
     F aL[4], aR[4];
     #pragma unroll
-    for (int m = 0; m < 4; ++m) { aL[m] = (F)par[8 + m]; aR[m] = (F)par[12 + m]; }
+    for (int m = 0; m < 4; ++m) { aL[m] = pf[8 + m]; aR[m] = pf[12 + m]; }
 
     // pass 2: heat flux of the interface distribution, compatibility moments for A
     Acc<F> s6a[6];
     for (int k = tid; k < nv; k += bs) {
         int a = k / Vg.nvv, b = k - a * Vg.nvv;
-        const F u = (F)Vg.u[k], v = (F)Vg.v[k], w = (F)Vg.w[k];
+        const F u = vu[k], v = vv[k], w = vw[k];
         F cx = u - fU0, cy = v - fV0, c2 = cx * cx + cy * cy;
         F e = F(0.5) * c2 * f0s[k] + f0s[nv + k];
         s6a[0].add(w * cx * e);
@@ -269,30 +350,47 @@ __global__ void __launch_bounds__(256) k_face_flux(FaceFluxArgs<F> A)
     block_total<6>(s6a, red, s6);
     // lane 0: time slope A from compatibility; lanes 1-5: one time integral each
     if (tid < 6) {
+        const double rho0 = par[0], U0 = par[1], V0 = par[2], lam0 = par[3];
         if (tid == 0) {
             double dwt[4], ir = -rcp64(rho0);
             for (int m = 0; m < 4; ++m) dwt[m] = s6[2 + m] * ir;
-            micro_slope(dwt, U0, V0, lam0, par + 16);
+            if constexpr (sizeof(F) == 8) {
+                micro_slope(dwt, U0, V0, lam0, par + 16);
+            } else {
+                float dwf[4] = {(float)dwt[0], (float)dwt[1], (float)dwt[2], (float)dwt[3]}, af[4];
+                micro_slope_t<float>(dwf, (float)U0, (float)V0, (float)lam0, af);
+                for (int m = 0; m < 4; ++m) par[16 + m] = af[m];
+            }
             par[6] = s6[0]; par[7] = s6[1];
         } else {
-            par[20 + tid - 1] = time_coeff_one(par[5], par[4], tid - 1);
+            if constexpr (sizeof(F) == 8) par[20 + tid - 1] = time_coeff_one(par[5], par[4], tid - 1);
+            else par[20 + tid - 1] = time_coeff_one_f((float)par[5], (float)par[4], tid - 1);
         }
+    }
+    __syncthreads();
+    if (tid < 32) {
+        const double rho0 = par[0], lam0 = par[3];
+        F val = F(0);
+        if (tid < 4) val = (F)par[16 + tid];             // A
+        else if (tid < 9) val = (F)(par[20 + tid - 4] * (1.0 / par[5]));   // q_i / dt
+        else if (tid == 9) val = (F)((1.0 - A.gas.pr) * 4.0 * lam0 * lam0 / (5.0 * rho0));
+        else if (tid == 10) val = (F)par[6];
+        else if (tid == 11) val = (F)par[7];
+        else if (tid == 12) val = (F)(2.0 * lam0);
+        if (tid < 13) pf[24 + tid] = val;
     }
     __syncthreads();
     F As[4];
     #pragma unroll
-    for (int m = 0; m < 4; ++m) As[m] = (F)par[16 + m];
-    const double idt = 1.0 / par[5];
-    const F q1 = (F)(par[20] * idt), q2 = (F)(par[21] * idt), q3 = (F)(par[22] * idt), q4 = (F)(par[23] * idt),
-            q5 = (F)(par[24] * idt);
-    const F shk = (F)((1.0 - A.gas.pr) * 4.0 * lam0 * lam0 / (5.0 * rho0));
-    const F qx = (F)par[6], qy = (F)par[7], flam2 = (F)(2.0 * lam0);
+    for (int m = 0; m < 4; ++m) As[m] = pf[24 + m];
+    const F q1 = pf[28], q2 = pf[29], q3 = pf[30], q4 = pf[31], q5 = pf[32];
+    const F shk = pf[33], qx = pf[34], qy = pf[35], flam2 = pf[36];
 
     // pass 3: time-averaged flux of every discrete velocity and its moments
     Acc<F> Fa[4];
     for (int k = tid; k < nv; k += bs) {
         int a = k / Vg.nvv, b = k - a * Vg.nvv;
-        const F u = (F)Vg.u[k], v = (F)Vg.v[k], w = (F)Vg.w[k];
+        const F u = vu[k], v = vv[k], w = vw[k];
         const F un = axis == 0 ? u : v;
         F cx = u - fU0, cy = v - fV0, c2 = cx * cx + cy * cy;
         F gM = gnorm * Eu[a] * Ev[b], hM = gM * hfac;
@@ -317,7 +415,7 @@ __global__ void __launch_bounds__(256) k_face_flux(FaceFluxArgs<F> A)
 template <typename F>
 size_t face_flux_smem(const VelDev& V)
 {
-    return sizeof(double) * (256 + 64) + sizeof(F) * (4 * (size_t)V.nv + V.nu + V.nvv);
+    return sizeof(double) * (256 + 128) + sizeof(F) * (4 * (size_t)V.nv + V.nu + V.nvv);
 }
 
 template <typename F>

@@ -43,6 +43,7 @@ struct miugks_solver {
     GasDev gas{};
     std::vector<BcDev> bch;
     std::vector<double> uh, vh, wh, uah, vbh;
+    std::vector<float> ufh, vfh, wfh;
     VelDev vel{};
     BcDev* bc = nullptr;
     double *Cw = nullptr, *Zw = nullptr;
@@ -567,6 +568,12 @@ miugks_status miugks_create(const miugks_mesh* mesh, const miugks_vgrid* vg, con
         if ((st = upload(s, (double**)&s->vel.w, s->wh)) != MIUGKS_OK) break;
         if ((st = upload(s, (double**)&s->vel.ua, s->uah)) != MIUGKS_OK) break;
         if ((st = upload(s, (double**)&s->vel.vb, s->vbh)) != MIUGKS_OK) break;
+        s->ufh.assign(s->uh.begin(), s->uh.end());
+        s->vfh.assign(s->vh.begin(), s->vh.end());
+        s->wfh.assign(s->wh.begin(), s->wh.end());
+        if ((st = upload(s, (float**)&s->vel.uf, s->ufh)) != MIUGKS_OK) break;
+        if ((st = upload(s, (float**)&s->vel.vf, s->vfh)) != MIUGKS_OK) break;
+        if ((st = upload(s, (float**)&s->vel.wf, s->wfh)) != MIUGKS_OK) break;
         s->vel.nu = s->nu; s->vel.nvv = s->nvv; s->vel.nv = s->nv; s->vel.umax = s->umax; s->vel.vmax = s->vmax;
         if ((st = upload(s, &s->bc, s->bch)) != MIUGKS_OK) break;
         s->Cwh.assign((size_t)n_bcs * s->nv, 0.0);
