@@ -38,6 +38,20 @@ struct LevelDev {
 
 struct GasDev { double mu_ref, omega, pr; };
 
+// per-velocity nodes and weights in the arithmetic type
+template <typename F> struct VelT;
+template <> struct VelT<double> {
+    static __device__ __forceinline__ const double* u(const VelDev& V) { return V.u; }
+    static __device__ __forceinline__ const double* v(const VelDev& V) { return V.v; }
+    static __device__ __forceinline__ const double* w(const VelDev& V) { return V.w; }
+};
+template <> struct VelT<float> {
+    static __device__ __forceinline__ const float* u(const VelDev& V) { return V.uf; }
+    static __device__ __forceinline__ const float* v(const VelDev& V) { return V.vf; }
+    static __device__ __forceinline__ const float* w(const VelDev& V) { return V.wf; }
+};
+
+
 // ---------------------------------------------------------------------------
 // gas model
 __device__ __forceinline__ void prim4(const double* W, double& rho, double& U, double& V, double& lam)

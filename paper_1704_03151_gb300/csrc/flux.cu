@@ -104,19 +104,6 @@ __device__ __forceinline__ float time_coeff_one_f(float dt, float tau, int m)
     }
 }
 
-// per-velocity nodes and weights in the arithmetic type
-template <typename F> struct VelT;
-template <> struct VelT<double> {
-    static __device__ __forceinline__ const double* u(const VelDev& V) { return V.u; }
-    static __device__ __forceinline__ const double* v(const VelDev& V) { return V.v; }
-    static __device__ __forceinline__ const double* w(const VelDev& V) { return V.w; }
-};
-template <> struct VelT<float> {
-    static __device__ __forceinline__ const float* u(const VelDev& V) { return V.uf; }
-    static __device__ __forceinline__ const float* v(const VelDev& V) { return V.vf; }
-    static __device__ __forceinline__ const float* w(const VelDev& V) { return V.wf; }
-};
-
 // van Leer limited slope 2 s1 s2 / (s1 + s2) when s1 s2 > 0, else 0
 __device__ __forceinline__ double vl_limited(double s1, double s2)
 {

@@ -613,10 +613,61 @@ __global__ void k_restrict(LevelDev F, LevelDev C, int m, int nblk, const T* __r
     coarse[(size_t)blk * per + rem] = (T)(s / vs);
 }
 
+// the same for long rows (the per-velocity arrays): one CTA per coarse cell, the
+// cell's volumes once, threads along the contiguous values.  FP64: the element
+// arithmetic of k_restrict; FP32: normalised weights and FP32 sums.
+template <typename T>
+__global__ void k_restrict_rows(LevelDev F, LevelDev C, int m, int nblk, const T* __restrict__ fine,
+                                T* __restrict__ coarse)
+{
+    __shared__ size_t sidx[4];
+    __shared__ double sV[5];
+    const int cc = blockIdx.x, I = cc % C.nx, J = cc / C.nx;
+    if (threadIdx.x == 0) {
+        double vs = 0.0;
+        for (int s = 0; s < 4; ++s) {
+            const int i = 2 * I + (s & 1), j = 2 * J + (s >> 1);
+            sidx[s] = (size_t)(j * F.nx + i) * m;
+            sV[s] = F.dx[i] * F.dy[j];
+            vs += sV[s];
+        }
+        sV[4] = vs;
+    }
+    __syncthreads();
+    const size_t i0 = sidx[0], i1 = sidx[1], i2 = sidx[2], i3 = sidx[3];
+    if constexpr (sizeof(T) == 8) {
+        const double V0 = sV[0], V1 = sV[1], V2 = sV[2], V3 = sV[3], vs = sV[4];
+        for (int blk = 0; blk < nblk; ++blk) {
+            const T* fb = fine + (size_t)blk * F.nc * m;
+            T* cb = coarse + ((size_t)blk * C.nc + cc) * m;
+            for (int q = threadIdx.x; q < m; q += blockDim.x) {
+                double s = 0.0;
+                s += fb[i0 + q] * V0; s += fb[i1 + q] * V1; s += fb[i2 + q] * V2; s += fb[i3 + q] * V3;
+                cb[q] = s / vs;
+            }
+        }
+    } else {
+        __shared__ float sw[4];
+        if (threadIdx.x < 4) sw[threadIdx.x] = (float)(sV[threadIdx.x] / sV[4]);
+        __syncthreads();
+        const float w0 = sw[0], w1 = sw[1], w2 = sw[2], w3 = sw[3];
+        for (int blk = 0; blk < nblk; ++blk) {
+            const T* fb = fine + (size_t)blk * F.nc * m;
+            T* cb = coarse + ((size_t)blk * C.nc + cc) * m;
+            for (int q = threadIdx.x; q < m; q += blockDim.x)
+                cb[q] = w0 * fb[i0 + q] + w1 * fb[i1 + q] + w2 * fb[i2 + q] + w3 * fb[i3 + q];
+        }
+    }
+}
+
 template <typename T>
 cudaError_t launch_restrict(const LevelDev& F, const LevelDev& C, int m, int nblk, const T* fine, T* coarse,
                             cudaStream_t st)
 {
+    if (m >= 32) {
+        k_restrict_rows<T><<<C.nc, 256, 0, st>>>(F, C, m, nblk, fine, coarse);
+        return cudaGetLastError();
+    }
     size_t n = (size_t)C.nc * m * nblk;
     k_restrict<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(F, C, m, nblk, fine, coarse);
     return cudaGetLastError();
@@ -645,10 +696,52 @@ __global__ void k_prolong_add(LevelDev F, LevelDev C, int m, int nblk, const int
     if (out_pro) out_pro[t] = (T)v;
 }
 
+// the same for long rows: one CTA per fine cell with its stencil loaded once.
+// FP64: the element arithmetic of k_prolong_add; FP32: FP32 weights and sums.
+template <typename T>
+__global__ void k_prolong_rows(LevelDev F, LevelDev C, int m, int nblk, const int* __restrict__ idx4,
+                               const double* __restrict__ w4, const T* __restrict__ coarse, T* __restrict__ fine,
+                               T* __restrict__ out_pro)
+{
+    __shared__ size_t sidx[4];
+    __shared__ double sw[4];
+    const int c = blockIdx.x;
+    if (threadIdx.x < 4) {
+        sidx[threadIdx.x] = (size_t)idx4[4 * c + threadIdx.x] * m;
+        sw[threadIdx.x] = w4[4 * c + threadIdx.x];
+    }
+    __syncthreads();
+    const size_t i0 = sidx[0], i1 = sidx[1], i2 = sidx[2], i3 = sidx[3];
+    for (int blk = 0; blk < nblk; ++blk) {
+        const T* cb = coarse + (size_t)blk * C.nc * m;
+        const size_t off = ((size_t)blk * F.nc + c) * m;
+        if constexpr (sizeof(T) == 8) {
+            const double w0 = sw[0], w1 = sw[1], w2 = sw[2], w3 = sw[3];
+            for (int q = threadIdx.x; q < m; q += blockDim.x) {
+                double v = 0.0;
+                v += w0 * cb[i0 + q]; v += w1 * cb[i1 + q]; v += w2 * cb[i2 + q]; v += w3 * cb[i3 + q];
+                fine[off + q] = fine[off + q] + v;
+                if (out_pro) out_pro[off + q] = v;
+            }
+        } else {
+            const float w0 = (float)sw[0], w1 = (float)sw[1], w2 = (float)sw[2], w3 = (float)sw[3];
+            for (int q = threadIdx.x; q < m; q += blockDim.x) {
+                const float v = w0 * cb[i0 + q] + w1 * cb[i1 + q] + w2 * cb[i2 + q] + w3 * cb[i3 + q];
+                fine[off + q] = fine[off + q] + v;
+                if (out_pro) out_pro[off + q] = v;
+            }
+        }
+    }
+}
+
 template <typename T>
 cudaError_t launch_prolong_add(const LevelDev& F, const LevelDev& C, int m, int nblk, const int* idx4,
                                const double* w4, const T* coarse, T* fine, T* out_pro, cudaStream_t st)
 {
+    if (m >= 32) {
+        k_prolong_rows<T><<<F.nc, 256, 0, st>>>(F, C, m, nblk, idx4, w4, coarse, fine, out_pro);
+        return cudaGetLastError();
+    }
     size_t n = (size_t)F.nc * m * nblk;
     k_prolong_add<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(F, C, m, nblk, idx4, w4, coarse, fine, out_pro);
     return cudaGetLastError();

@@ -69,6 +69,11 @@ __device__ __forceinline__ F geomD(const LevelDev& L, int i, int j, F u, F v)
 {
     return fabs(u) * (F)L.rdx[i] + fabs(v) * (F)L.rdy[j];
 }
+template <typename F>
+__device__ __forceinline__ F geomD_r(F rdxi, F rdyj, F u, F v)
+{
+    return fabs(u) * rdxi + fabs(v) * rdyj;
+}
 
 // coefficient (1/V) u_n S of a neighbour (or ghost) through the face with outward normal
 // outsign * e_axis, zero unless u_n < 0; rS = S/V = 1/dx (x-faces) or 1/dy (y-faces)
@@ -98,30 +103,64 @@ __global__ void __launch_bounds__(256) k_micro_residual(MicroArgs M, GasDev gas,
     const int c = blockIdx.x, nv = Vg.nv, nx = L.nx;
     const int i = c % nx, j = c / nx;
     const size_t nc = L.nc;
-    double* cs = sm;                            // cell scalars
-    F* Eu = reinterpret_cast<F*>(sm + 8);
+    // cell constants: FP64 state from thread 0, then one constant per lane of warp 0
+    // (an FP64 instruction costs a warp as much as thirty-two lanes of it)
+    double* cs = sm;                            // cell scalars (FP64), [8]
+    F* cf = reinterpret_cast<F*>(sm + 8);       // cell constants in F, [16]
+    F* Eu = reinterpret_cast<F*>(sm + 24);
     F* Ev = Eu + Vg.nu;
     if (threadIdx.x == 0) {
         double rho, U, V, lam;
         prim4(Wt + 4 * (size_t)c, rho, U, V, lam);
-        double it = 1.0 / tau_of(gas, rho, lam);
+        double it;
+        if constexpr (sizeof(F) == 8) it = 1.0 / tau_of(gas, rho, lam);
+        else it = (double)(1.0f / tau_of_f(gas, (float)rho, (float)lam));
         cs[0] = rho; cs[1] = U; cs[2] = V; cs[3] = lam; cs[4] = it;
         inv_tau[c] = it + dtn_inv;
     }
     __syncthreads();
-    const double rho = cs[0], U = cs[1], V = cs[2], lam = cs[3], itau = cs[4];
-    for (int a = threadIdx.x; a < Vg.nu; a += blockDim.x) { double d = Vg.ua[a] - U; Eu[a] = (F)exp(-lam * d * d); }
-    for (int b = threadIdx.x; b < Vg.nvv; b += blockDim.x) { double d = Vg.vb[b] - V; Ev[b] = (F)exp(-lam * d * d); }
+    {
+        const double rho = cs[0], U = cs[1], V = cs[2], lam = cs[3], itau = cs[4];
+        const int t = threadIdx.x;
+        if (t < 32) {
+            F val = F(0);
+            switch (t) {
+            case 0: val = (F)(rho * lam / kPi); break;
+            case 1: val = (F)(kKint / (4.0 * lam)); break;
+            case 2: val = (F)(2.0 * lam); break;
+            case 3: val = (F)((1.0 - gas.pr) * 4.0 * lam * lam / (5.0 * rho)); break;
+            case 4: val = (F)q[2 * (size_t)c]; break;
+            case 5: val = (F)q[2 * (size_t)c + 1]; break;
+            case 6: val = (F)U; break;
+            case 7: val = (F)V; break;
+            case 8: val = (F)L.rdx[i]; break;
+            case 9: val = (F)L.rdy[j]; break;
+            case 10: val = (F)itau; break;
+            case 11: val = (F)(itau + dtn_inv); break;
+            default: break;
+            }
+            if (t < 12) cf[t] = val;
+        } else {
+            for (int e = t - 32; e < Vg.nu + Vg.nvv; e += blockDim.x - 32) {
+                const bool isu = e < Vg.nu;
+                const double d = isu ? Vg.ua[e] - U : Vg.vb[e - Vg.nu] - V;
+                F ex;
+                if constexpr (sizeof(F) == 8) ex = exp(-lam * d * d);
+                else ex = expf((float)(-lam * d * d));
+                (isu ? Eu[e] : Ev[e - Vg.nu]) = ex;
+            }
+        }
+    }
     __syncthreads();
-    const F gnorm = (F)(rho * lam / kPi), hfac = (F)(kKint / (4.0 * lam)), flam2 = (F)(2.0 * lam);
-    const F shk = (F)((1.0 - gas.pr) * 4.0 * lam * lam / (5.0 * rho));
-    const F qx = (F)q[2 * (size_t)c], qy = (F)q[2 * (size_t)c + 1], fU = (F)U, fV = (F)V;
-    const F rdxi = (F)L.rdx[i], rdyj = (F)L.rdy[j], fitau = (F)itau, fdiag = (F)(itau + dtn_inv);
+    const F gnorm = cf[0], hfac = cf[1], flam2 = cf[2], shk = cf[3], qx = cf[4], qy = cf[5], fU = cf[6], fV = cf[7];
+    const F rdxi = cf[8], rdyj = cf[9], fitau = cf[10], fdiag = cf[11];
+    const F* __restrict__ vu = VelT<F>::u(Vg);
+    const F* __restrict__ vv = VelT<F>::v(Vg);
     const size_t nfx = L.nfx, nfy = L.nfy;
     const size_t fW = (size_t)j * (nx + 1) + i, fE = fW + 1, fS = (size_t)j * nx + i, fN = (size_t)(j + 1) * nx + i;
     for (int k = threadIdx.x; k < nv; k += blockDim.x) {
         int a = k / Vg.nvv, b = k - a * Vg.nvv;
-        const F u = (F)Vg.u[k], v = (F)Vg.v[k];
+        const F u = vu[k], v = vv[k];
         F cx = u - fU, cy = v - fV, c2 = cx * cx + cy * cy;
         F gM = gnorm * Eu[a] * Ev[b], hM = gM * hfac;
         F Fq = shk * (cx * qx + cy * qy);
@@ -133,7 +172,7 @@ __global__ void __launch_bounds__(256) k_micro_residual(MicroArgs M, GasDev gas,
             F div = (px[fE * nv + k] - px[fW * nv + k]) * rdxi + (py[fN * nv + k] - py[fS * nv + k]) * rdyj;
             r[(cp * nc + c) * nv + k] = (gt[cp] - f[(cp * nc + c) * nv + k]) * fitau - div;
         }
-        invD[(size_t)c * nv + k] = recip(fdiag + geomD<F>(L, i, j, u, v));
+        invD[(size_t)c * nv + k] = recip(fdiag + geomD_r<F>(rdxi, rdyj, u, v));
     }
 }
 
@@ -142,7 +181,7 @@ cudaError_t launch_micro_residual(const MicroArgs& m, GasDev gas, const double* 
                                   const F* phx, const F* phy, double dtn_inv, double* inv_tau, F* invD, F* r,
                                   cudaStream_t st)
 {
-    size_t smem = sizeof(double) * 8 + sizeof(F) * (m.V.nu + m.V.nvv);
+    size_t smem = sizeof(double) * 24 + sizeof(F) * (m.V.nu + m.V.nvv);
     k_micro_residual<F><<<m.L.nc, m.V.nv >= 256 ? 256 : 128, smem, st>>>(m, gas, Wt, q, f, phx, phy, dtn_inv,
                                                                           inv_tau, invD, r);
     return cudaGetLastError();
@@ -160,17 +199,23 @@ __global__ void k_coarse_coeffs(MicroArgs M, GasDev gas, const double* __restric
 {
     const LevelDev& L = M.L;
     const int c = blockIdx.x, i = c % L.nx, j = c / L.nx;
-    __shared__ double sit;
+    __shared__ F sc[3];
     if (threadIdx.x == 0) {
         double rho, U, V, lam;
         prim4(Wt + 4 * (size_t)c, rho, U, V, lam);
-        sit = 1.0 / tau_of(gas, rho, lam) + dtn_inv;
-        inv_tau[c] = sit;
+        double it;
+        if constexpr (sizeof(F) == 8) it = 1.0 / tau_of(gas, rho, lam);
+        else it = (double)(1.0f / tau_of_f(gas, (float)rho, (float)lam));
+        it += dtn_inv;
+        inv_tau[c] = it;
+        sc[0] = (F)it; sc[1] = (F)L.rdx[i]; sc[2] = (F)L.rdy[j];
     }
     __syncthreads();
-    const double it = sit;
+    const F fit = sc[0], rdxi = sc[1], rdyj = sc[2];
+    const F* __restrict__ vu = VelT<F>::u(M.V);
+    const F* __restrict__ vv = VelT<F>::v(M.V);
     for (int k = threadIdx.x; k < M.V.nv; k += blockDim.x)
-        invD[(size_t)c * M.V.nv + k] = recip((F)it + geomD<F>(L, i, j, (F)M.V.u[k], (F)M.V.v[k]));
+        invD[(size_t)c * M.V.nv + k] = recip(fit + geomD_r<F>(rdxi, rdyj, vu[k], vv[k]));
 }
 
 template <typename F>
@@ -979,15 +1024,18 @@ __global__ void __launch_bounds__(256) k_micro_renew(MicroArgs M, const double* 
     const int c = blockIdx.x, nx = L.nx, ny = L.ny, nv = Vg.nv, i = c % nx, j = c / nx;
     const size_t nc = L.nc;
     if (acc)
-        for (int e = threadIdx.x; e < 2 * nv; e += blockDim.x) {
-            int cp = e / nv, k = e - cp * nv;
-            size_t id = (cp * nc + c) * nv + k;
-            acc[id] = acc[id] + x[id];
-        }
+        for (int cp = 0; cp < 2; ++cp)
+            for (int k = threadIdx.x; k < nv; k += blockDim.x) {
+                size_t id = (cp * nc + c) * nv + k;
+                acc[id] = acc[id] + x[id];
+            }
     if (!renew) return;
     BFace bf[4];
     int nb = side_faces(L, i, j, 2, bf);
-    F rho[4] = {0, 0, 0, 0};
+    __shared__ F srho[4], sgeo[3];
+    const F* __restrict__ vu = VelT<F>::u(Vg);
+    const F* __restrict__ vv = VelT<F>::v(Vg);
+    const F* __restrict__ vw = VelT<F>::w(Vg);
     int nwall = 0;
     for (int b = 0; b < nb; ++b) nwall += M.bc[bf[b].bc].type == BC_WALL;
     if (nwall > 0) {
@@ -995,42 +1043,51 @@ __global__ void __launch_bounds__(256) k_micro_renew(MicroArgs M, const double* 
         for (int k = threadIdx.x; k < nv; k += blockDim.x)
             for (int b = 0; b < nb; ++b) {
                 if (M.bc[bf[b].bc].type != BC_WALL) continue;
-                F uo = (F)(bf[b].axis == 0 ? Vg.u[k] : Vg.v[k]);
+                F uo = bf[b].axis == 0 ? vu[k] : vv[k];
                 uo = bf[b].outsign < 0 ? -uo : uo;
-                if (uo > F(0)) sa[b].add((F)Vg.w[k] * uo * x[c * (size_t)nv + k]);
+                if (uo > F(0)) sa[b].add(vw[k] * uo * x[c * (size_t)nv + k]);
             }
-        double sd[4] = {sa[0].value(), sa[1].value(), sa[2].value(), sa[3].value()};
-        block_sum<4>(sd, red);
-        for (int b = 0; b < nb; ++b)
-            if (M.bc[bf[b].bc].type == BC_WALL)
-                rho[b] = (F)(-sd[b] / Zw[bf[b].bc * 4 + bf[b].axis * 2 + (bf[b].outsign > 0)]);
+        double sd[4];
+        block_total<4>(sa, red, sd);
+        if (threadIdx.x == 0)
+            for (int b = 0; b < 4; ++b)
+                srho[b] = b < nb && M.bc[bf[b].bc].type == BC_WALL
+                              ? (F)(-sd[b] / Zw[bf[b].bc * 4 + bf[b].axis * 2 + (bf[b].outsign > 0)]) : F(0);
     }
-    const F itau = (F)M.inv_tau[c], rdxi = (F)L.rdx[i], rdyj = (F)L.rdy[j];
-    for (int e = threadIdx.x; e < 2 * nv; e += blockDim.x) {
-        int cp = e / nv, k = e - cp * nv;
-        const F u = (F)Vg.u[k], v = (F)Vg.v[k];
+    if (threadIdx.x == 0) {
+        sgeo[0] = (F)M.inv_tau[c]; sgeo[1] = (F)L.rdx[i]; sgeo[2] = (F)L.rdy[j];
+        if (nwall == 0) srho[0] = srho[1] = srho[2] = srho[3] = F(0);
+    }
+    __syncthreads();
+    F rho[4] = {srho[0], srho[1], srho[2], srho[3]};
+    const F itau = sgeo[0], rdxi = sgeo[1], rdyj = sgeo[2];
+    for (int cp = 0; cp < 2; ++cp) {
         const F* xb = x + cp * nc * nv;
-        size_t id = (size_t)c * nv + k;
-        F a = (itau + geomD<F>(L, i, j, u, v)) * xb[id];
-        if (i > 0) a += Dface<F>(0, -1, rdxi, u, v) * xb[id - nv];
-        if (i < nx - 1) a += Dface<F>(0, 1, rdxi, u, v) * xb[id + nv];
-        if (j > 0) a += Dface<F>(1, -1, rdyj, u, v) * xb[id - (size_t)nx * nv];
-        if (j < ny - 1) a += Dface<F>(1, 1, rdyj, u, v) * xb[id + (size_t)nx * nv];
-        for (int b = 0; b < nb; ++b) {
-            F Db = Dface<F>(bf[b].axis, bf[b].outsign, (F)bf[b].rS, u, v);
-            if (Db == F(0)) continue;
-            int ty = M.bc[bf[b].bc].type;
-            if (ty == BC_WALL)
-                a += Db * (F)(M.Cw[(size_t)bf[b].bc * nv + k] * (cp == 0 ? 1.0 : kKint * M.bc[bf[b].bc].t / 4.0)) * rho[b];
-            else if (ty == BC_SYMMETRY) {
-                int aa = k / Vg.nvv, bb = k - aa * Vg.nvv;
-                int km = bf[b].axis == 0 ? (Vg.nu - 1 - aa) * Vg.nvv + bb : aa * Vg.nvv + (Vg.nvv - 1 - bb);
-                a += Db * xb[(size_t)c * nv + km];
-            } else if (ty == BC_OUTFLOW) {
-                a += Db * xb[id];
+        F* rb = r + cp * nc * nv;
+        for (int k = threadIdx.x; k < nv; k += blockDim.x) {
+            const F u = vu[k], v = vv[k];
+            size_t id = (size_t)c * nv + k;
+            F a = (itau + geomD_r<F>(rdxi, rdyj, u, v)) * xb[id];
+            if (i > 0) a += Dface<F>(0, -1, rdxi, u, v) * xb[id - nv];
+            if (i < nx - 1) a += Dface<F>(0, 1, rdxi, u, v) * xb[id + nv];
+            if (j > 0) a += Dface<F>(1, -1, rdyj, u, v) * xb[id - (size_t)nx * nv];
+            if (j < ny - 1) a += Dface<F>(1, 1, rdyj, u, v) * xb[id + (size_t)nx * nv];
+            for (int b = 0; b < nb; ++b) {
+                F Db = Dface<F>(bf[b].axis, bf[b].outsign, (F)bf[b].rS, u, v);
+                if (Db == F(0)) continue;
+                int ty = M.bc[bf[b].bc].type;
+                if (ty == BC_WALL)
+                    a += Db * (F)(M.Cw[(size_t)bf[b].bc * nv + k] * (cp == 0 ? 1.0 : kKint * M.bc[bf[b].bc].t / 4.0)) * rho[b];
+                else if (ty == BC_SYMMETRY) {
+                    int aa = k / Vg.nvv, bb = k - aa * Vg.nvv;
+                    int km = bf[b].axis == 0 ? (Vg.nu - 1 - aa) * Vg.nvv + bb : aa * Vg.nvv + (Vg.nvv - 1 - bb);
+                    a += Db * xb[(size_t)c * nv + km];
+                } else if (ty == BC_OUTFLOW) {
+                    a += Db * xb[id];
+                }
             }
+            rb[id] = rb[id] - a;
         }
-        r[cp * nc * nv + id] = r[cp * nc * nv + id] - a;
     }
 }
 
@@ -1055,8 +1112,12 @@ __global__ void __launch_bounds__(256) k_update_moments(LevelDev L, VelDev Vg, F
     __shared__ double red[32 * 4];
     const int c = blockIdx.x, nv = Vg.nv;
     const size_t nc = L.nc;
+    __shared__ F sUV[2];
     F* fG = f + (size_t)c * nv;
     F* fH = f + (nc + c) * (size_t)nv;
+    const F* __restrict__ vu = VelT<F>::u(Vg);
+    const F* __restrict__ vv = VelT<F>::v(Vg);
+    const F* __restrict__ vw = VelT<F>::w(Vg);
     Acc<F> sa[4];
     for (int k = threadIdx.x; k < nv; k += blockDim.x) {
         F g = fG[k], h = fH[k];
@@ -1065,20 +1126,25 @@ __global__ void __launch_bounds__(256) k_update_moments(LevelDev L, VelDev Vg, F
             h = h + df[(nc + c) * (size_t)nv + k];
             fG[k] = g; fH[k] = h;
         }
-        const F u = (F)Vg.u[k], v = (F)Vg.v[k], w = (F)Vg.w[k];
+        const F u = vu[k], v = vv[k], w = vw[k];
         sa[0].add(w * g); sa[1].add(w * u * g); sa[2].add(w * v * g);
         sa[3].add(w * (F(0.5) * (u * u + v * v) * g + h));
     }
     double s[4];
     block_total<4>(sa, red, s);
-    const double ir = rcp64(s[0]);
-    const F fU = (F)(s[1] * ir), fV = (F)(s[2] * ir);
+    if (threadIdx.x == 0) {
+        const double ir = rcp64(s[0]);
+        sUV[0] = (F)(s[1] * ir);
+        sUV[1] = (F)(s[2] * ir);
+    }
+    __syncthreads();
+    const F fU = sUV[0], fV = sUV[1];
     Acc<F> ta[2];
     for (int k = threadIdx.x; k < nv; k += blockDim.x) {
-        F cx = (F)Vg.u[k] - fU, cy = (F)Vg.v[k] - fV;
+        F cx = vu[k] - fU, cy = vv[k] - fV;
         F e = F(0.5) * (cx * cx + cy * cy) * fG[k] + fH[k];
-        ta[0].add((F)Vg.w[k] * cx * e);
-        ta[1].add((F)Vg.w[k] * cy * e);
+        ta[0].add(vw[k] * cx * e);
+        ta[1].add(vw[k] * cy * e);
     }
     double t[2];
     block_total<2>(ta, red, t);
