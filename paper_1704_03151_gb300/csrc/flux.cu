@@ -446,30 +446,31 @@ cudaError_t launch_cell_residual(const LevelDev& L, const double* Fx, const doub
 }
 
 // sum of squares of R per component: per-block partials, then one block
-__global__ void k_rms_partial(const double* __restrict__ R, int nc, double* __restrict__ part)
+// partial sums of R^2 per component and the count of unphysical cells
+// (non-positive density or internal energy, or NaN) per CTA
+__global__ void k_rms_partial(const double* __restrict__ R, const double* __restrict__ W, int nc,
+                              double* __restrict__ part)
 {
-    __shared__ double red[32 * 4];
-    double s[4] = {0, 0, 0, 0};
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x)
+    __shared__ double red[32 * 5];
+    double s[5] = {0, 0, 0, 0, 0};
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
         for (int m = 0; m < 4; ++m) s[m] += R[4 * (size_t)c + m] * R[4 * (size_t)c + m];
-    block_sum<4>(s, red);
+        const double* w = W + 4 * (size_t)c;
+        // rho e_int = E - |m|^2 / (2 rho), tested as rho E - |m|^2 / 2 > 0 with rho > 0
+        const double e2 = w[3] * w[0] - 0.5 * (w[1] * w[1] + w[2] * w[2]);
+        if (!(w[0] > 0.0) || !(e2 > 0.0)) s[4] += 1.0;
+    }
+    block_sum<5>(s, red);
     if (threadIdx.x == 0)
-        for (int m = 0; m < 4; ++m) part[4 * blockIdx.x + m] = s[m];
+        for (int m = 0; m < 5; ++m) part[5 * blockIdx.x + m] = s[m];
 }
 
-__global__ void k_rms_final(const double* __restrict__ part, int nblk, int nc, const double* __restrict__ W,
-                            double* __restrict__ out)
+__global__ void k_rms_final(const double* __restrict__ part, int nblk, int nc, double* __restrict__ out)
 {
     __shared__ double red[32 * 5];
     double s[5] = {0, 0, 0, 0, 0};
     for (int b = threadIdx.x; b < nblk; b += blockDim.x)
-        for (int m = 0; m < 4; ++m) s[m] += part[4 * b + m];
-    // health of the state: count cells with non-positive density or internal energy (or NaN)
-    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
-        const double* w = W + 4 * (size_t)c;
-        double eint = w[3] - 0.5 * (w[1] * w[1] + w[2] * w[2]) / w[0];
-        if (!(w[0] > 0.0) || !(eint > 0.0)) s[4] += 1.0;
-    }
+        for (int m = 0; m < 5; ++m) s[m] += part[5 * b + m];
     block_sum<5>(s, red);
     if (threadIdx.x == 0) {
         for (int m = 0; m < 4; ++m) out[m] = sqrt(s[m] / nc);
@@ -480,8 +481,8 @@ __global__ void k_rms_final(const double* __restrict__ part, int nblk, int nc, c
 cudaError_t launch_rms(const double* R, const double* W, int nc, double* part, double* out, cudaStream_t st)
 {
     int nblk = 64;
-    k_rms_partial<<<nblk, 256, 0, st>>>(R, nc, part);
-    k_rms_final<<<1, 256, 0, st>>>(part, nblk, nc, W, out);
+    k_rms_partial<<<nblk, 256, 0, st>>>(R, W, nc, part);
+    k_rms_final<<<1, 64, 0, st>>>(part, nblk, nc, out);
     return cudaGetLastError();
 }
 

@@ -182,49 +182,53 @@ __device__ __forceinline__ double face_gamma(const LevelDev& L, const double* gx
     return axis == 0 ? gx[j * (L.nx + 1) + i + up] : gy[(j + up) * L.nx + i];
 }
 
-// R_E of one cell: -(1/V) sum_faces S F_split(W_i, W_j)
-__device__ void macro_resid_cell(const MacroArgs& a, const double* W, const double* gx, const double* gy,
-                                 int i, int j, double RE[4])
-{
-    const LevelDev& L = a.L;
-    int c = j * L.nx + i;
-    double V = L.dx[i] * L.dy[j], acc[4] = {0, 0, 0, 0};
-    const double* Wi = W + 4 * (size_t)c;
-    double Ti[4][4];
-    #pragma unroll
-    for (int f = 0; f < 4; ++f) {
-        int axis = f >> 1, up = f & 1;
-        double sgn = up ? 1.0 : -1.0, S = axis == 0 ? L.dy[j] : L.dx[i];
-        int bcid, nb; double dum = 0;
-        face_of(L, i, j, f, bcid, nb, dum);
-        double G[4], Tj[4];
-        const double* Wj;
-        if (bcid >= 0) { macro_ghost(a.bc[bcid], axis, Wi, G, nullptr); Wj = G; }
-        else Wj = W + 4 * (size_t)nb;
-        euler_flux(Wi, axis, sgn, Ti[f]);
-        euler_flux(Wj, axis, sgn, Tj);
-        double gm = face_gamma(L, gx, gy, i, j, f);
-        for (int m = 0; m < 4; ++m) acc[m] += S * (0.5 * (Ti[f][m] + Tj[m] + gm * (Wi[m] - Wj[m])));
-    }
-    for (int m = 0; m < 4; ++m) RE[m] = -acc[m] / V;
-}
-
+// R_E of a cell: -(1/V) sum_faces S F_split(W_i, W_j).  Four lanes per cell,
+// one face each (the FP64 latency of a cell is spread over four lanes); the
+// face terms are added in face order.
 __global__ void k_macro_resid(MacroArgs a, const double* __restrict__ W, const double* __restrict__ gx,
                               const double* __restrict__ gy, const double* __restrict__ Rin, double* __restrict__ out,
                               int mode)
 {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= a.L.nc) return;
-    double RE[4];
-    macro_resid_cell(a, W, gx, gy, c % a.L.nx, c / a.L.nx, RE);
-    for (int m = 0; m < 4; ++m)
-        out[4 * (size_t)c + m] = mode == 0 ? Rin[4 * (size_t)c + m] - RE[m] : Rin[4 * (size_t)c + m] + RE[m];
+    const LevelDev& L = a.L;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = t >> 2, f = t & 3;
+    const bool on = c < L.nc;
+    const int cc = on ? c : 0, i = cc % L.nx, j = cc / L.nx;
+    const double* Wi = W + 4 * (size_t)cc;
+    double term[4];
+    {
+        const int axis = f >> 1, up = f & 1;
+        const double sgn = up ? 1.0 : -1.0, S = axis == 0 ? L.dy[j] : L.dx[i];
+        int bcid, nb; double dum = 0;
+        face_of(L, i, j, f, bcid, nb, dum);
+        double G[4], Ti[4], Tj[4];
+        const double* Wj;
+        if (bcid >= 0) { macro_ghost(a.bc[bcid], axis, Wi, G, nullptr); Wj = G; }
+        else Wj = W + 4 * (size_t)nb;
+        euler_flux(Wi, axis, sgn, Ti);
+        euler_flux(Wj, axis, sgn, Tj);
+        const double gm = face_gamma(L, gx, gy, i, j, f);
+        for (int m = 0; m < 4; ++m) term[m] = S * (0.5 * (Ti[m] + Tj[m] + gm * (Wi[m] - Wj[m])));
+    }
+    const int base = threadIdx.x & ~3;
+    double acc[4] = {0, 0, 0, 0};
+    #pragma unroll
+    for (int q = 0; q < 4; ++q)
+        #pragma unroll
+        for (int m = 0; m < 4; ++m) acc[m] += __shfl_sync(0xffffffffu, term[m], (base + q) & 31);
+    if (on && f == 0) {
+        const double V = L.dx[i] * L.dy[j];
+        for (int m = 0; m < 4; ++m) {
+            const double RE = -acc[m] / V;
+            out[4 * (size_t)c + m] = mode == 0 ? Rin[4 * (size_t)c + m] - RE : Rin[4 * (size_t)c + m] + RE;
+        }
+    }
 }
 
 cudaError_t launch_macro_resid(const MacroArgs& a, const double* W, const double* gx, const double* gy,
                                const double* Rin, double* out, int mode, cudaStream_t st)
 {
-    k_macro_resid<<<(a.L.nc + 127) / 128, 128, 0, st>>>(a, W, gx, gy, Rin, out, mode);
+    k_macro_resid<<<(4 * a.L.nc + 127) / 128, 128, 0, st>>>(a, W, gx, gy, Rin, out, mode);
     return cudaGetLastError();
 }
 

@@ -1023,12 +1023,27 @@ __global__ void __launch_bounds__(256) k_micro_renew(MicroArgs M, const double* 
     const VelDev& Vg = M.V;
     const int c = blockIdx.x, nx = L.nx, ny = L.ny, nv = Vg.nv, i = c % nx, j = c / nx;
     const size_t nc = L.nc;
-    if (acc)
-        for (int cp = 0; cp < 2; ++cp)
-            for (int k = threadIdx.x; k < nv; k += blockDim.x) {
-                size_t id = (cp * nc + c) * nv + k;
-                acc[id] = acc[id] + x[id];
-            }
+    const bool vec = sizeof(F) == 4 && (nv & 3) == 0;   // 16-byte accesses over four velocities
+    if (acc) {
+        if (vec) {
+            for (int cp = 0; cp < 2; ++cp)
+                for (int g = threadIdx.x; g < nv / 4; g += blockDim.x) {
+                    const size_t id = (cp * nc + c) * nv + 4 * g;
+                    F xa[4], aa[4];
+                    ld4(x + id, xa);
+                    ld4(acc + id, aa);
+                    #pragma unroll
+                    for (int q = 0; q < 4; ++q) aa[q] = aa[q] + xa[q];
+                    st4(acc + id, aa);
+                }
+        } else {
+            for (int cp = 0; cp < 2; ++cp)
+                for (int k = threadIdx.x; k < nv; k += blockDim.x) {
+                    size_t id = (cp * nc + c) * nv + k;
+                    acc[id] = acc[id] + x[id];
+                }
+        }
+    }
     if (!renew) return;
     BFace bf[4];
     int nb = side_faces(L, i, j, 2, bf);
@@ -1061,6 +1076,44 @@ __global__ void __launch_bounds__(256) k_micro_renew(MicroArgs M, const double* 
     __syncthreads();
     F rho[4] = {srho[0], srho[1], srho[2], srho[3]};
     const F itau = sgeo[0], rdxi = sgeo[1], rdyj = sgeo[2];
+    if (vec && nb == 0) {
+        // interior cell: four velocities per thread, both components, 16-byte accesses
+        for (int g = threadIdx.x; g < nv / 4; g += blockDim.x) {
+            F u[4], v[4], cW[4], cE[4], cS[4], cN[4], dg[4];
+            ld4(vu + 4 * g, u);
+            ld4(vv + 4 * g, v);
+            #pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                dg[q] = itau + geomD_r<F>(rdxi, rdyj, u[q], v[q]);
+                cW[q] = Dface<F>(0, -1, rdxi, u[q], v[q]);
+                cE[q] = Dface<F>(0, 1, rdxi, u[q], v[q]);
+                cS[q] = Dface<F>(1, -1, rdyj, u[q], v[q]);
+                cN[q] = Dface<F>(1, 1, rdyj, u[q], v[q]);
+            }
+            #pragma unroll
+            for (int cp = 0; cp < 2; ++cp) {
+                const size_t id = (cp * nc + c) * nv + 4 * g;
+                F xc[4], xw[4], xe[4], xs[4], xn[4], rr[4];
+                ld4(x + id, xc);
+                ld4(x + id - nv, xw);
+                ld4(x + id + nv, xe);
+                ld4(x + id - (size_t)nx * nv, xs);
+                ld4(x + id + (size_t)nx * nv, xn);
+                ld4(r + id, rr);
+                #pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    F a = dg[q] * xc[q];
+                    a += cW[q] * xw[q];
+                    a += cE[q] * xe[q];
+                    a += cS[q] * xs[q];
+                    a += cN[q] * xn[q];
+                    rr[q] = rr[q] - a;
+                }
+                st4(r + id, rr);
+            }
+        }
+        return;
+    }
     for (int cp = 0; cp < 2; ++cp) {
         const F* xb = x + cp * nc * nv;
         F* rb = r + cp * nc * nv;

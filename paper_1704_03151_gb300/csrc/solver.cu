@@ -612,7 +612,7 @@ miugks_status miugks_create(const miugks_mesh* mesh, const miugks_vgrid* vg, con
         if ((st = falloc(s, &s->phy, 2 * (size_t)L0.nfy * nv)) != MIUGKS_OK) break;
         if ((st = dalloc(s, &s->Fx, 4 * (size_t)L0.nfx)) != MIUGKS_OK) break;
         if ((st = dalloc(s, &s->Fy, 4 * (size_t)L0.nfy)) != MIUGKS_OK) break;
-        if ((st = dalloc(s, &s->rms_part, 64 * 4)) != MIUGKS_OK) break;
+        if ((st = dalloc(s, &s->rms_part, 64 * 5)) != MIUGKS_OK) break;
         if ((st = dalloc(s, &s->rms_out, 8)) != MIUGKS_OK) break;
         if (cudaMemset(s->rms_out, 0, 8 * sizeof(double)) != cudaSuccess) { st = fail(s, MIUGKS_ECUDA, "cudaMemset"); break; }
         if ((st = falloc(s, &s->xcorner, micro_scratch_elems(nv, mesh->nx + mesh->ny))) != MIUGKS_OK) break;
