@@ -76,6 +76,14 @@ def lib():
         L.oracle_stage_prolong.argtypes = [vp, i, i, vp, vp]
         L.oracle_level_size.argtypes = [vp, i, P(i), P(i)]
         L.oracle_nv.argtypes = [vp]
+        L.oracle_time_coeffs_dtau.argtypes = [d, d, vp]
+        L.oracle_time_coeffs_dtau.restype = None
+        L.oracle_micro_slope_adj.argtypes = [vp, d, d, d, vp, vp, vp]
+        L.oracle_micro_slope_adj.restype = None
+        L.oracle_steady_residual.argtypes = [vp, vp]
+        L.oracle_adjoint_residual.argtypes = [vp, vp, vp]
+        L.oracle_objective.argtypes = [vp, i, i, vp, vp, vp]
+        L.oracle_residual_dtheta.argtypes = [vp, i, i, vp]
         _lib = L
     return _lib
 
@@ -170,6 +178,36 @@ class Oracle:
 
     def iterations(self):
         return lib().oracle_iterations(self.h)
+
+    # ---- steady equations and their adjoint ----
+    def steady_residual(self):
+        """N(f) of the steady equations at the current f (Eq. microResidualDef
+        with the predicted state equal to the moments of f)."""
+        N = np.zeros((2, self.nc, self.nv))
+        _check(lib().oracle_steady_residual(self.h, _p(N)))
+        return N
+
+    def adjoint_residual(self, mu):
+        """(dN/df)^T mu at the current f."""
+        mu = np.ascontiguousarray(mu, dtype=np.float64).reshape(2, self.nc, self.nv)
+        out = np.zeros_like(mu)
+        _check(lib().oracle_adjoint_residual(self.h, _p(mu), _p(out)))
+        return out
+
+    def objective(self, obj, bc):
+        """J = sum over the faces of wall `bc` of face length x (shear, heat
+        flux, pressure)[obj]; returns J, dJ/df and dJ/d(T, u, v) of that wall."""
+        J = np.zeros(1)
+        dJdf = np.zeros((2, self.nc, self.nv))
+        dJdth = np.zeros(3)
+        _check(lib().oracle_objective(self.h, obj, bc, _p(J), _p(dJdf), _p(dJdth)))
+        return float(J[0]), dJdf, dJdth
+
+    def residual_dtheta(self, bc, param):
+        """dN/dtheta at fixed f, theta = (T, u, v)[param] of wall `bc`."""
+        dN = np.zeros((2, self.nc, self.nv))
+        _check(lib().oracle_residual_dtheta(self.h, bc, param, _p(dN)))
+        return dN
 
     # ---- stages for the pins ----
     def level_size(self, lev):
@@ -266,3 +304,67 @@ def wall_ghost(W, Uw, Vw, Tw):
     G = np.zeros(4)
     lib().oracle_wall_ghost(_p(W), Uw, Vw, Tw, _p(G))
     return G
+
+
+def time_coeffs_dtau(dt, tau):
+    q = np.zeros(5)
+    lib().oracle_time_coeffs_dtau(dt, tau, _p(q))
+    return q
+
+
+def micro_slope_adj(dw, U, V, lam, abar):
+    """Reverse of micro_slope: returns (dL/d dw, dL/d(U, V, lam)) for dL/da = abar."""
+    dw = np.ascontiguousarray(dw, dtype=np.float64)
+    ab = np.ascontiguousarray(abar, dtype=np.float64)
+    dwb, pb = np.zeros(4), np.zeros(3)
+    lib().oracle_micro_slope_adj(_p(dw), U, V, lam, _p(ab), _p(dwb), _p(pb))
+    return dwb, pb
+
+
+def closed_domain(case):
+    """True when every boundary is a wall or a symmetry plane: the steady
+    equations then fix the state only up to its total mass."""
+    return all(b["type"] in (WALL, SYMMETRY) for b in case["bcs"])
+
+
+def mass_weights(o):
+    """dM/df of the total mass M = sum_i V_i sum_k w_k G_i,k (2 x nc x nv)."""
+    c = o.case
+    vg = c["vgrid"]
+    _, wu = vgrid(vg["nu"], vg["umin"], vg["umax"], vg["rule"])
+    _, wv = vgrid(vg["nv"], vg["vmin"], vg["vmax"], vg["rule"])
+    V = np.outer(np.diff(c["y_nodes"]), np.diff(c["x_nodes"])).ravel()
+    m = np.zeros((2, o.nc, o.nv))
+    m[0] = V[:, None] * np.outer(wu, wv).ravel()[None, :]
+    return m
+
+
+def adjoint_matrix(o):
+    """Dense (dN/df)^T at the current f, column by column from adjoint_residual
+    (tiny problems only)."""
+    n = 2 * o.nc * o.nv
+    A = np.zeros((n, n))
+    e = np.zeros(n)
+    for i in range(n):
+        e[i] = 1.0
+        A[:, i] = o.adjoint_residual(e).ravel()
+        e[i] = 0.0
+    return A
+
+
+def adjoint_gradient(o, obj, bc, param, A=None):
+    """Gradient of the wall objective J with respect to theta = (T, u, v)[param]
+    of wall `bc` at the current (converged) f of oracle `o`: dense solve of
+    (dN/df)^T lambda = -(dJ/df)^T, then dJ/dtheta = dJ/dtheta|_f + lambda .
+    dN/dtheta|_f.  In a closed domain the total mass is held fixed: the
+    transposed Jacobian gets the rank-one term -m m^T/|m|^2 (m = dM/df), which
+    leaves the fixed-mass derivative unchanged.  Returns (gradient, lambda)."""
+    if A is None:
+        A = adjoint_matrix(o)
+    if closed_domain(o.case):
+        m = mass_weights(o).ravel()
+        A = A - np.outer(m, m) / np.dot(m, m)
+    J, dJdf, dJdth = o.objective(obj, bc)
+    lam = np.linalg.solve(A, -dJdf.ravel())
+    dN = o.residual_dtheta(bc, param)
+    return float(dJdth[param] + np.dot(lam, dN.ravel())), lam.reshape(2, o.nc, o.nv)

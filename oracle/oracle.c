@@ -7,6 +7,11 @@
  * order the paper states the steps.  Where the paper is silent the reading
  * taken is stated at the function (and listed in the design notes).
  *
+ * The last section differentiates the steady equations by hand (reverse
+ * mode) for the adjoint gradient of wall objectives; its pins are
+ * finite-difference and high-precision derivatives and converged forward
+ * solves (tests/test_oracle_adjoint.py).
+ *
  * Parity pins (tests/test_oracle_*.py) cover every function here except the
  * physical time step rule of face_dt(), which the paper leaves open and which
  * is therefore "parity unpinned" (both implementations follow the same rule).
@@ -1492,5 +1497,678 @@ int oracle_stage_prolong(oracle_solver *s, int lev, int m, const double *coarse,
 {
     if (lev < 0 || lev + 1 >= s->L) return fail("bad level");
     prolong_lv(&s->lev[lev], &s->lev[lev + 1], m, coarse, fine);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Steady equations and their adjoint.                                  */
+/*                                                                      */
+/* At convergence the outer iteration has Delta f = 0, which with the   */
+/* predicted state equal to the moments of f is the discrete steady     */
+/* equation N(f; theta) = 0 of Eq. microResidualDef:                    */
+/*   N_i,k = (g+_k(W_i, q_i) - f_i,k)/tau(W_i)                          */
+/*           - (1/V_i) sum_j S_ij Phi_ij,k / dt_p,                      */
+/* with W_i, q_i the moments of f_i and Phi the UGKS flux of Step 1.    */
+/* theta (a wall temperature or velocity) enters only through the       */
+/* diffuse wall (Sec. 3.2).  For an objective J(f; theta) the adjoint   */
+/* state solves (dN/df)^T lambda = -(dJ/df)^T and                       */
+/*   dJ/dtheta = dJ/dtheta|_f + lambda . dN/dtheta|_f.                   */
+/* The functions below are hand-written reverse-mode derivatives of     */
+/* the forward functions of this file, in the same order of operations. */
+/* ------------------------------------------------------------------ */
+
+/* d q_m / d tau of the five time integrals.  Closed form from
+ * d e/d tau = e x / tau; for x < 1 the series of oracle_time_coeffs
+ * differentiated term by term: q_m = dt^p s_m(x) gives
+ * dq_m/dtau = -(dt^p / tau) sum_n n c_mn x^n. */
+void oracle_time_coeffs_dtau(double dt, double tau, double dq[5])
+{
+    double x = dt / tau;
+    if (x < 1.0) {
+        double p[28];
+        p[0] = 1.0;
+        for (int n = 1; n < 28; ++n) p[n] = p[n - 1] * x / n; /* x^n / n! */
+        double s1 = 0, s2 = 0, s3 = 0, s4 = 0, s5 = 0;
+        for (int n = 1; n < 26; ++n) {
+            double sg = (n % 2) ? -1.0 : 1.0;                          /* (-1)^n */
+            s4 += n * sg * p[n] / (n + 1);                             /* n (-1)^n x^n/(n+1)! */
+            s1 += n * -sg * p[n] / (n + 1);                            /* n (-1)^{n+1} x^n/(n+1)! */
+            s3 += n * -sg * p[n] / ((double)(n + 1) * (n + 2));        /* n (-1)^{n+1} x^n/(n+2)! */
+            s2 += n * sg * n * p[n] / ((double)(n + 1) * (n + 2));     /* n (-1)^n n x^n/(n+2)! */
+            s5 += n * -sg * (n + 1) * p[n] / ((double)(n + 1) * (n + 2)); /* n (-1)^{n+1}(n+1) x^n/(n+2)! */
+        }
+        dq[0] = -dt / tau * s1;
+        dq[1] = -dt * dt / tau * s2;
+        dq[2] = -dt * dt / tau * s3;
+        dq[3] = -dt / tau * s4;
+        dq[4] = -dt * dt / tau * s5;
+    } else {
+        double e = exp(-x), E1 = -expm1(-x);
+        dq[0] = -E1 + x * e;
+        dq[1] = -dt * (1.0 + e) - dt * x * e + 4.0 * tau * E1 - 2.0 * tau * x * e;
+        dq[2] = -dt + 2.0 * tau * E1 - tau * x * e;
+        dq[3] = E1 - x * e;
+        dq[4] = dt * e + dt * x * e - 2.0 * tau * E1 + tau * x * e;
+    }
+}
+
+/* Reverse of oracle_micro_slope: given abar = dL/da, accumulate dL/d(dw)
+ * into dwb and dL/d(U, V, lam) into pb[0..2]. */
+void oracle_micro_slope_adj(const double dw[4], double U, double V, double lam, const double abar[4],
+                            double dwb[4], double pb[3])
+{
+    double Kp2 = KINT + 2.0;
+    double cc = U * U + V * V + Kp2 / (2.0 * lam);
+    double R4 = 2.0 * dw[3] - cc * dw[0];
+    double R3 = dw[2] - V * dw[0];
+    double R2 = dw[1] - U * dw[0];
+    double X = R4 - 2.0 * U * R2 - 2.0 * V * R3;
+    double a3 = 4.0 * lam * lam / Kp2 * X;
+    double a2 = 2.0 * lam * R3 - V * a3;
+    double a1 = 2.0 * lam * R2 - U * a3;
+    double ab[4] = {abar[0], abar[1], abar[2], abar[3]};
+    double Ub = 0, Vb = 0, lb = 0, ccb = 0, R2b = 0, R3b = 0, R4b = 0;
+    /* a0 = dw0 - U a1 - V a2 - a3 cc / 2 */
+    dwb[0] += ab[0];
+    Ub -= ab[0] * a1; ab[1] -= ab[0] * U;
+    Vb -= ab[0] * a2; ab[2] -= ab[0] * V;
+    ab[3] -= ab[0] * 0.5 * cc; ccb -= ab[0] * 0.5 * a3;
+    /* a1 = 2 lam R2 - U a3 */
+    lb += ab[1] * 2.0 * R2; R2b += ab[1] * 2.0 * lam; Ub -= ab[1] * a3; ab[3] -= ab[1] * U;
+    /* a2 = 2 lam R3 - V a3 */
+    lb += ab[2] * 2.0 * R3; R3b += ab[2] * 2.0 * lam; Vb -= ab[2] * a3; ab[3] -= ab[2] * V;
+    /* a3 = 4 lam^2 X / Kp2 */
+    double Xb = ab[3] * 4.0 * lam * lam / Kp2;
+    lb += ab[3] * 8.0 * lam / Kp2 * X;
+    R4b += Xb; Ub -= Xb * 2.0 * R2; R2b -= Xb * 2.0 * U; Vb -= Xb * 2.0 * R3; R3b -= Xb * 2.0 * V;
+    /* R2, R3, R4 */
+    dwb[1] += R2b; Ub -= R2b * dw[0]; dwb[0] -= R2b * U;
+    dwb[2] += R3b; Vb -= R3b * dw[0]; dwb[0] -= R3b * V;
+    dwb[3] += 2.0 * R4b; ccb -= R4b * dw[0]; dwb[0] -= R4b * cc;
+    /* cc */
+    Ub += 2.0 * U * ccb; Vb += 2.0 * V * ccb; lb -= ccb * Kp2 / (2.0 * lam * lam);
+    pb[0] += Ub; pb[1] += Vb; pb[2] += lb;
+}
+
+/* Reverse of slope_moments: (mGb, mHb) -> a, gM, hM and xi4q adjoints. */
+static void slope_moments_adj(const double a[4], double u, double v, double gM, double hM, double xi4q,
+                              double mGb, double mHb, double ab[4], double *gMb, double *hMb, double *xib)
+{
+    double b = a[0] + a[1] * u + a[2] * v + 0.5 * a[3] * (u * u + v * v);
+    double bb = mGb * gM + mHb * hM;
+    ab[0] += bb; ab[1] += bb * u; ab[2] += bb * v;
+    ab[3] += bb * 0.5 * (u * u + v * v) + mGb * hM + mHb * xi4q * gM;
+    *gMb += mGb * b + mHb * a[3] * xi4q;
+    *hMb += mGb * a[3] + mHb * b;
+    *xib += mHb * a[3] * gM;
+}
+
+/* Reverse of prim(): (rho, U, V, lam) adjoints -> W adjoint (accumulated). */
+static void prim_adj(const double *W, double rb, double Ub, double Vb, double lb, double *Wb)
+{
+    double rho, U, V, lam;
+    prim(W, &rho, &U, &V, &lam);
+    double eint = W[3] - 0.5 * (W[1] * W[1] + W[2] * W[2]) / W[0];
+    double eb = -lb * lam / eint;
+    Wb[0] += rb + lb * lam / rho + eb * 0.5 * (U * U + V * V) - (Ub * U + Vb * V) / rho;
+    Wb[1] += Ub / rho - eb * U;
+    Wb[2] += Vb / rho - eb * V;
+    Wb[3] += eb;
+}
+
+/* Reverse of a Maxwellian pair gM = rho (lam/pi) e^{-lam c^2}, hM = gM K/(4 lam)
+ * at peculiar velocity (cx, cy): accumulates rho, U, V, lam adjoints. */
+static void maxw_adj(double gM, double hM, double rho, double lam, double cx, double cy,
+                     double gMb, double hMb, double *rb, double *Ub, double *Vb, double *lb)
+{
+    double c2 = cx * cx + cy * cy;
+    gMb += hMb * KINT / (4.0 * lam);
+    *lb -= hMb * hM / lam;
+    *rb += gMb * gM / rho;
+    *lb += gMb * gM * (1.0 / lam - c2);
+    double c2b = -gMb * gM * lam;
+    *Ub -= 2.0 * cx * c2b;
+    *Vb -= 2.0 * cy * c2b;
+}
+
+#define OUTA(out, comp, c, k) ((out)[((size_t)(comp) * nc + (c)) * nv + (k)])
+
+/* Adjoint of interior_face: nuG, nuH = dL/d(Phi_k / dt) per velocity; the
+ * adjoint with respect to f of the four cells of the stencil is added to out. */
+static void interior_face_adj(oracle_solver *s, int axis, int cLL, int cL, int cR, int cRR,
+                              double dLLL, double dLR, double dRRR, double hL, double hR,
+                              double wL, double wR, const double *nuG, const double *nuH, double *out)
+{
+    int nv = s->nv;
+    size_t nc = s->lev[0].nc;
+    const double *u = s->u, *v = s->v, *w = s->w;
+    double *f0 = dalloc(2 * (size_t)nv), *sg = dalloc(2 * (size_t)nv);
+    double *f0b = dalloc(2 * (size_t)nv), *sgb = dalloc(2 * (size_t)nv);
+    /* ---- forward, as interior_face ---- */
+    for (int k = 0; k < nv; ++k) {
+        double un = axis == 0 ? u[k] : v[k];
+        for (int cp = 0; cp < 2; ++cp) {
+            double fL = FIX(s, cp, cL, k), fR = FIX(s, cp, cR, k);
+            double sL = 0.0, sR = 0.0;
+            if (cLL >= 0) sL = oracle_vanleer((fL - FIX(s, cp, cLL, k)) / dLLL, (fR - fL) / dLR);
+            if (cRR >= 0) sR = oracle_vanleer((fR - fL) / dLR, (FIX(s, cp, cRR, k) - fR) / dRRR);
+            double faceL = fL + sL * hL, faceR = fR - sR * hR;
+            if (un > 0) { f0[cp * nv + k] = faceL; sg[cp * nv + k] = sL; }
+            else if (un < 0) { f0[cp * nv + k] = faceR; sg[cp * nv + k] = sR; }
+            else { f0[cp * nv + k] = 0.5 * (faceL + faceR); sg[cp * nv + k] = 0.5 * (sL + sR); }
+        }
+    }
+    double W0[4] = {0, 0, 0, 0};
+    for (int k = 0; k < nv; ++k) {
+        double g = f0[k], h = f0[nv + k];
+        W0[0] += w[k] * g;
+        W0[1] += w[k] * u[k] * g;
+        W0[2] += w[k] * v[k] * g;
+        W0[3] += w[k] * (0.5 * (u[k] * u[k] + v[k] * v[k]) * g + h);
+    }
+    double rho0, U0, V0, lam0;
+    prim(W0, &rho0, &U0, &V0, &lam0);
+    double tau0 = tau_of(s, rho0, lam0);
+    double dt = face_dt(s, axis, wL, wR);
+    const double *WL = s->W + 4 * cL, *WR = s->W + 4 * cR;
+    double dwl[4], dwr[4], aL[4], aR[4];
+    for (int m = 0; m < 4; ++m) {
+        dwl[m] = (W0[m] - WL[m]) / hL / rho0;
+        dwr[m] = (WR[m] - W0[m]) / hR / rho0;
+    }
+    oracle_micro_slope(dwl, U0, V0, lam0, aL);
+    oracle_micro_slope(dwr, U0, V0, lam0, aR);
+    double xi4q = KINT * (KINT + 2.0) / (16.0 * lam0 * lam0);
+    double q0[2] = {0, 0}, Mt[4] = {0, 0, 0, 0};
+    for (int k = 0; k < nv; ++k) {
+        double cx = u[k] - U0, cy = v[k] - V0, c2 = cx * cx + cy * cy;
+        double g = f0[k], h = f0[nv + k];
+        q0[0] += w[k] * cx * (0.5 * c2 * g + h);
+        q0[1] += w[k] * cy * (0.5 * c2 * g + h);
+        double un = axis == 0 ? u[k] : v[k];
+        if (un == 0.0) continue;
+        double gM = maxw(rho0, U0, V0, lam0, u[k], v[k]), hM = gM * KINT / (4.0 * lam0);
+        double mG, mH;
+        slope_moments(un > 0 ? aL : aR, u[k], v[k], gM, hM, lam0, &mG, &mH);
+        Mt[0] += w[k] * un * mG;
+        Mt[1] += w[k] * un * u[k] * mG;
+        Mt[2] += w[k] * un * v[k] * mG;
+        Mt[3] += w[k] * un * (0.5 * (u[k] * u[k] + v[k] * v[k]) * mG + mH);
+    }
+    double dwt[4], A[4];
+    for (int m = 0; m < 4; ++m) dwt[m] = -Mt[m] / rho0;
+    oracle_micro_slope(dwt, U0, V0, lam0, A);
+    double qc[5], dqc[5];
+    oracle_time_coeffs(dt, tau0, qc);
+    oracle_time_coeffs_dtau(dt, tau0, dqc);
+    double shk = (1.0 - s->pr) * 4.0 * lam0 * lam0 / (5.0 * rho0);
+
+    /* ---- reverse of the flux assembly (last loop of interior_face) ---- */
+    double qcb[5] = {0, 0, 0, 0, 0}, aLb[4] = {0, 0, 0, 0}, aRb[4] = {0, 0, 0, 0}, Ab[4] = {0, 0, 0, 0};
+    double rb = 0, Ub = 0, Vb = 0, lb = 0, shkb = 0, xib = 0, q0b[2] = {0, 0};
+    for (int k = 0; k < nv; ++k) {
+        double un = axis == 0 ? u[k] : v[k];
+        if (un == 0.0) continue; /* Phi_k = 0 identically */
+        double cx = u[k] - U0, cy = v[k] - V0, c2 = cx * cx + cy * cy;
+        double gM = maxw(rho0, U0, V0, lam0, u[k], v[k]), hM = gM * KINT / (4.0 * lam0);
+        double Fq = shk * (cx * q0[0] + cy * q0[1]);
+        double eG = 2.0 * lam0 * c2 - 4.0, eH = 2.0 * lam0 * c2 - 2.0;
+        double gP = gM * (1.0 + Fq * eG), hP = hM * (1.0 + Fq * eH);
+        const double *as = un > 0 ? aL : aR;
+        double *asb = un > 0 ? aLb : aRb;
+        double mGa, mHa, mGA, mHA;
+        slope_moments(as, u[k], v[k], gM, hM, lam0, &mGa, &mHa);
+        slope_moments(A, u[k], v[k], gM, hM, lam0, &mGA, &mHA);
+        double PbG = nuG[k] / dt, PbH = nuH[k] / dt;
+        qcb[0] += un * (PbG * gP + PbH * hP);
+        qcb[1] += un * un * (PbG * mGa + PbH * mHa);
+        qcb[2] += un * (PbG * mGA + PbH * mHA);
+        qcb[3] += un * (PbG * f0[k] + PbH * f0[nv + k]);
+        qcb[4] += un * un * (PbG * sg[k] + PbH * sg[nv + k]);
+        f0b[k] += un * qc[3] * PbG;
+        f0b[nv + k] += un * qc[3] * PbH;
+        sgb[k] += un * un * qc[4] * PbG;
+        sgb[nv + k] += un * un * qc[4] * PbH;
+        double gPb = un * qc[0] * PbG, hPb = un * qc[0] * PbH;
+        double gMb = 0, hMb = 0;
+        slope_moments_adj(as, u[k], v[k], gM, hM, xi4q, un * un * qc[1] * PbG, un * un * qc[1] * PbH,
+                          asb, &gMb, &hMb, &xib);
+        slope_moments_adj(A, u[k], v[k], gM, hM, xi4q, un * qc[2] * PbG, un * qc[2] * PbH, Ab, &gMb, &hMb, &xib);
+        /* Shakhov factors */
+        gMb += gPb * (1.0 + Fq * eG);
+        hMb += hPb * (1.0 + Fq * eH);
+        double Fqb = gPb * gM * eG + hPb * hM * eH;
+        double eb = (gPb * gM + hPb * hM) * Fq;          /* both e's carry 2 lam c^2 */
+        lb += eb * 2.0 * c2;
+        double c2b = eb * 2.0 * lam0;
+        shkb += Fqb * (cx * q0[0] + cy * q0[1]);
+        q0b[0] += Fqb * shk * cx;
+        q0b[1] += Fqb * shk * cy;
+        double cxb = Fqb * shk * q0[0] + 2.0 * cx * c2b, cyb = Fqb * shk * q0[1] + 2.0 * cy * c2b;
+        Ub -= cxb; Vb -= cyb;
+        maxw_adj(gM, hM, rho0, lam0, cx, cy, gMb, hMb, &rb, &Ub, &Vb, &lb);
+    }
+    /* shk = (1-Pr) 4 lam^2 / (5 rho) */
+    lb += shkb * 2.0 * shk / lam0;
+    rb -= shkb * shk / rho0;
+    /* A = slope(dwt), dwt = -Mt/rho0 */
+    double dwtb[4] = {0, 0, 0, 0}, pb[3] = {0, 0, 0};
+    oracle_micro_slope_adj(dwt, U0, V0, lam0, Ab, dwtb, pb);
+    Ub += pb[0]; Vb += pb[1]; lb += pb[2];
+    double Mtb[4];
+    for (int m = 0; m < 4; ++m) {
+        Mtb[m] = -dwtb[m] / rho0;
+        rb += dwtb[m] * Mt[m] / (rho0 * rho0);
+    }
+    /* time integrals through tau0 = tau(rho0, lam0) = 2 mu_ref lam^(1-omega)/rho */
+    double taub = 0.0;
+    for (int m = 0; m < 5; ++m) taub += qcb[m] * dqc[m];
+    rb -= taub * tau0 / rho0;
+    lb += taub * tau0 * (1.0 - s->omega) / lam0;
+    /* ---- reverse of the heat-flux and compatibility loop ---- */
+    for (int k = 0; k < nv; ++k) {
+        double cx = u[k] - U0, cy = v[k] - V0, c2 = cx * cx + cy * cy;
+        double g = f0[k], h = f0[nv + k], E = 0.5 * c2 * g + h;
+        double un = axis == 0 ? u[k] : v[k];
+        if (un != 0.0) {
+            double gM = maxw(rho0, U0, V0, lam0, u[k], v[k]), hM = gM * KINT / (4.0 * lam0);
+            double mGb = w[k] * un * (Mtb[0] + Mtb[1] * u[k] + Mtb[2] * v[k] + Mtb[3] * 0.5 * (u[k] * u[k] + v[k] * v[k]));
+            double mHb = w[k] * un * Mtb[3];
+            double gMb = 0, hMb = 0;
+            slope_moments_adj(un > 0 ? aL : aR, u[k], v[k], gM, hM, xi4q, mGb, mHb, un > 0 ? aLb : aRb,
+                              &gMb, &hMb, &xib);
+            maxw_adj(gM, hM, rho0, lam0, cx, cy, gMb, hMb, &rb, &Ub, &Vb, &lb);
+        }
+        double qdc = q0b[0] * cx + q0b[1] * cy;
+        f0b[k] += w[k] * qdc * 0.5 * c2;
+        f0b[nv + k] += w[k] * qdc;
+        double cxb = w[k] * (q0b[0] * (E + cx * cx * g) + q0b[1] * cy * cx * g);
+        double cyb = w[k] * (q0b[1] * (E + cy * cy * g) + q0b[0] * cx * cy * g);
+        Ub -= cxb; Vb -= cyb;
+    }
+    /* xi4q = K(K+2)/(16 lam^2) */
+    lb += xib * (-2.0 * xi4q / lam0);
+    /* equilibrium slopes */
+    double dwlb[4] = {0, 0, 0, 0}, dwrb[4] = {0, 0, 0, 0};
+    pb[0] = Ub; pb[1] = Vb; pb[2] = lb;
+    oracle_micro_slope_adj(dwl, U0, V0, lam0, aLb, dwlb, pb);
+    oracle_micro_slope_adj(dwr, U0, V0, lam0, aRb, dwrb, pb);
+    Ub = pb[0]; Vb = pb[1]; lb = pb[2];
+    double W0b[4] = {0, 0, 0, 0}, WLb[4], WRb[4];
+    for (int m = 0; m < 4; ++m) {
+        W0b[m] += dwlb[m] / (hL * rho0) - dwrb[m] / (hR * rho0);
+        WLb[m] = -dwlb[m] / (hL * rho0);
+        WRb[m] = dwrb[m] / (hR * rho0);
+        rb -= (dwlb[m] * dwl[m] + dwrb[m] * dwr[m]) / rho0;
+    }
+    prim_adj(W0, rb, Ub, Vb, lb, W0b);
+    /* ---- reverse of W0 and of the reconstruction ---- */
+    for (int k = 0; k < nv; ++k) {
+        double un = axis == 0 ? u[k] : v[k];
+        double e2 = 0.5 * (u[k] * u[k] + v[k] * v[k]);
+        for (int cp = 0; cp < 2; ++cp) {
+            double psiW0 = cp == 0 ? W0b[0] + u[k] * W0b[1] + v[k] * W0b[2] + e2 * W0b[3] : W0b[3];
+            double psiL = cp == 0 ? WLb[0] + u[k] * WLb[1] + v[k] * WLb[2] + e2 * WLb[3] : WLb[3];
+            double psiR = cp == 0 ? WRb[0] + u[k] * WRb[1] + v[k] * WRb[2] + e2 * WRb[3] : WRb[3];
+            double fb = f0b[cp * nv + k] + w[k] * psiW0, sb = sgb[cp * nv + k];
+            double fLb = w[k] * psiL, fRb = w[k] * psiR, sLb = 0.0, sRb = 0.0;
+            if (un > 0) { fLb += fb; sLb = fb * hL + sb; }
+            else if (un < 0) { fRb += fb; sRb = -fb * hR + sb; }
+            else { fLb += 0.5 * fb; fRb += 0.5 * fb; sLb = 0.5 * fb * hL + 0.5 * sb; sRb = -0.5 * fb * hR + 0.5 * sb; }
+            double fL = FIX(s, cp, cL, k), fR = FIX(s, cp, cR, k);
+            if (cLL >= 0) {
+                double s1 = (fL - FIX(s, cp, cLL, k)) / dLLL, s2 = (fR - fL) / dLR;
+                if (s1 * s2 > 0.0) {
+                    double d = (s1 + s2) * (s1 + s2);
+                    double s1b = sLb * 2.0 * s2 * s2 / d, s2b = sLb * 2.0 * s1 * s1 / d;
+                    fLb += s1b / dLLL - s2b / dLR;
+                    OUTA(out, cp, cLL, k) -= s1b / dLLL;
+                    fRb += s2b / dLR;
+                }
+            }
+            if (cRR >= 0) {
+                double s2 = (fR - fL) / dLR, s3 = (FIX(s, cp, cRR, k) - fR) / dRRR;
+                if (s2 * s3 > 0.0) {
+                    double d = (s2 + s3) * (s2 + s3);
+                    double s2b = sRb * 2.0 * s3 * s3 / d, s3b = sRb * 2.0 * s2 * s2 / d;
+                    fRb += s2b / dLR - s3b / dRRR;
+                    fLb -= s2b / dLR;
+                    OUTA(out, cp, cRR, k) += s3b / dRRR;
+                }
+            }
+            OUTA(out, cp, cL, k) += fLb;
+            OUTA(out, cp, cR, k) += fRb;
+        }
+    }
+    free(f0); free(sg); free(f0b); free(sgb);
+}
+
+/* Adjoint of boundary_face (free transport of the boundary face distribution). */
+static void boundary_face_adj(const oracle_solver *s, int bcid, int axis, int outsign, int c,
+                              const double *nuG, const double *nuH, double *out)
+{
+    int nv = s->nv;
+    size_t nc = s->lev[0].nc;
+    const obc_t *b = &s->bc[bcid];
+    double lamw = 1.0 / b->t, rhowb = 0.0, den = 0.0;
+    for (int k = 0; k < nv; ++k) {
+        double un = axis == 0 ? s->u[k] : s->v[k], uo = outsign * un;
+        if (uo >= 0 || b->type == ORC_BC_OUTFLOW) {
+            OUTA(out, 0, c, k) += un * nuG[k];
+            OUTA(out, 1, c, k) += un * nuH[k];
+        } else if (b->type == ORC_BC_WALL) {
+            double C = s->Cw[(size_t)bcid * nv + k];
+            rhowb += un * (nuG[k] * C + nuH[k] * C * KINT / (4.0 * lamw));
+            den += s->w[k] * uo * C;
+        } else if (b->type == ORC_BC_SYMMETRY) {
+            int km = axis == 0 ? s->mxk[k] : s->myk[k];
+            OUTA(out, 0, c, km) += un * nuG[k];
+            OUTA(out, 1, c, km) += un * nuH[k];
+        }
+    }
+    if (b->type == ORC_BC_WALL)
+        for (int k = 0; k < nv; ++k) {
+            double uo = outsign * (axis == 0 ? s->u[k] : s->v[k]);
+            if (uo > 0) OUTA(out, 0, c, k) += -s->w[k] * uo * rhowb / den;
+        }
+}
+
+/* Adjoint of the collision term (g+(W, q) - f)/tau(W) of one cell, with W,
+ * q the moments of f about its own velocity; mu = dL/dN of that cell. */
+static void collision_adj(const oracle_solver *s, int c, const double *mu, double *out)
+{
+    int nv = s->nv;
+    size_t nc = s->lev[0].nc;
+    const double *W = s->W + 4 * c, *q = s->q + 2 * c;
+    double rho, U, V, lam;
+    prim(W, &rho, &U, &V, &lam);
+    double itau = 1.0 / tau_of(s, rho, lam);
+    double S = (1.0 - s->pr) * 4.0 / 5.0 * lam * lam / rho;
+    double rb = 0, Ub = 0, Vb = 0, lb = 0, Sb = 0, itb = 0, qb[2] = {0, 0};
+    for (int k = 0; k < nv; ++k) {
+        double cx = s->u[k] - U, cy = s->v[k] - V, c2 = cx * cx + cy * cy;
+        double gM = maxw(rho, U, V, lam, s->u[k], s->v[k]), hM = gM * KINT / (4.0 * lam);
+        double Fq = S * (cx * q[0] + cy * q[1]);
+        double eG = 2.0 * lam * c2 - 4.0, eH = 2.0 * lam * c2 - 2.0;
+        double gP = gM * (1.0 + Fq * eG), hP = hM * (1.0 + Fq * eH);
+        double mG = OUTA(mu, 0, c, k), mH = OUTA(mu, 1, c, k);
+        OUTA(out, 0, c, k) -= mG * itau;
+        OUTA(out, 1, c, k) -= mH * itau;
+        itb += mG * (gP - FIX(s, 0, c, k)) + mH * (hP - FIX(s, 1, c, k));
+        double gPb = mG * itau, hPb = mH * itau;
+        double gMb = gPb * (1.0 + Fq * eG), hMb = hPb * (1.0 + Fq * eH);
+        double Fqb = gPb * gM * eG + hPb * hM * eH;
+        double eb = (gPb * gM + hPb * hM) * Fq;
+        lb += eb * 2.0 * c2;
+        double c2b = eb * 2.0 * lam;
+        Sb += Fqb * (cx * q[0] + cy * q[1]);
+        qb[0] += Fqb * S * cx;
+        qb[1] += Fqb * S * cy;
+        double cxb = Fqb * S * q[0] + 2.0 * cx * c2b, cyb = Fqb * S * q[1] + 2.0 * cy * c2b;
+        Ub -= cxb; Vb -= cyb;
+        maxw_adj(gM, hM, rho, lam, cx, cy, gMb, hMb, &rb, &Ub, &Vb, &lb);
+    }
+    lb += Sb * 2.0 * S / lam;
+    rb -= Sb * S / rho;
+    /* itau = rho lam^(omega-1) / (2 mu_ref) */
+    rb += itb * itau / rho;
+    lb += itb * itau * (s->omega - 1.0) / lam;
+    /* q = sum_k w c (c^2 G/2 + H) about U(f) */
+    for (int k = 0; k < nv; ++k) {
+        double cx = s->u[k] - U, cy = s->v[k] - V, c2 = cx * cx + cy * cy;
+        double g = FIX(s, 0, c, k), E = 0.5 * c2 * g + FIX(s, 1, c, k);
+        double qdc = qb[0] * cx + qb[1] * cy;
+        OUTA(out, 0, c, k) += s->w[k] * qdc * 0.5 * c2;
+        OUTA(out, 1, c, k) += s->w[k] * qdc;
+        Ub -= s->w[k] * (qb[0] * (E + cx * cx * g) + qb[1] * cy * cx * g);
+        Vb -= s->w[k] * (qb[1] * (E + cy * cy * g) + qb[0] * cx * cy * g);
+    }
+    double Wb[4] = {0, 0, 0, 0};
+    prim_adj(W, rb, Ub, Vb, lb, Wb);
+    for (int k = 0; k < nv; ++k) {
+        double e2 = 0.5 * (s->u[k] * s->u[k] + s->v[k] * s->v[k]);
+        OUTA(out, 0, c, k) += s->w[k] * (Wb[0] + s->u[k] * Wb[1] + s->v[k] * Wb[2] + e2 * Wb[3]);
+        OUTA(out, 1, c, k) += s->w[k] * Wb[3];
+    }
+}
+
+/* N(f) of the steady equations at the current f (W, q renewed from f). */
+int oracle_steady_residual(oracle_solver *s, double *N)
+{
+    olev_t *L0 = &s->lev[0];
+    int nx = L0->nx, ny = L0->ny, nv = s->nv;
+    size_t nc = L0->nc;
+    moments(s);
+    flux_stage(s);
+    double shk0 = (1.0 - s->pr) * 4.0 / 5.0;
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            int c = j * nx + i;
+            double rho, U, V, lam;
+            prim(s->W + 4 * c, &rho, &U, &V, &lam);
+            double itau = 1.0 / tau_of(s, rho, lam);
+            double Vol = L0->dx[i] * L0->dy[j];
+            double qx = s->q[2 * c], qy = s->q[2 * c + 1];
+            int fW = j * (nx + 1) + i, fE = fW + 1, fS = j * nx + i, fN = (j + 1) * nx + i;
+            for (int k = 0; k < nv; ++k) {
+                double cx = s->u[k] - U, cy = s->v[k] - V, c2 = cx * cx + cy * cy;
+                double gM = maxw(rho, U, V, lam, s->u[k], s->v[k]), hM = gM * KINT / (4.0 * lam);
+                double Fq = shk0 * lam * lam / rho * (cx * qx + cy * qy);
+                double gt[2] = {gM * (1.0 + Fq * (2.0 * lam * c2 - 4.0)), hM * (1.0 + Fq * (2.0 * lam * c2 - 2.0))};
+                for (int cp = 0; cp < 2; ++cp) {
+                    const double *px = s->phx + (size_t)cp * L0->nfx * nv, *py = s->phy + (size_t)cp * L0->nfy * nv;
+                    double div = (L0->dy[j] * (px[(size_t)fE * nv + k] - px[(size_t)fW * nv + k]) +
+                                  L0->dx[i] * (py[(size_t)fN * nv + k] - py[(size_t)fS * nv + k])) / Vol;
+                    OUTA(N, cp, c, k) = (gt[cp] - FIX(s, cp, c, k)) * itau - div;
+                }
+            }
+        }
+    return 0;
+}
+
+/* out = (dN/df)^T mu at the current f. */
+int oracle_adjoint_residual(oracle_solver *s, const double *mu, double *out)
+{
+    olev_t *L0 = &s->lev[0];
+    int nx = L0->nx, ny = L0->ny, nv = s->nv;
+    size_t nc = L0->nc;
+    moments(s);
+    memset(out, 0, 2 * nc * nv * sizeof(double));
+    double *nuG = dalloc(nv), *nuH = dalloc(nv);
+    /* x-faces: N_L gets -Phi/dx_L, N_R gets +Phi/dx_R */
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i <= nx; ++i) {
+            int fi = j * (nx + 1) + i, bcid = L0->fbx[fi];
+            int cL = i > 0 ? j * nx + i - 1 : -1, cR = i < nx ? j * nx + i : -1;
+            for (int k = 0; k < nv; ++k) {
+                nuG[k] = nuH[k] = 0.0;
+                if (cL >= 0) { nuG[k] -= OUTA(mu, 0, cL, k) / L0->dx[i - 1]; nuH[k] -= OUTA(mu, 1, cL, k) / L0->dx[i - 1]; }
+                if (cR >= 0) { nuG[k] += OUTA(mu, 0, cR, k) / L0->dx[i]; nuH[k] += OUTA(mu, 1, cR, k) / L0->dx[i]; }
+            }
+            if (bcid >= 0) {
+                if (i == 0) boundary_face_adj(s, bcid, 0, -1, cR, nuG, nuH, out);
+                else boundary_face_adj(s, bcid, 0, +1, cL, nuG, nuH, out);
+                continue;
+            }
+            int hasLL = (i - 1 > 0) && L0->fbx[fi - 1] < 0;
+            int hasRR = (i + 1 < nx) && L0->fbx[fi + 1] < 0;
+            interior_face_adj(s, 0, hasLL ? cL - 1 : -1, cL, cR, hasRR ? cR + 1 : -1,
+                              hasLL ? L0->xc[i - 1] - L0->xc[i - 2] : 1.0, L0->xc[i] - L0->xc[i - 1],
+                              hasRR ? L0->xc[i + 1] - L0->xc[i] : 1.0,
+                              L0->xn[i] - L0->xc[i - 1], L0->xc[i] - L0->xn[i],
+                              L0->dx[i - 1], L0->dx[i], nuG, nuH, out);
+        }
+    for (int j = 0; j <= ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            int fi = j * nx + i, bcid = L0->fby[fi];
+            int cL = j > 0 ? (j - 1) * nx + i : -1, cR = j < ny ? j * nx + i : -1;
+            for (int k = 0; k < nv; ++k) {
+                nuG[k] = nuH[k] = 0.0;
+                if (cL >= 0) { nuG[k] -= OUTA(mu, 0, cL, k) / L0->dy[j - 1]; nuH[k] -= OUTA(mu, 1, cL, k) / L0->dy[j - 1]; }
+                if (cR >= 0) { nuG[k] += OUTA(mu, 0, cR, k) / L0->dy[j]; nuH[k] += OUTA(mu, 1, cR, k) / L0->dy[j]; }
+            }
+            if (bcid >= 0) {
+                if (j == 0) boundary_face_adj(s, bcid, 1, -1, cR, nuG, nuH, out);
+                else boundary_face_adj(s, bcid, 1, +1, cL, nuG, nuH, out);
+                continue;
+            }
+            int hasLL = (j - 1 > 0) && L0->fby[fi - nx] < 0;
+            int hasRR = (j + 1 < ny) && L0->fby[fi + nx] < 0;
+            interior_face_adj(s, 1, hasLL ? cL - nx : -1, cL, cR, hasRR ? cR + nx : -1,
+                              hasLL ? L0->yc[j - 1] - L0->yc[j - 2] : 1.0, L0->yc[j] - L0->yc[j - 1],
+                              hasRR ? L0->yc[j + 1] - L0->yc[j] : 1.0,
+                              L0->yn[j] - L0->yc[j - 1], L0->yc[j] - L0->yn[j],
+                              L0->dy[j - 1], L0->dy[j], nuG, nuH, out);
+        }
+    for (size_t c = 0; c < nc; ++c) collision_adj(s, (int)c, mu, out);
+    free(nuG); free(nuH);
+    return 0;
+}
+
+/* Wall objective J = sum over the faces of BC bc of S_face * Q_face, with Q
+ * the wall shear (obj 0), heat flux (obj 1) or pressure (obj 2) of
+ * oracle_get_wall.  Optionally returns dJ/df (2 x nc x nv, at fixed theta)
+ * and dJ/dtheta (theta = T, u, v of the BC, at fixed f). */
+int oracle_objective(oracle_solver *s, int obj, int bc, double *J, double *dJdf, double *dJdth)
+{
+    const olev_t *L0 = &s->lev[0];
+    int nx = L0->nx, ny = L0->ny, nv = s->nv;
+    size_t nc = L0->nc;
+    if (bc < 0 || bc >= s->nbc || s->bc[bc].type != ORC_BC_WALL) return fail("objective: BC %d is not a wall", bc);
+    if (obj < 0 || obj > 2) return fail("objective: unknown objective %d", obj);
+    const obc_t *B = &s->bc[bc];
+    double T = B->t, lam = 1.0 / T, Jt = 0.0, th[3] = {0, 0, 0};
+    if (dJdf) memset(dJdf, 0, 2 * nc * nv * sizeof(double));
+    for (int pass = 0; pass < 2; ++pass) {
+        int nfc = pass == 0 ? L0->nfx : L0->nfy;
+        for (int fi = 0; fi < nfc; ++fi) {
+            int b = pass == 0 ? L0->fbx[fi] : L0->fby[fi];
+            if (b != bc) continue;
+            int axis = pass, outsign, c;
+            double S;
+            if (axis == 0) {
+                int i = fi % (nx + 1), j = fi / (nx + 1);
+                outsign = i == 0 ? -1 : 1; c = j * nx + (i == 0 ? 0 : nx - 1); S = L0->dy[j];
+            } else {
+                int i = fi % nx, j = fi / nx;
+                outsign = j == 0 ? -1 : 1; c = (j == 0 ? 0 : ny - 1) * nx + i; S = L0->dx[i];
+            }
+            double Uwt = axis == 0 ? B->v : B->u;
+            /* weights of the face distribution in Q: Q = sum_k w uo (aG fG + aH fH) */
+            double num = 0.0, den = 0.0, dden[3] = {0, 0, 0};
+            for (int k = 0; k < nv; ++k) {
+                double uo = outsign * (axis == 0 ? s->u[k] : s->v[k]);
+                if (uo > 0) num += s->w[k] * uo * FIX(s, 0, c, k);
+                else if (uo < 0) {
+                    double C = s->Cw[(size_t)bc * nv + k];
+                    double du = s->u[k] - B->u, dv = s->v[k] - B->v, cw2 = du * du + dv * dv;
+                    den += s->w[k] * uo * C;
+                    dden[0] += s->w[k] * uo * C * (lam * lam * cw2 - lam);
+                    dden[1] += s->w[k] * uo * C * 2.0 * lam * du;
+                    dden[2] += s->w[k] * uo * C * 2.0 * lam * dv;
+                }
+            }
+            double rhow = -num / den, rhowb = 0.0;
+            double Q = 0.0;
+            for (int k = 0; k < nv; ++k) {
+                double uo = outsign * (axis == 0 ? s->u[k] : s->v[k]);
+                double ut = axis == 0 ? s->v[k] : s->u[k];
+                double du = s->u[k] - B->u, dv = s->v[k] - B->v, cw2 = du * du + dv * dv;
+                double aG, aH, daG[3] = {0, 0, 0};
+                if (obj == 0) { aG = ut - Uwt; aH = 0.0; daG[axis == 0 ? 2 : 1] = -1.0; }
+                else if (obj == 1) { aG = 0.5 * cw2; aH = 1.0; daG[1] = -du; daG[2] = -dv; }
+                else { aG = uo; aH = 0.0; }
+                double wk = s->w[k] * uo;
+                if (uo >= 0) {
+                    double fG = FIX(s, 0, c, k), fH = FIX(s, 1, c, k);
+                    Q += wk * (aG * fG + aH * fH);
+                    for (int p = 0; p < 3; ++p) th[p] += S * wk * daG[p] * fG;
+                    if (dJdf) {
+                        OUTA(dJdf, 0, c, k) += S * wk * aG;
+                        OUTA(dJdf, 1, c, k) += S * wk * aH;
+                    }
+                } else {
+                    double C = s->Cw[(size_t)bc * nv + k];
+                    double dC[3] = {C * (lam * lam * cw2 - lam), C * 2.0 * lam * du, C * 2.0 * lam * dv};
+                    double hf = KINT * T / 4.0;                 /* H/G ratio of the wall Maxwellian */
+                    double a = aG + aH * hf;
+                    Q += wk * rhow * C * a;
+                    rhowb += S * wk * C * a;
+                    for (int p = 0; p < 3; ++p) {
+                        double drho = -rhow / den * dden[p];
+                        double da = daG[p] + (p == 0 ? aH * KINT / 4.0 : 0.0);
+                        th[p] += S * wk * (drho * C * a + rhow * dC[p] * a + rhow * C * da);
+                    }
+                }
+            }
+            Jt += S * Q;
+            if (dJdf)
+                for (int k = 0; k < nv; ++k) {
+                    double uo = outsign * (axis == 0 ? s->u[k] : s->v[k]);
+                    if (uo > 0) OUTA(dJdf, 0, c, k) += -s->w[k] * uo * rhowb / den;
+                }
+        }
+    }
+    *J = Jt;
+    if (dJdth) for (int p = 0; p < 3; ++p) dJdth[p] = th[p];
+    return 0;
+}
+
+/* dN/dtheta at fixed f for theta = T (param 0), u (1) or v (2) of wall BC bc:
+ * only the incoming velocities of the wall faces of that BC depend on it. */
+int oracle_residual_dtheta(oracle_solver *s, int bc, int param, double *dN)
+{
+    const olev_t *L0 = &s->lev[0];
+    int nx = L0->nx, ny = L0->ny, nv = s->nv;
+    size_t nc = L0->nc;
+    if (bc < 0 || bc >= s->nbc || s->bc[bc].type != ORC_BC_WALL) return fail("dtheta: BC %d is not a wall", bc);
+    if (param < 0 || param > 2) return fail("dtheta: unknown parameter %d", param);
+    const obc_t *B = &s->bc[bc];
+    double T = B->t, lam = 1.0 / T;
+    memset(dN, 0, 2 * nc * nv * sizeof(double));
+    for (int pass = 0; pass < 2; ++pass) {
+        int nfc = pass == 0 ? L0->nfx : L0->nfy;
+        for (int fi = 0; fi < nfc; ++fi) {
+            int b = pass == 0 ? L0->fbx[fi] : L0->fby[fi];
+            if (b != bc) continue;
+            int axis = pass, outsign, c;
+            double h;
+            if (axis == 0) {
+                int i = fi % (nx + 1), j = fi / (nx + 1);
+                outsign = i == 0 ? -1 : 1; c = j * nx + (i == 0 ? 0 : nx - 1); h = L0->dx[i == 0 ? 0 : nx - 1];
+            } else {
+                int i = fi % nx, j = fi / nx;
+                outsign = j == 0 ? -1 : 1; c = (j == 0 ? 0 : ny - 1) * nx + i; h = L0->dy[j == 0 ? 0 : ny - 1];
+            }
+            /* N_c += outsign * (-1/h) * Phi_face: the face is the cell's upper face when outsign = +1 */
+            double coef = -outsign / h;
+            double num = 0.0, den = 0.0, dden = 0.0;
+            for (int k = 0; k < nv; ++k) {
+                double uo = outsign * (axis == 0 ? s->u[k] : s->v[k]);
+                if (uo > 0) num += s->w[k] * uo * FIX(s, 0, c, k);
+                else if (uo < 0) {
+                    double C = s->Cw[(size_t)bc * nv + k];
+                    double du = s->u[k] - B->u, dv = s->v[k] - B->v;
+                    double dC = param == 0 ? C * (lam * lam * (du * du + dv * dv) - lam)
+                                           : C * 2.0 * lam * (param == 1 ? du : dv);
+                    den += s->w[k] * uo * C;
+                    dden += s->w[k] * uo * dC;
+                }
+            }
+            double rhow = -num / den, drho = -rhow / den * dden;
+            for (int k = 0; k < nv; ++k) {
+                double un = axis == 0 ? s->u[k] : s->v[k], uo = outsign * un;
+                if (!(uo < 0)) continue;
+                double C = s->Cw[(size_t)bc * nv + k];
+                double du = s->u[k] - B->u, dv = s->v[k] - B->v;
+                double dC = param == 0 ? C * (lam * lam * (du * du + dv * dv) - lam)
+                                       : C * 2.0 * lam * (param == 1 ? du : dv);
+                double dG = drho * C + rhow * dC;
+                double dH = dG * KINT * T / 4.0 + (param == 0 ? rhow * C * KINT / 4.0 : 0.0);
+                OUTA(dN, 0, c, k) += coef * un * dG;
+                OUTA(dN, 1, c, k) += coef * un * dH;
+            }
+        }
+    }
     return 0;
 }

@@ -95,6 +95,20 @@ int oracle_stage_prolong(oracle_solver *s, int lev, int ncomp, const double *coa
 int oracle_level_size(const oracle_solver *s, int lev, int *nx, int *ny);
 int oracle_nv(const oracle_solver *s);
 
+/* ---- steady equations and their adjoint (differentiation form) ----
+ * N(f; theta) = (g+(W(f), q(f)) - f)/tau(W(f)) - (1/V) sum S Phi(f; theta)/dt_p,
+ * the discrete steady equations the outer iteration converges to.  theta =
+ * (T, u, v) of one wall BC.  Objectives (wall bc, face order of
+ * oracle_get_wall): obj 0 = sum_faces S * shear, 1 = S * heat flux,
+ * 2 = S * pressure. */
+int oracle_steady_residual(oracle_solver *s, double *N);
+int oracle_adjoint_residual(oracle_solver *s, const double *mu, double *out);  /* (dN/df)^T mu */
+int oracle_objective(oracle_solver *s, int obj, int bc, double *J, double *dJdf, double *dJdtheta);
+int oracle_residual_dtheta(oracle_solver *s, int bc, int param, double *dN);
+void oracle_time_coeffs_dtau(double dt, double tau, double dq[5]);
+void oracle_micro_slope_adj(const double dw[4], double U, double V, double lam, const double abar[4],
+                            double dwbar[4], double pbar[3]);
+
 #ifdef __cplusplus
 }
 #endif
