@@ -37,13 +37,22 @@ LEVELS = 3
 METRIC = "cell-velocity updates/s (MIUGKS outer iterations)"
 UNIT = "cell*velocity/s"
 WORKLOAD = "cavity64x64_v32x32_kn1_lid0.16_3level_Vcycle"
-# algorithmic work of the dominant kernel ("Roofline"): FP64
-# flops of the interface-flux kernel per (face, velocity), and the measured
-# FP64 FMA throughput of a GB300 (FMA-chain kernel, no MEASURED_PEAKS.json entry)
+# algorithmic work of the interface-flux kernel: flops per (face, velocity)
 FLUX_FLOPS_PER_FACE_VELOCITY = 175.0
-FP64_PEAK_TFLOPS = 1.20
-FP32_PEAK_TFLOPS = 70.0
-HBM_PEAK_GBS = 6500.0
+# ALU peaks of a GB300 from its unit counts and clock: 152 SMs x 128 FP32
+# lanes x 2 flops (FMA) x 2.07 GHz; FP64 at its nominal 1.25 TFLOP/s
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP64_PEAK_TFLOPS = 1.25
+
+
+def hbm_peak():
+    """Measured copy bandwidth of the GB300s (MEASURED_PEAKS.json),
+    else the fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except Exception:
+        return 6800.0, "fallback 6.8 TB/s"
 
 
 def case():
@@ -227,15 +236,15 @@ def flux_roofline(m, precision):
     flops = FLUX_FLOPS_PER_FACE_VELOCITY * fv / t / 1e12
     bytes_ = (2 * NX * NY * NVEL * NVEL + 2 * fv) * size / t / 1e9
     fpeak = FP32_PEAK_TFLOPS if precision == "mixed" else FP64_PEAK_TFLOPS
-    if flops / fpeak >= bytes_ / HBM_PEAK_GBS:
+    hpeak, hsrc = hbm_peak()
+    if flops / fpeak >= bytes_ / hpeak:
         return {"bound": "alu", "kernel": "k_face_flux", "achieved": flops, "peak": fpeak, "unit": "TFLOP/s",
                 "frac": flops / fpeak, "traffic": None,
-                "peak_source": "measured %s FMA chain on GB300 (no MEASURED_PEAKS.json)" %
-                               ("FP32" if precision == "mixed" else "FP64"),
-                "hbm_frac": bytes_ / HBM_PEAK_GBS}
-    return {"bound": "hbm", "kernel": "k_face_flux", "achieved": bytes_, "peak": HBM_PEAK_GBS, "unit": "GB/s",
-            "frac": bytes_ / HBM_PEAK_GBS, "traffic": None,
-            "peak_source": "measured copy kernel on GB300 (no MEASURED_PEAKS.json)", "alu_frac": flops / fpeak}
+                "peak_source": "%s peak from unit counts and clock (152 SMs, 2.07 GHz)" %
+                               ("FP32" if precision == "mixed" else "FP64 nominal"),
+                "hbm_frac": bytes_ / hpeak, "hbm_peak_source": hsrc}
+    return {"bound": "hbm", "kernel": "k_face_flux", "achieved": bytes_, "peak": hpeak, "unit": "GB/s",
+            "frac": bytes_ / hpeak, "traffic": None, "peak_source": hsrc, "alu_frac": flops / fpeak}
 
 
 def main():

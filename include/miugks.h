@@ -159,6 +159,40 @@ miugks_status miugks_stage_resid_macro(miugks_solver *s, int lev, const double *
 miugks_status miugks_stage_restrict(miugks_solver *s, int lev, int m, const double *fine, double *coarse);
 miugks_status miugks_stage_prolong(miugks_solver *s, int lev, int m, const double *coarse, double *fine);
 
+/* ---- Differentiation form: adjoint of the steady equations ----
+ * At a converged state the outer iteration solves the discrete steady
+ * equations N(f; theta) = 0 of Eq. microResidualDef (Sec. 2.1) with the
+ * predicted state equal to the moments of f, the UGKS interface flux of Step 1
+ * and the diffuse wall of Sec. 3.2 (Eq. f_on_wall).  theta is the temperature
+ * (param 0), x-velocity (1) or y-velocity (2) of one wall BC.  Objectives of a
+ * wall BC: obj 0 = sum over its faces of face length x shear stress, 1 = heat
+ * flux, 2 = pressure (the quantities of miugks_get_wall).  All in FP64 on an
+ * FP64 copy (checkpoint) of the current f, whatever the solver's precision.
+ *
+ *  stage_adjoint_residual: out = (dN/df)^T mu at the current f, host arrays
+ *        of 2 x nc x nv ([comp][cell][k]).
+ *  stage_sgs_micro_transposed: x = P^T r with P one LU-SGS pass of the
+ *        evolution smoother on level 0 (collision frequency inv_tau, nc).
+ *  objective: J, dJ/df (host, 2 x nc x nv, may be NULL) and dJ/dtheta at
+ *        fixed f (3 values: T, u, v).
+ *  adjoint: gradient dJ/dtheta = dJ/dtheta|_f + lambda . dN/dtheta|_f with
+ *        (dN/df)^T lambda = -(dJ/df)^T solved by restarted GMRES (restart
+ *        length `restart`, at most 32) right-preconditioned by the transposed
+ *        LU-SGS pass, to relative residual tol or max_iter iterations.  In a
+ *        domain bounded only by walls and symmetry planes the steady state is
+ *        fixed up to its total mass M; the total mass is then held fixed (the
+ *        transposed Jacobian gets the rank-one term -m m^T/|m|^2, m = dM/df).
+ *        info (may be NULL) receives {J, iterations, final relative residual}.
+ *        Returns MIUGKS_ENOTCONVERGED when tol was not reached (the gradient
+ *        of the last iterate is still written).  Device work memory (restart+3
+ *        vectors of 2 nc nv doubles) comes from the solver's allocator on the
+ *        first call and is kept. */
+miugks_status miugks_stage_adjoint_residual(miugks_solver *s, const double *mu, double *out);
+miugks_status miugks_stage_sgs_micro_transposed(miugks_solver *s, const double *inv_tau, const double *r, double *x);
+miugks_status miugks_objective(miugks_solver *s, int obj, int bc, double *J, double *dJdf, double dJdtheta[3]);
+miugks_status miugks_adjoint(miugks_solver *s, int obj, int bc, int param, double tol, int max_iter, int restart,
+                             double *grad, double info[3]);
+
 /* Sizes and the CUDA events bracketing the last Step-1 flux launch (for
  * roofline timing): elapsed milliseconds of the flux kernels of the last
  * iteration, or -1 when timing is off.  miugks_set_timing(s, 1) enables it. */

@@ -90,4 +90,42 @@ cudaError_t launch_wall_quantities(const LevelDev& L, const VelDev& V, const BcD
                                    const F* f, int bcid, const int* faces, int nfaces, double* out,
                                    cudaStream_t st);
 
+// ---- differentiation form: adjoint of the steady equations (FP64) ----
+constexpr int kFaceRec = 20;              // doubles per face record of the adjoint residual
+constexpr int kCellRec = 9;               // doubles per cell record
+constexpr int kMaxAdjNv = 8192;           // velocities per cell of the transposed sweep (shared memory)
+struct AdjDev {
+    LevelDev L; VelDev V; GasDev gas;
+    const BcDev* bc; const double* Cw;
+    const double* f;                       // [2][nc][nv] linearisation point (FP64 copy of f)
+    const double* W;                       // [nc][4] its moments
+    const double* q;                       // [nc][2] its heat flux
+    double cfl;
+};
+struct AdjSweepArgs {
+    LevelDev L; VelDev V; const BcDev* bc; const double* Cw; const double* Zw;
+    const double* inv_tau;                 // [nc]
+    const double* r;                       // [2][nc][nv] right-hand side
+    double* y;                             // [2][nc][nv] result of the ascending pass
+    double* x;                             // [2][nc][nv] result
+};
+// out = (dN/df)^T mu (+ pen * dM/df, M the total mass); rec*: per-face / per-cell scratch
+cudaError_t launch_adjoint_residual(const AdjDev& A, const double* mu, double* recx, double* recy, double* crec,
+                                    double pen, double* out, cudaStream_t st);
+// x = P^T r, P one LU-SGS pass of the evolution smoother on level 0
+cudaError_t launch_adjoint_sgs(const AdjSweepArgs& S, cudaStream_t st);
+// per wall face: part[4 m ..] = (S Q, S dQ/dT, S dQ/du, S dQ/dv); dJdf += dJ/df (may be null)
+cudaError_t launch_adjoint_objective(const AdjDev& A, int obj, int bcid, const int* faces, int nfaces, double* part,
+                                     double* dJdf, cudaStream_t st);
+// per wall face: part[3 m + p] = lambda . dN/dtheta_p
+cudaError_t launch_adjoint_dtheta(const AdjDev& A, int bcid, const int* faces, int nfaces, const double* lam,
+                                  double* part, cudaStream_t st);
+cudaError_t launch_multi_dot(const double* Vb, int m, size_t n, const double* w, double* part, int nblk,
+                             cudaStream_t st);
+cudaError_t launch_multi_axpy(const double* Vb, int m, size_t n, const double* h, double a, double* w,
+                              cudaStream_t st);
+cudaError_t launch_mass_dot(const LevelDev& L, const VelDev& V, const double* x, double* part, cudaStream_t st);
+template <typename F> cudaError_t launch_to_double(const F* a, double* b, size_t n, cudaStream_t st);
+cudaError_t launch_inv_tau(const GasDev& gas, const double* W, int nc, double* it, cudaStream_t st);
+
 } // namespace miugks

@@ -67,6 +67,16 @@ struct miugks_solver {
     bool graph_ok = true;
     int eager_done = 0;
     double t_flux = 0, t_sweep = 0, t_total = 0;
+    // adjoint work (FP64), allocated on first use
+    struct {
+        bool alloc = false;
+        int m = 0;                          // Krylov basis vectors allocated
+        double *f = nullptr, *W = nullptr, *q = nullptr, *itau = nullptr;
+        double *recx = nullptr, *recy = nullptr, *crec = nullptr;
+        double *b = nullptr, *x = nullptr, *w = nullptr, *z = nullptr, *t = nullptr, *Vb = nullptr;
+        double *part = nullptr, *fpart = nullptr;
+        int* faces = nullptr;
+    } adj;
 };
 
 namespace {
@@ -1014,6 +1024,305 @@ miugks_status miugks_stage_restrict(miugks_solver* s, int lev, int m, const doub
 miugks_status miugks_stage_prolong(miugks_solver* s, int lev, int m, const double* coarse, double* fine)
 {
     return transfer(s, lev, m, coarse, fine, false);
+}
+
+} // extern "C"
+
+// =========================================================================== adjoint (differentiation form)
+namespace {
+
+constexpr int kDotBlocks = 608;
+
+bool closed_domain(const miugks_solver* s)
+{
+    for (const BcDev& b : s->bch)
+        if (b.type != BC_WALL && b.type != BC_SYMMETRY) return false;
+    return true;
+}
+
+// allocate the adjoint work (basis of m + 1 vectors) and take the FP64 checkpoint of f
+miugks_status adj_prepare(miugks_solver* s, int m)
+{
+    HLevel& L0 = s->lev[0];
+    const size_t n = 2 * (size_t)L0.nc * s->nv;
+    auto& A = s->adj;
+    if (!A.alloc) {
+        ST(dalloc(s, &A.f, n)); ST(dalloc(s, &A.W, 4 * (size_t)L0.nc)); ST(dalloc(s, &A.q, 2 * (size_t)L0.nc));
+        ST(dalloc(s, &A.itau, (size_t)L0.nc));
+        ST(dalloc(s, &A.recx, (size_t)kFaceRec * L0.nfx)); ST(dalloc(s, &A.recy, (size_t)kFaceRec * L0.nfy));
+        ST(dalloc(s, &A.crec, (size_t)kCellRec * L0.nc));
+        ST(dalloc(s, &A.b, n)); ST(dalloc(s, &A.x, n)); ST(dalloc(s, &A.w, n)); ST(dalloc(s, &A.z, n));
+        ST(dalloc(s, &A.t, n));
+        ST(dalloc(s, &A.part, (size_t)kDotBlocks * 33 + L0.nc));
+        ST(dalloc(s, &A.fpart, 4 * (size_t)(L0.nfx + L0.nfy)));
+        ST(dalloc(s, &A.faces, (size_t)(L0.nfx + L0.nfy)));
+        A.alloc = true;
+    }
+    if (m > A.m) {
+        ST(dalloc(s, &A.Vb, (size_t)(m + 1) * n));
+        A.m = m;
+    }
+    if (s->mixed) CK(launch_to_double<float>((const float*)s->f, A.f, n, s->st));
+    else CK(cudaMemcpyAsync(A.f, s->f, n * sizeof(double), cudaMemcpyDeviceToDevice, s->st));
+    CK(launch_moments<double>(L0.dev, s->vel, A.f, A.W, A.q, s->st));
+    CK(launch_inv_tau(s->gas, A.W, L0.nc, A.itau, s->st));
+    return MIUGKS_OK;
+}
+
+AdjDev adj_dev(miugks_solver* s)
+{
+    return AdjDev{s->lev[0].dev, s->vel, s->gas, s->bc, s->Cw, s->adj.f, s->adj.W, s->adj.q, s->opts.cfl};
+}
+
+// host sum (fixed order) of nblk x m partials -> out[m]
+miugks_status sum_parts(miugks_solver* s, int nblk, int m, double* out)
+{
+    std::vector<double> h((size_t)nblk * m);
+    CK(cudaMemcpyAsync(h.data(), s->adj.part, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    for (int q = 0; q < m; ++q) {
+        double a = 0.0;
+        for (int b = 0; b < nblk; ++b) a += h[(size_t)b * m + q];
+        out[q] = a;
+    }
+    return MIUGKS_OK;
+}
+
+miugks_status vdots(miugks_solver* s, const double* Vb, int m, const double* w, double* out)
+{
+    const size_t n = 2 * (size_t)s->lev[0].nc * s->nv;
+    CK(launch_multi_dot(Vb, m, n, w, s->adj.part, kDotBlocks, s->st));
+    return sum_parts(s, kDotBlocks, m, out);
+}
+
+// out = B v = -((dN/df)^T v - m (m . v)/|m|^2 in a closed domain)
+miugks_status apply_B(miugks_solver* s, const double* v, double* out, double mm)
+{
+    HLevel& L0 = s->lev[0];
+    const size_t n = 2 * (size_t)L0.nc * s->nv;
+    double pen = 0.0;
+    if (mm > 0.0) {
+        CK(launch_mass_dot(L0.dev, s->vel, v, s->adj.part, s->st));
+        double mv;
+        ST(sum_parts(s, L0.nc, 1, &mv));
+        pen = -mv / mm;
+    }
+    CK(launch_adjoint_residual(adj_dev(s), v, s->adj.recx, s->adj.recy, s->adj.crec, pen, out, s->st));
+    CK(launch_multi_axpy(nullptr, 0, n, nullptr, -1.0, out, s->st));
+    return MIUGKS_OK;
+}
+
+miugks_status apply_PT(miugks_solver* s, const double* r, double* out)
+{
+    AdjSweepArgs S{s->lev[0].dev, s->vel, s->bc, s->Cw, s->Zw, s->adj.itau, r, s->adj.t, out};
+    CK(launch_adjoint_sgs(S, s->st));
+    return MIUGKS_OK;
+}
+
+miugks_status wall_face_list(miugks_solver* s, int bc, int* nfaces)
+{
+    HLevel& L0 = s->lev[0];
+    std::vector<int> faces;
+    for (int fi = 0; fi < L0.nfx; ++fi) if (L0.fbx[fi] == bc) faces.push_back(fi);
+    for (int fi = 0; fi < L0.nfy; ++fi) if (L0.fby[fi] == bc) faces.push_back((1 << 30) | fi);
+    *nfaces = (int)faces.size();
+    if (!faces.empty())
+        CK(cudaMemcpyAsync(s->adj.faces, faces.data(), faces.size() * sizeof(int), cudaMemcpyHostToDevice, s->st));
+    return MIUGKS_OK;
+}
+
+// J, dJ/dtheta at fixed f (and dJ/df into dJdf_dev when not null) from the checkpoint
+miugks_status objective_dev(miugks_solver* s, int obj, int bc, double* dJdf_dev, double out[4])
+{
+    int nf = 0;
+    ST(wall_face_list(s, bc, &nf));
+    if (dJdf_dev) CK(cudaMemsetAsync(dJdf_dev, 0, 2 * (size_t)s->lev[0].nc * s->nv * sizeof(double), s->st));
+    CK(launch_adjoint_objective(adj_dev(s), obj, bc, s->adj.faces, nf, s->adj.fpart, dJdf_dev, s->st));
+    std::vector<double> h(4 * (size_t)nf);
+    if (nf) CK(cudaMemcpyAsync(h.data(), s->adj.fpart, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    for (int p = 0; p < 4; ++p) {
+        out[p] = 0.0;
+        for (int f = 0; f < nf; ++f) out[p] += h[4 * (size_t)f + p];
+    }
+    return MIUGKS_OK;
+}
+
+miugks_status check_wall_args(miugks_solver* s, int obj, int bc)
+{
+    if (!s->initialised) return fail(s, MIUGKS_ESTATE, "adjoint before init");
+    if (bc < 0 || bc >= s->nbc || s->bch[bc].type != BC_WALL) return fail(s, MIUGKS_EINVAL, "BC %d is not a wall", bc);
+    if (obj < 0 || obj > 2) return fail(s, MIUGKS_EINVAL, "unknown objective %d", obj);
+    if (s->nv > kMaxAdjNv) return fail(s, MIUGKS_EINVAL, "adjoint supports at most %d velocities", kMaxAdjNv);
+    return MIUGKS_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+miugks_status miugks_stage_adjoint_residual(miugks_solver* s, const double* mu, double* out)
+{
+    if (!s || !mu || !out) return MIUGKS_EINVAL;
+    if (!s->initialised) return fail(s, MIUGKS_ESTATE, "stage before init");
+    if (s->nv > kMaxAdjNv) return fail(s, MIUGKS_EINVAL, "adjoint supports at most %d velocities", kMaxAdjNv);
+    ST(adj_prepare(s, 0));
+    const size_t n = 2 * (size_t)s->lev[0].nc * s->nv;
+    CK(cudaMemcpyAsync(s->adj.b, mu, n * sizeof(double), cudaMemcpyHostToDevice, s->st));
+    CK(launch_adjoint_residual(adj_dev(s), s->adj.b, s->adj.recx, s->adj.recy, s->adj.crec, 0.0, s->adj.w, s->st));
+    CK(cudaMemcpyAsync(out, s->adj.w, n * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    return MIUGKS_OK;
+}
+
+miugks_status miugks_stage_sgs_micro_transposed(miugks_solver* s, const double* inv_tau, const double* r, double* x)
+{
+    if (!s || !inv_tau || !r || !x) return MIUGKS_EINVAL;
+    if (!s->initialised) return fail(s, MIUGKS_ESTATE, "stage before init");
+    if (s->nv > kMaxAdjNv) return fail(s, MIUGKS_EINVAL, "adjoint supports at most %d velocities", kMaxAdjNv);
+    ST(adj_prepare(s, 0));
+    HLevel& L0 = s->lev[0];
+    const size_t n = 2 * (size_t)L0.nc * s->nv;
+    CK(cudaMemcpyAsync(s->adj.itau, inv_tau, L0.nc * sizeof(double), cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemcpyAsync(s->adj.b, r, n * sizeof(double), cudaMemcpyHostToDevice, s->st));
+    ST(apply_PT(s, s->adj.b, s->adj.x));
+    CK(cudaMemcpyAsync(x, s->adj.x, n * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    return MIUGKS_OK;
+}
+
+miugks_status miugks_objective(miugks_solver* s, int obj, int bc, double* J, double* dJdf, double dJdtheta[3])
+{
+    if (!s) return MIUGKS_EINVAL;
+    ST(check_wall_args(s, obj, bc));
+    ST(adj_prepare(s, 0));
+    double o[4];
+    ST(objective_dev(s, obj, bc, dJdf ? s->adj.b : nullptr, o));
+    if (J) *J = o[0];
+    if (dJdtheta) for (int p = 0; p < 3; ++p) dJdtheta[p] = o[1 + p];
+    if (dJdf) {
+        CK(cudaMemcpyAsync(dJdf, s->adj.b, 2 * (size_t)s->lev[0].nc * s->nv * sizeof(double), cudaMemcpyDeviceToHost,
+                           s->st));
+        CK(cudaStreamSynchronize(s->st));
+    }
+    return MIUGKS_OK;
+}
+
+miugks_status miugks_adjoint(miugks_solver* s, int obj, int bc, int param, double tol, int max_iter, int restart,
+                             double* grad, double info[3])
+{
+    if (!s || !grad) return MIUGKS_EINVAL;
+    ST(check_wall_args(s, obj, bc));
+    if (param < 0 || param > 2) return fail(s, MIUGKS_EINVAL, "unknown parameter %d", param);
+    if (restart < 1 || restart > 32) return fail(s, MIUGKS_EINVAL, "restart length must be in 1..32");
+    if (!(tol > 0) || max_iter < 1) return fail(s, MIUGKS_EINVAL, "need tol > 0 and max_iter >= 1");
+    const int m = restart;
+    ST(adj_prepare(s, m));
+    HLevel& L0 = s->lev[0];
+    const size_t n = 2 * (size_t)L0.nc * s->nv;
+    auto& A = s->adj;
+    double mm = 0.0;
+    if (closed_domain(s)) {
+        // |m|^2 = sum_c V_c^2 sum_k w_k^2 (G component)
+        double w2 = 0.0;
+        for (int k = 0; k < s->nv; ++k) w2 += s->wh[k] * s->wh[k];
+        for (int j = 0; j < L0.ny; ++j)
+            for (int i = 0; i < L0.nx; ++i) mm += (L0.dx[i] * L0.dy[j]) * (L0.dx[i] * L0.dy[j]) * w2;
+    }
+    double o[4];
+    ST(objective_dev(s, obj, bc, A.b, o));           // b = dJ/df
+    double bnorm;
+    ST(vdots(s, A.b, 1, A.b, &bnorm));
+    bnorm = std::sqrt(bnorm);
+    CK(cudaMemsetAsync(A.x, 0, n * sizeof(double), s->st));
+    int it = 0;
+    double rel = bnorm > 0 ? 1.0 : 0.0;
+    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m), h(m + 1), h2(m + 1);
+    while (bnorm > 0 && it < max_iter && rel > tol) {
+        // r = b - B x into V_0
+        double* V0 = A.Vb;
+        ST(apply_B(s, A.x, A.w, mm));
+        CK(cudaMemcpyAsync(V0, A.b, n * sizeof(double), cudaMemcpyDeviceToDevice, s->st));
+        CK(launch_axpy(V0, A.w, -1.0, n, s->st));
+        double beta;
+        ST(vdots(s, V0, 1, V0, &beta));
+        beta = std::sqrt(beta);
+        rel = beta / bnorm;
+        if (rel <= tol) break;
+        double sc = 1.0 / beta;
+        CK(launch_multi_axpy(nullptr, 0, n, nullptr, sc, V0, s->st));
+        std::fill(g.begin(), g.end(), 0.0);
+        g[0] = beta;
+        int jdone = 0;
+        for (int j = 0; j < m && it < max_iter; ++j) {
+            double* Vj = A.Vb + (size_t)j * n;
+            double* Vn = A.Vb + (size_t)(j + 1) * n;
+            ST(apply_PT(s, Vj, A.z));
+            ST(apply_B(s, A.z, Vn, mm));
+            // classical Gram-Schmidt, twice
+            ST(vdots(s, A.Vb, j + 1, Vn, h.data()));
+            for (int q = 0; q <= j; ++q) h2[q] = -h[q];
+            CK(launch_multi_axpy(A.Vb, j + 1, n, h2.data(), 1.0, Vn, s->st));
+            ST(vdots(s, A.Vb, j + 1, Vn, h2.data()));
+            for (int q = 0; q <= j; ++q) { h[q] += h2[q]; h2[q] = -h2[q]; }
+            CK(launch_multi_axpy(A.Vb, j + 1, n, h2.data(), 1.0, Vn, s->st));
+            double hn;
+            ST(vdots(s, Vn, 1, Vn, &hn));
+            hn = std::sqrt(hn);
+            h[j + 1] = hn;
+            if (hn > 0) CK(launch_multi_axpy(nullptr, 0, n, nullptr, 1.0 / hn, Vn, s->st));
+            // Givens rotations
+            for (int q = 0; q < j; ++q) {
+                double a = cs[q] * h[q] + sn[q] * h[q + 1];
+                h[q + 1] = -sn[q] * h[q] + cs[q] * h[q + 1];
+                h[q] = a;
+            }
+            double rr = std::hypot(h[j], h[j + 1]);
+            cs[j] = rr > 0 ? h[j] / rr : 1.0;
+            sn[j] = rr > 0 ? h[j + 1] / rr : 0.0;
+            h[j] = rr;
+            h[j + 1] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            for (int q = 0; q <= j; ++q) H[(size_t)q * m + j] = h[q];
+            ++it;
+            jdone = j + 1;
+            rel = std::fabs(g[j + 1]) / bnorm;
+            if (rel <= tol || hn == 0.0) break;
+        }
+        // y from the triangular system, x += P^T (V y)
+        for (int q = jdone - 1; q >= 0; --q) {
+            double a = g[q];
+            for (int p2 = q + 1; p2 < jdone; ++p2) a -= H[(size_t)q * m + p2] * y[p2];
+            y[q] = a / H[(size_t)q * m + q];
+        }
+        CK(launch_multi_axpy(A.Vb, jdone, n, y.data(), 0.0, A.w, s->st));
+        ST(apply_PT(s, A.w, A.z));
+        CK(launch_axpy(A.x, A.z, 1.0, n, s->st));
+    }
+    // true relative residual of the final iterate
+    if (bnorm > 0) {
+        ST(apply_B(s, A.x, A.w, mm));
+        CK(launch_axpy(A.w, A.b, -1.0, n, s->st));
+        double rn;
+        ST(vdots(s, A.w, 1, A.w, &rn));
+        rel = std::sqrt(rn) / bnorm;
+    }
+    // gradient: dJ/dtheta|_f + lambda . dN/dtheta|_f with lambda = -x ... sign: B = -(dN/df)^T, B x = dJ/df
+    // gives (dN/df)^T x = -dJ/df, so lambda = x
+    int nf = 0;
+    ST(wall_face_list(s, bc, &nf));
+    CK(launch_adjoint_dtheta(adj_dev(s), bc, A.faces, nf, A.x, A.fpart, s->st));
+    std::vector<double> hp(3 * (size_t)nf);
+    if (nf) CK(cudaMemcpyAsync(hp.data(), A.fpart, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    double ln = 0.0;
+    for (int f = 0; f < nf; ++f) ln += hp[3 * (size_t)f + param];
+    *grad = o[1 + param] + ln;
+    if (info) { info[0] = o[0]; info[1] = it; info[2] = rel; }
+    if (!(rel <= tol)) return fail(s, MIUGKS_ENOTCONVERGED, "adjoint GMRES reached %d iterations at relative residual %.3e",
+                                   it, rel);
+    return MIUGKS_OK;
 }
 
 } // extern "C"

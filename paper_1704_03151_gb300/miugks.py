@@ -84,6 +84,9 @@ def load():
         "miugks_stage_prolong": [vp, _i, _i, vp, vp], "miugks_sizes": [vp, _P(_i), _P(_i), _P(_i), _P(_i)],
         "miugks_set_timing": [vp, _i], "miugks_kernel_times": [vp, _P(_d), _P(_d), _P(_d)],
         "miugks_step_async": [vp, _i], "miugks_wait": [vp, vp],
+        "miugks_stage_adjoint_residual": [vp, vp, vp], "miugks_stage_sgs_micro_transposed": [vp, vp, vp, vp],
+        "miugks_objective": [vp, _i, _i, vp, vp, vp],
+        "miugks_adjoint": [vp, _i, _i, _i, _d, _i, _i, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -103,7 +106,9 @@ def exported_symbols():
             "miugks_get_f", "miugks_set_f", "miugks_get_wall", "miugks_set_bc", "miugks_stage_flux",
             "miugks_stage_sgs_micro", "miugks_stage_apply_micro", "miugks_stage_sgs_macro",
             "miugks_stage_resid_macro", "miugks_stage_restrict", "miugks_stage_prolong", "miugks_sizes",
-            "miugks_set_timing", "miugks_kernel_times", "miugks_step_async", "miugks_wait"]
+            "miugks_set_timing", "miugks_kernel_times", "miugks_step_async", "miugks_wait",
+            "miugks_stage_adjoint_residual", "miugks_stage_sgs_micro_transposed", "miugks_objective",
+            "miugks_adjoint", "miugks_residual_rms_noalloc"]
 
 
 def _ptr(a):
@@ -308,3 +313,84 @@ class Solver:
         fine = np.zeros((self.nc // 4 ** lev, m))
         self._check(self._lib.miugks_stage_prolong(self.h, lev, m, _ptr(coarse), _ptr(fine)))
         return fine
+
+    # ---- differentiation form (adjoint of the steady equations)
+    def adjoint_residual(self, mu):
+        """(dN/df)^T mu at the current f (host arrays, 2 x nc x nv)."""
+        mu = np.ascontiguousarray(mu, dtype=np.float64).reshape(2, self.nc, self.nv)
+        out = np.zeros_like(mu)
+        self._check(self._lib.miugks_stage_adjoint_residual(self.h, _ptr(mu), _ptr(out)))
+        return out
+
+    def sgs_micro_transposed(self, inv_tau, r):
+        """P^T r, P one LU-SGS pass of the evolution smoother on level 0."""
+        r = np.ascontiguousarray(r, dtype=np.float64)
+        it = np.ascontiguousarray(inv_tau, dtype=np.float64)
+        x = np.zeros_like(r)
+        self._check(self._lib.miugks_stage_sgs_micro_transposed(self.h, _ptr(it), _ptr(r), _ptr(x)))
+        return x
+
+    def objective(self, obj, bc):
+        """J, dJ/df and dJ/d(T, u, v) of wall `bc` at the current f."""
+        J = np.zeros(1)
+        dJdf = np.zeros((2, self.nc, self.nv))
+        dth = np.zeros(3)
+        self._check(self._lib.miugks_objective(self.h, obj, bc, _ptr(J), _ptr(dJdf), _ptr(dth)))
+        return float(J[0]), dJdf, dth
+
+    def adjoint(self, obj, bc, param, tol=1e-10, max_iter=2000, restart=30):
+        """dJ/dtheta at the current (converged) state by the adjoint solve;
+        returns (gradient, {"J", "iterations", "residual"})."""
+        g = np.zeros(1)
+        info = np.zeros(3)
+        st = self._lib.miugks_adjoint(self.h, obj, bc, param, tol, max_iter, restart, _ptr(g), _ptr(info))
+        if st not in (MIUGKS_OK, MIUGKS_ENOTCONVERGED):
+            self._check(st)
+        return float(g[0]), {"J": float(info[0]), "iterations": int(info[1]), "residual": float(info[2]),
+                             "converged": st == MIUGKS_OK}
+
+
+OBJECTIVES = {"shear": 0, "heat_flux": 1, "pressure": 2}
+PARAMS = {"t": 0, "u": 1, "v": 2}
+_WallObjective = None
+
+
+def wall_objective(solver, theta, obj="shear", bc=0, param="t", tol=1e-10, max_iter=5000, adj_tol=1e-10,
+                   adj_max_iter=2000):
+    """J(theta): a wall objective at the converged state, as a differentiable
+    torch function of one wall parameter (temperature or velocity component of
+    wall `bc`).  Forward: set the parameter, run the solver to RMS residual
+    `tol`, evaluate J and keep a checkpoint of the converged f.  Backward:
+    restore the checkpoint and return the adjoint gradient times the incoming
+    gradient.  theta is a 0-d (or 1-element) float64 tensor."""
+    global _WallObjective
+    import torch
+    if _WallObjective is None:
+        class _WO(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, th, s, o, b, p, tl, mi, atl, ami):
+                B = s.case["bcs"][b]
+                vals = {"t": B["t"], "u": B["u"], "v": B["v"]}
+                vals[p] = float(th.detach().cpu().reshape(-1)[0])
+                s.set_bc(b, B["type"], B["rho"], vals["u"], vals["v"], vals["t"])
+                s.init_uniform(s.case["init"]["rho"], s.case["init"]["u"], s.case["init"]["v"], s.case["init"]["t"])
+                it, res, ok = s.run(tl, mi)
+                if not ok:
+                    raise MiugksError(MIUGKS_ENOTCONVERGED, "forward solve not converged (%s)" % res)
+                J = s.objective(OBJECTIVES[o], b)[0]
+                ctx.solver, ctx.args = s, (OBJECTIVES[o], b, PARAMS[p], atl, ami)
+                ctx.f_ckpt = s.get_f()
+                return th.new_tensor(J)
+
+            @staticmethod
+            def backward(ctx, gJ):
+                s = ctx.solver
+                s.set_f(ctx.f_ckpt)
+                obj_, b, p, atl, ami = ctx.args
+                g, info = s.adjoint(obj_, b, p, tol=atl, max_iter=ami)
+                if not info["converged"]:
+                    raise MiugksError(MIUGKS_ENOTCONVERGED, "adjoint not converged (%s)" % info)
+                return (gJ * g,) + (None,) * 8
+
+        _WallObjective = _WO
+    return _WallObjective.apply(theta, solver, obj, bc, param, tol, max_iter, adj_tol, adj_max_iter)
