@@ -166,7 +166,8 @@ def run_reference(args):
     return 0
 
 
-def measure(precision, steps, warmup, world, rank, dev, with_e2e=True, with_ttr=True, clocks=True):
+def measure(precision, steps, warmup, world, rank, dev, with_e2e=True, with_ttr=True, clocks=True,
+            with_adjoint=False):
     import torch
     from paper_1704_03151_gb300 import miugks, workloads
     stream = torch.cuda.Stream()
@@ -191,12 +192,15 @@ def measure(precision, steps, warmup, world, rank, dev, with_e2e=True, with_ttr=
     # stage breakdown in a separate pass (per-stage events synchronise the host every iteration)
     s.set_timing(True)
     s.kernel_times()
+    s.macro_sweep_times()
     nst = max(3, steps // 5)
     s.step(nst)
     flux_ms, sweep_ms, total_ms = s.kernel_times()
+    macro_ms, macro_n = s.macro_sweep_times()
     s.set_timing(False)
     out = {"value": cv * steps * world / (ms * 1e-3), "ms_per_step": ms / steps, "clocks": clk,
            "flux_ms_per_launch": flux_ms / nst / 2.0,
+           "macro_ms_per_launch": macro_ms / max(macro_n, 1), "macro_launches_per_step": macro_n / nst,
            "stage_ms_per_step": {"flux": flux_ms / nst, "evolution_cs": sweep_ms / nst, "total": total_ms / nst},
            "residual_last": [float(x) for x in res]}
     if with_e2e:
@@ -221,8 +225,37 @@ def measure(precision, steps, warmup, world, rank, dev, with_e2e=True, with_ttr=
         iters, rr, ok = s.run(1e-6, 3000)
         out["time_to_residual"] = {"seconds": time.perf_counter() - t0, "iterations": iters, "converged": bool(ok),
                                    "residual": [float(x) for x in rr]}
+        if with_adjoint:
+            # differentiation form at the converged state: d(lid shear)/d(lid speed), FP64 adjoint
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g, info = s.adjoint(0, 2, 1, tol=1e-8, max_iter=600)
+            out["adjoint"] = {"objective": "lid-wall shear force", "parameter": "lid speed", "gradient": g,
+                              "seconds": time.perf_counter() - t0, "gmres_iterations": info["iterations"],
+                              "relative_residual": info["residual"], "converged": info["converged"]}
     s.close()
     return out
+
+
+# Dominant kernel of the step (largest share of the ncu launch list): the
+# prediction smoother's LU-SGS sweep, k_macro_sgs, on the finest level.
+# Algorithmic bytes per cell and launch: reads W, R (4 doubles each), the
+# inverse diagonal (1), the Gamma of the faces (2 per cell), writes dW and W
+# (4 each): 19 doubles = 152 B.
+MACRO_BYTES_PER_CELL = 152.0
+# DRAM bytes (read + write) of one finest-level k_macro_sgs<float> launch from
+# the ncu capture summarised in profiles/k_macro_sgs_cavity64_v32_mixed.md
+MACRO_TRAFFIC_MIXED = 1.793792e6
+
+
+def macro_roofline(m, precision):
+    t = m["macro_ms_per_launch"] * 1e-3
+    hpeak, hsrc = hbm_peak()
+    gbs = MACRO_BYTES_PER_CELL * NX * NY / t / 1e9
+    return {"bound": "hbm", "kernel": "k_macro_sgs (finest level)", "achieved": gbs, "peak": hpeak, "unit": "GB/s",
+            "frac": gbs / hpeak, "traffic": MACRO_TRAFFIC_MIXED if precision == "mixed" else None,
+            "peak_source": hsrc, "launch_ms": m["macro_ms_per_launch"],
+            "limiter": "dependency chain: %d anti-diagonals per sweep, one halo exchange each" % (NX + NY - 1)}
 
 
 def flux_roofline(m, precision):
@@ -247,6 +280,24 @@ def flux_roofline(m, precision):
             "frac": bytes_ / hpeak, "traffic": None, "peak_source": hsrc, "alu_frac": flops / fpeak}
 
 
+# algorithmic passes over one per-velocity array (Nc Nv 2 values) per outer
+# iteration of the 3-level V(2,1) cycle with 4 coarsest smoothings: flux and
+# residual 2, every fine smoothing 4-5, transfers 3.5, update 3, coarse levels
+# about 6 (see the design notes): 29 passes
+PASSES_PER_ITERATION = 29.0
+
+
+def step_hbm(m, precision):
+    """Whole-step bandwidth: the method's compulsory bytes per iteration over
+    the measured time per iteration."""
+    size = 4 if precision == "mixed" else 8
+    b = PASSES_PER_ITERATION * 2 * NX * NY * NVEL * NVEL * size
+    hpeak, hsrc = hbm_peak()
+    gbs = b / (m["ms_per_step"] * 1e-3) / 1e9
+    return {"bytes_per_step": b, "achieved": gbs, "peak": hpeak, "unit": "GB/s", "frac": gbs / hpeak,
+            "peak_source": hsrc}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -257,6 +308,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttr", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint gradient at the converged state")
     ap.add_argument("--workload", default="cavity64", choices=["cavity64", "kn_sweep"])
     ap.add_argument("--count", type=int, default=32, help="cavities of the Kn sweep")
     ap.add_argument("--max-iter", type=int, default=1500)
@@ -271,7 +323,8 @@ def main():
     from paper_1704_03151_gb300 import build
     build.build()
     dev = torch.cuda.current_device()
-    head = measure(args.precision, args.steps, args.warmup, world, rank, dev, with_ttr=not args.no_ttr)
+    head = measure(args.precision, args.steps, args.warmup, world, rank, dev, with_ttr=not args.no_ttr,
+                   with_adjoint=not args.no_adjoint)
     other = None
     if not args.no_fp64 and args.precision == "mixed":
         other = measure("fp64", max(3, args.steps // 3), args.warmup, world, rank, dev, with_e2e=False,
@@ -297,17 +350,22 @@ def main():
         "gpu_launches": count_launches() * args.steps,
         "clocks": head["clocks"],
         "e2e": head["e2e"],
-        "roofline": flux_roofline(head, args.precision),
+        "roofline": macro_roofline(head, args.precision),
+        "roofline_flux": flux_roofline(head, args.precision),
+        "step_hbm": step_hbm(head, args.precision),
         "stage_ms_per_step": head["stage_ms_per_step"],
         "residual_last": head["residual_last"],
         "time_to_residual": head.get("time_to_residual"),
+        "adjoint": head.get("adjoint"),
         "cpu_baseline": cpu,
     }
     if other:
         line["fp64"] = {"value": other["value"], "ms_per_step": other["ms_per_step"],
                         "stage_ms_per_step": other["stage_ms_per_step"],
                         "time_to_residual": other.get("time_to_residual"),
-                        "roofline": flux_roofline(other, "fp64")}
+                        "roofline": macro_roofline(other, "fp64"),
+                        "roofline_flux": flux_roofline(other, "fp64"),
+                        "step_hbm": step_hbm(other, "fp64")}
     print(json.dumps(line))
     return 0
 

@@ -193,12 +193,25 @@ miugks_status miugks_objective(miugks_solver *s, int obj, int bc, double *J, dou
 miugks_status miugks_adjoint(miugks_solver *s, int obj, int bc, int param, double tol, int max_iter, int restart,
                              double *grad, double info[3]);
 
+/* Checkpoint and resume: save writes the state (f in FP64, the BC table and
+ * the iteration count) to a file; load reads it into a solver created with the
+ * same mesh size, velocity grid and BC types, replacing its f, BC values and
+ * iteration count.  Errors: MIUGKS_EINVAL for an unreadable, truncated or
+ * mismatching file; the solver is unchanged unless the file was valid. */
+miugks_status miugks_save(miugks_solver *s, const char *path);
+miugks_status miugks_load(miugks_solver *s, const char *path);
+
 /* Sizes and the CUDA events bracketing the last Step-1 flux launch (for
  * roofline timing): elapsed milliseconds of the flux kernels of the last
  * iteration, or -1 when timing is off.  miugks_set_timing(s, 1) enables it. */
 miugks_status miugks_sizes(const miugks_solver *s, int *nx, int *ny, int *nv, int *levels);
 miugks_status miugks_set_timing(miugks_solver *s, int on);
 miugks_status miugks_kernel_times(miugks_solver *s, double *flux_ms, double *sweep_ms, double *total_ms);
+/* With timing on, every launch of the prediction smoother's LU-SGS kernel on
+ * the finest level (Eq. macroFinalDefect, Sec. 2.1.1) is bracketed by its own
+ * pair of CUDA events: total milliseconds and launch count since the last
+ * call (-1 and 0 when timing is off); the counters are reset. */
+miugks_status miugks_macro_sweep_times(miugks_solver *s, double *ms, int *launches);
 
 /* Residual norm of caller-owned device arrays without allocating anything.
  * The paper has no counterpart: this serves callers that cannot allocate at

@@ -67,6 +67,11 @@ struct miugks_solver {
     bool graph_ok = true;
     int eager_done = 0;
     double t_flux = 0, t_sweep = 0, t_total = 0;
+    // per-launch events of the finest-level prediction sweep (timing mode only)
+    std::vector<cudaEvent_t> ev_macro;
+    int n_macro_used = 0;
+    double t_macro = 0;
+    long n_macro = 0;
     // adjoint work (FP64), allocated on first use
     struct {
         bool alloc = false;
@@ -254,6 +259,25 @@ cudaError_t macro_sgs(miugks_solver* s, const MacroArgs& ma, HLevel& Lv)
     return launch_macro_sgs<double>(ma, Lv.Wc, Lv.gx, Lv.gy, Lv.idiag, Lv.T, Lv.R, Lv.dW, s->st);
 }
 
+// one prediction sweep; on the finest level, bracketed by events in timing mode
+miugks_status timed_macro_sgs(miugks_solver* s, const MacroArgs& ma, HLevel& Lv, int l)
+{
+    if (!s->timing || l != 0) {
+        CK(macro_sgs(s, ma, Lv));
+        return MIUGKS_OK;
+    }
+    while ((int)s->ev_macro.size() < 2 * (s->n_macro_used + 1)) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        s->ev_macro.push_back(e);
+    }
+    CK(cudaEventRecord(s->ev_macro[2 * s->n_macro_used], s->st));
+    CK(macro_sgs(s, ma, Lv));
+    CK(cudaEventRecord(s->ev_macro[2 * s->n_macro_used + 1], s->st));
+    s->n_macro_used++;
+    return MIUGKS_OK;
+}
+
 miugks_status fas(miugks_solver* s, int l, double dti)
 {
     HLevel& Lv = s->lev[l];
@@ -266,7 +290,7 @@ miugks_status fas(miugks_solver* s, int l, double dti)
     const bool coarsest = l == s->L - 1;
     const int npre = coarsest ? (s->L == 1 ? 1 : s->opts.nu_coarse) : s->opts.nu1;
     for (int m = 0; m < npre; ++m) {
-        CK(macro_sgs(s, ma, Lv));
+        ST(timed_macro_sgs(s, ma, Lv, l));
         if (coarsest && m == npre - 1) break;
         CK(launch_macro_resid(ma, Lv.Wc, Lv.gx, Lv.gy, Lv.P, Lv.R, 1, s->st));  // renewal P + R_E(W)
     }
@@ -279,7 +303,7 @@ miugks_status fas(miugks_solver* s, int l, double dti)
     CK(launch_prolong_add<double>(Lv.dev, Cv.dev, 4, 1, Lv.pidx, Lv.pw, Cv.dW, Lv.Wc, (double*)nullptr, s->st));
     for (int m = 0; m < s->opts.nu2; ++m) {
         CK(launch_macro_resid(ma, Lv.Wc, Lv.gx, Lv.gy, Lv.P, Lv.R, 1, s->st));
-        CK(macro_sgs(s, ma, Lv));
+        ST(timed_macro_sgs(s, ma, Lv, l));
     }
     return MIUGKS_OK;
 }
@@ -454,6 +478,7 @@ void miugks_destroy(miugks_solver* s)
     }
     for (auto& e : s->ev)
         if (e) cudaEventDestroy(e);
+    for (auto& e : s->ev_macro) cudaEventDestroy(e);
     if (s->gexec) cudaGraphExecDestroy(s->gexec);
     if (s->graph) cudaGraphDestroy(s->graph);
     delete s;
@@ -718,6 +743,13 @@ static miugks_status enqueue_iterations(miugks_solver* s, int n_iter)
                 CK(cudaEventElapsedTime(&b, s->ev[2], s->ev[3]));
                 CK(cudaEventElapsedTime(&c, s->ev[0], s->ev[4]));
                 s->t_flux += a; s->t_sweep += b; s->t_total += c;
+                for (int q = 0; q < s->n_macro_used; ++q) {
+                    float t = 0;
+                    CK(cudaEventElapsedTime(&t, s->ev_macro[2 * q], s->ev_macro[2 * q + 1]));
+                    s->t_macro += t;
+                }
+                s->n_macro += s->n_macro_used;
+                s->n_macro_used = 0;
             }
         }
         s->iter++;
@@ -888,6 +920,16 @@ miugks_status miugks_set_timing(miugks_solver* s, int on)
     if (!s) return MIUGKS_EINVAL;
     s->timing = on != 0;
     s->t_flux = s->t_sweep = s->t_total = 0;
+    return MIUGKS_OK;
+}
+
+miugks_status miugks_macro_sweep_times(miugks_solver* s, double* ms, int* launches)
+{
+    if (!s) return MIUGKS_EINVAL;
+    if (ms) *ms = s->timing ? s->t_macro : -1.0;
+    if (launches) *launches = s->timing ? (int)s->n_macro : 0;
+    s->t_macro = 0;
+    s->n_macro = 0;
     return MIUGKS_OK;
 }
 
@@ -1322,6 +1364,70 @@ miugks_status miugks_adjoint(miugks_solver* s, int obj, int bc, int param, doubl
     if (info) { info[0] = o[0]; info[1] = it; info[2] = rel; }
     if (!(rel <= tol)) return fail(s, MIUGKS_ENOTCONVERGED, "adjoint GMRES reached %d iterations at relative residual %.3e",
                                    it, rel);
+    return MIUGKS_OK;
+}
+
+} // extern "C"
+
+// =========================================================================== checkpoint / resume
+extern "C" {
+
+// File layout (native byte order): 8-byte magic "MIUGKSv1", int32 nx, ny, nu, nvv, nbc, iter,
+// then nbc x {int32 type, 4 doubles rho, u, v, T}, then f as FP64 [2][nc][nv].
+miugks_status miugks_save(miugks_solver* s, const char* path)
+{
+    if (!s || !path) return MIUGKS_EINVAL;
+    if (!s->initialised) return fail(s, MIUGKS_ESTATE, "save before init");
+    const size_t n = 2 * (size_t)s->lev[0].nc * s->nv;
+    std::vector<double> f(n);
+    ST(to_host(s, f.data(), s->f, n));
+    FILE* fp = std::fopen(path, "wb");
+    if (!fp) return fail(s, MIUGKS_EINVAL, "cannot open %s for writing", path);
+    const char magic[8] = {'M', 'I', 'U', 'G', 'K', 'S', 'v', '1'};
+    int32_t hdr[6] = {s->lev[0].nx, s->lev[0].ny, s->nu, s->nvv, s->nbc, s->iter};
+    bool ok = std::fwrite(magic, 1, 8, fp) == 8 && std::fwrite(hdr, sizeof hdr, 1, fp) == 1;
+    for (int b = 0; ok && b < s->nbc; ++b) {
+        int32_t t = s->bch[b].type;
+        double v[4] = {s->bch[b].rho, s->bch[b].u, s->bch[b].v, s->bch[b].t};
+        ok = std::fwrite(&t, sizeof t, 1, fp) == 1 && std::fwrite(v, sizeof v, 1, fp) == 1;
+    }
+    ok = ok && std::fwrite(f.data(), sizeof(double), n, fp) == n;
+    ok = (std::fclose(fp) == 0) && ok;
+    return ok ? MIUGKS_OK : fail(s, MIUGKS_EINVAL, "write to %s failed", path);
+}
+
+miugks_status miugks_load(miugks_solver* s, const char* path)
+{
+    if (!s || !path) return MIUGKS_EINVAL;
+    FILE* fp = std::fopen(path, "rb");
+    if (!fp) return fail(s, MIUGKS_EINVAL, "cannot open %s", path);
+    char magic[8];
+    int32_t hdr[6];
+    bool ok = std::fread(magic, 1, 8, fp) == 8 && std::memcmp(magic, "MIUGKSv1", 8) == 0 &&
+              std::fread(hdr, sizeof hdr, 1, fp) == 1;
+    if (!ok || hdr[0] != s->lev[0].nx || hdr[1] != s->lev[0].ny || hdr[2] != s->nu || hdr[3] != s->nvv ||
+        hdr[4] != s->nbc) {
+        std::fclose(fp);
+        return fail(s, MIUGKS_EINVAL, "%s is not a checkpoint of this mesh, velocity grid and BC table", path);
+    }
+    std::vector<BcDev> bcs(s->nbc);
+    for (int b = 0; ok && b < s->nbc; ++b) {
+        int32_t t;
+        double v[4];
+        ok = std::fread(&t, sizeof t, 1, fp) == 1 && std::fread(v, sizeof v, 1, fp) == 1 && t == s->bch[b].type;
+        bcs[b] = BcDev{t, v[0], v[1], v[2], v[3]};
+    }
+    const size_t n = 2 * (size_t)s->lev[0].nc * s->nv;
+    std::vector<double> f(n);
+    ok = ok && std::fread(f.data(), sizeof(double), n, fp) == n;
+    std::fclose(fp);
+    if (!ok) return fail(s, MIUGKS_EINVAL, "%s is truncated or its BC types differ", path);
+    for (int b = 0; b < s->nbc; ++b) {
+        miugks_bc v{(miugks_bc_type)bcs[b].type, bcs[b].rho, bcs[b].u, bcs[b].v, bcs[b].t};
+        ST(miugks_set_bc(s, b, &v));
+    }
+    ST(miugks_set_f(s, f.data()));
+    s->iter = hdr[5];
     return MIUGKS_OK;
 }
 

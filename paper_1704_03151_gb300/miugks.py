@@ -87,6 +87,8 @@ def load():
         "miugks_stage_adjoint_residual": [vp, vp, vp], "miugks_stage_sgs_micro_transposed": [vp, vp, vp, vp],
         "miugks_objective": [vp, _i, _i, vp, vp, vp],
         "miugks_adjoint": [vp, _i, _i, _i, _d, _i, _i, vp, vp],
+        "miugks_save": [vp, ctypes.c_char_p], "miugks_load": [vp, ctypes.c_char_p],
+        "miugks_macro_sweep_times": [vp, _P(_d), _P(_i)],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -108,7 +110,8 @@ def exported_symbols():
             "miugks_stage_resid_macro", "miugks_stage_restrict", "miugks_stage_prolong", "miugks_sizes",
             "miugks_set_timing", "miugks_kernel_times", "miugks_step_async", "miugks_wait",
             "miugks_stage_adjoint_residual", "miugks_stage_sgs_micro_transposed", "miugks_objective",
-            "miugks_adjoint", "miugks_residual_rms_noalloc"]
+            "miugks_adjoint", "miugks_residual_rms_noalloc", "miugks_save", "miugks_load",
+            "miugks_macro_sweep_times"]
 
 
 def _ptr(a):
@@ -266,6 +269,12 @@ class Solver:
         self._check(self._lib.miugks_kernel_times(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
         return a.value, b.value, c.value
 
+    def macro_sweep_times(self):
+        """(total ms, launches) of the finest-level prediction sweeps since the last call."""
+        ms, n = _d(), _i()
+        self._check(self._lib.miugks_macro_sweep_times(self.h, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
     # ---- stages
     def stage_flux(self):
         nfx, nfy = (self.nx + 1) * self.ny, self.nx * (self.ny + 1)
@@ -313,6 +322,12 @@ class Solver:
         fine = np.zeros((self.nc // 4 ** lev, m))
         self._check(self._lib.miugks_stage_prolong(self.h, lev, m, _ptr(coarse), _ptr(fine)))
         return fine
+
+    def save(self, path):
+        self._check(self._lib.miugks_save(self.h, os.fsencode(path)))
+
+    def load(self, path):
+        self._check(self._lib.miugks_load(self.h, os.fsencode(path)))
 
     # ---- differentiation form (adjoint of the steady equations)
     def adjoint_residual(self, mu):
