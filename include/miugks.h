@@ -178,17 +178,24 @@ miugks_status miugks_stage_prolong(miugks_solver *s, int lev, int m, const doubl
  *  adjoint: gradient dJ/dtheta = dJ/dtheta|_f + lambda . dN/dtheta|_f with
  *        (dN/df)^T lambda = -(dJ/df)^T solved by restarted GMRES (restart
  *        length `restart`, at most 32) right-preconditioned by the transposed
- *        LU-SGS pass, to relative residual tol or max_iter iterations.  In a
+ *        CS cycle (stage_cs_transposed; one transposed LU-SGS pass on a single
+ *        grid), to relative residual tol or max_iter iterations.  In a
  *        domain bounded only by walls and symmetry planes the steady state is
  *        fixed up to its total mass M; the total mass is then held fixed (the
  *        transposed Jacobian gets the rank-one term -m m^T/|m|^2, m = dM/df).
  *        info (may be NULL) receives {J, iterations, final relative residual}.
  *        Returns MIUGKS_ENOTCONVERGED when tol was not reached (the gradient
  *        of the last iterate is still written).  Device work memory (restart+3
- *        vectors of 2 nc nv doubles) comes from the solver's allocator on the
- *        first call and is kept. */
+ *        vectors of 2 nc nv doubles, and six per level for the transposed cycle)
+ *        comes from the solver's allocator on the first call and is kept. */
 miugks_status miugks_stage_adjoint_residual(miugks_solver *s, const double *mu, double *out);
 miugks_status miugks_stage_sgs_micro_transposed(miugks_solver *s, const double *inv_tau, const double *r, double *x);
+/*  stage_cs_transposed: out = M^T z with M one CS cycle (Eq. CSCYC, the
+ *        solver's levels and smoothing counts) as a linear map of the level-0
+ *        residual, frozen collision frequencies inv_tau of every level
+ *        concatenated level after level (sum of nc_l values).  The adjoint
+ *        solve uses this transposed cycle as its preconditioner. */
+miugks_status miugks_stage_cs_transposed(miugks_solver *s, const double *inv_tau, const double *z, double *out);
 miugks_status miugks_objective(miugks_solver *s, int obj, int bc, double *J, double *dJdf, double dJdtheta[3]);
 miugks_status miugks_adjoint(miugks_solver *s, int obj, int bc, int param, double tol, int max_iter, int restart,
                              double *grad, double info[3]);

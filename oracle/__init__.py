@@ -84,6 +84,7 @@ def lib():
         L.oracle_adjoint_residual.argtypes = [vp, vp, vp]
         L.oracle_objective.argtypes = [vp, i, i, vp, vp, vp]
         L.oracle_residual_dtheta.argtypes = [vp, i, i, vp]
+        L.oracle_stage_cs.argtypes = [vp, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -228,6 +229,14 @@ class Oracle:
         x = np.zeros_like(r)
         _check(lib().oracle_stage_sgs_micro(self.h, lev, _p(it), _p(r), _p(x), order))
         return x
+
+    def cs_cycle(self, inv_tau_levels, r):
+        """One CS cycle (frozen coefficients) applied to the level-0 residual r."""
+        it = np.ascontiguousarray(np.concatenate([np.ravel(a) for a in inv_tau_levels]), dtype=np.float64)
+        r = np.ascontiguousarray(r, dtype=np.float64)
+        df = np.zeros_like(r)
+        _check(lib().oracle_stage_cs(self.h, _p(it), _p(r), _p(df)))
+        return df
 
     def apply_micro(self, lev, inv_tau, x):
         x = np.ascontiguousarray(x, dtype=np.float64)

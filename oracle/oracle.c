@@ -2172,3 +2172,20 @@ int oracle_residual_dtheta(oracle_solver *s, int bc, int param, double *dN)
     }
     return 0;
 }
+
+/* One CS cycle (Eq. CSCYC) as a linear map of the level-0 residual r with
+ * frozen coefficients: inv_tau holds the collision frequency of every level,
+ * level after level (sum of nc_l values); df = the total correction. */
+int oracle_stage_cs(oracle_solver *s, const double *inv_tau, const double *r, double *df)
+{
+    size_t off = 0;
+    for (int l = 0; l < s->L; ++l) {
+        memcpy(s->lev[l].inv_tau, inv_tau + off, (size_t)s->lev[l].nc * sizeof(double));
+        off += (size_t)s->lev[l].nc;
+    }
+    size_t n = 2 * (size_t)s->lev[0].nc * s->nv;
+    memcpy(s->lev[0].r, r, n * sizeof(double));
+    cs(s, 0);
+    memcpy(df, s->lev[0].df, n * sizeof(double));
+    return 0;
+}

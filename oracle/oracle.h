@@ -93,6 +93,9 @@ int oracle_stage_resid_macro(oracle_solver *s, int lev, const double *W,
 int oracle_stage_restrict(oracle_solver *s, int lev, int ncomp, const double *fine, double *coarse);
 int oracle_stage_prolong(oracle_solver *s, int lev, int ncomp, const double *coarse, double *fine);
 int oracle_level_size(const oracle_solver *s, int lev, int *nx, int *ny);
+/*  cs : one CS cycle as a linear map of the level-0 residual r (2 x nc x nv),
+ *       inv_tau of every level concatenated (sum of nc_l values) -> df.      */
+int oracle_stage_cs(oracle_solver *s, const double *inv_tau, const double *r, double *df);
 int oracle_nv(const oracle_solver *s);
 
 /* ---- steady equations and their adjoint (differentiation form) ----

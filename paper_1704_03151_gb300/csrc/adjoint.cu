@@ -24,6 +24,7 @@ namespace miugks {
 namespace {
 
 constexpr int kRed = 32;   // shared reduction slots per value (one per warp)
+constexpr size_t kAdjCacheBytes = 160 * 1024;   // dynamic shared memory of the cached face kernel (at most)
 
 // time integrals q_m(dt, tau) of the UGKS integral solution and their tau
 // derivatives: closed form for x = dt/tau >= 1, power series below
@@ -174,6 +175,7 @@ __device__ __forceinline__ double adj_vl(double s1, double s2)
 struct FaceGeo {
     int cLL, cL, cR, cRR;
     double dLLL, dLR, dRRR, hL, hR, wL, wR;
+    double rLLL, rLR, rRRR;                 // reciprocals of the centre distances
 };
 
 __device__ __forceinline__ FaceGeo face_geo(const LevelDev& L, int axis, int fi)
@@ -201,6 +203,7 @@ __device__ __forceinline__ FaceGeo face_geo(const LevelDev& L, int axis, int fi)
         g.hL = L.yn[j] - L.yc[j - 1]; g.hR = L.yc[j] - L.yn[j];
         g.wL = L.dy[j - 1]; g.wR = L.dy[j];
     }
+    g.rLLL = 1.0 / g.dLLL; g.rLR = 1.0 / g.dLR; g.rRRR = 1.0 / g.dRRR;
     return g;
 }
 
@@ -209,8 +212,8 @@ __device__ __forceinline__ void face_recon(const double* fc, size_t nv, int k, c
                                            double& f0, double& sg)
 {
     double fL = fc[g.cL * nv + k], fR = fc[g.cR * nv + k];
-    double sL = g.cLL >= 0 ? adj_vl((fL - fc[g.cLL * nv + k]) / g.dLLL, (fR - fL) / g.dLR) : 0.0;
-    double sR = g.cRR >= 0 ? adj_vl((fR - fL) / g.dLR, (fc[g.cRR * nv + k] - fR) / g.dRRR) : 0.0;
+    double sL = g.cLL >= 0 ? adj_vl((fL - fc[g.cLL * nv + k]) * g.rLLL, (fR - fL) * g.rLR) : 0.0;
+    double sR = g.cRR >= 0 ? adj_vl((fR - fL) * g.rLR, (fc[g.cRR * nv + k] - fR) * g.rRRR) : 0.0;
     double faceL = fL + sL * g.hL, faceR = fR - sR * g.hR;
     if (un > 0) { f0 = faceL; sg = sL; }
     else if (un < 0) { f0 = faceR; sg = sR; }
@@ -228,11 +231,18 @@ __device__ __forceinline__ void red_sum(double (&v)[N], double* scratch)
 // ---------------------------------------------------------------------------
 // per-face record: [0..3] W0 adjoint, [4..5] q0 adjoint, [6] U0, [7] V0,
 // [8] q4/dt, [9] q5/dt, [10..13] W_L adjoint, [14..17] W_R adjoint,
-// [18] wall faces: rho_w adjoint / sum_in w u_o C
+// [18] wall faces: rho_w adjoint / sum_in w u_o C, [20..22] reciprocal centre
+// distances LL-L, L-R, R-RR, [23..24] face-centre distances h_L, h_R,
+// [25..26] dN/dPhi coefficients of mu_L, mu_R, [27] 1 (LL exists) + 2 (RR exists).
+// CACHE: the upwinded face values and slopes of every velocity are kept in
+// shared memory after the first pass instead of being reconstructed again.
+template <bool CACHE>
 __global__ void __launch_bounds__(256) k_adj_face(AdjDev A, int axis, const double* __restrict__ mu,
                                                    double* __restrict__ rec)
 {
     __shared__ double red[kRed * 25];
+    extern __shared__ double etab[];           // e^{-lam0 (u_a - U0)^2} [nu], then e^{-lam0 (v_b - V0)^2} [nvv]
+    double* fcache = etab + (A.V.nu + A.V.nvv);   // CACHE: [4][nv] f0 G, f0 H, slope G, slope H
     const LevelDev& L = A.L;
     const VelDev& Vg = A.V;
     const int nv = Vg.nv, tid = threadIdx.x, bs = blockDim.x, fi = blockIdx.x;
@@ -273,13 +283,23 @@ __global__ void __launch_bounds__(256) k_adj_face(AdjDev A, int axis, const doub
 
     const FaceGeo g = face_geo(L, axis, fi);
     const double nuL = -1.0 / g.wL, nuR = 1.0 / g.wR;      // nu = nuL mu_L + nuR mu_R
+    // upwinded reconstructed values and slopes of velocity k (both components)
+    auto recon = [&](int k, double un, double& f0g, double& f0h, double& sgg, double& sgh) {
+        if (CACHE) {
+            f0g = fcache[k]; f0h = fcache[nv + k]; sgg = fcache[2 * nv + k]; sgh = fcache[3 * nv + k];
+        } else {
+            face_recon(fG, snv, k, g, un, f0g, sgg);
+            face_recon(fH, snv, k, g, un, f0h, sgh);
+        }
+    };
     // ---- forward pass A: interface conservative variables
     double W0[4] = {0, 0, 0, 0};
     for (int k = tid; k < nv; k += bs) {
         double un = axis == 0 ? Vg.u[k] : Vg.v[k];
-        double f0g, f0h, sg;
+        double f0g, f0h, sg, sgh;
         face_recon(fG, snv, k, g, un, f0g, sg);
-        face_recon(fH, snv, k, g, un, f0h, sg);
+        face_recon(fH, snv, k, g, un, f0h, sgh);
+        if (CACHE) { fcache[k] = f0g; fcache[nv + k] = f0h; fcache[2 * nv + k] = sg; fcache[3 * nv + k] = sgh; }
         double u = Vg.u[k], v = Vg.v[k], w = Vg.w[k];
         W0[0] += w * f0g; W0[1] += w * u * f0g; W0[2] += w * v * f0g;
         W0[3] += w * (0.5 * (u * u + v * v) * f0g + f0h);
@@ -300,19 +320,26 @@ __global__ void __launch_bounds__(256) k_adj_face(AdjDev A, int axis, const doub
     adj_slope(dwl, U0, V0, lam0, aL);
     adj_slope(dwr, U0, V0, lam0, aR);
     const double xi = kKint * (kKint + 2.0) / (16.0 * lam0 * lam0);
+    // separable equilibrium: gM(k) = rho0 lam0/pi Eu[a] Ev[b] (nu + nvv exponentials per face)
+    for (int e = tid; e < Vg.nu + Vg.nvv; e += bs) {
+        double dlt = e < Vg.nu ? Vg.ua[e] - U0 : Vg.vb[e - Vg.nu] - V0;
+        etab[e] = exp(-lam0 * dlt * dlt);
+    }
+    __syncthreads();
+    const double gnorm = rho0 * lam0 / kPi, hfac = kKint / (4.0 * lam0), idt = 1.0 / dt;
+    auto gM_of = [&](int k) -> double { int a = k / Vg.nvv; return gnorm * etab[a] * etab[Vg.nu + k - a * Vg.nvv]; };
     // ---- forward pass B: heat flux of f0 and compatibility moments
     double s6[6] = {0, 0, 0, 0, 0, 0};
     for (int k = tid; k < nv; k += bs) {
         double un = axis == 0 ? Vg.u[k] : Vg.v[k];
-        double f0g, f0h, sg;
-        face_recon(fG, snv, k, g, un, f0g, sg);
-        face_recon(fH, snv, k, g, un, f0h, sg);
+        double f0g, f0h, sg, sgh;
+        recon(k, un, f0g, f0h, sg, sgh);
         double u = Vg.u[k], v = Vg.v[k], w = Vg.w[k];
         double cx = u - U0, cy = v - V0, c2 = cx * cx + cy * cy, e = 0.5 * c2 * f0g + f0h;
         s6[0] += w * cx * e;
         s6[1] += w * cy * e;
         if (un != 0.0) {
-            double gM = adj_maxw(rho0, U0, V0, lam0, u, v), hM = gM * kKint / (4.0 * lam0), mG, mH;
+            double gM = gM_of(k), hM = gM * hfac, mG, mH;
             adj_smom(un > 0 ? aL : aR, u, v, gM, hM, xi, mG, mH);
             s6[2] += w * un * mG; s6[3] += w * un * u * mG; s6[4] += w * un * v * mG;
             s6[5] += w * un * (0.5 * (u * u + v * v) * mG + mH);
@@ -337,11 +364,10 @@ __global__ void __launch_bounds__(256) k_adj_face(AdjDev A, int axis, const doub
         double un = axis == 0 ? Vg.u[k] : Vg.v[k];
         if (un == 0.0) continue;
         double f0g, f0h, sgg, sgh;
-        face_recon(fG, snv, k, g, un, f0g, sgg);
-        face_recon(fH, snv, k, g, un, f0h, sgh);
+        recon(k, un, f0g, f0h, sgg, sgh);
         double u = Vg.u[k], v = Vg.v[k];
         double cx = u - U0, cy = v - V0, c2 = cx * cx + cy * cy;
-        double gM = adj_maxw(rho0, U0, V0, lam0, u, v), hM = gM * kKint / (4.0 * lam0);
+        double gM = gM_of(k), hM = gM * hfac;
         double Fq = shk * (cx * q0[0] + cy * q0[1]);
         double eG = 2.0 * lam0 * c2 - 4.0, eH = 2.0 * lam0 * c2 - 2.0;
         double gP = gM * (1.0 + Fq * eG), hP = hM * (1.0 + Fq * eH);
@@ -350,8 +376,8 @@ __global__ void __launch_bounds__(256) k_adj_face(AdjDev A, int axis, const doub
         double mGa, mHa, mGA, mHA;
         adj_smom(as, u, v, gM, hM, xi, mGa, mHa);
         adj_smom(At, u, v, gM, hM, xi, mGA, mHA);
-        double PbG = (nuL * muG[g.cL * snv + k] + nuR * muG[g.cR * snv + k]) / dt;
-        double PbH = (nuL * muH[g.cL * snv + k] + nuR * muH[g.cR * snv + k]) / dt;
+        double PbG = (nuL * muG[g.cL * snv + k] + nuR * muG[g.cR * snv + k]) * idt;
+        double PbH = (nuL * muH[g.cL * snv + k] + nuR * muH[g.cR * snv + k]) * idt;
         r[0] += un * (PbG * gP + PbH * hP);
         r[1] += un * un * (PbG * mGa + PbH * mHa);
         r[2] += un * (PbG * mGA + PbH * mHA);
@@ -397,13 +423,12 @@ __global__ void __launch_bounds__(256) k_adj_face(AdjDev A, int axis, const doub
     for (int m = 0; m < 13; ++m) t[m] = 0.0;      // [0..3] aL, [4..7] aR, [8] rho, [9] U, [10] V, [11] lam, [12] xi
     for (int k = tid; k < nv; k += bs) {
         double un = axis == 0 ? Vg.u[k] : Vg.v[k];
-        double f0g, f0h, sg;
-        face_recon(fG, snv, k, g, un, f0g, sg);
-        face_recon(fH, snv, k, g, un, f0h, sg);
+        double f0g, f0h, sg, sgh;
+        recon(k, un, f0g, f0h, sg, sgh);
         double u = Vg.u[k], v = Vg.v[k], w = Vg.w[k];
         double cx = u - U0, cy = v - V0, c2 = cx * cx + cy * cy, E = 0.5 * c2 * f0g + f0h;
         if (un != 0.0) {
-            double gM = adj_maxw(rho0, U0, V0, lam0, u, v), hM = gM * kKint / (4.0 * lam0);
+            double gM = gM_of(k), hM = gM * hfac;
             double mGb = w * un * (Mtb[0] + Mtb[1] * u + Mtb[2] * v + Mtb[3] * 0.5 * (u * u + v * v));
             double mHb = w * un * Mtb[3];
             double gMb = 0.0, hMb = 0.0;
@@ -434,6 +459,8 @@ __global__ void __launch_bounds__(256) k_adj_face(AdjDev A, int axis, const doub
         out[6] = U0; out[7] = V0;
         out[8] = qc[3] / dt; out[9] = qc[4] / dt;
         out[18] = 0.0; out[19] = 0.0;
+        out[20] = g.rLLL; out[21] = g.rLR; out[22] = g.rRRR; out[23] = g.hL; out[24] = g.hR;
+        out[25] = nuL; out[26] = nuR; out[27] = (g.cLL >= 0 ? 1.0 : 0.0) + (g.cRR >= 0 ? 2.0 : 0.0);
     }
 }
 
@@ -513,14 +540,27 @@ __device__ __forceinline__ void face_contrib(const AdjDev& A, const double* mu, 
     const LevelDev& L = A.L;
     const VelDev& Vg = A.V;
     const size_t nc = L.nc, snv = Vg.nv;
-    const FaceGeo g = face_geo(L, axis, fi);
-    if ((pos == 0 && g.cLL < 0) || (pos == 3 && g.cRR < 0)) return;
     const double* R = rec + (size_t)fi * kFaceRec;
+    const int flags = (int)R[27];
+    if ((pos == 0 && !(flags & 1)) || (pos == 3 && !(flags & 2))) return;
+    // stencil and geometry of the face (computed once per face by k_adj_face)
+    FaceGeo g;
+    const int nx = L.nx;
+    if (axis == 0) {
+        int i = fi % (nx + 1), j = fi / (nx + 1);
+        g.cL = j * nx + i - 1; g.cR = g.cL + 1;
+        g.cLL = (flags & 1) ? g.cL - 1 : -1; g.cRR = (flags & 2) ? g.cR + 1 : -1;
+    } else {
+        int i = fi % nx, j = fi / nx;
+        g.cL = (j - 1) * nx + i; g.cR = g.cL + nx;
+        g.cLL = (flags & 1) ? g.cL - nx : -1; g.cRR = (flags & 2) ? g.cR + nx : -1;
+    }
+    g.rLLL = R[20]; g.rLR = R[21]; g.rRRR = R[22]; g.hL = R[23]; g.hR = R[24];
     const double u = Vg.u[k], v = Vg.v[k], w = Vg.w[k];
     const double un = axis == 0 ? u : v;
     const double e2 = 0.5 * (u * u + v * v);
     const double cx = u - R[6], cy = v - R[7], qdc = R[4] * cx + R[5] * cy;
-    const double nuL = -1.0 / g.wL, nuR = 1.0 / g.wR;
+    const double nuL = R[25], nuR = R[26];
     for (int cp = 0; cp < 2; ++cp) {
         const double* fc = A.f + cp * nc * snv;
         const double* mc = mu + cp * nc * snv;
@@ -537,23 +577,23 @@ __device__ __forceinline__ void face_contrib(const AdjDev& A, const double* mu, 
         double fL = fc[g.cL * snv + k], fR = fc[g.cR * snv + k];
         double res = pos == 1 ? fLb : pos == 2 ? fRb : 0.0;
         if (g.cLL >= 0 && sLb != 0.0) {
-            double s1 = (fL - fc[g.cLL * snv + k]) / g.dLLL, s2 = (fR - fL) / g.dLR;
+            double s1 = (fL - fc[g.cLL * snv + k]) * g.rLLL, s2 = (fR - fL) * g.rLR;
             if (s1 * s2 > 0.0) {
-                double dd = (s1 + s2) * (s1 + s2);
-                double s1b = sLb * 2.0 * s2 * s2 / dd, s2b = sLb * 2.0 * s1 * s1 / dd;
-                if (pos == 0) res -= s1b / g.dLLL;
-                else if (pos == 1) res += s1b / g.dLLL - s2b / g.dLR;
-                else if (pos == 2) res += s2b / g.dLR;
+                double dd = 2.0 * sLb / ((s1 + s2) * (s1 + s2));
+                double s1b = dd * s2 * s2, s2b = dd * s1 * s1;
+                if (pos == 0) res -= s1b * g.rLLL;
+                else if (pos == 1) res += s1b * g.rLLL - s2b * g.rLR;
+                else if (pos == 2) res += s2b * g.rLR;
             }
         }
         if (g.cRR >= 0 && sRb != 0.0) {
-            double s2 = (fR - fL) / g.dLR, s3 = (fc[g.cRR * snv + k] - fR) / g.dRRR;
+            double s2 = (fR - fL) * g.rLR, s3 = (fc[g.cRR * snv + k] - fR) * g.rRRR;
             if (s2 * s3 > 0.0) {
-                double dd = (s2 + s3) * (s2 + s3);
-                double s2b = sRb * 2.0 * s3 * s3 / dd, s3b = sRb * 2.0 * s2 * s2 / dd;
-                if (pos == 1) res -= s2b / g.dLR;
-                else if (pos == 2) res += s2b / g.dLR - s3b / g.dRRR;
-                else if (pos == 3) res += s3b / g.dRRR;
+                double dd = 2.0 * sRb / ((s2 + s3) * (s2 + s3));
+                double s2b = dd * s3 * s3, s3b = dd * s2 * s2;
+                if (pos == 1) res -= s2b * g.rLR;
+                else if (pos == 2) res += s2b * g.rLR - s3b * g.rRRR;
+                else if (pos == 3) res += s3b * g.rRRR;
             }
         }
         out[cp] += res;
@@ -688,10 +728,14 @@ __global__ void __launch_bounds__(256) k_adjT_sweep(AdjSweepArgs S, int pass, in
         return uo < 0 ? uo * bS[b] : 0.0;
     };
     auto Dk = [&](int k) -> double { return it + fabs(Vg.u[k]) * rdx + fabs(Vg.v[k]) * rdy; };
-    auto den_of = [&](int k) -> double {
+    bool outflow = false;
+    for (int b = 0; b < nb; ++b) outflow = outflow || btype[b] == BC_OUTFLOW;
+    // reciprocal of the diagonal (with the outflow ghost, which is the cell itself)
+    auto rden_of = [&](int k) -> double {
+        if (!outflow) return S.invD[(size_t)c * snv + k];
         double dd = Dk(k);
         for (int b = 0; b < nb; ++b) if (btype[b] == BC_OUTFLOW) dd += Db(b, k);
-        return dd;
+        return 1.0 / dd;
     };
     auto base_of = [&](int cp, int k) -> double {
         size_t e = (cp * nc + c) * snv + k;
@@ -714,9 +758,9 @@ __global__ void __launch_bounds__(256) k_adjT_sweep(AdjSweepArgs S, int pass, in
 
     if (nwall + nsym == 0) {
         for (int k = tid; k < nv; k += bs) {
-            double dd = den_of(k);
-            dst[(size_t)c * snv + k] = base_of(0, k) / dd;
-            dst[(nc + c) * snv + k] = base_of(1, k) / dd;
+            double rd = rden_of(k);
+            dst[(size_t)c * snv + k] = base_of(0, k) * rd;
+            dst[(nc + c) * snv + k] = base_of(1, k) * rd;
         }
         return;
     }
@@ -725,15 +769,15 @@ __global__ void __launch_bounds__(256) k_adjT_sweep(AdjSweepArgs S, int pass, in
         // s_b = a_b + m_b s_o with o the other wall
         double acc[4] = {0, 0, 0, 0};
         for (int k = tid; k < nv; k += bs) {
-            double dd = den_of(k), b0 = base_of(0, k), b1 = base_of(1, k);
+            double rd = rden_of(k), b0 = base_of(0, k), b1 = base_of(1, k);
             for (int b = 0; b < 2; ++b) {
                 double Dbk = Db(b, k);
                 if (Dbk == 0.0) continue;
                 int o = 1 - b;
                 double C = S.Cw[(size_t)bid[b] * nv + k];
-                acc[b] += Dbk * C * (b0 + Hf[b] * b1) / dd;
+                acc[b] += Dbk * C * (b0 + Hf[b] * b1) * rd;
                 double uoo = bos[o] * (bax[o] == 0 ? Vg.u[k] : Vg.v[k]);
-                if (uoo > 0) acc[2 + b] += Dbk * C * Vg.w[k] * uoo / Z[o] / dd;
+                if (uoo > 0) acc[2 + b] += Dbk * C * Vg.w[k] * uoo / Z[o] * rd;
             }
         }
         red_sum<4>(acc, red);
@@ -741,22 +785,22 @@ __global__ void __launch_bounds__(256) k_adjT_sweep(AdjSweepArgs S, int pass, in
         double s1 = acc[1] + acc[3] * s0;
         double sb[2] = {s0, s1};
         for (int k = tid; k < nv; k += bs) {
-            double dd = den_of(k), g0 = base_of(0, k);
+            double rd = rden_of(k), g0 = base_of(0, k);
             for (int b = 0; b < 2; ++b) {
                 double uo = bos[b] * (bax[b] == 0 ? Vg.u[k] : Vg.v[k]);
                 if (uo > 0) g0 += Vg.w[k] * uo / Z[b] * sb[b];
             }
-            dst[(size_t)c * snv + k] = g0 / dd;
-            dst[(nc + c) * snv + k] = base_of(1, k) / dd;
+            dst[(size_t)c * snv + k] = g0 * rd;
+            dst[(nc + c) * snv + k] = base_of(1, k) * rd;
         }
         return;
     }
     // three substitution rounds (exact: the coupling is nilpotent of the same
     // degree as in the untransposed block)
     for (int k = tid; k < nv; k += bs) {
-        double dd = den_of(k);
-        ys[k] = base_of(0, k) / dd;
-        ys[nv + k] = base_of(1, k) / dd;
+        double rd = rden_of(k);
+        ys[k] = base_of(0, k) * rd;
+        ys[nv + k] = base_of(1, k) * rd;
     }
     __syncthreads();
     for (int round = 0; round < 3; ++round) {
@@ -769,7 +813,7 @@ __global__ void __launch_bounds__(256) k_adjT_sweep(AdjSweepArgs S, int pass, in
             }
         red_sum<2>(sb, red);     // ends with a barrier: ys is read by all before it changes
         for (int k = tid; k < nv; k += bs) {
-            double dd = den_of(k), g0 = base_of(0, k), g1 = base_of(1, k);
+            double rd = rden_of(k), g0 = base_of(0, k), g1 = base_of(1, k);
             for (int b = 0; b < nb; ++b) {
                 double uo = bos[b] * (bax[b] == 0 ? Vg.u[k] : Vg.v[k]);
                 if (!(uo > 0)) continue;
@@ -781,8 +825,8 @@ __global__ void __launch_bounds__(256) k_adjT_sweep(AdjSweepArgs S, int pass, in
                     g1 -= Dm * ys[nv + km];
                 }
             }
-            dst[(size_t)c * snv + k] = g0 / dd;
-            dst[(nc + c) * snv + k] = g1 / dd;
+            dst[(size_t)c * snv + k] = g0 * rd;
+            dst[(nc + c) * snv + k] = g1 * rd;
         }
         __syncthreads();
         for (int k = tid; k < nv; k += bs) {
@@ -790,6 +834,109 @@ __global__ void __launch_bounds__(256) k_adjT_sweep(AdjSweepArgs S, int pass, in
             ys[nv + k] = dst[(nc + c) * snv + k];
         }
         __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// y = A^T x on one level: A is the evolution operator of Eq. microFinalDefect
+// with every neighbour and every boundary ghost (the operator of the residual
+// renewal, Eq. renewResidualMicro).  Row c of A^T collects the coefficient that
+// each neighbour's row holds for c, and the transposed within-cell ghost block.
+// One CTA per cell.
+__global__ void __launch_bounds__(256) k_adjT_apply(AdjSweepArgs S, const double* __restrict__ x,
+                                                     double* __restrict__ y)
+{
+    __shared__ double red[kRed * 4];
+    const LevelDev& L = S.L;
+    const VelDev& Vg = S.V;
+    const int nx = L.nx, ny = L.ny, nv = Vg.nv, tid = threadIdx.x, bs = blockDim.x;
+    const size_t nc = L.nc, snv = nv;
+    const int c = blockIdx.x, i = c % nx, j = c / nx;
+    const double rdx = 1.0 / L.dx[i], rdy = 1.0 / L.dy[j], it = S.inv_tau[c];
+    const bool nW = i > 0 && L.fbx[j * (nx + 1) + i] < 0, nE = i < nx - 1 && L.fbx[j * (nx + 1) + i + 1] < 0;
+    const bool nS = j > 0 && L.fby[j * nx + i] < 0, nN = j < ny - 1 && L.fby[(j + 1) * nx + i] < 0;
+    const double cW = nW ? 1.0 / L.dx[i - 1] : 0.0, cE = nE ? 1.0 / L.dx[i + 1] : 0.0;
+    const double cS = nS ? 1.0 / L.dy[j - 1] : 0.0, cN = nN ? 1.0 / L.dy[j + 1] : 0.0;
+    int nb = 0, bax[4], bos[4], btype[4], bid[4];
+    double bS[4], Z[4], Hf[4];
+    auto addb = [&](int ax, int os, int id, double rS) {
+        bax[nb] = ax; bos[nb] = os; bid[nb] = id; bS[nb] = rS; btype[nb] = S.bc[id].type;
+        Hf[nb] = kKint * S.bc[id].t / 4.0;
+        Z[nb] = btype[nb] == BC_WALL ? S.Zw[id * 4 + ax * 2 + (os > 0)] : 0.0;
+        ++nb;
+    };
+    if (i == 0) addb(0, -1, L.fbx[j * (nx + 1)], rdx);
+    if (j == 0) addb(1, -1, L.fby[i], rdy);
+    if (i == nx - 1) addb(0, 1, L.fbx[j * (nx + 1) + nx], rdx);
+    if (j == ny - 1) addb(1, 1, L.fby[ny * nx + i], rdy);
+    auto Db = [&](int b, int k) -> double {
+        double uo = bos[b] * (bax[b] == 0 ? Vg.u[k] : Vg.v[k]);
+        return uo < 0 ? uo * bS[b] : 0.0;
+    };
+    // wall sums s_b = sum over velocities incoming at b of Db (C x_G + C Hf x_H)
+    double sb[4] = {0, 0, 0, 0};
+    for (int k = tid; k < nv; k += bs)
+        for (int b = 0; b < nb; ++b) {
+            if (btype[b] != BC_WALL) continue;
+            double Dbk = Db(b, k);
+            if (Dbk != 0.0)
+                sb[b] += Dbk * S.Cw[(size_t)bid[b] * nv + k] * (x[c * snv + k] + Hf[b] * x[(nc + c) * snv + k]);
+        }
+    red_sum<4>(sb, red);
+    for (int k = tid; k < nv; k += bs) {
+        const double u = Vg.u[k], v = Vg.v[k];
+        const double D = it + fabs(u) * rdx + fabs(v) * rdy;
+        for (int cp = 0; cp < 2; ++cp) {
+            const size_t e = (cp * nc + c) * snv + k;
+            double acc = D * x[e];
+            if (nW && u < 0) acc += u * cW * x[e - snv];
+            if (nE && u > 0) acc -= u * cE * x[e + snv];
+            if (nS && v < 0) acc += v * cS * x[e - (size_t)nx * snv];
+            if (nN && v > 0) acc -= v * cN * x[e + (size_t)nx * snv];
+            for (int b = 0; b < nb; ++b) {
+                if (btype[b] == BC_OUTFLOW) { acc += Db(b, k) * x[e]; continue; }
+                double uo = bos[b] * (bax[b] == 0 ? u : v);
+                if (!(uo > 0)) continue;
+                if (btype[b] == BC_WALL) {
+                    if (cp == 0) acc += -Vg.w[k] * uo / Z[b] * sb[b];
+                } else if (btype[b] == BC_SYMMETRY) {
+                    int a = k / Vg.nvv, bb = k - a * Vg.nvv;
+                    int km = bax[b] == 0 ? (Vg.nu - 1 - a) * Vg.nvv + bb : a * Vg.nvv + (Vg.nvv - 1 - bb);
+                    acc += Db(b, km) * x[(cp * nc + c) * snv + km];
+                }
+            }
+            y[e] = acc;
+        }
+    }
+}
+
+// fine = R^T coarse: R is the volume-weighted restriction of Eq. microRestriction,
+// so fine cell j of coarse cell I receives V_j / V_I times coarse_I (2 x nv values per cell)
+__global__ void k_adjT_restrict(LevelDev F, LevelDev C, int nv, const double* __restrict__ coarse,
+                                double* __restrict__ fine)
+{
+    const int c = blockIdx.x, i = c % F.nx, j = c / F.nx, I = i / 2, J = j / 2, cc = J * C.nx + I;
+    double VI = 0.0;          // sum of the four fine volumes, as the restriction divides by it
+    for (int q = 0; q < 4; ++q) VI += F.dx[2 * I + (q & 1)] * F.dy[2 * J + (q >> 1)];
+    const double wgt = F.dx[i] * F.dy[j] / VI;
+    for (int q = threadIdx.x; q < 2 * nv; q += blockDim.x) {
+        const int cp = q / nv, k = q - cp * nv;
+        fine[((size_t)cp * F.nc + c) * nv + k] = wgt * coarse[((size_t)cp * C.nc + cc) * nv + k];
+    }
+}
+
+// coarse = P^T fine: P is the bilinear prolongation (Eq. prolongation); rows of P^T
+// are gathered through the inverse stencil (CSR: ptr[I] .. ptr[I+1] of (fine cell, weight))
+__global__ void k_adjT_prolong(LevelDev F, LevelDev C, int nv, const int* __restrict__ ptr,
+                               const int* __restrict__ cell, const double* __restrict__ wgt,
+                               const double* __restrict__ fine, double* __restrict__ coarse)
+{
+    const int I = blockIdx.x, p0 = ptr[I], p1 = ptr[I + 1];
+    for (int q = threadIdx.x; q < 2 * nv; q += blockDim.x) {
+        const int cp = q / nv, k = q - cp * nv;
+        double acc = 0.0;
+        for (int p = p0; p < p1; ++p) acc += wgt[p] * fine[((size_t)cp * F.nc + cell[p]) * nv + k];
+        coarse[((size_t)cp * C.nc + I) * nv + k] = acc;
     }
 }
 
@@ -980,6 +1127,15 @@ __global__ void k_to_double(const F* __restrict__ a, double* __restrict__ b, siz
         b[e] = (double)a[e];
 }
 
+// 1 / (1/tau_c + |u_k|/dx + |v_k|/dy) per (cell, velocity) of one level
+__global__ void k_adj_invD(LevelDev L, VelDev Vg, const double* __restrict__ it, double* __restrict__ invD)
+{
+    const int c = blockIdx.x, i = c % L.nx, j = c / L.nx;
+    const double rdx = 1.0 / L.dx[i], rdy = 1.0 / L.dy[j];
+    for (int k = threadIdx.x; k < Vg.nv; k += blockDim.x)
+        invD[(size_t)c * Vg.nv + k] = 1.0 / (it[c] + fabs(Vg.u[k]) * rdx + fabs(Vg.v[k]) * rdy);
+}
+
 __global__ void k_inv_tau_of(GasDev gas, const double* __restrict__ W, int nc, double* __restrict__ it)
 {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -996,8 +1152,18 @@ __global__ void k_inv_tau_of(GasDev gas, const double* __restrict__ W, int nc, d
 cudaError_t launch_adjoint_residual(const AdjDev& A, const double* mu, double* recx, double* recy, double* crec,
                                     double pen, double* out, cudaStream_t st)
 {
-    k_adj_face<<<A.L.nfx, 256, 0, st>>>(A, 0, mu, recx);
-    k_adj_face<<<A.L.nfy, 256, 0, st>>>(A, 1, mu, recy);
+    const size_t etab = (size_t)(A.V.nu + A.V.nvv) * sizeof(double);
+    const size_t cache = etab + 4 * (size_t)A.V.nv * sizeof(double);
+    if (cache <= kAdjCacheBytes) {
+        cudaError_t e = cudaFuncSetAttribute(k_adj_face<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kAdjCacheBytes);
+        if (e != cudaSuccess) return e;
+        k_adj_face<true><<<A.L.nfx, 256, cache, st>>>(A, 0, mu, recx);
+        k_adj_face<true><<<A.L.nfy, 256, cache, st>>>(A, 1, mu, recy);
+    } else {
+        k_adj_face<false><<<A.L.nfx, 256, etab, st>>>(A, 0, mu, recx);
+        k_adj_face<false><<<A.L.nfy, 256, etab, st>>>(A, 1, mu, recy);
+    }
     k_adj_cell<<<A.L.nc, 256, 0, st>>>(A, mu, crec);
     dim3 grid(A.L.nc, (A.V.nv + 127) / 128);
     k_adj_gather<<<grid, 128, 0, st>>>(A, mu, recx, recy, crec, pen, out);
@@ -1018,6 +1184,26 @@ cudaError_t launch_adjoint_sgs(const AdjSweepArgs& S, cudaStream_t st)
             int ilo = d - (ny - 1) > 0 ? d - (ny - 1) : 0, ihi = d < nx - 1 ? d : nx - 1;
             k_adjT_sweep<<<ihi - ilo + 1, 256, smem, st>>>(S, pass, d);
         }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_apply(const AdjSweepArgs& S, const double* x, double* y, cudaStream_t st)
+{
+    k_adjT_apply<<<S.L.nc, 256, 0, st>>>(S, x, y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_restrict_t(const LevelDev& F, const LevelDev& C, int nv, const double* coarse,
+                                      double* fine, cudaStream_t st)
+{
+    k_adjT_restrict<<<F.nc, 256, 0, st>>>(F, C, nv, coarse, fine);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_prolong_t(const LevelDev& F, const LevelDev& C, int nv, const int* ptr, const int* cell,
+                                     const double* wgt, const double* fine, double* coarse, cudaStream_t st)
+{
+    k_adjT_prolong<<<C.nc, 256, 0, st>>>(F, C, nv, ptr, cell, wgt, fine, coarse);
     return cudaGetLastError();
 }
 
@@ -1065,6 +1251,12 @@ cudaError_t launch_to_double(const F* a, double* b, size_t n, cudaStream_t st)
 }
 template cudaError_t launch_to_double<float>(const float*, double*, size_t, cudaStream_t);
 template cudaError_t launch_to_double<double>(const double*, double*, size_t, cudaStream_t);
+
+cudaError_t launch_adjoint_invD(const LevelDev& L, const VelDev& V, const double* it, double* invD, cudaStream_t st)
+{
+    k_adj_invD<<<L.nc, 256, 0, st>>>(L, V, it, invD);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_inv_tau(const GasDev& gas, const double* W, int nc, double* it, cudaStream_t st)
 {

@@ -91,7 +91,7 @@ cudaError_t launch_wall_quantities(const LevelDev& L, const VelDev& V, const BcD
                                    cudaStream_t st);
 
 // ---- differentiation form: adjoint of the steady equations (FP64) ----
-constexpr int kFaceRec = 20;              // doubles per face record of the adjoint residual
+constexpr int kFaceRec = 28;              // doubles per face record of the adjoint residual
 constexpr int kCellRec = 9;               // doubles per cell record
 constexpr int kMaxAdjNv = 8192;           // velocities per cell of the transposed sweep (shared memory)
 struct AdjDev {
@@ -105,6 +105,7 @@ struct AdjDev {
 struct AdjSweepArgs {
     LevelDev L; VelDev V; const BcDev* bc; const double* Cw; const double* Zw;
     const double* inv_tau;                 // [nc]
+    const double* invD;                    // [nc][nv] 1 / (1/tau + |u|/dx + |v|/dy)
     const double* r;                       // [2][nc][nv] right-hand side
     double* y;                             // [2][nc][nv] result of the ascending pass
     double* x;                             // [2][nc][nv] result
@@ -114,6 +115,14 @@ cudaError_t launch_adjoint_residual(const AdjDev& A, const double* mu, double* r
                                     double pen, double* out, cudaStream_t st);
 // x = P^T r, P one LU-SGS pass of the evolution smoother on level 0
 cudaError_t launch_adjoint_sgs(const AdjSweepArgs& S, cudaStream_t st);
+// y = A^T x with the evolution operator of one level (all neighbours and ghosts)
+cudaError_t launch_adjoint_apply(const AdjSweepArgs& S, const double* x, double* y, cudaStream_t st);
+// fine = R^T coarse (volume-weighted restriction transposed), coarse = P^T fine (bilinear
+// prolongation transposed, inverse stencil in CSR form); 2 x nv values per cell
+cudaError_t launch_adjoint_restrict_t(const LevelDev& F, const LevelDev& C, int nv, const double* coarse,
+                                      double* fine, cudaStream_t st);
+cudaError_t launch_adjoint_prolong_t(const LevelDev& F, const LevelDev& C, int nv, const int* ptr, const int* cell,
+                                     const double* wgt, const double* fine, double* coarse, cudaStream_t st);
 // per wall face: part[4 m ..] = (S Q, S dQ/dT, S dQ/du, S dQ/dv); dJdf += dJ/df (may be null)
 cudaError_t launch_adjoint_objective(const AdjDev& A, int obj, int bcid, const int* faces, int nfaces, double* part,
                                      double* dJdf, cudaStream_t st);
@@ -127,5 +136,6 @@ cudaError_t launch_multi_axpy(const double* Vb, int m, size_t n, const double* h
 cudaError_t launch_mass_dot(const LevelDev& L, const VelDev& V, const double* x, double* part, cudaStream_t st);
 template <typename F> cudaError_t launch_to_double(const F* a, double* b, size_t n, cudaStream_t st);
 cudaError_t launch_inv_tau(const GasDev& gas, const double* W, int nc, double* it, cudaStream_t st);
+cudaError_t launch_adjoint_invD(const LevelDev& L, const VelDev& V, const double* it, double* invD, cudaStream_t st);
 
 } // namespace miugks

@@ -81,6 +81,14 @@ struct miugks_solver {
         double *b = nullptr, *x = nullptr, *w = nullptr, *z = nullptr, *t = nullptr, *Vb = nullptr;
         double *part = nullptr, *fpart = nullptr;
         int* faces = nullptr;
+        // per level: state of the transposed CS cycle (checkpointed W and 1/tau,
+        // work vectors, inverse prolongation stencil to the next coarser level)
+        struct Lvl {
+            double *W = nullptr, *itau = nullptr, *invD = nullptr, *T[6] = {}, *z = nullptr, *o = nullptr;
+            int *pptr = nullptr, *pcell = nullptr;
+            double* pw = nullptr;
+        } lv[kMaxLevels];
+        bool lv_alloc = false;
     } adj;
 };
 
@@ -1082,6 +1090,9 @@ bool closed_domain(const miugks_solver* s)
     return true;
 }
 
+miugks_status adj_prepare_levels(miugks_solver* s);
+miugks_status refresh_invD(miugks_solver* s);
+
 // allocate the adjoint work (basis of m + 1 vectors) and take the FP64 checkpoint of f
 miugks_status adj_prepare(miugks_solver* s, int m)
 {
@@ -1108,6 +1119,142 @@ miugks_status adj_prepare(miugks_solver* s, int m)
     else CK(cudaMemcpyAsync(A.f, s->f, n * sizeof(double), cudaMemcpyDeviceToDevice, s->st));
     CK(launch_moments<double>(L0.dev, s->vel, A.f, A.W, A.q, s->st));
     CK(launch_inv_tau(s->gas, A.W, L0.nc, A.itau, s->st));
+    return adj_prepare_levels(s);
+}
+
+// per-level work of the transposed CS cycle; W and 1/tau of every level from
+// the volume-restricted checkpoint (the coarse collision time of the forward cycle)
+miugks_status adj_prepare_levels(miugks_solver* s)
+{
+    auto& A = s->adj;
+    if (!A.lv_alloc) {
+        for (int l = 0; l < s->L; ++l) {
+            HLevel& Lv = s->lev[l];
+            auto& V = A.lv[l];
+            const size_t n = 2 * (size_t)Lv.nc * s->nv;
+            if (l > 0) {
+                ST(dalloc(s, &V.W, 4 * (size_t)Lv.nc)); ST(dalloc(s, &V.itau, (size_t)Lv.nc));
+                ST(dalloc(s, &V.z, n)); ST(dalloc(s, &V.o, n));
+            }
+            for (int q = 0; q < 6; ++q) ST(dalloc(s, &V.T[q], n));
+            ST(dalloc(s, &V.invD, (size_t)Lv.nc * s->nv));
+            if (l + 1 < s->L) {
+                // inverse of the bilinear prolongation stencil (same weights as the forward cycle)
+                HLevel& C = s->lev[l + 1];
+                std::vector<std::vector<std::pair<int, double>>> inv((size_t)C.nc);
+                for (int j = 0; j < Lv.ny; ++j)
+                    for (int i = 0; i < Lv.nx; ++i) {
+                        int I = i / 2, J = j / 2, IN, JN;
+                        double ax, bx, ay, by;
+                        lin_weights(C.xc, I, Lv.xc[i], IN, ax, bx);
+                        lin_weights(C.yc, J, Lv.yc[j], JN, ay, by);
+                        int c = j * Lv.nx + i;
+                        inv[(size_t)J * C.nx + I].push_back({c, ax * ay});
+                        inv[(size_t)J * C.nx + IN].push_back({c, bx * ay});
+                        inv[(size_t)JN * C.nx + I].push_back({c, ax * by});
+                        inv[(size_t)JN * C.nx + IN].push_back({c, bx * by});
+                    }
+                std::vector<int> ptr(1, 0), cell;
+                std::vector<double> w;
+                for (auto& v : inv) {
+                    for (auto& e : v) { cell.push_back(e.first); w.push_back(e.second); }
+                    ptr.push_back((int)cell.size());
+                }
+                ST(upload(s, &V.pptr, ptr)); ST(upload(s, &V.pcell, cell)); ST(upload(s, &V.pw, w));
+            }
+        }
+        A.lv_alloc = true;
+    }
+    A.lv[0].W = A.W;
+    A.lv[0].itau = A.itau;
+    for (int l = 1; l < s->L; ++l) {
+        CK(launch_restrict<double>(s->lev[l - 1].dev, s->lev[l].dev, 4, 1, A.lv[l - 1].W, A.lv[l].W, s->st));
+        CK(launch_inv_tau(s->gas, A.lv[l].W, s->lev[l].nc, A.lv[l].itau, s->st));
+    }
+    return refresh_invD(s);
+}
+
+// inverse diagonals of every level from the current collision frequencies
+miugks_status refresh_invD(miugks_solver* s)
+{
+    for (int l = 0; l < s->L; ++l)
+        CK(launch_adjoint_invD(s->lev[l].dev, s->vel, s->adj.lv[l].itau, s->adj.lv[l].invD, s->st));
+    return MIUGKS_OK;
+}
+
+AdjSweepArgs lvl_args(miugks_solver* s, int l, const double* r, double* out)
+{
+    auto& V = s->adj.lv[l];
+    return AdjSweepArgs{s->lev[l].dev, s->vel, s->bc, s->Cw, s->Zw, V.itau, V.invD, r, V.T[5], out};
+}
+
+// out = S^T r and y = A^T x on level l
+miugks_status sweep_T(miugks_solver* s, int l, const double* r, double* out)
+{
+    CK(launch_adjoint_sgs(lvl_args(s, l, r, out), s->st));
+    return MIUGKS_OK;
+}
+miugks_status apply_AT(miugks_solver* s, int l, const double* x, double* y)
+{
+    CK(launch_adjoint_apply(lvl_args(s, l, nullptr, nullptr), x, y, s->st));
+    return MIUGKS_OK;
+}
+// t <- E^T t = t - S^T (A^T t), with work vectors a, b
+miugks_status step_ET(miugks_solver* s, int l, double* t, double* a, double* b)
+{
+    const size_t n = 2 * (size_t)s->lev[l].nc * s->nv;
+    ST(apply_AT(s, l, t, a));
+    ST(sweep_T(s, l, a, b));
+    CK(launch_axpy(t, b, -1.0, n, s->st));
+    return MIUGKS_OK;
+}
+
+// out = M_l^T z, M_l the CS cycle of level l (Eq. CSCYC) as a linear map of its
+// residual: M_l = sum_{m<nu1} S E^m + P M_{l+1} R E^nu1 + sum_{m<nu2} S E^m G E^nu1
+// with E = I - A S and G = I - A P M_{l+1} R; on the coarsest level
+// M = sum_{m<nc} S E^m.  Transposed with E^T = I - S^T A^T:
+//   M_l^T z = sum_{m<nu1} (E^T)^m S^T z + (E^T)^nu1 [u + R^T M_{l+1}^T P^T (z - A^T u)],
+//   u = sum_{m<nu2} (E^T)^m S^T z.
+miugks_status cs_T(miugks_solver* s, int l, const double* z, double* out)
+{
+    auto& V = s->adj.lv[l];
+    const size_t n = 2 * (size_t)s->lev[l].nc * s->nv, nb = n * sizeof(double);
+    double **T = V.T;
+    const bool coarsest = l == s->L - 1;
+    if (coarsest) {
+        const int nsm = s->L == 1 ? 1 : s->opts.nu_coarse;
+        ST(sweep_T(s, l, z, T[0]));
+        CK(cudaMemcpyAsync(out, T[0], nb, cudaMemcpyDeviceToDevice, s->st));
+        for (int m = 1; m < nsm; ++m) {
+            ST(step_ET(s, l, T[0], T[2], T[3]));
+            CK(launch_axpy(out, T[0], 1.0, n, s->st));
+        }
+        return MIUGKS_OK;
+    }
+    HLevel& F = s->lev[l];
+    HLevel& C = s->lev[l + 1];
+    auto& Vc = s->adj.lv[l + 1];
+    ST(sweep_T(s, l, z, T[0]));                                   // s0 = S^T z
+    CK(cudaMemcpyAsync(T[1], T[0], nb, cudaMemcpyDeviceToDevice, s->st));
+    CK(cudaMemcpyAsync(T[2], T[0], nb, cudaMemcpyDeviceToDevice, s->st));
+    for (int m = 1; m < s->opts.nu2; ++m) {                        // u = sum_{m<nu2} (E^T)^m s0
+        ST(step_ET(s, l, T[2], T[3], T[4]));
+        CK(launch_axpy(T[1], T[2], 1.0, n, s->st));
+    }
+    ST(apply_AT(s, l, T[1], T[2]));                               // w = z - A^T u
+    CK(launch_sub(T[2], z, T[2], n, s->st));
+    CK(launch_adjoint_prolong_t(F.dev, C.dev, s->nv, V.pptr, V.pcell, V.pw, T[2], Vc.z, s->st));
+    ST(cs_T(s, l + 1, Vc.z, Vc.o));
+    CK(launch_adjoint_restrict_t(F.dev, C.dev, s->nv, Vc.o, T[3], s->st));
+    CK(launch_axpy(T[1], T[3], 1.0, n, s->st));                   // v = u + R^T M^T P^T w
+    CK(cudaMemcpyAsync(out, T[0], nb, cudaMemcpyDeviceToDevice, s->st));
+    CK(cudaMemcpyAsync(T[2], T[0], nb, cudaMemcpyDeviceToDevice, s->st));
+    for (int m = 1; m < s->opts.nu1; ++m) {                        // sum_{m<nu1} (E^T)^m s0
+        ST(step_ET(s, l, T[2], T[3], T[4]));
+        CK(launch_axpy(out, T[2], 1.0, n, s->st));
+    }
+    for (int m = 0; m < s->opts.nu1; ++m) ST(step_ET(s, l, T[1], T[3], T[4]));   // (E^T)^nu1 v
+    CK(launch_axpy(out, T[1], 1.0, n, s->st));
     return MIUGKS_OK;
 }
 
@@ -1154,11 +1301,11 @@ miugks_status apply_B(miugks_solver* s, const double* v, double* out, double mm)
     return MIUGKS_OK;
 }
 
+// preconditioner of the adjoint solve: the transposed CS cycle of the solver's
+// own multigrid (one transposed LU-SGS pass on a single grid)
 miugks_status apply_PT(miugks_solver* s, const double* r, double* out)
 {
-    AdjSweepArgs S{s->lev[0].dev, s->vel, s->bc, s->Cw, s->Zw, s->adj.itau, r, s->adj.t, out};
-    CK(launch_adjoint_sgs(S, s->st));
-    return MIUGKS_OK;
+    return cs_T(s, 0, r, out);
 }
 
 miugks_status wall_face_list(miugks_solver* s, int bc, int* nfaces)
@@ -1227,8 +1374,30 @@ miugks_status miugks_stage_sgs_micro_transposed(miugks_solver* s, const double* 
     const size_t n = 2 * (size_t)L0.nc * s->nv;
     CK(cudaMemcpyAsync(s->adj.itau, inv_tau, L0.nc * sizeof(double), cudaMemcpyHostToDevice, s->st));
     CK(cudaMemcpyAsync(s->adj.b, r, n * sizeof(double), cudaMemcpyHostToDevice, s->st));
-    ST(apply_PT(s, s->adj.b, s->adj.x));
+    ST(refresh_invD(s));
+    ST(sweep_T(s, 0, s->adj.b, s->adj.x));
     CK(cudaMemcpyAsync(x, s->adj.x, n * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    return MIUGKS_OK;
+}
+
+miugks_status miugks_stage_cs_transposed(miugks_solver* s, const double* inv_tau, const double* z, double* out)
+{
+    if (!s || !inv_tau || !z || !out) return MIUGKS_EINVAL;
+    if (!s->initialised) return fail(s, MIUGKS_ESTATE, "stage before init");
+    if (s->nv > kMaxAdjNv) return fail(s, MIUGKS_EINVAL, "adjoint supports at most %d velocities", kMaxAdjNv);
+    ST(adj_prepare(s, 0));
+    size_t off = 0;
+    for (int l = 0; l < s->L; ++l) {
+        CK(cudaMemcpyAsync(s->adj.lv[l].itau, inv_tau + off, s->lev[l].nc * sizeof(double), cudaMemcpyHostToDevice,
+                           s->st));
+        off += s->lev[l].nc;
+    }
+    ST(refresh_invD(s));
+    const size_t n = 2 * (size_t)s->lev[0].nc * s->nv;
+    CK(cudaMemcpyAsync(s->adj.b, z, n * sizeof(double), cudaMemcpyHostToDevice, s->st));
+    ST(cs_T(s, 0, s->adj.b, s->adj.x));
+    CK(cudaMemcpyAsync(out, s->adj.x, n * sizeof(double), cudaMemcpyDeviceToHost, s->st));
     CK(cudaStreamSynchronize(s->st));
     return MIUGKS_OK;
 }

@@ -85,6 +85,7 @@ def load():
         "miugks_set_timing": [vp, _i], "miugks_kernel_times": [vp, _P(_d), _P(_d), _P(_d)],
         "miugks_step_async": [vp, _i], "miugks_wait": [vp, vp],
         "miugks_stage_adjoint_residual": [vp, vp, vp], "miugks_stage_sgs_micro_transposed": [vp, vp, vp, vp],
+        "miugks_stage_cs_transposed": [vp, vp, vp, vp],
         "miugks_objective": [vp, _i, _i, vp, vp, vp],
         "miugks_adjoint": [vp, _i, _i, _i, _d, _i, _i, vp, vp],
         "miugks_save": [vp, ctypes.c_char_p], "miugks_load": [vp, ctypes.c_char_p],
@@ -109,7 +110,8 @@ def exported_symbols():
             "miugks_stage_sgs_micro", "miugks_stage_apply_micro", "miugks_stage_sgs_macro",
             "miugks_stage_resid_macro", "miugks_stage_restrict", "miugks_stage_prolong", "miugks_sizes",
             "miugks_set_timing", "miugks_kernel_times", "miugks_step_async", "miugks_wait",
-            "miugks_stage_adjoint_residual", "miugks_stage_sgs_micro_transposed", "miugks_objective",
+            "miugks_stage_adjoint_residual", "miugks_stage_sgs_micro_transposed", "miugks_stage_cs_transposed",
+            "miugks_objective",
             "miugks_adjoint", "miugks_residual_rms_noalloc", "miugks_save", "miugks_load",
             "miugks_macro_sweep_times"]
 
@@ -344,6 +346,14 @@ class Solver:
         x = np.zeros_like(r)
         self._check(self._lib.miugks_stage_sgs_micro_transposed(self.h, _ptr(it), _ptr(r), _ptr(x)))
         return x
+
+    def cs_cycle_transposed(self, inv_tau_levels, z):
+        """M^T z, M one CS cycle with frozen per-level collision frequencies."""
+        it = np.ascontiguousarray(np.concatenate([np.ravel(a) for a in inv_tau_levels]), dtype=np.float64)
+        z = np.ascontiguousarray(z, dtype=np.float64)
+        out = np.zeros_like(z)
+        self._check(self._lib.miugks_stage_cs_transposed(self.h, _ptr(it), _ptr(z), _ptr(out)))
+        return out
 
     def objective(self, obj, bc):
         """J, dJ/df and dJ/d(T, u, v) of wall `bc` at the current f."""

@@ -206,3 +206,24 @@ def test_torch_autograd_wall_objective(lib):
     ref, _ = s.adjoint(1, 0, 0, tol=1e-12, max_iter=3000)
     assert float(theta.grad) == pytest.approx(ref, rel=1e-8)
     assert float(J) == pytest.approx(s.objective(1, 0)[0], rel=1e-12)
+
+
+@pytest.mark.parametrize("levels", [2, 3])
+def test_transposed_cs_cycle_is_the_transpose_of_the_oracle_cycle(lib, levels):
+    """The adjoint's preconditioner is the exact transpose of one CS cycle
+    (frozen coefficients) of the forward solve."""
+    n = 4 if levels == 2 else 8
+    nvel = 6 if levels == 2 else 4
+    case = wl.cavity(n=n, nvel=nvel, kn=0.5, lid=0.2, levels=levels, nx=n, ny=n)
+    o, g, rng = _pair(lib, case, 9)
+    its = [rng.uniform(0.5, 3.0, size=(n // 2 ** l) ** 2) for l in range(levels)]
+    N = 2 * o.nc * o.nv
+    M = np.zeros((N, N))
+    e = np.zeros(N)
+    for i in range(N):
+        e[i] = 1.0
+        M[:, i] = o.cs_cycle(its, e.reshape(2, o.nc, o.nv)).ravel()
+        e[i] = 0.0
+    for _ in range(2):
+        z = rng.normal(size=(2, o.nc, o.nv))
+        assert rel(g.cs_cycle_transposed(its, z), (M.T @ z.ravel()).reshape(z.shape)) < TOL, levels
