@@ -25,6 +25,7 @@ namespace {
 
 constexpr int kRed = 32;   // shared reduction slots per value (one per warp)
 constexpr size_t kAdjCacheBytes = 160 * 1024;   // dynamic shared memory of the cached face kernel (at most)
+constexpr int kAdjKc = 16;                        // velocities per CTA of the transposed wavefront
 
 // time integrals q_m(dt, tau) of the UGKS integral solution and their tau
 // derivatives: closed form for x = dt/tau >= 1, power series below
@@ -305,28 +306,40 @@ __global__ void __launch_bounds__(256) k_adj_face(AdjDev A, int axis, const doub
         W0[3] += w * (0.5 * (u * u + v * v) * f0g + f0h);
     }
     red_sum<4>(W0, red);
-    double rho0, U0, V0, lam0;
-    adj_prim(W0, rho0, U0, V0, lam0);
-    const double T0 = 1.0 / lam0;
-    const double tau0 = A.gas.mu_ref * pow(T0, A.gas.omega) / (0.5 * rho0 * T0);
-    const double dt = A.cfl * fmin(g.wL, g.wR) / (axis == 0 ? Vg.umax : Vg.vmax);
-    const double* WL = A.W + 4 * (size_t)g.cL;
-    const double* WR = A.W + 4 * (size_t)g.cR;
+    // Face scalars are computed by thread 0 and broadcast through shared memory
+    // (an FP64 division or series costs the SM as much for one lane as for 32).
+    __shared__ double sc[32];
+    double rho0, U0, V0, lam0, tau0 = 0, dt = 0, xi;
     double dwl[4], dwr[4], aL[4], aR[4];
-    for (int m = 0; m < 4; ++m) {
-        dwl[m] = (W0[m] - WL[m]) / g.hL / rho0;
-        dwr[m] = (WR[m] - W0[m]) / g.hR / rho0;
+    if (tid == 0) {
+        adj_prim(W0, rho0, U0, V0, lam0);
+        const double T0 = 1.0 / lam0;
+        tau0 = A.gas.mu_ref * pow(T0, A.gas.omega) / (0.5 * rho0 * T0);
+        dt = A.cfl * fmin(g.wL, g.wR) / (axis == 0 ? Vg.umax : Vg.vmax);
+        const double* WL = A.W + 4 * (size_t)g.cL;
+        const double* WR = A.W + 4 * (size_t)g.cR;
+        for (int m = 0; m < 4; ++m) {
+            dwl[m] = (W0[m] - WL[m]) / g.hL / rho0;
+            dwr[m] = (WR[m] - W0[m]) / g.hR / rho0;
+        }
+        adj_slope(dwl, U0, V0, lam0, aL);
+        adj_slope(dwr, U0, V0, lam0, aR);
+        sc[0] = rho0; sc[1] = U0; sc[2] = V0; sc[3] = lam0; sc[4] = tau0; sc[5] = dt;
+        for (int m = 0; m < 4; ++m) { sc[6 + m] = aL[m]; sc[10 + m] = aR[m]; }
+        sc[14] = kKint * (kKint + 2.0) / (16.0 * lam0 * lam0);
+        sc[15] = rho0 * lam0 / kPi; sc[16] = kKint / (4.0 * lam0); sc[17] = 1.0 / dt;
     }
-    adj_slope(dwl, U0, V0, lam0, aL);
-    adj_slope(dwr, U0, V0, lam0, aR);
-    const double xi = kKint * (kKint + 2.0) / (16.0 * lam0 * lam0);
+    __syncthreads();
+    rho0 = sc[0]; U0 = sc[1]; V0 = sc[2]; lam0 = sc[3];
+    for (int m = 0; m < 4; ++m) { aL[m] = sc[6 + m]; aR[m] = sc[10 + m]; }
+    xi = sc[14];
     // separable equilibrium: gM(k) = rho0 lam0/pi Eu[a] Ev[b] (nu + nvv exponentials per face)
     for (int e = tid; e < Vg.nu + Vg.nvv; e += bs) {
         double dlt = e < Vg.nu ? Vg.ua[e] - U0 : Vg.vb[e - Vg.nu] - V0;
         etab[e] = exp(-lam0 * dlt * dlt);
     }
     __syncthreads();
-    const double gnorm = rho0 * lam0 / kPi, hfac = kKint / (4.0 * lam0), idt = 1.0 / dt;
+    const double gnorm = sc[15], hfac = sc[16], idt = sc[17];
     auto gM_of = [&](int k) -> double { int a = k / Vg.nvv; return gnorm * etab[a] * etab[Vg.nu + k - a * Vg.nvv]; };
     // ---- forward pass B: heat flux of f0 and compatibility moments
     double s6[6] = {0, 0, 0, 0, 0, 0};
@@ -348,12 +361,19 @@ __global__ void __launch_bounds__(256) k_adj_face(AdjDev A, int axis, const doub
     red_sum<6>(s6, red);
     const double q0[2] = {s6[0], s6[1]};
     const double Mt[4] = {s6[2], s6[3], s6[4], s6[5]};
-    double dwt[4], At[4];
-    for (int m = 0; m < 4; ++m) dwt[m] = -Mt[m] / rho0;
-    adj_slope(dwt, U0, V0, lam0, At);
-    double qc[5], dqc[5];
-    adj_time_coeffs(dt, tau0, qc, dqc);
-    const double shk = (1.0 - A.gas.pr) * 4.0 * lam0 * lam0 / (5.0 * rho0);
+    double dwt[4], At[4], qc[5], dqc[5];
+    if (tid == 0) {
+        for (int m = 0; m < 4; ++m) dwt[m] = -Mt[m] / rho0;
+        adj_slope(dwt, U0, V0, lam0, At);
+        adj_time_coeffs(dt, tau0, qc, dqc);
+        for (int m = 0; m < 4; ++m) sc[18 + m] = At[m];
+        for (int m = 0; m < 5; ++m) sc[22 + m] = qc[m];
+        sc[27] = (1.0 - A.gas.pr) * 4.0 * lam0 * lam0 / (5.0 * rho0);
+    }
+    __syncthreads();
+    for (int m = 0; m < 4; ++m) At[m] = sc[18 + m];
+    for (int m = 0; m < 5; ++m) qc[m] = sc[22 + m];
+    const double shk = sc[27];
 
     // ---- reverse pass C: the flux assembly
     // r[0..4] qc adjoint, [5..8] aL, [9..12] aR, [13..16] A, [17] rho, [18] U, [19] V, [20] lam,
@@ -404,19 +424,25 @@ __global__ void __launch_bounds__(256) k_adj_face(AdjDev A, int axis, const doub
     double aLb[4] = {r[5], r[6], r[7], r[8]}, aRb[4] = {r[9], r[10], r[11], r[12]};
     double rb = r[17], Ub = r[18], Vb = r[19], lb = r[20], xib = r[22];
     const double q0b[2] = {r[23], r[24]};
-    lb += r[21] * 2.0 * shk / lam0;
-    rb -= r[21] * shk / rho0;
-    double dwtb[4] = {0, 0, 0, 0};
-    adj_slope_rev(dwt, U0, V0, lam0, r + 13, dwtb, Ub, Vb, lb);
     double Mtb[4];
-    for (int m = 0; m < 4; ++m) {
-        Mtb[m] = -dwtb[m] / rho0;
-        rb += dwtb[m] * Mt[m] / (rho0 * rho0);
+    __shared__ double sM[4];
+    if (tid == 0) {
+        lb += r[21] * 2.0 * shk / lam0;
+        rb -= r[21] * shk / rho0;
+        double dwtb[4] = {0, 0, 0, 0};
+        adj_slope_rev(dwt, U0, V0, lam0, r + 13, dwtb, Ub, Vb, lb);
+        for (int m = 0; m < 4; ++m) {
+            Mtb[m] = -dwtb[m] / rho0;
+            rb += dwtb[m] * Mt[m] / (rho0 * rho0);
+            sM[m] = Mtb[m];
+        }
+        double taub = 0.0;
+        for (int m = 0; m < 5; ++m) taub += r[m] * dqc[m];
+        rb -= taub * tau0 / rho0;
+        lb += taub * tau0 * (1.0 - A.gas.omega) / lam0;
     }
-    double taub = 0.0;
-    for (int m = 0; m < 5; ++m) taub += r[m] * dqc[m];
-    rb -= taub * tau0 / rho0;
-    lb += taub * tau0 * (1.0 - A.gas.omega) / lam0;
+    __syncthreads();
+    for (int m = 0; m < 4; ++m) Mtb[m] = sM[m];
 
     // ---- reverse pass D: heat flux and compatibility moments
     double t[13];
@@ -439,13 +465,13 @@ __global__ void __launch_bounds__(256) k_adj_face(AdjDev A, int axis, const doub
         t[10] -= w * (q0b[1] * (E + cy * cy * f0g) + q0b[0] * cx * cy * f0g);
     }
     red_sum<13>(t, red);
-    for (int m = 0; m < 4; ++m) { aLb[m] += t[m]; aRb[m] += t[4 + m]; }
-    rb += t[8]; Ub += t[9]; Vb += t[10]; lb += t[11]; xib += t[12];
-    lb += xib * (-2.0 * xi / lam0);
-    double dwlb[4] = {0, 0, 0, 0}, dwrb[4] = {0, 0, 0, 0};
-    adj_slope_rev(dwl, U0, V0, lam0, aLb, dwlb, Ub, Vb, lb);
-    adj_slope_rev(dwr, U0, V0, lam0, aRb, dwrb, Ub, Vb, lb);
     if (tid == 0) {
+        for (int m = 0; m < 4; ++m) { aLb[m] += t[m]; aRb[m] += t[4 + m]; }
+        rb += t[8]; Ub += t[9]; Vb += t[10]; lb += t[11]; xib += t[12];
+        lb += xib * (-2.0 * xi / lam0);
+        double dwlb[4] = {0, 0, 0, 0}, dwrb[4] = {0, 0, 0, 0};
+        adj_slope_rev(dwl, U0, V0, lam0, aLb, dwlb, Ub, Vb, lb);
+        adj_slope_rev(dwr, U0, V0, lam0, aRb, dwrb, Ub, Vb, lb);
         double W0b[4] = {0, 0, 0, 0};
         for (int m = 0; m < 4; ++m) {
             W0b[m] += dwlb[m] / (g.hL * rho0) - dwrb[m] / (g.hR * rho0);
@@ -683,19 +709,15 @@ __global__ void __launch_bounds__(128) k_adj_gather(AdjDev A, const double* __re
 // transposed couplings of the cell's upper boundary faces); pass 1 solves
 // (D + L'^T) x = D y in descending order.  One CTA per cell of one
 // anti-diagonal; one launch per diagonal.
-__global__ void __launch_bounds__(256) k_adjT_sweep(AdjSweepArgs S, int pass, int d)
+// one cell (i, j) of a transposed pass, all velocities, by the whole CTA
+// (ys: 2 nv doubles of shared memory, red: 4 kRed doubles)
+__device__ void adjT_cell(const AdjSweepArgs& S, int pass, int i, int j, double* ys, double* red)
 {
-    extern __shared__ double ys[];              // [2][nv] iterate of the boundary-block solve
-    __shared__ double red[kRed * 4];
     const LevelDev& L = S.L;
     const VelDev& Vg = S.V;
     const int nx = L.nx, ny = L.ny, nv = Vg.nv, tid = threadIdx.x, bs = blockDim.x;
     const size_t nc = L.nc, snv = nv;
-    const int ilo = d - (ny - 1) > 0 ? d - (ny - 1) : 0;
-    const int ihi = d < nx - 1 ? d : nx - 1;
-    const int i = pass == 0 ? ilo + (int)blockIdx.x : ihi - (int)blockIdx.x;
-    if (i < ilo || i > ihi) return;
-    const int j = d - i, c = j * nx + i;
+    const int c = j * nx + i;
     const double rdx = 1.0 / L.dx[i], rdy = 1.0 / L.dy[j];
     const double it = S.inv_tau[c];
     double* dst = pass == 0 ? S.y : S.x;
@@ -795,6 +817,40 @@ __global__ void __launch_bounds__(256) k_adjT_sweep(AdjSweepArgs S, int pass, in
         }
         return;
     }
+    if (nb == 1 && nwall == 1) {
+        // incoming rows have no coupling; the outgoing G rows need their sum
+        double acc[4] = {0, 0, 0, 0};
+        for (int k = tid; k < nv; k += bs) {
+            double Dbk = Db(0, k);
+            if (Dbk != 0.0)
+                acc[0] += Dbk * S.Cw[(size_t)bid[0] * nv + k] * (base_of(0, k) + Hf[0] * base_of(1, k)) * rden_of(k);
+        }
+        red_sum<4>(acc, red);
+        for (int k = tid; k < nv; k += bs) {
+            double rd = rden_of(k), g0 = base_of(0, k);
+            double uo = bos[0] * (bax[0] == 0 ? Vg.u[k] : Vg.v[k]);
+            if (uo > 0) g0 += Vg.w[k] * uo / Z[0] * acc[0];
+            dst[(size_t)c * snv + k] = g0 * rd;
+            dst[(nc + c) * snv + k] = base_of(1, k) * rd;
+        }
+        return;
+    }
+    if (nb == 1 && nsym == 1) {
+        // the outgoing rows take the mirrored incoming values, which have no coupling
+        for (int k = tid; k < nv; k += bs) {
+            double rd = rden_of(k), g0 = base_of(0, k), g1 = base_of(1, k);
+            double uo = bos[0] * (bax[0] == 0 ? Vg.u[k] : Vg.v[k]);
+            if (uo > 0) {
+                int km = mirror(0, k);
+                double Dm = Db(0, km), rm = rden_of(km);
+                g0 -= Dm * base_of(0, km) * rm;
+                g1 -= Dm * base_of(1, km) * rm;
+            }
+            dst[(size_t)c * snv + k] = g0 * rd;
+            dst[(nc + c) * snv + k] = g1 * rd;
+        }
+        return;
+    }
     // three substitution rounds (exact: the coupling is nilpotent of the same
     // degree as in the untransposed block)
     for (int k = tid; k < nv; k += bs) {
@@ -832,6 +888,68 @@ __global__ void __launch_bounds__(256) k_adjT_sweep(AdjSweepArgs S, int pass, in
         for (int k = tid; k < nv; k += bs) {
             ys[k] = dst[(size_t)c * snv + k];
             ys[nv + k] = dst[(nc + c) * snv + k];
+        }
+        __syncthreads();
+    }
+}
+
+// The boundary lines on the side of a pass are sinks of its order: pass 0
+// (ascending, upper boundary blocks) the last row then the last column, pass 1
+// (descending, lower blocks) the first row then the first column.  One CTA
+// walks them in that order, one cell at a time.
+__global__ void __launch_bounds__(256) k_adjT_chain(AdjSweepArgs S, int pass)
+{
+    extern __shared__ double ys[];
+    __shared__ double red[kRed * 4];
+    const int nx = S.L.nx, ny = S.L.ny;
+    if (pass == 0) {
+        for (int i = 0; i < nx - 1; ++i) { adjT_cell(S, 0, i, ny - 1, ys, red); __syncthreads(); }
+        for (int j = 0; j < ny; ++j) { adjT_cell(S, 0, nx - 1, j, ys, red); __syncthreads(); }
+    } else {
+        for (int i = nx - 1; i >= 1; --i) { adjT_cell(S, 1, i, 0, ys, red); __syncthreads(); }
+        for (int j = ny - 1; j >= 0; --j) { adjT_cell(S, 1, 0, j, ys, red); __syncthreads(); }
+    }
+}
+
+// Every other cell of a pass has no boundary face on its side: a plain
+// triangular solve along anti-diagonals, independent per velocity.  Each CTA
+// owns kAdjKc consecutive velocities and sweeps all those cells diagonal by
+// diagonal with only block barriers between diagonals.
+__global__ void __launch_bounds__(128) k_adjT_wave(AdjSweepArgs S, int pass)
+{
+    const LevelDev& L = S.L;
+    const VelDev& Vg = S.V;
+    const int nx = L.nx, ny = L.ny, nv = Vg.nv;
+    const size_t nc = L.nc, snv = nv;
+    const int k0 = blockIdx.x * kAdjKc;
+    // interior block: pass 0 i <= nx-2, j <= ny-2; pass 1 i >= 1, j >= 1
+    const int mx = nx - 1, my = ny - 1;                 // its extent
+    if (mx <= 0 || my <= 0) return;
+    const int nd = mx + my - 1;
+    for (int t = 0; t < nd; ++t) {
+        const int dd = pass == 0 ? t : nd - 1 - t;      // diagonal within the block
+        const int ilo = dd - (my - 1) > 0 ? dd - (my - 1) : 0, ihi = dd < mx - 1 ? dd : mx - 1;
+        const int m = ihi - ilo + 1;
+        for (int q = threadIdx.x; q < m * kAdjKc; q += blockDim.x) {
+            const int kk = q % kAdjKc, k = k0 + kk;
+            if (k >= nv) continue;
+            const int bi = ilo + q / kAdjKc, bj = dd - bi;
+            const int i = pass == 0 ? bi : bi + 1, j = pass == 0 ? bj : bj + 1, c = j * nx + i;
+            const double u = Vg.u[k], v = Vg.v[k], rD = S.invD[(size_t)c * snv + k];
+            for (int cp = 0; cp < 2; ++cp) {
+                const size_t e = (cp * nc + c) * snv + k;
+                if (pass == 0) {
+                    double b = S.r[e];
+                    if (u < 0 && i > 0 && L.fbx[j * (nx + 1) + i] < 0) b -= u * L.rdx[i - 1] * S.y[e - snv];
+                    if (v < 0 && j > 0 && L.fby[j * nx + i] < 0) b -= v * L.rdy[j - 1] * S.y[e - (size_t)nx * snv];
+                    S.y[e] = b * rD;
+                } else {
+                    double b = 0.0;
+                    if (u > 0 && L.fbx[j * (nx + 1) + i + 1] < 0) b += u * L.rdx[i + 1] * S.x[e + snv];
+                    if (v > 0 && L.fby[(j + 1) * nx + i] < 0) b += v * L.rdy[j + 1] * S.x[e + (size_t)nx * snv];
+                    S.x[e] = S.y[e] + b * rD;
+                }
+            }
         }
         __syncthreads();
     }
@@ -1172,18 +1290,16 @@ cudaError_t launch_adjoint_residual(const AdjDev& A, const double* mu, double* r
 
 cudaError_t launch_adjoint_sgs(const AdjSweepArgs& S, cudaStream_t st)
 {
-    const int nx = S.L.nx, ny = S.L.ny, nd = nx + ny - 1;
     const size_t smem = 2 * (size_t)S.V.nv * sizeof(double);
     if (S.V.nv > kMaxAdjNv) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(k_adjT_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_adjT_chain, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          2 * kMaxAdjNv * (int)sizeof(double));
     if (e != cudaSuccess) return e;
-    for (int pass = 0; pass < 2; ++pass)
-        for (int t = 0; t < nd; ++t) {
-            int d = pass == 0 ? t : nd - 1 - t;
-            int ilo = d - (ny - 1) > 0 ? d - (ny - 1) : 0, ihi = d < nx - 1 ? d : nx - 1;
-            k_adjT_sweep<<<ihi - ilo + 1, 256, smem, st>>>(S, pass, d);
-        }
+    const int nblk = (S.V.nv + kAdjKc - 1) / kAdjKc;
+    for (int pass = 0; pass < 2; ++pass) {
+        k_adjT_wave<<<nblk, 128, 0, st>>>(S, pass);
+        k_adjT_chain<<<1, 256, smem, st>>>(S, pass);
+    }
     return cudaGetLastError();
 }
 
