@@ -25,7 +25,7 @@ namespace {
 
 constexpr int kRed = 32;   // shared reduction slots per value (one per warp)
 constexpr size_t kAdjCacheBytes = 160 * 1024;   // dynamic shared memory of the cached face kernel (at most)
-constexpr int kAdjKc = 16;                        // velocities per CTA of the transposed wavefront
+constexpr int kAdjKc = 4;                         // velocities per CTA of the transposed wavefront
 
 // time integrals q_m(dt, tau) of the UGKS integral solution and their tau
 // derivatives: closed form for x = dt/tau >= 1, power series below
@@ -894,20 +894,27 @@ __device__ void adjT_cell(const AdjSweepArgs& S, int pass, int i, int j, double*
 }
 
 // The boundary lines on the side of a pass are sinks of its order: pass 0
-// (ascending, upper boundary blocks) the last row then the last column, pass 1
-// (descending, lower blocks) the first row then the first column.  One CTA
-// walks them in that order, one cell at a time.
-__global__ void __launch_bounds__(256) k_adjT_chain(AdjSweepArgs S, int pass)
+// (ascending, upper boundary blocks) the last row and the last column, pass 1
+// (descending, lower blocks) the first row and the first column.  They depend
+// on each other only through the corner cell they share: CTA 0 walks the row,
+// CTA 1 the column without the corner, one cell at a time; the corner follows
+// in a launch of its own (corner = 1).
+__global__ void __launch_bounds__(512) k_adjT_chain(AdjSweepArgs S, int pass, int corner)
 {
     extern __shared__ double ys[];
     __shared__ double red[kRed * 4];
     const int nx = S.L.nx, ny = S.L.ny;
+    if (corner) {
+        if (pass == 0) adjT_cell(S, 0, nx - 1, ny - 1, ys, red);
+        else adjT_cell(S, 1, 0, 0, ys, red);
+        return;
+    }
     if (pass == 0) {
-        for (int i = 0; i < nx - 1; ++i) { adjT_cell(S, 0, i, ny - 1, ys, red); __syncthreads(); }
-        for (int j = 0; j < ny; ++j) { adjT_cell(S, 0, nx - 1, j, ys, red); __syncthreads(); }
+        if (blockIdx.x == 0) for (int i = 0; i < nx - 1; ++i) { adjT_cell(S, 0, i, ny - 1, ys, red); __syncthreads(); }
+        else for (int j = 0; j < ny - 1; ++j) { adjT_cell(S, 0, nx - 1, j, ys, red); __syncthreads(); }
     } else {
-        for (int i = nx - 1; i >= 1; --i) { adjT_cell(S, 1, i, 0, ys, red); __syncthreads(); }
-        for (int j = ny - 1; j >= 0; --j) { adjT_cell(S, 1, 0, j, ys, red); __syncthreads(); }
+        if (blockIdx.x == 0) for (int i = nx - 1; i >= 1; --i) { adjT_cell(S, 1, i, 0, ys, red); __syncthreads(); }
+        else for (int j = ny - 1; j >= 1; --j) { adjT_cell(S, 1, 0, j, ys, red); __syncthreads(); }
     }
 }
 
@@ -915,7 +922,7 @@ __global__ void __launch_bounds__(256) k_adjT_chain(AdjSweepArgs S, int pass)
 // triangular solve along anti-diagonals, independent per velocity.  Each CTA
 // owns kAdjKc consecutive velocities and sweeps all those cells diagonal by
 // diagonal with only block barriers between diagonals.
-__global__ void __launch_bounds__(128) k_adjT_wave(AdjSweepArgs S, int pass)
+__global__ void __launch_bounds__(256) k_adjT_wave(AdjSweepArgs S, int pass)
 {
     const LevelDev& L = S.L;
     const VelDev& Vg = S.V;
@@ -1297,8 +1304,9 @@ cudaError_t launch_adjoint_sgs(const AdjSweepArgs& S, cudaStream_t st)
     if (e != cudaSuccess) return e;
     const int nblk = (S.V.nv + kAdjKc - 1) / kAdjKc;
     for (int pass = 0; pass < 2; ++pass) {
-        k_adjT_wave<<<nblk, 128, 0, st>>>(S, pass);
-        k_adjT_chain<<<1, 256, smem, st>>>(S, pass);
+        k_adjT_wave<<<nblk, 256, 0, st>>>(S, pass);
+        k_adjT_chain<<<2, 512, smem, st>>>(S, pass, 0);
+        k_adjT_chain<<<1, 512, smem, st>>>(S, pass, 1);
     }
     return cudaGetLastError();
 }
