@@ -227,3 +227,23 @@ def test_transposed_cs_cycle_is_the_transpose_of_the_oracle_cycle(lib, levels):
     for _ in range(2):
         z = rng.normal(size=(2, o.nc, o.nv))
         assert rel(g.cs_cycle_transposed(its, z), (M.T @ z.ravel()).reshape(z.shape)) < TOL, levels
+
+
+def test_flat_plate_drag_gradient_matches_oracle(lib):
+    """Half-domain flat plate (wall on part of the lower edge, symmetry on the
+    rest, farfield elsewhere; stretched mesh): d(drag)/d(plate wall
+    temperature) and d(drag)/d(plate velocity) at the converged state."""
+    case = wl.flat_plate(kn=0.5, ma=0.2, nvel=16, vmax=5.0, levels=1, n_up=1, n_plate=2, n_down=1, ny=3,
+                         growth=1.3)
+    o = oracle.Oracle(case)
+    o.init_uniform(case["init"]["rho"], case["init"]["u"], case["init"]["v"], case["init"]["t"])
+    o.step(300)
+    g = lib.Solver(case)
+    g.init_uniform(case["init"]["rho"], case["init"]["u"], case["init"]["v"], case["init"]["t"])
+    g.set_f(o.get_f())
+    A = oracle.adjoint_matrix(o)
+    for obj, param in ((0, 0), (0, 1), (1, 0)):
+        go, _ = oracle.adjoint_gradient(o, obj, 0, param, A=A)
+        gg, info = g.adjoint(obj, 0, param, tol=1e-13, max_iter=3000)
+        assert info["converged"], info
+        assert gg == pytest.approx(go, rel=1e-8, abs=1e-12), (obj, param, info)
