@@ -141,9 +141,11 @@ def oracle_iterations_per_s(n_iter):
 
 def run_reference(args):
     rank, world = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
-    plate = None
+    plate = series = None
     if not args.no_plate and rank == 0:
         plate = measure_plate(max(5, args.steps // 5), args.warmup)
+    if not args.no_ttr and rank == 0:
+        series = kn_series()
     if rank != 0:
         return 0
     cv = NX * NY * NVEL * NVEL
@@ -301,6 +303,40 @@ def step_hbm(m, precision):
             "peak_source": hsrc}
 
 
+def kn_series(max_iter=600):
+    """The 64x64 cavity at the three Kn of its configuration (0.075, 1, 10):
+    time to RMS residual 1e-6 from rest in the FP64 and the mixed form, and the
+    mixed form's converged error against the FP64 solver (relative L-infinity of
+    density, velocity, temperature and lid-wall shear)."""
+    import torch
+    from paper_1704_03151_gb300 import miugks, workloads
+    out = []
+    for kn in (0.075, 1.0, 10.0):
+        row = {"kn": kn}
+        sol = {}
+        for prec in ("fp64", "mixed"):
+            c = workloads.cavity(n=NX, nvel=NVEL, kn=kn, lid=0.16, levels=LEVELS)
+            s = miugks.Solver(c, precision=prec)
+            s.init_uniform(1.0, 0.0, 0.0, 1.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            iters, rr, ok = s.run(1e-6, max_iter)
+            row[prec] = {"seconds": time.perf_counter() - t0, "iterations": iters, "converged": bool(ok),
+                         "residual": [float(x) for x in rr]}
+            m = s.macro()
+            sol[prec] = (m, s.wall(2)[1])
+            s.close()
+        (m64, tw64), (m32, tw32) = sol["fp64"], sol["mixed"]
+        speed = np.hypot(m64["u"], m64["v"]).max()
+        row["mixed_error"] = {
+            "rho": float(np.abs(m32["rho"] - m64["rho"]).max() / np.abs(m64["rho"]).max()),
+            "velocity": float(max(np.abs(m32["u"] - m64["u"]).max(), np.abs(m32["v"] - m64["v"]).max()) / speed),
+            "t": float(np.abs(m32["t"] - m64["t"]).max() / np.abs(m64["t"]).max()),
+            "lid_shear": float(np.abs(tw32 - tw64).max() / np.abs(tw64).max())}
+        out.append(row)
+    return out
+
+
 def measure_plate(steps, warmup):
     """The flat-plate configuration at full size (128x96 stretched cells, 48x48
     velocities on [-5,5]^2, Kn = 0.1, 4-level V-cycle, mixed form): 28.3 M cell-
@@ -343,14 +379,17 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint gradient at the converged state")
     ap.add_argument("--no-plate", action="store_true", help="skip the full-size flat-plate throughput line")
-    ap.add_argument("--workload", default="cavity64", choices=["cavity64", "kn_sweep"])
+    ap.add_argument("--workload", default="cavity64", choices=["cavity64", "kn_sweep", "adjoint"])
     ap.add_argument("--count", type=int, default=32, help="cavities of the Kn sweep")
     ap.add_argument("--max-iter", type=int, default=1500)
+    ap.add_argument("--adjoint", action="store_true", help="Kn sweep: adjoint lid-shear gradient of every case")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "kn_sweep":
         return run_kn_sweep(args)
+    if args.workload == "adjoint":
+        return run_adjoint(args)
     args.warmup = max(args.warmup, 3)
     import torch
     rank, world = dist_setup(args.gpus)
@@ -363,9 +402,11 @@ def main():
     if not args.no_fp64 and args.precision == "mixed":
         other = measure("fp64", max(3, args.steps // 3), args.warmup, world, rank, dev, with_e2e=False,
                         with_ttr=not args.no_ttr, clocks=False)
-    plate = None
+    plate = series = None
     if not args.no_plate and rank == 0:
         plate = measure_plate(max(5, args.steps // 5), args.warmup)
+    if not args.no_ttr and rank == 0:
+        series = kn_series()
     if rank != 0:
         return 0
     cv = NX * NY * NVEL * NVEL
@@ -395,6 +436,7 @@ def main():
         "time_to_residual": head.get("time_to_residual"),
         "adjoint": head.get("adjoint"),
         "flat_plate": plate,
+        "kn_series": series,
         "cpu_baseline": cpu,
     }
     if other:
@@ -408,6 +450,29 @@ def main():
     return 0
 
 
+def run_adjoint(args):
+    """The differentiation form alone: the 64x64 cavity solved in the mixed form
+    to RMS residual 1e-6 from rest, then the FP64 adjoint gradient of the
+    lid-wall shear force with respect to the lid speed (GMRES to 1e-8 or
+    --max-iter iterations)."""
+    import torch
+    from paper_1704_03151_gb300 import build, miugks
+    build.build()
+    s = miugks.Solver(case(), precision=args.precision)
+    s.init_uniform(1.0, 0.0, 0.0, 1.0)
+    iters, rr, ok = s.run(1e-6, 3000)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g, info = s.adjoint(0, 2, 1, tol=1e-8, max_iter=args.max_iter)
+    sec = time.perf_counter() - t0
+    print(json.dumps({"metric": "adjoint gradient time (d lid-wall shear / d lid speed)", "value": sec, "unit": "s",
+                      "higher_is_better": False, "config": {"workload": WORKLOAD, "forward_precision": args.precision,
+                                                             "forward_iterations": iters},
+                      "gradient": g, "gmres_iterations": info["iterations"],
+                      "relative_residual": info["residual"], "converged": info["converged"]}))
+    return 0
+
+
 def run_kn_sweep(args):
     """Kn sweep: `count` independent 96x96 cavities, 40x40 velocities, 4-level
     V-cycle, mixed form, Kn log-uniform on [0.01, 10] and lid speed uniform on
@@ -418,6 +483,21 @@ def run_kn_sweep(args):
     build.build()
     cases = workloads.kn_sweep(count=args.count)
     out = sweep.run_concurrent(cases, tol=1e-6, max_iter=args.max_iter, chunk=5, precision=args.precision)
+    adj = None
+    if args.adjoint:
+        # differentiation form per case at its converged state: d(lid-wall shear)/d(lid speed), FP64
+        # adjoint; each solver is released after its gradient so the work memory is reused
+        adj = {"objective": "lid-wall shear force", "parameter": "lid speed", "gradients": [], "seconds": [],
+               "gmres_iterations": [], "converged": []}
+        for q, s in enumerate(out["solvers"]):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g, info = s.adjoint(0, 2, 1, tol=1e-8, max_iter=800)
+            adj["seconds"].append(time.perf_counter() - t0)
+            adj["gradients"].append(g)
+            adj["gmres_iterations"].append(info["iterations"])
+            adj["converged"].append(info["converged"])
+            s.close()
     cv = 96 * 96 * 40 * 40
     total_updates = cv * sum(out["iterations"])
     line = {"metric": "Kn-sweep cell-velocity updates/s (concurrent cavities to RMS residual 1e-6)",
@@ -426,46 +506,36 @@ def run_kn_sweep(args):
             "config": {"workload": "kn_sweep_%dx_cavity96_v40_L4" % args.count, "count": args.count},
             "seconds_to_solve_all": out["seconds"], "iterations": out["iterations"],
             "converged": [max(r) < 1e-6 for r in out["residuals"]],
-            "kn": [c["gas"]["kn"] for c in cases], "lid": [c["bcs"][2]["u"] for c in cases]}
+            "kn": [c["gas"]["kn"] for c in cases], "lid": [c["bcs"][2]["u"] for c in cases], "adjoint": adj}
     print(json.dumps(line))
     return 0
 
 
 def count_launches():
-    """Kernel launches of one outer iteration of the workload (host-side count of
-    the launch sequence; every launch is one of this library's kernels)."""
-    L = LEVELS
-    nu1, nu2, nuc = 2, 1, 4
-    per_sgs_micro = 4          # chain + interior, forward and backward
-    per_renew = 1
-    # Step 1: 2 flux + 1 residual + 2 rms
-    n = 5
-    # Step 2 FAS: gamma + forcing per level, smoother launches and renewals, transfers
-    fas = 0
-    for l in range(L):
+    """Kernel launches of one outer iteration of the workload, following the
+    library's launch sequence (every launch is one of this library's kernels;
+    memsets and copies are not counted).  Matches the ncu launch list of the
+    same workload (133 per iteration for 3 levels)."""
+    L, nu1, nu2, nuc = LEVELS, 2, 1, 4
+    macro_sweep = 2            # per-diagonal record kernel + cluster sweep
+    micro_sweep = 6            # boundary-line chain, line fold and wavefront, forward and backward
+    n = 2 + 1 + 2              # Step 1: two face-flux launches, cell residual, RMS (partial + final)
+    for l in range(L):         # Step 2: FAS
         coarsest = l == L - 1
-        fas += 2
-        if coarsest:
-            fas += nuc + (nuc - 1)
-        else:
-            fas += nu1 * 2 + 2 + 1 + 1 + nu2 * 2
-    n += fas
-    # Steps 3-4: micro residual + coarse coefficients (restrict + coeffs per coarse level)
-    n += 1 + 2 * (L - 1)
-    # Step 5 CS
-    cs = 0
-    for l in range(L):
+        npre = nuc if coarsest else nu1
+        n += 2 + 1             # Gamma and inverse diagonal, forcing
+        n += npre * macro_sweep + (npre - 1 if coarsest else npre)
+        if not coarsest:
+            n += 2 + 1 + 1 + nu2 * (1 + macro_sweep)   # restrictions, difference, prolongation, post-smoothing
+    n += 1 + 2 * (L - 1)       # Steps 3-4: micro residual; per coarse level restriction + coefficients
+    for l in range(L):         # Step 5: CS
         coarsest = l == L - 1
-        cs += 0  # memset is not a kernel launch of this library
-        if coarsest:
-            cs += nuc * (per_sgs_micro + per_renew)
-        else:
-            cs += nu1 * (per_sgs_micro + per_renew) + 1 + 1 + nu2 * (per_renew + per_sgs_micro + per_renew)
-    n += cs
-    # Steps 6-7
-    n += 1
+        npre = nuc if coarsest else nu1
+        n += npre * (micro_sweep + 1)
+        if not coarsest:
+            n += 1 + 1 + nu2 * (1 + micro_sweep + 1)
+    n += 1                     # Steps 6-7
     return n
-
 
 if __name__ == "__main__":
     sys.exit(main())

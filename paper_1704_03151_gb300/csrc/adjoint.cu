@@ -718,7 +718,7 @@ __device__ void adjT_cell(const AdjSweepArgs& S, int pass, int i, int j, double*
     const int nx = L.nx, ny = L.ny, nv = Vg.nv, tid = threadIdx.x, bs = blockDim.x;
     const size_t nc = L.nc, snv = nv;
     const int c = j * nx + i;
-    const double rdx = 1.0 / L.dx[i], rdy = 1.0 / L.dy[j];
+    const double rdx = L.rdx[i], rdy = L.rdy[j];
     const double it = S.inv_tau[c];
     double* dst = pass == 0 ? S.y : S.x;
     // neighbours: pass 0 lower (west, south), pass 1 upper (east, north)
@@ -726,8 +726,8 @@ __device__ void adjT_cell(const AdjSweepArgs& S, int pass, int i, int j, double*
     const bool nS = pass == 0 && j > 0 && L.fby[j * nx + i] < 0;
     const bool nE = pass == 1 && i < nx - 1 && L.fbx[j * (nx + 1) + i + 1] < 0;
     const bool nN = pass == 1 && j < ny - 1 && L.fby[(j + 1) * nx + i] < 0;
-    const double cW = nW ? 1.0 / L.dx[i - 1] : 0.0, cS = nS ? 1.0 / L.dy[j - 1] : 0.0;
-    const double cE = nE ? 1.0 / L.dx[i + 1] : 0.0, cN = nN ? 1.0 / L.dy[j + 1] : 0.0;
+    const double cW = nW ? L.rdx[i - 1] : 0.0, cS = nS ? L.rdy[j - 1] : 0.0;
+    const double cE = nE ? L.rdx[i + 1] : 0.0, cN = nN ? L.rdy[j + 1] : 0.0;
     // boundary faces on this pass's side: pass 0 upper (east, north), pass 1 lower (west, south)
     int nb = 0, bax[2], bos[2], bid[2];
     double bS[2];
@@ -788,10 +788,13 @@ __device__ void adjT_cell(const AdjSweepArgs& S, int pass, int i, int j, double*
     }
     if (nwall == 2 && nb == 2) {
         // s_b = sum over velocities incoming at wall b of Db (C y_G + C Hf y_H);
-        // s_b = a_b + m_b s_o with o the other wall
+        // s_b = a_b + m_b s_o with o the other wall.  The right-hand sides stay
+        // in shared memory between the two loops (each thread its own entries).
         double acc[4] = {0, 0, 0, 0};
         for (int k = tid; k < nv; k += bs) {
             double rd = rden_of(k), b0 = base_of(0, k), b1 = base_of(1, k);
+            ys[k] = b0;
+            ys[nv + k] = b1;
             for (int b = 0; b < 2; ++b) {
                 double Dbk = Db(b, k);
                 if (Dbk == 0.0) continue;
@@ -807,48 +810,59 @@ __device__ void adjT_cell(const AdjSweepArgs& S, int pass, int i, int j, double*
         double s1 = acc[1] + acc[3] * s0;
         double sb[2] = {s0, s1};
         for (int k = tid; k < nv; k += bs) {
-            double rd = rden_of(k), g0 = base_of(0, k);
+            double rd = rden_of(k), g0 = ys[k];
             for (int b = 0; b < 2; ++b) {
                 double uo = bos[b] * (bax[b] == 0 ? Vg.u[k] : Vg.v[k]);
                 if (uo > 0) g0 += Vg.w[k] * uo / Z[b] * sb[b];
             }
             dst[(size_t)c * snv + k] = g0 * rd;
-            dst[(nc + c) * snv + k] = base_of(1, k) * rd;
+            dst[(nc + c) * snv + k] = ys[nv + k] * rd;
         }
+        __syncthreads();
         return;
     }
     if (nb == 1 && nwall == 1) {
         // incoming rows have no coupling; the outgoing G rows need their sum
-        double acc[4] = {0, 0, 0, 0};
+        double acc[1] = {0};
         for (int k = tid; k < nv; k += bs) {
+            double b0 = base_of(0, k), b1 = base_of(1, k);
+            ys[k] = b0;
+            ys[nv + k] = b1;
             double Dbk = Db(0, k);
-            if (Dbk != 0.0)
-                acc[0] += Dbk * S.Cw[(size_t)bid[0] * nv + k] * (base_of(0, k) + Hf[0] * base_of(1, k)) * rden_of(k);
+            if (Dbk != 0.0) acc[0] += Dbk * S.Cw[(size_t)bid[0] * nv + k] * (b0 + Hf[0] * b1) * rden_of(k);
         }
-        red_sum<4>(acc, red);
+        red_sum<1>(acc, red);
+        const double sZ = acc[0] / Z[0];
         for (int k = tid; k < nv; k += bs) {
-            double rd = rden_of(k), g0 = base_of(0, k);
+            double rd = rden_of(k), g0 = ys[k];
             double uo = bos[0] * (bax[0] == 0 ? Vg.u[k] : Vg.v[k]);
-            if (uo > 0) g0 += Vg.w[k] * uo / Z[0] * acc[0];
+            if (uo > 0) g0 += Vg.w[k] * uo * sZ;
             dst[(size_t)c * snv + k] = g0 * rd;
-            dst[(nc + c) * snv + k] = base_of(1, k) * rd;
+            dst[(nc + c) * snv + k] = ys[nv + k] * rd;
         }
+        __syncthreads();
         return;
     }
     if (nb == 1 && nsym == 1) {
         // the outgoing rows take the mirrored incoming values, which have no coupling
         for (int k = tid; k < nv; k += bs) {
-            double rd = rden_of(k), g0 = base_of(0, k), g1 = base_of(1, k);
+            ys[k] = base_of(0, k);
+            ys[nv + k] = base_of(1, k);
+        }
+        __syncthreads();
+        for (int k = tid; k < nv; k += bs) {
+            double rd = rden_of(k), g0 = ys[k], g1 = ys[nv + k];
             double uo = bos[0] * (bax[0] == 0 ? Vg.u[k] : Vg.v[k]);
             if (uo > 0) {
                 int km = mirror(0, k);
                 double Dm = Db(0, km), rm = rden_of(km);
-                g0 -= Dm * base_of(0, km) * rm;
-                g1 -= Dm * base_of(1, km) * rm;
+                g0 -= Dm * ys[km] * rm;
+                g1 -= Dm * ys[nv + km] * rm;
             }
             dst[(size_t)c * snv + k] = g0 * rd;
             dst[(nc + c) * snv + k] = g1 * rd;
         }
+        __syncthreads();
         return;
     }
     // three substitution rounds (exact: the coupling is nilpotent of the same
