@@ -305,7 +305,10 @@ def step_hbm(m, precision):
 
 def kn_series(max_iter=600):
     """The 64x64 cavity at the three Kn of its configuration (0.075, 1, 10):
-    time to RMS residual 1e-6 from rest in the FP64 and the mixed form, and the
+    time to RMS residual 1e-6 from rest in the FP64 and the mixed form (or to
+    the floor that the truncated [-4,4]^2 velocity grid sets at small Kn: the
+    discrete moments of the Maxwellian miss W by about 1e-7, which the
+    collision term divides by tau), and the
     mixed form's converged error against the FP64 solver (relative L-infinity of
     density, velocity, temperature and lid-wall shear)."""
     import torch
@@ -320,8 +323,20 @@ def kn_series(max_iter=600):
             s.init_uniform(1.0, 0.0, 0.0, 1.0)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            iters, rr, ok = s.run(1e-6, max_iter)
-            row[prec] = {"seconds": time.perf_counter() - t0, "iterations": iters, "converged": bool(ok),
+            # to RMS 1e-6, or to the discretisation floor: the residual of the truncated
+            # velocity grid stops falling (change below 0.1 % over 5 iterations)
+            iters, prev, stop = 0, None, "max_iter"
+            while iters < max_iter:
+                rr = s.step(5)
+                iters += 5
+                if max(rr) < 1e-6:
+                    stop = "tolerance"
+                    break
+                if prev is not None and abs(max(rr) - prev) < 1e-3 * prev:
+                    stop = "floor"
+                    break
+                prev = max(rr)
+            row[prec] = {"seconds": time.perf_counter() - t0, "iterations": iters, "stopped_at": stop,
                          "residual": [float(x) for x in rr]}
             m = s.macro()
             sol[prec] = (m, s.wall(2)[1])
@@ -505,7 +520,8 @@ def run_kn_sweep(args):
             "dtype": "f32/f64" if args.precision == "mixed" else "f64", "data": "synthetic",
             "config": {"workload": "kn_sweep_%dx_cavity96_v40_L4" % args.count, "count": args.count},
             "seconds_to_solve_all": out["seconds"], "iterations": out["iterations"],
-            "converged": [max(r) < 1e-6 for r in out["residuals"]],
+            "converged": [max(r) < 1e-6 for r in out["residuals"]], "stopped_at": out["stopped_at"],
+            "residuals": out["residuals"],
             "kn": [c["gas"]["kn"] for c in cases], "lid": [c["bcs"][2]["u"] for c in cases], "adjoint": adj}
     print(json.dumps(line))
     return 0
