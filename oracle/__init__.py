@@ -85,6 +85,7 @@ def lib():
         L.oracle_objective.argtypes = [vp, i, i, vp, vp, vp]
         L.oracle_residual_dtheta.argtypes = [vp, i, i, vp]
         L.oracle_stage_cs.argtypes = [vp, vp, vp, vp]
+        L.oracle_set_cycle.argtypes = [vp, i]
         _lib = L
     return _lib
 
@@ -133,6 +134,10 @@ class Oracle:
             self.close()
         except Exception:
             pass
+
+    def set_cycle(self, cycle):
+        """Multigrid cycle type of both cycles: "V", "W" or "F"."""
+        _check(lib().oracle_set_cycle(self.h, {"V": 0, "W": 1, "F": 2}[cycle]))
 
     def init_uniform(self, rho, u, v, t):
         _check(lib().oracle_init_uniform(self.h, rho, u, v, t))

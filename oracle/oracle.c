@@ -64,6 +64,7 @@ struct oracle_solver {
     obc_t *bc;
     double *Cw; /* per BC: unit-density Maxwellian at the BC state, G part */
     int nu1, nu2, nuc;
+    int cycle; /* 0 V, 1 W, 2 F (Sec. 3.4: V, W, F and adaptive cycles) */
     double cfl, dtn_growth, dtp_min;
     int iter;
     double *f, *W, *q, *R;
@@ -790,16 +791,34 @@ static void prolong_lv(const olev_t *F, const olev_t *C, int m, const double *co
 }
 
 /* FAS cycle (Eq. FASCYC): W_l <- FAS(l, W_l^n, R_l); lv->Wn holds W_l^n and
- * lv->Rc the restricted (or UGKS) residual on entry; the result is left in lv->Wc. */
-static void fas(oracle_solver *s, int l)
+ * lv->Rc the restricted (or UGKS) residual on entry; the result is left in lv->Wc.
+ * The cycle type (Sec. 3.4) sets the coarse visits of a level: V one visit, W
+ * two W visits, F one F visit then one V visit.  A visit after the first starts
+ * from the coarse state the previous one left, with the same forcing function
+ * and the same frozen Gamma. */
+static void fas_visit(oracle_solver *s, int l, int type, int first);
+
+static void fas(oracle_solver *s, int l, int type)
 {
     olev_t *Lv = &s->lev[l];
     size_t n4 = 4 * (size_t)Lv->nc;
     resid_macro(s, Lv, Lv->Wn, Lv->Wn, Lv->RE);
     for (size_t q = 0; q < n4; ++q) Lv->P[q] = Lv->Rc[q] - Lv->RE[q]; /* forcing function */
     memcpy(Lv->Wc, Lv->Wn, n4 * sizeof(double));
+    fas_visit(s, l, type, 1);
+}
+
+static void fas_visit(oracle_solver *s, int l, int type, int first)
+{
+    olev_t *Lv = &s->lev[l];
+    size_t n4 = 4 * (size_t)Lv->nc;
     double *R = (double *)malloc(n4 * sizeof(double));
-    memcpy(R, Lv->Rc, n4 * sizeof(double));
+    if (first) {
+        memcpy(R, Lv->Rc, n4 * sizeof(double));
+    } else {
+        resid_macro(s, Lv, Lv->Wc, Lv->Wn, Lv->RE);
+        for (size_t q = 0; q < n4; ++q) R[q] = Lv->P[q] + Lv->RE[q];
+    }
     int coarsest = (l == s->L - 1);
     int npre = coarsest ? (s->L == 1 ? 1 : s->nuc) : s->nu1;
     for (int m = 0; m < npre; ++m) {
@@ -813,7 +832,8 @@ static void fas(oracle_solver *s, int l)
         olev_t *Cv = &s->lev[l + 1];
         restrict_lv(Lv, Cv, 4, Lv->Wc, Cv->Wn);
         restrict_lv(Lv, Cv, 4, R, Cv->Rc);
-        fas(s, l + 1);
+        fas(s, l + 1, type);                                   /* first coarse visit, of this type */
+        if (type != 0) fas_visit(s, l + 1, type == 1 ? 1 : 0, 0); /* W: another W visit; F: a V visit */
         size_t c4 = 4 * (size_t)Cv->nc;
         for (size_t q = 0; q < c4; ++q) Cv->dW[q] = Cv->Wc[q] - Cv->Wn[q];
         double *corr = (double *)malloc(n4 * sizeof(double));
@@ -1061,8 +1081,11 @@ static void apply_micro(const oracle_solver *s, const olev_t *Lv, const double *
 }
 
 /* CS cycle (Eq. CSCYC): on entry lv->r holds the residual of level l (it is
- * renewed in place); on exit lv->df holds the total correction. */
-static void cs(oracle_solver *s, int l)
+ * renewed in place); on exit lv->df holds the total correction.  Cycle types
+ * as for FAS: a second coarse visit (W: of type W, F: of type V) solves for the
+ * coarse residual that the first visit's correction leaves, r_H - A_H df_H,
+ * and the two corrections add. */
+static void cs(oracle_solver *s, int l, int type)
 {
     olev_t *Lv = &s->lev[l];
     size_t n = 2 * (size_t)Lv->nc * s->nv;
@@ -1079,7 +1102,20 @@ static void cs(oracle_solver *s, int l)
     olev_t *Cv = &s->lev[l + 1];
     for (int cp = 0; cp < 2; ++cp)
         restrict_lv(Lv, Cv, s->nv, Lv->r + (size_t)cp * Lv->nc * s->nv, Cv->r + (size_t)cp * Cv->nc * s->nv);
-    cs(s, l + 1);
+    size_t nC = 2 * (size_t)Cv->nc * s->nv;
+    double *r0 = type != 0 ? dalloc(nC) : NULL;
+    if (r0) memcpy(r0, Cv->r, nC * sizeof(double));
+    cs(s, l + 1, type);
+    if (type != 0) {
+        double *acc = dalloc(nC);
+        memcpy(acc, Cv->df, nC * sizeof(double));
+        apply_micro(s, Cv, Cv->inv_tau, acc, Cv->Ad);
+        for (size_t q = 0; q < nC; ++q) Cv->r[q] = r0[q] - Cv->Ad[q];
+        cs(s, l + 1, type == 1 ? 1 : 0);
+        for (size_t q = 0; q < nC; ++q) Cv->df[q] += acc[q];
+        free(acc);
+        free(r0);
+    }
     for (int cp = 0; cp < 2; ++cp)
         prolong_lv(Lv, Cv, s->nv, Cv->df + (size_t)cp * Cv->nc * s->nv, Lv->dl + (size_t)cp * Lv->nc * s->nv);
     for (size_t q = 0; q < n; ++q) Lv->df[q] += Lv->dl[q];
@@ -1144,7 +1180,7 @@ static void one_iteration(oracle_solver *s, double res[4])
     /* Step 2: predicted conservative variables by FAS */
     memcpy(L0->Wn, s->W, 4 * nc * sizeof(double));
     memcpy(L0->Rc, s->R, 4 * nc * sizeof(double));
-    fas(s, 0);
+    fas(s, 0, s->cycle);
     memcpy(L0->Wtil, L0->Wc, 4 * nc * sizeof(double));
     /* Step 3: predicted equilibrium and collision time; coarse tau from the
      * volume-restricted predicted state */
@@ -1183,7 +1219,7 @@ static void one_iteration(oracle_solver *s, double res[4])
             }
         }
     /* Step 5: total correction by the CS cycle */
-    cs(s, 0);
+    cs(s, 0, s->cycle);
     /* Steps 6-7 */
     size_t n = 2 * nc * nv;
     for (size_t q = 0; q < n; ++q) s->f[q] += L0->df[q];
@@ -2185,7 +2221,16 @@ int oracle_stage_cs(oracle_solver *s, const double *inv_tau, const double *r, do
     }
     size_t n = 2 * (size_t)s->lev[0].nc * s->nv;
     memcpy(s->lev[0].r, r, n * sizeof(double));
-    cs(s, 0);
+    cs(s, 0, s->cycle);
     memcpy(df, s->lev[0].df, n * sizeof(double));
+    return 0;
+}
+
+/* Multigrid cycle type of both the FAS and the CS cycle (Sec. 3.4 names V, W,
+ * F and adaptive cycles): 0 V (default), 1 W, 2 F. */
+int oracle_set_cycle(oracle_solver *s, int type)
+{
+    if (type < 0 || type > 2) return fail("cycle type %d: 0 V, 1 W, 2 F", type);
+    s->cycle = type;
     return 0;
 }

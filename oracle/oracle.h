@@ -51,6 +51,8 @@ int oracle_init_fields(oracle_solver *s, const double *rho, const double *u,
                        const double *v, const double *t);
 /* n outer iterations (Steps 1-8); res = RMS residual of the last Step 1. */
 int oracle_step(oracle_solver *s, int n, double res[4]);
+/* Multigrid cycle type of the FAS and CS cycles: 0 V (default), 1 W, 2 F. */
+int oracle_set_cycle(oracle_solver *s, int type);
 int oracle_get_macro(const oracle_solver *s, double *rho, double *u, double *v,
                      double *t, double *qx, double *qy);
 int oracle_get_f(const oracle_solver *s, double *f);

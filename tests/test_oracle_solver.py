@@ -344,3 +344,29 @@ def test_multigrid_and_single_grid_reach_the_same_steady_state():
         out[levels] = o.macro()
     for k in ("rho", "u", "v", "t"):
         assert np.allclose(out[1][k], out[3][k], rtol=1e-9, atol=1e-10), k
+
+
+def test_w_and_f_cycles_reach_the_v_cycle_steady_state():
+    """W and F cycles (Sec. 3.4 names them) change the path, not the fixed
+    point: all three reach the same discrete steady state, and on a 3-level
+    hierarchy the first iterates differ (the coarse levels are visited more)."""
+    out, first = {}, {}
+    for cyc in ("V", "W", "F"):
+        case = wl.cavity(n=8, nvel=24, kn=0.3, lid=0.2, vmax=6.0, levels=3)
+        case["bcs"][2] = wl.bc(wl.FARFIELD, rho=1.0, u=0.2, v=0.0, t=1.0)
+        o = oracle.Oracle(case)
+        o.set_cycle(cyc)
+        o.init_uniform(1.0, 0.0, 0.0, 1.0)
+        o.step(1)
+        first[cyc] = o.get_f()
+        for _ in range(300):
+            res = o.step(1)
+            if np.all(res < 1e-12):
+                break
+        assert np.all(res < 1e-11), (cyc, res)
+        out[cyc] = o.macro()
+    for a, b in (("V", "W"), ("W", "F"), ("V", "F")):
+        assert np.abs(first[a] - first[b]).max() > 1e-9 * np.abs(first["V"]).max(), (a, b)
+    for cyc in ("W", "F"):
+        for k in ("rho", "u", "v", "t"):
+            assert np.allclose(out[cyc][k], out["V"][k], rtol=1e-9, atol=1e-10), (cyc, k)
