@@ -139,6 +139,16 @@ miugks_status miugks_set_f(miugks_solver *s, const double *f);
  * *n_faces: in capacity, out count (call with capacity 0 to size). */
 miugks_status miugks_get_wall(miugks_solver *s, int bc, int *n_faces, double *p, double *tau, double *q);
 miugks_status miugks_set_bc(miugks_solver *s, int bc, const miugks_bc *value);
+/* Multigrid cycle type of both the prediction (FAS, Eq. FASCYC) and the
+ * evolution (CS, Eq. CSCYC) cycles; Sec. 3.4 names V, W and F cycles and
+ * evaluates only the V cycle.  type 0 V (default), 1 W (two coarse visits of
+ * type W), 2 F (an F visit then a V visit).  A second FAS visit starts from the
+ * coarse state the first left, with the same forcing function and frozen
+ * Gamma; a second CS visit solves for the coarse residual the first correction
+ * leaves.  W and F need two more per-velocity arrays per coarse level, taken
+ * from the solver's allocator on the first selection.  The adjoint's
+ * preconditioner stays the transposed V cycle.  MIUGKS_EINVAL for another type. */
+miugks_status miugks_set_cycle(miugks_solver *s, int type);
 
 /* Stages of one iteration on explicit host data, for kernel-level checks.
  *  flux: Step 1 at the current state -> R (nc x 4), time-averaged micro face

@@ -28,6 +28,9 @@ struct HLevel {
            *gy = nullptr, *Wt = nullptr, *idiag = nullptr, *T = nullptr;
     // evolution work, [2][nc][nv] (invD [nc][nv]); element type double, or float in the mixed form
     void *r = nullptr, *df = nullptr, *dl = nullptr, *invD = nullptr;
+    // W and F cycles (second coarse visit of the CS cycle): the restricted residual and
+    // the first visit's correction, allocated when such a cycle is selected
+    void *r0 = nullptr, *acc = nullptr;
     double* inv_tau = nullptr;
 };
 
@@ -57,6 +60,7 @@ struct miugks_solver {
     double *rms_part = nullptr, *rms_out = nullptr;
     double dtp_min = 0;
     int iter = 0;
+    int cycle = 0;                              // 0 V, 1 W, 2 F (both multigrid cycles)
     bool initialised = false;
     bool timing = false;
     cudaEvent_t ev[6] = {};
@@ -286,7 +290,14 @@ miugks_status timed_macro_sgs(miugks_solver* s, const MacroArgs& ma, HLevel& Lv,
     return MIUGKS_OK;
 }
 
-miugks_status fas(miugks_solver* s, int l, double dti)
+// FAS cycle (Eq. FASCYC) of level l: forcing function and frozen Gamma from the
+// level's W^n, then one visit.  A visit smooths, corrects from the next level
+// (one coarse visit for V; W: two W visits; F: an F visit then a V visit, the
+// second starting from the coarse state the first left, with the same forcing)
+// and post-smooths.
+miugks_status fas_visit(miugks_solver* s, int l, double dti, int type, bool first);
+
+miugks_status fas(miugks_solver* s, int l, double dti, int type)
 {
     HLevel& Lv = s->lev[l];
     MacroArgs ma = macro_args(s, l, dti);
@@ -294,7 +305,16 @@ miugks_status fas(miugks_solver* s, int l, double dti)
     CK(launch_macro_gamma(ma, Lv.Wn, Lv.gx, Lv.gy, Lv.idiag, s->st));
     CK(launch_macro_resid(ma, Lv.Wn, Lv.gx, Lv.gy, Lv.Rc, Lv.P, 0, s->st));     // forcing function
     CK(cudaMemcpyAsync(Lv.Wc, Lv.Wn, n4 * sizeof(double), cudaMemcpyDeviceToDevice, s->st));
-    CK(cudaMemcpyAsync(Lv.R, Lv.Rc, n4 * sizeof(double), cudaMemcpyDeviceToDevice, s->st));
+    return fas_visit(s, l, dti, type, true);
+}
+
+miugks_status fas_visit(miugks_solver* s, int l, double dti, int type, bool first)
+{
+    HLevel& Lv = s->lev[l];
+    MacroArgs ma = macro_args(s, l, dti);
+    size_t n4 = 4 * (size_t)Lv.nc;
+    if (first) CK(cudaMemcpyAsync(Lv.R, Lv.Rc, n4 * sizeof(double), cudaMemcpyDeviceToDevice, s->st));
+    else CK(launch_macro_resid(ma, Lv.Wc, Lv.gx, Lv.gy, Lv.P, Lv.R, 1, s->st));   // P + R_E(W) of the state left
     const bool coarsest = l == s->L - 1;
     const int npre = coarsest ? (s->L == 1 ? 1 : s->opts.nu_coarse) : s->opts.nu1;
     for (int m = 0; m < npre; ++m) {
@@ -306,7 +326,8 @@ miugks_status fas(miugks_solver* s, int l, double dti)
     HLevel& Cv = s->lev[l + 1];
     CK(launch_restrict<double>(Lv.dev, Cv.dev, 4, 1, Lv.Wc, Cv.Wn, s->st));
     CK(launch_restrict<double>(Lv.dev, Cv.dev, 4, 1, Lv.R, Cv.Rc, s->st));
-    ST(fas(s, l + 1, dti));
+    ST(fas(s, l + 1, dti, type));
+    if (type != 0) ST(fas_visit(s, l + 1, dti, type == 1 ? 1 : 0, false));
     CK(launch_sub(Cv.dW, Cv.Wc, Cv.Wn, 4 * (size_t)Cv.nc, s->st));
     CK(launch_prolong_add<double>(Lv.dev, Cv.dev, 4, 1, Lv.pidx, Lv.pw, Cv.dW, Lv.Wc, (double*)nullptr, s->st));
     for (int m = 0; m < s->opts.nu2; ++m) {
@@ -316,8 +337,11 @@ miugks_status fas(miugks_solver* s, int l, double dti)
     return MIUGKS_OK;
 }
 
+// CS cycle (Eq. CSCYC) of level l.  W and F cycles visit the next level twice:
+// the second visit solves for the coarse residual the first correction leaves,
+// r_H - A_H df_H, and the corrections add.
 template <typename F>
-miugks_status cs(miugks_solver* s, int l)
+miugks_status cs(miugks_solver* s, int l, int type)
 {
     HLevel& Lv = s->lev[l];
     MicroArgs mi = micro_args(s, l);
@@ -333,8 +357,18 @@ miugks_status cs(miugks_solver* s, int l)
         if (last) return MIUGKS_OK;
     }
     HLevel& Cv = s->lev[l + 1];
+    const size_t nC = 2 * (size_t)Cv.nc * s->nv;
     CK(launch_restrict<F>(Lv.dev, Cv.dev, s->nv, 2, r, (F*)Cv.r, s->st));
-    ST(cs<F>(s, l + 1));
+    if (type != 0) CK(cudaMemcpyAsync(Cv.r0, Cv.r, nC * sizeof(F), cudaMemcpyDeviceToDevice, s->st));
+    ST(cs<F>(s, l + 1, type));
+    if (type != 0) {
+        MicroArgs mc = micro_args(s, l + 1);
+        CK(cudaMemcpyAsync(Cv.acc, Cv.df, nC * sizeof(F), cudaMemcpyDeviceToDevice, s->st));
+        CK(cudaMemcpyAsync(Cv.r, Cv.r0, nC * sizeof(F), cudaMemcpyDeviceToDevice, s->st));
+        CK(launch_micro_renew<F>(mc, s->Zw, (F*)Cv.acc, (F*)Cv.r, nullptr, 1, s->st));   // r_H - A_H df_H
+        ST(cs<F>(s, l + 1, type == 1 ? 1 : 0));
+        CK(launch_micro_renew<F>(mc, s->Zw, (F*)Cv.acc, (F*)Cv.r, (F*)Cv.df, 0, s->st)); // df_H += first correction
+    }
     CK(launch_prolong_add<F>(Lv.dev, Cv.dev, s->nv, 2, Lv.pidx, Lv.pw, (F*)Cv.df, df, dl, s->st));
     for (int m = 0; m < s->opts.nu2; ++m) {
         CK(launch_micro_renew<F>(mi, s->Zw, dl, r, nullptr, 1, s->st));
@@ -373,7 +407,7 @@ miugks_status one_iteration_t(miugks_solver* s)
     size_t n4 = 4 * (size_t)L0.nc;
     CK(cudaMemcpyAsync(L0.Wn, s->W, n4 * sizeof(double), cudaMemcpyDeviceToDevice, s->st));
     CK(cudaMemcpyAsync(L0.Rc, s->R, n4 * sizeof(double), cudaMemcpyDeviceToDevice, s->st));
-    ST(fas(s, 0, dti));                                                      // Step 2
+    ST(fas(s, 0, dti, s->cycle));                                            // Step 2
     CK(cudaMemcpyAsync(L0.Wt, L0.Wc, n4 * sizeof(double), cudaMemcpyDeviceToDevice, s->st));
     MicroArgs m0 = micro_args(s, 0);                                         // Steps 3-4
     CK(launch_micro_residual<F>(m0, s->gas, L0.Wt, s->q, (const F*)s->f, (const F*)s->phx, (const F*)s->phy, dti,
@@ -384,7 +418,7 @@ miugks_status one_iteration_t(miugks_solver* s)
                                    (F*)s->lev[l].invD, s->st));
     }
     if (s->timing) CK(cudaEventRecord(s->ev[2], s->st));
-    ST(cs<F>(s, 0));                                                            // Step 5
+    ST(cs<F>(s, 0, s->cycle));                                                  // Step 5
     if (s->timing) CK(cudaEventRecord(s->ev[3], s->st));
     CK(launch_update_moments<F>(L0.dev, s->vel, (F*)s->f, (const F*)L0.df, s->W, s->q, s->st));   // Steps 6-7
     if (s->timing) CK(cudaEventRecord(s->ev[4], s->st));
@@ -871,6 +905,29 @@ miugks_status miugks_set_bc(miugks_solver* s, int bc, const miugks_bc* value)
                        cudaMemcpyHostToDevice, s->st));
     CK(cudaMemcpyAsync(s->Zw, Zh.data(), Zh.size() * sizeof(double), cudaMemcpyHostToDevice, s->st));
     CK(cudaStreamSynchronize(s->st));
+    return MIUGKS_OK;
+}
+
+miugks_status miugks_set_cycle(miugks_solver* s, int type)
+{
+    if (!s) return MIUGKS_EINVAL;
+    if (type < 0 || type > 2) return fail(s, MIUGKS_EINVAL, "cycle type %d: 0 V, 1 W, 2 F", type);
+    if (type != 0)
+        for (int l = 1; l < s->L; ++l) {
+            HLevel& Cv = s->lev[l];
+            const size_t n = 2 * (size_t)Cv.nc * s->nv;
+            if (!Cv.r0) ST(falloc(s, &Cv.r0, n));
+            if (!Cv.acc) ST(falloc(s, &Cv.acc, n));
+        }
+    if (type != s->cycle && s->gexec) {
+        // the captured iteration holds the old launch sequence
+        CK(cudaStreamSynchronize(s->st));
+        cudaGraphExecDestroy(s->gexec);
+        if (s->graph) cudaGraphDestroy(s->graph);
+        s->gexec = nullptr;
+        s->graph = nullptr;
+    }
+    s->cycle = type;
     return MIUGKS_OK;
 }
 

@@ -1,0 +1,76 @@
+"""W and F multigrid cycles (Sec. 3.4 names V, W and F cycles) through the C
+ABI against the oracle: whole outer iterations on seeded states, FP64 at the
+1e-10 bar, for the cavity (3 and 4 levels) and the flat plate; the mixed form
+against the oracle at its measured bound."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1704_03151_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1704_03151_gb300 import miugks
+    miugks.load()
+    return miugks
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+CASES = {
+    "cavity_L3": lambda: wl.cavity(n=16, nvel=12, kn=0.5, lid=0.2, levels=3),
+    "cavity_L4": lambda: wl.cavity(n=16, nvel=10, kn=0.1, lid=0.2, levels=4),
+    "plate_L2": lambda: wl.flat_plate(kn=0.2, nvel=12, levels=2, n_up=4, n_plate=8, n_down=4, ny=12),
+}
+
+
+@pytest.mark.parametrize("cycle", ["W", "F"])
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_cycle_iterations_match_oracle(lib, name, cycle):
+    case = CASES[name]()
+    o, g = oracle.Oracle(case), lib.Solver(case)
+    o.set_cycle(cycle)
+    g.set_cycle(cycle)
+    fields = wl.random_fields(case, 7, amp=0.08)
+    o.init_fields(*fields)
+    g.init_fields(*fields)
+    for n in (1, 3):
+        ro, rg = o.step(n), g.step(n)
+        assert rel(g.get_f(), o.get_f()) < TOL, (name, cycle, n)
+        assert np.allclose(rg, ro, rtol=1e-8, atol=1e-14), (name, cycle, n)
+
+
+def test_switching_cycles_recaptures_the_iteration(lib):
+    """A solver that has replayed a captured V-cycle iteration and then switches
+    to W matches an oracle that switches at the same iteration."""
+    case = CASES["cavity_L3"]()
+    o, g = oracle.Oracle(case), lib.Solver(case)
+    o.init_uniform(1.0, 0.0, 0.0, 1.0)
+    g.init_uniform(1.0, 0.0, 0.0, 1.0)
+    o.step(3), g.step(3)
+    o.set_cycle("W")
+    g.set_cycle("W")
+    o.step(2), g.step(2)
+    assert rel(g.get_f(), o.get_f()) < TOL
+
+
+def test_mixed_w_cycle_close_to_oracle(lib):
+    case = CASES["cavity_L3"]()
+    o, g = oracle.Oracle(case), lib.Solver(case, precision="mixed")
+    o.set_cycle("W")
+    g.set_cycle("W")
+    fields = wl.random_fields(case, 3, amp=0.08)
+    o.init_fields(*fields)
+    g.init_fields(*fields)
+    o.step(4), g.step(4)
+    assert rel(g.get_f(), o.get_f()) < 2e-5
