@@ -394,7 +394,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint gradient at the converged state")
     ap.add_argument("--no-plate", action="store_true", help="skip the full-size flat-plate throughput line")
-    ap.add_argument("--workload", default="cavity64", choices=["cavity64", "kn_sweep", "adjoint"])
+    ap.add_argument("--workload", default="cavity64", choices=["cavity64", "kn_sweep", "adjoint", "cycles"])
     ap.add_argument("--count", type=int, default=32, help="cavities of the Kn sweep")
     ap.add_argument("--max-iter", type=int, default=1500)
     ap.add_argument("--adjoint", action="store_true", help="Kn sweep: adjoint lid-shear gradient of every case")
@@ -405,6 +405,8 @@ def main():
         return run_kn_sweep(args)
     if args.workload == "adjoint":
         return run_adjoint(args)
+    if args.workload == "cycles":
+        return run_cycles(args)
     args.warmup = max(args.warmup, 3)
     import torch
     rank, world = dist_setup(args.gpus)
@@ -485,6 +487,37 @@ def run_adjoint(args):
                                                              "forward_iterations": iters},
                       "gradient": g, "gmres_iterations": info["iterations"],
                       "relative_residual": info["residual"], "converged": info["converged"]}))
+    return 0
+
+
+def run_cycles(args):
+    """Cycle and smoothing-count study (Sec. 3.4 names V, W and F cycles and
+    leaves the smoothing counts open): the 64x64 cavity from rest to RMS 1e-6
+    (or to the residual floor, as in the Kn series) for each cycle type and
+    (nu1, nu2), at Kn 1 and 10, in the precision of --precision."""
+    import torch
+    from paper_1704_03151_gb300 import build, miugks, workloads
+    build.build()
+    rows = []
+    for kn in (1.0, 10.0):
+        for cyc in ("V", "W", "F"):
+            for nu1, nu2 in ((1, 1), (2, 1), (2, 2), (3, 1)):
+                c = workloads.cavity(n=NX, nvel=NVEL, kn=kn, lid=0.16, levels=LEVELS, nu1=nu1, nu2=nu2)
+                s = miugks.Solver(c, precision=args.precision)
+                s.set_cycle(cyc)
+                s.init_uniform(1.0, 0.0, 0.0, 1.0)
+                s.step(1)                                  # one eager iteration (kernel set-up)
+                s.init_uniform(1.0, 0.0, 0.0, 1.0)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                iters, rr, ok = s.run(1e-6, args.max_iter)
+                rows.append({"kn": kn, "cycle": cyc, "nu1": nu1, "nu2": nu2, "iterations": iters,
+                             "seconds": time.perf_counter() - t0, "converged": bool(ok),
+                             "residual": [float(x) for x in rr]})
+                s.close()
+    print(json.dumps({"metric": "time to RMS residual 1e-6 by multigrid cycle and smoothing counts", "unit": "s",
+                      "higher_is_better": False, "config": {"workload": WORKLOAD, "precision": args.precision},
+                      "rows": rows}))
     return 0
 
 
