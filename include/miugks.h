@@ -149,6 +149,15 @@ miugks_status miugks_set_bc(miugks_solver *s, int bc, const miugks_bc *value);
  * from the solver's allocator on the first selection.  The adjoint's
  * preconditioner stays the transposed V cycle.  MIUGKS_EINVAL for another type. */
 miugks_status miugks_set_cycle(miugks_solver *s, int type);
+/* Full-multigrid start-up (Sec. 3.5): the state of `coarse`, a solver of the
+ * same problem on the next coarser mesh (every second grid line of s's mesh,
+ * same velocity grid and precision), becomes s's initial state by the bilinear
+ * prolongation of Eq. prolongation applied to f velocity by velocity; W and q
+ * follow from its moments and the iteration count restarts at 0.  s needs at
+ * least two levels.  Waits for coarse's stream.  MIUGKS_EINVAL when the meshes,
+ * velocity grids or precisions do not match, MIUGKS_ESTATE when coarse has no
+ * state. */
+miugks_status miugks_init_from_coarse(miugks_solver *s, const miugks_solver *coarse);
 
 /* Stages of one iteration on explicit host data, for kernel-level checks.
  *  flux: Step 1 at the current state -> R (nc x 4), time-averaged micro face

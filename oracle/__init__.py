@@ -86,6 +86,7 @@ def lib():
         L.oracle_residual_dtheta.argtypes = [vp, i, i, vp]
         L.oracle_stage_cs.argtypes = [vp, vp, vp, vp]
         L.oracle_set_cycle.argtypes = [vp, i]
+        L.oracle_init_from_coarse.argtypes = [vp, vp]
         _lib = L
     return _lib
 
@@ -134,6 +135,10 @@ class Oracle:
             self.close()
         except Exception:
             pass
+
+    def init_from_coarse(self, coarse):
+        """Initial state by bilinear prolongation of f from an oracle on the next coarser mesh."""
+        _check(lib().oracle_init_from_coarse(self.h, coarse.h))
 
     def set_cycle(self, cycle):
         """Multigrid cycle type of both cycles: "V", "W" or "F"."""

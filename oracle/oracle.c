@@ -2234,3 +2234,25 @@ int oracle_set_cycle(oracle_solver *s, int type)
     s->cycle = type;
     return 0;
 }
+
+/* Full-multigrid start-up (Sec. 3.5): the state of a solver on the next
+ * coarser mesh (every second grid line, same velocity grid) becomes the
+ * initial state of this one by the bilinear prolongation of Eq. prolongation,
+ * applied to f velocity by velocity; W and q follow from the moments. */
+int oracle_init_from_coarse(oracle_solver *s, const oracle_solver *c)
+{
+    if (s->L < 2) return fail("init_from_coarse: the fine solver needs at least two levels");
+    const olev_t *F1 = &s->lev[1], *C0 = &c->lev[0];
+    if (c->nv != s->nv || C0->nx != F1->nx || C0->ny != F1->ny)
+        return fail("init_from_coarse: the coarse solver is not on the next coarser mesh");
+    for (int i = 0; i <= F1->nx; ++i)
+        if (fabs(C0->xn[i] - F1->xn[i]) > 1e-12 * (1.0 + fabs(F1->xn[i]))) return fail("init_from_coarse: x nodes differ");
+    for (int j = 0; j <= F1->ny; ++j)
+        if (fabs(C0->yn[j] - F1->yn[j]) > 1e-12 * (1.0 + fabs(F1->yn[j]))) return fail("init_from_coarse: y nodes differ");
+    size_t ncC = C0->nc, ncF = s->lev[0].nc;
+    for (int cp = 0; cp < 2; ++cp)
+        prolong_lv(&s->lev[0], &s->lev[1], s->nv, c->f + (size_t)cp * ncC * s->nv, s->f + (size_t)cp * ncF * s->nv);
+    moments(s);
+    s->iter = 0;
+    return 0;
+}

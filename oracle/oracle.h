@@ -51,6 +51,9 @@ int oracle_init_fields(oracle_solver *s, const double *rho, const double *u,
                        const double *v, const double *t);
 /* n outer iterations (Steps 1-8); res = RMS residual of the last Step 1. */
 int oracle_step(oracle_solver *s, int n, double res[4]);
+/* Full-multigrid start-up: f of a solver on the next coarser mesh (every
+ * second grid line, same velocity grid) prolonged bilinearly onto this one. */
+int oracle_init_from_coarse(oracle_solver *s, const oracle_solver *coarse);
 /* Multigrid cycle type of the FAS and CS cycles: 0 V (default), 1 W, 2 F. */
 int oracle_set_cycle(oracle_solver *s, int type);
 int oracle_get_macro(const oracle_solver *s, double *rho, double *u, double *v,

@@ -908,6 +908,39 @@ miugks_status miugks_set_bc(miugks_solver* s, int bc, const miugks_bc* value)
     return MIUGKS_OK;
 }
 
+miugks_status miugks_init_from_coarse(miugks_solver* s, const miugks_solver* c)
+{
+    if (!s || !c) return MIUGKS_EINVAL;
+    if (s->L < 2) return fail(s, MIUGKS_EINVAL, "init_from_coarse: the fine solver needs at least two levels");
+    const HLevel& F1 = s->lev[1];
+    const HLevel& C0 = c->lev[0];
+    if (c->nv != s->nv || c->nu != s->nu || C0.nx != F1.nx || C0.ny != F1.ny)
+        return fail(s, MIUGKS_EINVAL, "init_from_coarse: the coarse solver is not on the next coarser mesh");
+    if (c->mixed != s->mixed) return fail(s, MIUGKS_EINVAL, "init_from_coarse: the two solvers differ in precision");
+    if (!c->initialised) return fail(s, MIUGKS_ESTATE, "init_from_coarse: the coarse solver has no state");
+    for (int i = 0; i <= F1.nx; ++i)
+        if (std::fabs(C0.xn[i] - F1.xn[i]) > 1e-12 * (1.0 + std::fabs(F1.xn[i])))
+            return fail(s, MIUGKS_EINVAL, "init_from_coarse: x nodes differ");
+    for (int j = 0; j <= F1.ny; ++j)
+        if (std::fabs(C0.yn[j] - F1.yn[j]) > 1e-12 * (1.0 + std::fabs(F1.yn[j])))
+            return fail(s, MIUGKS_EINVAL, "init_from_coarse: y nodes differ");
+    HLevel& L0 = s->lev[0];
+    const size_t n = 2 * (size_t)L0.nc * s->nv;
+    CK(cudaStreamSynchronize(c->st));                      // the coarse state is complete
+    CK(cudaMemsetAsync(s->f, 0, n * s->fsz, s->st));
+    if (s->mixed)
+        CK(launch_prolong_add<float>(L0.dev, F1.dev, s->nv, 2, L0.pidx, L0.pw, (const float*)c->f, (float*)s->f,
+                                     (float*)nullptr, s->st));
+    else
+        CK(launch_prolong_add<double>(L0.dev, F1.dev, s->nv, 2, L0.pidx, L0.pw, (const double*)c->f, (double*)s->f,
+                                      (double*)nullptr, s->st));
+    ST(moments_now(s));
+    CK(cudaStreamSynchronize(s->st));
+    s->initialised = true;
+    s->iter = 0;
+    return MIUGKS_OK;
+}
+
 miugks_status miugks_set_cycle(miugks_solver* s, int type)
 {
     if (!s) return MIUGKS_EINVAL;

@@ -90,6 +90,7 @@ def load():
         "miugks_adjoint": [vp, _i, _i, _i, _d, _i, _i, vp, vp],
         "miugks_save": [vp, ctypes.c_char_p], "miugks_load": [vp, ctypes.c_char_p],
         "miugks_macro_sweep_times": [vp, _P(_d), _P(_i)], "miugks_set_cycle": [vp, _i],
+        "miugks_init_from_coarse": [vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -113,7 +114,7 @@ def exported_symbols():
             "miugks_stage_adjoint_residual", "miugks_stage_sgs_micro_transposed", "miugks_stage_cs_transposed",
             "miugks_objective",
             "miugks_adjoint", "miugks_residual_rms_noalloc", "miugks_save", "miugks_load",
-            "miugks_macro_sweep_times", "miugks_set_cycle"]
+            "miugks_macro_sweep_times", "miugks_set_cycle", "miugks_init_from_coarse"]
 
 
 def _ptr(a):
@@ -255,6 +256,10 @@ class Solver:
 
     def set_bc(self, b, type_, rho, u, v, t):
         self._check(self._lib.miugks_set_bc(self.h, b, ctypes.byref(miugks_bc(type_, rho, u, v, t))))
+
+    def init_from_coarse(self, coarse):
+        """Initial state by bilinear prolongation of f from a solver on the next coarser mesh."""
+        self._check(self._lib.miugks_init_from_coarse(self.h, coarse.h))
 
     def set_cycle(self, cycle):
         """Multigrid cycle type of both cycles: "V", "W" or "F"."""

@@ -128,6 +128,29 @@ def flat_plate(kn=0.1, ma=0.2, nvel=48, vmax=5.0, levels=4, n_up=32, n_plate=64,
     }
 
 
+def coarsen_case(case):
+    """The same problem on the next coarser mesh (every second grid line, as
+    the multigrid levels of Sec. 3.1), with one multigrid level fewer: the
+    coarse problems of a full-multigrid start-up."""
+    nx, ny = case["nx"], case["ny"]
+    if nx % 2 or ny % 2 or case["mg"]["levels"] < 2:
+        raise ValueError("cannot coarsen %dx%d with %d levels" % (nx, ny, case["mg"]["levels"]))
+    fbx = np.asarray(case["face_bc_x"]).reshape(ny, nx + 1)
+    fby = np.asarray(case["face_bc_y"]).reshape(ny + 1, nx)
+    if not (np.array_equal(fbx[0::2, 0::2], fbx[1::2, 0::2]) and np.array_equal(fby[0::2, 0::2], fby[0::2, 1::2])):
+        raise ValueError("a coarse face would span two boundary ids")
+    c = dict(case)
+    c["name"] = case["name"] + "_coarse"
+    c["nx"], c["ny"] = nx // 2, ny // 2
+    c["x_nodes"] = np.asarray(case["x_nodes"])[0::2].copy()
+    c["y_nodes"] = np.asarray(case["y_nodes"])[0::2].copy()
+    c["face_bc_x"] = fbx[0::2, 0::2].ravel().copy()
+    c["face_bc_y"] = fby[0::2, 0::2].ravel().copy()
+    c["mg"] = dict(case["mg"], levels=case["mg"]["levels"] - 1)
+    c["bcs"] = [dict(b) for b in case["bcs"]]
+    return c
+
+
 def splitmix64(seed):
     """SplitMix64 stream of uniform doubles in [0, 1) (53-bit)."""
     state = seed & 0xFFFFFFFFFFFFFFFF

@@ -1,0 +1,83 @@
+"""Full-multigrid start-up (Sec. 3.5) through the C ABI: the prolonged initial
+state and the iterations after it against the oracle, refusal of mismatched
+solvers, and the FMG driver reaching the steady state of a plain solve."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1704_03151_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1704_03151_gb300 import fmg, miugks
+    miugks.load()
+    return miugks, fmg
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+@pytest.mark.parametrize("make", [
+    lambda: wl.cavity(n=16, nvel=12, kn=0.5, lid=0.2, levels=3),
+    lambda: wl.flat_plate(kn=0.2, nvel=12, levels=2, n_up=4, n_plate=8, n_down=4, ny=12),
+])
+def test_init_from_coarse_matches_oracle(env, make):
+    miugks, _ = env
+    case = make()
+    coarse = wl.coarsen_case(case)
+    oc = oracle.Oracle(coarse)
+    oc.init_fields(*wl.random_fields(coarse, 2, amp=0.1))
+    oc.step(2)
+    gc = miugks.Solver(coarse)
+    gc.init_uniform(1.0, 0.0, 0.0, 1.0)
+    gc.set_f(oc.get_f())
+    o, g = oracle.Oracle(case), miugks.Solver(case)
+    o.init_from_coarse(oc)
+    g.init_from_coarse(gc)
+    assert rel(g.get_f(), o.get_f()) < 1e-12
+    for k in ("rho", "u", "v", "t"):
+        assert rel(g.macro()[k], o.macro()[k]) < 1e-12, k
+    o.step(2), g.step(2)
+    assert rel(g.get_f(), o.get_f()) < 1e-10
+
+
+def test_init_from_coarse_refuses_mismatch(env):
+    miugks, _ = env
+    case = wl.cavity(n=16, nvel=12, kn=0.5, lid=0.2, levels=3)
+    same = miugks.Solver(case)
+    same.init_uniform(1.0, 0.0, 0.0, 1.0)
+    fine = miugks.Solver(case)
+    with pytest.raises(miugks.MiugksError):
+        fine.init_from_coarse(same)                       # not the next coarser mesh
+    other = miugks.Solver(wl.coarsen_case(wl.cavity(n=16, nvel=10, kn=0.5, lid=0.2, levels=3)))
+    other.init_uniform(1.0, 0.0, 0.0, 1.0)
+    with pytest.raises(miugks.MiugksError):
+        fine.init_from_coarse(other)                      # another velocity grid
+    fresh = miugks.Solver(wl.coarsen_case(case))
+    with pytest.raises(miugks.MiugksError):
+        fine.init_from_coarse(fresh)                      # coarse solver without a state
+
+
+def test_fmg_reaches_the_plain_steady_state(env):
+    miugks, fmg = env
+    # farfield top and a wide velocity grid: a unique steady state with a residual that falls to round-off
+    case = wl.cavity(n=16, nvel=24, kn=0.3, lid=0.2, vmax=6.0, levels=3)
+    case["bcs"][2] = wl.bc(wl.FARFIELD, rho=1.0, u=0.2, v=0.0, t=1.0)
+    s, info = fmg.run(case, tol=1e-11, max_iter=600)
+    assert [m["nx"] for m in info["meshes"]] == [4, 8, 16]
+    assert info["meshes"][-1]["stopped_at"] == "tolerance", info
+    p = miugks.Solver(case)
+    p.init_uniform(1.0, 0.0, 0.0, 1.0)
+    it, res, ok = p.run(1e-11, 600)
+    assert ok, res
+    a, b = s.macro(), p.macro()
+    for k in ("rho", "u", "v", "t"):
+        assert np.allclose(a[k], b[k], rtol=1e-8, atol=1e-9), k
