@@ -215,6 +215,18 @@ miugks_status miugks_stage_sgs_micro_transposed(miugks_solver *s, const double *
  *        concatenated level after level (sum of nc_l values).  The adjoint
  *        solve uses this transposed cycle as its preconditioner. */
 miugks_status miugks_stage_cs_transposed(miugks_solver *s, const double *inv_tau, const double *z, double *out);
+/*  stage_macro_jacobian_transposed: y = J^T x with J = dR_E/dW the Jacobian of
+ *        the split Euler residual of the prediction step (Eqs. macroFluxSplitting,
+ *        forcingFunction; wall ghosts by Eq. boundaryWall) on level 0 at the
+ *        state W, Gamma frozen at W; W, x, y host arrays of nc x 4.  The
+ *        adjoint's macroscopic correction solves with this operator. */
+miugks_status miugks_stage_macro_jacobian_transposed(miugks_solver *s, const double *W, const double *x, double *y);
+/* Adjoint preconditioner options: macro_correction != 0 (default) adds to the
+ * transposed CS cycle the transpose of the prediction step's effect (the
+ * linearised forward iteration, prediction included, transposed: an inner
+ * Krylov solve with the transposed Jacobian of the split Euler residual;
+ * the outer solve is then flexible GMRES); 0 uses the transposed CS cycle alone. */
+miugks_status miugks_set_adjoint_options(miugks_solver *s, int macro_correction);
 miugks_status miugks_objective(miugks_solver *s, int obj, int bc, double *J, double *dJdf, double dJdtheta[3]);
 miugks_status miugks_adjoint(miugks_solver *s, int obj, int bc, int param, double tol, int max_iter, int restart,
                              double *grad, double info[3]);

@@ -1259,6 +1259,105 @@ __global__ void __launch_bounds__(256) k_mass_dot(LevelDev L, VelDev Vg, const d
     if (threadIdx.x == 0) part[c] = L.dx[i] * L.dy[j] * s[0];
 }
 
+// m_c = (dr_c / dW~_c)^T y_c: how the micro residual r = (g~(W~, q) - f) / tau(W~) of a cell
+// moves with its predicted state W~ (q held), contracted with y.  One CTA per cell.
+__global__ void __launch_bounds__(256) k_adj_macro_m(AdjDev A, const double* __restrict__ y, double* __restrict__ m)
+{
+    __shared__ double red[kRed * 6];
+    const VelDev& Vg = A.V;
+    const int nv = Vg.nv, tid = threadIdx.x, bs = blockDim.x, c = blockIdx.x;
+    const size_t nc = A.L.nc, snv = nv;
+    const double* fG = A.f + c * snv;
+    const double* fH = A.f + (nc + c) * snv;
+    const double* yG = y + c * snv;
+    const double* yH = y + (nc + c) * snv;
+    const double* W = A.W + 4 * (size_t)c;
+    const double* q = A.q + 2 * (size_t)c;
+    double rho, U, V, lam;
+    adj_prim(W, rho, U, V, lam);
+    const double T = 1.0 / lam;
+    const double itau = 1.0 / (A.gas.mu_ref * pow(T, A.gas.omega) / (0.5 * rho * T));
+    const double S = (1.0 - A.gas.pr) * 4.0 / 5.0 * lam * lam / rho;
+    double r[6] = {0, 0, 0, 0, 0, 0};       // rho, U, V, lam, S, itau adjoints
+    for (int k = tid; k < nv; k += bs) {
+        double u = Vg.u[k], v = Vg.v[k];
+        double cx = u - U, cy = v - V, c2 = cx * cx + cy * cy;
+        double gM = adj_maxw(rho, U, V, lam, u, v), hM = gM * kKint / (4.0 * lam);
+        double Fq = S * (cx * q[0] + cy * q[1]);
+        double eG = 2.0 * lam * c2 - 4.0, eH = 2.0 * lam * c2 - 2.0;
+        double gP = gM * (1.0 + Fq * eG), hP = hM * (1.0 + Fq * eH);
+        double a = yG[k], b = yH[k];
+        r[5] += a * (gP - fG[k]) + b * (hP - fH[k]);
+        double gPb = a * itau, hPb = b * itau;
+        double gMb = gPb * (1.0 + Fq * eG), hMb = hPb * (1.0 + Fq * eH);
+        double Fqb = gPb * gM * eG + hPb * hM * eH;
+        double eb = (gPb * gM + hPb * hM) * Fq;
+        r[3] += eb * 2.0 * c2;
+        double c2b = eb * 2.0 * lam;
+        r[4] += Fqb * (cx * q[0] + cy * q[1]);
+        r[1] -= Fqb * S * q[0] + 2.0 * cx * c2b;
+        r[2] -= Fqb * S * q[1] + 2.0 * cy * c2b;
+        adj_maxw_rev(gM, hM, rho, lam, cx, cy, gMb, hMb, r[0], r[1], r[2], r[3]);
+    }
+    red_sum<6>(r, red);
+    if (tid == 0) {
+        double rb = r[0], lb = r[3];
+        lb += r[4] * 2.0 * S / lam;
+        rb -= r[4] * S / rho;
+        rb += r[5] * itau / rho;
+        lb += r[5] * itau * (A.gas.omega - 1.0) / lam;
+        double Wb[4] = {0, 0, 0, 0};
+        adj_prim_rev(W, rb, r[1], r[2], lb, Wb);
+        for (int q2 = 0; q2 < 4; ++q2) m[4 * (size_t)c + q2] = Wb[q2];
+    }
+}
+
+// out -= Pi^T w: the moment weights of every velocity times the cell's 4-vector w
+__global__ void k_adj_macro_spread(LevelDev L, VelDev Vg, const double* __restrict__ w, double* __restrict__ out)
+{
+    const int c = blockIdx.x;
+    const size_t nc = L.nc, snv = Vg.nv;
+    const double w0 = w[4 * (size_t)c], w1 = w[4 * (size_t)c + 1], w2 = w[4 * (size_t)c + 2], w3 = w[4 * (size_t)c + 3];
+    for (int k = threadIdx.x; k < Vg.nv; k += blockDim.x) {
+        const double u = Vg.u[k], v = Vg.v[k], wk = Vg.w[k];
+        out[c * snv + k] -= wk * (w0 + u * w1 + v * w2 + 0.5 * (u * u + v * v) * w3);
+        out[(nc + c) * snv + k] -= wk * w3;
+    }
+}
+
+// partial sums of sum_c V_c w_c[0] (the closed-domain null direction of the transposed
+// split Euler Jacobian: total mass is conserved by every state)
+__global__ void __launch_bounds__(256) k_macro_null_dot(LevelDev L, const double* __restrict__ w, double* __restrict__ part)
+{
+    __shared__ double red[kRed];
+    double s[1] = {0.0};
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < L.nc; c += gridDim.x * blockDim.x) {
+        const int i = c % L.nx, j = c / L.nx;
+        s[0] += L.dx[i] * L.dy[j] * w[4 * (size_t)c];
+    }
+    red_sum<1>(s, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = s[0];
+}
+
+// w_c[0] -= coef V_c
+__global__ void k_macro_null_sub(LevelDev L, double coef, double* __restrict__ w)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= L.nc) return;
+    w[4 * (size_t)c] -= coef * L.dx[c % L.nx] * L.dy[c / L.nx];
+}
+
+// z_c = binv_c r_c (4x4 blocks)
+__global__ void k_block_apply(int nc, const double* __restrict__ binv, const double* __restrict__ r,
+                              double* __restrict__ z)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    const double* B = binv + 16 * (size_t)c;
+    const double* x = r + 4 * (size_t)c;
+    for (int a = 0; a < 4; ++a) z[4 * (size_t)c + a] = B[a * 4] * x[0] + B[a * 4 + 1] * x[1] + B[a * 4 + 2] * x[2] + B[a * 4 + 3] * x[3];
+}
+
 template <typename F>
 __global__ void k_to_double(const F* __restrict__ a, double* __restrict__ b, size_t n)
 {
@@ -1389,6 +1488,37 @@ cudaError_t launch_to_double(const F* a, double* b, size_t n, cudaStream_t st)
 }
 template cudaError_t launch_to_double<float>(const float*, double*, size_t, cudaStream_t);
 template cudaError_t launch_to_double<double>(const double*, double*, size_t, cudaStream_t);
+
+cudaError_t launch_adjoint_macro_m(const AdjDev& A, const double* y, double* m, cudaStream_t st)
+{
+    k_adj_macro_m<<<A.L.nc, 256, 0, st>>>(A, y, m);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_macro_spread(const LevelDev& L, const VelDev& V, const double* w, double* out,
+                                        cudaStream_t st)
+{
+    k_adj_macro_spread<<<L.nc, 256, 0, st>>>(L, V, w, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_macro_null_dot(const LevelDev& L, const double* w, double* part, int nblk, cudaStream_t st)
+{
+    k_macro_null_dot<<<nblk, 256, 0, st>>>(L, w, part);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_macro_null_sub(const LevelDev& L, double coef, double* w, cudaStream_t st)
+{
+    k_macro_null_sub<<<(L.nc + 127) / 128, 128, 0, st>>>(L, coef, w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_apply(int nc, const double* binv, const double* r, double* z, cudaStream_t st)
+{
+    k_block_apply<<<(nc + 127) / 128, 128, 0, st>>>(nc, binv, r, z);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_adjoint_invD(const LevelDev& L, const VelDev& V, const double* it, double* invD, cudaStream_t st)
 {

@@ -33,6 +33,10 @@ cudaError_t launch_macro_gamma(const MacroArgs& a, const double* Wg, double* gx,
 // mode 0: out = Rin - R_E(W)  (forcing);  mode 1: out = Rin + R_E(W)  (renewal P + R_E)
 cudaError_t launch_macro_resid(const MacroArgs& a, const double* W, const double* gx, const double* gy,
                                const double* Rin, double* out, int mode, cudaStream_t st);
+// y = J^T x, J = dR_E/dW at W with Gamma frozen (gx, gy); x may be null (no product);
+// binv (16 per cell, may be null) receives the inverses of the transposed diagonal blocks
+cudaError_t launch_macro_jacT(const MacroArgs& a, const double* W, const double* gx, const double* gy,
+                              const double* x, double* y, double* binv, cudaStream_t st);
 // one LU-SGS pass: dW from R at state W; then W += dW.  F: arithmetic of the sweep
 // (double, or float with increments); rec: macro_rec_bytes(nx, ny, F == float) of scratch
 template <typename F>
@@ -137,5 +141,14 @@ cudaError_t launch_mass_dot(const LevelDev& L, const VelDev& V, const double* x,
 template <typename F> cudaError_t launch_to_double(const F* a, double* b, size_t n, cudaStream_t st);
 cudaError_t launch_inv_tau(const GasDev& gas, const double* W, int nc, double* it, cudaStream_t st);
 cudaError_t launch_adjoint_invD(const LevelDev& L, const VelDev& V, const double* it, double* invD, cudaStream_t st);
+// m_c = (dr_c/dW~_c)^T y_c (micro residual w.r.t. the predicted state, heat flux held)
+cudaError_t launch_adjoint_macro_m(const AdjDev& A, const double* y, double* m, cudaStream_t st);
+// out -= Pi^T w (moment weights times the cell 4-vectors)
+cudaError_t launch_adjoint_macro_spread(const LevelDev& L, const VelDev& V, const double* w, double* out,
+                                        cudaStream_t st);
+cudaError_t launch_block_apply(int nc, const double* binv, const double* r, double* z, cudaStream_t st);
+// closed domains: partial sums of sum_c V_c w_c[0], and w_c[0] -= coef V_c
+cudaError_t launch_macro_null_dot(const LevelDev& L, const double* w, double* part, int nblk, cudaStream_t st);
+cudaError_t launch_macro_null_sub(const LevelDev& L, double coef, double* w, cudaStream_t st);
 
 } // namespace miugks

@@ -225,6 +225,104 @@ __global__ void k_macro_resid(MacroArgs a, const double* __restrict__ W, const d
     }
 }
 
+// Jacobian of the Euler flux T(W) . n, n = sgn e_axis, with p = 2 e_int / (K + 2):
+// A[r * 4 + c] = dT_r / dW_c
+__device__ void euler_jac(const double* W, int axis, double sgn, double A[16])
+{
+    const double rho = W[0], u = W[1] / rho, v = W[2] / rho;
+    const double g1 = 2.0 / (kKint + 2.0), gam = 1.0 + g1;
+    const double q2 = u * u + v * v, p = g1 * (W[3] - 0.5 * rho * q2), H = (W[3] + p) / rho;
+    const double nx = axis == 0 ? sgn : 0.0, ny = axis == 1 ? sgn : 0.0, Un = u * nx + v * ny;
+    A[0] = 0.0; A[1] = nx; A[2] = ny; A[3] = 0.0;
+    A[4] = -u * Un + nx * g1 * 0.5 * q2; A[5] = Un + u * nx - g1 * u * nx; A[6] = u * ny - g1 * v * nx; A[7] = g1 * nx;
+    A[8] = -v * Un + ny * g1 * 0.5 * q2; A[9] = v * nx - g1 * u * ny; A[10] = Un + v * ny - g1 * v * ny; A[11] = g1 * ny;
+    A[12] = Un * (g1 * 0.5 * q2 - H); A[13] = H * nx - g1 * u * Un; A[14] = H * ny - g1 * v * Un; A[15] = gam * Un;
+}
+
+// y = J^T x with J = dR_E/dW at W (Gamma frozen in gx, gy): R_E,c = -(1/V_c) sum_f S F_split,
+// so dR_E,c/dW_c = -(1/V_c) sum_f S (A_n(W_c) + Gamma) / 2 (plus (A_n(W_g) - Gamma) dB/dW / 2
+// at a boundary face), and a neighbour nb across face f holds dR_E,nb/dW_c =
+// (S / V_nb) (A_n(W_c) + Gamma) / 2 (n the outward normal of c).  One thread per
+// cell; binv (when not null) receives the inverse of the transposed diagonal block.
+__global__ void k_macro_jacT(MacroArgs a, const double* __restrict__ W, const double* __restrict__ gx,
+                             const double* __restrict__ gy, const double* __restrict__ x, double* __restrict__ y,
+                             double* __restrict__ binv)
+{
+    const LevelDev& L = a.L;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= L.nc) return;
+    const int nx = L.nx, i = c % nx, j = c / nx;
+    const double* Wc = W + 4 * (size_t)c;
+    const double Vc = L.dx[i] * L.dy[j];
+    double D[16], yc[4] = {0, 0, 0, 0}, A[16];
+    for (int q = 0; q < 16; ++q) D[q] = 0.0;
+    for (int f = 0; f < 4; ++f) {
+        const int axis = f >> 1, up = f & 1;
+        const double sgn = up ? 1.0 : -1.0, S = axis == 0 ? L.dy[j] : L.dx[i];
+        int bcid, nb; double dum = 0;
+        face_of(L, i, j, f, bcid, nb, dum);
+        const double gm = face_gamma(L, gx, gy, i, j, f);
+        euler_jac(Wc, axis, sgn, A);
+        for (int r = 0; r < 4; ++r)
+            for (int q = 0; q < 4; ++q) D[r * 4 + q] -= S / Vc * 0.5 * (A[r * 4 + q] + (r == q ? gm : 0.0));
+        if (bcid >= 0) {
+            double G[4], M[16], Ag[16];
+            macro_ghost(a.bc[bcid], axis, Wc, G, M);
+            euler_jac(G, axis, sgn, Ag);
+            for (int r = 0; r < 4; ++r)
+                for (int q = 0; q < 4; ++q) {
+                    double acc = 0.0;
+                    for (int t = 0; t < 4; ++t) acc += (Ag[r * 4 + t] - (r == t ? gm : 0.0)) * M[t * 4 + q];
+                    D[r * 4 + q] -= S / Vc * 0.5 * acc;
+                }
+        } else if (x) {
+            const int ni = nb % nx, nj = nb / nx;
+            const double Vn = L.dx[ni] * L.dy[nj];
+            const double* xn = x + 4 * (size_t)nb;
+            for (int q = 0; q < 4; ++q) {
+                double acc = 0.0;
+                for (int r = 0; r < 4; ++r) acc += (A[r * 4 + q] + (r == q ? gm : 0.0)) * xn[r];
+                yc[q] += S / Vn * 0.5 * acc;
+            }
+        }
+    }
+    if (x) {
+        const double* xc = x + 4 * (size_t)c;
+        for (int q = 0; q < 4; ++q) {
+            double acc = yc[q];
+            for (int r = 0; r < 4; ++r) acc += D[r * 4 + q] * xc[r];
+            y[4 * (size_t)c + q] = acc;
+        }
+    }
+    if (binv) {
+        // Gauss-Jordan on the 4x4 transposed block with partial pivoting
+        double Mx[4][8];
+        for (int r = 0; r < 4; ++r)
+            for (int q = 0; q < 4; ++q) { Mx[r][q] = D[q * 4 + r]; Mx[r][4 + q] = r == q ? 1.0 : 0.0; }
+        for (int col = 0; col < 4; ++col) {
+            int piv = col;
+            for (int r = col + 1; r < 4; ++r) if (fabs(Mx[r][col]) > fabs(Mx[piv][col])) piv = r;
+            for (int q = 0; q < 8; ++q) { double t = Mx[col][q]; Mx[col][q] = Mx[piv][q]; Mx[piv][q] = t; }
+            const double ip = 1.0 / Mx[col][col];
+            for (int q = 0; q < 8; ++q) Mx[col][q] *= ip;
+            for (int r = 0; r < 4; ++r) {
+                if (r == col) continue;
+                const double fct = Mx[r][col];
+                for (int q = 0; q < 8; ++q) Mx[r][q] -= fct * Mx[col][q];
+            }
+        }
+        for (int r = 0; r < 4; ++r)
+            for (int q = 0; q < 4; ++q) binv[16 * (size_t)c + r * 4 + q] = Mx[r][4 + q];
+    }
+}
+
+cudaError_t launch_macro_jacT(const MacroArgs& a, const double* W, const double* gx, const double* gy,
+                              const double* x, double* y, double* binv, cudaStream_t st)
+{
+    k_macro_jacT<<<(a.L.nc + 127) / 128, 128, 0, st>>>(a, W, gx, gy, x, y, binv);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_macro_resid(const MacroArgs& a, const double* W, const double* gx, const double* gy,
                                const double* Rin, double* out, int mode, cudaStream_t st)
 {

@@ -93,6 +93,13 @@ struct miugks_solver {
             double* pw = nullptr;
         } lv[kMaxLevels];
         bool lv_alloc = false;
+        // macroscopic correction of the preconditioner (transposed prediction step): Gamma at the
+        // checkpoint, inverse transposed diagonal blocks of dR_E/dW, 4-vectors and the inner basis
+        double *gx = nullptr, *gy = nullptr, *idiag = nullptr, *binv = nullptr;
+        double *m4 = nullptr, *w4 = nullptr, *t4 = nullptr, *Vi = nullptr;
+        double* Zb = nullptr;                 // flexible-GMRES preconditioned basis
+        int mz = 0;
+        bool macro = true;                    // apply the macroscopic correction
     } adj;
 };
 
@@ -1172,6 +1179,9 @@ miugks_status miugks_stage_prolong(miugks_solver* s, int lev, int m, const doubl
 namespace {
 
 constexpr int kDotBlocks = 608;
+constexpr int kInnerRestart = 20;           // basis of the inner (macroscopic) Krylov solve of the adjoint
+constexpr int kInnerIters = 40;
+constexpr double kInnerTol = 1e-2;
 
 bool closed_domain(const miugks_solver* s)
 {
@@ -1199,16 +1209,25 @@ miugks_status adj_prepare(miugks_solver* s, int m)
         ST(dalloc(s, &A.part, (size_t)kDotBlocks * 33 + L0.nc));
         ST(dalloc(s, &A.fpart, 4 * (size_t)(L0.nfx + L0.nfy)));
         ST(dalloc(s, &A.faces, (size_t)(L0.nfx + L0.nfy)));
+        ST(dalloc(s, &A.gx, (size_t)L0.nfx)); ST(dalloc(s, &A.gy, (size_t)L0.nfy));
+        ST(dalloc(s, &A.idiag, (size_t)L0.nc)); ST(dalloc(s, &A.binv, 16 * (size_t)L0.nc));
+        ST(dalloc(s, &A.m4, 4 * (size_t)L0.nc)); ST(dalloc(s, &A.w4, 8 * (size_t)L0.nc));
+        ST(dalloc(s, &A.t4, 4 * (size_t)L0.nc));
+        ST(dalloc(s, &A.Vi, (size_t)(kInnerRestart + 1) * 4 * L0.nc));
         A.alloc = true;
     }
     if (m > A.m) {
         ST(dalloc(s, &A.Vb, (size_t)(m + 1) * n));
+        ST(dalloc(s, &A.Zb, (size_t)m * n));
         A.m = m;
     }
     if (s->mixed) CK(launch_to_double<float>((const float*)s->f, A.f, n, s->st));
     else CK(cudaMemcpyAsync(A.f, s->f, n * sizeof(double), cudaMemcpyDeviceToDevice, s->st));
     CK(launch_moments<double>(L0.dev, s->vel, A.f, A.W, A.q, s->st));
     CK(launch_inv_tau(s->gas, A.W, L0.nc, A.itau, s->st));
+    MacroArgs ma = macro_args(s, 0, 0.0);
+    CK(launch_macro_gamma(ma, A.W, A.gx, A.gy, A.idiag, s->st));
+    CK(launch_macro_jacT(ma, A.W, A.gx, A.gy, nullptr, nullptr, A.binv, s->st));
     return adj_prepare_levels(s);
 }
 
@@ -1367,11 +1386,93 @@ miugks_status sum_parts(miugks_solver* s, int nblk, int m, double* out)
     return MIUGKS_OK;
 }
 
-miugks_status vdots(miugks_solver* s, const double* Vb, int m, const double* w, double* out)
+miugks_status vdots_n(miugks_solver* s, const double* Vb, int m, size_t n, const double* w, double* out)
 {
-    const size_t n = 2 * (size_t)s->lev[0].nc * s->nv;
     CK(launch_multi_dot(Vb, m, n, w, s->adj.part, kDotBlocks, s->st));
     return sum_parts(s, kDotBlocks, m, out);
+}
+
+miugks_status vdots(miugks_solver* s, const double* Vb, int m, const double* w, double* out)
+{
+    return vdots_n(s, Vb, m, 2 * (size_t)s->lev[0].nc * s->nv, w, out);
+}
+
+
+// w ~ J^{-T} m with J = dR_E/dW at the checkpoint (Gamma frozen there): restarted GMRES,
+// right-preconditioned by the inverse transposed diagonal blocks, to kInnerTol
+miugks_status macro_solve_T(miugks_solver* s, const double* m, double* w)
+{
+    auto& A = s->adj;
+    HLevel& L0 = s->lev[0];
+    const size_t n = 4 * (size_t)L0.nc, nb = n * sizeof(double);
+    const int mi = kInnerRestart;
+    MacroArgs ma = macro_args(s, 0, 0.0);
+    CK(cudaMemsetAsync(w, 0, nb, s->st));
+    double bn;
+    ST(vdots_n(s, m, 1, n, m, &bn));
+    bn = std::sqrt(bn);
+    if (!(bn > 0)) return MIUGKS_OK;
+    std::vector<double> H((size_t)(mi + 1) * mi), cs(mi), sn(mi), g(mi + 1), y(mi), h(mi + 1), h2(mi + 1);
+    int it = 0;
+    double rel = 1.0;
+    while (it < kInnerIters && rel > kInnerTol) {
+        double* V0 = A.Vi;
+        CK(launch_macro_jacT(ma, A.W, A.gx, A.gy, w, A.t4, nullptr, s->st));
+        CK(cudaMemcpyAsync(V0, m, nb, cudaMemcpyDeviceToDevice, s->st));
+        CK(launch_axpy(V0, A.t4, -1.0, n, s->st));
+        double beta;
+        ST(vdots_n(s, V0, 1, n, V0, &beta));
+        beta = std::sqrt(beta);
+        rel = beta / bn;
+        if (rel <= kInnerTol) break;
+        CK(launch_multi_axpy(nullptr, 0, n, nullptr, 1.0 / beta, V0, s->st));
+        std::fill(g.begin(), g.end(), 0.0);
+        g[0] = beta;
+        int jdone = 0;
+        for (int j = 0; j < mi && it < kInnerIters; ++j) {
+            double* Vj = A.Vi + (size_t)j * n;
+            double* Vn = A.Vi + (size_t)(j + 1) * n;
+            CK(launch_block_apply(L0.nc, A.binv, Vj, A.w4, s->st));
+            CK(launch_macro_jacT(ma, A.W, A.gx, A.gy, A.w4, Vn, nullptr, s->st));
+            ST(vdots_n(s, A.Vi, j + 1, n, Vn, h.data()));
+            for (int q = 0; q <= j; ++q) h2[q] = -h[q];
+            CK(launch_multi_axpy(A.Vi, j + 1, n, h2.data(), 1.0, Vn, s->st));
+            ST(vdots_n(s, A.Vi, j + 1, n, Vn, h2.data()));
+            for (int q = 0; q <= j; ++q) { h[q] += h2[q]; h2[q] = -h2[q]; }
+            CK(launch_multi_axpy(A.Vi, j + 1, n, h2.data(), 1.0, Vn, s->st));
+            double hn;
+            ST(vdots_n(s, Vn, 1, n, Vn, &hn));
+            hn = std::sqrt(hn);
+            h[j + 1] = hn;
+            if (hn > 0) CK(launch_multi_axpy(nullptr, 0, n, nullptr, 1.0 / hn, Vn, s->st));
+            for (int q = 0; q < j; ++q) {
+                double a = cs[q] * h[q] + sn[q] * h[q + 1];
+                h[q + 1] = -sn[q] * h[q] + cs[q] * h[q + 1];
+                h[q] = a;
+            }
+            double rr = std::hypot(h[j], h[j + 1]);
+            cs[j] = rr > 0 ? h[j] / rr : 1.0;
+            sn[j] = rr > 0 ? h[j + 1] / rr : 0.0;
+            h[j] = rr;
+            h[j + 1] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            for (int q = 0; q <= j; ++q) H[(size_t)q * mi + j] = h[q];
+            ++it;
+            jdone = j + 1;
+            rel = std::fabs(g[j + 1]) / bn;
+            if (rel <= kInnerTol || hn == 0.0) break;
+        }
+        for (int q = jdone - 1; q >= 0; --q) {
+            double a = g[q];
+            for (int p2 = q + 1; p2 < jdone; ++p2) a -= H[(size_t)q * mi + p2] * y[p2];
+            y[q] = a / H[(size_t)q * mi + q];
+        }
+        CK(launch_multi_axpy(A.Vi, jdone, n, y.data(), 0.0, A.t4, s->st));
+        CK(launch_block_apply(L0.nc, A.binv, A.t4, A.w4, s->st));
+        CK(launch_axpy(w, A.w4, 1.0, n, s->st));
+    }
+    return MIUGKS_OK;
 }
 
 // out = B v = -((dN/df)^T v - m (m . v)/|m|^2 in a closed domain)
@@ -1393,9 +1494,34 @@ miugks_status apply_B(miugks_solver* s, const double* v, double* out, double mm)
 
 // preconditioner of the adjoint solve: the transposed CS cycle of the solver's
 // own multigrid (one transposed LU-SGS pass on a single grid)
+//
+// With the macroscopic correction the preconditioner is the transpose of the
+// forward iteration's linearisation, prediction included: the forward step is
+// df = M r with r = N + (dr/dW~) dW~ and dW~ = -J^{-1} R, R ~ Pi N (the moments of
+// the residual), so P = M (I - (dr/dW~) J^{-1} Pi) and
+//   P^T z = y - Pi^T J^{-T} (dr/dW~)^T y,   y = M^T z.
+// The inner solve with J^T is inexact, so the outer Krylov method is flexible GMRES.
 miugks_status apply_PT(miugks_solver* s, const double* r, double* out)
 {
-    return cs_T(s, 0, r, out);
+    ST(cs_T(s, 0, r, out));
+    if (!s->adj.macro) return MIUGKS_OK;
+    auto& A = s->adj;
+    HLevel& L0 = s->lev[0];
+    double* w = A.w4 + 4 * (size_t)L0.nc;
+    CK(launch_adjoint_macro_m(adj_dev(s), out, A.m4, s->st));
+    ST(macro_solve_T(s, A.m4, w));
+    if (closed_domain(s)) {
+        // the total mass is a null direction of J^T there (V_c in the density of every cell):
+        // keep w orthogonal to it, or the inexact inner solve can drift along it
+        CK(launch_macro_null_dot(L0.dev, w, A.part, 64, s->st));
+        double wn, nn = 0.0;
+        ST(sum_parts(s, 64, 1, &wn));
+        for (int j = 0; j < L0.ny; ++j)
+            for (int i = 0; i < L0.nx; ++i) nn += (L0.dx[i] * L0.dy[j]) * (L0.dx[i] * L0.dy[j]);
+        CK(launch_macro_null_sub(L0.dev, wn / nn, w, s->st));
+    }
+    CK(launch_adjoint_macro_spread(L0.dev, s->vel, w, out, s->st));
+    return MIUGKS_OK;
 }
 
 miugks_status wall_face_list(miugks_solver* s, int bc, int* nfaces)
@@ -1468,6 +1594,36 @@ miugks_status miugks_stage_sgs_micro_transposed(miugks_solver* s, const double* 
     ST(sweep_T(s, 0, s->adj.b, s->adj.x));
     CK(cudaMemcpyAsync(x, s->adj.x, n * sizeof(double), cudaMemcpyDeviceToHost, s->st));
     CK(cudaStreamSynchronize(s->st));
+    return MIUGKS_OK;
+}
+
+miugks_status miugks_set_adjoint_options(miugks_solver* s, int macro_correction)
+{
+    if (!s) return MIUGKS_EINVAL;
+    s->adj.macro = macro_correction != 0;
+    return MIUGKS_OK;
+}
+
+miugks_status miugks_stage_macro_jacobian_transposed(miugks_solver* s, const double* W, const double* x, double* y)
+{
+    if (!s || !W || !x || !y) return MIUGKS_EINVAL;
+    HLevel& L0 = s->lev[0];
+    const size_t n4 = 4 * (size_t)L0.nc;
+    // scratch for this test stage only, released before returning
+    const size_t tot = 3 * n4 + (size_t)L0.nfx + L0.nfy + L0.nc;
+    double* buf = nullptr;
+    cudaError_t e = cudaMalloc(&buf, tot * sizeof(double));
+    if (e != cudaSuccess) return fail(s, MIUGKS_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e));
+    double *dW = buf, *dx = dW + n4, *dy = dx + n4, *gx = dy + n4, *gy = gx + L0.nfx, *id = gy + L0.nfy;
+    MacroArgs ma = macro_args(s, 0, 0.0);
+    e = cudaMemcpyAsync(dW, W, n4 * sizeof(double), cudaMemcpyHostToDevice, s->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dx, x, n4 * sizeof(double), cudaMemcpyHostToDevice, s->st);
+    if (e == cudaSuccess) e = launch_macro_gamma(ma, dW, gx, gy, id, s->st);
+    if (e == cudaSuccess) e = launch_macro_jacT(ma, dW, gx, gy, dx, dy, nullptr, s->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(y, dy, n4 * sizeof(double), cudaMemcpyDeviceToHost, s->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+    cudaFree(buf);
+    if (e != cudaSuccess) return fail(s, MIUGKS_ECUDA, "macro_jacobian_transposed: %s", cudaGetErrorString(e));
     return MIUGKS_OK;
 }
 
@@ -1558,8 +1714,9 @@ miugks_status miugks_adjoint(miugks_solver* s, int obj, int bc, int param, doubl
         for (int j = 0; j < m && it < max_iter; ++j) {
             double* Vj = A.Vb + (size_t)j * n;
             double* Vn = A.Vb + (size_t)(j + 1) * n;
-            ST(apply_PT(s, Vj, A.z));
-            ST(apply_B(s, A.z, Vn, mm));
+            double* Zj = A.Zb + (size_t)j * n;       // flexible GMRES: keep the preconditioned vector
+            ST(apply_PT(s, Vj, Zj));
+            ST(apply_B(s, Zj, Vn, mm));
             // classical Gram-Schmidt, twice
             ST(vdots(s, A.Vb, j + 1, Vn, h.data()));
             for (int q = 0; q <= j; ++q) h2[q] = -h[q];
@@ -1597,9 +1754,8 @@ miugks_status miugks_adjoint(miugks_solver* s, int obj, int bc, int param, doubl
             for (int p2 = q + 1; p2 < jdone; ++p2) a -= H[(size_t)q * m + p2] * y[p2];
             y[q] = a / H[(size_t)q * m + q];
         }
-        CK(launch_multi_axpy(A.Vb, jdone, n, y.data(), 0.0, A.w, s->st));
-        ST(apply_PT(s, A.w, A.z));
-        CK(launch_axpy(A.x, A.z, 1.0, n, s->st));
+        CK(launch_multi_axpy(A.Zb, jdone, n, y.data(), 0.0, A.w, s->st));
+        CK(launch_axpy(A.x, A.w, 1.0, n, s->st));
     }
     // true relative residual of the final iterate
     if (bnorm > 0) {

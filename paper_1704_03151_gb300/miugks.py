@@ -91,6 +91,7 @@ def load():
         "miugks_save": [vp, ctypes.c_char_p], "miugks_load": [vp, ctypes.c_char_p],
         "miugks_macro_sweep_times": [vp, _P(_d), _P(_i)], "miugks_set_cycle": [vp, _i],
         "miugks_init_from_coarse": [vp, vp],
+        "miugks_set_adjoint_options": [vp, _i], "miugks_stage_macro_jacobian_transposed": [vp, vp, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -114,7 +115,8 @@ def exported_symbols():
             "miugks_stage_adjoint_residual", "miugks_stage_sgs_micro_transposed", "miugks_stage_cs_transposed",
             "miugks_objective",
             "miugks_adjoint", "miugks_residual_rms_noalloc", "miugks_save", "miugks_load",
-            "miugks_macro_sweep_times", "miugks_set_cycle", "miugks_init_from_coarse"]
+            "miugks_macro_sweep_times", "miugks_set_cycle", "miugks_init_from_coarse",
+            "miugks_set_adjoint_options", "miugks_stage_macro_jacobian_transposed"]
 
 
 def _ptr(a):
@@ -363,6 +365,17 @@ class Solver:
         out = np.zeros_like(z)
         self._check(self._lib.miugks_stage_cs_transposed(self.h, _ptr(it), _ptr(z), _ptr(out)))
         return out
+
+    def macro_jacobian_transposed(self, W, x):
+        """J^T x, J the Jacobian of the split Euler residual at W (Gamma frozen at W)."""
+        W = np.ascontiguousarray(W, dtype=np.float64)
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        y = np.zeros_like(x)
+        self._check(self._lib.miugks_stage_macro_jacobian_transposed(self.h, _ptr(W), _ptr(x), _ptr(y)))
+        return y
+
+    def set_adjoint_options(self, macro_correction=True):
+        self._check(self._lib.miugks_set_adjoint_options(self.h, 1 if macro_correction else 0))
 
     def objective(self, obj, bc):
         """J, dJ/df and dJ/d(T, u, v) of wall `bc` at the current f."""

@@ -247,3 +247,43 @@ def test_flat_plate_drag_gradient_matches_oracle(lib):
         gg, info = g.adjoint(obj, 0, param, tol=1e-13, max_iter=3000)
         assert info["converged"], info
         assert gg == pytest.approx(go, rel=1e-8, abs=1e-12), (obj, param, info)
+
+
+@pytest.mark.parametrize("name", ["stretched_cavity", "open_box", "couette_corners"])
+def test_macro_jacobian_transpose_dot_product(lib, name):
+    """J^T of the split Euler residual (the prediction step's operator, used by
+    the adjoint's macroscopic correction) against central differences of the
+    oracle's residual R_E(W) with Gamma frozen: <x, J v> = <J^T x, v>."""
+    case = CASES[name]()
+    o, g, rng = _pair(lib, case, 13)
+    W = np.column_stack([o.macro()[k] for k in ("rho",)])          # shape check only
+    m = o.macro()
+    rho, u, v, t = m["rho"], m["u"], m["v"], m["t"]
+    W = np.column_stack([rho, rho * u, rho * v, 0.5 * rho * (u * u + v * v) + 0.75 * rho * t])
+    for _ in range(3):
+        x = rng.normal(size=W.shape)
+        d = rng.normal(size=W.shape) * np.abs(W)
+        h = 1e-6
+        fd = (o.resid_macro(0, W + h * d, W) - o.resid_macro(0, W - h * d, W)) / (2 * h)
+        lhs = np.sum(x * fd)
+        rhs = np.sum(g.macro_jacobian_transposed(W, x) * d)
+        assert abs(lhs - rhs) < 1e-7 * max(1.0, abs(lhs)), (name, lhs, rhs)
+
+
+def test_macro_correction_keeps_the_gradient(lib):
+    """The preconditioner changes the Krylov path only: with and without the
+    macroscopic correction the adjoint gradient agrees with the oracle's."""
+    case, bc = _closed(), 2
+    o = oracle.Oracle(case)
+    o.init_uniform(1.0, 0.0, 0.0, 1.0)
+    o.step(300)
+    A = oracle.adjoint_matrix(o)
+    go, _ = oracle.adjoint_gradient(o, 0, bc, 1, A=A)
+    for corr in (True, False):
+        g = lib.Solver(case)
+        g.init_uniform(1.0, 0.0, 0.0, 1.0)
+        g.set_f(o.get_f())
+        g.set_adjoint_options(corr)
+        gg, info = g.adjoint(0, bc, 1, tol=1e-13, max_iter=3000)
+        assert info["converged"], (corr, info)
+        assert gg == pytest.approx(go, rel=1e-8), corr
