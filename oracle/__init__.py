@@ -40,7 +40,7 @@ def lib():
         P = ctypes.POINTER
         d, i, vp = ctypes.c_double, ctypes.c_int, ctypes.c_void_p
         L.oracle_create.restype = vp
-        L.oracle_create.argtypes = [i, i, vp, vp, vp, vp, i, vp, vp, i, i, d, d, d, d, i,
+        L.oracle_create.argtypes = [i, i, vp, vp, vp, vp, vp, i, vp, vp, i, i, d, d, d, d, i,
                                     d, d, d, i, i, i, i, d, d]
         L.oracle_last_error.restype = ctypes.c_char_p
         L.oracle_destroy.argtypes = [vp]
@@ -112,12 +112,15 @@ class Oracle:
         self.nc = self.nx * self.ny
         self._keep = [np.ascontiguousarray(case[k], dtype=np.float64) for k in ("x_nodes", "y_nodes")]
         self._keep += [np.ascontiguousarray(case[k], dtype=np.int32) for k in ("face_bc_x", "face_bc_y")]
+        solid = case.get("solid")
+        self.solid = None if solid is None else np.ascontiguousarray(solid, dtype=np.uint8).reshape(-1)
         bt = np.ascontiguousarray([b["type"] for b in case["bcs"]], dtype=np.int32)
         bv = np.ascontiguousarray([[b["rho"], b["u"], b["v"], b["t"]] for b in case["bcs"]], dtype=np.float64)
         self._keep += [bt, bv]
         vg, gas, mg = case["vgrid"], case["gas"], case["mg"]
         self.h = L.oracle_create(self.nx, self.ny, _p(self._keep[0]), _p(self._keep[1]), _p(self._keep[2]),
-                                 _p(self._keep[3]), len(bt), _p(bt), _p(bv),
+                                 _p(self._keep[3]), None if self.solid is None else _p(self.solid),
+                                 len(bt), _p(bt), _p(bv),
                                  vg["nu"], vg["nv"], vg["umin"], vg["umax"], vg["vmin"], vg["vmax"], vg["rule"],
                                  gas["kn"], gas["omega"], gas["pr"],
                                  mg["levels"], mg["nu1"], mg["nu2"], mg["nuc"], mg["cfl"], mg["dtn_growth"])

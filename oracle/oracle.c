@@ -44,6 +44,8 @@ typedef struct {
     int nx, ny, nc, nfx, nfy;
     double *xn, *yn, *xc, *yc, *dx, *dy;
     int *fbx, *fby;
+    unsigned char *solid; /* per cell: 1 inside a body (no state, never updated) */
+    int nfluid;
     /* FAS work (nc x 4) and CS work (2 x nc x nv) */
     double *Wn, *Wc, *Rc, *P, *RE, *dW, *Wtil;
     double *r, *df, *dl, *Ad, *inv_tau;
@@ -271,6 +273,17 @@ static int coarsen(const olev_t *F, olev_t *C)
     for (int J = 0; J <= C->ny; ++J) C->yn[J] = F->yn[2 * J];
     C->fbx = (int *)calloc(C->nfx, sizeof(int));
     C->fby = (int *)calloc(C->nfy, sizeof(int));
+    C->solid = (unsigned char *)calloc(C->nc, 1);
+    C->nfluid = 0;
+    for (int J = 0; J < C->ny; ++J)
+        for (int I = 0; I < C->nx; ++I) {
+            int ns = 0;
+            for (int b = 0; b < 2; ++b)
+                for (int a = 0; a < 2; ++a) ns += F->solid[(2 * J + b) * F->nx + 2 * I + a];
+            if (ns != 0 && ns != 4) return fail("solid cells must fill whole coarse cells (coarse cell %d,%d)", I, J);
+            C->solid[J * C->nx + I] = ns == 4;
+            C->nfluid += ns == 0;
+        }
     for (int J = 0; J < C->ny; ++J)
         for (int I = 0; I <= C->nx; ++I) {
             int a = F->fbx[(2 * J) * (F->nx + 1) + 2 * I], b = F->fbx[(2 * J + 1) * (F->nx + 1) + 2 * I];
@@ -292,11 +305,30 @@ static int cell_bfaces(const olev_t *Lv, int i, int j, int side, bface_t *bf)
 {
     int n = 0, nx = Lv->nx;
     double V = Lv->dx[i] * Lv->dy[j];
-    if (side != 1 && i == 0) bf[n++] = (bface_t){Lv->fbx[j * (nx + 1)], 0, -1, Lv->dy[j], V};
-    if (side != 1 && j == 0) bf[n++] = (bface_t){Lv->fby[i], 1, -1, Lv->dx[i], V};
-    if (side != 0 && i == nx - 1) bf[n++] = (bface_t){Lv->fbx[j * (nx + 1) + nx], 0, +1, Lv->dy[j], V};
-    if (side != 0 && j == Lv->ny - 1) bf[n++] = (bface_t){Lv->fby[(Lv->ny) * nx + i], 1, +1, Lv->dx[i], V};
+    int w = Lv->fbx[j * (nx + 1) + i], e = Lv->fbx[j * (nx + 1) + i + 1];
+    int so = Lv->fby[j * nx + i], no = Lv->fby[(j + 1) * nx + i];
+    if (side != 1 && w >= 0) bf[n++] = (bface_t){w, 0, -1, Lv->dy[j], V};
+    if (side != 1 && so >= 0) bf[n++] = (bface_t){so, 1, -1, Lv->dx[i], V};
+    if (side != 0 && e >= 0) bf[n++] = (bface_t){e, 0, +1, Lv->dy[j], V};
+    if (side != 0 && no >= 0) bf[n++] = (bface_t){no, 1, +1, Lv->dx[i], V};
     return n;
+}
+
+/* The fluid cell of boundary face (i, j) along `axis` (x-face i in 0..nx, or
+ * y-face j in 0..ny) and the sign of the face's outward normal seen from it:
+ * the face lies on the domain edge or between a fluid and a solid cell. */
+static void face_side(const olev_t *Lv, int axis, int i, int j, int *c, int *outsign)
+{
+    int nx = Lv->nx;
+    if (axis == 0) {
+        int lo_fluid = i > 0 && !Lv->solid[j * nx + i - 1];
+        *c = lo_fluid ? j * nx + i - 1 : j * nx + i;
+        *outsign = lo_fluid ? +1 : -1;
+    } else {
+        int lo_fluid = j > 0 && !Lv->solid[(j - 1) * nx + i];
+        *c = lo_fluid ? (j - 1) * nx + i : j * nx + i;
+        *outsign = lo_fluid ? +1 : -1;
+    }
 }
 
 /* ------------------------------------------------------------------ */
@@ -469,11 +501,17 @@ static void flux_stage(oracle_solver *s)
             double *pG = s->phx + (size_t)fi * nv, *pH = s->phx + (nfx + fi) * (size_t)nv;
             int bcid = Lv->fbx[fi];
             if (bcid >= 0) {
-                if (i == 0) boundary_face(s, bcid, 0, -1, j * nx, pG, pH, s->Fx + 4 * fi);
-                else boundary_face(s, bcid, 0, +1, j * nx + nx - 1, pG, pH, s->Fx + 4 * fi);
+                int c, os;
+                face_side(Lv, 0, i, j, &c, &os);
+                boundary_face(s, bcid, 0, os, c, pG, pH, s->Fx + 4 * fi);
                 continue;
             }
             int cL = j * nx + i - 1, cR = j * nx + i;
+            if (i == 0 || i == nx || Lv->solid[cL] || Lv->solid[cR]) { /* a face inside a body */
+                memset(s->Fx + 4 * fi, 0, 4 * sizeof(double));
+                for (int k = 0; k < nv; ++k) pG[k] = pH[k] = 0.0;
+                continue;
+            }
             int hasLL = (i - 1 > 0) && Lv->fbx[fi - 1] < 0;
             int hasRR = (i + 1 < nx) && Lv->fbx[fi + 1] < 0;
             interior_face(s, 0, hasLL ? cL - 1 : -1, cL, cR, hasRR ? cR + 1 : -1,
@@ -488,11 +526,17 @@ static void flux_stage(oracle_solver *s)
             double *pG = s->phy + (size_t)fi * nv, *pH = s->phy + (nfy + fi) * (size_t)nv;
             int bcid = Lv->fby[fi];
             if (bcid >= 0) {
-                if (j == 0) boundary_face(s, bcid, 1, -1, i, pG, pH, s->Fy + 4 * fi);
-                else boundary_face(s, bcid, 1, +1, (ny - 1) * nx + i, pG, pH, s->Fy + 4 * fi);
+                int c, os;
+                face_side(Lv, 1, i, j, &c, &os);
+                boundary_face(s, bcid, 1, os, c, pG, pH, s->Fy + 4 * fi);
                 continue;
             }
             int cL = (j - 1) * nx + i, cR = j * nx + i;
+            if (j == 0 || j == ny || Lv->solid[cL] || Lv->solid[cR]) {
+                memset(s->Fy + 4 * fi, 0, 4 * sizeof(double));
+                for (int k = 0; k < nv; ++k) pG[k] = pH[k] = 0.0;
+                continue;
+            }
             int hasLL = (j - 1 > 0) && Lv->fby[fi - nx] < 0;
             int hasRR = (j + 1 < ny) && Lv->fby[fi + nx] < 0;
             interior_face(s, 1, hasLL ? cL - nx : -1, cL, cR, hasRR ? cR + nx : -1,
@@ -508,7 +552,7 @@ static void flux_stage(oracle_solver *s)
             const double *FW = s->Fx + 4 * (j * (nx + 1) + i), *FE = FW + 4;
             const double *FS = s->Fy + 4 * (j * nx + i), *FN = s->Fy + 4 * ((j + 1) * nx + i);
             for (int m = 0; m < 4; ++m)
-                s->R[4 * c + m] = -(Lv->dy[j] * (FE[m] - FW[m]) + Lv->dx[i] * (FN[m] - FS[m])) / V;
+                s->R[4 * c + m] = Lv->solid[c] ? 0.0 : -(Lv->dy[j] * (FE[m] - FW[m]) + Lv->dx[i] * (FN[m] - FS[m])) / V;
         }
 }
 
@@ -639,6 +683,7 @@ static void resid_macro(const oracle_solver *s, const olev_t *Lv, const double *
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
             int c = j * nx + i;
+            if (Lv->solid[c]) { for (int m = 0; m < 4; ++m) RE[4 * c + m] = 0.0; continue; }
             double V = Lv->dx[i] * Lv->dy[j], gm[4], acc[4] = {0, 0, 0, 0};
             cell_gammas(s, Lv, Wg, i, j, gm);
             for (int f = 0; f < 4; ++f) {
@@ -697,6 +742,7 @@ static void sgs_macro(const oracle_solver *s, const olev_t *Lv, const double *W,
                 }
             }
             int c = j * nx + i;
+            if (Lv->solid[c]) { for (int m = 0; m < 4; ++m) dW[4 * c + m] = 0.0; continue; }
             double V = Lv->dx[i] * Lv->dy[j], gm[4];
             cell_gammas(s, Lv, Wg, i, j, gm);
             double diag = 0.0;
@@ -758,36 +804,72 @@ static void restrict_lv(const olev_t *F, const olev_t *C, int m, const double *f
         }
 }
 
-/* 1-D linear weights for a fine centre x in coarse cell I: the second coarse
- * cell is the neighbour on the side of x, or the one on the other side when
- * that neighbour does not exist (extrapolation, signed weights). */
-static void lin1d(const double *Xc, int n, int I, double x, int *N, double *wA, double *wN)
+static int fluid_at(const olev_t *C, int I, int J)
 {
-    int nb = x < Xc[I] ? I - 1 : I + 1;
-    if (nb < 0 || nb >= n) nb = x < Xc[I] ? I + 1 : I - 1;
-    if (nb < 0 || nb >= n) { *N = I; *wA = 1.0; *wN = 0.0; return; }
-    *N = nb;
-    *wA = (Xc[nb] - x) / (Xc[nb] - Xc[I]);
-    *wN = (x - Xc[I]) / (Xc[nb] - Xc[I]);
+    return I >= 0 && I < C->nx && J >= 0 && J < C->ny && !C->solid[J * C->nx + I];
+}
+
+/* Prolongation stencil of fine cell (i, j) in coarse cell (I, J): the coarse
+ * neighbour along each axis is the one on the side of the fine centre, or the
+ * one on the other side (extrapolation, signed weights) when that one lies
+ * outside the domain or in a body; with neither, the axis is constant.  When
+ * the diagonal cell of the two chosen neighbours lies in a body (a fine cell
+ * diagonal to a body's corner), the first pair of x- and y-options (preferred
+ * side first, x outer) whose three cells are fluid is taken; with none, the
+ * y-axis is dropped.  Without bodies this is the plain bilinear stencil with
+ * one-sided extrapolation at the domain edges. */
+static void stencil(const olev_t *F, const olev_t *C, int i, int j, int *IN, int *JN, double *wx, double *wy)
+{
+    int I = i / 2, J = j / 2;
+    double x = F->xc[i], y = F->yc[j];
+    int ox[2], oy[2], nox = 0, noy = 0;
+    int sx = x < C->xc[I] ? -1 : 1, sy = y < C->yc[J] ? -1 : 1;
+    for (int q = 0; q < 2; ++q) {
+        int a = I + (q == 0 ? sx : -sx), b = J + (q == 0 ? sy : -sy);
+        if (fluid_at(C, a, J)) ox[nox++] = a;
+        if (fluid_at(C, I, b)) oy[noy++] = b;
+    }
+    int ix = nox ? ox[0] : I, jy = noy ? oy[0] : J;
+    if (nox && noy && !fluid_at(C, ix, jy)) {
+        int found = 0;
+        for (int p = 0; p < nox && !found; ++p)
+            for (int q = 0; q < noy && !found; ++q)
+                if (fluid_at(C, ox[p], oy[q])) { ix = ox[p]; jy = oy[q]; found = 1; }
+        if (!found) jy = J;
+    }
+    *IN = ix; *JN = jy;
+    /* 1-D linear weights of the own and the neighbour centre */
+    wx[0] = 1.0; wx[1] = 0.0; wy[0] = 1.0; wy[1] = 0.0;
+    if (ix != I) { wx[0] = (C->xc[ix] - x) / (C->xc[ix] - C->xc[I]); wx[1] = (x - C->xc[I]) / (C->xc[ix] - C->xc[I]); }
+    if (jy != J) { wy[0] = (C->yc[jy] - y) / (C->yc[jy] - C->yc[J]); wy[1] = (y - C->yc[J]) / (C->yc[jy] - C->yc[J]); }
 }
 
 /* Bilinear prolongation from level l+1 to l (Eqs. prolongation, prolongationWeight):
  * on a rectilinear mesh the weights h_BC h_CD / S_ABCD etc. are the products of
- * the 1-D linear weights in each direction. */
-static void prolong_lv(const olev_t *F, const olev_t *C, int m, const double *coarse, double *fine)
+ * the 1-D linear weights in each direction.  Cells in a body receive zero (a
+ * correction), or their coarse cell's value with inject_solid (a state). */
+static void prolong_lv_s(const olev_t *F, const olev_t *C, int m, const double *coarse, double *fine, int inject_solid)
 {
     for (int j = 0; j < F->ny; ++j)
         for (int i = 0; i < F->nx; ++i) {
             int I = i / 2, J = j / 2, IN, JN;
-            double ax, bx, ay, by;
-            lin1d(C->xc, C->nx, I, F->xc[i], &IN, &ax, &bx);
-            lin1d(C->yc, C->ny, J, F->yc[j], &JN, &ay, &by);
-            const double *A = coarse + (size_t)(J * C->nx + I) * m, *B = coarse + (size_t)(J * C->nx + IN) * m;
-            const double *D = coarse + (size_t)(JN * C->nx + I) * m, *Cc = coarse + (size_t)(JN * C->nx + IN) * m;
             double *out = fine + (size_t)(j * F->nx + i) * m;
+            const double *A = coarse + (size_t)(J * C->nx + I) * m;
+            if (F->solid[j * F->nx + i]) {
+                for (int q = 0; q < m; ++q) out[q] = inject_solid ? A[q] : 0.0;
+                continue;
+            }
+            double wx[2], wy[2];
+            stencil(F, C, i, j, &IN, &JN, wx, wy);
+            const double *B = coarse + (size_t)(J * C->nx + IN) * m;
+            const double *D = coarse + (size_t)(JN * C->nx + I) * m, *Cc = coarse + (size_t)(JN * C->nx + IN) * m;
             for (int q = 0; q < m; ++q)
-                out[q] = ax * ay * A[q] + bx * ay * B[q] + ax * by * D[q] + bx * by * Cc[q];
+                out[q] = wx[0] * wy[0] * A[q] + wx[1] * wy[0] * B[q] + wx[0] * wy[1] * D[q] + wx[1] * wy[1] * Cc[q];
         }
+}
+static void prolong_lv(const olev_t *F, const olev_t *C, int m, const double *coarse, double *fine)
+{
+    prolong_lv_s(F, C, m, coarse, fine, 0);
 }
 
 /* FAS cycle (Eq. FASCYC): W_l <- FAS(l, W_l^n, R_l); lv->Wn holds W_l^n and
@@ -997,6 +1079,11 @@ static void sgs_micro(oracle_solver *s, const olev_t *Lv, const double *inv_tau,
                 }
             }
             int c = j * nx + i;
+            if (Lv->solid[c]) {
+                for (int cp = 0; cp < 2; ++cp)
+                    for (int k = 0; k < nv; ++k) AT(x, nc, nv, cp, c, k) = 0.0;
+                continue;
+            }
             double V = Lv->dx[i] * Lv->dy[j];
             for (int k = 0; k < nv; ++k) D[k] = Dii(s, Lv, i, j, inv_tau[c], k);
             for (int cp = 0; cp < 2; ++cp)
@@ -1040,6 +1127,11 @@ static void apply_micro(const oracle_solver *s, const olev_t *Lv, const double *
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
             int c = j * nx + i;
+            if (Lv->solid[c]) {
+                for (int cp = 0; cp < 2; ++cp)
+                    for (int k = 0; k < nv; ++k) AT(y, nc, nv, cp, c, k) = 0.0;
+                continue;
+            }
             double V = Lv->dx[i] * Lv->dy[j];
             bface_t bf[4];
             int nb = cell_bfaces(Lv, i, j, 2, bf);
@@ -1159,13 +1251,14 @@ static void moments(oracle_solver *s)
     }
 }
 
+/* RMS over the fluid cells (Eq. Residual_Def); R is zero in bodies */
 static void rms(const oracle_solver *s, double res[4])
 {
     size_t nc = s->lev[0].nc;
     for (int m = 0; m < 4; ++m) {
         double a = 0.0;
         for (size_t c = 0; c < nc; ++c) a += s->R[4 * c + m] * s->R[4 * c + m];
-        res[m] = sqrt(a / nc);
+        res[m] = sqrt(a / s->lev[0].nfluid);
     }
 }
 
@@ -1199,6 +1292,11 @@ static void one_iteration(oracle_solver *s, double res[4])
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
             int c = j * nx + i;
+            if (L0->solid[c]) {
+                for (int cp = 0; cp < 2; ++cp)
+                    for (int k = 0; k < nv; ++k) AT(L0->r, nc, nv, cp, c, k) = 0.0;
+                continue;
+            }
             double rho, U, V, lam;
             prim(L0->Wtil + 4 * c, &rho, &U, &V, &lam);
             double itau = 1.0 / tau_of(s, rho, lam);
@@ -1232,7 +1330,7 @@ static void one_iteration(oracle_solver *s, double res[4])
 /* ------------------------------------------------------------------ */
 
 oracle_solver *oracle_create(int nx, int ny, const double *xn, const double *yn,
-                             const int *face_bc_x, const int *face_bc_y,
+                             const int *face_bc_x, const int *face_bc_y, const unsigned char *solid,
                              int nbc, const int *bc_type, const double *bc_vals,
                              int nu, int nv, double umin, double umax,
                              double vmin, double vmax, int rule,
@@ -1295,10 +1393,21 @@ oracle_solver *oracle_create(int nx, int ny, const double *xn, const double *yn,
     L0->fby = (int *)malloc(L0->nfy * sizeof(int));
     memcpy(L0->fbx, face_bc_x, L0->nfx * sizeof(int));
     memcpy(L0->fby, face_bc_y, L0->nfy * sizeof(int));
+    L0->solid = (unsigned char *)calloc(L0->nc, 1);
+    if (solid)
+        for (int c = 0; c < L0->nc; ++c) L0->solid[c] = solid[c] != 0;
+    L0->nfluid = 0;
+    for (int c = 0; c < L0->nc; ++c) L0->nfluid += !L0->solid[c];
+    if (L0->nfluid == 0) { fail("no fluid cell"); oracle_destroy(s); return NULL; }
+    /* A face between two fluid cells is interior (id -1); a face between a
+     * fluid cell and a body or the domain edge needs a BC id; a face with no
+     * fluid cell on either side is inactive (set to -1). */
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i <= nx; ++i) {
-            int b = L0->fbx[j * (nx + 1) + i], bnd = (i == 0 || i == nx);
-            if (bnd ? (b < 0 || b >= nbc) : (b != -1)) {
+            int *b = &L0->fbx[j * (nx + 1) + i];
+            int fl = i > 0 && !L0->solid[j * nx + i - 1], fr = i < nx && !L0->solid[j * nx + i];
+            if (!fl && !fr) { *b = -1; continue; }
+            if ((fl && fr) ? (*b != -1) : (*b < 0 || *b >= nbc)) {
                 fail("x-face (%d,%d): boundary faces need a BC id, interior faces -1", i, j);
                 oracle_destroy(s);
                 return NULL;
@@ -1306,8 +1415,10 @@ oracle_solver *oracle_create(int nx, int ny, const double *xn, const double *yn,
         }
     for (int j = 0; j <= ny; ++j)
         for (int i = 0; i < nx; ++i) {
-            int b = L0->fby[j * nx + i], bnd = (j == 0 || j == ny);
-            if (bnd ? (b < 0 || b >= nbc) : (b != -1)) {
+            int *b = &L0->fby[j * nx + i];
+            int fl = j > 0 && !L0->solid[(j - 1) * nx + i], fr = j < ny && !L0->solid[j * nx + i];
+            if (!fl && !fr) { *b = -1; continue; }
+            if ((fl && fr) ? (*b != -1) : (*b < 0 || *b >= nbc)) {
                 fail("y-face (%d,%d): boundary faces need a BC id, interior faces -1", i, j);
                 oracle_destroy(s);
                 return NULL;
@@ -1337,7 +1448,7 @@ void oracle_destroy(oracle_solver *s)
     for (int l = 0; l < MAXL; ++l) {
         olev_t *Lv = &s->lev[l];
         free(Lv->xn); free(Lv->yn); free(Lv->xc); free(Lv->yc); free(Lv->dx); free(Lv->dy);
-        free(Lv->fbx); free(Lv->fby);
+        free(Lv->fbx); free(Lv->fby); free(Lv->solid);
         free(Lv->Wn); free(Lv->Wc); free(Lv->Rc); free(Lv->P); free(Lv->RE); free(Lv->dW); free(Lv->Wtil);
         free(Lv->r); free(Lv->df); free(Lv->dl); free(Lv->Ad); free(Lv->inv_tau);
     }
@@ -1449,13 +1560,8 @@ int oracle_get_wall(const oracle_solver *s, int bc, int *nf, double *p, double *
             int b = pass == 0 ? L0->fbx[fi] : L0->fby[fi];
             if (b != bc) continue;
             int axis = pass, outsign, c;
-            if (axis == 0) {
-                int i = fi % (nx + 1), j = fi / (nx + 1);
-                outsign = i == 0 ? -1 : 1; c = j * nx + (i == 0 ? 0 : nx - 1);
-            } else {
-                int i = fi % nx, j = fi / nx;
-                outsign = j == 0 ? -1 : 1; c = (j == 0 ? 0 : ny - 1) * nx + i;
-            }
+            if (axis == 0) face_side(L0, 0, fi % (nx + 1), fi / (nx + 1), &c, &outsign);
+            else face_side(L0, 1, fi % nx, fi / nx, &c, &outsign);
             boundary_face_f(s, bc, axis, outsign, c, fG, fH);
             double P = 0, T = 0, Q = 0, Uwt = axis == 0 ? B->v : B->u;
             for (int k = 0; k < nv; ++k) {
@@ -1972,6 +2078,7 @@ static void collision_adj(const oracle_solver *s, int c, const double *mu, doubl
 int oracle_steady_residual(oracle_solver *s, double *N)
 {
     olev_t *L0 = &s->lev[0];
+    if (L0->nfluid != L0->nc) return fail("adjoint: meshes with solid cells are not supported");
     int nx = L0->nx, ny = L0->ny, nv = s->nv;
     size_t nc = L0->nc;
     moments(s);
@@ -2006,6 +2113,7 @@ int oracle_steady_residual(oracle_solver *s, double *N)
 int oracle_adjoint_residual(oracle_solver *s, const double *mu, double *out)
 {
     olev_t *L0 = &s->lev[0];
+    if (L0->nfluid != L0->nc) return fail("adjoint: meshes with solid cells are not supported");
     int nx = L0->nx, ny = L0->ny, nv = s->nv;
     size_t nc = L0->nc;
     moments(s);
@@ -2068,6 +2176,7 @@ int oracle_adjoint_residual(oracle_solver *s, const double *mu, double *out)
 int oracle_objective(oracle_solver *s, int obj, int bc, double *J, double *dJdf, double *dJdth)
 {
     const olev_t *L0 = &s->lev[0];
+    if (L0->nfluid != L0->nc) return fail("adjoint: meshes with solid cells are not supported");
     int nx = L0->nx, ny = L0->ny, nv = s->nv;
     size_t nc = L0->nc;
     if (bc < 0 || bc >= s->nbc || s->bc[bc].type != ORC_BC_WALL) return fail("objective: BC %d is not a wall", bc);
@@ -2155,6 +2264,7 @@ int oracle_objective(oracle_solver *s, int obj, int bc, double *J, double *dJdf,
 int oracle_residual_dtheta(oracle_solver *s, int bc, int param, double *dN)
 {
     const olev_t *L0 = &s->lev[0];
+    if (L0->nfluid != L0->nc) return fail("adjoint: meshes with solid cells are not supported");
     int nx = L0->nx, ny = L0->ny, nv = s->nv;
     size_t nc = L0->nc;
     if (bc < 0 || bc >= s->nbc || s->bc[bc].type != ORC_BC_WALL) return fail("dtheta: BC %d is not a wall", bc);
@@ -2251,7 +2361,7 @@ int oracle_init_from_coarse(oracle_solver *s, const oracle_solver *c)
         if (fabs(C0->yn[j] - F1->yn[j]) > 1e-12 * (1.0 + fabs(F1->yn[j]))) return fail("init_from_coarse: y nodes differ");
     size_t ncC = C0->nc, ncF = s->lev[0].nc;
     for (int cp = 0; cp < 2; ++cp)
-        prolong_lv(&s->lev[0], &s->lev[1], s->nv, c->f + (size_t)cp * ncC * s->nv, s->f + (size_t)cp * ncF * s->nv);
+        prolong_lv_s(&s->lev[0], &s->lev[1], s->nv, c->f + (size_t)cp * ncC * s->nv, s->f + (size_t)cp * ncF * s->nv, 1);
     moments(s);
     s->iter = 0;
     return 0;

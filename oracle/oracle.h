@@ -36,7 +36,7 @@ typedef struct oracle_solver oracle_solver;
  * (bc_vals = nbc x {rho, u, v, T}), velocity grid, gas and multigrid options.
  * levels = 1 is the single-grid implicit UGKS (one smoothing per step). */
 oracle_solver *oracle_create(int nx, int ny, const double *xn, const double *yn,
-                             const int *face_bc_x, const int *face_bc_y,
+                             const int *face_bc_x, const int *face_bc_y, const unsigned char *solid,
                              int nbc, const int *bc_type, const double *bc_vals,
                              int nu, int nv, double umin, double umax,
                              double vmin, double vmax, int rule,

@@ -128,6 +128,81 @@ def flat_plate(kn=0.1, ma=0.2, nvel=48, vmax=5.0, levels=4, n_up=32, n_plate=64,
     }
 
 
+def body_face_ids(solid, fbx, fby, bc_id):
+    """Give every face between a fluid cell and a solid cell the BC id `bc_id`
+    and mark faces with no fluid cell on either side inactive (-1); returns
+    new (fbx, fby) arrays.  `solid` is (ny, nx)."""
+    solid = np.asarray(solid, dtype=bool)
+    ny, nx = solid.shape
+    fbx = np.asarray(fbx, dtype=np.int32).reshape(ny, nx + 1).copy()
+    fby = np.asarray(fby, dtype=np.int32).reshape(ny + 1, nx).copy()
+    fl = np.zeros((ny, nx + 1), dtype=bool)   # fluid cell on the lower side of x-face i
+    fr = np.zeros((ny, nx + 1), dtype=bool)
+    fl[:, 1:] = ~solid
+    fr[:, :-1] = ~solid
+    fbx[(fl ^ fr) & ~((np.arange(nx + 1) == 0) | (np.arange(nx + 1) == nx))[None, :]] = bc_id
+    fbx[~fl & ~fr] = -1
+    gl = np.zeros((ny + 1, nx), dtype=bool)
+    gr = np.zeros((ny + 1, nx), dtype=bool)
+    gl[1:, :] = ~solid
+    gr[:-1, :] = ~solid
+    fby[(gl ^ gr) & ~((np.arange(ny + 1) == 0) | (np.arange(ny + 1) == ny))[:, None]] = bc_id
+    fby[~gl & ~gr] = -1
+    return fbx.ravel(), fby.ravel()
+
+
+def square_cylinder(ma=5.0, kn=0.1, nvel=89, vmax=15.0, levels=4, nx_side=64, nx_sq=32, ny_side=48, ny_sq=24,
+                    half=7.5, omega=0.81, dtn_growth=3.0, rule=None):
+    """Flow past a unit square at the centre of the box [-half, half]^2
+    (Sec. 4.3, on the full domain): nx_side | nx_sq | nx_side cells in x and
+    ny_side | ny_sq | ny_side in y, uniform across the square and stretched
+    geometrically away from its faces (the first outer cell as wide as a square
+    cell).  The square's cells are solid.  BC ids: 0 square wall (T_w = T_inf),
+    1 farfield (inflow, top, bottom), 2 outflow (zero gradient, downstream).
+    The initial state is the freestream with a rear region x > 0.5 at 0.1 of
+    its density and at rest (`rear` key, see initial_fields)."""
+    gamma = 5.0 / 3.0
+    u_inf = ma * math.sqrt(gamma / 2.0)
+    hx, hy = 1.0 / nx_sq, 1.0 / ny_sq
+    x = np.concatenate([geometric_nodes(-half, -0.5, nx_side, hx, at_start=False),
+                        np.linspace(-0.5, 0.5, nx_sq + 1)[1:], geometric_nodes(0.5, half, nx_side, hx)[1:]])
+    y = np.concatenate([geometric_nodes(-half, -0.5, ny_side, hy, at_start=False),
+                        np.linspace(-0.5, 0.5, ny_sq + 1)[1:], geometric_nodes(0.5, half, ny_side, hy)[1:]])
+    nx, ny = len(x) - 1, len(y) - 1
+    solid = np.zeros((ny, nx), dtype=np.uint8)
+    solid[ny_side:ny_side + ny_sq, nx_side:nx_side + nx_sq] = 1
+    fbx, fby = edge_face_ids(nx, ny, 1, 2, 1, 1)
+    fbx, fby = body_face_ids(solid, fbx, fby, 0)
+    if rule is None:
+        rule = BOOLE if (nvel - 1) % 4 == 0 else TRAPEZOID
+    return {
+        "name": "square%dx%d_v%d_ma%g_kn%g" % (nx, ny, nvel, ma, kn),
+        "nx": nx, "ny": ny, "x_nodes": x, "y_nodes": y,
+        "face_bc_x": fbx, "face_bc_y": fby, "solid": solid.ravel(),
+        "bcs": [bc(WALL, t=1.0), bc(FARFIELD, rho=1.0, u=u_inf, v=0.0, t=1.0), bc(OUTFLOW)],
+        "vgrid": {"nu": nvel, "nv": nvel, "umin": -vmax, "umax": vmax, "vmin": -vmax, "vmax": vmax, "rule": rule},
+        "gas": {"kn": kn, "omega": omega, "pr": 2.0 / 3.0},
+        "mg": {"levels": levels, "nu1": 2, "nu2": 1, "nuc": 4, "cfl": 0.8, "dtn_growth": dtn_growth},
+        "init": {"rho": 1.0, "u": u_inf, "v": 0.0, "t": 1.0},
+        "rear": {"x": 0.5, "rho": 0.1, "u": 0.0, "v": 0.0, "t": 1.0},
+    }
+
+
+def initial_fields(case):
+    """Per-cell initial (rho, u, v, T): the uniform `init` state, with the
+    `rear` region (cell centres downstream of rear["x"]), if the case has one,
+    at its own state (Sec. 4.3)."""
+    nx, ny = case["nx"], case["ny"]
+    out = [np.full(nx * ny, float(case["init"][k])) for k in ("rho", "u", "v", "t")]
+    rear = case.get("rear")
+    if rear is not None:
+        xc = 0.5 * (np.asarray(case["x_nodes"])[1:] + np.asarray(case["x_nodes"])[:-1])
+        sel = np.broadcast_to(xc[None, :] > rear["x"], (ny, nx)).ravel()
+        for q, k in enumerate(("rho", "u", "v", "t")):
+            out[q][sel] = rear[k]
+    return out
+
+
 def coarsen_case(case):
     """The same problem on the next coarser mesh (every second grid line, as
     the multigrid levels of Sec. 3.1), with one multigrid level fewer: the
@@ -146,6 +221,12 @@ def coarsen_case(case):
     c["y_nodes"] = np.asarray(case["y_nodes"])[0::2].copy()
     c["face_bc_x"] = fbx[0::2, 0::2].ravel().copy()
     c["face_bc_y"] = fby[0::2, 0::2].ravel().copy()
+    if case.get("solid") is not None:
+        sol = np.asarray(case["solid"]).reshape(ny, nx)
+        blocks = sol.reshape(ny // 2, 2, nx // 2, 2).sum(axis=(1, 3))
+        if np.any((blocks != 0) & (blocks != 4)):
+            raise ValueError("solid cells do not fill whole coarse cells")
+        c["solid"] = (blocks == 4).astype(np.uint8).ravel()
     c["mg"] = dict(case["mg"], levels=case["mg"]["levels"] - 1)
     c["bcs"] = [dict(b) for b in case["bcs"]]
     return c
@@ -196,4 +277,5 @@ CONFIGS = {
     "c1": lambda: cavity(n=24, nvel=20, kn=1.0, lid=0.16, levels=1),
     "c2": lambda kn=1.0: cavity(n=64, nvel=32, kn=kn, lid=0.16, levels=3),
     "c3": lambda: flat_plate(),
+    "c4": lambda: square_cylinder(),
 }
