@@ -20,7 +20,8 @@
  * f dxi_z) with discrete velocity k = a*nv_v + b, u_k = u_a, v_k = v_b.
  * x-faces are indexed j*(nx+1) + i (between cells i-1 and i), y-faces
  * j*nx + i (between rows j-1 and j); a face BC id of -1 marks an interior face.
- * Only the outer edges of the rectangle may carry boundary ids.
+ * Boundary ids sit on the outer edges of the rectangle and on the faces of
+ * bodies (solid cells, see miugks_mesh).
  *
  * Ownership and errors.  The library owns all device memory of a solver; it
  * allocates through the caller's callbacks when given (the Python binding
@@ -59,12 +60,18 @@ typedef enum { MIUGKS_BC_WALL = 0, MIUGKS_BC_SYMMETRY = 1, MIUGKS_BC_FARFIELD = 
  * residual stay in double. */
 typedef enum { MIUGKS_FP64 = 0, MIUGKS_MIXED = 1 } miugks_precision;
 
-/* rectilinear mesh: x_nodes[nx+1], y_nodes[ny+1] increasing; face ids as above */
+/* rectilinear mesh: x_nodes[nx+1], y_nodes[ny+1] increasing; face ids as above.
+ * solid (nx*ny, NULL = none) marks cells inside bodies (the square cylinder of
+ * Sec. 4.3): they hold no state and are never updated.  A face between two
+ * fluid cells has id -1; a face between a fluid cell and a body or the domain
+ * edge needs a BC id; a face with no fluid cell on either side is ignored.
+ * With multigrid, bodies must fill whole cells of every coarse level. */
 typedef struct {
     int nx, ny;
     const double *x_nodes, *y_nodes;
     const int *face_bc_x;      /* (nx+1)*ny */
     const int *face_bc_y;      /* nx*(ny+1) */
+    const unsigned char *solid;
 } miugks_mesh;
 
 /* discrete velocities: nu x nv nodes, placed symmetrically on [umin,umax] x

@@ -920,7 +920,16 @@ static void fas_visit(oracle_solver *s, int l, int type, int first)
         for (size_t q = 0; q < c4; ++q) Cv->dW[q] = Cv->Wc[q] - Cv->Wn[q];
         double *corr = (double *)malloc(n4 * sizeof(double));
         prolong_lv(Lv, Cv, 4, Cv->dW, corr);
-        for (size_t q = 0; q < n4; ++q) Lv->Wc[q] += corr[q];
+        /* W_l += P dW_H; a correction that would leave a cell without positive
+         * density and internal energy is dropped there (reading: the paper is
+         * silent; at a strong shock the bilinear correction can overshoot) */
+        for (int c = 0; c < Lv->nc; ++c) {
+            double w[4];
+            for (int m = 0; m < 4; ++m) w[m] = Lv->Wc[4 * c + m] + corr[4 * c + m];
+            double e2 = w[3] * w[0] - 0.5 * (w[1] * w[1] + w[2] * w[2]);
+            if (w[0] > 0.0 && e2 > 0.0)
+                for (int m = 0; m < 4; ++m) Lv->Wc[4 * c + m] = w[m];
+        }
         free(corr);
         for (int m = 0; m < s->nu2; ++m) {
             resid_macro(s, Lv, Lv->Wc, Lv->Wn, Lv->RE);

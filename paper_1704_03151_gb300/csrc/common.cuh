@@ -32,9 +32,36 @@ struct VelDev {
 struct LevelDev {
     int nx, ny, nc, nfx, nfy;
     const double *xn, *yn, *xc, *yc, *dx, *dy;
-    const int *fbx, *fby;        // face BC id, -1 interior
+    const int *fbx, *fby;        // face BC id, -1 interior (or inactive: no fluid cell on either side)
     const double *rdx, *rdy;     // 1/dx, 1/dy
+    const unsigned char* solid;  // per cell: 1 inside a body (no state, never updated)
+    const int* ubc;              // fluid cells with a boundary face on the east or north side
+    int nubc;
 };
+
+// The fluid cell of boundary x-face (axis 0, i in 0..nx) or y-face (axis 1,
+// j in 0..ny) and the sign of the face's outward normal seen from it: the face
+// lies on the domain edge or between a fluid cell and a body.
+__device__ __forceinline__ void bface_side(const LevelDev& L, int axis, int i, int j, int& c, int& outsign)
+{
+    const int nx = L.nx;
+    if (axis == 0) {
+        const bool lo = i > 0 && !L.solid[j * nx + i - 1];
+        c = lo ? j * nx + i - 1 : j * nx + i;
+        outsign = lo ? 1 : -1;
+    } else {
+        const bool lo = j > 0 && !L.solid[(j - 1) * nx + i];
+        c = lo ? (j - 1) * nx + i : j * nx + i;
+        outsign = lo ? 1 : -1;
+    }
+}
+// a face without a BC id that does not join two fluid cells (inside a body)
+__device__ __forceinline__ bool inactive_face(const LevelDev& L, int axis, int i, int j)
+{
+    const int nx = L.nx;
+    if (axis == 0) return i == 0 || i == nx || L.solid[j * nx + i - 1] || L.solid[j * nx + i];
+    return j == 0 || j == L.ny || L.solid[(j - 1) * nx + i] || L.solid[j * nx + i];
+}
 
 struct GasDev { double mu_ref, omega, pr; };
 

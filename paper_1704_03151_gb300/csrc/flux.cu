@@ -155,8 +155,8 @@ __global__ void __launch_bounds__(256) k_face_flux(FaceFluxArgs<F> A)
 
     if (bcid >= 0) {
         // ---------------- boundary face: free transport of the face distribution
-        const int outsign = (axis == 0 ? i == 0 : j == 0) ? -1 : 1;
-        const int c = axis == 0 ? j * nx + (i == 0 ? 0 : nx - 1) : (j == 0 ? 0 : ny - 1) * nx + i;
+        int outsign, c;
+        bface_side(L, axis, i, j, c, outsign);
         const BcDev B = A.bc[bcid];
         const double* Cb = A.Cw + (size_t)bcid * nv;
         const double Hfac = kKint * B.t / 4.0;   // K / (4 lambda_b)
@@ -197,6 +197,12 @@ __global__ void __launch_bounds__(256) k_face_flux(FaceFluxArgs<F> A)
         return;
     }
 
+    if (inactive_face(L, axis, i, j)) {   // inside a body: no flux
+        for (int k = tid; k < nv; k += bs) { phG[k] = F(0); phH[k] = F(0); }
+        if (tid == 0)
+            for (int m = 0; m < 4; ++m) A.Fm[4 * (size_t)fi + m] = 0.0;
+        return;
+    }
     // ---------------- interior face between cL (lower) and cR (upper)
     // Face constants are computed once (by one thread or one lane each) and
     // broadcast through shared memory as F: an FP64 instruction occupies a
@@ -430,6 +436,10 @@ __global__ void k_cell_residual(LevelDev L, const double* __restrict__ Fx, const
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= L.nc) return;
     int i = c % L.nx, j = c / L.nx;
+    if (L.solid[c]) {
+        for (int m = 0; m < 4; ++m) R[4 * (size_t)c + m] = 0.0;
+        return;
+    }
     double V = L.dx[i] * L.dy[j];
     const double* FW = Fx + 4 * (size_t)(j * (L.nx + 1) + i);
     const double* FE = FW + 4;
@@ -465,7 +475,7 @@ __global__ void k_rms_partial(const double* __restrict__ R, const double* __rest
         for (int m = 0; m < 5; ++m) part[5 * blockIdx.x + m] = s[m];
 }
 
-__global__ void k_rms_final(const double* __restrict__ part, int nblk, int nc, double* __restrict__ out)
+__global__ void k_rms_final(const double* __restrict__ part, int nblk, int nfluid, double* __restrict__ out)
 {
     __shared__ double red[32 * 5];
     double s[5] = {0, 0, 0, 0, 0};
@@ -473,16 +483,17 @@ __global__ void k_rms_final(const double* __restrict__ part, int nblk, int nc, d
         for (int m = 0; m < 5; ++m) s[m] += part[5 * b + m];
     block_sum<5>(s, red);
     if (threadIdx.x == 0) {
-        for (int m = 0; m < 4; ++m) out[m] = sqrt(s[m] / nc);
+        for (int m = 0; m < 4; ++m) out[m] = sqrt(s[m] / nfluid);
         out[4] = s[4];
     }
 }
 
-cudaError_t launch_rms(const double* R, const double* W, int nc, double* part, double* out, cudaStream_t st)
+// RMS over the fluid cells (R is zero in bodies)
+cudaError_t launch_rms(const double* R, const double* W, int nc, int nfluid, double* part, double* out, cudaStream_t st)
 {
     int nblk = 64;
     k_rms_partial<<<nblk, 256, 0, st>>>(R, W, nc, part);
-    k_rms_final<<<1, 64, 0, st>>>(part, nblk, nc, out);
+    k_rms_final<<<1, 64, 0, st>>>(part, nblk, nfluid, out);
     return cudaGetLastError();
 }
 

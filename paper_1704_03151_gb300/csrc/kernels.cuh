@@ -18,7 +18,7 @@ struct FaceFluxArgs {
 void upload_series_coefficients();
 template <typename F> cudaError_t launch_face_flux(const FaceFluxArgs<F>& a, cudaStream_t st);
 cudaError_t launch_cell_residual(const LevelDev& L, const double* Fx, const double* Fy, double* R, cudaStream_t st);
-cudaError_t launch_rms(const double* R, const double* W, int nc, double* part, double* out, cudaStream_t st);
+cudaError_t launch_rms(const double* R, const double* W, int nc, int nfluid, double* part, double* out, cudaStream_t st);
 
 // ---- prediction step (macroscopic state in FP64) ----
 struct MacroArgs {
@@ -53,13 +53,34 @@ template <typename T>
 cudaError_t launch_prolong_add(const LevelDev& F, const LevelDev& C, int m, int nblk, const int* idx4,
                                const double* w4, const T* coarse, T* fine, T* out_pro, cudaStream_t st);
 cudaError_t launch_axpy(double* y, const double* x, double a, size_t n, cudaStream_t st);
+// FAS correction W += P dWc of the [nc][4] state, dropped in a cell where it would
+// leave the density or the internal energy non-positive
+cudaError_t launch_prolong_state(const LevelDev& F, const int* idx4, const double* w4, const double* dWc, double* W,
+                                 cudaStream_t st);
 cudaError_t launch_sub(double* out, const double* a, const double* b, size_t n, cudaStream_t st);
 
 // ---- evolution step (microscopic) ----
+// The sweep order of one level (device tables, per pass 0 forward / 1 backward).
+// A boundary-line cell is a fluid cell with a boundary face on the sweep side:
+// the domain edge's column and row (a corner cell first), and the lines along
+// bodies.  Each such cell has a fold entry e (its ghost-folded inputs).
+struct SweepPlanDev {
+    const int* code[2];     // per cell: -1 ordinary, -2 in a body, else e << 2 | x-face line << 1 | y-face line
+    const int4* lcell[2];   // per fold entry: {cell, line axis (0 x-face, 1 y-face), wall-density slot, final}
+    const int* lines[2];    // lines along bodies: [q][8] = {i0, j0, di, dj, len, line axis, density slot, 0}
+    int nl[2];              // fold entries of the edge lines (the rest belong to body lines)
+    int nl_max;             // fold-entry stride of the layout
+};
+constexpr int kMaxBodyLines = 64;   // lines along bodies per pass and level
 struct MicroArgs {
     LevelDev L; VelDev V; const BcDev* bc; const double* Cw;
     const double* inv_tau;                 // [nc] collision frequency (+ 1/dt_n)
+    SweepPlanDev P;
 };
+// Host schedule of the body lines of one pass: after wave step dd - 1, the lines
+// q0 .. q0 + nq - 1 (fold entries e0 .. e0 + ne - 1) are walked and folded.
+struct SweepBreak { int dd, q0, nq, e0, ne; };
+struct SweepPlanHost { const SweepBreak* brk[2]; int nbrk[2]; };
 // Step 3-4: r = (g~ - f)/tau~ - div(ph) on level 0; also inv_tau (with dtn_inv) and invD
 template <typename F>
 cudaError_t launch_micro_residual(const MicroArgs& m, GasDev gas, const double* Wt, const double* q,
@@ -70,12 +91,12 @@ template <typename F>
 cudaError_t launch_coarse_coeffs(const MicroArgs& m, GasDev gas, const double* Wt, double dtn_inv,
                                  double* inv_tau, F* invD, cudaStream_t st);
 // one symmetric Gauss-Seidel pass: x = SGS(r).  Zw[b*4 + axis*2 + (outsign>0)] = sum over the
-// incoming velocities of w u_n C_k of wall BC b; xcorner: scratch of micro_scratch_elems(nv, nx + ny)
-// values (nx + ny of the finest level)
-size_t micro_scratch_elems(int nv, int nl);
+// incoming velocities of w u_n C_k of wall BC b; xcorner: scratch of
+// micro_scratch_elems(nv, nl_max, body lines) values (the largest over the levels)
+size_t micro_scratch_elems(int nv, int nl, int nlines);
 template <typename F>
-cudaError_t launch_micro_sgs(const MicroArgs& m, const double* Zw, const F* invD, const F* r, F* x, F* xcorner,
-                             cudaStream_t st);
+cudaError_t launch_micro_sgs(const MicroArgs& m, const SweepPlanHost& plan, const double* Zw, const F* invD,
+                             const F* r, F* x, F* xcorner, cudaStream_t st);
 // r -= A x (when renew) and acc += x (when acc != null)
 template <typename F>
 cudaError_t launch_micro_renew(const MicroArgs& m, const double* Zw, const F* x, F* r, F* acc, int renew,

@@ -25,6 +25,7 @@
 //     diagonals (no grid-wide synchronisation); the incoming velocities of
 //     line cells are ordinary updates there, their ghost term being known.
 #include "kernels.cuh"
+#include <algorithm>
 
 namespace cg = cooperative_groups;
 
@@ -158,6 +159,7 @@ __global__ void __launch_bounds__(256) k_micro_residual(MicroArgs M, GasDev gas,
     const F* __restrict__ vv = VelT<F>::v(Vg);
     const size_t nfx = L.nfx, nfy = L.nfy;
     const size_t fW = (size_t)j * (nx + 1) + i, fE = fW + 1, fS = (size_t)j * nx + i, fN = (size_t)(j + 1) * nx + i;
+    const bool body = L.solid[c];   // cells in a body: zero residual
     for (int k = threadIdx.x; k < nv; k += blockDim.x) {
         int a = k / Vg.nvv, b = k - a * Vg.nvv;
         const F u = vu[k], v = vv[k];
@@ -170,7 +172,7 @@ __global__ void __launch_bounds__(256) k_micro_residual(MicroArgs M, GasDev gas,
             const F* px = phx + cp * nfx * nv;
             const F* py = phy + cp * nfy * nv;
             F div = (px[fE * nv + k] - px[fW * nv + k]) * rdxi + (py[fN * nv + k] - py[fS * nv + k]) * rdyj;
-            r[(cp * nc + c) * nv + k] = (gt[cp] - f[(cp * nc + c) * nv + k]) * fitau - div;
+            r[(cp * nc + c) * nv + k] = body ? F(0) : (gt[cp] - f[(cp * nc + c) * nv + k]) * fitau - div;
         }
         invD[(size_t)c * nv + k] = recip(fdiag + geomD_r<F>(rdxi, rdyj, u, v));
     }
@@ -234,13 +236,17 @@ template cudaError_t launch_coarse_coeffs<float>(const MicroArgs&, GasDev, const
 // boundary faces of a cell on one sweep side (0 lower = west/south, 1 upper = east/north)
 struct BFace { int bc, axis, outsign; double rS; };   // rS = face area / cell volume
 
+// (of a fluid cell: its faces with a BC id, on the domain edge or on a body)
 __device__ __forceinline__ int side_faces(const LevelDev& L, int i, int j, int side, BFace* bf)
 {
-    int n = 0, nx = L.nx, ny = L.ny;
-    if (side != 1 && i == 0) bf[n++] = {L.fbx[j * (nx + 1)], 0, -1, L.rdx[i]};
-    if (side != 1 && j == 0) bf[n++] = {L.fby[i], 1, -1, L.rdy[j]};
-    if (side != 0 && i == nx - 1) bf[n++] = {L.fbx[j * (nx + 1) + nx], 0, 1, L.rdx[i]};
-    if (side != 0 && j == ny - 1) bf[n++] = {L.fby[ny * nx + i], 1, 1, L.rdy[j]};
+    int n = 0;
+    const int nx = L.nx;
+    const int w = L.fbx[j * (nx + 1) + i], e = L.fbx[j * (nx + 1) + i + 1];
+    const int so = L.fby[j * nx + i], no = L.fby[(j + 1) * nx + i];
+    if (side != 1 && w >= 0) bf[n++] = {w, 0, -1, L.rdx[i]};
+    if (side != 1 && so >= 0) bf[n++] = {so, 1, -1, L.rdy[j]};
+    if (side != 0 && e >= 0) bf[n++] = {e, 0, 1, L.rdx[i]};
+    if (side != 0 && no >= 0) bf[n++] = {no, 1, 1, L.rdy[j]};
     return n;
 }
 
@@ -291,8 +297,9 @@ __device__ __forceinline__ void cluster_sum(cg::cluster_group& cl, T (&v)[NR], T
 }
 
 
-// Cells 1.. of a boundary line (after the corner), given the corner values in
-// xprev.  Every such cell has one boundary face on the sweep side, with a
+// Cells 1.. of a boundary line, given the values of cell 0 in xprev: on the
+// domain edge, cell 0 is the corner; along a body, cell 0 is the fluid cell
+// before the line (a wavefront cell).  Cell st is (i0 + st di, j0 + st dj).  Every such cell has one boundary face on the sweep side, with a
 // fixed orientation along the line, so velocities split into
 //   outgoing (u_n >= 0 at that face): no ghost term, a recurrence along the
 //     line per velocity (phase A, inputs streamed RA cells ahead through a
@@ -308,7 +315,8 @@ __device__ __forceinline__ void cluster_sum(cg::cluster_group& cl, T (&v)[NR], T
 template <typename F, int kChainKpt>
 __device__ void chain_rest(cg::cluster_group& cl, const MicroArgs& M, const double* __restrict__ iZw,
                            const F* __restrict__ invD, const F* __restrict__ r, F* __restrict__ x, int pass,
-                           int line, int len, const int (&kk)[kChainKpt], F (&xprev)[kChainKpt][2],
+                           int line, int i0, int j0, int di, int dj, int len, const int (&kk)[kChainKpt],
+                           F (&xprev)[kChainKpt][2],
                            F* __restrict__ rho_out, F* ring, int RA, const int* lk, const F* lw, int nloc)
 {
     __shared__ F part[kMaxLine];              // wall sum of this CTA's velocities per cell
@@ -317,18 +325,15 @@ __device__ void chain_rest(cg::cluster_group& cl, const MicroArgs& M, const doub
     __shared__ F psum[kChainThreads];
     const LevelDev& L = M.L;
     const VelDev& Vg = M.V;
-    const int nx = L.nx, ny = L.ny, nv = Vg.nv;
+    const int nx = L.nx, nv = Vg.nv;
     const size_t nc = L.nc;
     const int tid = threadIdx.x, B = blockDim.x;
     const int nb_axis = line == 0 ? 1 : 0, nb_sign = pass == 0 ? -1 : 1;
     // orientation of the line's boundary face (column lines: x-faces, row lines: y-faces)
     const int f_axis = line == 0 ? 0 : 1, f_out = pass == 0 ? -1 : 1;
-    auto cell = [&](int st, int& i, int& j) {
-        if (pass == 0) { i = line == 0 ? 0 : st; j = line == 0 ? st : 0; }
-        else { i = line == 0 ? nx - 1 : nx - 1 - st; j = line == 0 ? ny - 1 - st : ny - 1; }
-    };
-    auto face_bc = [&](int i, int j) {
-        return f_axis == 0 ? L.fbx[j * (nx + 1) + (f_out < 0 ? 0 : nx)] : L.fby[(f_out < 0 ? 0 : ny) * nx + i];
+    auto cell = [&](int st, int& i, int& j) { i = i0 + st * di; j = j0 + st * dj; };
+    auto face_bc = [&](int i, int j) {   // the line face of cell (i, j): west / south (forward), east / north
+        return f_axis == 0 ? L.fbx[j * (nx + 1) + i + (f_out > 0)] : L.fby[(j + (f_out > 0)) * nx + i];
     };
     for (int st = tid; st < len; st += B) {
         int i, j;
@@ -684,12 +689,72 @@ k_sgs_chain(MicroArgs M, const double* __restrict__ Zw, const F* __restrict__ in
             lk[m] = k;
             lw[m] = wuo;
         }
-        chain_rest<F, kChainKpt>(cl, M, iZw, invD, r, x, pass, line, len, kk, xprev, rho_lines + line * kMaxLine,
-                                 ring, RA, lk, lw, nloc);
+        const int i0 = pass == 0 ? 0 : nx - 1, j0 = pass == 0 ? 0 : ny - 1, sg = pass == 0 ? 1 : -1;
+        chain_rest<F, kChainKpt>(cl, M, iZw, invD, r, x, pass, line, i0, j0, line == 0 ? 0 : sg, line == 0 ? sg : 0,
+                                 len, kk, xprev, rho_lines + line * kMaxLine, ring, RA, lk, lw, nloc);
     }
     cl.sync();   // keep every CTA's shared memory alive until all remote reads are done
 }
 
+
+// The lines along bodies of one sweep pass that start after the same
+// wavefront step, one cluster per line.  Cell 0 of a line is the fluid cell
+// before it, whose values (all velocities) the wavefront has already written
+// to x; chain_rest walks the line's outgoing velocities and publishes the
+// wall densities, and the wavefront then finishes its incoming velocities.
+template <typename F, int kChainKpt>
+__global__ void __cluster_dims__(kChainCluster, 1, 1) __launch_bounds__(kChainThreads)
+k_sgs_chain_body(MicroArgs M, const double* __restrict__ Zw, const F* __restrict__ invD, const F* __restrict__ r,
+                 F* __restrict__ x, F* __restrict__ rho_lines, int pass, int q0, int RA)
+{
+    const double* __restrict__ iZw = Zw + 4 * kMaxBcs;
+    extern __shared__ double xsm_raw[];
+    F* xsm = reinterpret_cast<F*>(xsm_raw);
+    cg::cluster_group cl = cg::this_cluster();
+    const VelDev& Vg = M.V;
+    const int rank = cl.block_rank(), nv = Vg.nv, nx = M.L.nx;
+    const size_t nc = M.L.nc;
+    const int* ld = M.P.lines[pass] + 8 * (q0 + blockIdx.x / kChainCluster);
+    const int i0 = ld[0], j0 = ld[1], di = ld[2], dj = ld[3], len = ld[4], line = ld[5], slot = ld[6];
+    const int ngroups = (Vg.nu + 1) / 2;
+    const int nloc = ((ngroups + kChainCluster - 1) / kChainCluster) * 2 * Vg.nvv;
+    int kk[kChainKpt], mu[kChainKpt], mvv[kChainKpt];
+    #pragma unroll
+    for (int t = 0; t < kChainKpt; ++t) {
+        int m = threadIdx.x + t * blockDim.x;
+        kk[t] = m < nloc ? chain_k(Vg, rank, m, &mu[t], &mvv[t]) : -1;
+    }
+    F xprev[kChainKpt][2];
+    const size_t c0 = (size_t)j0 * nx + i0;
+    #pragma unroll
+    for (int t = 0; t < kChainKpt; ++t) {
+        xprev[t][0] = xprev[t][1] = F(0);
+        if (kk[t] >= 0) {
+            xprev[t][0] = x[c0 * nv + kk[t]];
+            xprev[t][1] = x[(nc + c0) * nv + kk[t]];
+        }
+    }
+    F* lw = xsm + 2 * nloc;
+    F* ring = lw + nloc;
+    int* lk = reinterpret_cast<int*>(ring + (size_t)RA * kChainKpt * 3 * blockDim.x);
+    #pragma unroll
+    for (int t = 0; t < kChainKpt; ++t) {
+        const int m = threadIdx.x + t * blockDim.x;
+        if (m >= nloc) continue;
+        const int k = kk[t];
+        F wuo = F(0);
+        if (k >= 0) {
+            const F un = (F)(line == 0 ? Vg.u[k] : Vg.v[k]), uo = pass == 0 ? -un : un;
+            wuo = uo > F(0) ? (F)Vg.w[k] * uo : F(0);
+        }
+        lk[m] = k;
+        lw[m] = wuo;
+    }
+    __syncthreads();
+    chain_rest<F, kChainKpt>(cl, M, iZw, invD, r, x, pass, line, i0, j0, di, dj, len, kk, xprev, rho_lines + slot,
+                             ring, RA, lk, lw, nloc);
+    cl.sync();   // keep every CTA's shared memory alive until all remote reads are done
+}
 
 // asynchronous 16-byte copy (both addresses 16-byte aligned)
 __device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc)
@@ -739,42 +804,41 @@ __device__ __forceinline__ void cp_async_k4(F* sdst, const F* gsrc, int nk)
     }
 }
 
-// Inputs of the boundary-line cells for k_sgs_wave, after k_sgs_chain: per
-// cell of the two lines (column: e = st, row: e = ny + st) and velocity, the
-// right-hand side b of G and H and 1/D, laid out as the wavefront's ring
-// entries, fold[blk][e][3][kInteriorKc] (blk = k / kInteriorKc).  Outgoing
-// velocities and the corner carry their final value (applied as is).
-// Incoming ones carry the ghost term folded in: forward b = r - g, backward
-// b = (D x - g) / D, with g = Db C rho_s (wall) or Db x_mirror (symmetry), and
-// 1/(D + Db) in place of 1/D at an outflow face.
+// Inputs of the boundary-line cells for k_sgs_wave, after their line walk
+// (k_sgs_chain, k_sgs_chain_body): per fold entry e in [e0, e0 + ne) (a cell
+// of a line, from the plan's table) and velocity, the right-hand side b of G
+// and H and 1/D, laid out as the wavefront's ring entries,
+// fold[blk][e][3][kInteriorKc] (blk = k / kInteriorKc).  Outgoing velocities
+// and the corner carry their final value (applied as is).  Incoming ones carry
+// the ghost term folded in: forward b = r - g, backward b = (D x - g) / D, with
+// g = Db C rho_s (wall) or Db x_mirror (symmetry), and 1/(D + Db) in place of
+// 1/D at an outflow face.
 template <typename F>
 __global__ void k_line_fold(MicroArgs M, const F* __restrict__ invD, const F* __restrict__ r,
-                            const F* __restrict__ x, const F* __restrict__ rho_lines, F* __restrict__ fold, int pass)
+                            const F* __restrict__ x, const F* __restrict__ rho_lines, F* __restrict__ fold, int pass,
+                            int e0, int ne)
 {
     constexpr int K = kInteriorKc;
     const LevelDev& L = M.L;
     const VelDev& Vg = M.V;
-    const int nx = L.nx, ny = L.ny, nv = Vg.nv, nl = nx + ny;
+    const int nx = L.nx, nv = Vg.nv, nls = M.P.nl_max;
     const size_t nc = L.nc;
     const int nblk = (nv + K - 1) / K;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nblk * nl * K) return;
-    const int kk = t % K, e = (t / K) % nl, blk = t / (K * nl), kq = blk * K + kk;
-    const int ib = pass == 0 ? 0 : nx - 1, jb = pass == 0 ? 0 : ny - 1, fout = pass == 0 ? -1 : 1;
-    const int line = e < ny ? 0 : 1, st = line == 0 ? e : e - ny;
-    const int i = line == 0 ? ib : (pass == 0 ? st : nx - 1 - st);
-    const int j = line == 0 ? (pass == 0 ? st : ny - 1 - st) : jb;
+    if (t >= nblk * ne * K) return;
+    const int kk = t % K, e = e0 + (t / K) % ne, blk = t / (K * ne), kq = blk * K + kk;
+    const int4 lc = M.P.lcell[pass][e];                  // {cell, line axis, density slot, final}
+    const int c = lc.x, line = lc.y, i = c % nx, j = c / nx, fout = pass == 0 ? -1 : 1;
     F b[2] = {F(0), F(0)}, iv = F(1);
     if (kq < nv) {
-        const int c = j * nx + i;
         const size_t id = (size_t)c * nv + kq;
         const F u = (F)Vg.u[kq], v = (F)Vg.v[kq];
         const F uo = fout < 0 ? -(line == 0 ? u : v) : (line == 0 ? u : v);   // u_n at the line face
-        if (st == 0 || uo >= F(0)) {
+        if (lc.w || uo >= F(0)) {
             b[0] = x[id];
             b[1] = x[nc * nv + id];
         } else {
-            const int bc = line == 0 ? L.fbx[j * (nx + 1) + (fout < 0 ? 0 : nx)] : L.fby[(fout < 0 ? 0 : ny) * nx + i];
+            const int bc = line == 0 ? L.fbx[j * (nx + 1) + i + (fout > 0)] : L.fby[(j + (fout > 0)) * nx + i];
             const BcDev Bc = M.bc[bc];
             const F Db = uo * (line == 0 ? (F)L.rdx[i] : (F)L.rdy[j]);
             const F D = (F)M.inv_tau[c] + geomD<F>(L, i, j, u, v);
@@ -788,32 +852,34 @@ __global__ void k_line_fold(MicroArgs M, const F* __restrict__ invD, const F* __
             for (int cp = 0; cp < 2; ++cp) {
                 F g = F(0);
                 if (Bc.type == BC_WALL)
-                    g = Db * ((F)(M.Cw[(size_t)bc * nv + kq] * (cp == 0 ? 1.0 : kKint * Bc.t / 4.0)) *
-                              rho_lines[line * kMaxLine + st]);
+                    g = Db * ((F)(M.Cw[(size_t)bc * nv + kq] * (cp == 0 ? 1.0 : kKint * Bc.t / 4.0)) * rho_lines[lc.z]);
                 else if (Bc.type == BC_SYMMETRY)
                     g = Db * x[cp * nc * nv + (size_t)c * nv + km];   // an outgoing velocity: final
                 b[cp] = pass == 0 ? r[cp * nc * nv + id] - g : (D * x[cp * nc * nv + id] - g) * iv;
             }
         }
     }
-    F* o = fold + ((size_t)(blk * nl + e) * 3) * K + kk;
+    F* o = fold + ((size_t)(blk * nls + e) * 3) * K + kk;
     o[0] = b[0];
     o[K] = b[1];
     o[2 * K] = iv;
 }
 
-// One sweep over every cell for the kInteriorKc velocities of this CTA, in
-// anti-diagonal order, one thread per cell of the diagonal handling the
-// 2 x kInteriorKc values (G and H, consecutive velocities) of its cell.
-// Ordinary update: (forward) x = (b - D_W x_W - D_S x_S) / D with b the
-// residual, (backward) x = b - (D_E x_E + D_N x_N) / D with b the forward
-// value.  Boundary-line cells take b and 1/D from k_line_fold.  Values of the
-// previous diagonal stay in shared memory; the inputs of the next R - 1
-// diagonals are in flight as asynchronous copies into a ring of R shared
-// buffers, so the per-diagonal path only touches shared memory.
+// Wavefront steps [dd0, dd1) of one sweep over every cell for the
+// kInteriorKc velocities of this CTA, in anti-diagonal order, one thread per
+// cell of the diagonal handling the 2 x kInteriorKc values (G and H,
+// consecutive velocities) of its cell.  Ordinary update: (forward)
+// x = (b - D_W x_W - D_S x_S) / D with b the residual, (backward)
+// x = b - (D_E x_E + D_N x_N) / D with b the forward value.  Boundary-line
+// cells take b and 1/D from k_line_fold and drop the neighbour across their
+// line face; cells in a body are zero.  Values of the previous diagonal stay
+// in shared memory (a segment after the first reloads them from x); the inputs
+// of the next R - 1 diagonals are in flight as asynchronous copies into a ring
+// of R shared buffers, so the per-diagonal path only touches shared memory.
 template <typename F, int R, bool VEC>
 __global__ void __launch_bounds__(512) k_sgs_wave(MicroArgs M, const F* __restrict__ invD, const F* __restrict__ r,
-                                                  F* __restrict__ x, const F* __restrict__ fold, int pass)
+                                                  F* __restrict__ x, const F* __restrict__ fold, int pass, int dd0,
+                                                  int dd1)
 {
     extern __shared__ __align__(16) double sraw[];
     constexpr int K = kInteriorKc, W = 2 * K;
@@ -823,29 +889,27 @@ __global__ void __launch_bounds__(512) k_sgs_wave(MicroArgs M, const F* __restri
     const size_t nc = L.nc;
     const int B = blockDim.x, tid = threadIdx.x;
     const int k0 = blockIdx.x * K, nk = min(K, nv - k0);
-    const int nd = nx + ny - 1, nl = nx + ny;
+    const int nd = nx + ny - 1, nls = M.P.nl_max;
+    const int* __restrict__ code = M.P.code[pass];
     F* sx = reinterpret_cast<F*>(sraw);                 // [2][nx][W] values of the previous diagonal
     F* ring = sx + 2 * (size_t)nx * W;                  // [R][3][B][K] b (G, H) and 1/D of upcoming diagonals
     F* srdx = ring + (size_t)R * 3 * B * K;             // [nx] 1/dx
     F* srdy = srdx + nx;                                // [ny] 1/dy
-    const int ib = pass == 0 ? 0 : nx - 1, jb = pass == 0 ? 0 : ny - 1;   // boundary column and row of the sweep
-    const int fout = pass == 0 ? -1 : 1;
     const F* src = pass == 0 ? r : x;
     auto issue = [&](int dd) {
-        if (dd < nd) {
+        if (dd < dd1) {
             const int d = pass == 0 ? dd : nd - 1 - dd;
             const int ilo = max(0, d - (ny - 1)), ncell = min(nx - 1, d) - ilo + 1;
             if (tid < ncell) {
-                const int i = ilo + tid, j = d - i;
+                const int i = ilo + tid, j = d - i, cd = code[j * nx + i];
                 F* ra = ring + ((size_t)(dd % R) * 3 * B + tid) * K;
-                if (i != ib && j != jb) {
+                if (cd == -1) {
                     const size_t e = ((size_t)j * nx + i) * nv + k0;
                     cp_async_k4<F, VEC>(ra, src + e, nk);
                     cp_async_k4<F, VEC>(ra + (size_t)B * K, src + nc * nv + e, nk);
                     cp_async_k4<F, VEC>(ra + (size_t)2 * B * K, invD + e, nk);
-                } else {                                // a boundary-line cell: its folded inputs
-                    const int e = i == ib ? (pass == 0 ? j : ny - 1 - j) : ny + (pass == 0 ? i : nx - 1 - i);
-                    const F* fo = fold + ((size_t)(blockIdx.x * nl + e) * 3) * K;
+                } else if (cd >= 0) {                   // a boundary-line cell: its folded inputs
+                    const F* fo = fold + ((size_t)(blockIdx.x * nls + (cd >> 2)) * 3) * K;
                     cp_async_k4<F, true>(ra, fo, K);
                     cp_async_k4<F, true>(ra + (size_t)B * K, fo + K, K);
                     cp_async_k4<F, true>(ra + (size_t)2 * B * K, fo + 2 * K, K);
@@ -855,13 +919,23 @@ __global__ void __launch_bounds__(512) k_sgs_wave(MicroArgs M, const F* __restri
         cp_async_commit();
     };
     if constexpr (R > 1)
-        for (int dd = 0; dd < R - 1; ++dd) issue(dd);
-    // prologue: diagonal buffers and spacings
+        for (int dd = dd0; dd < dd0 + R - 1; ++dd) issue(dd);
+    // prologue: diagonal buffers (the previous segment's last diagonal from x) and spacings
     for (int q = tid; q < 2 * nx * W; q += B) sx[q] = F(0);
+    __syncthreads();
+    if (dd0 > 0) {
+        const int d = pass == 0 ? dd0 - 1 : nd - dd0;
+        const int ilo = max(0, d - (ny - 1)), ncell = min(nx - 1, d) - ilo + 1;
+        F* prev = sx + (size_t)((dd0 + 1) & 1) * nx * W;
+        for (int q = tid; q < ncell * W; q += B) {
+            const int i = ilo + q / W, w = q % W, cp = w / K, kk = w % K;
+            if (kk < nk) prev[(size_t)i * W + w] = x[(cp * nc + (size_t)(d - i) * nx + i) * nv + k0 + kk];
+        }
+    }
     for (int q = tid; q < nx; q += B) srdx[q] = (F)L.rdx[q];
     for (int q = tid; q < ny; q += B) srdy[q] = (F)L.rdy[q];
     // per velocity: neighbour coefficients (zero where the upwind neighbour is on the other side)
-    // and which velocities leave through the column / row line faces
+    // and which velocities leave through a column / row line face
     F cu[K], cv[K];
     unsigned outc = 0, outr = 0;
     #pragma unroll
@@ -870,12 +944,12 @@ __global__ void __launch_bounds__(512) k_sgs_wave(MicroArgs M, const F* __restri
         const F u = kq < nv ? (F)Vg.u[kq] : F(0), v = kq < nv ? (F)Vg.v[kq] : F(0);
         cu[kk] = pass == 0 ? (u > F(0) ? -u : F(0)) : (u < F(0) ? u : F(0));
         cv[kk] = pass == 0 ? (v > F(0) ? -v : F(0)) : (v < F(0) ? v : F(0));
-        if ((fout < 0 ? -u : u) >= F(0)) outc |= 1u << kk;
-        if ((fout < 0 ? -v : v) >= F(0)) outr |= 1u << kk;
+        if ((pass == 0 ? -u : u) >= F(0)) outc |= 1u << kk;
+        if ((pass == 0 ? -v : v) >= F(0)) outr |= 1u << kk;
     }
     const int xo = pass == 0 ? -1 : 1;                  // x neighbour: i - 1 (forward) or i + 1
     __syncthreads();
-    for (int dd = 0; dd < nd; ++dd) {
+    for (int dd = dd0; dd < dd1; ++dd) {
         if constexpr (R == 1) {
             issue(dd);
             cp_async_wait_n<0>();
@@ -887,32 +961,37 @@ __global__ void __launch_bounds__(512) k_sgs_wave(MicroArgs M, const F* __restri
         const F* prev = sx + (size_t)((dd + 1) & 1) * nx * W;
         F* cur = sx + (size_t)(dd & 1) * nx * W;
         if (tid < ncell) {
-            const int i = ilo + tid, j = d - i;
+            const int i = ilo + tid, j = d - i, cd = code[j * nx + i];
             const F* ra = ring + ((size_t)(dd % R) * 3 * B + tid) * K;
             static_assert(K == 4, "vector accesses assume four velocities per CTA");
-            F a[2][K], iv[K], pwv[2][K], psv[2][K];
-            ld4(ra, a[0]);
-            ld4(ra + (size_t)B * K, a[1]);
-            ld4(ra + (size_t)2 * B * K, iv);
-            const bool hx = i != ib, hy = j != jb;
-            const F fx = hx ? srdx[i] : F(0), fy = hy ? srdy[j] : F(0);
-            const F* pw = prev + (size_t)(hx ? i + xo : i) * W;
-            const F* ps = prev + (size_t)i * W;
-            ld4(pw, pwv[0]);
-            ld4(pw + K, pwv[1]);
-            ld4(ps, psv[0]);
-            ld4(ps + K, psv[1]);
-            // boundary-line cell: the final values (corner, outgoing velocities) are applied as is
-            const unsigned ld = hx && hy ? 0u : (!hx && !hy ? 0xFu : (!hx ? outc : outr));
             F res[2][K];
-            #pragma unroll
-            for (int cp = 0; cp < 2; ++cp)
+            if (cd == -2) {                             // in a body
                 #pragma unroll
-                for (int kk = 0; kk < K; ++kk) {
-                    const F y = cu[kk] * fx * pwv[cp][kk] + cv[kk] * fy * psv[cp][kk];
-                    const F rv = pass == 0 ? (a[cp][kk] - y) * iv[kk] : a[cp][kk] - y * iv[kk];
-                    res[cp][kk] = (ld >> kk) & 1u ? a[cp][kk] : rv;
-                }
+                for (int kk = 0; kk < K; ++kk) res[0][kk] = res[1][kk] = F(0);
+            } else {
+                F a[2][K], iv[K], pwv[2][K], psv[2][K];
+                ld4(ra, a[0]);
+                ld4(ra + (size_t)B * K, a[1]);
+                ld4(ra + (size_t)2 * B * K, iv);
+                const bool hx = !(cd >= 0 && (cd & 2)), hy = !(cd >= 0 && (cd & 1));
+                const F fx = hx ? srdx[i] : F(0), fy = hy ? srdy[j] : F(0);
+                const F* pw = prev + (size_t)(hx ? i + xo : i) * W;
+                const F* ps = prev + (size_t)i * W;
+                ld4(pw, pwv[0]);
+                ld4(pw + K, pwv[1]);
+                ld4(ps, psv[0]);
+                ld4(ps + K, psv[1]);
+                // boundary-line cell: the final values (corner, outgoing velocities) are applied as is
+                const unsigned ld = hx && hy ? 0u : (!hx && !hy ? 0xFu : (!hx ? outc : outr));
+                #pragma unroll
+                for (int cp = 0; cp < 2; ++cp)
+                    #pragma unroll
+                    for (int kk = 0; kk < K; ++kk) {
+                        const F y = cu[kk] * fx * pwv[cp][kk] + cv[kk] * fy * psv[cp][kk];
+                        const F rv = pass == 0 ? (a[cp][kk] - y) * iv[kk] : a[cp][kk] - y * iv[kk];
+                        res[cp][kk] = (ld >> kk) & 1u ? a[cp][kk] : rv;
+                    }
+            }
             #pragma unroll
             for (int cp = 0; cp < 2; ++cp) {
                 F* xd = x + (cp * nc + (size_t)j * nx + i) * nv + k0;
@@ -937,35 +1016,47 @@ __global__ void __launch_bounds__(512) k_sgs_wave(MicroArgs M, const F* __restri
     cp_async_wait_n<0>();
 }
 
-// sweep scratch (elements of the storage type): corner copy, line wall densities, folded line inputs
-size_t micro_fold_offset(int nv) { return ((2 * (size_t)nv + 2 * kMaxLine + 3) / 4) * 4; }
-size_t micro_scratch_elems(int nv, int nl)
+// sweep scratch (elements of the storage type): corner copy, wall densities of
+// the edge lines and the body lines, folded line inputs
+size_t micro_fold_offset(int nv, int nlines) { return ((2 * (size_t)nv + (2 + (size_t)nlines) * kMaxLine + 3) / 4) * 4; }
+size_t micro_scratch_elems(int nv, int nl, int nlines)
 {
-    return micro_fold_offset(nv) + (size_t)((nv + kInteriorKc - 1) / kInteriorKc) * nl * 3 * kInteriorKc;
+    return micro_fold_offset(nv, nlines) + (size_t)((nv + kInteriorKc - 1) / kInteriorKc) * nl * 3 * kInteriorKc;
 }
 
 template <typename F>
-cudaError_t launch_micro_sgs(const MicroArgs& m, const double* Zw, const F* invD, const F* r, F* x, F* xcorner,
-                             cudaStream_t st)
+cudaError_t launch_micro_sgs(const MicroArgs& m, const SweepPlanHost& plan, const double* Zw, const F* invD,
+                             const F* r, F* x, F* xcorner, cudaStream_t st)
 {
-    F* rho_lines = xcorner + 2 * (size_t)m.V.nv;       // 2 x kMaxLine wall densities after the corner copy
-    F* fold = xcorner + micro_fold_offset(m.V.nv);      // k_line_fold output
+    int nlines = 0;
+    for (int p = 0; p < 2; ++p)
+        for (int b = 0; b < plan.nbrk[p]; ++b)
+            nlines = std::max(nlines, plan.brk[p][b].q0 + plan.brk[p][b].nq);
+    F* rho_lines = xcorner + 2 * (size_t)m.V.nv;       // (2 + body lines) x kMaxLine wall densities
+    F* fold = xcorner + micro_fold_offset(m.V.nv, nlines);
     const int ngroups = (m.V.nu + 1) / 2;
     const int nloc = ((ngroups + kChainCluster - 1) / kChainCluster) * 2 * m.V.nvv;
     if (nloc > kChainKptMax * kChainThreads) return cudaErrorInvalidValue;
     if (m.L.nx > kMaxLine || m.L.ny > kMaxLine) return cudaErrorInvalidValue;
     const int kpt = (nloc + kChainThreads - 1) / kChainThreads;
-    const int kpt_t = kpt <= 1 ? 1 : kpt <= 2 ? 2 : kpt <= 4 ? 4 : kpt <= 8 ? 8 : 16;   // instantiated
-    const size_t rslot = sizeof(F) * (size_t)kpt_t * 3 * kChainThreads;
+    const size_t rslot = sizeof(F) * (size_t)(kpt <= 1 ? 1 : kpt <= 2 ? 2 : kpt <= 4 ? 4 : kpt <= 8 ? 8 : 16) * 3 *
+                         kChainThreads;
     int RA = (int)((96 * 1024) / rslot);
     RA = RA < 1 ? 1 : (RA > kWaveRingMax ? kWaveRingMax : RA);
     size_t smem = sizeof(F) * 2 * nloc + (sizeof(F) + sizeof(int)) * (size_t)nloc + rslot * RA;
     void (*chain)(MicroArgs, const double*, const F*, const F*, F*, const F*, F*, int, int) =
         kpt <= 1 ? k_sgs_chain<F, 1> : kpt <= 2 ? k_sgs_chain<F, 2> : kpt <= 4 ? k_sgs_chain<F, 4>
                  : kpt <= 8 ? k_sgs_chain<F, 8> : k_sgs_chain<F, 16>;
+    void (*chain_b)(MicroArgs, const double*, const F*, const F*, F*, F*, int, int, int) =
+        kpt <= 1 ? k_sgs_chain_body<F, 1> : kpt <= 2 ? k_sgs_chain_body<F, 2> : kpt <= 4 ? k_sgs_chain_body<F, 4>
+                 : kpt <= 8 ? k_sgs_chain_body<F, 8> : k_sgs_chain_body<F, 16>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(chain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
+        if (nlines > 0) {
+            e = cudaFuncSetAttribute(chain_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
     }
     const int nblk = (m.V.nv + kInteriorKc - 1) / kInteriorKc;
     const int maxdiag = m.L.nx < m.L.ny ? m.L.nx : m.L.ny;
@@ -978,8 +1069,7 @@ cudaError_t launch_micro_sgs(const MicroArgs& m, const double* Zw, const F* invD
     if (fixed + slot > kSmemMax) return cudaErrorInvalidValue;
     const size_t rfit = (kSmemMax - fixed) / slot;
     const int R = rfit >= 8 ? 8 : rfit >= 4 ? 4 : rfit >= 2 ? 2 : 1;
-    void (*wave)(MicroArgs, const F*, const F*, F*, const F*, int);
-    const int nfold = ((m.V.nv + kInteriorKc - 1) / kInteriorKc) * (int)nl * kInteriorKc;
+    void (*wave)(MicroArgs, const F*, const F*, F*, const F*, int, int, int);
     if (vec) wave = R == 8 ? k_sgs_wave<F, 8, true> : R == 4 ? k_sgs_wave<F, 4, true> : R == 2 ? k_sgs_wave<F, 2, true> : k_sgs_wave<F, 1, true>;
     else wave = R == 8 ? k_sgs_wave<F, 8, false> : R == 4 ? k_sgs_wave<F, 4, false> : R == 2 ? k_sgs_wave<F, 2, false> : k_sgs_wave<F, 1, false>;
     const size_t wsmem = fixed + slot * R;
@@ -987,7 +1077,13 @@ cudaError_t launch_micro_sgs(const MicroArgs& m, const double* Zw, const F* invD
         cudaError_t e = cudaFuncSetAttribute(wave, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem);
         if (e != cudaSuccess) return e;
     }
+    auto fold_range = [&](int pass, int e0, int ne) {
+        const int n = nblk * ne * kInteriorKc;
+        if (n > 0) k_line_fold<F><<<(n + 255) / 256, 256, 0, st>>>(m, invD, r, x, rho_lines, fold, pass, e0, ne);
+        return cudaGetLastError();
+    };
     const size_t nc = m.L.nc, nv = m.V.nv, corner = (size_t)m.L.nc - 1;
+    const int nd = m.L.nx + m.L.ny - 1;
     for (int pass = 0; pass < 2; ++pass) {
         if (pass == 1)
             for (int cp = 0; cp < 2; ++cp) {
@@ -998,19 +1094,30 @@ cudaError_t launch_micro_sgs(const MicroArgs& m, const double* Zw, const F* invD
         chain<<<2 * kChainCluster, kChainThreads, smem, st>>>(m, Zw, invD, r, x, xcorner, rho_lines, pass, RA);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        k_line_fold<F><<<(nfold + 255) / 256, 256, 0, st>>>(m, invD, r, x, rho_lines, fold, pass);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-        wave<<<nblk, nthr, wsmem, st>>>(m, invD, r, x, fold, pass);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
+        if ((e = fold_range(pass, 0, m.P.nl[pass])) != cudaSuccess) return e;
+        // wavefront segments between the body lines' walks
+        int dd = 0;
+        for (int b = 0; b <= plan.nbrk[pass]; ++b) {
+            const int end = b < plan.nbrk[pass] ? plan.brk[pass][b].dd : nd;
+            if (end > dd) {
+                wave<<<nblk, nthr, wsmem, st>>>(m, invD, r, x, fold, pass, dd, end);
+                if ((e = cudaGetLastError()) != cudaSuccess) return e;
+                dd = end;
+            }
+            if (b < plan.nbrk[pass]) {
+                const SweepBreak& k = plan.brk[pass][b];
+                chain_b<<<k.nq * kChainCluster, kChainThreads, smem, st>>>(m, Zw, invD, r, x, rho_lines, pass, k.q0, RA);
+                if ((e = cudaGetLastError()) != cudaSuccess) return e;
+                if ((e = fold_range(pass, k.e0, k.ne)) != cudaSuccess) return e;
+            }
+        }
     }
     return cudaSuccess;
 }
-template cudaError_t launch_micro_sgs<double>(const MicroArgs&, const double*, const double*, const double*, double*,
-                                              double*, cudaStream_t);
-template cudaError_t launch_micro_sgs<float>(const MicroArgs&, const double*, const float*, const float*, float*,
-                                             float*, cudaStream_t);
+template cudaError_t launch_micro_sgs<double>(const MicroArgs&, const SweepPlanHost&, const double*, const double*,
+                                              const double*, double*, double*, cudaStream_t);
+template cudaError_t launch_micro_sgs<float>(const MicroArgs&, const SweepPlanHost&, const double*, const float*,
+                                             const float*, float*, float*, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // r -= A x (full operator with every neighbour and ghost), acc += x
@@ -1021,7 +1128,7 @@ __global__ void __launch_bounds__(256) k_micro_renew(MicroArgs M, const double* 
     __shared__ double red[32 * 4];
     const LevelDev& L = M.L;
     const VelDev& Vg = M.V;
-    const int c = blockIdx.x, nx = L.nx, ny = L.ny, nv = Vg.nv, i = c % nx, j = c / nx;
+    const int c = blockIdx.x, nx = L.nx, nv = Vg.nv, i = c % nx, j = c / nx;
     const size_t nc = L.nc;
     const bool vec = sizeof(F) == 4 && (nv & 3) == 0;   // 16-byte accesses over four velocities
     if (acc) {
@@ -1044,7 +1151,7 @@ __global__ void __launch_bounds__(256) k_micro_renew(MicroArgs M, const double* 
                 }
         }
     }
-    if (!renew) return;
+    if (!renew || L.solid[c]) return;   // a body keeps a zero residual
     BFace bf[4];
     int nb = side_faces(L, i, j, 2, bf);
     __shared__ F srho[4], sgeo[3];
@@ -1121,10 +1228,10 @@ __global__ void __launch_bounds__(256) k_micro_renew(MicroArgs M, const double* 
             const F u = vu[k], v = vv[k];
             size_t id = (size_t)c * nv + k;
             F a = (itau + geomD_r<F>(rdxi, rdyj, u, v)) * xb[id];
-            if (i > 0) a += Dface<F>(0, -1, rdxi, u, v) * xb[id - nv];
-            if (i < nx - 1) a += Dface<F>(0, 1, rdxi, u, v) * xb[id + nv];
-            if (j > 0) a += Dface<F>(1, -1, rdyj, u, v) * xb[id - (size_t)nx * nv];
-            if (j < ny - 1) a += Dface<F>(1, 1, rdyj, u, v) * xb[id + (size_t)nx * nv];
+            if (L.fbx[j * (nx + 1) + i] < 0) a += Dface<F>(0, -1, rdxi, u, v) * xb[id - nv];
+            if (L.fbx[j * (nx + 1) + i + 1] < 0) a += Dface<F>(0, 1, rdxi, u, v) * xb[id + nv];
+            if (L.fby[j * nx + i] < 0) a += Dface<F>(1, -1, rdyj, u, v) * xb[id - (size_t)nx * nv];
+            if (L.fby[(j + 1) * nx + i] < 0) a += Dface<F>(1, 1, rdyj, u, v) * xb[id + (size_t)nx * nv];
             for (int b = 0; b < nb; ++b) {
                 F Db = Dface<F>(bf[b].axis, bf[b].outsign, (F)bf[b].rS, u, v);
                 if (Db == F(0)) continue;
@@ -1261,11 +1368,11 @@ __global__ void k_wall_quantities(LevelDev L, VelDev Vg, const BcDev* __restrict
     __shared__ double red[32 * 4];
     const int code = faces[blockIdx.x];
     const int axis = code >> 30, fi = code & ((1 << 30) - 1);
-    const int nx = L.nx, ny = L.ny, nv = Vg.nv;
+    const int nx = L.nx, nv = Vg.nv;
     const size_t nc = L.nc;
     int i = axis == 0 ? fi % (nx + 1) : fi % nx, j = axis == 0 ? fi / (nx + 1) : fi / nx;
-    int outsign = (axis == 0 ? i == 0 : j == 0) ? -1 : 1;
-    int c = axis == 0 ? j * nx + (i == 0 ? 0 : nx - 1) : (j == 0 ? 0 : ny - 1) * nx + i;
+    int outsign, c;
+    bface_side(L, axis, i, j, c, outsign);
     const BcDev B = bc[bcid];
     const double* Cb = Cw + (size_t)bcid * nv;
     double s[2] = {0, 0};

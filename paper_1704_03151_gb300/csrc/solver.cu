@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -20,9 +21,16 @@ struct HLevel {
     int nx = 0, ny = 0, nc = 0, nfx = 0, nfy = 0;
     std::vector<double> xn, yn, xc, yc, dx, dy;
     std::vector<int> fbx, fby;
+    std::vector<unsigned char> solid;   // 1 in a body
+    int nfluid = 0;
     LevelDev dev{};
+    SweepPlanDev plan{};                // sweep order tables (device)
+    std::vector<SweepBreak> brk[2];     // body-line walks between wavefront segments
+    int nlines = 0;                     // body lines (larger pass)
     int* pidx = nullptr;      // prolongation stencil from the next coarser level
     double* pw = nullptr;
+    int* sidx = nullptr;      // the same for a state (cells in bodies take their coarse cell's value)
+    double* sw = nullptr;
     // prediction work, [nc][4]
     double *Wn = nullptr, *Wc = nullptr, *Rc = nullptr, *P = nullptr, *R = nullptr, *dW = nullptr, *gx = nullptr,
            *gy = nullptr, *Wt = nullptr, *idiag = nullptr, *T = nullptr;
@@ -221,30 +229,69 @@ void level_geometry(HLevel& Lv)
     for (int j = 0; j < Lv.ny; ++j) { Lv.dy[j] = Lv.yn[j + 1] - Lv.yn[j]; Lv.yc[j] = 0.5 * (Lv.yn[j] + Lv.yn[j + 1]); }
 }
 
-// linear weights in one direction for a fine centre x inside coarse cell I
-void lin_weights(const std::vector<double>& Xc, int I, double x, int& N, double& wA, double& wN)
+// Prolongation stencil of fine cell (i, j) inside coarse cell (I, J), as
+// four coarse cells with weights (Eqs. prolongation, prolongationWeight; on a
+// rectilinear mesh the products of 1-D linear weights).  Along each axis the
+// second coarse cell is the neighbour on the side of the fine centre, else the
+// one on the other side (signed weights: extrapolation), skipping cells
+// outside the domain or in a body; with neither the axis is constant.  If the
+// corner cell of the two chosen neighbours is in a body, the first
+// combination of the axis options (own side first, x outer) whose three cells
+// are fluid is used, else the y-axis is dropped.  Fine cells in a body get
+// zero weights (a correction), or weight 1 on their own coarse cell with
+// inject_solid (a state).
+void prolong_stencil(const HLevel& F, const HLevel& C, int i, int j, int idx[4], double w[4], bool inject_solid = false)
 {
-    int n = (int)Xc.size();
-    int nb = x < Xc[I] ? I - 1 : I + 1;
-    if (nb < 0 || nb >= n) nb = x < Xc[I] ? I + 1 : I - 1;
-    if (nb < 0 || nb >= n) { N = I; wA = 1.0; wN = 0.0; return; }
-    N = nb;
-    double span = Xc[nb] - Xc[I];
-    wA = (Xc[nb] - x) / span;
-    wN = (x - Xc[I]) / span;
+    const int I = i / 2, J = j / 2;
+    auto fluid = [&](int a, int b) { return a >= 0 && a < C.nx && b >= 0 && b < C.ny && !C.solid[b * C.nx + a]; };
+    const int own = J * C.nx + I;
+    if (F.solid[(size_t)j * F.nx + i]) {
+        for (int q = 0; q < 4; ++q) { idx[q] = own; w[q] = 0.0; }
+        if (inject_solid) w[0] = 1.0;
+        return;
+    }
+    const double x = F.xc[i], y = F.yc[j];
+    const int dx = x < C.xc[I] ? -1 : 1, dy = y < C.yc[J] ? -1 : 1;
+    std::vector<int> ox, oy;
+    for (int a : {I + dx, I - dx}) if (fluid(a, J)) ox.push_back(a);
+    for (int b : {J + dy, J - dy}) if (fluid(I, b)) oy.push_back(b);
+    int IN = ox.empty() ? I : ox[0], JN = oy.empty() ? J : oy[0];
+    if (!ox.empty() && !oy.empty() && !fluid(IN, JN)) {
+        bool found = false;
+        for (size_t p = 0; p < ox.size() && !found; ++p)
+            for (size_t q = 0; q < oy.size() && !found; ++q)
+                if (fluid(ox[p], oy[q])) { IN = ox[p]; JN = oy[q]; found = true; }
+        if (!found) JN = J;
+    }
+    double ax = 1.0, bx = 0.0, ay = 1.0, by = 0.0;
+    if (IN != I) { double sp = C.xc[IN] - C.xc[I]; ax = (C.xc[IN] - x) / sp; bx = (x - C.xc[I]) / sp; }
+    if (JN != J) { double sp = C.yc[JN] - C.yc[J]; ay = (C.yc[JN] - y) / sp; by = (y - C.yc[J]) / sp; }
+    idx[0] = own;               w[0] = ax * ay;
+    idx[1] = J * C.nx + IN;     w[1] = bx * ay;
+    idx[2] = JN * C.nx + I;     w[2] = ax * by;
+    idx[3] = JN * C.nx + IN;    w[3] = bx * by;
 }
 
 miugks_status upload_level(miugks_solver* s, HLevel& Lv)
 {
     double *xn, *yn, *xc, *yc, *dx, *dy, *rdx, *rdy;
     int *fbx, *fby;
+    unsigned char* solid;
     std::vector<double> rdxh(Lv.nx), rdyh(Lv.ny);
     for (int i = 0; i < Lv.nx; ++i) rdxh[i] = 1.0 / Lv.dx[i];
     for (int j = 0; j < Lv.ny; ++j) rdyh[j] = 1.0 / Lv.dy[j];
     ST(upload(s, &xn, Lv.xn)); ST(upload(s, &yn, Lv.yn)); ST(upload(s, &xc, Lv.xc)); ST(upload(s, &yc, Lv.yc));
     ST(upload(s, &dx, Lv.dx)); ST(upload(s, &dy, Lv.dy)); ST(upload(s, &fbx, Lv.fbx)); ST(upload(s, &fby, Lv.fby));
-    ST(upload(s, &rdx, rdxh)); ST(upload(s, &rdy, rdyh));
-    Lv.dev = LevelDev{Lv.nx, Lv.ny, Lv.nc, Lv.nfx, Lv.nfy, xn, yn, xc, yc, dx, dy, fbx, fby, rdx, rdy};
+    ST(upload(s, &rdx, rdxh)); ST(upload(s, &rdy, rdyh)); ST(upload(s, &solid, Lv.solid));
+    std::vector<int> ubc;   // fluid cells with an east or north boundary face
+    for (int j = 0; j < Lv.ny; ++j)
+        for (int i = 0; i < Lv.nx; ++i)
+            if (!Lv.solid[j * Lv.nx + i] && (Lv.fbx[j * (Lv.nx + 1) + i + 1] >= 0 || Lv.fby[(j + 1) * Lv.nx + i] >= 0))
+                ubc.push_back(j * Lv.nx + i);
+    int* ubcd;
+    ST(upload(s, &ubcd, ubc));
+    Lv.dev = LevelDev{Lv.nx, Lv.ny, Lv.nc, Lv.nfx, Lv.nfy, xn, yn, xc, yc, dx, dy, fbx, fby, rdx, rdy, solid,
+                      ubcd, (int)ubc.size()};
     size_t n4 = 4 * (size_t)Lv.nc, nf = 2 * (size_t)Lv.nc * s->nv;
     ST(dalloc(s, &Lv.Wn, n4)); ST(dalloc(s, &Lv.Wc, n4)); ST(dalloc(s, &Lv.Rc, n4)); ST(dalloc(s, &Lv.P, n4));
     ST(dalloc(s, &Lv.R, n4)); ST(dalloc(s, &Lv.dW, n4)); ST(dalloc(s, &Lv.Wt, n4));
@@ -257,7 +304,121 @@ miugks_status upload_level(miugks_solver* s, HLevel& Lv)
 
 MicroArgs micro_args(miugks_solver* s, int l)
 {
-    return MicroArgs{s->lev[l].dev, s->vel, s->bc, s->Cw, s->lev[l].inv_tau};
+    return MicroArgs{s->lev[l].dev, s->vel, s->bc, s->Cw, s->lev[l].inv_tau, s->lev[l].plan};
+}
+
+SweepPlanHost sweep_plan(const HLevel& Lv)
+{
+    SweepPlanHost h{};
+    for (int p = 0; p < 2; ++p) { h.brk[p] = Lv.brk[p].data(); h.nbrk[p] = (int)Lv.brk[p].size(); }
+    return h;
+}
+
+// Sweep order of a level.  Per pass (0 forward: west / south faces on the
+// sweep side; 1 backward: east / north), every fluid cell with a boundary
+// face on the sweep side is a boundary-line cell: the domain edge's column and
+// row (walked from the corner before the wavefront), and runs of cells along
+// a body's faces, walked from the fluid cell before the run once the
+// wavefront has passed that cell.  Every cell may have at most one such face
+// (the two corners of the domain excepted), so the cells of the domain edge
+// must be fluid and bodies keep one cell away from the edge.
+miugks_status build_sweep_plan(miugks_solver* s, HLevel& Lv)
+{
+    const int nx = Lv.nx, ny = Lv.ny, nc = Lv.nc, nd = nx + ny - 1;
+    auto bx = [&](int p, int i, int j) { return Lv.fbx[j * (nx + 1) + i + p] >= 0; };
+    auto by = [&](int p, int i, int j) { return Lv.fby[(j + p) * nx + i] >= 0; };
+    int nl_max = 0;
+    for (int p = 0; p < 2; ++p) {
+        std::vector<int> code(nc, -1);
+        std::vector<int> lcell;              // int4 per entry
+        for (int c = 0; c < nc; ++c) if (Lv.solid[c]) code[c] = -2;
+        const int ie = p == 0 ? 0 : nx - 1, je = p == 0 ? 0 : ny - 1, sg = p == 0 ? 1 : -1;
+        // the edge column (e = st) and row (e = ny + st), the corner first
+        for (int st = 0; st < ny; ++st) {
+            int i = ie, j = je + sg * st, c = j * nx + i;
+            if (Lv.solid[c]) return fail(s, MIUGKS_EINVAL, "level with %dx%d cells: the cells on the domain edge must be fluid", nx, ny);
+            lcell.insert(lcell.end(), {c, 0, st, st == 0});
+            code[c] = (st << 2) | 2 | (st == 0 ? 1 : 0);
+        }
+        for (int st = 0; st < nx; ++st) {
+            int i = ie + sg * st, j = je, c = j * nx + i;
+            if (Lv.solid[c]) return fail(s, MIUGKS_EINVAL, "level with %dx%d cells: the cells on the domain edge must be fluid", nx, ny);
+            lcell.insert(lcell.end(), {c, 1, kMaxLine + st, st == 0});
+            if (st > 0) code[c] = ((ny + st) << 2) | 1;
+        }
+        Lv.plan.nl[p] = nx + ny;
+        // every other fluid cell: at most one sweep-side boundary face
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                int c = j * nx + i;
+                if (Lv.solid[c] || code[c] != -1) continue;
+                if (bx(p, i, j) && by(p, i, j))
+                    return fail(s, MIUGKS_EINVAL, "cell (%d,%d) of a %dx%d level has two boundary faces on one sweep side "
+                                  "(bodies must keep one cell away from the domain edge and from each other)", i, j, nx, ny);
+            }
+        // runs along bodies: x-face runs along columns, y-face runs along rows
+        struct Run { int i0, j0, di, dj, len, axis, dd; };
+        std::vector<Run> runs;
+        for (int axis = 0; axis < 2; ++axis) {
+            const int nout = axis == 0 ? nx : ny, nin = axis == 0 ? ny : nx;
+            for (int a = 0; a < nout; ++a) {
+                int b = 0;
+                while (b < nin) {
+                    auto member = [&](int t) {
+                        int i = axis == 0 ? a : t, j = axis == 0 ? t : a, c = j * nx + i;
+                        return !Lv.solid[c] && code[c] == -1 && (axis == 0 ? bx(p, i, j) : by(p, i, j));
+                    };
+                    if (!member(b)) { ++b; continue; }
+                    int e = b;
+                    while (e + 1 < nin && member(e + 1)) ++e;
+                    // walk direction: +j / +i forward, -j / -i backward; cell 0 the fluid cell before the run
+                    int first = p == 0 ? b : e, pre = first - sg;
+                    int pi = axis == 0 ? a : pre, pj = axis == 0 ? pre : a;
+                    if (pre < 0 || pre >= nin || Lv.solid[pj * nx + pi])
+                        return fail(s, MIUGKS_EINVAL, "a body line of a %dx%d level has no fluid cell before it", nx, ny);
+                    int dpre = pi + pj, ddpre = p == 0 ? dpre : nd - 1 - dpre;
+                    runs.push_back({pi, pj, axis == 0 ? 0 : sg, axis == 0 ? sg : 0, e - b + 2, axis, ddpre + 1});
+                    b = e + 1;
+                }
+            }
+        }
+        std::stable_sort(runs.begin(), runs.end(), [](const Run& x, const Run& y) { return x.dd < y.dd; });
+        if ((int)runs.size() > kMaxBodyLines) return fail(s, MIUGKS_EINVAL, "too many body lines (%d > %d)", (int)runs.size(), kMaxBodyLines);
+        std::vector<int> lines;
+        Lv.brk[p].clear();
+        for (int q = 0; q < (int)runs.size(); ++q) {
+            const Run& R = runs[q];
+            const int slot = (2 + q) * kMaxLine, e0 = (int)lcell.size() / 4;
+            lines.insert(lines.end(), {R.i0, R.j0, R.di, R.dj, R.len, R.axis, slot, 0});
+            for (int st = 1; st < R.len; ++st) {
+                int i = R.i0 + st * R.di, j = R.j0 + st * R.dj, c = j * nx + i;
+                code[c] = (((int)lcell.size() / 4) << 2) | (R.axis == 0 ? 2 : 1);
+                lcell.insert(lcell.end(), {c, R.axis, slot + st, 0});
+            }
+            const int ne = (int)lcell.size() / 4 - e0;
+            if (!Lv.brk[p].empty() && Lv.brk[p].back().dd == R.dd) {
+                Lv.brk[p].back().nq++;
+                Lv.brk[p].back().ne += ne;
+            } else {
+                Lv.brk[p].push_back(SweepBreak{R.dd, q, 1, e0, ne});
+            }
+        }
+        Lv.nlines = std::max(Lv.nlines, (int)runs.size());
+        nl_max = std::max(nl_max, (int)lcell.size() / 4);
+        int* dcode;
+        int4* dl;
+        int* dlines = nullptr;
+        ST(upload(s, &dcode, code));
+        std::vector<int4> l4(lcell.size() / 4);
+        for (size_t e = 0; e < l4.size(); ++e) l4[e] = make_int4(lcell[4 * e], lcell[4 * e + 1], lcell[4 * e + 2], lcell[4 * e + 3]);
+        ST(upload(s, &dl, l4));
+        if (!lines.empty()) ST(upload(s, &dlines, lines));
+        Lv.plan.code[p] = dcode;
+        Lv.plan.lcell[p] = dl;
+        Lv.plan.lines[p] = dlines;
+    }
+    Lv.plan.nl_max = nl_max;
+    return MIUGKS_OK;
 }
 
 MacroArgs macro_args(miugks_solver* s, int l, double dtn_inv)
@@ -336,7 +497,7 @@ miugks_status fas_visit(miugks_solver* s, int l, double dti, int type, bool firs
     ST(fas(s, l + 1, dti, type));
     if (type != 0) ST(fas_visit(s, l + 1, dti, type == 1 ? 1 : 0, false));
     CK(launch_sub(Cv.dW, Cv.Wc, Cv.Wn, 4 * (size_t)Cv.nc, s->st));
-    CK(launch_prolong_add<double>(Lv.dev, Cv.dev, 4, 1, Lv.pidx, Lv.pw, Cv.dW, Lv.Wc, (double*)nullptr, s->st));
+    CK(launch_prolong_state(Lv.dev, Lv.pidx, Lv.pw, Cv.dW, Lv.Wc, s->st));
     for (int m = 0; m < s->opts.nu2; ++m) {
         CK(launch_macro_resid(ma, Lv.Wc, Lv.gx, Lv.gy, Lv.P, Lv.R, 1, s->st));
         ST(timed_macro_sgs(s, ma, Lv, l));
@@ -358,7 +519,7 @@ miugks_status cs(miugks_solver* s, int l, int type)
     const bool coarsest = l == s->L - 1;
     const int npre = coarsest ? (s->L == 1 ? 1 : s->opts.nu_coarse) : s->opts.nu1;
     for (int m = 0; m < npre; ++m) {
-        CK(launch_micro_sgs<F>(mi, s->Zw, invD, r, dl, xc, s->st));
+        CK(launch_micro_sgs<F>(mi, sweep_plan(Lv), s->Zw, invD, r, dl, xc, s->st));
         bool last = coarsest && m == npre - 1;
         CK(launch_micro_renew<F>(mi, s->Zw, dl, r, df, last ? 0 : 1, s->st));
         if (last) return MIUGKS_OK;
@@ -379,7 +540,7 @@ miugks_status cs(miugks_solver* s, int l, int type)
     CK(launch_prolong_add<F>(Lv.dev, Cv.dev, s->nv, 2, Lv.pidx, Lv.pw, (F*)Cv.df, df, dl, s->st));
     for (int m = 0; m < s->opts.nu2; ++m) {
         CK(launch_micro_renew<F>(mi, s->Zw, dl, r, nullptr, 1, s->st));
-        CK(launch_micro_sgs<F>(mi, s->Zw, invD, r, dl, xc, s->st));
+        CK(launch_micro_sgs<F>(mi, sweep_plan(Lv), s->Zw, invD, r, dl, xc, s->st));
         CK(launch_micro_renew<F>(mi, s->Zw, dl, r, df, 0, s->st));
     }
     return MIUGKS_OK;
@@ -410,7 +571,7 @@ miugks_status one_iteration_t(miugks_solver* s)
     if (s->timing) CK(cudaEventRecord(s->ev[0], s->st));
     ST(flux_stage(s));                                                       // Step 1
     if (s->timing) CK(cudaEventRecord(s->ev[1], s->st));
-    CK(launch_rms(s->R, s->W, L0.nc, s->rms_part, s->rms_out, s->st));
+    CK(launch_rms(s->R, s->W, L0.nc, L0.nfluid, s->rms_part, s->rms_out, s->st));
     size_t n4 = 4 * (size_t)L0.nc;
     CK(cudaMemcpyAsync(L0.Wn, s->W, n4 * sizeof(double), cudaMemcpyDeviceToDevice, s->st));
     CK(cudaMemcpyAsync(L0.Rc, s->R, n4 * sizeof(double), cudaMemcpyDeviceToDevice, s->st));
@@ -604,17 +765,28 @@ miugks_status miugks_create(const miugks_mesh* mesh, const miugks_vgrid* vg, con
             if (!(L0.xn[i + 1] > L0.xn[i])) st = bad("x nodes must increase");
         for (int j = 0; j < L0.ny && st == MIUGKS_OK; ++j)
             if (!(L0.yn[j + 1] > L0.yn[j])) st = bad("y nodes must increase");
+        L0.solid.assign(L0.nc, 0);
+        if (mesh->solid)
+            for (int c = 0; c < L0.nc; ++c) L0.solid[c] = mesh->solid[c] != 0;
+        L0.nfluid = 0;
+        for (int c = 0; c < L0.nc; ++c) L0.nfluid += !L0.solid[c];
+        if (L0.nfluid == 0) { st = bad("no fluid cell"); break; }
+        // a face joining two fluid cells is interior (-1); a face between a fluid
+        // cell and a body or the domain edge needs a BC id; a face with no fluid
+        // cell on either side is inactive (stored as -1)
         for (int j = 0; j < L0.ny && st == MIUGKS_OK; ++j)
             for (int i = 0; i <= L0.nx; ++i) {
-                int b = L0.fbx[j * (L0.nx + 1) + i];
-                bool edge = i == 0 || i == L0.nx;
-                if (edge ? (b < 0 || b >= n_bcs) : b != -1) { st = bad("x-face (%d,%d): edge faces need a BC id, interior faces -1", i, j); break; }
+                int& b = L0.fbx[j * (L0.nx + 1) + i];
+                bool fl = i > 0 && !L0.solid[j * L0.nx + i - 1], fr = i < L0.nx && !L0.solid[j * L0.nx + i];
+                if (!fl && !fr) { b = -1; continue; }
+                if ((fl && fr) ? b != -1 : (b < 0 || b >= n_bcs)) { st = bad("x-face (%d,%d): boundary faces need a BC id, interior faces -1", i, j); break; }
             }
         for (int j = 0; j <= L0.ny && st == MIUGKS_OK; ++j)
             for (int i = 0; i < L0.nx; ++i) {
-                int b = L0.fby[j * L0.nx + i];
-                bool edge = j == 0 || j == L0.ny;
-                if (edge ? (b < 0 || b >= n_bcs) : b != -1) { st = bad("y-face (%d,%d): edge faces need a BC id, interior faces -1", i, j); break; }
+                int& b = L0.fby[j * L0.nx + i];
+                bool fl = j > 0 && !L0.solid[(j - 1) * L0.nx + i], fr = j < L0.ny && !L0.solid[j * L0.nx + i];
+                if (!fl && !fr) { b = -1; continue; }
+                if ((fl && fr) ? b != -1 : (b < 0 || b >= n_bcs)) { st = bad("y-face (%d,%d): boundary faces need a BC id, interior faces -1", i, j); break; }
             }
         if (st != MIUGKS_OK) break;
         level_geometry(L0);
@@ -626,6 +798,16 @@ miugks_status miugks_create(const miugks_mesh* mesh, const miugks_vgrid* vg, con
             for (int I = 0; I <= C.nx; ++I) C.xn.push_back(F.xn[2 * I]);
             for (int J = 0; J <= C.ny; ++J) C.yn.push_back(F.yn[2 * J]);
             C.fbx.resize(C.nfx); C.fby.resize(C.nfy);
+            C.solid.assign(C.nc, 0);
+            C.nfluid = 0;
+            for (int J = 0; J < C.ny && st == MIUGKS_OK; ++J)
+                for (int I = 0; I < C.nx; ++I) {
+                    int ns = F.solid[(2 * J) * F.nx + 2 * I] + F.solid[(2 * J) * F.nx + 2 * I + 1] +
+                             F.solid[(2 * J + 1) * F.nx + 2 * I] + F.solid[(2 * J + 1) * F.nx + 2 * I + 1];
+                    if (ns != 0 && ns != 4) { st = bad("level %d: solid cells must fill whole coarse cells (%d,%d)", l, I, J); break; }
+                    C.solid[J * C.nx + I] = ns == 4;
+                    C.nfluid += ns == 0;
+                }
             for (int J = 0; J < C.ny && st == MIUGKS_OK; ++J)
                 for (int I = 0; I <= C.nx; ++I) {
                     int a = F.fbx[(2 * J) * (F.nx + 1) + 2 * I], b = F.fbx[(2 * J + 1) * (F.nx + 1) + 2 * I];
@@ -666,24 +848,24 @@ miugks_status miugks_create(const miugks_mesh* mesh, const miugks_vgrid* vg, con
         if ((st = upload(s, &s->Zw, wall_norms(s))) != MIUGKS_OK) break;
         for (int l = 0; l < s->L && st == MIUGKS_OK; ++l) st = upload_level(s, s->lev[l]);
         if (st != MIUGKS_OK) break;
+        for (int l = 0; l < s->L && st == MIUGKS_OK; ++l) st = build_sweep_plan(s, s->lev[l]);
+        if (st != MIUGKS_OK) break;
         for (int l = 0; l + 1 < s->L && st == MIUGKS_OK; ++l) {
             HLevel& F = s->lev[l];
             HLevel& C = s->lev[l + 1];
             std::vector<int> idx(4 * (size_t)F.nc);
             std::vector<double> w(4 * (size_t)F.nc);
+            std::vector<int> sidx(4 * (size_t)F.nc);
+            std::vector<double> sw(4 * (size_t)F.nc);
             for (int j = 0; j < F.ny; ++j)
                 for (int i = 0; i < F.nx; ++i) {
-                    int I = i / 2, J = j / 2, IN, JN;
-                    double ax, bx, ay, by;
-                    lin_weights(C.xc, I, F.xc[i], IN, ax, bx);
-                    lin_weights(C.yc, J, F.yc[j], JN, ay, by);
                     size_t c = (size_t)j * F.nx + i;
-                    idx[4 * c + 0] = J * C.nx + I;   w[4 * c + 0] = ax * ay;
-                    idx[4 * c + 1] = J * C.nx + IN;  w[4 * c + 1] = bx * ay;
-                    idx[4 * c + 2] = JN * C.nx + I;  w[4 * c + 2] = ax * by;
-                    idx[4 * c + 3] = JN * C.nx + IN; w[4 * c + 3] = bx * by;
+                    prolong_stencil(F, C, i, j, &idx[4 * c], &w[4 * c]);
+                    prolong_stencil(F, C, i, j, &sidx[4 * c], &sw[4 * c], true);
                 }
             if ((st = upload(s, &F.pidx, idx)) != MIUGKS_OK) break;
+            if ((st = upload(s, &F.sidx, sidx)) != MIUGKS_OK) break;
+            if ((st = upload(s, &F.sw, sw)) != MIUGKS_OK) break;
             st = upload(s, &F.pw, w);
         }
         if (st != MIUGKS_OK) break;
@@ -699,7 +881,14 @@ miugks_status miugks_create(const miugks_mesh* mesh, const miugks_vgrid* vg, con
         if ((st = dalloc(s, &s->rms_part, 64 * 5)) != MIUGKS_OK) break;
         if ((st = dalloc(s, &s->rms_out, 8)) != MIUGKS_OK) break;
         if (cudaMemset(s->rms_out, 0, 8 * sizeof(double)) != cudaSuccess) { st = fail(s, MIUGKS_ECUDA, "cudaMemset"); break; }
-        if ((st = falloc(s, &s->xcorner, micro_scratch_elems(nv, mesh->nx + mesh->ny))) != MIUGKS_OK) break;
+        {
+            int nlines = 0, nlm = 0;
+            for (int l = 0; l < s->L; ++l) {
+                nlines = std::max(nlines, s->lev[l].nlines);
+                nlm = std::max(nlm, s->lev[l].plan.nl_max);
+            }
+            if ((st = falloc(s, &s->xcorner, micro_scratch_elems(nv, nlm, nlines))) != MIUGKS_OK) break;
+        }
         // smallest interior physical time step (for the numerical time step)
         s->dtp_min = 1e300;
         for (int i = 1; i < L0.nx; ++i) s->dtp_min = std::fmin(s->dtp_min, opts->cfl * std::fmin(L0.dx[i - 1], L0.dx[i]) / s->umax);
@@ -854,7 +1043,7 @@ miugks_status miugks_residual(miugks_solver* s, double res_out[4])
     if (!s) return MIUGKS_EINVAL;
     if (!s->initialised) return fail(s, MIUGKS_ESTATE, "residual before init");
     ST(flux_stage(s));
-    CK(launch_rms(s->R, s->W, s->lev[0].nc, s->rms_part, s->rms_out, s->st));
+    CK(launch_rms(s->R, s->W, s->lev[0].nc, s->lev[0].nfluid, s->rms_part, s->rms_out, s->st));
     return read_residual(s, res_out);
 }
 
@@ -924,6 +1113,7 @@ miugks_status miugks_init_from_coarse(miugks_solver* s, const miugks_solver* c)
     if (c->nv != s->nv || c->nu != s->nu || C0.nx != F1.nx || C0.ny != F1.ny)
         return fail(s, MIUGKS_EINVAL, "init_from_coarse: the coarse solver is not on the next coarser mesh");
     if (c->mixed != s->mixed) return fail(s, MIUGKS_EINVAL, "init_from_coarse: the two solvers differ in precision");
+    if (C0.solid != F1.solid) return fail(s, MIUGKS_EINVAL, "init_from_coarse: the bodies differ");
     if (!c->initialised) return fail(s, MIUGKS_ESTATE, "init_from_coarse: the coarse solver has no state");
     for (int i = 0; i <= F1.nx; ++i)
         if (std::fabs(C0.xn[i] - F1.xn[i]) > 1e-12 * (1.0 + std::fabs(F1.xn[i])))
@@ -936,10 +1126,10 @@ miugks_status miugks_init_from_coarse(miugks_solver* s, const miugks_solver* c)
     CK(cudaStreamSynchronize(c->st));                      // the coarse state is complete
     CK(cudaMemsetAsync(s->f, 0, n * s->fsz, s->st));
     if (s->mixed)
-        CK(launch_prolong_add<float>(L0.dev, F1.dev, s->nv, 2, L0.pidx, L0.pw, (const float*)c->f, (float*)s->f,
+        CK(launch_prolong_add<float>(L0.dev, F1.dev, s->nv, 2, L0.sidx, L0.sw, (const float*)c->f, (float*)s->f,
                                      (float*)nullptr, s->st));
     else
-        CK(launch_prolong_add<double>(L0.dev, F1.dev, s->nv, 2, L0.pidx, L0.pw, (const double*)c->f, (double*)s->f,
+        CK(launch_prolong_add<double>(L0.dev, F1.dev, s->nv, 2, L0.sidx, L0.sw, (const double*)c->f, (double*)s->f,
                                       (double*)nullptr, s->st));
     ST(moments_now(s));
     CK(cudaStreamSynchronize(s->st));
@@ -1074,11 +1264,11 @@ miugks_status miugks_stage_sgs_micro(miugks_solver* s, int lev, const double* in
     if (s->mixed) {
         k_invD_from_itau<float><<<Lv.nc, 128, 0, s->st>>>(Lv.dev, s->vel, Lv.inv_tau, (float*)Lv.invD);
         CK(cudaGetLastError());
-        CK(launch_micro_sgs<float>(mi, s->Zw, (float*)Lv.invD, (float*)Lv.r, (float*)Lv.dl, (float*)s->xcorner, s->st));
+        CK(launch_micro_sgs<float>(mi, sweep_plan(Lv), s->Zw, (float*)Lv.invD, (float*)Lv.r, (float*)Lv.dl, (float*)s->xcorner, s->st));
     } else {
         k_invD_from_itau<double><<<Lv.nc, 128, 0, s->st>>>(Lv.dev, s->vel, Lv.inv_tau, (double*)Lv.invD);
         CK(cudaGetLastError());
-        CK(launch_micro_sgs<double>(mi, s->Zw, (double*)Lv.invD, (double*)Lv.r, (double*)Lv.dl, (double*)s->xcorner,
+        CK(launch_micro_sgs<double>(mi, sweep_plan(Lv), s->Zw, (double*)Lv.invD, (double*)Lv.r, (double*)Lv.dl, (double*)s->xcorner,
                                     s->st));
     }
     return to_host(s, x, Lv.dl, n);
@@ -1197,6 +1387,7 @@ miugks_status refresh_invD(miugks_solver* s);
 miugks_status adj_prepare(miugks_solver* s, int m)
 {
     HLevel& L0 = s->lev[0];
+    if (L0.nfluid != L0.nc) return fail(s, MIUGKS_EINVAL, "adjoint: meshes with bodies (solid cells) are not supported");
     const size_t n = 2 * (size_t)L0.nc * s->nv;
     auto& A = s->adj;
     if (!A.alloc) {
@@ -1253,15 +1444,11 @@ miugks_status adj_prepare_levels(miugks_solver* s)
                 std::vector<std::vector<std::pair<int, double>>> inv((size_t)C.nc);
                 for (int j = 0; j < Lv.ny; ++j)
                     for (int i = 0; i < Lv.nx; ++i) {
-                        int I = i / 2, J = j / 2, IN, JN;
-                        double ax, bx, ay, by;
-                        lin_weights(C.xc, I, Lv.xc[i], IN, ax, bx);
-                        lin_weights(C.yc, J, Lv.yc[j], JN, ay, by);
+                        int idx[4];
+                        double pw[4];
+                        prolong_stencil(Lv, C, i, j, idx, pw);
                         int c = j * Lv.nx + i;
-                        inv[(size_t)J * C.nx + I].push_back({c, ax * ay});
-                        inv[(size_t)J * C.nx + IN].push_back({c, bx * ay});
-                        inv[(size_t)JN * C.nx + I].push_back({c, ax * by});
-                        inv[(size_t)JN * C.nx + IN].push_back({c, bx * by});
+                        for (int q = 0; q < 4; ++q) inv[(size_t)idx[q]].push_back({c, pw[q]});
                     }
                 std::vector<int> ptr(1, 0), cell;
                 std::vector<double> w;
@@ -1608,6 +1795,7 @@ miugks_status miugks_stage_macro_jacobian_transposed(miugks_solver* s, const dou
 {
     if (!s || !W || !x || !y) return MIUGKS_EINVAL;
     HLevel& L0 = s->lev[0];
+    if (L0.nfluid != L0.nc) return fail(s, MIUGKS_EINVAL, "adjoint: meshes with bodies (solid cells) are not supported");
     const size_t n4 = 4 * (size_t)L0.nc;
     // scratch for this test stage only, released before returning
     const size_t tot = 3 * n4 + (size_t)L0.nfx + L0.nfy + L0.nc;

@@ -22,7 +22,8 @@ _d, _i, _vp, _P = ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.POINTER
 
 
 class miugks_mesh(ctypes.Structure):
-    _fields_ = [("nx", _i), ("ny", _i), ("x_nodes", _vp), ("y_nodes", _vp), ("face_bc_x", _vp), ("face_bc_y", _vp)]
+    _fields_ = [("nx", _i), ("ny", _i), ("x_nodes", _vp), ("y_nodes", _vp), ("face_bc_x", _vp), ("face_bc_y", _vp),
+                ("solid", _vp)]
 
 
 class miugks_vgrid(ctypes.Structure):
@@ -161,7 +162,11 @@ class Solver:
                         np.ascontiguousarray(case["y_nodes"], dtype=np.float64),
                         np.ascontiguousarray(case["face_bc_x"], dtype=np.int32),
                         np.ascontiguousarray(case["face_bc_y"], dtype=np.int32)]
-        mesh = miugks_mesh(self.nx, self.ny, *[_ptr(a) for a in self._arrays])
+        solid = case.get("solid")
+        if solid is not None:
+            self._arrays.append(np.ascontiguousarray(solid, dtype=np.uint8).reshape(-1))
+        mesh = miugks_mesh(self.nx, self.ny, *[_ptr(a) for a in self._arrays[:4]],
+                           _ptr(self._arrays[4]) if solid is not None else None)
         vg = case["vgrid"]
         vgrid = miugks_vgrid(vg["nu"], vg["nv"], vg["umin"], vg["umax"], vg["vmin"], vg["vmax"], vg["rule"])
         gas = miugks_gas(case["gas"]["kn"], case["gas"]["omega"], case["gas"]["pr"])

@@ -1,0 +1,168 @@
+"""Parity of the CUDA library with the FP64 oracle on meshes with bodies
+(solid cells), the geometry of the square cylinder (Sec. 4.3): stage by stage
+(fluxes, both smoothers and the operator on every level, transfers), whole
+iterations, and the wall quantities on the bodies' faces.  The sweeps walk
+the lines along the bodies between segments of the wavefront; these cases
+have one body (one line per sweep side and pass) or two bodies at different
+diagonals (several walks per pass), on single and multigrid meshes.  Bar:
+1e-10 relative in FP64 (max abs difference over the max magnitude)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1704_03151_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1704_03151_gb300 import miugks
+    miugks.load()
+    return miugks
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def box_with_bodies(nx, ny, bodies, nvel=10, lid=0.25, levels=2, kn=0.5):
+    case = wl.cavity(nx=nx, ny=ny, nvel=nvel, kn=kn, lid=lid, levels=levels)
+    solid = np.zeros((ny, nx), dtype=np.uint8)
+    for i0, i1, j0, j1 in bodies:
+        solid[j0:j1, i0:i1] = 1
+    case["bcs"] = case["bcs"] + [wl.bc(wl.WALL, t=1.2)]
+    fbx, fby = wl.body_face_ids(solid, case["face_bc_x"], case["face_bc_y"], len(case["bcs"]) - 1)
+    return dict(case, face_bc_x=fbx, face_bc_y=fby, solid=solid.ravel())
+
+
+def cases():
+    sq = wl.square_cylinder(ma=2.0, kn=0.5, nvel=13, vmax=8.0, levels=2, nx_side=6, nx_sq=4, ny_side=4, ny_sq=4,
+                            half=3.0, dtn_growth=0.0)
+    # Ma 5 from the rear-region start, full velocity grid: the first FAS
+    # correction is dropped in the cells where it would overshoot
+    ma5 = wl.square_cylinder(nx_side=4, nx_sq=4, ny_side=4, ny_sq=4, levels=2, nvel=89, dtn_growth=3.0)
+    return {
+        "square_ma5": ma5,
+        "one_body_3lev": box_with_bodies(16, 16, [(4, 8, 8, 12)], levels=3),
+        "two_bodies": box_with_bodies(24, 16, [(4, 8, 4, 8), (14, 18, 8, 12)], nvel=8, levels=2),
+        "single_grid": box_with_bodies(12, 10, [(3, 6, 2, 7)], nvel=9, levels=1),
+        "square_cylinder": sq,
+    }
+
+
+CASES = cases()
+
+
+def make_pair(lib, case, seed=0, precision="fp64"):
+    o = oracle.Oracle(case)
+    g = lib.Solver(case, precision=precision)
+    fields = wl.random_fields(case, seed, amp=0.08)
+    if case.get("rear") is not None:
+        fields = wl.initial_fields(case)
+    o.init_fields(*fields)
+    g.init_fields(*fields)
+    return o, g
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_flux_stage_with_bodies(lib, name):
+    o, g = make_pair(lib, CASES[name], seed=1)
+    Ro, pxo, pyo = o.stage_flux()
+    Rg, pxg, pyg = g.stage_flux()
+    assert rel(pxg, pxo) < TOL
+    assert rel(pyg, pyo) < TOL
+    assert rel(Rg, Ro) < 1e-9
+    assert np.all(Rg[CASES[name]["solid"].astype(bool)] == 0.0)
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_micro_sweep_and_operator_with_bodies(lib, name):
+    case = CASES[name]
+    o, g = make_pair(lib, case, seed=2)
+    rng = np.random.default_rng(3)
+    for lev in range(case["mg"]["levels"]):
+        nx, ny = o.level_size(lev)
+        nc = nx * ny
+        it = rng.uniform(0.2, 3.0, nc)
+        r = rng.normal(size=(2, nc, o.nv))
+        xo, xg = o.sgs_micro(lev, it, r), g.sgs_micro(lev, it, r)
+        assert rel(xg, xo) < TOL, lev
+        x = rng.normal(size=(2, nc, o.nv))
+        assert rel(g.apply_micro(lev, it, x), o.apply_micro(lev, it, x)) < TOL, lev
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_macro_smoother_with_bodies(lib, name):
+    case = CASES[name]
+    o, g = make_pair(lib, case, seed=4)
+    rng = np.random.default_rng(5)
+    for lev in range(case["mg"]["levels"]):
+        nx, ny = o.level_size(lev)
+        nc = nx * ny
+        rho = 1 + 0.1 * rng.uniform(-1, 1, nc)
+        U, V, T = 0.1 * rng.uniform(-1, 1, nc), 0.1 * rng.uniform(-1, 1, nc), 1 + 0.1 * rng.uniform(-1, 1, nc)
+        W = np.stack([rho, rho * U, rho * V, 0.5 * rho * (U * U + V * V) + 0.75 * rho * T], axis=1)
+        Wg = W * (1 + 0.01 * rng.uniform(-1, 1, W.shape))
+        R = 1e-2 * rng.normal(size=W.shape)
+        assert rel(g.resid_macro(lev, W, Wg), o.resid_macro(lev, W, Wg)) < TOL, lev
+        assert rel(g.sgs_macro(lev, W, Wg, R), o.sgs_macro(lev, W, Wg, R)) < TOL, lev
+
+
+@pytest.mark.parametrize("name", ["one_body_3lev", "two_bodies"])
+def test_transfers_with_bodies(lib, name):
+    case = CASES[name]
+    o, g = make_pair(lib, case)
+    rng = np.random.default_rng(6)
+    for lev in range(case["mg"]["levels"] - 1):
+        nx, ny = o.level_size(lev)
+        cx, cy = o.level_size(lev + 1)
+        for m in (4, o.nv):
+            fine = rng.normal(size=(nx * ny, m))
+            assert rel(g.restrict(lev, fine), o.restrict(lev, fine)) < 1e-14
+            coarse = rng.normal(size=(cx * cy, m))
+            assert rel(g.prolong(lev, coarse), o.prolong(lev, coarse)) < 1e-14
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_whole_iterations_with_bodies(lib, name):
+    case = CASES[name]
+    o, g = make_pair(lib, case, seed=7)
+    for n in (1, 4):
+        ro, rg = o.step(n), g.step(n)
+        assert rel(rg, ro) < 1e-8, (n, rg, ro)
+        assert rel(g.get_f(), o.get_f()) < TOL, n
+        mo, mg = o.macro(), g.macro()
+        for k in ("rho", "u", "v", "t"):
+            assert rel(mg[k], mo[k]) < TOL, (n, k)
+    body_bc = 0 if name.startswith("square") else len(case["bcs"]) - 1
+    for qo, qg in zip(o.wall(body_bc), g.wall(body_bc)):
+        assert rel(qg, qo) < 1e-9
+
+
+def test_mixed_form_with_a_body_stays_close(lib):
+    case = CASES["one_body_3lev"]
+    o, g = make_pair(lib, case, seed=8, precision="mixed")
+    o.step(6)
+    g.step(6)
+    mo, mg = o.macro(), g.macro()
+    for k in ("rho", "u", "v", "t"):
+        assert rel(mg[k], mo[k]) < 2e-5, k
+
+
+def test_body_layouts_the_sweeps_cannot_take_are_refused(lib):
+    near_edge = box_with_bodies(12, 12, [(0, 4, 4, 8)], levels=2)
+    with pytest.raises(lib.MiugksError, match="edge"):
+        lib.Solver(near_edge)
+    misaligned = box_with_bodies(12, 12, [(3, 6, 4, 8)], levels=2)
+    with pytest.raises(lib.MiugksError, match="coarse"):
+        lib.Solver(misaligned)
+    s = lib.Solver(CASES["single_grid"])
+    s.init_uniform(1.0, 0.0, 0.0, 1.0)
+    with pytest.raises(lib.MiugksError, match="bodies"):
+        s.adjoint(0, 2, 1, tol=1e-6, max_iter=2)
