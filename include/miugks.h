@@ -173,7 +173,8 @@ miugks_status miugks_init_from_coarse(miugks_solver *s, const miugks_solver *coa
  *        collision frequency inv_tau (nc_l) for residual r (2 x nc_l x nv).
  *  apply_micro: y = A x with the full evolution operator of level lev.
  *  sgs_macro: one LU-SGS pass of the prediction smoother at state W with
- *        Gamma frozen at Wg, residual R; returns dW (all nc_l x 4).
+ *        Gamma frozen at Wg, residual R, and 1/dt_n of the current iteration
+ *        on the diagonal (when dt_n growth is on); returns dW (all nc_l x 4).
  *  resid_macro: split-Euler residual R_E(W) with Gamma frozen at Wg.
  *  restrict / prolong: transfer of an [nc][m] array between lev and lev+1. */
 miugks_status miugks_stage_flux(miugks_solver *s, double *R, double *phx, double *phy);

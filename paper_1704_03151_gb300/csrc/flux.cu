@@ -128,7 +128,11 @@ __device__ __forceinline__ void slope_mom(const F* a, F u, F v, F gM, F hM, F xi
 // Per-velocity arithmetic runs in F (FP64, or FP32 in the mixed form); the
 // velocity sums are FP64 (or Kahan-compensated FP32) per thread and combined in
 // FP64; the per-face scalars (interface state, slopes, time integrals) are FP64.
-template <typename F>
+// CACHE keeps the upwinded face values and slopes of every velocity in shared
+// memory between the three velocity passes; without it (a velocity grid too
+// large for shared memory in FP64) the later passes recompute them from f with
+// the same arithmetic.
+template <typename F, bool CACHE>
 __global__ void __launch_bounds__(256) k_face_flux(FaceFluxArgs<F> A)
 {
     extern __shared__ double sm[];
@@ -141,9 +145,9 @@ __global__ void __launch_bounds__(256) k_face_flux(FaceFluxArgs<F> A)
     double* red = sm;                       // 32 * 8
     double* par = red + 256;                // face scalars (FP64), [64]
     F* pf = reinterpret_cast<F*>(par + 64); // face constants in F, [64]
-    F* f0s = reinterpret_cast<F*>(par + 128);  // [2][nv]
-    F* sgs = f0s + 2 * nv;                  // [2][nv]
-    F* Eu = sgs + 2 * nv;                   // [nu]
+    F* f0s = reinterpret_cast<F*>(par + 128);  // [2][nv] (CACHE)
+    F* sgs = f0s + (CACHE ? 2 * nv : 0);    // [2][nv] (CACHE)
+    F* Eu = sgs + (CACHE ? 2 * nv : 0);     // [nu]
     F* Ev = Eu + Vg.nu;                     // [nvv]
     const int i = axis == 0 ? fi % (nx + 1) : fi % nx;
     const int j = axis == 0 ? fi / (nx + 1) : fi / nx;
@@ -241,10 +245,8 @@ __global__ void __launch_bounds__(256) k_face_flux(FaceFluxArgs<F> A)
     }
     __syncthreads();
     const F r1 = pf[0], r2 = pf[1], r3 = pf[2], fhL = pf[3], fhR = pf[4];
-
-    // pass 1: reconstruction, upwinding, interface conservative variables
-    Acc<F> W0a[4];
-    for (int k = tid; k < nv; k += bs) {
+    // van Leer reconstruction and upwinding of velocity k: face value f0 and slope sg of G and H
+    auto recon = [&](int k, F (&f0)[2], F (&sg)[2]) {
         const F un = axis == 0 ? vu[k] : vv[k];
         #pragma unroll
         for (int cp = 0; cp < 2; ++cp) {
@@ -254,16 +256,31 @@ __global__ void __launch_bounds__(256) k_face_flux(FaceFluxArgs<F> A)
             F sL = cLL >= 0 ? vl_limited((fL - fc[cLL * (size_t)nv + k]) * r1, d2) : F(0);
             F sR = cRR >= 0 ? vl_limited(d2, (fc[cRR * (size_t)nv + k] - fR) * r3) : F(0);
             F faceL = fL + sL * fhL, faceR = fR - sR * fhR;
-            F f0, sg;
-            if (un > F(0)) { f0 = faceL; sg = sL; }
-            else if (un < F(0)) { f0 = faceR; sg = sR; }
-            else { f0 = F(0.5) * (faceL + faceR); sg = F(0.5) * (sL + sR); }
-            f0s[cp * nv + k] = f0;
-            sgs[cp * nv + k] = sg;
+            if (un > F(0)) { f0[cp] = faceL; sg[cp] = sL; }
+            else if (un < F(0)) { f0[cp] = faceR; sg[cp] = sR; }
+            else { f0[cp] = F(0.5) * (faceL + faceR); sg[cp] = F(0.5) * (sL + sR); }
         }
-        const F w = vw[k], u = vu[k], v = vv[k], g = f0s[k];
+    };
+    auto face_vals = [&](int k, F (&f0)[2], F (&sg)[2]) {
+        if constexpr (CACHE) {
+            f0[0] = f0s[k]; f0[1] = f0s[nv + k]; sg[0] = sgs[k]; sg[1] = sgs[nv + k];
+        } else {
+            recon(k, f0, sg);
+        }
+    };
+
+    // pass 1: reconstruction, upwinding, interface conservative variables
+    Acc<F> W0a[4];
+    for (int k = tid; k < nv; k += bs) {
+        F f0[2], sg[2];
+        recon(k, f0, sg);
+        if constexpr (CACHE) {
+            f0s[k] = f0[0]; f0s[nv + k] = f0[1];
+            sgs[k] = sg[0]; sgs[nv + k] = sg[1];
+        }
+        const F w = vw[k], u = vu[k], v = vv[k], g = f0[0];
         W0a[0].add(w * g); W0a[1].add(w * u * g); W0a[2].add(w * v * g);
-        W0a[3].add(w * (F(0.5) * (u * u + v * v) * g + f0s[nv + k]));
+        W0a[3].add(w * (F(0.5) * (u * u + v * v) * g + f0[1]));
     }
     double W0[4];
     block_total<4>(W0a, red, W0);
@@ -327,7 +344,9 @@ __global__ void __launch_bounds__(256) k_face_flux(FaceFluxArgs<F> A)
         int a = k / Vg.nvv, b = k - a * Vg.nvv;
         const F u = vu[k], v = vv[k], w = vw[k];
         F cx = u - fU0, cy = v - fV0, c2 = cx * cx + cy * cy;
-        F e = F(0.5) * c2 * f0s[k] + f0s[nv + k];
+        F f0[2], sg[2];
+        face_vals(k, f0, sg);
+        F e = F(0.5) * c2 * f0[0] + f0[1];
         s6a[0].add(w * cx * e);
         s6a[1].add(w * cy * e);
         F un = axis == 0 ? u : v;
@@ -393,8 +412,10 @@ __global__ void __launch_bounds__(256) k_face_flux(FaceFluxArgs<F> A)
         F mGa, mHa, mGA, mHA;
         slope_mom<F>(un > F(0) ? aL : aR, u, v, gM, hM, xi4q, mGa, mHa);
         slope_mom<F>(As, u, v, gM, hM, xi4q, mGA, mHA);
-        F pg = un * (q1 * gP + q2 * un * mGa + q3 * mGA + q4 * f0s[k] + q5 * un * sgs[k]);
-        F ph = un * (q1 * hP + q2 * un * mHa + q3 * mHA + q4 * f0s[nv + k] + q5 * un * sgs[nv + k]);
+        F f0[2], sg[2];
+        face_vals(k, f0, sg);
+        F pg = un * (q1 * gP + q2 * un * mGa + q3 * mGA + q4 * f0[0] + q5 * un * sg[0]);
+        F ph = un * (q1 * hP + q2 * un * mHa + q3 * mHA + q4 * f0[1] + q5 * un * sg[1]);
         phG[k] = pg; phH[k] = ph;
         Fa[0].add(w * pg); Fa[1].add(w * u * pg); Fa[2].add(w * v * pg);
         Fa[3].add(w * (F(0.5) * (u * u + v * v) * pg + ph));
@@ -406,24 +427,31 @@ __global__ void __launch_bounds__(256) k_face_flux(FaceFluxArgs<F> A)
 }
 
 template <typename F>
-size_t face_flux_smem(const VelDev& V)
+size_t face_flux_smem(const VelDev& V, bool cache)
 {
-    return sizeof(double) * (256 + 128) + sizeof(F) * (4 * (size_t)V.nv + V.nu + V.nvv);
+    return sizeof(double) * (256 + 128) + sizeof(F) * ((cache ? 4 * (size_t)V.nv : 0) + V.nu + V.nvv);
 }
 
 template <typename F>
 cudaError_t launch_face_flux(const FaceFluxArgs<F>& a, cudaStream_t st)
 {
-    size_t smem = face_flux_smem<F>(a.V);
+    constexpr size_t kSmemMax = 227 * 1024;
+    const bool cache = face_flux_smem<F>(a.V, true) <= kSmemMax;
+    const size_t smem = face_flux_smem<F>(a.V, cache);
+    if (smem > kSmemMax) return cudaErrorInvalidValue;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_face_flux<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        cudaError_t e = cudaFuncSetAttribute(k_face_flux<F, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kSmemMax);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_face_flux<F, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     int nf = a.axis == 0 ? a.L.nfx : a.L.nfy;
     int threads = a.V.nv >= 256 ? 256 : 128;
-    k_face_flux<F><<<nf, threads, smem, st>>>(a);
+    if (cache) k_face_flux<F, true><<<nf, threads, smem, st>>>(a);
+    else k_face_flux<F, false><<<nf, threads, smem, st>>>(a);
     return cudaGetLastError();
 }
 template cudaError_t launch_face_flux<double>(const FaceFluxArgs<double>&, cudaStream_t);

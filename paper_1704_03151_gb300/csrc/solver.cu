@@ -1300,7 +1300,7 @@ miugks_status miugks_stage_sgs_macro(miugks_solver* s, int lev, const double* W,
     CK(cudaMemcpyAsync(Lv.Wc, W, n4 * sizeof(double), cudaMemcpyHostToDevice, s->st));
     CK(cudaMemcpyAsync(Lv.Wn, Wg, n4 * sizeof(double), cudaMemcpyHostToDevice, s->st));
     CK(cudaMemcpyAsync(Lv.R, R, n4 * sizeof(double), cudaMemcpyHostToDevice, s->st));
-    MacroArgs ma = macro_args(s, lev, 0.0);
+    MacroArgs ma = macro_args(s, lev, dtn_inv(s));   // the diagonal of the current iteration
     CK(launch_macro_gamma(ma, Lv.Wn, Lv.gx, Lv.gy, Lv.idiag, s->st));
     CK(macro_sgs(s, ma, Lv));
     CK(cudaMemcpyAsync(dW, Lv.dW, n4 * sizeof(double), cudaMemcpyDeviceToHost, s->st));
