@@ -699,7 +699,7 @@ def count_launches():
     """Kernel launches of one outer iteration of the workload, following the
     library's launch sequence (every launch is one of this library's kernels;
     memsets and copies are not counted).  Matches the ncu launch list of the
-    same workload (133 per iteration for 3 levels)."""
+    same workload (134 per iteration for 3 levels)."""
     L, nu1, nu2, nuc = LEVELS, 2, 1, 4
     macro_sweep = 2            # per-diagonal record kernel + cluster sweep
     micro_sweep = 6            # boundary-line chain, line fold and wavefront, forward and backward
@@ -711,6 +711,7 @@ def count_launches():
         n += npre * macro_sweep + (npre - 1 if coarsest else npre)
         if not coarsest:
             n += 2 + 1 + 1 + nu2 * (1 + macro_sweep)   # restrictions, difference, prolongation, post-smoothing
+    n += 1                     # the predicted state (FAS result, or W^n where it is unphysical)
     n += 1 + 2 * (L - 1)       # Steps 3-4: micro residual; per coarse level restriction + coefficients
     for l in range(L):         # Step 5: CS
         coarsest = l == L - 1

@@ -1283,7 +1283,14 @@ static void one_iteration(oracle_solver *s, double res[4])
     memcpy(L0->Wn, s->W, 4 * nc * sizeof(double));
     memcpy(L0->Rc, s->R, 4 * nc * sizeof(double));
     fas(s, 0, s->cycle);
-    memcpy(L0->Wtil, L0->Wc, 4 * nc * sizeof(double));
+    /* the predicted state; a cell where it has non-positive density or
+     * internal energy keeps W^n (reading: the paper is silent) */
+    for (size_t c = 0; c < nc; ++c) {
+        const double *w = L0->Wc + 4 * c;
+        double e2 = w[3] * w[0] - 0.5 * (w[1] * w[1] + w[2] * w[2]);
+        const double *src = (w[0] > 0.0 && e2 > 0.0) ? w : L0->Wn + 4 * c;
+        for (int m = 0; m < 4; ++m) L0->Wtil[4 * c + m] = src[m];
+    }
     /* Step 3: predicted equilibrium and collision time; coarse tau from the
      * volume-restricted predicted state */
     double add = dtn_inv(s);

@@ -53,6 +53,8 @@ template <typename T>
 cudaError_t launch_prolong_add(const LevelDev& F, const LevelDev& C, int m, int nblk, const int* idx4,
                                const double* w4, const T* coarse, T* fine, T* out_pro, cudaStream_t st);
 cudaError_t launch_axpy(double* y, const double* x, double a, size_t n, cudaStream_t st);
+// Wt = Wc, or Wn in a cell where Wc has non-positive density or internal energy
+cudaError_t launch_predicted_state(int nc, const double* Wn, const double* Wc, double* Wt, cudaStream_t st);
 // FAS correction W += P dWc of the [nc][4] state, dropped in a cell where it would
 // leave the density or the internal energy non-positive
 cudaError_t launch_prolong_state(const LevelDev& F, const int* idx4, const double* w4, const double* dWc, double* W,

@@ -836,6 +836,28 @@ cudaError_t launch_prolong_state(const LevelDev& F, const int* idx4, const doubl
     return cudaGetLastError();
 }
 
+// Predicted state of Step 2: Wt = Wc (the FAS result), except in a cell where
+// Wc has non-positive density or internal energy, which keeps its state W^n
+// (no prediction there; the paper is silent, and with smooth flow the test
+// never triggers).
+__global__ void k_predicted_state(int nc, const double* __restrict__ Wn, const double* __restrict__ Wc,
+                                  double* __restrict__ Wt)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    const double* w = Wc + 4 * (size_t)c;
+    const double e2 = w[3] * w[0] - 0.5 * (w[1] * w[1] + w[2] * w[2]);
+    const double* src = (w[0] > 0.0 && e2 > 0.0) ? w : Wn + 4 * (size_t)c;
+    #pragma unroll
+    for (int q = 0; q < 4; ++q) Wt[4 * (size_t)c + q] = src[q];
+}
+
+cudaError_t launch_predicted_state(int nc, const double* Wn, const double* Wc, double* Wt, cudaStream_t st)
+{
+    k_predicted_state<<<(nc + 127) / 128, 128, 0, st>>>(nc, Wn, Wc, Wt);
+    return cudaGetLastError();
+}
+
 // the same for long rows: one CTA per fine cell with its stencil loaded once.
 // FP64: the element arithmetic of k_prolong_add; FP32: FP32 weights and sums.
 template <typename T>

@@ -576,7 +576,7 @@ miugks_status one_iteration_t(miugks_solver* s)
     CK(cudaMemcpyAsync(L0.Wn, s->W, n4 * sizeof(double), cudaMemcpyDeviceToDevice, s->st));
     CK(cudaMemcpyAsync(L0.Rc, s->R, n4 * sizeof(double), cudaMemcpyDeviceToDevice, s->st));
     ST(fas(s, 0, dti, s->cycle));                                            // Step 2
-    CK(cudaMemcpyAsync(L0.Wt, L0.Wc, n4 * sizeof(double), cudaMemcpyDeviceToDevice, s->st));
+    CK(launch_predicted_state(L0.nc, L0.Wn, L0.Wc, L0.Wt, s->st));
     MicroArgs m0 = micro_args(s, 0);                                         // Steps 3-4
     CK(launch_micro_residual<F>(m0, s->gas, L0.Wt, s->q, (const F*)s->f, (const F*)s->phx, (const F*)s->phy, dti,
                                 L0.inv_tau, (F*)L0.invD, (F*)L0.r, s->st));
