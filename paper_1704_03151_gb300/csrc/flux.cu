@@ -436,7 +436,10 @@ template <typename F>
 cudaError_t launch_face_flux(const FaceFluxArgs<F>& a, cudaStream_t st)
 {
     constexpr size_t kSmemMax = 227 * 1024;
-    const bool cache = face_flux_smem<F>(a.V, true) <= kSmemMax;
+    // the cache pays while it leaves room for several CTAs per SM; above that the
+    // recomputing variant (a few KB) keeps the SMs' occupancy and hits in L2
+    constexpr size_t kCacheMax = 64 * 1024;
+    const bool cache = face_flux_smem<F>(a.V, true) <= kCacheMax;
     const size_t smem = face_flux_smem<F>(a.V, cache);
     if (smem > kSmemMax) return cudaErrorInvalidValue;
     static bool attr_set = false;

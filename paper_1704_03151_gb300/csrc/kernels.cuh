@@ -72,6 +72,7 @@ struct SweepPlanDev {
     const int* lines[2];    // lines along bodies: [q][8] = {i0, j0, di, dj, len, line axis, density slot, 0}
     int nl[2];              // fold entries of the edge lines (the rest belong to body lines)
     int nl_max;             // fold-entry stride of the layout
+    int bodies;             // the level has solid cells
 };
 constexpr int kMaxBodyLines = 64;   // lines along bodies per pass and level
 struct MicroArgs {

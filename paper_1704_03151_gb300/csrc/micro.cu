@@ -876,7 +876,9 @@ __global__ void k_line_fold(MicroArgs M, const F* __restrict__ invD, const F* __
 // in shared memory (a segment after the first reloads them from x); the inputs
 // of the next R - 1 diagonals are in flight as asynchronous copies into a ring
 // of R shared buffers, so the per-diagonal path only touches shared memory.
-template <typename F, int R, bool VEC>
+// BODIES: cell codes from the plan's table (a mesh with bodies); without
+// bodies the code of a cell follows from its position (the edge column and row).
+template <typename F, int R, bool VEC, bool BODIES>
 __global__ void __launch_bounds__(512) k_sgs_wave(MicroArgs M, const F* __restrict__ invD, const F* __restrict__ r,
                                                   F* __restrict__ x, const F* __restrict__ fold, int pass, int dd0,
                                                   int dd1)
@@ -895,14 +897,32 @@ __global__ void __launch_bounds__(512) k_sgs_wave(MicroArgs M, const F* __restri
     F* ring = sx + 2 * (size_t)nx * W;                  // [R][3][B][K] b (G, H) and 1/D of upcoming diagonals
     F* srdx = ring + (size_t)R * 3 * B * K;             // [nx] 1/dx
     F* srdy = srdx + nx;                                // [ny] 1/dy
+    int* cring = reinterpret_cast<int*>(srdy + ny);     // [R][B] cell codes of the upcoming diagonals
     const F* src = pass == 0 ? r : x;
-    auto issue = [&](int dd) {
+    // code of cell (i, j) when the mesh has no bodies: the edge column (the corner first), the edge row
+    const int ib = pass == 0 ? 0 : nx - 1, jb = pass == 0 ? 0 : ny - 1;
+    auto edge_code = [&](int i, int j) {
+        if (i == ib) return ((pass == 0 ? j : ny - 1 - j) << 2) | 2 | (j == jb ? 1 : 0);
+        if (j == jb) return ((ny + (pass == 0 ? i : nx - 1 - i)) << 2) | 1;
+        return -1;
+    };
+    // code of this thread's cell on wavefront step dd (loaded one step before it is needed)
+    auto code_of = [&](int dd) {
+        if (dd >= dd1) return -3;
+        const int d = pass == 0 ? dd : nd - 1 - dd;
+        const int ilo = max(0, d - (ny - 1)), ncell = min(nx - 1, d) - ilo + 1;
+        if (tid >= ncell) return -3;
+        if constexpr (BODIES) return code[(d - ilo - tid) * nx + ilo + tid];
+        else return edge_code(ilo + tid, d - ilo - tid);
+    };
+    auto issue = [&](int dd, int cd) {
         if (dd < dd1) {
             const int d = pass == 0 ? dd : nd - 1 - dd;
             const int ilo = max(0, d - (ny - 1)), ncell = min(nx - 1, d) - ilo + 1;
             if (tid < ncell) {
-                const int i = ilo + tid, j = d - i, cd = code[j * nx + i];
+                const int i = ilo + tid, j = d - i;
                 F* ra = ring + ((size_t)(dd % R) * 3 * B + tid) * K;
+                if constexpr (BODIES) cring[(dd % R) * B + tid] = cd;   // read back by this thread when swept
                 if (cd == -1) {
                     const size_t e = ((size_t)j * nx + i) * nv + k0;
                     cp_async_k4<F, VEC>(ra, src + e, nk);
@@ -919,7 +939,8 @@ __global__ void __launch_bounds__(512) k_sgs_wave(MicroArgs M, const F* __restri
         cp_async_commit();
     };
     if constexpr (R > 1)
-        for (int dd = dd0; dd < dd0 + R - 1; ++dd) issue(dd);
+        for (int dd = dd0; dd < dd0 + R - 1; ++dd) issue(dd, code_of(dd));
+    int cd_next = code_of(dd0 + R - 1);                 // for the issue of the first sweep step
     // prologue: diagonal buffers (the previous segment's last diagonal from x) and spacings
     for (int q = tid; q < 2 * nx * W; q += B) sx[q] = F(0);
     __syncthreads();
@@ -951,7 +972,8 @@ __global__ void __launch_bounds__(512) k_sgs_wave(MicroArgs M, const F* __restri
     __syncthreads();
     for (int dd = dd0; dd < dd1; ++dd) {
         if constexpr (R == 1) {
-            issue(dd);
+            issue(dd, cd_next);
+            cd_next = code_of(dd + 1);
             cp_async_wait_n<0>();
         } else {
             cp_async_wait_n<R - 2>();
@@ -961,11 +983,14 @@ __global__ void __launch_bounds__(512) k_sgs_wave(MicroArgs M, const F* __restri
         const F* prev = sx + (size_t)((dd + 1) & 1) * nx * W;
         F* cur = sx + (size_t)(dd & 1) * nx * W;
         if (tid < ncell) {
-            const int i = ilo + tid, j = d - i, cd = code[j * nx + i];
+            int cd;
+            if constexpr (BODIES) cd = cring[(dd % R) * B + tid];
+            const int i = ilo + tid, j = d - i;
+            if constexpr (!BODIES) cd = edge_code(i, j);
             const F* ra = ring + ((size_t)(dd % R) * 3 * B + tid) * K;
             static_assert(K == 4, "vector accesses assume four velocities per CTA");
             F res[2][K];
-            if (cd == -2) {                             // in a body
+            if (BODIES && cd == -2) {                   // in a body
                 #pragma unroll
                 for (int kk = 0; kk < K; ++kk) res[0][kk] = res[1][kk] = F(0);
             } else {
@@ -1010,7 +1035,10 @@ __global__ void __launch_bounds__(512) k_sgs_wave(MicroArgs M, const F* __restri
                 }
             }
         }
-        if constexpr (R > 1) issue(dd + R - 1);
+        if constexpr (R > 1) {
+            issue(dd + R - 1, cd_next);
+            cd_next = code_of(dd + R);                  // consumed after the next step's work
+        }
         __syncthreads();
     }
     cp_async_wait_n<0>();
@@ -1064,14 +1092,19 @@ cudaError_t launch_micro_sgs(const MicroArgs& m, const SweepPlanHost& plan, cons
     const bool vec = (m.V.nv * sizeof(F)) % 16 == 0;
     const size_t nl = (size_t)m.L.nx + m.L.ny;
     const size_t fixed = sizeof(F) * (2 * (size_t)m.L.nx * 2 * kInteriorKc + nl);
-    const size_t slot = sizeof(F) * 3 * (size_t)nthr * kInteriorKc;
+    const size_t slot = sizeof(F) * 3 * (size_t)nthr * kInteriorKc + sizeof(int) * (size_t)nthr;
     constexpr size_t kSmemMax = 227 * 1024;
     if (fixed + slot > kSmemMax) return cudaErrorInvalidValue;
     const size_t rfit = (kSmemMax - fixed) / slot;
     const int R = rfit >= 8 ? 8 : rfit >= 4 ? 4 : rfit >= 2 ? 2 : 1;
     void (*wave)(MicroArgs, const F*, const F*, F*, const F*, int, int, int);
-    if (vec) wave = R == 8 ? k_sgs_wave<F, 8, true> : R == 4 ? k_sgs_wave<F, 4, true> : R == 2 ? k_sgs_wave<F, 2, true> : k_sgs_wave<F, 1, true>;
-    else wave = R == 8 ? k_sgs_wave<F, 8, false> : R == 4 ? k_sgs_wave<F, 4, false> : R == 2 ? k_sgs_wave<F, 2, false> : k_sgs_wave<F, 1, false>;
+    if (m.P.bodies) {
+        if (vec) wave = R == 8 ? k_sgs_wave<F, 8, true, true> : R == 4 ? k_sgs_wave<F, 4, true, true> : R == 2 ? k_sgs_wave<F, 2, true, true> : k_sgs_wave<F, 1, true, true>;
+        else wave = R == 8 ? k_sgs_wave<F, 8, false, true> : R == 4 ? k_sgs_wave<F, 4, false, true> : R == 2 ? k_sgs_wave<F, 2, false, true> : k_sgs_wave<F, 1, false, true>;
+    } else {
+        if (vec) wave = R == 8 ? k_sgs_wave<F, 8, true, false> : R == 4 ? k_sgs_wave<F, 4, true, false> : R == 2 ? k_sgs_wave<F, 2, true, false> : k_sgs_wave<F, 1, true, false>;
+        else wave = R == 8 ? k_sgs_wave<F, 8, false, false> : R == 4 ? k_sgs_wave<F, 4, false, false> : R == 2 ? k_sgs_wave<F, 2, false, false> : k_sgs_wave<F, 1, false, false>;
+    }
     const size_t wsmem = fixed + slot * R;
     if (wsmem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(wave, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem);
@@ -1221,6 +1254,9 @@ __global__ void __launch_bounds__(256) k_micro_renew(MicroArgs M, const double* 
         }
         return;
     }
+    // interior neighbours (faces without a BC id)
+    const bool hw = L.fbx[j * (nx + 1) + i] < 0, he = L.fbx[j * (nx + 1) + i + 1] < 0;
+    const bool hs = L.fby[j * nx + i] < 0, hn = L.fby[(j + 1) * nx + i] < 0;
     for (int cp = 0; cp < 2; ++cp) {
         const F* xb = x + cp * nc * nv;
         F* rb = r + cp * nc * nv;
@@ -1228,10 +1264,10 @@ __global__ void __launch_bounds__(256) k_micro_renew(MicroArgs M, const double* 
             const F u = vu[k], v = vv[k];
             size_t id = (size_t)c * nv + k;
             F a = (itau + geomD_r<F>(rdxi, rdyj, u, v)) * xb[id];
-            if (L.fbx[j * (nx + 1) + i] < 0) a += Dface<F>(0, -1, rdxi, u, v) * xb[id - nv];
-            if (L.fbx[j * (nx + 1) + i + 1] < 0) a += Dface<F>(0, 1, rdxi, u, v) * xb[id + nv];
-            if (L.fby[j * nx + i] < 0) a += Dface<F>(1, -1, rdyj, u, v) * xb[id - (size_t)nx * nv];
-            if (L.fby[(j + 1) * nx + i] < 0) a += Dface<F>(1, 1, rdyj, u, v) * xb[id + (size_t)nx * nv];
+            if (hw) a += Dface<F>(0, -1, rdxi, u, v) * xb[id - nv];
+            if (he) a += Dface<F>(0, 1, rdxi, u, v) * xb[id + nv];
+            if (hs) a += Dface<F>(1, -1, rdyj, u, v) * xb[id - (size_t)nx * nv];
+            if (hn) a += Dface<F>(1, 1, rdyj, u, v) * xb[id + (size_t)nx * nv];
             for (int b = 0; b < nb; ++b) {
                 F Db = Dface<F>(bf[b].axis, bf[b].outsign, (F)bf[b].rS, u, v);
                 if (Db == F(0)) continue;

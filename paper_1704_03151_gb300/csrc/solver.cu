@@ -418,6 +418,7 @@ miugks_status build_sweep_plan(miugks_solver* s, HLevel& Lv)
         Lv.plan.lines[p] = dlines;
     }
     Lv.plan.nl_max = nl_max;
+    Lv.plan.bodies = Lv.nfluid != Lv.nc;
     return MIUGKS_OK;
 }
 
