@@ -1334,9 +1334,22 @@ static void one_iteration(oracle_solver *s, double res[4])
         }
     /* Step 5: total correction by the CS cycle */
     cs(s, 0, s->cycle);
-    /* Steps 6-7 */
-    size_t n = 2 * nc * nv;
-    for (size_t q = 0; q < n; ++q) s->f[q] += L0->df[q];
+    /* Steps 6-7: f += df, except in a cell where f + df has non-positive
+     * density or internal energy, which keeps f (reading: the paper is silent) */
+    for (size_t c = 0; c < nc; ++c) {
+        double W[4] = {0, 0, 0, 0};
+        for (int k = 0; k < nv; ++k) {
+            double g = FIX(s, 0, c, k) + AT(L0->df, nc, nv, 0, c, k);
+            double h = FIX(s, 1, c, k) + AT(L0->df, nc, nv, 1, c, k);
+            W[0] += s->w[k] * g;
+            W[1] += s->w[k] * s->u[k] * g;
+            W[2] += s->w[k] * s->v[k] * g;
+            W[3] += s->w[k] * (0.5 * (s->u[k] * s->u[k] + s->v[k] * s->v[k]) * g + h);
+        }
+        if (W[0] > 0.0 && W[3] * W[0] - 0.5 * (W[1] * W[1] + W[2] * W[2]) > 0.0)
+            for (int cp = 0; cp < 2; ++cp)
+                for (int k = 0; k < nv; ++k) FIX(s, cp, c, k) += AT(L0->df, nc, nv, cp, c, k);
+    }
     moments(s);
     s->iter++;
 }

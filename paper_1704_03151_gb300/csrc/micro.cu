@@ -899,21 +899,13 @@ __global__ void __launch_bounds__(512) k_sgs_wave(MicroArgs M, const F* __restri
     F* srdy = srdx + nx;                                // [ny] 1/dy
     int* cring = reinterpret_cast<int*>(srdy + ny);     // [R][B] cell codes of the upcoming diagonals
     const F* src = pass == 0 ? r : x;
-    // code of cell (i, j) when the mesh has no bodies: the edge column (the corner first), the edge row
-    const int ib = pass == 0 ? 0 : nx - 1, jb = pass == 0 ? 0 : ny - 1;
-    auto edge_code = [&](int i, int j) {
-        if (i == ib) return ((pass == 0 ? j : ny - 1 - j) << 2) | 2 | (j == jb ? 1 : 0);
-        if (j == jb) return ((ny + (pass == 0 ? i : nx - 1 - i)) << 2) | 1;
-        return -1;
-    };
-    // code of this thread's cell on wavefront step dd (loaded one step before it is needed)
+    const int ib = pass == 0 ? 0 : nx - 1, jb = pass == 0 ? 0 : ny - 1;   // the edge column and row of the pass
+    // code of this thread's cell on wavefront step dd (with bodies; loaded one step before it is needed)
     auto code_of = [&](int dd) {
-        if (dd >= dd1) return -3;
+        if (!BODIES || dd >= dd1) return -3;
         const int d = pass == 0 ? dd : nd - 1 - dd;
         const int ilo = max(0, d - (ny - 1)), ncell = min(nx - 1, d) - ilo + 1;
-        if (tid >= ncell) return -3;
-        if constexpr (BODIES) return code[(d - ilo - tid) * nx + ilo + tid];
-        else return edge_code(ilo + tid, d - ilo - tid);
+        return tid < ncell ? code[(d - ilo - tid) * nx + ilo + tid] : -3;
     };
     auto issue = [&](int dd, int cd) {
         if (dd < dd1) {
@@ -922,7 +914,12 @@ __global__ void __launch_bounds__(512) k_sgs_wave(MicroArgs M, const F* __restri
             if (tid < ncell) {
                 const int i = ilo + tid, j = d - i;
                 F* ra = ring + ((size_t)(dd % R) * 3 * B + tid) * K;
-                if constexpr (BODIES) cring[(dd % R) * B + tid] = cd;   // read back by this thread when swept
+                if constexpr (BODIES) {
+                    cring[(dd % R) * B + tid] = cd;     // read back by this thread when swept
+                } else {                                // without bodies the position gives the code
+                    cd = i != ib && j != jb ? -1 : ((i == ib ? (pass == 0 ? j : ny - 1 - j)
+                                                             : ny + (pass == 0 ? i : nx - 1 - i)) << 2);
+                }
                 if (cd == -1) {
                     const size_t e = ((size_t)j * nx + i) * nv + k0;
                     cp_async_k4<F, VEC>(ra, src + e, nk);
@@ -983,10 +980,9 @@ __global__ void __launch_bounds__(512) k_sgs_wave(MicroArgs M, const F* __restri
         const F* prev = sx + (size_t)((dd + 1) & 1) * nx * W;
         F* cur = sx + (size_t)(dd & 1) * nx * W;
         if (tid < ncell) {
-            int cd;
-            if constexpr (BODIES) cd = cring[(dd % R) * B + tid];
             const int i = ilo + tid, j = d - i;
-            if constexpr (!BODIES) cd = edge_code(i, j);
+            int cd = -1;
+            if constexpr (BODIES) cd = cring[(dd % R) * B + tid];
             const F* ra = ring + ((size_t)(dd % R) * 3 * B + tid) * K;
             static_assert(K == 4, "vector accesses assume four velocities per CTA");
             F res[2][K];
@@ -998,7 +994,8 @@ __global__ void __launch_bounds__(512) k_sgs_wave(MicroArgs M, const F* __restri
                 ld4(ra, a[0]);
                 ld4(ra + (size_t)B * K, a[1]);
                 ld4(ra + (size_t)2 * B * K, iv);
-                const bool hx = !(cd >= 0 && (cd & 2)), hy = !(cd >= 0 && (cd & 1));
+                bool hx = i != ib, hy = j != jb;
+                if constexpr (BODIES) { hx = !(cd >= 0 && (cd & 2)); hy = !(cd >= 0 && (cd & 1)); }
                 const F fx = hx ? srdx[i] : F(0), fy = hy ? srdy[j] : F(0);
                 const F* pw = prev + (size_t)(hx ? i + xo : i) * W;
                 const F* ps = prev + (size_t)i * W;
@@ -1314,13 +1311,13 @@ __global__ void __launch_bounds__(256) k_update_moments(LevelDev L, VelDev Vg, F
     const F* __restrict__ vu = VelT<F>::u(Vg);
     const F* __restrict__ vv = VelT<F>::v(Vg);
     const F* __restrict__ vw = VelT<F>::w(Vg);
+    __shared__ int sok;
     Acc<F> sa[4];
     for (int k = threadIdx.x; k < nv; k += blockDim.x) {
         F g = fG[k], h = fH[k];
         if (df) {
             g = g + df[(size_t)c * nv + k];
             h = h + df[(nc + c) * (size_t)nv + k];
-            fG[k] = g; fH[k] = h;
         }
         const F u = vu[k], v = vv[k], w = vw[k];
         sa[0].add(w * g); sa[1].add(w * u * g); sa[2].add(w * v * g);
@@ -1328,6 +1325,27 @@ __global__ void __launch_bounds__(256) k_update_moments(LevelDev L, VelDev Vg, F
     }
     double s[4];
     block_total<4>(sa, red, s);
+    if (df) {
+        // commit f + df, unless it would leave the cell with non-positive density or
+        // internal energy: then the cell keeps f and its moments are those of f
+        if (threadIdx.x == 0) sok = s[0] > 0.0 && s[3] * s[0] - 0.5 * (s[1] * s[1] + s[2] * s[2]) > 0.0;
+        __syncthreads();
+        if (sok) {
+            for (int k = threadIdx.x; k < nv; k += blockDim.x) {
+                fG[k] = fG[k] + df[(size_t)c * nv + k];
+                fH[k] = fH[k] + df[(nc + c) * (size_t)nv + k];
+            }
+        } else {
+            Acc<F> sb[4];
+            for (int k = threadIdx.x; k < nv; k += blockDim.x) {
+                const F g = fG[k], h = fH[k], u = vu[k], v = vv[k], w = vw[k];
+                sb[0].add(w * g); sb[1].add(w * u * g); sb[2].add(w * v * g);
+                sb[3].add(w * (F(0.5) * (u * u + v * v) * g + h));
+            }
+            block_total<4>(sb, red, s);
+        }
+        __syncthreads();
+    }
     if (threadIdx.x == 0) {
         const double ir = rcp64(s[0]);
         sUV[0] = (F)(s[1] * ir);
