@@ -141,11 +141,6 @@ def oracle_iterations_per_s(n_iter):
 
 def run_reference(args):
     rank, world = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
-    plate = series = None
-    if not args.no_plate and rank == 0:
-        plate = measure_plate(max(5, args.steps // 5), args.warmup)
-    if not args.no_ttr and rank == 0:
-        series = kn_series()
     if rank != 0:
         return 0
     cv = NX * NY * NVEL * NVEL
@@ -500,6 +495,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint gradient at the converged state")
     ap.add_argument("--no-plate", action="store_true", help="skip the full-size flat-plate throughput line")
+    ap.add_argument("--no-square", action="store_true", help="skip the full-size square-cylinder throughput line")
     ap.add_argument("--workload", default="cavity64",
                     choices=["cavity64", "kn_sweep", "adjoint", "cycles", "plate_adjoint", "square"])
     ap.add_argument("--count", type=int, default=32, help="cavities of the Kn sweep")
@@ -532,9 +528,11 @@ def main():
     if not args.no_fp64 and args.precision == "mixed":
         other = measure("fp64", max(3, args.steps // 3), args.warmup, world, rank, dev, with_e2e=False,
                         with_ttr=not args.no_ttr, clocks=False)
-    plate = series = None
+    plate = series = square = None
     if not args.no_plate and rank == 0:
         plate = measure_plate(max(5, args.steps // 5), args.warmup)
+    if not args.no_square and rank == 0:
+        square = measure_square(3, 2, "mixed")
     if not args.no_ttr and rank == 0:
         series = kn_series()
     if rank != 0:
@@ -566,6 +564,7 @@ def main():
         "time_to_residual": head.get("time_to_residual"),
         "adjoint": head.get("adjoint"),
         "flat_plate": plate,
+        "square_cylinder": square,
         "kn_series": series,
         "cpu_baseline": cpu,
     }
