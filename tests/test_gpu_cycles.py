@@ -31,6 +31,8 @@ CASES = {
     "cavity_L3": lambda: wl.cavity(n=16, nvel=12, kn=0.5, lid=0.2, levels=3),
     "cavity_L4": lambda: wl.cavity(n=16, nvel=10, kn=0.1, lid=0.2, levels=4),
     "plate_L2": lambda: wl.flat_plate(kn=0.2, nvel=12, levels=2, n_up=4, n_plate=8, n_down=4, ny=12),
+    "square_L3": lambda: wl.square_cylinder(ma=2.0, kn=0.5, nvel=13, vmax=8.0, levels=3, nx_side=8, nx_sq=4,
+                                            ny_side=8, ny_sq=4, half=3.0, dtn_growth=0.0),
 }
 
 

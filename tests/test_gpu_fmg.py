@@ -25,7 +25,17 @@ def rel(a, b):
     return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
 
 
+def _box_with_body():
+    case = wl.cavity(n=16, nvel=10, kn=0.5, lid=0.2, levels=3)
+    solid = np.zeros((16, 16), dtype=np.uint8)
+    solid[8:12, 4:8] = 1
+    case["bcs"] = case["bcs"] + [wl.bc(wl.WALL, t=1.2)]
+    fbx, fby = wl.body_face_ids(solid, case["face_bc_x"], case["face_bc_y"], len(case["bcs"]) - 1)
+    return dict(case, face_bc_x=fbx, face_bc_y=fby, solid=solid.ravel())
+
+
 @pytest.mark.parametrize("make", [
+    _box_with_body,
     lambda: wl.cavity(n=16, nvel=12, kn=0.5, lid=0.2, levels=3),
     lambda: wl.flat_plate(kn=0.2, nvel=12, levels=2, n_up=4, n_plate=8, n_down=4, ny=12),
 ])
