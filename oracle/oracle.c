@@ -12,9 +12,19 @@
  * finite-difference and high-precision derivatives and converged forward
  * solves (tests/test_oracle_adjoint.py).
  *
+ * Bodies (solid cells, the square cylinder of Sec. 4.3) are handled by face
+ * ids: a face between a fluid and a solid cell is a boundary face of the fluid
+ * cell, and cells in a body hold no residual, update or correction (pins in
+ * tests/test_oracle_solid.py).  The adjoint section refuses meshes with
+ * bodies.
+ *
  * Parity pins (tests/test_oracle_*.py) cover every function here except the
  * physical time step rule of face_dt(), which the paper leaves open and which
- * is therefore "parity unpinned" (both implementations follow the same rule).
+ * is therefore "parity unpinned" (both implementations follow the same rule),
+ * and the three positivity rules of the prediction and the update (a cell
+ * whose corrected or updated state would have non-positive density or
+ * internal energy keeps its state), which never trigger in smooth flow and
+ * are pinned only by the Ma 5 square-cylinder start staying physical.
  */
 #include "oracle.h"
 #include <math.h>
