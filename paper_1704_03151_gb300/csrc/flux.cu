@@ -12,6 +12,27 @@
 #include "kernels.cuh"
 
 namespace miugks {
+namespace cg = cooperative_groups;
+
+// Sum of N per-CTA totals over the CTAs of a cluster (one face split over its
+// CTAs by velocity), in rank order: every thread of every CTA gets the same
+// value.  slots: N doubles of this CTA's shared memory, one set per reduction.
+template <int N>
+__device__ __forceinline__ void cluster_total(cg::cluster_group& cl, double (&v)[N], double* slots)
+{
+    const int nb = (int)cl.num_blocks();
+    if (nb == 1) return;
+    if (threadIdx.x == 0)
+        #pragma unroll
+        for (int q = 0; q < N; ++q) slots[q] = v[q];
+    cl.sync();
+    #pragma unroll
+    for (int q = 0; q < N; ++q) {
+        double t = 0.0;
+        for (int r = 0; r < nb; ++r) t += cl.map_shared_rank(slots, r)[q];
+        v[q] = t;
+    }
+}
 
 __constant__ double c_series[5][28];   // power-series coefficients of the time integrals
 __constant__ float c_series_f[5][28];  // the same rounded to FP32
@@ -132,22 +153,31 @@ __device__ __forceinline__ void slope_mom(const F* a, F u, F v, F gM, F hM, F xi
 // memory between the three velocity passes; without it (a velocity grid too
 // large for shared memory in FP64) the later passes recompute them from f with
 // the same arithmetic.
+//
+// A face may be split over the CTAs of a cluster (launched with a cluster
+// dimension): each CTA takes a contiguous chunk of the velocities and caches
+// only its chunk, and the three velocity reductions add the CTAs' totals in
+// rank order through distributed shared memory.  Boundary faces and faces
+// inside a body are done by rank 0 alone.
 template <typename F, bool CACHE>
 __global__ void __launch_bounds__(256) k_face_flux(FaceFluxArgs<F> A)
 {
     extern __shared__ double sm[];
+    cg::cluster_group cl = cg::this_cluster();
+    const int ncl = (int)cl.num_blocks(), rank = (int)cl.block_rank();
     const LevelDev& L = A.L;
     const VelDev& Vg = A.V;
     const int nv = Vg.nv, tid = threadIdx.x, bs = blockDim.x;
-    const int axis = A.axis, fi = blockIdx.x;
+    const int axis = A.axis, fi = blockIdx.x / ncl;
+    const int chunk = (nv + ncl - 1) / ncl, kb = rank * chunk, ke = min(nv, kb + chunk);
     const int nx = L.nx, ny = L.ny;
     const size_t nc = L.nc, nf = axis == 0 ? L.nfx : L.nfy;
     double* red = sm;                       // 32 * 8
-    double* par = red + 256;                // face scalars (FP64), [64]
+    double* par = red + 256;                // face scalars (FP64), [48]; cluster slots at 48..63
     F* pf = reinterpret_cast<F*>(par + 64); // face constants in F, [64]
-    F* f0s = reinterpret_cast<F*>(par + 128);  // [2][nv] (CACHE)
-    F* sgs = f0s + (CACHE ? 2 * nv : 0);    // [2][nv] (CACHE)
-    F* Eu = sgs + (CACHE ? 2 * nv : 0);     // [nu]
+    F* f0s = reinterpret_cast<F*>(par + 128);  // [2][chunk] (CACHE)
+    F* sgs = f0s + (CACHE ? 2 * chunk : 0); // [2][chunk] (CACHE)
+    F* Eu = sgs + (CACHE ? 2 * chunk : 0);  // [nu]
     F* Ev = Eu + Vg.nu;                     // [nvv]
     const int i = axis == 0 ? fi % (nx + 1) : fi % nx;
     const int j = axis == 0 ? fi / (nx + 1) : fi / nx;
@@ -158,6 +188,7 @@ __global__ void __launch_bounds__(256) k_face_flux(FaceFluxArgs<F> A)
     F* __restrict__ phH = A.ph + (nf + fi) * (size_t)nv;
 
     if (bcid >= 0) {
+        if (rank != 0) return;
         // ---------------- boundary face: free transport of the face distribution
         int outsign, c;
         bface_side(L, axis, i, j, c, outsign);
@@ -202,6 +233,7 @@ __global__ void __launch_bounds__(256) k_face_flux(FaceFluxArgs<F> A)
     }
 
     if (inactive_face(L, axis, i, j)) {   // inside a body: no flux
+        if (rank != 0) return;
         for (int k = tid; k < nv; k += bs) { phG[k] = F(0); phH[k] = F(0); }
         if (tid == 0)
             for (int m = 0; m < 4; ++m) A.Fm[4 * (size_t)fi + m] = 0.0;
@@ -263,7 +295,8 @@ __global__ void __launch_bounds__(256) k_face_flux(FaceFluxArgs<F> A)
     };
     auto face_vals = [&](int k, F (&f0)[2], F (&sg)[2]) {
         if constexpr (CACHE) {
-            f0[0] = f0s[k]; f0[1] = f0s[nv + k]; sg[0] = sgs[k]; sg[1] = sgs[nv + k];
+            const int e = k - kb;
+            f0[0] = f0s[e]; f0[1] = f0s[chunk + e]; sg[0] = sgs[e]; sg[1] = sgs[chunk + e];
         } else {
             recon(k, f0, sg);
         }
@@ -271,12 +304,13 @@ __global__ void __launch_bounds__(256) k_face_flux(FaceFluxArgs<F> A)
 
     // pass 1: reconstruction, upwinding, interface conservative variables
     Acc<F> W0a[4];
-    for (int k = tid; k < nv; k += bs) {
+    for (int k = kb + tid; k < ke; k += bs) {
         F f0[2], sg[2];
         recon(k, f0, sg);
         if constexpr (CACHE) {
-            f0s[k] = f0[0]; f0s[nv + k] = f0[1];
-            sgs[k] = sg[0]; sgs[nv + k] = sg[1];
+            const int e = k - kb;
+            f0s[e] = f0[0]; f0s[chunk + e] = f0[1];
+            sgs[e] = sg[0]; sgs[chunk + e] = sg[1];
         }
         const F w = vw[k], u = vu[k], v = vv[k], g = f0[0];
         W0a[0].add(w * g); W0a[1].add(w * u * g); W0a[2].add(w * v * g);
@@ -284,6 +318,7 @@ __global__ void __launch_bounds__(256) k_face_flux(FaceFluxArgs<F> A)
     }
     double W0[4];
     block_total<4>(W0a, red, W0);
+    cluster_total<4>(cl, W0, par + 48);
     // face scalars, spread over the lanes of warp 0: lane 0 the collision time and
     // time step, lanes 1 and 2 the left and right equilibrium slopes
     if (tid < 3) {
@@ -340,7 +375,7 @@ __global__ void __launch_bounds__(256) k_face_flux(FaceFluxArgs<F> A)
 
     // pass 2: heat flux of the interface distribution, compatibility moments for A
     Acc<F> s6a[6];
-    for (int k = tid; k < nv; k += bs) {
+    for (int k = kb + tid; k < ke; k += bs) {
         int a = k / Vg.nvv, b = k - a * Vg.nvv;
         const F u = vu[k], v = vv[k], w = vw[k];
         F cx = u - fU0, cy = v - fV0, c2 = cx * cx + cy * cy;
@@ -360,6 +395,7 @@ __global__ void __launch_bounds__(256) k_face_flux(FaceFluxArgs<F> A)
     }
     double s6[6];
     block_total<6>(s6a, red, s6);
+    cluster_total<6>(cl, s6, par + 52);
     // lane 0: time slope A from compatibility; lanes 1-5: one time integral each
     if (tid < 6) {
         const double rho0 = par[0], U0 = par[1], V0 = par[2], lam0 = par[3];
@@ -400,7 +436,7 @@ __global__ void __launch_bounds__(256) k_face_flux(FaceFluxArgs<F> A)
 
     // pass 3: time-averaged flux of every discrete velocity and its moments
     Acc<F> Fa[4];
-    for (int k = tid; k < nv; k += bs) {
+    for (int k = kb + tid; k < ke; k += bs) {
         int a = k / Vg.nvv, b = k - a * Vg.nvv;
         const F u = vu[k], v = vv[k], w = vw[k];
         const F un = axis == 0 ? u : v;
@@ -422,25 +458,32 @@ __global__ void __launch_bounds__(256) k_face_flux(FaceFluxArgs<F> A)
     }
     double Fm[4];
     block_total<4>(Fa, red, Fm);
-    if (tid == 0)
+    cluster_total<4>(cl, Fm, par + 58);
+    if (tid == 0 && rank == 0)
         for (int m = 0; m < 4; ++m) A.Fm[4 * (size_t)fi + m] = Fm[m];
+    if (ncl > 1) cl.sync();   // the other CTAs' slots stay alive until every remote read is done
 }
 
 template <typename F>
-size_t face_flux_smem(const VelDev& V, bool cache)
+size_t face_flux_smem(const VelDev& V, bool cache, int ncl)
 {
-    return sizeof(double) * (256 + 128) + sizeof(F) * ((cache ? 4 * (size_t)V.nv : 0) + V.nu + V.nvv);
+    const size_t chunk = ((size_t)V.nv + ncl - 1) / ncl;
+    return sizeof(double) * (256 + 128) + sizeof(F) * ((cache ? 4 * chunk : 0) + V.nu + V.nvv);
 }
 
 template <typename F>
 cudaError_t launch_face_flux(const FaceFluxArgs<F>& a, cudaStream_t st)
 {
     constexpr size_t kSmemMax = 227 * 1024;
-    // the cache pays while it leaves room for several CTAs per SM; above that the
-    // recomputing variant (a few KB) keeps the SMs' occupancy and hits in L2
+    // the cache pays while it leaves room for several CTAs per SM: a face is split
+    // over a cluster of 1, 2, 4 or 8 CTAs until each CTA's chunk fits in 64 KB;
+    // beyond that the recomputing variant (a few KB) is used
     constexpr size_t kCacheMax = 64 * 1024;
-    const bool cache = face_flux_smem<F>(a.V, true) <= kCacheMax;
-    const size_t smem = face_flux_smem<F>(a.V, cache);
+    int ncl = 1;
+    while (ncl < 8 && face_flux_smem<F>(a.V, true, ncl) > kCacheMax) ncl *= 2;
+    const bool cache = face_flux_smem<F>(a.V, true, ncl) <= kCacheMax;
+    if (!cache) ncl = 1;
+    const size_t smem = face_flux_smem<F>(a.V, cache, ncl);
     if (smem > kSmemMax) return cudaErrorInvalidValue;
     static bool attr_set = false;
     if (!attr_set) {
@@ -452,10 +495,28 @@ cudaError_t launch_face_flux(const FaceFluxArgs<F>& a, cudaStream_t st)
         attr_set = true;
     }
     int nf = a.axis == 0 ? a.L.nfx : a.L.nfy;
-    int threads = a.V.nv >= 256 ? 256 : 128;
-    if (cache) k_face_flux<F, true><<<nf, threads, smem, st>>>(a);
-    else k_face_flux<F, false><<<nf, threads, smem, st>>>(a);
-    return cudaGetLastError();
+    int threads = a.V.nv / ncl >= 256 ? 256 : 128;
+    if (!cache) {
+        k_face_flux<F, false><<<nf, threads, smem, st>>>(a);
+        return cudaGetLastError();
+    }
+    if (ncl == 1) {
+        k_face_flux<F, true><<<nf, threads, smem, st>>>(a);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(nf * ncl), 1, 1);
+    cfg.blockDim = dim3((unsigned)threads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)ncl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_face_flux<F, true>, a);
 }
 template cudaError_t launch_face_flux<double>(const FaceFluxArgs<double>&, cudaStream_t);
 template cudaError_t launch_face_flux<float>(const FaceFluxArgs<float>&, cudaStream_t);
