@@ -2401,6 +2401,27 @@ int oracle_init_from_coarse(oracle_solver *s, const oracle_solver *c)
     size_t ncC = C0->nc, ncF = s->lev[0].nc;
     for (int cp = 0; cp < 2; ++cp)
         prolong_lv_s(&s->lev[0], &s->lev[1], s->nv, c->f + (size_t)cp * ncC * s->nv, s->f + (size_t)cp * ncF * s->nv, 1);
+    /* a fine cell whose prolonged f has non-positive density or internal energy
+     * (extrapolation next to an edge or a body across a strong gradient) takes
+     * the f of its coarse cell instead (reading: the paper is silent) */
+    const olev_t *L0 = &s->lev[0];
+    int nv = s->nv;
+    for (int j = 0; j < L0->ny; ++j)
+        for (int i = 0; i < L0->nx; ++i) {
+            size_t cf = (size_t)j * L0->nx + i, cc = (size_t)(j / 2) * C0->nx + i / 2;
+            double W[4] = {0, 0, 0, 0};
+            for (int k = 0; k < nv; ++k) {
+                double g = FIX(s, 0, cf, k), h = FIX(s, 1, cf, k);
+                W[0] += s->w[k] * g;
+                W[1] += s->w[k] * s->u[k] * g;
+                W[2] += s->w[k] * s->v[k] * g;
+                W[3] += s->w[k] * (0.5 * (s->u[k] * s->u[k] + s->v[k] * s->v[k]) * g + h);
+            }
+            if (W[0] > 0.0 && W[3] * W[0] - 0.5 * (W[1] * W[1] + W[2] * W[2]) > 0.0) continue;
+            for (int cp = 0; cp < 2; ++cp)
+                for (int k = 0; k < nv; ++k)
+                    FIX(s, cp, cf, k) = c->f[((size_t)cp * ncC + cc) * nv + k];
+        }
     moments(s);
     s->iter = 0;
     return 0;

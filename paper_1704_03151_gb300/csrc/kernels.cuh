@@ -110,6 +110,10 @@ cudaError_t launch_update_moments(const LevelDev& L, const VelDev& V, F* f, cons
                                   cudaStream_t st);
 template <typename F>
 cudaError_t launch_moments(const LevelDev& L, const VelDev& V, const F* f, double* W, double* q, cudaStream_t st);
+// full-multigrid start-up: cells whose prolonged f is unphysical take their coarse cell's f
+template <typename F>
+cudaError_t launch_state_fallback(const LevelDev& L, const VelDev& V, int ncx, size_t ncc, const F* fc, F* f,
+                                  cudaStream_t st);
 template <typename F>
 cudaError_t launch_init_maxwell(const LevelDev& L, const VelDev& V, const double* prim, F* f, cudaStream_t st);
 // per wall face p, tau, q (one block per face of BC bc, in face order)

@@ -1391,6 +1391,45 @@ template cudaError_t launch_moments<float>(const LevelDev&, const VelDev&, const
                                            cudaStream_t);
 
 // discrete Maxwellian of (rho, U, V, T) per cell
+// Full-multigrid start-up: a fine cell whose prolonged state f has
+// non-positive density or internal energy takes the f of its coarse cell
+// (fc, the next coarser mesh with ncx cells per row).  One CTA per fine cell.
+template <typename F>
+__global__ void __launch_bounds__(256) k_state_fallback(LevelDev L, VelDev Vg, int ncx, size_t ncc,
+                                                        const F* __restrict__ fc, F* __restrict__ f)
+{
+    __shared__ double red[32 * 4];
+    const int c = blockIdx.x, nv = Vg.nv, i = c % L.nx, j = c / L.nx;
+    const size_t nc = L.nc, cc = (size_t)(j / 2) * ncx + i / 2;
+    const F* __restrict__ vu = VelT<F>::u(Vg);
+    const F* __restrict__ vv = VelT<F>::v(Vg);
+    const F* __restrict__ vw = VelT<F>::w(Vg);
+    Acc<F> sa[4];
+    for (int k = threadIdx.x; k < nv; k += blockDim.x) {
+        const F g = f[(size_t)c * nv + k], h = f[(nc + c) * (size_t)nv + k], u = vu[k], v = vv[k], w = vw[k];
+        sa[0].add(w * g); sa[1].add(w * u * g); sa[2].add(w * v * g);
+        sa[3].add(w * (F(0.5) * (u * u + v * v) * g + h));
+    }
+    double s[4];
+    block_total<4>(sa, red, s);
+    if (s[0] > 0.0 && s[3] * s[0] - 0.5 * (s[1] * s[1] + s[2] * s[2]) > 0.0) return;
+    for (int k = threadIdx.x; k < nv; k += blockDim.x) {
+        f[(size_t)c * nv + k] = fc[cc * nv + k];
+        f[(nc + c) * (size_t)nv + k] = fc[(ncc + cc) * nv + k];
+    }
+}
+template <typename F>
+cudaError_t launch_state_fallback(const LevelDev& L, const VelDev& V, int ncx, size_t ncc, const F* fc, F* f,
+                                  cudaStream_t st)
+{
+    k_state_fallback<F><<<L.nc, V.nv >= 256 ? 256 : 128, 0, st>>>(L, V, ncx, ncc, fc, f);
+    return cudaGetLastError();
+}
+template cudaError_t launch_state_fallback<double>(const LevelDev&, const VelDev&, int, size_t, const double*,
+                                                   double*, cudaStream_t);
+template cudaError_t launch_state_fallback<float>(const LevelDev&, const VelDev&, int, size_t, const float*, float*,
+                                                  cudaStream_t);
+
 template <typename F>
 __global__ void k_init_maxwell(LevelDev L, VelDev Vg, const double* __restrict__ prim, F* __restrict__ f)
 {

@@ -1132,6 +1132,13 @@ miugks_status miugks_init_from_coarse(miugks_solver* s, const miugks_solver* c)
     else
         CK(launch_prolong_add<double>(L0.dev, F1.dev, s->nv, 2, L0.sidx, L0.sw, (const double*)c->f, (double*)s->f,
                                       (double*)nullptr, s->st));
+    // cells whose prolonged state is unphysical take their coarse cell's f
+    if (s->mixed)
+        CK(launch_state_fallback<float>(L0.dev, s->vel, C0.nx, (size_t)C0.nc, (const float*)c->f, (float*)s->f,
+                                        s->st));
+    else
+        CK(launch_state_fallback<double>(L0.dev, s->vel, C0.nx, (size_t)C0.nc, (const double*)c->f, (double*)s->f,
+                                         s->st));
     ST(moments_now(s));
     CK(cudaStreamSynchronize(s->st));
     s->initialised = true;

@@ -1,6 +1,7 @@
 """Full-multigrid start-up (Sec. 3.5): solve the problem on the coarsest mesh
 of its hierarchy first, then carry each converged state to the next finer mesh
-by bilinear prolongation of f (miugks_init_from_coarse) and iterate there,
+by bilinear prolongation of f (miugks_init_from_coarse; a cell whose prolonged
+state is unphysical takes its coarse cell's f) and iterate there,
 until the finest mesh converges.  Each mesh runs the MIUGKS outer iteration
 with the multigrid levels below it.
 
@@ -51,8 +52,7 @@ def run(case, tol=1e-6, meshes=None, coarse_tol=None, max_iter=3000, chunk=5, pr
     for q, c in enumerate(cases):
         s = miugks.Solver(c, precision=precision)
         if prev is None:
-            init = c["init"]
-            s.init_uniform(init["rho"], init["u"], init["v"], init["t"])
+            s.init_fields(*workloads.initial_fields(c))
         else:
             s.init_from_coarse(prev)
             prev.close()

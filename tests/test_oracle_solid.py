@@ -183,3 +183,21 @@ def test_hypersonic_square_start_stays_physical():
     m = o.macro()
     fluid = ~case["solid"].astype(bool)
     assert np.all(m["rho"][fluid] > 0) and np.all(m["t"][fluid] > 0)
+
+
+def test_fmg_start_falls_back_where_prolongation_is_unphysical():
+    """After the coarse mesh has formed the Ma 5 bow shock, the bilinear
+    extrapolation of f at the domain edge gives negative temperatures; those
+    cells take their coarse cell's f and every fine state is physical."""
+    case = wl.square_cylinder(nx_side=4, nx_sq=4, ny_side=4, ny_sq=4, levels=2, nvel=89, dtn_growth=3.0)
+    coarse = wl.coarsen_case(case)
+    oc = oracle.Oracle(coarse)
+    oc.init_fields(*wl.initial_fields(coarse))
+    oc.step(40)
+    o = oracle.Oracle(case)
+    o.init_from_coarse(oc)
+    m = o.macro()
+    fluid = ~case["solid"].astype(bool)
+    assert np.all(m["rho"][fluid] > 0) and np.all(m["t"][fluid] > 0)
+    r = o.step(2)
+    assert np.all(np.isfinite(r))
