@@ -61,6 +61,6 @@ def run(case, tol=1e-6, meshes=None, coarse_tol=None, max_iter=3000, chunk=5, pr
         last = q == len(cases) - 1
         iters, res, stop = _iterate(s, tol if last else (coarse_tol or tol), max_iter, chunk, floor_rtol)
         levels.append({"nx": c["nx"], "ny": c["ny"], "iterations": iters, "seconds": time.perf_counter() - t0,
-                       "stopped_at": stop, "residual": [float(x) for x in res]})
+                       "stopped_at": stop, "residual": None if res is None else [float(x) for x in res]})
         prev = s
     return prev, {"seconds": time.perf_counter() - t_all, "meshes": levels}
