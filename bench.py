@@ -459,8 +459,24 @@ def square_convergence(precision, max_iter, chunk=5, dtn_growth=None):
         out.update({"wall_heat_flux_total": float(np.sum(q)), "wall_faces": int(len(q)),
                     "rho_range": [float(np.min(m["rho"][fl])), float(np.max(m["rho"][fl]))],
                     "t_range": [float(np.min(m["t"][fl])), float(np.max(m["t"][fl]))]})
+        out["_state"] = ({k: m[k][fl] for k in ("rho", "u", "v", "t")}, q)
     s.close()
     return out
+
+
+def square_mixed_error(conv):
+    """Mixed form against FP64 at the same iteration count: relative L-infinity
+    difference of density, velocity, temperature and the wall heat flux."""
+    a, b = conv[0].pop("_state", None), conv[1].pop("_state", None)
+    if a is None or b is None or conv[0]["iterations"] != conv[1]["iterations"]:
+        return None
+    (m32, q32), (m64, q64) = a, b
+    speed = np.hypot(m64["u"], m64["v"]).max()
+    return {"iterations": conv[0]["iterations"],
+            "rho": float(np.abs(m32["rho"] - m64["rho"]).max() / np.abs(m64["rho"]).max()),
+            "velocity": float(max(np.abs(m32["u"] - m64["u"]).max(), np.abs(m32["v"] - m64["v"]).max()) / speed),
+            "t": float(np.abs(m32["t"] - m64["t"]).max() / np.abs(m64["t"]).max()),
+            "wall_heat_flux": float(np.abs(q32 - q64).max() / np.abs(q64).max())}
 
 
 def run_square(args):
@@ -476,6 +492,9 @@ def run_square(args):
     fp64 = measure_square(2, 2, "fp64")
     conv = [square_convergence("mixed", args.max_iter, dtn_growth=args.dtn_growth),
             square_convergence("fp64", min(args.max_iter, 60), dtn_growth=args.dtn_growth)]
+    mixed_error = square_mixed_error(conv)
+    for cv in conv:
+        cv.pop("_state", None)
     # full-multigrid start-up (Sec. 3.5, used by the paper for this case): 20x15 -> 40x30 -> 80x60 -> 160x120
     from paper_1704_03151_gb300 import fmg, miugks, workloads
     c = workloads.square_cylinder() if args.dtn_growth is None else workloads.square_cylinder(dtn_growth=args.dtn_growth)
@@ -489,7 +508,7 @@ def run_square(args):
     line = {"metric": "square-cylinder cell-velocity updates/s (Ma 5, Kn 0.1)", "value": mixed["value"],
             "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": "f32/f64", "data": "synthetic",
             "config": {"workload": mixed["workload"]}, "mixed": mixed, "fp64": fp64, "convergence": conv,
-            "fmg": info}
+            "mixed_error": mixed_error, "fmg": info}
     print(json.dumps(line))
     return 0
 
