@@ -245,7 +245,7 @@ def measure(precision, steps, warmup, world, rank, dev, with_e2e=True, with_ttr=
 MACRO_BYTES_PER_CELL = 152.0
 # DRAM bytes (read + write) of one finest-level k_macro_sgs<float> launch from
 # the ncu capture summarised in profiles/k_macro_sgs_cavity64_v32_mixed.md
-MACRO_TRAFFIC_MIXED = 1.793792e6
+MACRO_TRAFFIC_MIXED = 1.796352e6
 
 
 def macro_roofline(m, precision):
