@@ -116,9 +116,12 @@ miugks_status miugks_init_fields(miugks_solver *s, const double *rho, const doub
                                  const double *t);
 
 /* n outer iterations (Steps 1-8).  res_out (may be NULL): RMS of the
- * macroscopic residual per component (rho, rho U, rho V, rho eps) evaluated in
- * Step 1 of the last iteration (Eq. Residual_Def).  Returns MIUGKS_EDIVERGED
- * when the state became unphysical. */
+ * macroscopic residual per component (rho, rho U, rho V, rho eps) over the
+ * fluid cells, evaluated in Step 1 of the last iteration (Eq. Residual_Def).
+ * A cell whose FAS correction, predicted state or update would have
+ * non-positive density or internal energy keeps its previous value there (the
+ * paper is silent; this never triggers in smooth flow).  Returns
+ * MIUGKS_EDIVERGED when the state became unphysical all the same. */
 miugks_status miugks_step(miugks_solver *s, int n_iter, double res_out[4]);
 /* Enqueue n outer iterations on the solver's stream and return without waiting;
  * miugks_wait() then waits for them and returns the RMS residual of the last
@@ -159,11 +162,12 @@ miugks_status miugks_set_cycle(miugks_solver *s, int type);
 /* Full-multigrid start-up (Sec. 3.5): the state of `coarse`, a solver of the
  * same problem on the next coarser mesh (every second grid line of s's mesh,
  * same velocity grid and precision), becomes s's initial state by the bilinear
- * prolongation of Eq. prolongation applied to f velocity by velocity; W and q
- * follow from its moments and the iteration count restarts at 0.  s needs at
- * least two levels.  Waits for coarse's stream.  MIUGKS_EINVAL when the meshes,
- * velocity grids or precisions do not match, MIUGKS_ESTATE when coarse has no
- * state. */
+ * prolongation of Eq. prolongation applied to f velocity by velocity (a cell
+ * whose prolonged f has non-positive density or internal energy, and a cell in
+ * a body, takes its coarse cell's f); W and q follow from its moments and the
+ * iteration count restarts at 0.  s needs at least two levels.  Waits for
+ * coarse's stream.  MIUGKS_EINVAL when the meshes, bodies, velocity grids or
+ * precisions do not match, MIUGKS_ESTATE when coarse has no state. */
 miugks_status miugks_init_from_coarse(miugks_solver *s, const miugks_solver *coarse);
 
 /* Stages of one iteration on explicit host data, for kernel-level checks.
