@@ -59,6 +59,8 @@ def lib():
         L.oracle_time_coeffs.restype = None
         L.oracle_micro_slope.argtypes = [vp, d, d, d, vp]
         L.oracle_micro_slope.restype = None
+        L.oracle_shakhov.argtypes = [d, d, d, d, d, d, d, i, vp, vp, vp, vp]
+        L.oracle_shakhov.restype = None
         L.oracle_vanleer.argtypes = [d, d]
         L.oracle_vanleer.restype = d
         L.oracle_mu_ref.argtypes = [d, d]
@@ -304,6 +306,15 @@ def micro_slope(dw, U, V, lam):
     a = np.zeros(4)
     lib().oracle_micro_slope(_p(dw), U, V, lam, _p(a))
     return a
+
+
+def shakhov(rho, U, V, lam, qx, qy, pr, u, v):
+    """Shakhov equilibrium (G+, H+) at the nodes (u, v) (Sec. 2.1)."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    G, H = np.empty_like(u), np.empty_like(u)
+    lib().oracle_shakhov(rho, U, V, lam, qx, qy, pr, u.size, _p(u), _p(v), _p(G), _p(H))
+    return G, H
 
 
 def vanleer(s1, s2):

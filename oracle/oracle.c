@@ -145,6 +145,30 @@ static double maxw(double rho, double U, double V, double lam, double u, double 
     return rho * (lam / PI) * exp(-lam * ((u - U) * (u - U) + (v - V) * (v - V)));
 }
 
+/* Shakhov equilibrium at node (u, v) (Sec. 2.1, the Shakhov-type model that
+ * gives the Prandtl number): the 3-D model f_M [1 + (1-Pr) c.q (c^2/RT - 5) /
+ * (5 p R T)] reduced over xi_z with <xi_z^2> = RT, <xi_z^4> = 3 (RT)^2 and
+ * R = 1/2, p = rho/(2 lambda):
+ *   G+ = G_M [1 + (1-Pr) (4 lambda^2 / (5 rho)) (c.q) (2 lambda c^2 - 4)],
+ *   H+ = H_M [1 + (1-Pr) (4 lambda^2 / (5 rho)) (c.q) (2 lambda c^2 - 2)],
+ * c = (u - U, v - V), H_M = G_M K_int / (4 lambda).  The correction carries no
+ * mass, momentum or energy, and the heat flux of (G+, H+) is (1-Pr) q. */
+static void shakhov(double rho, double U, double V, double lam, double qx, double qy, double pr, double u, double v,
+                    double *gP, double *hP)
+{
+    double cx = u - U, cy = v - V, c2 = cx * cx + cy * cy;
+    double gM = maxw(rho, U, V, lam, u, v), hM = gM * KINT / (4.0 * lam);
+    double Fq = (1.0 - pr) * 4.0 * lam * lam / (5.0 * rho) * (cx * qx + cy * qy);
+    *gP = gM * (1.0 + Fq * (2.0 * lam * c2 - 4.0));
+    *hP = hM * (1.0 + Fq * (2.0 * lam * c2 - 2.0));
+}
+
+void oracle_shakhov(double rho, double U, double V, double lam, double qx, double qy, double pr, int n,
+                    const double *u, const double *v, double *G, double *H)
+{
+    for (int k = 0; k < n; ++k) shakhov(rho, U, V, lam, qx, qy, pr, u[k], v[k], &G[k], &H[k]);
+}
+
 /* ------------------------------------------------------------------ */
 /* UGKS building blocks (the explicit flux is deferred by the paper to  */
 /* its references; these are the standard UGKS forms)                   */
@@ -418,15 +442,12 @@ static void interior_face(oracle_solver *s, int axis, int cLL, int cL, int cR, i
     oracle_micro_slope(dwt, U0, V0, lam0, A);
     double qc[5];
     oracle_time_coeffs(dt, tau0, qc);
-    double shk = (1.0 - s->pr) * 4.0 * lam0 * lam0 / (5.0 * rho0);
     for (int m = 0; m < 4; ++m) F[m] = 0.0;
     for (int k = 0; k < nv; ++k) {
         double un = axis == 0 ? u[k] : v[k];
-        double cx = u[k] - U0, cy = v[k] - V0, c2 = cx * cx + cy * cy;
         double gM = maxw(rho0, U0, V0, lam0, u[k], v[k]), hM = gM * KINT / (4.0 * lam0);
-        double Fq = shk * (cx * q0[0] + cy * q0[1]);
-        double gP = gM * (1.0 + Fq * (2.0 * lam0 * c2 - 4.0));
-        double hP = hM * (1.0 + Fq * (2.0 * lam0 * c2 - 2.0));
+        double gP, hP;
+        shakhov(rho0, U0, V0, lam0, q0[0], q0[1], s->pr, u[k], v[k], &gP, &hP);
         double mGa, mHa, mGA, mHA;
         slope_moments(un > 0 ? aL : aR, u[k], v[k], gM, hM, lam0, &mGa, &mHa);
         slope_moments(A, u[k], v[k], gM, hM, lam0, &mGA, &mHA);
@@ -1314,7 +1335,6 @@ static void one_iteration(oracle_solver *s, double res[4])
         }
     }
     /* Step 4: r = (g~ - f)/tau~ - (1/V) sum S u_n f~ (Eq. microResidualDef) */
-    double shk0 = (1.0 - s->pr) * 4.0 / 5.0;
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
             int c = j * nx + i;
@@ -1330,10 +1350,8 @@ static void one_iteration(oracle_solver *s, double res[4])
             double qx = s->q[2 * c], qy = s->q[2 * c + 1];
             int fW = j * (nx + 1) + i, fE = fW + 1, fS = j * nx + i, fN = (j + 1) * nx + i;
             for (int k = 0; k < nv; ++k) {
-                double cx = s->u[k] - U, cy = s->v[k] - V, c2 = cx * cx + cy * cy;
-                double gM = maxw(rho, U, V, lam, s->u[k], s->v[k]), hM = gM * KINT / (4.0 * lam);
-                double Fq = shk0 * lam * lam / rho * (cx * qx + cy * qy);
-                double gt[2] = {gM * (1.0 + Fq * (2.0 * lam * c2 - 4.0)), hM * (1.0 + Fq * (2.0 * lam * c2 - 2.0))};
+                double gt[2];
+                shakhov(rho, U, V, lam, qx, qy, s->pr, s->u[k], s->v[k], &gt[0], &gt[1]);
                 for (int cp = 0; cp < 2; ++cp) {
                     const double *px = s->phx + (size_t)cp * L0->nfx * nv, *py = s->phy + (size_t)cp * L0->nfy * nv;
                     double div = (L0->dy[j] * (px[(size_t)fE * nv + k] - px[(size_t)fW * nv + k]) +
@@ -2122,7 +2140,6 @@ int oracle_steady_residual(oracle_solver *s, double *N)
     size_t nc = L0->nc;
     moments(s);
     flux_stage(s);
-    double shk0 = (1.0 - s->pr) * 4.0 / 5.0;
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
             int c = j * nx + i;
@@ -2133,10 +2150,8 @@ int oracle_steady_residual(oracle_solver *s, double *N)
             double qx = s->q[2 * c], qy = s->q[2 * c + 1];
             int fW = j * (nx + 1) + i, fE = fW + 1, fS = j * nx + i, fN = (j + 1) * nx + i;
             for (int k = 0; k < nv; ++k) {
-                double cx = s->u[k] - U, cy = s->v[k] - V, c2 = cx * cx + cy * cy;
-                double gM = maxw(rho, U, V, lam, s->u[k], s->v[k]), hM = gM * KINT / (4.0 * lam);
-                double Fq = shk0 * lam * lam / rho * (cx * qx + cy * qy);
-                double gt[2] = {gM * (1.0 + Fq * (2.0 * lam * c2 - 4.0)), hM * (1.0 + Fq * (2.0 * lam * c2 - 2.0))};
+                double gt[2];
+                shakhov(rho, U, V, lam, qx, qy, s->pr, s->u[k], s->v[k], &gt[0], &gt[1]);
                 for (int cp = 0; cp < 2; ++cp) {
                     const double *px = s->phx + (size_t)cp * L0->nfx * nv, *py = s->phy + (size_t)cp * L0->nfy * nv;
                     double div = (L0->dy[j] * (px[(size_t)fE * nv + k] - px[(size_t)fW * nv + k]) +

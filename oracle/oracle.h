@@ -73,6 +73,9 @@ int oracle_iterations(const oracle_solver *s);
 int oracle_vgrid(int n, double a, double b, int rule, double *x, double *w);
 void oracle_time_coeffs(double dt, double tau, double q[5]);
 void oracle_micro_slope(const double dw[4], double U, double V, double lam, double a[4]);
+/* Shakhov equilibrium (G+, H+) of state (rho, U, V, lambda) with heat flux (qx, qy) at n nodes (Sec. 2.1) */
+void oracle_shakhov(double rho, double U, double V, double lam, double qx, double qy, double pr, int n,
+                    const double *u, const double *v, double *G, double *H);
 double oracle_vanleer(double s1, double s2);
 double oracle_mu_ref(double kn, double omega);
 void oracle_wall_jacobian(const double W[4], double Uw, double Vw, double Tw, double M[16]);

@@ -210,3 +210,59 @@ def test_transfer_accuracy_on_stretched_mesh():
     # bilinear prolongation reproduces linear fields exactly (m_P = 2)
     back = o.prolong(0, cen.reshape(-1, 1))
     assert np.allclose(back[:, 0], lin[:, 0], rtol=1e-12, atol=1e-9)
+
+
+# ---------------------------------------------------------------- Shakhov equilibrium
+@pytest.mark.parametrize("rho,U,V,T,qx,qy,pr", [
+    (1.3, 0.3, -0.2, 1.2, 0.05, -0.03, 2.0 / 3.0),
+    (0.7, -0.45, 0.1, 0.8, -0.02, 0.04, 0.5),
+    (2.0, 0.0, 0.25, 1.6, 0.1, 0.0, 2.0 / 3.0),
+])
+def test_shakhov_moments_and_heat_flux(rho, U, V, T, qx, qy, pr):
+    """Sec. 2.1 names the Shakhov model as the one that gives the right Prandtl
+    number.  Whatever its reduced form, two facts of the model are fixed by
+    mathematics: the correction to the Maxwellian carries no mass, momentum or
+    energy, and the heat flux of the equilibrium is (1 - Pr) q, so that
+    relaxation toward it damps q at Pr times the rate of the stress.  On a wide,
+    fine trapezoid grid (spectrally accurate for Gaussians) the discrete sums
+    are the integrals to round-off.  A wrong polynomial in G+ fails the
+    momentum check, a wrong one in H+ or a wrong prefactor fails the heat flux,
+    and a peculiar velocity taken about 0 instead of (U, V) fails the mass
+    check."""
+    x, w1 = oracle.vgrid(101, -10.0, 10.0, 0)
+    u = np.repeat(x, x.size)
+    v = np.tile(x, x.size)
+    w = np.outer(w1, w1).ravel()
+    lam = 1.0 / T
+    G, H = oracle.shakhov(rho, U, V, lam, qx, qy, pr, u, v)
+    cx, cy = u - U, v - V
+    c2 = cx * cx + cy * cy
+    GM = rho * lam / math.pi * np.exp(-lam * c2)
+    HM = GM / (4.0 * lam)                       # one internal degree of freedom
+    tol = 1e-12
+    # conservative moments: those of the Maxwellian, rho eps = rho |U|^2/2 + 3 rho/(4 lam)
+    mom = [np.dot(w, G), np.dot(w, u * G), np.dot(w, v * G), np.dot(w, 0.5 * (u * u + v * v) * G + H)]
+    exact = [rho, rho * U, rho * V, 0.5 * rho * (U * U + V * V) + 3.0 * rho / (4.0 * lam)]
+    for a, b in zip(mom, exact):
+        assert abs(a - b) < tol * max(1.0, abs(b)), (mom, exact)
+    # the correction alone: zero mass, momentum, energy and second moments (it is odd in c)
+    dG, dH = G - GM, H - HM
+    for psi in (np.ones_like(u), u, v, cx * cx, cx * cy):
+        assert abs(np.dot(w, psi * dG)) < tol
+    assert abs(np.dot(w, 0.5 * (u * u + v * v) * dG + dH)) < tol
+    # heat flux of the equilibrium: (1 - Pr) q
+    q = [np.dot(w, cx * (0.5 * c2 * G + H)), np.dot(w, cy * (0.5 * c2 * G + H))]
+    assert abs(q[0] - (1.0 - pr) * qx) < tol and abs(q[1] - (1.0 - pr) * qy) < tol, (q, qx, qy)
+
+
+def test_shakhov_reduces_to_maxwellian():
+    """With Pr = 1 or q = 0 the Shakhov equilibrium is the reduced Maxwellian
+    G_M = rho (lam/pi) exp(-lam |c|^2), H_M = G_M K_int / (4 lam)."""
+    x, _ = oracle.vgrid(24, -5.0, 5.0, 0)
+    u, v = np.repeat(x, x.size), np.tile(x, x.size)
+    rho, U, V, lam = 1.1, 0.2, -0.1, 0.9
+    GM = rho * lam / math.pi * np.exp(-lam * ((u - U) ** 2 + (v - V) ** 2))
+    for qx, qy, pr in ((0.3, -0.2, 1.0), (0.0, 0.0, 2.0 / 3.0)):
+        G, H = oracle.shakhov(rho, U, V, lam, qx, qy, pr, u, v)
+        assert np.allclose(G, GM, rtol=1e-14, atol=0)
+        assert np.allclose(H, GM / (4.0 * lam), rtol=1e-14, atol=0)
