@@ -264,28 +264,32 @@ miugks_status miugks_kernel_times(miugks_solver *s, double *flux_ms, double *swe
 miugks_status miugks_macro_sweep_times(miugks_solver *s, double *ms, int *launches);
 
 /* Residual norm of caller-owned device arrays without allocating anything.
- * The paper has no counterpart: this serves callers that cannot allocate at
- * the point where they need the convergence measure -- code running during a
- * CUDA graph capture (an allocation there breaks the capture), frameworks that
- * only hand out their own pre-sized pools, and latency-critical loops that
- * must not enter the allocator.
- *   R_dev:   nc x 4 residuals (device, [cell][component]);
- *   W_dev:   nc x 4 conservative variables (device), used for a health count;
- *   out_dev: 5 doubles (device): RMS of each component over the cells
- *            (Eq. Residual_Def) and the number of cells with non-positive
- *            density or internal energy (or NaN);
+ * The paper has no counterpart.  It serves callers that cannot allocate device
+ * memory at the point where they need the convergence measure: host frameworks
+ * that lend only their own pre-sized pools and forbid the CUDA allocator, and
+ * latency-critical loops that must not enter any allocator.
+ *   R_dev:     nc x 4 residuals (device, [cell][component]);
+ *   W_dev:     nc x 4 conservative variables (device), used for a health count;
+ *   solid_dev: nc bytes (device), nonzero for a cell inside a body, or NULL
+ *              when there is no body; such cells are skipped;
+ *   out_dev:   5 doubles (device): the root mean square of each residual
+ *              component over the fluid cells (the norm miugks_residual
+ *              reports), then the number of fluid cells with non-positive
+ *              density or internal energy (or NaN);
  *   cuda_stream: cudaStream_t or NULL (legacy default stream).
  * The partial sums live in a fixed scratch array inside the library (one
- * __device__ array of 4096 rows of 5 doubles per GPU that loads it, kept until
+ * __device__ array of 4096 rows of 6 doubles per GPU that loads it, kept until
  * process exit): nc is limited to 1,048,576 cells, and larger nc returns
- * MIUGKS_EINVAL.  The first call on a device resolves the scratch address with
- * that device current; make that first call before any stream capture.  Every
- * call overwrites the rows it reads, so nothing needs clearing, but all calls
- * share the one array: calls whose kernels overlap on the GPU race and must be
- * serialised by the caller.  Asynchronous on cuda_stream; the error message of
- * a failed call is returned by miugks_last_error(NULL). */
-miugks_status miugks_residual_rms_noalloc(const double *R_dev, const double *W_dev, int nc, double *out_dev,
-                                          void *cuda_stream);
+ * MIUGKS_EINVAL without launching anything.  The first call on a device
+ * resolves the scratch address with that device current and keeps it for the
+ * life of the process (so no cudaDeviceReset in between); make that first call
+ * before any stream capture.  Every call overwrites the rows it reads, so
+ * nothing needs clearing, but all calls share the one array: calls whose
+ * kernels overlap on the GPU race and must be serialised by the caller.
+ * Asynchronous on cuda_stream; the error message of a failed call is returned
+ * by miugks_last_error(NULL). */
+miugks_status miugks_residual_rms_noalloc(const double *R_dev, const double *W_dev, const unsigned char *solid_dev,
+                                          int nc, double *out_dev, void *cuda_stream);
 
 #ifdef __cplusplus
 }

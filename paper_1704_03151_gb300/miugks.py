@@ -100,7 +100,7 @@ def load():
         fn.restype = _i
     L.miugks_destroy.restype = None
     L.miugks_last_error.restype = ctypes.c_char_p
-    L.miugks_residual_rms_noalloc.argtypes = [vp, vp, _i, vp, vp]
+    L.miugks_residual_rms_noalloc.argtypes = [vp, vp, vp, _i, vp, vp]
     L.miugks_residual_rms_noalloc.restype = _i
     _lib = L
     return L
