@@ -152,7 +152,7 @@ def body_face_ids(solid, fbx, fby, bc_id):
 
 
 def square_cylinder(ma=5.0, kn=0.1, nvel=89, vmax=15.0, levels=4, nx_side=64, nx_sq=32, ny_side=48, ny_sq=24,
-                    half=7.5, omega=0.81, dtn_growth=3.0, rule=None):
+                    half=7.5, omega=0.81, dtn_growth=3.0, rule=TRAPEZOID):
     """Flow past a unit square at the centre of the box [-half, half]^2
     (Sec. 4.3, on the full domain): nx_side | nx_sq | nx_side cells in x and
     ny_side | ny_sq | ny_side in y, uniform across the square and stretched
@@ -160,7 +160,10 @@ def square_cylinder(ma=5.0, kn=0.1, nvel=89, vmax=15.0, levels=4, nx_side=64, nx
     cell).  The square's cells are solid.  BC ids: 0 square wall (T_w = T_inf),
     1 farfield (inflow, top, bottom), 2 outflow (zero gradient, downstream).
     The initial state is the freestream with a rear region x > 0.5 at 0.1 of
-    its density and at rest (`rear` key, see initial_fields)."""
+    its density and at rest (`rear` key, see initial_fields).  Velocity
+    weights: the trapezoid rule, the closed Newton-Cotes rule of degree 1
+    (Sec. 4.3 names Newton-Cotes rules without their degree); composite Boole
+    (rule=BOOLE) is available for (nvel - 1) % 4 == 0."""
     gamma = 5.0 / 3.0
     u_inf = ma * math.sqrt(gamma / 2.0)
     hx, hy = 1.0 / nx_sq, 1.0 / ny_sq
@@ -173,8 +176,6 @@ def square_cylinder(ma=5.0, kn=0.1, nvel=89, vmax=15.0, levels=4, nx_side=64, nx
     solid[ny_side:ny_side + ny_sq, nx_side:nx_side + nx_sq] = 1
     fbx, fby = edge_face_ids(nx, ny, 1, 2, 1, 1)
     fbx, fby = body_face_ids(solid, fbx, fby, 0)
-    if rule is None:
-        rule = BOOLE if (nvel - 1) % 4 == 0 else TRAPEZOID
     return {
         "name": "square%dx%d_v%d_ma%g_kn%g" % (nx, ny, nvel, ma, kn),
         "nx": nx, "ny": ny, "x_nodes": x, "y_nodes": y,
