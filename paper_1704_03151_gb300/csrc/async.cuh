@@ -92,4 +92,18 @@ __device__ __forceinline__ void st_async(unsigned raddr, double v, unsigned rmb)
                  : "memory");
 }
 
+// asynchronous 16-byte global -> shared copy (LDGSTS, cached in L2 only; both
+// addresses 16-byte aligned), completed per commit group of the issuing thread
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(sdst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// wait until at most N of this thread's most recent commit groups are pending
+template <int N>
+__device__ __forceinline__ void cp_async_wait_n()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 }  // namespace miugks

@@ -25,6 +25,7 @@
 //     diagonals (no grid-wide synchronisation); the incoming velocities of
 //     line cells are ordinary updates there, their ghost term being known.
 #include "kernels.cuh"
+#include "async.cuh"
 #include <algorithm>
 
 namespace cg = cooperative_groups;
@@ -46,7 +47,6 @@ __device__ __forceinline__ void cp_async_elem(F* sdst, const F* gsrc)
     else
         asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gsrc) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 // wait until at most n (0..7) of this thread's most recent groups are pending
 __device__ __forceinline__ void cp_async_wait(int n)
 {
@@ -423,9 +423,24 @@ __device__ void chain_rest(cg::cluster_group& cl, const MicroArgs& M, const doub
                 int i, j;
                 cell(st, i, j);
                 if (M.bc[face_bc(i, j)].type == BC_WALL) {
-                    const size_t c0 = (size_t)(j * nx + i) * nv;
-                    for (int q = p; q < nloc; q += P)
-                        if (lw[q] != F(0)) sum += lw[q] * x[c0 + lk[q]];
+                    // eight independent loads in flight (the values of incoming velocities are not
+                    // read: they belong to the previous sweep and may be anything)
+                    const F* xc0 = x + (size_t)(j * nx + i) * nv;
+                    F acc[8] = {F(0), F(0), F(0), F(0), F(0), F(0), F(0), F(0)};
+                    int q = p;
+                    for (; q + 7 * P < nloc; q += 8 * P) {
+                        F xv[8];
+                        #pragma unroll
+                        for (int u8 = 0; u8 < 8; ++u8) {
+                            const int qq = q + u8 * P;
+                            xv[u8] = lw[qq] != F(0) ? xc0[lk[qq]] : F(0);
+                        }
+                        #pragma unroll
+                        for (int u8 = 0; u8 < 8; ++u8) acc[u8] += lw[q + u8 * P] * xv[u8];
+                    }
+                    for (int u8 = 0; q < nloc; q += P, ++u8)
+                        if (lw[q] != F(0)) acc[u8] += lw[q] * xc0[lk[q]];
+                    sum = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
                 }
             }
             if (P == 1) {
@@ -756,17 +771,6 @@ k_sgs_chain_body(MicroArgs M, const double* __restrict__ Zw, const F* __restrict
     cl.sync();   // keep every CTA's shared memory alive until all remote reads are done
 }
 
-// asynchronous 16-byte copy (both addresses 16-byte aligned)
-__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc)
-{
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gsrc) : "memory");
-}
-template <int N>
-__device__ __forceinline__ void cp_async_wait_n()
-{
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
 
 // four consecutive values through 16-byte accesses (16-byte aligned for float, 32 for double)
 __device__ __forceinline__ void ld4(const float* p, float (&v)[4])
