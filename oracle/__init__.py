@@ -14,29 +14,44 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
+_LIB_OMP = os.path.join(_BUILD, "liboracle_omp.so")
 _lib = None
+_lib_omp = None
 
 WALL, SYMMETRY, FARFIELD, OUTFLOW = 0, 1, 2, 3
 
 
-def build(force=False):
-    """Compile the oracle into oracle/_build/liboracle.so (gcc, -O2, no fast-math)."""
+def build(force=False, omp=False):
+    """Compile the oracle into oracle/_build/liboracle.so (gcc, -O2, no fast-math);
+    omp=True builds liboracle_omp.so from the same source with -fopenmp (faces,
+    cells and the cells of each sweep diagonal over threads, the same bits)."""
     src = os.path.join(_HERE, "oracle.c")
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= max(
+    out = _LIB_OMP if omp else _LIB
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= max(
             os.path.getmtime(src), os.path.getmtime(os.path.join(_HERE, "oracle.h"))):
-        return _LIB
+        return out
     os.makedirs(_BUILD, exist_ok=True)
-    tmp = _LIB + ".%d.tmp" % os.getpid()
+    tmp = out + ".%d.tmp" % os.getpid()
     subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fno-fast-math",
-                           "-ffp-contract=off", "-o", tmp, src, "-lm"])
-    os.replace(tmp, _LIB)
-    return _LIB
+                           "-ffp-contract=off"] + (["-fopenmp"] if omp else []) + ["-o", tmp, src, "-lm"])
+    os.replace(tmp, out)
+    return out
 
 
-def lib():
-    global _lib
+def lib(omp=False):
+    global _lib, _lib_omp
+    if omp:
+        if _lib_omp is None:
+            _lib_omp = _declare(ctypes.CDLL(build(omp=True)))
+        return _lib_omp
     if _lib is None:
-        L = ctypes.CDLL(build())
+        _lib = _declare(ctypes.CDLL(build()))
+    return _lib
+
+
+def _declare(L):
+    """argument and result types of the exported functions"""
+    if True:
         P = ctypes.POINTER
         d, i, vp = ctypes.c_double, ctypes.c_int, ctypes.c_void_p
         L.oracle_create.restype = vp
@@ -88,9 +103,10 @@ def lib():
         L.oracle_residual_dtheta.argtypes = [vp, i, i, vp]
         L.oracle_stage_cs.argtypes = [vp, vp, vp, vp]
         L.oracle_set_cycle.argtypes = [vp, i]
+        L.oracle_adapt_log.argtypes = [vp, vp, i]
+        L.oracle_set_adapt_ratio.argtypes = [vp, d]
         L.oracle_init_from_coarse.argtypes = [vp, vp]
-        _lib = L
-    return _lib
+    return L
 
 
 def _p(a):
@@ -107,8 +123,9 @@ class Oracle:
     ``paper_1704_03151_gb300.workloads`` (mesh nodes, face BC ids, BC table,
     velocity grid, gas and multigrid options)."""
 
-    def __init__(self, case):
-        L = lib()
+    def __init__(self, case, omp=False):
+        """omp=True: the OpenMP build of the same source (same results bit for bit)."""
+        self._L = L = lib(omp)
         self.case = case
         self.nx, self.ny = case["nx"], case["ny"]
         self.nc = self.nx * self.ny
@@ -130,9 +147,13 @@ class Oracle:
             raise RuntimeError("oracle_create: " + L.oracle_last_error().decode())
         self.nv = L.oracle_nv(self.h)
 
+    def _check(self, st):
+        if st:
+            raise RuntimeError("oracle: " + self._L.oracle_last_error().decode())
+
     def close(self):
         if self.h:
-            lib().oracle_destroy(self.h)
+            self._L.oracle_destroy(self.h)
             self.h = None
 
     def __del__(self):
@@ -143,71 +164,80 @@ class Oracle:
 
     def init_from_coarse(self, coarse):
         """Initial state by bilinear prolongation of f from an oracle on the next coarser mesh."""
-        _check(lib().oracle_init_from_coarse(self.h, coarse.h))
+        self._check(self._L.oracle_init_from_coarse(self.h, coarse.h))
 
     def set_cycle(self, cycle):
-        """Multigrid cycle type of both cycles: "V", "W" or "F"."""
-        _check(lib().oracle_set_cycle(self.h, {"V": 0, "W": 1, "F": 2}[cycle]))
+        """Multigrid cycle type of both cycles: "V", "W", "F" or "A" (adaptive)."""
+        self._check(self._L.oracle_set_cycle(self.h, {"V": 0, "W": 1, "F": 2, "A": 3}[cycle]))
+
+    def set_adapt_ratio(self, ratio):
+        self._check(self._L.oracle_set_adapt_ratio(self.h, ratio))
+
+    def adapt_log(self, cap=4096):
+        """Decisions of the adaptive cycle so far, oldest first (1 = a second coarse visit)."""
+        out = np.zeros(cap, dtype=np.uint8)
+        n = self._L.oracle_adapt_log(self.h, _p(out), cap)
+        return out[:min(n, cap)].copy()
 
     def init_uniform(self, rho, u, v, t):
-        _check(lib().oracle_init_uniform(self.h, rho, u, v, t))
+        self._check(self._L.oracle_init_uniform(self.h, rho, u, v, t))
 
     def init_fields(self, rho, u, v, t):
         arrs = [np.ascontiguousarray(a, dtype=np.float64).ravel() for a in (rho, u, v, t)]
-        _check(lib().oracle_init_fields(self.h, *[_p(a) for a in arrs]))
+        self._check(self._L.oracle_init_fields(self.h, *[_p(a) for a in arrs]))
 
     def step(self, n=1):
         res = np.zeros(4)
-        _check(lib().oracle_step(self.h, n, _p(res)))
+        self._check(self._L.oracle_step(self.h, n, _p(res)))
         return res
 
     def residual(self):
         R = np.zeros((self.nc, 4))
-        _check(lib().oracle_residual(self.h, _p(R)))
+        self._check(self._L.oracle_residual(self.h, _p(R)))
         return R
 
     def macro(self):
         out = [np.zeros(self.nc) for _ in range(6)]
-        _check(lib().oracle_get_macro(self.h, *[_p(a) for a in out]))
+        self._check(self._L.oracle_get_macro(self.h, *[_p(a) for a in out]))
         return dict(zip(("rho", "u", "v", "t", "qx", "qy"), out))
 
     def get_f(self):
         f = np.zeros((2, self.nc, self.nv))
-        _check(lib().oracle_get_f(self.h, _p(f)))
+        self._check(self._L.oracle_get_f(self.h, _p(f)))
         return f
 
     def set_f(self, f):
         f = np.ascontiguousarray(f, dtype=np.float64)
-        _check(lib().oracle_set_f(self.h, _p(f)))
+        self._check(self._L.oracle_set_f(self.h, _p(f)))
 
     def set_bc(self, b, rho, u, v, t):
-        _check(lib().oracle_set_bc(self.h, b, rho, u, v, t))
+        self._check(self._L.oracle_set_bc(self.h, b, rho, u, v, t))
 
     def wall(self, bc):
         n = ctypes.c_int(0)
-        lib().oracle_get_wall(self.h, bc, ctypes.byref(n), None, None, None)
+        self._L.oracle_get_wall(self.h, bc, ctypes.byref(n), None, None, None)
         cap = n.value
         p, tau, q = np.zeros(cap), np.zeros(cap), np.zeros(cap)
         n = ctypes.c_int(cap)
-        _check(lib().oracle_get_wall(self.h, bc, ctypes.byref(n), _p(p), _p(tau), _p(q)))
+        self._check(self._L.oracle_get_wall(self.h, bc, ctypes.byref(n), _p(p), _p(tau), _p(q)))
         return p, tau, q
 
     def iterations(self):
-        return lib().oracle_iterations(self.h)
+        return self._L.oracle_iterations(self.h)
 
     # ---- steady equations and their adjoint ----
     def steady_residual(self):
         """N(f) of the steady equations at the current f (Eq. microResidualDef
         with the predicted state equal to the moments of f)."""
         N = np.zeros((2, self.nc, self.nv))
-        _check(lib().oracle_steady_residual(self.h, _p(N)))
+        self._check(self._L.oracle_steady_residual(self.h, _p(N)))
         return N
 
     def adjoint_residual(self, mu):
         """(dN/df)^T mu at the current f."""
         mu = np.ascontiguousarray(mu, dtype=np.float64).reshape(2, self.nc, self.nv)
         out = np.zeros_like(mu)
-        _check(lib().oracle_adjoint_residual(self.h, _p(mu), _p(out)))
+        self._check(self._L.oracle_adjoint_residual(self.h, _p(mu), _p(out)))
         return out
 
     def objective(self, obj, bc):
@@ -216,33 +246,33 @@ class Oracle:
         J = np.zeros(1)
         dJdf = np.zeros((2, self.nc, self.nv))
         dJdth = np.zeros(3)
-        _check(lib().oracle_objective(self.h, obj, bc, _p(J), _p(dJdf), _p(dJdth)))
+        self._check(self._L.oracle_objective(self.h, obj, bc, _p(J), _p(dJdf), _p(dJdth)))
         return float(J[0]), dJdf, dJdth
 
     def residual_dtheta(self, bc, param):
         """dN/dtheta at fixed f, theta = (T, u, v)[param] of wall `bc`."""
         dN = np.zeros((2, self.nc, self.nv))
-        _check(lib().oracle_residual_dtheta(self.h, bc, param, _p(dN)))
+        self._check(self._L.oracle_residual_dtheta(self.h, bc, param, _p(dN)))
         return dN
 
     # ---- stages for the pins ----
     def level_size(self, lev):
         nx, ny = ctypes.c_int(), ctypes.c_int()
-        _check(lib().oracle_level_size(self.h, lev, ctypes.byref(nx), ctypes.byref(ny)))
+        self._check(self._L.oracle_level_size(self.h, lev, ctypes.byref(nx), ctypes.byref(ny)))
         return nx.value, ny.value
 
     def stage_flux(self):
         nfx, nfy = (self.nx + 1) * self.ny, self.nx * (self.ny + 1)
         R = np.zeros((self.nc, 4))
         px, py = np.zeros((2, nfx, self.nv)), np.zeros((2, nfy, self.nv))
-        _check(lib().oracle_stage_flux(self.h, _p(R), _p(px), _p(py)))
+        self._check(self._L.oracle_stage_flux(self.h, _p(R), _p(px), _p(py)))
         return R, px, py
 
     def sgs_micro(self, lev, inv_tau, r, order=0):
         r = np.ascontiguousarray(r, dtype=np.float64)
         it = np.ascontiguousarray(inv_tau, dtype=np.float64)
         x = np.zeros_like(r)
-        _check(lib().oracle_stage_sgs_micro(self.h, lev, _p(it), _p(r), _p(x), order))
+        self._check(self._L.oracle_stage_sgs_micro(self.h, lev, _p(it), _p(r), _p(x), order))
         return x
 
     def cs_cycle(self, inv_tau_levels, r):
@@ -250,26 +280,26 @@ class Oracle:
         it = np.ascontiguousarray(np.concatenate([np.ravel(a) for a in inv_tau_levels]), dtype=np.float64)
         r = np.ascontiguousarray(r, dtype=np.float64)
         df = np.zeros_like(r)
-        _check(lib().oracle_stage_cs(self.h, _p(it), _p(r), _p(df)))
+        self._check(self._L.oracle_stage_cs(self.h, _p(it), _p(r), _p(df)))
         return df
 
     def apply_micro(self, lev, inv_tau, x):
         x = np.ascontiguousarray(x, dtype=np.float64)
         it = np.ascontiguousarray(inv_tau, dtype=np.float64)
         y = np.zeros_like(x)
-        _check(lib().oracle_stage_apply_micro(self.h, lev, _p(it), _p(x), _p(y)))
+        self._check(self._L.oracle_stage_apply_micro(self.h, lev, _p(it), _p(x), _p(y)))
         return y
 
     def sgs_macro(self, lev, W, Wg, R, order=0):
         W, Wg, R = (np.ascontiguousarray(a, dtype=np.float64) for a in (W, Wg, R))
         dW = np.zeros_like(W)
-        _check(lib().oracle_stage_sgs_macro(self.h, lev, _p(W), _p(Wg), _p(R), _p(dW), order))
+        self._check(self._L.oracle_stage_sgs_macro(self.h, lev, _p(W), _p(Wg), _p(R), _p(dW), order))
         return dW
 
     def resid_macro(self, lev, W, Wg):
         W, Wg = (np.ascontiguousarray(a, dtype=np.float64) for a in (W, Wg))
         RE = np.zeros_like(W)
-        _check(lib().oracle_stage_resid_macro(self.h, lev, _p(W), _p(Wg), _p(RE)))
+        self._check(self._L.oracle_stage_resid_macro(self.h, lev, _p(W), _p(Wg), _p(RE)))
         return RE
 
     def restrict(self, lev, fine):
@@ -277,7 +307,7 @@ class Oracle:
         nx, ny = self.level_size(lev + 1)
         m = fine.shape[-1]
         coarse = np.zeros((nx * ny, m))
-        _check(lib().oracle_stage_restrict(self.h, lev, m, _p(fine), _p(coarse)))
+        self._check(self._L.oracle_stage_restrict(self.h, lev, m, _p(fine), _p(coarse)))
         return coarse
 
     def prolong(self, lev, coarse):
@@ -285,7 +315,7 @@ class Oracle:
         nx, ny = self.level_size(lev)
         m = coarse.shape[-1]
         fine = np.zeros((nx * ny, m))
-        _check(lib().oracle_stage_prolong(self.h, lev, m, _p(coarse), _p(fine)))
+        self._check(self._L.oracle_stage_prolong(self.h, lev, m, _p(coarse), _p(fine)))
         return fine
 
 

@@ -33,6 +33,20 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* Optional OpenMP build (-fopenmp, a separate library): faces, cells and the
+ * cells of one anti-diagonal of a sweep are spread over threads; each face or
+ * cell is computed by one thread with the serial build's arithmetic in the
+ * serial build's order, so the two builds give the same bits.  Scratch is
+ * per thread. */
+#ifdef _OPENMP
+#include <omp.h>
+#define ORC_TID omp_get_thread_num()
+#define ORC_MAXTHR omp_get_max_threads()
+#else
+#define ORC_TID 0
+#define ORC_MAXTHR 1
+#endif
+
 #define KINT 1      /* internal (z-translational) degrees of freedom of the 2-D reduced model */
 #define MAXL 8
 #define PI 3.14159265358979323846
@@ -61,6 +75,16 @@ typedef struct {
     double *r, *df, *dl, *Ad, *inv_tau;
 } olev_t;
 
+/* Adaptive multigrid cycle (Sec. 3.4 names it without a rule; reading): a
+ * level visits its coarser level a second time when the first visit left more
+ * than a ratio (ADAPT_RATIO unless set) of the coarse residual it started from
+ * (L2 norms over all values), at most ADAPT_MAX_VISITS visits.  With ratio 0
+ * every level visits twice (the W cycle); with a ratio above any reduction,
+ * once (the V cycle). */
+#define ADAPT_RATIO 0.2
+#define ADAPT_MAX_VISITS 2
+#define ADAPT_LOG 4096
+
 /* one boundary face of a cell, as seen from that cell */
 typedef struct { int bc, axis, outsign; double S, V; } bface_t;
 
@@ -76,12 +100,17 @@ struct oracle_solver {
     obc_t *bc;
     double *Cw; /* per BC: unit-density Maxwellian at the BC state, G part */
     int nu1, nu2, nuc;
-    int cycle; /* 0 V, 1 W, 2 F (Sec. 3.4: V, W, F and adaptive cycles) */
+    int cycle; /* 0 V, 1 W, 2 F, 3 adaptive (Sec. 3.4: V, W, F and adaptive cycles) */
+    double adapt_ratio;                   /* ADAPT_RATIO unless set */
+    int adapt_n;                          /* adaptive-cycle decisions taken so far */
+    unsigned char adapt_log[ADAPT_LOG];   /* each: 1 = a second coarse visit (ring of ADAPT_LOG) */
     double cfl, dtn_growth, dtp_min;
     int iter;
     double *f, *W, *q, *R;
     double *phx, *phy, *Fx, *Fy;
-    double *tmp0, *tmp1, *tmp2; /* per-face / per-cell velocity scratch (2 x nv each) */
+    int nthr;                   /* threads of the parallel loops (1 in the serial build) */
+    double *tmp0, *tmp1, *tmp2; /* per-face / per-cell velocity scratch (2 x nv per thread each) */
+    double *sD, *sbase, *sxc;   /* sweep scratch (nv, 2 nv, 2 nv per thread) */
 };
 
 /* ------------------------------------------------------------------ */
@@ -382,7 +411,7 @@ static void interior_face(oracle_solver *s, int axis, int cLL, int cL, int cR, i
 {
     int nv = s->nv;
     const double *u = s->u, *v = s->v, *w = s->w;
-    double *f0 = s->tmp0, *sg = s->tmp1; /* [comp][k] */
+    double *f0 = s->tmp0 + (size_t)ORC_TID * 2 * nv, *sg = s->tmp1 + (size_t)ORC_TID * 2 * nv; /* [comp][k] */
     /* reconstruction (van Leer) and upwinding of the initial distribution */
     for (int k = 0; k < nv; ++k) {
         double un = axis == 0 ? u[k] : v[k];
@@ -505,7 +534,7 @@ static void boundary_face(oracle_solver *s, int bcid, int axis, int outsign, int
                           double *phG, double *phH, double F[4])
 {
     int nv = s->nv;
-    double *fG = s->tmp2, *fH = s->tmp2 + nv;
+    double *fG = s->tmp2 + (size_t)ORC_TID * 2 * nv, *fH = fG + nv;
     boundary_face_f(s, bcid, axis, outsign, c, fG, fH);
     for (int m = 0; m < 4; ++m) F[m] = 0.0;
     for (int k = 0; k < nv; ++k) {
@@ -526,6 +555,7 @@ static void flux_stage(oracle_solver *s)
     olev_t *Lv = &s->lev[0];
     int nx = Lv->nx, ny = Lv->ny, nv = s->nv;
     size_t nfx = Lv->nfx, nfy = Lv->nfy;
+#pragma omp parallel for num_threads(s->nthr) schedule(dynamic, 1)
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i <= nx; ++i) {
             int fi = j * (nx + 1) + i;
@@ -551,6 +581,7 @@ static void flux_stage(oracle_solver *s)
                           Lv->xn[i] - Lv->xc[i - 1], Lv->xc[i] - Lv->xn[i],
                           Lv->dx[i - 1], Lv->dx[i], pG, pH, s->Fx + 4 * fi);
         }
+#pragma omp parallel for num_threads(s->nthr) schedule(dynamic, 1)
     for (int j = 0; j <= ny; ++j)
         for (int i = 0; i < nx; ++i) {
             int fi = j * nx + i;
@@ -818,6 +849,7 @@ static void sgs_macro(const oracle_solver *s, const olev_t *Lv, const double *W,
 /* Volume-weighted restriction of an [cell][m] array from level l to l+1 */
 static void restrict_lv(const olev_t *F, const olev_t *C, int m, const double *fine, double *coarse)
 {
+#pragma omp parallel for schedule(static) if (m > 4)
     for (int J = 0; J < C->ny; ++J)
         for (int I = 0; I < C->nx; ++I) {
             double *out = coarse + (size_t)(J * C->nx + I) * m;
@@ -881,6 +913,7 @@ static void stencil(const olev_t *F, const olev_t *C, int i, int j, int *IN, int
  * correction), or their coarse cell's value with inject_solid (a state). */
 static void prolong_lv_s(const olev_t *F, const olev_t *C, int m, const double *coarse, double *fine, int inject_solid)
 {
+#pragma omp parallel for schedule(static) if (m > 4)
     for (int j = 0; j < F->ny; ++j)
         for (int i = 0; i < F->nx; ++i) {
             int I = i / 2, J = j / 2, IN, JN;
@@ -903,10 +936,18 @@ static void prolong_lv(const olev_t *F, const olev_t *C, int m, const double *co
     prolong_lv_s(F, C, m, coarse, fine, 0);
 }
 
+static double sumsq(const double *a, size_t n)
+{
+    double t = 0.0;
+    for (size_t q = 0; q < n; ++q) t += a[q] * a[q];
+    return t;
+}
+
 /* FAS cycle (Eq. FASCYC): W_l <- FAS(l, W_l^n, R_l); lv->Wn holds W_l^n and
  * lv->Rc the restricted (or UGKS) residual on entry; the result is left in lv->Wc.
  * The cycle type (Sec. 3.4) sets the coarse visits of a level: V one visit, W
- * two W visits, F one F visit then one V visit.  A visit after the first starts
+ * two W visits, F one F visit then one V visit, adaptive one adaptive visit and
+ * a second one when the first did not reduce the coarse residual five-fold.  A visit after the first starts
  * from the coarse state the previous one left, with the same forcing function
  * and the same frozen Gamma. */
 static void fas_visit(oracle_solver *s, int l, int type, int first);
@@ -946,7 +987,24 @@ static void fas_visit(oracle_solver *s, int l, int type, int first)
         restrict_lv(Lv, Cv, 4, Lv->Wc, Cv->Wn);
         restrict_lv(Lv, Cv, 4, R, Cv->Rc);
         fas(s, l + 1, type);                                   /* first coarse visit, of this type */
-        if (type != 0) fas_visit(s, l + 1, type == 1 ? 1 : 0, 0); /* W: another W visit; F: a V visit */
+        if (type == 1 || type == 2) fas_visit(s, l + 1, type == 1 ? 1 : 0, 0); /* W: another W visit; F: a V visit */
+        if (type == 3) {
+            /* adaptive: visit again while a visit leaves more than ADAPT_RATIO of the coarse
+             * residual it started from (the coarse residual on entry is the restricted R) */
+            size_t c4 = 4 * (size_t)Cv->nc;
+            double *Rh = (double *)malloc(c4 * sizeof(double));
+            double before = sumsq(Cv->Rc, c4);
+            for (int visit = 1; visit < ADAPT_MAX_VISITS; ++visit) {
+                resid_macro(s, Cv, Cv->Wc, Cv->Wn, Cv->RE);
+                for (size_t q = 0; q < c4; ++q) Rh[q] = Cv->P[q] + Cv->RE[q];
+                double after = sumsq(Rh, c4);
+                s->adapt_log[s->adapt_n++ % ADAPT_LOG] = after > s->adapt_ratio * s->adapt_ratio * before;
+                if (!(after > s->adapt_ratio * s->adapt_ratio * before)) break;
+                before = after;
+                fas_visit(s, l + 1, 3, 0);
+            }
+            free(Rh);
+        }
         size_t c4 = 4 * (size_t)Cv->nc;
         for (size_t q = 0; q < c4; ++q) Cv->dW[q] = Cv->Wc[q] - Cv->Wn[q];
         double *corr = (double *)malloc(n4 * sizeof(double));
@@ -1008,7 +1066,7 @@ static void cell_solve(const oracle_solver *s, int c, int nb, const bface_t *bf,
 {
     int nv = s->nv;
     size_t nc = s->lev[0].nc; (void)nc;
-    double *den = s->tmp0, *xo = s->tmp1;
+    double *den = s->tmp0 + (size_t)ORC_TID * 2 * nv, *xo = s->tmp1 + (size_t)ORC_TID * 2 * nv;
     for (int k = 0; k < nv; ++k) {
         den[k] = D[k];
         for (int b = 0; b < nb; ++b)
@@ -1088,74 +1146,80 @@ static void cell_solve(const oracle_solver *s, int c, int nb, const bface_t *bf,
 
 #define AT(arr, nc_, nv_, cp, c, k) ((arr)[((size_t)(cp) * (nc_) + (c)) * (nv_) + (k)])
 
+/* one cell (i, j) of a sweep pass: D, base and xc are scratch of nv, 2 nv, 2 nv */
+static void sweep_cell(oracle_solver *s, const olev_t *Lv, const double *inv_tau, const double *r, double *x, int pass,
+                       int i, int j, double *D, double *base, double *xc)
+{
+    int nx = Lv->nx, ny = Lv->ny, nv = s->nv;
+    size_t nc = Lv->nc;
+    int c = j * nx + i;
+    if (Lv->solid[c]) {
+        for (int cp = 0; cp < 2; ++cp)
+            for (int k = 0; k < nv; ++k) AT(x, nc, nv, cp, c, k) = 0.0;
+        return;
+    }
+    double V = Lv->dx[i] * Lv->dy[j];
+    for (int k = 0; k < nv; ++k) D[k] = Dii(s, Lv, i, j, inv_tau[c], k);
+    for (int cp = 0; cp < 2; ++cp)
+        for (int k = 0; k < nv; ++k) {
+            double y = 0.0;
+            if (pass == 0) {
+                if (i > 0 && Lv->fbx[j * (nx + 1) + i] < 0)
+                    y += Dij(s, 0, -1, Lv->dy[j], V, k) * AT(x, nc, nv, cp, c - 1, k);
+                if (j > 0 && Lv->fby[j * nx + i] < 0)
+                    y += Dij(s, 1, -1, Lv->dx[i], V, k) * AT(x, nc, nv, cp, c - nx, k);
+                base[cp * nv + k] = AT(r, nc, nv, cp, c, k) - y;
+            } else {
+                if (i < nx - 1 && Lv->fbx[j * (nx + 1) + i + 1] < 0)
+                    y += Dij(s, 0, +1, Lv->dy[j], V, k) * AT(x, nc, nv, cp, c + 1, k);
+                if (j < ny - 1 && Lv->fby[(j + 1) * nx + i] < 0)
+                    y += Dij(s, 1, +1, Lv->dx[i], V, k) * AT(x, nc, nv, cp, c + nx, k);
+                base[cp * nv + k] = D[k] * AT(x, nc, nv, cp, c, k) - y;
+            }
+        }
+    bface_t bf[4];
+    int nb = cell_bfaces(Lv, i, j, pass, bf);
+    if (nb == 0) {
+        for (int cp = 0; cp < 2; ++cp)
+            for (int k = 0; k < nv; ++k) AT(x, nc, nv, cp, c, k) = base[cp * nv + k] / D[k];
+    } else {
+        cell_solve(s, c, nb, bf, D, base, xc);
+        for (int cp = 0; cp < 2; ++cp)
+            for (int k = 0; k < nv; ++k) AT(x, nc, nv, cp, c, k) = xc[cp * nv + k];
+    }
+}
+
 /* One symmetric Gauss-Seidel pass (LU-SGS) on Eq. microFinalDefect:
  * forward  (D + L) x* = r, backward (D + U) x = D x*, lower = west/south
- * neighbours and ghosts, upper = east/north.  order 1 = anti-diagonal
- * wavefront order (same arithmetic per cell). */
+ * neighbours and ghosts, upper = east/north.  order 0 = lexicographic cell
+ * order, order 1 = anti-diagonal wavefront order (the cells of a diagonal
+ * depend only on the previous diagonal, so the arithmetic per cell is the
+ * same; the OpenMP build sweeps in this order, the cells of a diagonal
+ * spread over threads). */
 static void sgs_micro(oracle_solver *s, const olev_t *Lv, const double *inv_tau, const double *r, double *x, int order)
 {
     int nx = Lv->nx, ny = Lv->ny, nv = s->nv, nd = nx + ny - 1;
-    size_t nc = Lv->nc;
-    double *D = dalloc(nv), *base = dalloc(2 * (size_t)nv), *xc = dalloc(2 * (size_t)nv);
+    if (s->nthr > 1) order = 1;
     for (int pass = 0; pass < 2; ++pass) {
-        int ncell = nx * ny;
-        for (int t = 0; t < ncell; ++t) {
-            int i = 0, j = 0;
-            if (order == 0) {
+        if (order == 0) {
+            int ncell = nx * ny;
+            for (int t = 0; t < ncell; ++t) {
                 int tt = pass == 0 ? t : ncell - 1 - t;
-                i = tt % nx; j = tt / nx;
-            } else {
-                int cnt = 0, found = 0;
-                for (int d0 = 0; d0 < nd && !found; ++d0) {
-                    int d = pass == 0 ? d0 : nd - 1 - d0;
-                    int ilo = d - (ny - 1) > 0 ? d - (ny - 1) : 0, ihi = d < nx - 1 ? d : nx - 1;
-                    if (t < cnt + (ihi - ilo + 1)) {
-                        int off = t - cnt;
-                        i = pass == 0 ? ilo + off : ihi - off;
-                        j = d - i;
-                        found = 1;
-                    }
-                    cnt += ihi - ilo + 1;
-                }
+                sweep_cell(s, Lv, inv_tau, r, x, pass, tt % nx, tt / nx, s->sD, s->sbase, s->sxc);
             }
-            int c = j * nx + i;
-            if (Lv->solid[c]) {
-                for (int cp = 0; cp < 2; ++cp)
-                    for (int k = 0; k < nv; ++k) AT(x, nc, nv, cp, c, k) = 0.0;
-                continue;
-            }
-            double V = Lv->dx[i] * Lv->dy[j];
-            for (int k = 0; k < nv; ++k) D[k] = Dii(s, Lv, i, j, inv_tau[c], k);
-            for (int cp = 0; cp < 2; ++cp)
-                for (int k = 0; k < nv; ++k) {
-                    double y = 0.0;
-                    if (pass == 0) {
-                        if (i > 0 && Lv->fbx[j * (nx + 1) + i] < 0)
-                            y += Dij(s, 0, -1, Lv->dy[j], V, k) * AT(x, nc, nv, cp, c - 1, k);
-                        if (j > 0 && Lv->fby[j * nx + i] < 0)
-                            y += Dij(s, 1, -1, Lv->dx[i], V, k) * AT(x, nc, nv, cp, c - nx, k);
-                        base[cp * nv + k] = AT(r, nc, nv, cp, c, k) - y;
-                    } else {
-                        if (i < nx - 1 && Lv->fbx[j * (nx + 1) + i + 1] < 0)
-                            y += Dij(s, 0, +1, Lv->dy[j], V, k) * AT(x, nc, nv, cp, c + 1, k);
-                        if (j < ny - 1 && Lv->fby[(j + 1) * nx + i] < 0)
-                            y += Dij(s, 1, +1, Lv->dx[i], V, k) * AT(x, nc, nv, cp, c + nx, k);
-                        base[cp * nv + k] = D[k] * AT(x, nc, nv, cp, c, k) - y;
-                    }
-                }
-            bface_t bf[4];
-            int nb = cell_bfaces(Lv, i, j, pass, bf);
-            if (nb == 0) {
-                for (int cp = 0; cp < 2; ++cp)
-                    for (int k = 0; k < nv; ++k) AT(x, nc, nv, cp, c, k) = base[cp * nv + k] / D[k];
-            } else {
-                cell_solve(s, c, nb, bf, D, base, xc);
-                for (int cp = 0; cp < 2; ++cp)
-                    for (int k = 0; k < nv; ++k) AT(x, nc, nv, cp, c, k) = xc[cp * nv + k];
+            continue;
+        }
+        for (int d0 = 0; d0 < nd; ++d0) {
+            int d = pass == 0 ? d0 : nd - 1 - d0;
+            int ilo = d - (ny - 1) > 0 ? d - (ny - 1) : 0, ihi = d < nx - 1 ? d : nx - 1;
+#pragma omp parallel for num_threads(s->nthr) schedule(static) if (ihi - ilo >= 2)
+            for (int i = ilo; i <= ihi; ++i) {
+                size_t t = (size_t)ORC_TID;
+                sweep_cell(s, Lv, inv_tau, r, x, pass, i, d - i, s->sD + t * nv, s->sbase + t * 2 * nv,
+                           s->sxc + t * 2 * nv);
             }
         }
     }
-    free(D); free(base); free(xc);
 }
 
 /* y = A x, the full evolution operator of Eq. microFinalDefect with every
@@ -1164,6 +1228,7 @@ static void apply_micro(const oracle_solver *s, const olev_t *Lv, const double *
 {
     int nx = Lv->nx, ny = Lv->ny, nv = s->nv;
     size_t nc = Lv->nc;
+#pragma omp parallel for num_threads(s->nthr) schedule(static)
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
             int c = j * nx + i;
@@ -1226,9 +1291,11 @@ static void cs(oracle_solver *s, int l, int type)
     int npre = coarsest ? (s->L == 1 ? 1 : s->nuc) : s->nu1;
     for (int m = 0; m < npre; ++m) {
         sgs_micro(s, Lv, Lv->inv_tau, Lv->r, Lv->dl, 0);
+#pragma omp parallel for schedule(static)
         for (size_t q = 0; q < n; ++q) Lv->df[q] += Lv->dl[q];
         if (coarsest && m == npre - 1) return;
         apply_micro(s, Lv, Lv->inv_tau, Lv->dl, Lv->Ad); /* Eq. renewResidualMicro */
+#pragma omp parallel for schedule(static)
         for (size_t q = 0; q < n; ++q) Lv->r[q] -= Lv->Ad[q];
     }
     olev_t *Cv = &s->lev[l + 1];
@@ -1238,7 +1305,26 @@ static void cs(oracle_solver *s, int l, int type)
     double *r0 = type != 0 ? dalloc(nC) : NULL;
     if (r0) memcpy(r0, Cv->r, nC * sizeof(double));
     cs(s, l + 1, type);
-    if (type != 0) {
+    if (type == 3) {
+        /* adaptive: another coarse visit, for the coarse residual the corrections so far
+         * leave, while a visit leaves more than ADAPT_RATIO of the residual it started from */
+        double *acc = dalloc(nC);
+        double before = sumsq(r0, nC);
+        memcpy(acc, Cv->df, nC * sizeof(double));
+        for (int visit = 1; visit < ADAPT_MAX_VISITS; ++visit) {
+            apply_micro(s, Cv, Cv->inv_tau, acc, Cv->Ad);
+            for (size_t q = 0; q < nC; ++q) Cv->r[q] = r0[q] - Cv->Ad[q];
+            double after = sumsq(Cv->r, nC);
+            s->adapt_log[s->adapt_n++ % ADAPT_LOG] = after > s->adapt_ratio * s->adapt_ratio * before;
+            if (!(after > s->adapt_ratio * s->adapt_ratio * before)) break;
+            before = after;
+            cs(s, l + 1, 3);
+            for (size_t q = 0; q < nC; ++q) acc[q] += Cv->df[q];
+        }
+        memcpy(Cv->df, acc, nC * sizeof(double));
+        free(acc);
+        free(r0);
+    } else if (type != 0) {
         double *acc = dalloc(nC);
         memcpy(acc, Cv->df, nC * sizeof(double));
         apply_micro(s, Cv, Cv->inv_tau, acc, Cv->Ad);
@@ -1250,11 +1336,14 @@ static void cs(oracle_solver *s, int l, int type)
     }
     for (int cp = 0; cp < 2; ++cp)
         prolong_lv(Lv, Cv, s->nv, Cv->df + (size_t)cp * Cv->nc * s->nv, Lv->dl + (size_t)cp * Lv->nc * s->nv);
+#pragma omp parallel for schedule(static)
     for (size_t q = 0; q < n; ++q) Lv->df[q] += Lv->dl[q];
     for (int m = 0; m < s->nu2; ++m) {
         apply_micro(s, Lv, Lv->inv_tau, Lv->dl, Lv->Ad);
+#pragma omp parallel for schedule(static)
         for (size_t q = 0; q < n; ++q) Lv->r[q] -= Lv->Ad[q];
         sgs_micro(s, Lv, Lv->inv_tau, Lv->r, Lv->dl, 0);
+#pragma omp parallel for schedule(static)
         for (size_t q = 0; q < n; ++q) Lv->df[q] += Lv->dl[q];
     }
 }
@@ -1267,8 +1356,9 @@ static void cs(oracle_solver *s, int l, int type)
 static void moments(oracle_solver *s)
 {
     int nv = s->nv;
-    size_t nc = s->lev[0].nc;
-    for (size_t c = 0; c < nc; ++c) {
+    long nc = (long)s->lev[0].nc;
+#pragma omp parallel for num_threads(s->nthr) schedule(static)
+    for (long c = 0; c < nc; ++c) {
         double W[4] = {0, 0, 0, 0};
         for (int k = 0; k < nv; ++k) {
             double g = FIX(s, 0, c, k), h = FIX(s, 1, c, k);
@@ -1364,6 +1454,7 @@ static void one_iteration(oracle_solver *s, double res[4])
     cs(s, 0, s->cycle);
     /* Steps 6-7: f += df, except in a cell where f + df has non-positive
      * density or internal energy, which keeps f (reading: the paper is silent) */
+#pragma omp parallel for num_threads(s->nthr) schedule(static)
     for (size_t c = 0; c < nc; ++c) {
         double W[4] = {0, 0, 0, 0};
         for (int k = 0; k < nv; ++k) {
@@ -1404,6 +1495,7 @@ oracle_solver *oracle_create(int nx, int ny, const double *xn, const double *yn,
     s->nu = nu; s->nvv = nv; s->nv = nu * nv;
     s->kn = kn; s->omega = omega; s->pr = pr; s->mu_ref = oracle_mu_ref(kn, omega);
     s->nu1 = nu1; s->nu2 = nu2; s->nuc = nuc; s->cfl = cfl; s->dtn_growth = dtn_growth;
+    s->adapt_ratio = ADAPT_RATIO;
     double *ux = dalloc(nu), *wu = dalloc(nu), *vy = dalloc(nv), *wv = dalloc(nv);
     if (oracle_vgrid(nu, umin, umax, rule, ux, wu) || oracle_vgrid(nv, vmin, vmax, rule, vy, wv)) {
         free(ux); free(wu); free(vy); free(wv); free(s);
@@ -1490,7 +1582,12 @@ oracle_solver *oracle_create(int nx, int ny, const double *xn, const double *yn,
     s->f = dalloc(2 * nc * NV); s->W = dalloc(4 * nc); s->q = dalloc(2 * nc); s->R = dalloc(4 * nc);
     s->phx = dalloc(2 * (size_t)L0->nfx * NV); s->phy = dalloc(2 * (size_t)L0->nfy * NV);
     s->Fx = dalloc(4 * (size_t)L0->nfx); s->Fy = dalloc(4 * (size_t)L0->nfy);
-    s->tmp0 = dalloc(2 * (size_t)NV); s->tmp1 = dalloc(2 * (size_t)NV); s->tmp2 = dalloc(2 * (size_t)NV);
+    s->nthr = ORC_MAXTHR;
+    {
+        size_t per = 2 * (size_t)NV * s->nthr;
+        s->tmp0 = dalloc(per); s->tmp1 = dalloc(per); s->tmp2 = dalloc(per);
+        s->sD = dalloc((size_t)NV * s->nthr); s->sbase = dalloc(per); s->sxc = dalloc(per);
+    }
     if (!s->f || !s->phx || !s->phy) { fail("out of memory"); oracle_destroy(s); return NULL; }
     /* minimum physical time step over the interior faces (for dt_n) */
     s->dtp_min = 1e300;
@@ -1512,6 +1609,7 @@ void oracle_destroy(oracle_solver *s)
     free(s->u); free(s->v); free(s->w); free(s->mxk); free(s->myk); free(s->bc); free(s->Cw);
     free(s->f); free(s->W); free(s->q); free(s->R); free(s->phx); free(s->phy); free(s->Fx); free(s->Fy);
     free(s->tmp0); free(s->tmp1); free(s->tmp2);
+    free(s->sD); free(s->sbase); free(s->sxc);
     free(s);
 }
 
@@ -2392,9 +2490,26 @@ int oracle_stage_cs(oracle_solver *s, const double *inv_tau, const double *r, do
 
 /* Multigrid cycle type of both the FAS and the CS cycle (Sec. 3.4 names V, W,
  * F and adaptive cycles): 0 V (default), 1 W, 2 F. */
+/* decisions of the adaptive cycle so far (1 = a second coarse visit), the last
+ * min(n, cap, ADAPT_LOG) of them in order; returns their total count */
+int oracle_adapt_log(const oracle_solver *s, unsigned char *out, int cap)
+{
+    int n = s->adapt_n, m = n < cap ? n : cap;
+    if (m > ADAPT_LOG) m = ADAPT_LOG;
+    for (int q = 0; q < m; ++q) out[q] = s->adapt_log[(n - m + q) % ADAPT_LOG];
+    return n;
+}
+
+int oracle_set_adapt_ratio(oracle_solver *s, double ratio)
+{
+    if (!(ratio >= 0.0)) return fail("adaptive ratio %g must be >= 0", ratio);
+    s->adapt_ratio = ratio;
+    return 0;
+}
+
 int oracle_set_cycle(oracle_solver *s, int type)
 {
-    if (type < 0 || type > 2) return fail("cycle type %d: 0 V, 1 W, 2 F", type);
+    if (type < 0 || type > 3) return fail("cycle type %d: 0 V, 1 W, 2 F, 3 adaptive", type);
     s->cycle = type;
     return 0;
 }

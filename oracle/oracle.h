@@ -56,6 +56,8 @@ int oracle_step(oracle_solver *s, int n, double res[4]);
 int oracle_init_from_coarse(oracle_solver *s, const oracle_solver *coarse);
 /* Multigrid cycle type of the FAS and CS cycles: 0 V (default), 1 W, 2 F. */
 int oracle_set_cycle(oracle_solver *s, int type);
+int oracle_adapt_log(const oracle_solver *s, unsigned char *out, int cap);
+int oracle_set_adapt_ratio(oracle_solver *s, double ratio);
 int oracle_get_macro(const oracle_solver *s, double *rho, double *u, double *v,
                      double *t, double *qx, double *qy);
 int oracle_get_f(const oracle_solver *s, double *f);

@@ -370,3 +370,56 @@ def test_w_and_f_cycles_reach_the_v_cycle_steady_state():
     for cyc in ("W", "F"):
         for k in ("rho", "u", "v", "t"):
             assert np.allclose(out[cyc][k], out["V"][k], rtol=1e-9, atol=1e-10), (cyc, k)
+
+
+def _farfield_cavity(levels=3):
+    case = wl.cavity(n=8, nvel=24, kn=0.3, lid=0.2, vmax=6.0, levels=levels)
+    case["bcs"][2] = wl.bc(wl.FARFIELD, rho=1.0, u=0.2, v=0.0, t=1.0)
+    return case
+
+
+def test_adaptive_cycle_limits_are_the_v_and_w_cycles():
+    """The adaptive cycle (Sec. 3.4 names it; reading: a second coarse visit
+    when the first left more than a ratio of the coarse residual) is built
+    from the same visits as V and W: with ratio 0 every decision is a second
+    visit and its iterates are the W cycle's bit for bit, with a ratio no
+    visit reaches they are the V cycle's."""
+    f = {}
+    for cyc, ratio in (("V", None), ("W", None), ("A0", 0.0), ("Ainf", 1e300)):
+        o = oracle.Oracle(_farfield_cavity())
+        o.set_cycle(cyc[0])
+        if ratio is not None:
+            o.set_adapt_ratio(ratio)
+        o.init_uniform(1.0, 0.0, 0.0, 1.0)
+        o.step(3)
+        f[cyc] = o.get_f()
+        if cyc == "A0":
+            log = o.adapt_log()
+            assert log.size > 0 and np.all(log == 1)
+        if cyc == "Ainf":
+            log = o.adapt_log()
+            assert log.size > 0 and np.all(log == 0)
+    assert np.array_equal(f["A0"], f["W"])
+    assert np.array_equal(f["Ainf"], f["V"])
+    assert not np.array_equal(f["V"], f["W"])
+
+
+def test_adaptive_cycle_reaches_the_v_cycle_steady_state():
+    """With the default ratio (0.2) the adaptive cycle takes both decisions along the
+    way and converges to the V cycle's discrete steady state."""
+    out = {}
+    for cyc in ("V", "A"):
+        o = oracle.Oracle(_farfield_cavity())
+        o.set_cycle(cyc)
+        o.init_uniform(1.0, 0.0, 0.0, 1.0)
+        for _ in range(300):
+            res = o.step(1)
+            if np.all(res < 1e-12):
+                break
+        assert np.all(res < 1e-11), (cyc, res)
+        out[cyc] = o.macro()
+        if cyc == "A":
+            log = o.adapt_log()
+            assert 0 < log.sum() < log.size, log
+    for k in ("rho", "u", "v", "t"):
+        assert np.allclose(out["A"][k], out["V"][k], rtol=1e-9, atol=1e-10), k
