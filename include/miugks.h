@@ -152,13 +152,35 @@ miugks_status miugks_set_bc(miugks_solver *s, int bc, const miugks_bc *value);
 /* Multigrid cycle type of both the prediction (FAS, Eq. FASCYC) and the
  * evolution (CS, Eq. CSCYC) cycles; Sec. 3.4 names V, W and F cycles and
  * evaluates only the V cycle.  type 0 V (default), 1 W (two coarse visits of
- * type W), 2 F (an F visit then a V visit).  A second FAS visit starts from the
+ * type W), 2 F (an F visit then a V visit), 3 adaptive (below).  A second FAS visit starts from the
  * coarse state the first left, with the same forcing function and frozen
  * Gamma; a second CS visit solves for the coarse residual the first correction
  * leaves.  W and F need two more per-velocity arrays per coarse level, taken
  * from the solver's allocator on the first selection.  The adjoint's
  * preconditioner stays the transposed V cycle.  MIUGKS_EINVAL for another type. */
 miugks_status miugks_set_cycle(miugks_solver *s, int type);
+/* Adaptive cycle (type 3 of miugks_set_cycle; Sec. 3.4 names adaptive cycles
+ * without a rule): each level visits the next coarser level once and visits
+ * it a second time when the first visit left more than `ratio` (default 0.2)
+ * of the coarse residual it started from, in the L2 norm over all values: for
+ * FAS the restricted residual against P + R_E(W) of the coarse state left, for
+ * CS r_H against r_H - A_H df_H.  ratio 0 gives the W cycle, a ratio no visit
+ * reaches the V cycle.  Each decision reads a norm back to the host, so
+ * iterations of this type are launched eagerly, never from a captured graph.
+ * set_adaptive_ratio: MIUGKS_EINVAL for a negative ratio.
+ * adaptive_decisions: the last min(n, cap, 4096) decisions, oldest first
+ * (1 = a second visit), into out (may be NULL); returns n, the number taken. */
+miugks_status miugks_set_adaptive_ratio(miugks_solver *s, double ratio);
+/* Launch layout of the evolution smoother's sweeps (Eq. microFinalDefect); the
+ * result is the same bit for bit.  In a sweep pass a velocity whose u (or v)
+ * points away from the upwind neighbour in x (or y) has a zero coefficient
+ * there: velocities coupled in both directions need the anti-diagonal
+ * wavefront, the others are independent along rows, along columns or per
+ * cell.  mode 1 sweeps those in a separate line-parallel kernel, 2 sweeps every
+ * velocity in the wavefront kernel, 0 (default) splits a level from 20 Mi
+ * cell-velocity pairs on.  MIUGKS_EINVAL for another mode. */
+miugks_status miugks_set_sweep_split(miugks_solver *s, int mode);
+int miugks_adaptive_decisions(const miugks_solver *s, unsigned char *out, int cap);
 /* Full-multigrid start-up (Sec. 3.5): the state of `coarse`, a solver of the
  * same problem on the next coarser mesh (every second grid line of s's mesh,
  * same velocity grid and precision), becomes s's initial state by the bilinear
@@ -262,6 +284,12 @@ miugks_status miugks_kernel_times(miugks_solver *s, double *flux_ms, double *swe
  * pair of CUDA events: total milliseconds and launch count since the last
  * call (-1 and 0 when timing is off); the counters are reset. */
 miugks_status miugks_macro_sweep_times(miugks_solver *s, double *ms, int *launches);
+/* With timing on, every launch of the evolution smoother's sweep kernels on the
+ * finest level (Eq. microFinalDefect; see miugks_set_sweep_split) is bracketed
+ * by CUDA events.  out[0..2]: total milliseconds, launches and cell-velocity
+ * pairs swept by the wavefront kernel; out[3..5]: the same for the line-class
+ * kernel; since the last call (then reset).  -1 ms when timing is off. */
+miugks_status miugks_sweep_kernel_times(miugks_solver *s, double out[6]);
 
 /* Residual norm of caller-owned device arrays without allocating anything.
  * The paper has no counterpart.  It serves callers that cannot allocate device

@@ -26,6 +26,15 @@ struct VelDev {
     const double *ua, *vb;       // per-axis nodes
     const float *uf, *vf, *wf;   // u, v, w rounded to FP32 (for the mixed-precision kernels)
     double umax, vmax;           // largest |u|, |v|
+    // Coupling classes of the evolution sweep, per pass (0 forward, 1 backward),
+    // from the signs of u and v: the blocks of four consecutive velocities that
+    // hold a velocity coupled to both its x and its y upwind neighbour (swept as
+    // a wavefront), and every other velocity, listed as those coupled along rows
+    // only, along columns only, and to no neighbour (in that order in lk)
+    const int* wblk[2];
+    int nwblk[2];
+    const int* lk[2];
+    int nrow[2], ncol[2], nelem[2];
 };
 
 // one grid level (all device pointers)

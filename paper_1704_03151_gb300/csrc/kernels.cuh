@@ -1,6 +1,7 @@
 // kernels.cuh -- argument structs and launchers of the MIUGKS kernels.
 #pragma once
 #include "common.cuh"
+#include <vector>
 
 namespace miugks {
 
@@ -83,7 +84,17 @@ struct MicroArgs {
 // Host schedule of the body lines of one pass: after wave step dd - 1, the lines
 // q0 .. q0 + nq - 1 (fold entries e0 .. e0 + ne - 1) are walked and folded.
 struct SweepBreak { int dd, q0, nq, e0, ne; };
-struct SweepPlanHost { const SweepBreak* brk[2]; int nbrk[2]; };
+// Timing mode: event pairs around the launches of the wavefront and line-class
+// sweep kernels, with the cell-velocity pairs each launch sweeps.
+struct SweepTimer {
+    std::vector<cudaEvent_t> ev;  // two per launch
+    std::vector<int> kind;        // 0 wavefront, 1 line class
+    std::vector<double> units;
+    int used = 0;
+};
+// split: 0 by the level's size, 1 always split the velocities by coupling class, 2 never;
+// timer: null unless the launches are to be timed
+struct SweepPlanHost { const SweepBreak* brk[2]; int nbrk[2]; int split; SweepTimer* timer; };
 // Step 3-4: r = (g~ - f)/tau~ - div(ph) on level 0; also inv_tau (with dtn_inv) and invD
 template <typename F>
 cudaError_t launch_micro_residual(const MicroArgs& m, GasDev gas, const double* Wt, const double* q,
@@ -97,6 +108,12 @@ cudaError_t launch_coarse_coeffs(const MicroArgs& m, GasDev gas, const double* W
 // incoming velocities of w u_n C_k of wall BC b; xcorner: scratch of
 // micro_scratch_elems(nv, nl_max, body lines) values (the largest over the levels)
 size_t micro_scratch_elems(int nv, int nl, int nlines);
+// *out = sum of a[q]^2 over n values; part: scratch of 128 doubles
+template <typename T>
+cudaError_t launch_sumsq(const T* a, size_t n, double* part, double* out, cudaStream_t st);
+// coupling classes of the evolution sweep for one pass (VelDev::wblk, lk, nrow, ncol, nelem)
+void sweep_classes(const double* u, const double* v, int nv, int pass, std::vector<int>& wblk, std::vector<int>& lk,
+                   int& nrow, int& ncol, int& nelem);
 template <typename F>
 cudaError_t launch_micro_sgs(const MicroArgs& m, const SweepPlanHost& plan, const double* Zw, const F* invD,
                              const F* r, F* x, F* xcorner, cudaStream_t st);

@@ -36,6 +36,7 @@ constexpr int kChainCluster = 8;
 constexpr int kChainThreads = 128;    // 4 warps: one per SM sub-partition
 constexpr int kChainKptMax = 16;      // local velocities per thread in the chain kernel (at most)
 constexpr int kInteriorKc = 4;        // velocities per CTA in the wavefront kernel
+constexpr size_t kSweepSplitMinCv = 20u << 20;   // cell-velocity pairs of a level from which the sweep is split
 
 // asynchronous 4- or 8-byte global -> shared copies (LDGSTS), completed per commit group
 template <typename F>
@@ -885,8 +886,10 @@ __global__ void k_line_fold(MicroArgs M, const F* __restrict__ invD, const F* __
 template <typename F, int R, bool VEC, bool BODIES>
 __global__ void __launch_bounds__(512) k_sgs_wave(MicroArgs M, const F* __restrict__ invD, const F* __restrict__ r,
                                                   F* __restrict__ x, const F* __restrict__ fold, int pass, int dd0,
-                                                  int dd1)
+                                                  int dd1, int listed)
 {
+    // this CTA's block of velocities: every block, or the listed wavefront-class blocks
+    const int blk = listed ? M.V.wblk[pass][blockIdx.x] : blockIdx.x;
     extern __shared__ __align__(16) double sraw[];
     constexpr int K = kInteriorKc, W = 2 * K;
     const LevelDev& L = M.L;
@@ -894,7 +897,7 @@ __global__ void __launch_bounds__(512) k_sgs_wave(MicroArgs M, const F* __restri
     const int nx = L.nx, ny = L.ny, nv = Vg.nv;
     const size_t nc = L.nc;
     const int B = blockDim.x, tid = threadIdx.x;
-    const int k0 = blockIdx.x * K, nk = min(K, nv - k0);
+    const int k0 = blk * K, nk = min(K, nv - k0);
     const int nd = nx + ny - 1, nls = M.P.nl_max;
     const int* __restrict__ code = M.P.code[pass];
     F* sx = reinterpret_cast<F*>(sraw);                 // [2][nx][W] values of the previous diagonal
@@ -930,7 +933,7 @@ __global__ void __launch_bounds__(512) k_sgs_wave(MicroArgs M, const F* __restri
                     cp_async_k4<F, VEC>(ra + (size_t)B * K, src + nc * nv + e, nk);
                     cp_async_k4<F, VEC>(ra + (size_t)2 * B * K, invD + e, nk);
                 } else if (cd >= 0) {                   // a boundary-line cell: its folded inputs
-                    const F* fo = fold + ((size_t)(blockIdx.x * nls + (cd >> 2)) * 3) * K;
+                    const F* fo = fold + ((size_t)(blk * nls + (cd >> 2)) * 3) * K;
                     cp_async_k4<F, true>(ra, fo, K);
                     cp_async_k4<F, true>(ra + (size_t)B * K, fo + K, K);
                     cp_async_k4<F, true>(ra + (size_t)2 * B * K, fo + 2 * K, K);
@@ -1045,6 +1048,193 @@ __global__ void __launch_bounds__(512) k_sgs_wave(MicroArgs M, const F* __restri
     cp_async_wait_n<0>();
 }
 
+// Wavefront steps [dd0, dd1) of one sweep pass for the velocities that are
+// coupled to one upwind neighbour only, or to none (the sign of u or v puts the
+// other neighbour downwind, and its coefficient is an exact zero): such a
+// velocity is independent along every row (coupled along x only) or every
+// column (along y only), or every cell (neither), so one thread per (line,
+// velocity) walks the cells of its line that lie on the segment's diagonals,
+// with no barrier.  Consecutive threads take consecutive velocities of the
+// same line, so every access is coalesced, and each thread loads the inputs of
+// four cells before it updates them in order.  The update of a cell is the
+// wavefront kernel's with the zero coupling left out; boundary-line cells take
+// their folded inputs (incoming velocities) or keep the value of their line
+// walk (outgoing velocities and the corner), as in the wavefront kernel.  The
+// backward pass leaves the uncoupled velocities as they are (x = x).
+// Block b: rows (class 0) first, nbr blocks of 128 velocities per row, then
+// columns (class 1), nbc per column, then cells of no coupling by rows, nbe per
+// row (0 in the backward pass).
+template <typename F, bool BODIES>
+__global__ void __launch_bounds__(128) k_sgs_lines(MicroArgs M, const F* __restrict__ invD, const F* __restrict__ r,
+                                                   F* __restrict__ x, const F* __restrict__ fold, int pass, int dd0,
+                                                   int dd1, int nbr, int nbc, int nbe)
+{
+    constexpr int K = kInteriorKc, U = 4;
+    const LevelDev& L = M.L;
+    const VelDev& Vg = M.V;
+    const int nx = L.nx, ny = L.ny, nv = Vg.nv, nd = nx + ny - 1, nls = M.P.nl_max;
+    const size_t nc = L.nc;
+    int b = blockIdx.x, cls, line, q;
+    if (b < nbr * ny) {
+        cls = 0; line = b / nbr; q = (b % nbr) * 128 + threadIdx.x;
+        if (q >= Vg.nrow[pass]) return;
+    } else if ((b -= nbr * ny) < nbc * nx) {
+        cls = 1; line = b / nbc; q = (b % nbc) * 128 + threadIdx.x;
+        if (q >= Vg.ncol[pass]) return;
+        q += Vg.nrow[pass];
+    } else {
+        b -= nbc * nx;
+        cls = 2; line = b / nbe; q = (b % nbe) * 128 + threadIdx.x;
+        if (q >= Vg.nelem[pass]) return;
+        q += Vg.nrow[pass] + Vg.ncol[pass];
+    }
+    const int k = Vg.lk[pass][q];
+    const F u = (F)Vg.u[k], v = (F)Vg.v[k];
+    const F cu = pass == 0 ? (u > F(0) ? -u : F(0)) : (u < F(0) ? u : F(0));
+    const F cv = pass == 0 ? (v > F(0) ? -v : F(0)) : (v < F(0) ? v : F(0));
+    const F cc = cls == 0 ? cu : cls == 1 ? cv : F(0);   // coefficient of the neighbour along the line
+    // the line's cells on diagonals [dlo, dhi): position p along the line (i for rows, j for columns)
+    const int dlo = pass == 0 ? dd0 : nd - dd1, dhi = pass == 0 ? dd1 : nd - dd0;
+    const int len = cls == 1 ? ny : nx;
+    const int p0 = max(0, dlo - line), p1 = min(len, dhi - line);
+    if (p1 <= p0) return;
+    const int n = p1 - p0, step = pass == 0 ? 1 : -1, pfirst = pass == 0 ? p0 : p1 - 1;
+    const int ib = pass == 0 ? 0 : nx - 1, jb = pass == 0 ? 0 : ny - 1;
+    const int* __restrict__ code = M.P.code[pass];
+    const F* src = pass == 0 ? r : x;
+    const int kb = k / K, kk = k - kb * K;
+    auto cell_of = [&](int p) { return cls == 1 ? p * nx + line : line * nx + p; };
+    // value of the upwind neighbour of the first cell (from an earlier segment), 0 at the line's start
+    F xp[2] = {F(0), F(0)};
+    const int pnb = pfirst - step;
+    if (cls != 2 && pnb >= 0 && pnb < len) {
+        const size_t cn = (size_t)cell_of(pnb) * nv + k;
+        xp[0] = x[cn];
+        xp[1] = x[nc * nv + cn];
+    }
+    for (int s0 = 0; s0 < n; s0 += U) {
+        // inputs of up to U cells: kind 0 ordinary, 1 folded (incoming at a line face),
+        // 2 final (outgoing at a line face, or the corner), 3 in a body
+        F a[U][2], iv[U], rd[U];
+        int kind[U];
+        #pragma unroll
+        for (int t = 0; t < U; ++t) {
+            kind[t] = 2;
+            a[t][0] = a[t][1] = iv[t] = rd[t] = F(0);
+            if (s0 + t >= n) continue;
+            const int p = pfirst + (s0 + t) * step;
+            const int c = cell_of(p), i = cls == 1 ? line : p, j = cls == 1 ? p : line;
+            bool hasx, hasy;
+            int e = 0;
+            if constexpr (BODIES) {
+                const int cd = code[c];
+                if (cd == -2) { kind[t] = 3; continue; }
+                hasx = cd >= 0 && (cd & 2);
+                hasy = cd >= 0 && (cd & 1);
+                e = cd >> 2;
+            } else {
+                hasx = i == ib;
+                hasy = j == jb;
+                e = hasx ? (pass == 0 ? j : ny - 1 - j) : ny + (pass == 0 ? i : nx - 1 - i);
+            }
+            // the line face across which this class's velocities enter, and the one they leave by
+            const bool fin = cls == 0 ? hasy : cls == 1 ? hasx : (hasx || hasy);
+            const bool fld = !fin && (cls == 0 ? hasx : cls == 1 ? hasy : false);
+            const size_t id = (size_t)c * nv + k;
+            if (fin) {
+                kind[t] = 2;
+                if (cls != 2) { a[t][0] = x[id]; a[t][1] = x[nc * nv + id]; }
+            } else if (fld) {
+                kind[t] = 1;
+                const F* fo = fold + ((size_t)(kb * nls + e) * 3) * K + kk;
+                a[t][0] = fo[0]; a[t][1] = fo[K]; iv[t] = fo[2 * K];
+            } else {
+                kind[t] = 0;
+                a[t][0] = src[id]; a[t][1] = src[nc * nv + id]; iv[t] = invD[id];
+                rd[t] = cls == 0 ? (F)L.rdx[i] : cls == 1 ? (F)L.rdy[j] : F(0);
+            }
+        }
+        #pragma unroll
+        for (int t = 0; t < U; ++t) {
+            if (s0 + t >= n) continue;
+            const int p = pfirst + (s0 + t) * step;
+            const size_t id = (size_t)cell_of(p) * nv + k;
+            F res[2];
+            #pragma unroll
+            for (int cp = 0; cp < 2; ++cp) {
+                if (kind[t] == 3) res[cp] = F(0);
+                else if (kind[t] == 2) res[cp] = a[t][cp];
+                else if (kind[t] == 1) res[cp] = pass == 0 ? a[t][cp] * iv[t] : a[t][cp];
+                else {
+                    const F y = cls == 2 ? F(0) : cc * rd[t] * xp[cp];
+                    res[cp] = pass == 0 ? (a[t][cp] - y) * iv[t] : a[t][cp] - y * iv[t];
+                }
+                xp[cp] = res[cp];
+            }
+            if (kind[t] != 2) {
+                x[id] = res[0];
+                x[nc * nv + id] = res[1];
+            }
+        }
+    }
+}
+
+// Sum of squares of n values (deterministic: fixed grid, fixed per-thread order,
+// fixed reduction tree), for the decisions of the adaptive multigrid cycle.
+constexpr int kSumsqBlocks = 128;
+template <typename T>
+__global__ void k_sumsq_part(const T* __restrict__ a, size_t n, double* __restrict__ part)
+{
+    __shared__ double red[32];
+    double s[1] = {0.0};
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+        const double v = (double)a[q];
+        s[0] += v * v;
+    }
+    block_sum<1>(s, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = s[0];
+}
+__global__ void k_sumsq_final(const double* __restrict__ part, int nb, double* __restrict__ out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double t = 0.0;
+        for (int b = 0; b < nb; ++b) t += part[b];
+        *out = t;
+    }
+}
+template <typename T>
+cudaError_t launch_sumsq(const T* a, size_t n, double* part, double* out, cudaStream_t st)
+{
+    k_sumsq_part<T><<<kSumsqBlocks, 256, 0, st>>>(a, n, part);
+    k_sumsq_final<<<1, 32, 0, st>>>(part, kSumsqBlocks, out);
+    return cudaGetLastError();
+}
+template cudaError_t launch_sumsq<float>(const float*, size_t, double*, double*, cudaStream_t);
+template cudaError_t launch_sumsq<double>(const double*, size_t, double*, double*, cudaStream_t);
+
+// Coupling classes of one pass (0 forward, 1 backward) for the velocity nodes
+// (u_k, v_k): the wavefront blocks and the lists of the other velocities.
+void sweep_classes(const double* u, const double* v, int nv, int pass, std::vector<int>& wblk, std::vector<int>& lk,
+                   int& nrow, int& ncol, int& nelem)
+{
+    const int K = kInteriorKc, nblk = (nv + K - 1) / K;
+    auto cx = [&](int k) { return pass == 0 ? u[k] > 0.0 : u[k] < 0.0; };
+    auto cy = [&](int k) { return pass == 0 ? v[k] > 0.0 : v[k] < 0.0; };
+    std::vector<int> rows, cols, elem;
+    wblk.clear();
+    for (int b = 0; b < nblk; ++b) {
+        bool wave = false;
+        for (int k = b * K; k < std::min(nv, b * K + K); ++k) wave = wave || (cx(k) && cy(k));
+        if (wave) { wblk.push_back(b); continue; }
+        for (int k = b * K; k < std::min(nv, b * K + K); ++k)
+            (cx(k) ? rows : cy(k) ? cols : elem).push_back(k);
+    }
+    nrow = (int)rows.size(); ncol = (int)cols.size(); nelem = (int)elem.size();
+    lk = rows;
+    lk.insert(lk.end(), cols.begin(), cols.end());
+    lk.insert(lk.end(), elem.begin(), elem.end());
+}
+
 // sweep scratch (elements of the storage type): corner copy, wall densities of
 // the edge lines and the body lines, folded line inputs
 size_t micro_fold_offset(int nv, int nlines) { return ((2 * (size_t)nv + (2 + (size_t)nlines) * kMaxLine + 3) / 4) * 4; }
@@ -1098,7 +1288,7 @@ cudaError_t launch_micro_sgs(const MicroArgs& m, const SweepPlanHost& plan, cons
     if (fixed + slot > kSmemMax) return cudaErrorInvalidValue;
     const size_t rfit = (kSmemMax - fixed) / slot;
     const int R = rfit >= 8 ? 8 : rfit >= 4 ? 4 : rfit >= 2 ? 2 : 1;
-    void (*wave)(MicroArgs, const F*, const F*, F*, const F*, int, int, int);
+    void (*wave)(MicroArgs, const F*, const F*, F*, const F*, int, int, int, int);
     if (m.P.bodies) {
         if (vec) wave = R == 8 ? k_sgs_wave<F, 8, true, true> : R == 4 ? k_sgs_wave<F, 4, true, true> : R == 2 ? k_sgs_wave<F, 2, true, true> : k_sgs_wave<F, 1, true, true>;
         else wave = R == 8 ? k_sgs_wave<F, 8, false, true> : R == 4 ? k_sgs_wave<F, 4, false, true> : R == 2 ? k_sgs_wave<F, 2, false, true> : k_sgs_wave<F, 1, false, true>;
@@ -1111,6 +1301,57 @@ cudaError_t launch_micro_sgs(const MicroArgs& m, const SweepPlanHost& plan, cons
         cudaError_t e = cudaFuncSetAttribute(wave, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem);
         if (e != cudaSuccess) return e;
     }
+    void (*lines)(MicroArgs, const F*, const F*, F*, const F*, int, int, int, int, int, int) =
+        m.P.bodies ? k_sgs_lines<F, true> : k_sgs_lines<F, false>;
+    // one segment.  On a large level the wavefront kernel takes only the blocks of
+    // velocities coupled in both directions and the line-class kernel the rest; on a
+    // small one the wavefront's dependency chain, not its traffic, sets the time and
+    // one wavefront launch over every block is faster than two launches.
+    const bool split = plan.split == 1 || (plan.split == 0 && (size_t)m.L.nc * m.V.nv >= kSweepSplitMinCv);
+    // timing mode: an event pair around a launch, with the cell-velocity pairs it sweeps
+    auto timed = [&](int kind, double units, auto&& launch) {
+        SweepTimer* T = plan.timer;
+        if (!T) { launch(); return cudaGetLastError(); }
+        while ((int)T->ev.size() < 2 * (T->used + 1)) {
+            cudaEvent_t e;
+            cudaError_t ce = cudaEventCreate(&e);
+            if (ce != cudaSuccess) return ce;
+            T->ev.push_back(e);
+        }
+        if ((int)T->kind.size() <= T->used) { T->kind.resize(T->used + 1); T->units.resize(T->used + 1); }
+        cudaError_t e = cudaEventRecord(T->ev[2 * T->used], st);
+        if (e != cudaSuccess) return e;
+        launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(T->ev[2 * T->used + 1], st)) != cudaSuccess) return e;
+        T->kind[T->used] = kind;
+        T->units[T->used] = units;
+        T->used++;
+        return cudaSuccess;
+    };
+    auto segment = [&](int pass, int dd, int end) {
+        const int nw = split ? m.V.nwblk[pass] : nblk;
+        const int nbr = (m.V.nrow[pass] + 127) / 128, nbc = (m.V.ncol[pass] + 127) / 128;
+        const int nbe = pass == 0 ? (m.V.nelem[pass] + 127) / 128 : 0;
+        const int nb = split ? nbr * m.L.ny + nbc * m.L.nx + nbe * m.L.ny : 0;
+        double cells = 0.0;                            // cells on the segment's diagonals
+        for (int q = dd; q < end; ++q) {
+            const int d = pass == 0 ? q : m.L.nx + m.L.ny - 2 - q;
+            cells += std::min(m.L.nx - 1, d) - std::max(0, d - (m.L.ny - 1)) + 1;
+        }
+        const double kl = (double)m.V.nrow[pass] + m.V.ncol[pass] + (pass == 0 ? m.V.nelem[pass] : 0);
+        const double kw = std::min((double)nw * kInteriorKc, (double)m.V.nv);
+        cudaError_t e = cudaSuccess;
+        if (nb > 0 && (e = timed(1, cells * kl, [&] {
+                lines<<<nb, 128, 0, st>>>(m, invD, r, x, fold, pass, dd, end, nbr, nbc, nbe);
+            })) != cudaSuccess)
+            return e;
+        if (nw > 0 && (e = timed(0, cells * kw, [&] {
+                wave<<<nw, nthr, wsmem, st>>>(m, invD, r, x, fold, pass, dd, end, split ? 1 : 0);
+            })) != cudaSuccess)
+            return e;
+        return cudaSuccess;
+    };
     auto fold_range = [&](int pass, int e0, int ne) {
         const int n = nblk * ne * kInteriorKc;
         if (n > 0) k_line_fold<F><<<(n + 255) / 256, 256, 0, st>>>(m, invD, r, x, rho_lines, fold, pass, e0, ne);
@@ -1134,8 +1375,7 @@ cudaError_t launch_micro_sgs(const MicroArgs& m, const SweepPlanHost& plan, cons
         for (int b = 0; b <= plan.nbrk[pass]; ++b) {
             const int end = b < plan.nbrk[pass] ? plan.brk[pass][b].dd : nd;
             if (end > dd) {
-                wave<<<nblk, nthr, wsmem, st>>>(m, invD, r, x, fold, pass, dd, end);
-                if ((e = cudaGetLastError()) != cudaSuccess) return e;
+                if ((e = segment(pass, dd, end)) != cudaSuccess) return e;
                 dd = end;
             }
             if (b < plan.nbrk[pass]) {

@@ -68,7 +68,18 @@ struct miugks_solver {
     double *rms_part = nullptr, *rms_out = nullptr;
     double dtp_min = 0;
     int iter = 0;
-    int cycle = 0;                              // 0 V, 1 W, 2 F (both multigrid cycles)
+    int cycle = 0;                              // 0 V, 1 W, 2 F, 3 adaptive (both multigrid cycles)
+    // adaptive cycle: a second coarse visit when the first left more than adapt_ratio of the
+    // coarse residual it started from; decisions kept in a ring (1 = second visit)
+    double adapt_ratio = 0.2;
+    long adapt_n = 0;
+    std::vector<unsigned char> adapt_log = std::vector<unsigned char>(4096);
+    double* nrm = nullptr;                      // device: 128 partial sums and the total
+    int sweep_split = 0;                        // evolution sweep: 0 by size, 1 split by coupling class, 2 never
+    // timing mode: the finest level's wavefront and line-class sweep launches; totals since the last read
+    SweepTimer sweep_timer;
+    double t_sweepk[2] = {0, 0}, u_sweepk[2] = {0, 0};
+    long n_sweepk[2] = {0, 0};
     bool initialised = false;
     bool timing = false;
     cudaEvent_t ev[6] = {};
@@ -307,10 +318,12 @@ MicroArgs micro_args(miugks_solver* s, int l)
     return MicroArgs{s->lev[l].dev, s->vel, s->bc, s->Cw, s->lev[l].inv_tau, s->lev[l].plan};
 }
 
-SweepPlanHost sweep_plan(const HLevel& Lv)
+SweepPlanHost sweep_plan(const miugks_solver* s, const HLevel& Lv)
 {
     SweepPlanHost h{};
     for (int p = 0; p < 2; ++p) { h.brk[p] = Lv.brk[p].data(); h.nbrk[p] = (int)Lv.brk[p].size(); }
+    h.split = s->sweep_split;
+    h.timer = s->timing && &Lv == &s->lev[0] ? const_cast<SweepTimer*>(&s->sweep_timer) : nullptr;
     return h;
 }
 
@@ -459,6 +472,25 @@ miugks_status timed_macro_sgs(miugks_solver* s, const MacroArgs& ma, HLevel& Lv,
     return MIUGKS_OK;
 }
 
+// host value of the sum of squares of n device values (synchronises the stream)
+template <typename T>
+miugks_status sumsq(miugks_solver* s, const T* a, size_t n, double* h)
+{
+    CK(launch_sumsq<T>(a, n, s->nrm, s->nrm + 128, s->st));
+    CK(cudaMemcpyAsync(h, s->nrm + 128, sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    return MIUGKS_OK;
+}
+
+// adaptive cycle: is another coarse visit due (and record the decision)
+bool adapt_again(miugks_solver* s, double before, double after)
+{
+    const bool again = after > s->adapt_ratio * s->adapt_ratio * before;
+    s->adapt_log[s->adapt_n++ % s->adapt_log.size()] = again ? 1 : 0;
+    return again;
+}
+constexpr int kAdaptMaxVisits = 2;
+
 // FAS cycle (Eq. FASCYC) of level l: forcing function and frozen Gamma from the
 // level's W^n, then one visit.  A visit smooths, corrects from the next level
 // (one coarse visit for V; W: two W visits; F: an F visit then a V visit, the
@@ -496,7 +528,21 @@ miugks_status fas_visit(miugks_solver* s, int l, double dti, int type, bool firs
     CK(launch_restrict<double>(Lv.dev, Cv.dev, 4, 1, Lv.Wc, Cv.Wn, s->st));
     CK(launch_restrict<double>(Lv.dev, Cv.dev, 4, 1, Lv.R, Cv.Rc, s->st));
     ST(fas(s, l + 1, dti, type));
-    if (type != 0) ST(fas_visit(s, l + 1, dti, type == 1 ? 1 : 0, false));
+    if (type == 1 || type == 2) ST(fas_visit(s, l + 1, dti, type == 1 ? 1 : 0, false));
+    if (type == 3) {
+        // adaptive: the coarse residual on entry is the restricted R; after a visit, P + R_E(W)
+        const size_t c4 = 4 * (size_t)Cv.nc;
+        MacroArgs mc = macro_args(s, l + 1, dti);
+        double before = 0.0, after = 0.0;
+        ST(sumsq<double>(s, Cv.Rc, c4, &before));
+        for (int visit = 1; visit < kAdaptMaxVisits; ++visit) {
+            CK(launch_macro_resid(mc, Cv.Wc, Cv.gx, Cv.gy, Cv.P, Cv.R, 1, s->st));
+            ST(sumsq<double>(s, Cv.R, c4, &after));
+            if (!adapt_again(s, before, after)) break;
+            before = after;
+            ST(fas_visit(s, l + 1, dti, 3, false));
+        }
+    }
     CK(launch_sub(Cv.dW, Cv.Wc, Cv.Wn, 4 * (size_t)Cv.nc, s->st));
     CK(launch_prolong_state(Lv.dev, Lv.pidx, Lv.pw, Cv.dW, Lv.Wc, s->st));
     for (int m = 0; m < s->opts.nu2; ++m) {
@@ -520,7 +566,7 @@ miugks_status cs(miugks_solver* s, int l, int type)
     const bool coarsest = l == s->L - 1;
     const int npre = coarsest ? (s->L == 1 ? 1 : s->opts.nu_coarse) : s->opts.nu1;
     for (int m = 0; m < npre; ++m) {
-        CK(launch_micro_sgs<F>(mi, sweep_plan(Lv), s->Zw, invD, r, dl, xc, s->st));
+        CK(launch_micro_sgs<F>(mi, sweep_plan(s, Lv), s->Zw, invD, r, dl, xc, s->st));
         bool last = coarsest && m == npre - 1;
         CK(launch_micro_renew<F>(mi, s->Zw, dl, r, df, last ? 0 : 1, s->st));
         if (last) return MIUGKS_OK;
@@ -530,7 +576,24 @@ miugks_status cs(miugks_solver* s, int l, int type)
     CK(launch_restrict<F>(Lv.dev, Cv.dev, s->nv, 2, r, (F*)Cv.r, s->st));
     if (type != 0) CK(cudaMemcpyAsync(Cv.r0, Cv.r, nC * sizeof(F), cudaMemcpyDeviceToDevice, s->st));
     ST(cs<F>(s, l + 1, type));
-    if (type != 0) {
+    if (type == 3) {
+        // adaptive: another visit for the coarse residual r_H - A_H df_H the corrections so
+        // far leave, while a visit leaves more than the ratio of the residual it started from
+        MicroArgs mc = micro_args(s, l + 1);
+        double before = 0.0, after = 0.0;
+        ST(sumsq<F>(s, (const F*)Cv.r0, nC, &before));
+        CK(cudaMemcpyAsync(Cv.acc, Cv.df, nC * sizeof(F), cudaMemcpyDeviceToDevice, s->st));
+        for (int visit = 1; visit < kAdaptMaxVisits; ++visit) {
+            CK(cudaMemcpyAsync(Cv.r, Cv.r0, nC * sizeof(F), cudaMemcpyDeviceToDevice, s->st));
+            CK(launch_micro_renew<F>(mc, s->Zw, (F*)Cv.acc, (F*)Cv.r, nullptr, 1, s->st));   // r_H - A_H acc
+            ST(sumsq<F>(s, (const F*)Cv.r, nC, &after));
+            if (!adapt_again(s, before, after)) break;
+            before = after;
+            ST(cs<F>(s, l + 1, 3));
+            CK(launch_micro_renew<F>(mc, s->Zw, (F*)Cv.df, (F*)Cv.r, (F*)Cv.acc, 0, s->st));  // acc += df_H
+        }
+        CK(cudaMemcpyAsync(Cv.df, Cv.acc, nC * sizeof(F), cudaMemcpyDeviceToDevice, s->st));
+    } else if (type != 0) {
         MicroArgs mc = micro_args(s, l + 1);
         CK(cudaMemcpyAsync(Cv.acc, Cv.df, nC * sizeof(F), cudaMemcpyDeviceToDevice, s->st));
         CK(cudaMemcpyAsync(Cv.r, Cv.r0, nC * sizeof(F), cudaMemcpyDeviceToDevice, s->st));
@@ -541,7 +604,7 @@ miugks_status cs(miugks_solver* s, int l, int type)
     CK(launch_prolong_add<F>(Lv.dev, Cv.dev, s->nv, 2, Lv.pidx, Lv.pw, (F*)Cv.df, df, dl, s->st));
     for (int m = 0; m < s->opts.nu2; ++m) {
         CK(launch_micro_renew<F>(mi, s->Zw, dl, r, nullptr, 1, s->st));
-        CK(launch_micro_sgs<F>(mi, sweep_plan(Lv), s->Zw, invD, r, dl, xc, s->st));
+        CK(launch_micro_sgs<F>(mi, sweep_plan(s, Lv), s->Zw, invD, r, dl, xc, s->st));
         CK(launch_micro_renew<F>(mi, s->Zw, dl, r, df, 0, s->st));
     }
     return MIUGKS_OK;
@@ -842,6 +905,16 @@ miugks_status miugks_create(const miugks_mesh* mesh, const miugks_vgrid* vg, con
         if ((st = upload(s, (float**)&s->vel.vf, s->vfh)) != MIUGKS_OK) break;
         if ((st = upload(s, (float**)&s->vel.wf, s->wfh)) != MIUGKS_OK) break;
         s->vel.nu = s->nu; s->vel.nvv = s->nvv; s->vel.nv = s->nv; s->vel.umax = s->umax; s->vel.vmax = s->vmax;
+        for (int p = 0; p < 2 && st == MIUGKS_OK; ++p) {
+            std::vector<int> wb, lk;
+            sweep_classes(s->uh.data(), s->vh.data(), s->nv, p, wb, lk, s->vel.nrow[p], s->vel.ncol[p], s->vel.nelem[p]);
+            s->vel.nwblk[p] = (int)wb.size();
+            if (wb.empty()) wb.push_back(0);        // keep a valid pointer
+            if (lk.empty()) lk.push_back(0);
+            if ((st = upload(s, (int**)&s->vel.wblk[p], wb)) != MIUGKS_OK) break;
+            st = upload(s, (int**)&s->vel.lk[p], lk);
+        }
+        if (st != MIUGKS_OK) break;
         if ((st = upload(s, &s->bc, s->bch)) != MIUGKS_OK) break;
         s->Cwh.assign((size_t)n_bcs * s->nv, 0.0);
         for (int b = 0; b < n_bcs; ++b) refresh_bc_tables(s, b);
@@ -881,6 +954,7 @@ miugks_status miugks_create(const miugks_mesh* mesh, const miugks_vgrid* vg, con
         if ((st = dalloc(s, &s->Fy, 4 * (size_t)L0.nfy)) != MIUGKS_OK) break;
         if ((st = dalloc(s, &s->rms_part, 64 * 5)) != MIUGKS_OK) break;
         if ((st = dalloc(s, &s->rms_out, 8)) != MIUGKS_OK) break;
+        if ((st = dalloc(s, &s->nrm, 129)) != MIUGKS_OK) break;
         if (cudaMemset(s->rms_out, 0, 8 * sizeof(double)) != cudaSuccess) { st = fail(s, MIUGKS_ECUDA, "cudaMemset"); break; }
         {
             int nlines = 0, nlm = 0;
@@ -952,7 +1026,7 @@ static miugks_status enqueue_iterations(miugks_solver* s, int n_iter)
 {
     for (int it = 0; it < n_iter; ++it) {
         bool graphable = s->graph_ok && !s->timing && s->st != nullptr && !(s->opts.dtn_growth > 0.0) &&
-                         s->eager_done > 0;
+                         s->eager_done > 0 && s->cycle != 3;
         if (graphable && !s->gexec) {
             cudaError_t e = cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal);
             miugks_status st = e == cudaSuccess ? one_iteration(s) : MIUGKS_ECUDA;
@@ -989,6 +1063,15 @@ static miugks_status enqueue_iterations(miugks_solver* s, int n_iter)
                 }
                 s->n_macro += s->n_macro_used;
                 s->n_macro_used = 0;
+                SweepTimer& T = s->sweep_timer;
+                for (int q = 0; q < T.used; ++q) {
+                    float t = 0;
+                    CK(cudaEventElapsedTime(&t, T.ev[2 * q], T.ev[2 * q + 1]));
+                    s->t_sweepk[T.kind[q]] += t;
+                    s->u_sweepk[T.kind[q]] += T.units[q];
+                    s->n_sweepk[T.kind[q]]++;
+                }
+                T.used = 0;
             }
         }
         s->iter++;
@@ -1149,7 +1232,7 @@ miugks_status miugks_init_from_coarse(miugks_solver* s, const miugks_solver* c)
 miugks_status miugks_set_cycle(miugks_solver* s, int type)
 {
     if (!s) return MIUGKS_EINVAL;
-    if (type < 0 || type > 2) return fail(s, MIUGKS_EINVAL, "cycle type %d: 0 V, 1 W, 2 F", type);
+    if (type < 0 || type > 3) return fail(s, MIUGKS_EINVAL, "cycle type %d: 0 V, 1 W, 2 F, 3 adaptive", type);
     if (type != 0)
         for (int l = 1; l < s->L; ++l) {
             HLevel& Cv = s->lev[l];
@@ -1167,6 +1250,40 @@ miugks_status miugks_set_cycle(miugks_solver* s, int type)
     }
     s->cycle = type;
     return MIUGKS_OK;
+}
+
+miugks_status miugks_set_sweep_split(miugks_solver* s, int mode)
+{
+    if (!s) return MIUGKS_EINVAL;
+    if (mode < 0 || mode > 2) return fail(s, MIUGKS_EINVAL, "sweep split mode %d: 0 by size, 1 always, 2 never", mode);
+    if (mode != s->sweep_split && s->gexec) {
+        // the captured iteration holds the old launch sequence
+        CK(cudaStreamSynchronize(s->st));
+        cudaGraphExecDestroy(s->gexec);
+        if (s->graph) cudaGraphDestroy(s->graph);
+        s->gexec = nullptr;
+        s->graph = nullptr;
+    }
+    s->sweep_split = mode;
+    return MIUGKS_OK;
+}
+
+miugks_status miugks_set_adaptive_ratio(miugks_solver* s, double ratio)
+{
+    if (!s) return MIUGKS_EINVAL;
+    if (!(ratio >= 0.0)) return fail(s, MIUGKS_EINVAL, "adaptive ratio %g must be >= 0", ratio);
+    s->adapt_ratio = ratio;
+    return MIUGKS_OK;
+}
+
+int miugks_adaptive_decisions(const miugks_solver* s, unsigned char* out, int cap)
+{
+    if (!s) return -1;
+    const long n = s->adapt_n, ring = (long)s->adapt_log.size();
+    long m = n < cap ? n : cap;
+    if (m > ring) m = ring;
+    for (long q = 0; q < m && out; ++q) out[q] = s->adapt_log[(n - m + q) % ring];
+    return (int)n;
 }
 
 miugks_status miugks_get_wall(miugks_solver* s, int bc, int* n_faces, double* p, double* tau, double* q)
@@ -1236,6 +1353,19 @@ miugks_status miugks_macro_sweep_times(miugks_solver* s, double* ms, int* launch
     return MIUGKS_OK;
 }
 
+miugks_status miugks_sweep_kernel_times(miugks_solver* s, double out[6])
+{
+    if (!s || !out) return MIUGKS_EINVAL;
+    for (int k = 0; k < 2; ++k) {
+        out[3 * k] = s->timing ? s->t_sweepk[k] : -1.0;
+        out[3 * k + 1] = s->timing ? (double)s->n_sweepk[k] : 0.0;
+        out[3 * k + 2] = s->timing ? s->u_sweepk[k] : 0.0;
+        s->t_sweepk[k] = s->u_sweepk[k] = 0.0;
+        s->n_sweepk[k] = 0;
+    }
+    return MIUGKS_OK;
+}
+
 miugks_status miugks_kernel_times(miugks_solver* s, double* flux_ms, double* sweep_ms, double* total_ms)
 {
     if (!s) return MIUGKS_EINVAL;
@@ -1272,11 +1402,11 @@ miugks_status miugks_stage_sgs_micro(miugks_solver* s, int lev, const double* in
     if (s->mixed) {
         k_invD_from_itau<float><<<Lv.nc, 128, 0, s->st>>>(Lv.dev, s->vel, Lv.inv_tau, (float*)Lv.invD);
         CK(cudaGetLastError());
-        CK(launch_micro_sgs<float>(mi, sweep_plan(Lv), s->Zw, (float*)Lv.invD, (float*)Lv.r, (float*)Lv.dl, (float*)s->xcorner, s->st));
+        CK(launch_micro_sgs<float>(mi, sweep_plan(s, Lv), s->Zw, (float*)Lv.invD, (float*)Lv.r, (float*)Lv.dl, (float*)s->xcorner, s->st));
     } else {
         k_invD_from_itau<double><<<Lv.nc, 128, 0, s->st>>>(Lv.dev, s->vel, Lv.inv_tau, (double*)Lv.invD);
         CK(cudaGetLastError());
-        CK(launch_micro_sgs<double>(mi, sweep_plan(Lv), s->Zw, (double*)Lv.invD, (double*)Lv.r, (double*)Lv.dl, (double*)s->xcorner,
+        CK(launch_micro_sgs<double>(mi, sweep_plan(s, Lv), s->Zw, (double*)Lv.invD, (double*)Lv.r, (double*)Lv.dl, (double*)s->xcorner,
                                     s->st));
     }
     return to_host(s, x, Lv.dl, n);

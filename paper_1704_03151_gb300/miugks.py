@@ -93,6 +93,8 @@ def load():
         "miugks_macro_sweep_times": [vp, _P(_d), _P(_i)], "miugks_set_cycle": [vp, _i],
         "miugks_init_from_coarse": [vp, vp],
         "miugks_set_adjoint_options": [vp, _i], "miugks_stage_macro_jacobian_transposed": [vp, vp, vp, vp],
+        "miugks_set_adaptive_ratio": [vp, _d], "miugks_adaptive_decisions": [vp, vp, _i],
+        "miugks_set_sweep_split": [vp, _i], "miugks_sweep_kernel_times": [vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -117,7 +119,8 @@ def exported_symbols():
             "miugks_objective",
             "miugks_adjoint", "miugks_residual_rms_noalloc", "miugks_save", "miugks_load",
             "miugks_macro_sweep_times", "miugks_set_cycle", "miugks_init_from_coarse",
-            "miugks_set_adjoint_options", "miugks_stage_macro_jacobian_transposed"]
+            "miugks_set_adjoint_options", "miugks_stage_macro_jacobian_transposed", "miugks_set_adaptive_ratio",
+            "miugks_adaptive_decisions", "miugks_set_sweep_split", "miugks_sweep_kernel_times"]
 
 
 def _ptr(a):
@@ -269,8 +272,21 @@ class Solver:
         self._check(self._lib.miugks_init_from_coarse(self.h, coarse.h))
 
     def set_cycle(self, cycle):
-        """Multigrid cycle type of both cycles: "V", "W" or "F"."""
-        self._check(self._lib.miugks_set_cycle(self.h, {"V": 0, "W": 1, "F": 2}[cycle]))
+        """Multigrid cycle type of both cycles: "V", "W", "F" or "A" (adaptive)."""
+        self._check(self._lib.miugks_set_cycle(self.h, {"V": 0, "W": 1, "F": 2, "A": 3}[cycle]))
+
+    def set_sweep_split(self, mode):
+        """Evolution-sweep layout: "auto" (by level size), "split" or "wave" (same results)."""
+        self._check(self._lib.miugks_set_sweep_split(self.h, {"auto": 0, "split": 1, "wave": 2}[mode]))
+
+    def set_adaptive_ratio(self, ratio):
+        self._check(self._lib.miugks_set_adaptive_ratio(self.h, float(ratio)))
+
+    def adaptive_decisions(self, cap=4096):
+        """Decisions of the adaptive cycle so far, oldest first (1 = a second coarse visit)."""
+        out = np.zeros(cap, dtype=np.uint8)
+        n = self._lib.miugks_adaptive_decisions(self.h, _ptr(out), cap)
+        return out[:min(n, cap)].copy()
 
     def wall(self, bc):
         n = _i(0)
@@ -286,6 +302,13 @@ class Solver:
         a, b, c = _d(), _d(), _d()
         self._check(self._lib.miugks_kernel_times(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
         return a.value, b.value, c.value
+
+    def sweep_kernel_times(self):
+        """Finest-level evolution-sweep kernels since the last call (timing mode):
+        {"wave": (ms, launches, cell-velocity pairs), "lines": (...)}."""
+        out = np.zeros(6)
+        self._check(self._lib.miugks_sweep_kernel_times(self.h, _ptr(out)))
+        return {"wave": (out[0], int(out[1]), out[2]), "lines": (out[3], int(out[4]), out[5])}
 
     def macro_sweep_times(self):
         """(total ms, launches) of the finest-level prediction sweeps since the last call."""

@@ -76,3 +76,32 @@ def test_mixed_w_cycle_close_to_oracle(lib):
     g.init_fields(*fields)
     o.step(4), g.step(4)
     assert rel(g.get_f(), o.get_f()) < 2e-5
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_adaptive_cycle_matches_oracle(lib, name):
+    """Adaptive cycle (Sec. 3.4 names it; a second coarse visit when the first
+    left more than a ratio of the coarse residual): both implementations take
+    the same decisions, and their iterates agree at the 1e-10 bar.  Ratios 0
+    and 'never' reproduce the W and V cycles bit for bit on the GPU too."""
+    case = CASES[name]()
+    fields = wl.random_fields(case, 7, amp=0.08)
+    o, g = oracle.Oracle(case), lib.Solver(case)
+    for s in (o, g):
+        s.set_cycle("A")
+        s.init_fields(*fields)
+    for n in (1, 3):
+        ro, rg = o.step(n), g.step(n)
+        assert np.array_equal(g.adaptive_decisions(), o.adapt_log()), (name, n)
+        assert rel(g.get_f(), o.get_f()) < TOL, (name, n)
+        assert np.allclose(rg, ro, rtol=1e-8, atol=1e-14), (name, n)
+    f = {}
+    for label, cyc, ratio in (("W", "W", None), ("A0", "A", 0.0), ("V", "V", None), ("Ainf", "A", 1e300)):
+        s = lib.Solver(case)
+        s.set_cycle(cyc)
+        if ratio is not None:
+            s.set_adaptive_ratio(ratio)
+        s.init_fields(*fields)
+        s.step(2)
+        f[label] = s.get_f()
+    assert np.array_equal(f["A0"], f["W"]) and np.array_equal(f["Ainf"], f["V"])
