@@ -12,8 +12,8 @@ residual out); time_to_residual = wall time to RMS residual 1e-6 from rest.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
---impl reference times the FP64 CPU oracle (serial C) on the host on the
-same workload.  Under torchrun with N > 1 every rank runs an independent
+--impl reference times the FP64 CPU oracle (its OpenMP build, on every host
+core) on the same workload.  Under torchrun with N > 1 every rank runs an independent
 replica (the method has no data-parallel exchange step) and value sums the
 ranks' updates over the slowest rank's time.
 """
@@ -129,9 +129,16 @@ def max_over_ranks(x, world):
     return float(t.item())
 
 
-def oracle_iterations_per_s(n_iter):
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_iterations_per_s(n_iter, omp=False):
     import oracle
-    o = oracle.Oracle(case())
+    o = oracle.Oracle(case(), omp=omp)
     o.init_uniform(1.0, 0.0, 0.0, 1.0)
     t0 = time.perf_counter()
     o.step(n_iter)
@@ -145,7 +152,7 @@ def run_reference(args):
         return 0
     cv = NX * NY * NVEL * NVEL
     import oracle
-    o = oracle.Oracle(case())
+    o = oracle.Oracle(case(), omp=True)                 # the OpenMP build: every host core, serial bits
     o.init_uniform(1.0, 0.0, 0.0, 1.0)
     for _ in range(args.warmup):
         o.step(1)
@@ -159,8 +166,9 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, "nvel": NVEL, "levels": LEVELS, "kn": KN},
             "impl": "reference",
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "%d full outer iterations of the workload, serial C oracle" % args.steps},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+                             "sample": "%d full outer iterations of the workload, OpenMP build of the C oracle "
+                                       "on all host cores" % args.steps},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -258,7 +266,7 @@ def macro_roofline(m, precision):
             "limiter": "dependency chain: %d anti-diagonals per sweep, one halo exchange each" % (NX + NY - 1)}
 
 
-def flux_roofline(m, precision, nx=None, ny=None, nv=None):
+def flux_roofline(m, precision, nx=None, ny=None, nv=None, traffic=None):
     """Roofline of the face-flux kernel: algorithmic flops per (face, velocity)
     in the arithmetic type against that type's measured peak, and algorithmic
     bytes (f read once, fluxes written once) against the measured copy rate."""
@@ -278,7 +286,7 @@ def flux_roofline(m, precision, nx=None, ny=None, nv=None):
                                ("FP32" if precision == "mixed" else "FP64 nominal"),
                 "hbm_frac": bytes_ / hpeak, "hbm_peak_source": hsrc}
     return {"bound": "hbm", "kernel": "k_face_flux", "achieved": bytes_, "peak": hpeak, "unit": "GB/s",
-            "frac": bytes_ / hpeak, "traffic": None, "peak_source": hsrc, "alu_frac": flops / fpeak}
+            "frac": bytes_ / hpeak, "traffic": traffic, "peak_source": hsrc, "alu_frac": flops / fpeak}
 
 
 # algorithmic passes over one per-velocity array (Nc Nv 2 values) per outer
@@ -368,20 +376,64 @@ def measure_plate(steps, warmup):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
+    # per-launch event timing of the flux and evolution-sweep kernels (timing mode, a separate pass)
+    s.set_timing(True)
+    s.kernel_times()
+    s.sweep_kernel_times()
+    nst = 3
+    s.step(nst)
+    flux_ms, sweep_ms, total_ms = s.kernel_times()
+    sk = s.sweep_kernel_times()
+    s.set_timing(False)
     cv = c["nx"] * c["ny"] * c["vgrid"]["nu"] * c["vgrid"]["nv"]
     b = PASSES_PER_ITERATION * 2 * cv * 4
     hpeak, hsrc = hbm_peak()
     s.close()
     return {"workload": "flat_plate_%dx%d_v48x48_kn0.1_4level_mixed" % (c["nx"], c["ny"]), "steps": steps,
             "value": cv / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "residual_last": [float(x) for x in res],
+            "stage_ms_per_step": {"flux": flux_ms / nst, "evolution_cs": sweep_ms / nst, "total": total_ms / nst},
+            "roofline_flux": flux_roofline({"flux_ms_per_launch": flux_ms / nst / 2.0}, "mixed", c["nx"], c["ny"],
+                                           c["vgrid"]["nu"] * c["vgrid"]["nv"], traffic=FLUX_TRAFFIC_PLATE_MIXED),
+            "roofline_sweep": sweep_roofline(sk, "mixed"),
             "step_hbm": {"bytes_per_step": b, "achieved": b / (ms * 1e-3) / 1e9, "peak": hpeak, "unit": "GB/s",
                          "frac": b / (ms * 1e-3) / 1e9 / hpeak, "peak_source": hsrc}}
+
+
+# Evolution-sweep kernels: per (cell, velocity) and sweep direction the
+# algorithmic traffic is three values read (the residual of G and H and the
+# inverse diagonal forward; the forward result and the inverse diagonal
+# backward) and two written (the new G and H): 20 B in FP32, 40 B in FP64.
+SWEEP_VALUES_PER_CV = 5
+# DRAM bytes of one finest-level launch of each flat-plate sweep kernel (mixed,
+# forward direction) per cell-velocity pair it sweeps, from the ncu captures
+# summarised in profiles/k_sgs_plate128x96_v48_mixed.md (None until captured)
+SWEEP_TRAFFIC_PER_CV = {"lines": None, "wave": None}
+FLUX_TRAFFIC_PLATE_MIXED = None
+
+
+def sweep_roofline(sk, precision):
+    """Per kernel: algorithmic bytes of its finest-level launches over their
+    event-timed duration, against the measured copy rate."""
+    size = 4 if precision == "mixed" else 8
+    hpeak, hsrc = hbm_peak()
+    out = {}
+    for name in ("lines", "wave"):
+        ms, n, units = sk[name]
+        if n <= 0 or ms <= 0:
+            continue
+        gbs = SWEEP_VALUES_PER_CV * size * units / (ms * 1e-3) / 1e9
+        tr = SWEEP_TRAFFIC_PER_CV[name]
+        out[name] = {"bound": "hbm", "kernel": "k_sgs_lines" if name == "lines" else "k_sgs_wave",
+                     "achieved": gbs, "peak": hpeak, "unit": "GB/s", "frac": gbs / hpeak,
+                     "traffic": None if tr is None else tr * units / n, "peak_source": hsrc,
+                     "launch_ms": ms / n, "cv_per_launch": units / n}
+    return out
 
 
 def measure_square(steps, warmup, precision="mixed"):
     """The square-cylinder configuration at full size (160x120 cells with the
     32x24-cell square solid, 18,432 fluid cells, 89x89 velocities on
-    [-15,15]^2 with the composite Boole rule, Ma 5, Kn 0.1, 4-level V-cycle,
+    [-15,15]^2 with the trapezoid rule, Ma 5, Kn 0.1, 4-level V-cycle,
     dt_n growth 3, rear region at 0.1 of the freestream density): 152 M
     cell-velocity pairs (the body's cells counted, as they are swept), one
     FP32 per-velocity array 1.2 GB.  Same timing as the headline."""
@@ -418,6 +470,48 @@ def measure_square(steps, warmup, precision="mixed"):
             "residual_last": [float(x) for x in res],
             "step_hbm": {"bytes_per_step": b, "achieved": b / (ms * 1e-3) / 1e9, "peak": hpeak, "unit": "GB/s",
                          "frac": b / (ms * 1e-3) / 1e9 / hpeak, "peak_source": hsrc}}
+
+
+def converge_big(name, max_iter=1500):
+    """The flat plate or the square cylinder at full size from its initial
+    state to RMS residual 1e-6 (Sec. 4.1): the mixed form until the residual
+    stops falling (the FP32 floor of these stretched meshes), then FP64 from
+    that state (refine.run); and the FP64 form alone, for comparison.  Wall
+    times include every host read of the residual (one per 5 iterations)."""
+    import torch
+    from paper_1704_03151_gb300 import miugks, refine, workloads
+    c = workloads.flat_plate() if name == "plate" else workloads.square_cylinder()
+    warm = miugks.Solver(c, precision="mixed")               # one-time kernel set-up of both forms
+    warm.init_fields(*workloads.initial_fields(c))
+    warm.step(2)
+    w64 = miugks.Solver(c, precision="fp64")
+    w64.copy_state(warm)
+    w64.step(2)
+    warm.close()
+    w64.close()
+    s, info = refine.run(c, tol=1e-6, max_iter=max_iter)
+    s.close()
+    d = miugks.Solver(c, precision="fp64")
+    d.init_fields(*workloads.initial_fields(c))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    iters, prev, stop = 0, None, "max_iter"
+    while iters < max_iter:
+        rr = d.step(5)
+        iters += 5
+        if max(rr) < 1e-6:
+            stop = "tolerance"
+            break
+        if prev is not None and abs(max(rr) - prev) < 1e-3 * prev:
+            stop = "floor"
+            break
+        prev = max(rr)
+    torch.cuda.synchronize()
+    fp64 = {"seconds": time.perf_counter() - t0, "iterations": iters, "stopped_at": stop,
+            "residual": [float(x) for x in rr]}
+    d.close()
+    return {"mixed_then_fp64": info, "fp64": fp64,
+            "speedup": fp64["seconds"] / info["seconds"] if info["converged"] and stop == "tolerance" else None}
 
 
 def square_convergence(precision, max_iter, chunk=5, dtn_growth=None):
@@ -479,6 +573,23 @@ def square_mixed_error(conv):
             "wall_heat_flux": float(np.abs(q32 - q64).max() / np.abs(q64).max())}
 
 
+def run_plate_iter(args):
+    """--workload plate_iter: --steps outer iterations of the full-size flat
+    plate (mixed form) from its initial state, eagerly launched after the
+    first; a small, fixed target for kernel profiles."""
+    import torch
+    from paper_1704_03151_gb300 import build, miugks, workloads
+    build.build()
+    c = workloads.flat_plate()
+    s = miugks.Solver(c, precision=args.precision)
+    s.init_fields(*workloads.initial_fields(c))
+    res = s.step(args.steps)
+    torch.cuda.synchronize()
+    print(json.dumps({"workload": "flat_plate_%dx%d_v48x48_kn0.1_4level_%s" % (c["nx"], c["ny"], args.precision),
+                      "iterations": args.steps, "residual": [float(x) for x in res]}))
+    return 0
+
+
 def run_square(args):
     """--workload square: the full-size square cylinder, throughput in both
     forms over iterations 3-5 from the initial state (the start is violent at
@@ -527,7 +638,7 @@ def main():
     ap.add_argument("--no-plate", action="store_true", help="skip the full-size flat-plate throughput line")
     ap.add_argument("--no-square", action="store_true", help="skip the full-size square-cylinder throughput line")
     ap.add_argument("--workload", default="cavity64",
-                    choices=["cavity64", "kn_sweep", "adjoint", "cycles", "plate_adjoint", "square"])
+                    choices=["cavity64", "kn_sweep", "adjoint", "cycles", "plate_adjoint", "square", "plate_iter"])
     ap.add_argument("--count", type=int, default=32, help="cavities of the Kn sweep")
     ap.add_argument("--max-iter", type=int, default=1500)
     ap.add_argument("--adjoint", action="store_true", help="Kn sweep: adjoint lid-shear gradient of every case")
@@ -544,6 +655,8 @@ def main():
         return run_cycles(args)
     if args.workload == "plate_adjoint":
         return run_plate_adjoint(args)
+    if args.workload == "plate_iter":
+        return run_plate_iter(args)
     if args.workload == "square":
         return run_square(args)
     args.warmup = max(args.warmup, 3)
@@ -561,8 +674,12 @@ def main():
     plate = series = square = None
     if not args.no_plate and rank == 0:
         plate = measure_plate(max(5, args.steps // 5), args.warmup)
+        if not args.no_ttr:
+            plate["time_to_residual"] = converge_big("plate")
     if not args.no_square and rank == 0:
         square = measure_square(3, 2, "mixed")
+        if not args.no_ttr:
+            square["time_to_residual"] = converge_big("square", max_iter=400)
     if not args.no_ttr and rank == 0:
         series = kn_series()
     if rank != 0:
@@ -570,11 +687,16 @@ def main():
     cv = NX * NY * NVEL * NVEL
     cpu = None
     if not args.no_cpu_baseline:
-        n_iter = 4
-        ips, secs = oracle_iterations_per_s(n_iter)
-        cpu = {"value": ips * cv, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "%d outer iterations of the same workload (%.1f s), serial C oracle on the host" %
-                         (n_iter, secs)}
+        # the oracle as it stands on the host: its OpenMP build on every core (the same bits as the
+        # serial build), and the serial build on one core
+        n_omp, n_ser = 10, 5
+        ips, secs = oracle_iterations_per_s(n_omp, omp=True)
+        ips1, secs1 = oracle_iterations_per_s(n_ser, omp=False)
+        cpu = {"value": ips * cv, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+               "sample": "%d outer iterations of the same workload from rest (%.1f s), OpenMP build of the C "
+                         "oracle on all host cores" % (n_omp, secs),
+               "serial": {"value": ips1 * cv, "unit": UNIT, "cores": 1,
+                          "sample": "%d outer iterations (%.1f s), serial build" % (n_ser, secs1)}}
     line = {
         "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",

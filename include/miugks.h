@@ -191,6 +191,14 @@ int miugks_adaptive_decisions(const miugks_solver *s, unsigned char *out, int ca
  * coarse's stream.  MIUGKS_EINVAL when the meshes, bodies, velocity grids or
  * precisions do not match, MIUGKS_ESTATE when coarse has no state. */
 miugks_status miugks_init_from_coarse(miugks_solver *s, const miugks_solver *coarse);
+/* The state of src (f, and the iteration count that sets dt_n) becomes s's: a
+ * solver of the same mesh, bodies and velocity grid, of either precision (f is
+ * converted; W and q follow from its moments).  With it a run can take its
+ * bulk of iterations in the mixed form and finish in FP64, where the FP32
+ * rounding of the per-velocity fluxes sets a residual floor above the
+ * tolerance (the paper runs FP64 throughout).  Waits for src's stream.
+ * MIUGKS_EINVAL when the problems differ, MIUGKS_ESTATE when src has no state. */
+miugks_status miugks_copy_state(miugks_solver *s, const miugks_solver *src);
 
 /* Stages of one iteration on explicit host data, for kernel-level checks.
  *  flux: Step 1 at the current state -> R (nc x 4), time-averaged micro face

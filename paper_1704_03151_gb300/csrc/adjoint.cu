@@ -1489,6 +1489,17 @@ cudaError_t launch_to_double(const F* a, double* b, size_t n, cudaStream_t st)
 template cudaError_t launch_to_double<float>(const float*, double*, size_t, cudaStream_t);
 template cudaError_t launch_to_double<double>(const double*, double*, size_t, cudaStream_t);
 
+__global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, size_t n)
+{
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+        b[e] = (float)a[e];
+}
+cudaError_t launch_to_float(const double* a, float* b, size_t n, cudaStream_t st)
+{
+    k_to_float<<<1216, 256, 0, st>>>(a, b, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_adjoint_macro_m(const AdjDev& A, const double* y, double* m, cudaStream_t st)
 {
     k_adj_macro_m<<<A.L.nc, 256, 0, st>>>(A, y, m);

@@ -184,6 +184,7 @@ cudaError_t launch_multi_axpy(const double* Vb, int m, size_t n, const double* h
                               cudaStream_t st);
 cudaError_t launch_mass_dot(const LevelDev& L, const VelDev& V, const double* x, double* part, cudaStream_t st);
 template <typename F> cudaError_t launch_to_double(const F* a, double* b, size_t n, cudaStream_t st);
+cudaError_t launch_to_float(const double* a, float* b, size_t n, cudaStream_t st);
 cudaError_t launch_inv_tau(const GasDev& gas, const double* W, int nc, double* it, cudaStream_t st);
 cudaError_t launch_adjoint_invD(const LevelDev& L, const VelDev& V, const double* it, double* invD, cudaStream_t st);
 // m_c = (dr_c/dW~_c)^T y_c (micro residual w.r.t. the predicted state, heat flux held)

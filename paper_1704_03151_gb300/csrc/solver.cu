@@ -1229,6 +1229,33 @@ miugks_status miugks_init_from_coarse(miugks_solver* s, const miugks_solver* c)
     return MIUGKS_OK;
 }
 
+miugks_status miugks_copy_state(miugks_solver* s, const miugks_solver* src)
+{
+    if (!s || !src) return MIUGKS_EINVAL;
+    const HLevel& A = s->lev[0];
+    const HLevel& B = src->lev[0];
+    if (src->nv != s->nv || src->nu != s->nu || A.nx != B.nx || A.ny != B.ny || A.solid != B.solid)
+        return fail(s, MIUGKS_EINVAL, "copy_state: the solvers differ in mesh, bodies or velocity grid");
+    for (int i = 0; i <= A.nx; ++i)
+        if (A.xn[i] != B.xn[i]) return fail(s, MIUGKS_EINVAL, "copy_state: x nodes differ");
+    for (int j = 0; j <= A.ny; ++j)
+        if (A.yn[j] != B.yn[j]) return fail(s, MIUGKS_EINVAL, "copy_state: y nodes differ");
+    for (int k = 0; k < s->nv; ++k)
+        if (s->uh[k] != src->uh[k] || s->vh[k] != src->vh[k] || s->wh[k] != src->wh[k])
+            return fail(s, MIUGKS_EINVAL, "copy_state: velocity grids differ");
+    if (!src->initialised) return fail(s, MIUGKS_ESTATE, "copy_state: the source solver has no state");
+    const size_t n = 2 * (size_t)A.nc * s->nv;
+    CK(cudaStreamSynchronize(src->st));                    // the source state is complete
+    if (s->mixed == src->mixed) CK(cudaMemcpyAsync(s->f, src->f, n * s->fsz, cudaMemcpyDeviceToDevice, s->st));
+    else if (!s->mixed) CK(launch_to_double<float>((const float*)src->f, (double*)s->f, n, s->st));
+    else CK(launch_to_float((const double*)src->f, (float*)s->f, n, s->st));
+    ST(moments_now(s));
+    CK(cudaStreamSynchronize(s->st));
+    s->initialised = true;
+    s->iter = src->iter;
+    return MIUGKS_OK;
+}
+
 miugks_status miugks_set_cycle(miugks_solver* s, int type)
 {
     if (!s) return MIUGKS_EINVAL;

@@ -95,6 +95,7 @@ def load():
         "miugks_set_adjoint_options": [vp, _i], "miugks_stage_macro_jacobian_transposed": [vp, vp, vp, vp],
         "miugks_set_adaptive_ratio": [vp, _d], "miugks_adaptive_decisions": [vp, vp, _i],
         "miugks_set_sweep_split": [vp, _i], "miugks_sweep_kernel_times": [vp, vp],
+        "miugks_copy_state": [vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -120,7 +121,8 @@ def exported_symbols():
             "miugks_adjoint", "miugks_residual_rms_noalloc", "miugks_save", "miugks_load",
             "miugks_macro_sweep_times", "miugks_set_cycle", "miugks_init_from_coarse",
             "miugks_set_adjoint_options", "miugks_stage_macro_jacobian_transposed", "miugks_set_adaptive_ratio",
-            "miugks_adaptive_decisions", "miugks_set_sweep_split", "miugks_sweep_kernel_times"]
+            "miugks_adaptive_decisions", "miugks_set_sweep_split", "miugks_sweep_kernel_times",
+            "miugks_copy_state"]
 
 
 def _ptr(a):
@@ -270,6 +272,10 @@ class Solver:
     def init_from_coarse(self, coarse):
         """Initial state by bilinear prolongation of f from a solver on the next coarser mesh."""
         self._check(self._lib.miugks_init_from_coarse(self.h, coarse.h))
+
+    def copy_state(self, src):
+        """f (converted to this solver's precision) and the iteration count of src."""
+        self._check(self._lib.miugks_copy_state(self.h, src.h))
 
     def set_cycle(self, cycle):
         """Multigrid cycle type of both cycles: "V", "W", "F" or "A" (adaptive)."""

@@ -79,3 +79,28 @@ def test_mixed_converges_to_fp64_steady_state(lib):
     report("c2_converged it64=%d it32=%d" % (it64, it32), errs)
     assert abs(it32 - it64) <= max(3, it64 // 5)
     assert all(v < 1e-4 for v in errs.values()), errs
+
+
+def test_copy_state_converts_precision(lib):
+    """miugks_copy_state carries f between solvers of the same problem: mixed
+    to FP64 is exact (every float is a double), FP64 to mixed rounds to the
+    nearest float, and the copied solver then iterates as one given that f
+    through miugks_set_f."""
+    case = wl.cavity(n=16, nvel=12, kn=0.5, lid=0.2, levels=2)
+    m = lib.Solver(case, precision="mixed")
+    m.init_fields(*wl.random_fields(case, 4, amp=0.08))
+    m.step(3)
+    d = lib.Solver(case, precision="fp64")
+    d.copy_state(m)
+    assert d.iterations() == m.iterations() == 3
+    fm = m.get_f()
+    assert np.array_equal(d.get_f(), fm)
+    ref = lib.Solver(case, precision="fp64")
+    ref.set_f(fm)
+    rd, rr = d.step(2), ref.step(2)
+    assert np.array_equal(d.get_f(), ref.get_f()) and np.array_equal(rd, rr)
+    back = lib.Solver(case, precision="mixed")
+    back.copy_state(d)
+    assert np.array_equal(back.get_f(), d.get_f().astype(np.float32).astype(np.float64))
+    with pytest.raises(lib.MiugksError):
+        lib.Solver(wl.cavity(n=16, nvel=10, kn=0.5, lid=0.2, levels=2)).copy_state(m)
