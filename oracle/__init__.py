@@ -105,6 +105,7 @@ def _declare(L):
         L.oracle_set_cycle.argtypes = [vp, i]
         L.oracle_adapt_log.argtypes = [vp, vp, i]
         L.oracle_set_adapt_ratio.argtypes = [vp, d]
+        L.oracle_set_shock_capturing.argtypes = [vp, i]
         L.oracle_init_from_coarse.argtypes = [vp, vp]
     return L
 
@@ -169,6 +170,9 @@ class Oracle:
     def set_cycle(self, cycle):
         """Multigrid cycle type of both cycles: "V", "W", "F" or "A" (adaptive)."""
         self._check(self._L.oracle_set_cycle(self.h, {"V": 0, "W": 1, "F": 2, "A": 3}[cycle]))
+
+    def set_shock_capturing(self, on):
+        self._check(self._L.oracle_set_shock_capturing(self.h, 1 if on else 0))
 
     def set_adapt_ratio(self, ratio):
         self._check(self._L.oracle_set_adapt_ratio(self.h, ratio))

@@ -101,6 +101,7 @@ struct oracle_solver {
     double *Cw; /* per BC: unit-density Maxwellian at the BC state, G part */
     int nu1, nu2, nuc;
     int cycle; /* 0 V, 1 W, 2 F, 3 adaptive (Sec. 3.4: V, W, F and adaptive cycles) */
+    int shock; /* pressure-jump collision time at interior faces (0 off) */
     double adapt_ratio;                   /* ADAPT_RATIO unless set */
     int adapt_n;                          /* adaptive-cycle decisions taken so far */
     unsigned char adapt_log[ADAPT_LOG];   /* each: 1 = a second coarse visit (ring of ADAPT_LOG) */
@@ -441,6 +442,16 @@ static void interior_face(oracle_solver *s, int axis, int cLL, int cL, int cR, i
     double dt = face_dt(s, axis, wL, wR);
     /* equilibrium slopes on either side from the cell averages */
     const double *WL = s->W + 4 * cL, *WR = s->W + 4 * cR;
+    if (s->shock) {
+        /* shock capturing (off by default; the paper is silent, reading): the
+         * interface collision time gains the pressure-jump term of the gas-kinetic
+         * schemes, dt |p_L - p_R| / (p_L + p_R), p = rho / (2 lambda) of the cells */
+        double rl, ul, vl, ll, rr, ur, vr, lr;
+        prim(WL, &rl, &ul, &vl, &ll);
+        prim(WR, &rr, &ur, &vr, &lr);
+        double pl = rl / (2.0 * ll), pr = rr / (2.0 * lr);
+        tau0 += dt * fabs(pl - pr) / (pl + pr);
+    }
     double dwl[4], dwr[4], aL[4], aR[4];
     for (int m = 0; m < 4; ++m) {
         dwl[m] = (W0[m] - WL[m]) / hL / rho0;
@@ -2233,7 +2244,7 @@ static void collision_adj(const oracle_solver *s, int c, const double *mu, doubl
 int oracle_steady_residual(oracle_solver *s, double *N)
 {
     olev_t *L0 = &s->lev[0];
-    if (L0->nfluid != L0->nc) return fail("adjoint: meshes with solid cells are not supported");
+    if (s->shock) return fail("adjoint: the pressure-jump collision time is not differentiated");
     int nx = L0->nx, ny = L0->ny, nv = s->nv;
     size_t nc = L0->nc;
     moments(s);
@@ -2241,6 +2252,12 @@ int oracle_steady_residual(oracle_solver *s, double *N)
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
             int c = j * nx + i;
+            if (L0->solid[c]) {
+                /* a cell in a body holds no state: N = -f keeps the Jacobian regular there */
+                for (int cp = 0; cp < 2; ++cp)
+                    for (int k = 0; k < nv; ++k) OUTA(N, cp, c, k) = -FIX(s, cp, c, k);
+                continue;
+            }
             double rho, U, V, lam;
             prim(s->W + 4 * c, &rho, &U, &V, &lam);
             double itau = 1.0 / tau_of(s, rho, lam);
@@ -2265,7 +2282,7 @@ int oracle_steady_residual(oracle_solver *s, double *N)
 int oracle_adjoint_residual(oracle_solver *s, const double *mu, double *out)
 {
     olev_t *L0 = &s->lev[0];
-    if (L0->nfluid != L0->nc) return fail("adjoint: meshes with solid cells are not supported");
+    if (s->shock) return fail("adjoint: the pressure-jump collision time is not differentiated");
     int nx = L0->nx, ny = L0->ny, nv = s->nv;
     size_t nc = L0->nc;
     moments(s);
@@ -2275,15 +2292,18 @@ int oracle_adjoint_residual(oracle_solver *s, const double *mu, double *out)
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i <= nx; ++i) {
             int fi = j * (nx + 1) + i, bcid = L0->fbx[fi];
-            int cL = i > 0 ? j * nx + i - 1 : -1, cR = i < nx ? j * nx + i : -1;
+            int cL = i > 0 && !L0->solid[j * nx + i - 1] ? j * nx + i - 1 : -1;
+            int cR = i < nx && !L0->solid[j * nx + i] ? j * nx + i : -1;
+            if (bcid < 0 && (cL < 0 || cR < 0)) continue;        /* inside a body: no flux */
             for (int k = 0; k < nv; ++k) {
                 nuG[k] = nuH[k] = 0.0;
                 if (cL >= 0) { nuG[k] -= OUTA(mu, 0, cL, k) / L0->dx[i - 1]; nuH[k] -= OUTA(mu, 1, cL, k) / L0->dx[i - 1]; }
                 if (cR >= 0) { nuG[k] += OUTA(mu, 0, cR, k) / L0->dx[i]; nuH[k] += OUTA(mu, 1, cR, k) / L0->dx[i]; }
             }
             if (bcid >= 0) {
-                if (i == 0) boundary_face_adj(s, bcid, 0, -1, cR, nuG, nuH, out);
-                else boundary_face_adj(s, bcid, 0, +1, cL, nuG, nuH, out);
+                int c, os;
+                face_side(L0, 0, i, j, &c, &os);
+                boundary_face_adj(s, bcid, 0, os, c, nuG, nuH, out);
                 continue;
             }
             int hasLL = (i - 1 > 0) && L0->fbx[fi - 1] < 0;
@@ -2297,15 +2317,18 @@ int oracle_adjoint_residual(oracle_solver *s, const double *mu, double *out)
     for (int j = 0; j <= ny; ++j)
         for (int i = 0; i < nx; ++i) {
             int fi = j * nx + i, bcid = L0->fby[fi];
-            int cL = j > 0 ? (j - 1) * nx + i : -1, cR = j < ny ? j * nx + i : -1;
+            int cL = j > 0 && !L0->solid[(j - 1) * nx + i] ? (j - 1) * nx + i : -1;
+            int cR = j < ny && !L0->solid[j * nx + i] ? j * nx + i : -1;
+            if (bcid < 0 && (cL < 0 || cR < 0)) continue;        /* inside a body: no flux */
             for (int k = 0; k < nv; ++k) {
                 nuG[k] = nuH[k] = 0.0;
                 if (cL >= 0) { nuG[k] -= OUTA(mu, 0, cL, k) / L0->dy[j - 1]; nuH[k] -= OUTA(mu, 1, cL, k) / L0->dy[j - 1]; }
                 if (cR >= 0) { nuG[k] += OUTA(mu, 0, cR, k) / L0->dy[j]; nuH[k] += OUTA(mu, 1, cR, k) / L0->dy[j]; }
             }
             if (bcid >= 0) {
-                if (j == 0) boundary_face_adj(s, bcid, 1, -1, cR, nuG, nuH, out);
-                else boundary_face_adj(s, bcid, 1, +1, cL, nuG, nuH, out);
+                int c, os;
+                face_side(L0, 1, i, j, &c, &os);
+                boundary_face_adj(s, bcid, 1, os, c, nuG, nuH, out);
                 continue;
             }
             int hasLL = (j - 1 > 0) && L0->fby[fi - nx] < 0;
@@ -2316,7 +2339,14 @@ int oracle_adjoint_residual(oracle_solver *s, const double *mu, double *out)
                               L0->yn[j] - L0->yc[j - 1], L0->yc[j] - L0->yn[j],
                               L0->dy[j - 1], L0->dy[j], nuG, nuH, out);
         }
-    for (size_t c = 0; c < nc; ++c) collision_adj(s, (int)c, mu, out);
+    for (size_t c = 0; c < nc; ++c) {
+        if (L0->solid[c]) {                                   /* N = -f in a body */
+            for (int cp = 0; cp < 2; ++cp)
+                for (int k = 0; k < nv; ++k) OUTA(out, cp, c, k) -= OUTA(mu, cp, c, k);
+            continue;
+        }
+        collision_adj(s, (int)c, mu, out);
+    }
     free(nuG); free(nuH);
     return 0;
 }
@@ -2328,7 +2358,7 @@ int oracle_adjoint_residual(oracle_solver *s, const double *mu, double *out)
 int oracle_objective(oracle_solver *s, int obj, int bc, double *J, double *dJdf, double *dJdth)
 {
     const olev_t *L0 = &s->lev[0];
-    if (L0->nfluid != L0->nc) return fail("adjoint: meshes with solid cells are not supported");
+    if (s->shock) return fail("adjoint: the pressure-jump collision time is not differentiated");
     int nx = L0->nx, ny = L0->ny, nv = s->nv;
     size_t nc = L0->nc;
     if (bc < 0 || bc >= s->nbc || s->bc[bc].type != ORC_BC_WALL) return fail("objective: BC %d is not a wall", bc);
@@ -2345,10 +2375,10 @@ int oracle_objective(oracle_solver *s, int obj, int bc, double *J, double *dJdf,
             double S;
             if (axis == 0) {
                 int i = fi % (nx + 1), j = fi / (nx + 1);
-                outsign = i == 0 ? -1 : 1; c = j * nx + (i == 0 ? 0 : nx - 1); S = L0->dy[j];
+                face_side(L0, 0, i, j, &c, &outsign); S = L0->dy[j];
             } else {
                 int i = fi % nx, j = fi / nx;
-                outsign = j == 0 ? -1 : 1; c = (j == 0 ? 0 : ny - 1) * nx + i; S = L0->dx[i];
+                face_side(L0, 1, i, j, &c, &outsign); S = L0->dx[i];
             }
             double Uwt = axis == 0 ? B->v : B->u;
             /* weights of the face distribution in Q: Q = sum_k w uo (aG fG + aH fH) */
@@ -2416,7 +2446,7 @@ int oracle_objective(oracle_solver *s, int obj, int bc, double *J, double *dJdf,
 int oracle_residual_dtheta(oracle_solver *s, int bc, int param, double *dN)
 {
     const olev_t *L0 = &s->lev[0];
-    if (L0->nfluid != L0->nc) return fail("adjoint: meshes with solid cells are not supported");
+    if (s->shock) return fail("adjoint: the pressure-jump collision time is not differentiated");
     int nx = L0->nx, ny = L0->ny, nv = s->nv;
     size_t nc = L0->nc;
     if (bc < 0 || bc >= s->nbc || s->bc[bc].type != ORC_BC_WALL) return fail("dtheta: BC %d is not a wall", bc);
@@ -2433,10 +2463,10 @@ int oracle_residual_dtheta(oracle_solver *s, int bc, int param, double *dN)
             double h;
             if (axis == 0) {
                 int i = fi % (nx + 1), j = fi / (nx + 1);
-                outsign = i == 0 ? -1 : 1; c = j * nx + (i == 0 ? 0 : nx - 1); h = L0->dx[i == 0 ? 0 : nx - 1];
+                face_side(L0, 0, i, j, &c, &outsign); h = L0->dx[c % nx];
             } else {
                 int i = fi % nx, j = fi / nx;
-                outsign = j == 0 ? -1 : 1; c = (j == 0 ? 0 : ny - 1) * nx + i; h = L0->dy[j == 0 ? 0 : ny - 1];
+                face_side(L0, 1, i, j, &c, &outsign); h = L0->dy[c / nx];
             }
             /* N_c += outsign * (-1/h) * Phi_face: the face is the cell's upper face when outsign = +1 */
             double coef = -outsign / h;
@@ -2498,6 +2528,12 @@ int oracle_adapt_log(const oracle_solver *s, unsigned char *out, int cap)
     if (m > ADAPT_LOG) m = ADAPT_LOG;
     for (int q = 0; q < m; ++q) out[q] = s->adapt_log[(n - m + q) % ADAPT_LOG];
     return n;
+}
+
+int oracle_set_shock_capturing(oracle_solver *s, int on)
+{
+    s->shock = on != 0;
+    return 0;
 }
 
 int oracle_set_adapt_ratio(oracle_solver *s, double ratio)

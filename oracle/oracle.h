@@ -58,6 +58,8 @@ int oracle_init_from_coarse(oracle_solver *s, const oracle_solver *coarse);
 int oracle_set_cycle(oracle_solver *s, int type);
 int oracle_adapt_log(const oracle_solver *s, unsigned char *out, int cap);
 int oracle_set_adapt_ratio(oracle_solver *s, double ratio);
+/* pressure-jump term of the interface collision time (shock capturing), 0 off (default) */
+int oracle_set_shock_capturing(oracle_solver *s, int on);
 int oracle_get_macro(const oracle_solver *s, double *rho, double *u, double *v,
                      double *t, double *qx, double *qy);
 int oracle_get_f(const oracle_solver *s, double *f);

@@ -266,3 +266,41 @@ def test_shakhov_reduces_to_maxwellian():
         G, H = oracle.shakhov(rho, U, V, lam, qx, qy, pr, u, v)
         assert np.allclose(G, GM, rtol=1e-14, atol=0)
         assert np.allclose(H, GM / (4.0 * lam), rtol=1e-14, atol=0)
+
+
+# ---------------------------------------------------------------- shock capturing (off by default)
+def test_pressure_jump_collision_time_only_acts_on_pressure_jumps():
+    """The pressure-jump term dt |p_L - p_R| / (p_L + p_R) of the interface
+    collision time (the paper is silent; the gas-kinetic schemes' shock
+    capturing) vanishes where the two cells have the same pressure: with
+    density and temperature uniform and the velocity varying, every face flux
+    is the same with the option on (to the rounding of the cell pressures);
+    with a pressure jump the faces across it change and the others do not."""
+    # 40 nodes on [-6, 6]: the discrete moments of each cell's Maxwellian are its (rho, U, V, T) to
+    # round-off, so cells of equal density and temperature have equal pressure
+    case = wl.cavity(n=8, nvel=40, vmax=6.0, kn=0.01, lid=0.2, levels=1)
+    nx = ny = 8
+    rng = np.random.default_rng(5)
+    rho, t = np.full(nx * ny, 1.2), np.full(nx * ny, 0.9)
+    u, v = 0.1 * rng.uniform(-1, 1, nx * ny), 0.1 * rng.uniform(-1, 1, nx * ny)
+    out = {}
+    for on in (False, True):
+        o = oracle.Oracle(case)
+        o.set_shock_capturing(on)
+        o.init_fields(rho, u, v, t)
+        out[on] = o.stage_flux()
+    for a, b in zip(out[False], out[True]):           # pressures equal up to the rounding of W
+        assert np.allclose(a, b, rtol=1e-12, atol=1e-14 * np.abs(a).max())
+    # a pressure jump across the x-faces between columns 3 and 4
+    rho2 = rho.reshape(ny, nx).copy()
+    rho2[:, 4:] *= 1.5
+    for on in (False, True):
+        o = oracle.Oracle(case)
+        o.set_shock_capturing(on)
+        o.init_fields(rho2.ravel(), u, v, t)
+        out[on] = o.stage_flux()
+    px0, px1 = out[False][1], out[True][1]          # [2][nfx][nv], x-face index j * (nx + 1) + i
+    d = (np.abs(px1 - px0).max(axis=(0, 2)) / np.abs(px0).max()).reshape(ny, nx + 1)
+    assert np.all(d[:, 4] > 1e-4) and np.all(np.delete(d, 4, axis=1) < 1e-12), d
+    with pytest.raises(RuntimeError):
+        o.steady_residual()
