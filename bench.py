@@ -404,10 +404,10 @@ def measure_plate(steps, warmup):
 # inverse diagonal forward; the forward result and the inverse diagonal
 # backward) and two written (the new G and H): 20 B in FP32, 40 B in FP64.
 SWEEP_VALUES_PER_CV = 5
-# DRAM bytes of one finest-level launch of each flat-plate sweep kernel (mixed,
-# forward direction) per cell-velocity pair it sweeps, from the ncu captures
-# summarised in profiles/k_sgs_plate128x96_v48_mixed.md (None until captured)
-SWEEP_TRAFFIC_PER_CV = {"lines": None, "wave": None}
+# DRAM bytes per cell-velocity pair of the flat plate's finest-level sweep
+# kernels (mixed), from the ncu captures summarised in
+# profiles/k_sgs_plate128x96_v48_mixed.md (forward and backward launches)
+SWEEP_TRAFFIC_PER_CV = {"lines": 30.2, "wave": 29.8}
 FLUX_TRAFFIC_PLATE_MIXED = None
 
 
@@ -573,6 +573,46 @@ def square_mixed_error(conv):
             "wall_heat_flux": float(np.abs(q32 - q64).max() / np.abs(q64).max())}
 
 
+def run_square_adjoint(args):
+    """--workload square_adjoint: the square cylinder at full size solved to RMS
+    1e-8 (mixed form to its floor, then FP64: refine.run), then the FP64
+    adjoint gradient of the heat flux into the square (the sum over its wall
+    faces of face length x heat flux, BC 0) with respect to its wall
+    temperature: flexible GMRES(--restart) to --adj-tol, preconditioned by the
+    transposed multigrid cycle (approximate at the body's faces).  With --fd,
+    also central differences of two more converged solves (T_w = 1 +- 5e-3)."""
+    import torch
+    from paper_1704_03151_gb300 import build, miugks, refine, workloads
+    build.build()
+    c = workloads.square_cylinder()
+    s, fwd = refine.run(c, tol=1e-8, max_iter=args.max_iter)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g, info = s.adjoint(1, 0, 0, tol=args.adj_tol, max_iter=600, restart=args.restart)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    J = info["J"]
+    s.close()
+    fd = None
+    if args.fd:
+        h = 5e-3
+        Js = []
+        for sg in (1, -1):
+            cc = workloads.square_cylinder()
+            cc["bcs"][0]["t"] = 1.0 + sg * h
+            sp, _ = refine.run(cc, tol=1e-8, max_iter=args.max_iter)
+            Js.append(sp.objective(1, 0)[0])
+            sp.close()
+        fd = (Js[0] - Js[1]) / (2 * h)
+    print(json.dumps({"metric": "square-cylinder heat-flux gradient w.r.t. wall temperature (adjoint)", "unit": "s",
+                      "value": secs, "higher_is_better": False,
+                      "config": {"workload": "square_cylinder_160x120_v89x89_ma5_kn0.1_4level", "restart": args.restart},
+                      "forward": fwd, "heat_flux": J, "gradient": g, "gmres_iterations": info["iterations"],
+                      "relative_residual": info["residual"], "converged": info["converged"],
+                      "central_difference": fd}))
+    return 0
+
+
 def run_plate_iter(args):
     """--workload plate_iter: --steps outer iterations of the full-size flat
     plate (mixed form) from its initial state, eagerly launched after the
@@ -638,8 +678,12 @@ def main():
     ap.add_argument("--no-plate", action="store_true", help="skip the full-size flat-plate throughput line")
     ap.add_argument("--no-square", action="store_true", help="skip the full-size square-cylinder throughput line")
     ap.add_argument("--workload", default="cavity64",
-                    choices=["cavity64", "kn_sweep", "adjoint", "cycles", "plate_adjoint", "square", "plate_iter"])
+                    choices=["cavity64", "kn_sweep", "adjoint", "cycles", "plate_adjoint", "square", "plate_iter",
+                             "square_adjoint"])
     ap.add_argument("--count", type=int, default=32, help="cavities of the Kn sweep")
+    ap.add_argument("--restart", type=int, default=20, help="GMRES restart length of --workload square_adjoint")
+    ap.add_argument("--adj-tol", type=float, default=1e-6, help="adjoint GMRES tolerance of --workload square_adjoint")
+    ap.add_argument("--fd", action="store_true", help="square_adjoint: also central differences of converged solves")
     ap.add_argument("--max-iter", type=int, default=1500)
     ap.add_argument("--adjoint", action="store_true", help="Kn sweep: adjoint lid-shear gradient of every case")
     ap.add_argument("--dtn-growth", type=float, default=None,
@@ -657,6 +701,8 @@ def main():
         return run_plate_adjoint(args)
     if args.workload == "plate_iter":
         return run_plate_iter(args)
+    if args.workload == "square_adjoint":
+        return run_square_adjoint(args)
     if args.workload == "square":
         return run_square(args)
     args.warmup = max(args.warmup, 3)

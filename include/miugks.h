@@ -180,6 +180,25 @@ miugks_status miugks_set_adaptive_ratio(miugks_solver *s, double ratio);
  * velocity in the wavefront kernel, 0 (default) splits a level from 20 Mi
  * cell-velocity pairs on.  MIUGKS_EINVAL for another mode. */
 miugks_status miugks_set_sweep_split(miugks_solver *s, int mode);
+/* Shock capturing (off by default; the paper describes none, and runs its
+ * Ma 5 case without): on != 0 adds the pressure-jump term of the gas-kinetic
+ * schemes, dt_p |p_L - p_R| / (p_L + p_R) with p = rho / (2 lambda) of the two
+ * cells, to the collision time of every interior interface in Step 1's flux
+ * (Sec. 2.1), which adds numerical dissipation where the pressure jumps and
+ * nothing where it is continuous.  The adjoint (which does not differentiate
+ * this term) returns MIUGKS_EINVAL while it is on. */
+miugks_status miugks_set_shock_capturing(miugks_solver *s, int on);
+/* Bound of the prediction smoother's device waits (the cluster sweep of Eq.
+ * macroFinalDefect waits for each diagonal's inputs and its neighbours'
+ * values): a wait that has not completed after `seconds` (default 0.2, at
+ * most 10) gives up, the kernel drains its copies in flight (waits bounded by
+ * the default) and returns, and the next miugks_step / miugks_wait returns
+ * MIUGKS_ETIMEOUT (sticky for the solver).  0 makes every such wait give up
+ * without testing its inputs: it exercises the failure path without a fault
+ * (the kernel computes one step on whatever the buffers hold, then drains and
+ * returns; the state is garbage and the solver is to be destroyed), and the
+ * CUDA context stays usable.  MIUGKS_EINVAL outside [0, 10]. */
+miugks_status miugks_set_wait_limit(miugks_solver *s, double seconds);
 int miugks_adaptive_decisions(const miugks_solver *s, unsigned char *out, int cap);
 /* Full-multigrid start-up (Sec. 3.5): the state of `coarse`, a solver of the
  * same problem on the next coarser mesh (every second grid line of s's mesh,
@@ -229,6 +248,10 @@ miugks_status miugks_stage_prolong(miugks_solver *s, int lev, int m, const doubl
  * wall BC: obj 0 = sum over its faces of face length x shear stress, 1 = heat
  * flux, 2 = pressure (the quantities of miugks_get_wall).  All in FP64 on an
  * FP64 copy (checkpoint) of the current f, whatever the solver's precision.
+ * On a mesh with bodies a body's faces are wall faces of the fluid cells beside
+ * them and a cell in a body holds no state (N = -f there); the transposed-cycle
+ * preconditioner keeps the ghost couplings of the domain edge only (it is an
+ * approximation at a body's faces, which the Krylov solve corrects).
  *
  *  stage_adjoint_residual: out = (dN/df)^T mu at the current f, host arrays
  *        of 2 x nc x nv ([comp][cell][k]).

@@ -262,9 +262,9 @@ __global__ void __launch_bounds__(256) k_adj_face(AdjDev A, int axis, const doub
         const BcDev B = A.bc[bcid];
         if (tid < kFaceRec) out[tid] = 0.0;
         if (B.type != BC_WALL) return;
-        const int outsign = (axis == 0 ? i == 0 : j == 0) ? -1 : 1;
-        const int c = axis == 0 ? j * nx + (i == 0 ? 0 : nx - 1) : (j == 0 ? 0 : ny - 1) * nx + i;
-        const double d = axis == 0 ? L.dx[i == 0 ? 0 : nx - 1] : L.dy[j == 0 ? 0 : ny - 1];
+        int outsign, c;                          // the face's fluid cell (domain edge or body face)
+        bface_side(L, axis, i, j, c, outsign);
+        const double d = axis == 0 ? L.dx[c % nx] : L.dy[c / nx];
         const double coef = (outsign < 0 ? 1.0 : -1.0) / d;     // nu = coef * mu_c
         const double* Cb = A.Cw + (size_t)bcid * nv;
         const double hf = kKint * B.t / 4.0;
@@ -282,6 +282,10 @@ __global__ void __launch_bounds__(256) k_adj_face(AdjDev A, int axis, const doub
         return;
     }
 
+    if (inactive_face(L, axis, i, j)) {          // inside a body: no flux, an empty record
+        if (tid < kFaceRec) out[tid] = 0.0;
+        return;
+    }
     const FaceGeo g = face_geo(L, axis, fi);
     const double nuL = -1.0 / g.wL, nuR = 1.0 / g.wR;      // nu = nuL mu_L + nuR mu_R
     // upwinded reconstructed values and slopes of velocity k (both components)
@@ -663,6 +667,11 @@ __global__ void __launch_bounds__(128) k_adj_gather(AdjDev A, const double* __re
     if (k >= nv) return;
     const int nx = L.nx, ny = L.ny, i = c % nx, j = c / nx;
     const size_t nc = L.nc, snv = nv;
+    if (L.solid[c]) {                              // N = -f in a body
+        out[c * snv + k] = -mu[c * snv + k];
+        out[(nc + c) * snv + k] = -mu[(nc + c) * snv + k];
+        return;
+    }
     double acc[2] = {0.0, 0.0};
     // collision term of the cell itself
     {
@@ -677,20 +686,28 @@ __global__ void __launch_bounds__(128) k_adj_gather(AdjDev A, const double* __re
         if (ii < 0 || ii > nx) continue;
         const int fi = j * (nx + 1) + ii;
         if (L.fbx[fi] >= 0) {
-            if (ii == i && ii == 0) boundary_contrib(A, mu, recx, 0, fi, c, -1, L.dx[0], k, acc);
-            else if (ii == i + 1 && ii == nx) boundary_contrib(A, mu, recx, 0, fi, c, +1, L.dx[nx - 1], k, acc);
+            if (ii == i || ii == i + 1) {              // a boundary face of this cell (domain edge or body)
+                int cc, os;
+                bface_side(L, 0, ii, j, cc, os);
+                if (cc == c) boundary_contrib(A, mu, recx, 0, fi, c, os, L.dx[i], k, acc);
+            }
             continue;
         }
+        if (inactive_face(L, 0, ii, j)) continue;
         face_contrib(A, mu, recx, 0, fi, ii - i + 1 == 0 ? 3 : ii - i + 1 == 1 ? 2 : ii - i + 1 == 2 ? 1 : 0, k, acc);
     }
     for (int jj = j - 1; jj <= j + 2; ++jj) {
         if (jj < 0 || jj > ny) continue;
         const int fi = jj * nx + i;
         if (L.fby[fi] >= 0) {
-            if (jj == j && jj == 0) boundary_contrib(A, mu, recy, 1, fi, c, -1, L.dy[0], k, acc);
-            else if (jj == j + 1 && jj == ny) boundary_contrib(A, mu, recy, 1, fi, c, +1, L.dy[ny - 1], k, acc);
+            if (jj == j || jj == j + 1) {
+                int cc, os;
+                bface_side(L, 1, i, jj, cc, os);
+                if (cc == c) boundary_contrib(A, mu, recy, 1, fi, c, os, L.dy[j], k, acc);
+            }
             continue;
         }
+        if (inactive_face(L, 1, i, jj)) continue;
         face_contrib(A, mu, recy, 1, fi, jj - j + 1 == 0 ? 3 : jj - j + 1 == 1 ? 2 : jj - j + 1 == 2 ? 1 : 0, k, acc);
     }
     if (pen != 0.0) acc[0] += pen * L.dx[i] * L.dy[j] * Vg.w[k];
@@ -1097,10 +1114,10 @@ __global__ void __launch_bounds__(256) k_adj_objective(AdjDev A, int obj, int bc
     double S;
     if (axis == 0) {
         int i = fi % (nx + 1), j = fi / (nx + 1);
-        outsign = i == 0 ? -1 : 1; c = j * nx + (i == 0 ? 0 : nx - 1); S = L.dy[j];
+        bface_side(L, 0, i, j, c, outsign); S = L.dy[j];
     } else {
         int i = fi % nx, j = fi / nx;
-        outsign = j == 0 ? -1 : 1; c = (j == 0 ? 0 : ny - 1) * nx + i; S = L.dx[i];
+        bface_side(L, 1, i, j, c, outsign); S = L.dx[i];
     }
     const BcDev B = A.bc[bcid];
     const double T = B.t, lam = 1.0 / T, hf = kKint * T / 4.0, Uwt = axis == 0 ? B.v : B.u;
@@ -1175,10 +1192,10 @@ __global__ void __launch_bounds__(256) k_adj_dtheta(AdjDev A, int bcid, const in
     double h;
     if (axis == 0) {
         int i = fi % (nx + 1), j = fi / (nx + 1);
-        outsign = i == 0 ? -1 : 1; c = j * nx + (i == 0 ? 0 : nx - 1); h = L.dx[i == 0 ? 0 : nx - 1];
+        bface_side(L, 0, i, j, c, outsign); h = L.dx[c % nx];
     } else {
         int i = fi % nx, j = fi / nx;
-        outsign = j == 0 ? -1 : 1; c = (j == 0 ? 0 : ny - 1) * nx + i; h = L.dy[j == 0 ? 0 : ny - 1];
+        bface_side(L, 1, i, j, c, outsign); h = L.dy[c / nx];
     }
     const BcDev B = A.bc[bcid];
     const double T = B.t, lam = 1.0 / T, coef = -outsign / h;
@@ -1267,6 +1284,10 @@ __global__ void __launch_bounds__(256) k_adj_macro_m(AdjDev A, const double* __r
     const VelDev& Vg = A.V;
     const int nv = Vg.nv, tid = threadIdx.x, bs = blockDim.x, c = blockIdx.x;
     const size_t nc = A.L.nc, snv = nv;
+    if (A.L.solid[c]) {                          // no equation in a body
+        if (tid < 4) m[4 * (size_t)c + tid] = 0.0;
+        return;
+    }
     const double* fG = A.f + c * snv;
     const double* fH = A.f + (nc + c) * snv;
     const double* yG = y + c * snv;
@@ -1356,6 +1377,21 @@ __global__ void k_block_apply(int nc, const double* __restrict__ binv, const dou
     const double* B = binv + 16 * (size_t)c;
     const double* x = r + 4 * (size_t)c;
     for (int a = 0; a < 4; ++a) z[4 * (size_t)c + a] = B[a * 4] * x[0] + B[a * 4 + 1] * x[1] + B[a * 4 + 2] * x[2] + B[a * 4 + 3] * x[3];
+}
+
+// x = 0 in the cells of bodies (2 x nc x nv values)
+__global__ void k_zero_solid(LevelDev L, int nv, double* __restrict__ x)
+{
+    const size_t n = 2 * (size_t)L.nc * nv;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t c = (e / nv) % L.nc;
+        if (L.solid[c]) x[e] = 0.0;
+    }
+}
+cudaError_t launch_zero_solid(const LevelDev& L, int nv, double* x, cudaStream_t st)
+{
+    k_zero_solid<<<1216, 256, 0, st>>>(L, nv, x);
+    return cudaGetLastError();
 }
 
 template <typename F>

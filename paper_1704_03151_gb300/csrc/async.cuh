@@ -45,14 +45,19 @@ __device__ __forceinline__ uint64_t global_ns()
 constexpr uint64_t kWaitNs = 200000000ull;   // a wait gives up after 0.2 s ...
 constexpr int kWaitRounds = 1 << 26;         // ... or this many try_wait rounds
 
-// wait for the phase with the given parity to complete; false when the bound is reached
-__device__ __forceinline__ bool mbar_wait(uint64_t* mb, unsigned parity)
+// wait for the phase with the given parity to complete; false when the bound
+// (limit_ns of global time, or kWaitRounds rounds) is reached.  limit 0 gives
+// up without testing the phase at all: it drives the caller's timeout path on
+// purpose (the inputs of a sweep step are normally complete at the first test,
+// so a short bound alone would not reach that path).
+__device__ __forceinline__ bool mbar_wait(uint64_t* mb, unsigned parity, uint64_t limit_ns = kWaitNs)
 {
+    if (limit_ns == 0) return false;
     if (mbar_try_wait(mb, parity)) return true;
     const uint64_t t0 = global_ns();
     for (int it = 0; it < kWaitRounds; ++it) {
         if (mbar_try_wait(mb, parity)) return true;
-        if (global_ns() - t0 > kWaitNs) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     }
     return false;
 }

@@ -160,7 +160,7 @@ __device__ __forceinline__ void slope_mom(const F* a, F u, F v, F gM, F hM, F xi
 // rank order through distributed shared memory.  Boundary faces and faces
 // inside a body are done by rank 0 alone.
 template <typename F, bool CACHE>
-__global__ void __launch_bounds__(256) k_face_flux(FaceFluxArgs<F> A)
+__global__ void __launch_bounds__(256, sizeof(F) == 4 ? 4 : 2) k_face_flux(FaceFluxArgs<F> A)
 {
     extern __shared__ double sm[];
     cg::cluster_group cl = cg::this_cluster();
@@ -330,6 +330,13 @@ __global__ void __launch_bounds__(256) k_face_flux(FaceFluxArgs<F> A)
             if constexpr (sizeof(F) == 8) par[4] = tau_of(A.gas, rho, lam);
             else par[4] = (double)tau_of_f(A.gas, (float)rho, (float)lam);
             par[5] = A.cfl * fmin(par[28], par[29]) / (axis == 0 ? Vg.umax : Vg.vmax);
+            if (A.shock) {
+                double rl, ul, vl, ll, rr, ur, vr, lr;
+                prim4(A.W + 4 * (size_t)cL, rl, ul, vl, ll);
+                prim4(A.W + 4 * (size_t)cR, rr, ur, vr, lr);
+                const double pl = rl / (2.0 * ll), pr = rr / (2.0 * lr);
+                par[4] += par[5] * fabs(pl - pr) / (pl + pr);
+            }
         } else {
             const double* Wc = A.W + 4 * (size_t)(tid == 1 ? cL : cR);
             double hf = (tid == 1 ? 1.0 : -1.0) * ir * rcp64(tid == 1 ? par[26] : par[27]), dw[4];
@@ -373,10 +380,13 @@ __global__ void __launch_bounds__(256) k_face_flux(FaceFluxArgs<F> A)
     #pragma unroll
     for (int m = 0; m < 4; ++m) { aL[m] = pf[8 + m]; aR[m] = pf[12 + m]; }
 
+    // velocity k = a * nvv + b of this thread, stepped by the block size without a division
+    const int ka0 = (kb + tid) / Vg.nvv, kb0 = kb + tid - ka0 * Vg.nvv;
+    const int sa = bs / Vg.nvv, sb = bs - sa * Vg.nvv;
     // pass 2: heat flux of the interface distribution, compatibility moments for A
     Acc<F> s6a[6];
-    for (int k = kb + tid; k < ke; k += bs) {
-        int a = k / Vg.nvv, b = k - a * Vg.nvv;
+    for (int k = kb + tid, a = ka0, b = kb0; k < ke; k += bs, a += sa, b += sb) {
+        if (b >= Vg.nvv) { b -= Vg.nvv; ++a; }
         const F u = vu[k], v = vv[k], w = vw[k];
         F cx = u - fU0, cy = v - fV0, c2 = cx * cx + cy * cy;
         F f0[2], sg[2];
@@ -436,8 +446,8 @@ __global__ void __launch_bounds__(256) k_face_flux(FaceFluxArgs<F> A)
 
     // pass 3: time-averaged flux of every discrete velocity and its moments
     Acc<F> Fa[4];
-    for (int k = kb + tid; k < ke; k += bs) {
-        int a = k / Vg.nvv, b = k - a * Vg.nvv;
+    for (int k = kb + tid, a = ka0, b = kb0; k < ke; k += bs, a += sa, b += sb) {
+        if (b >= Vg.nvv) { b -= Vg.nvv; ++a; }
         const F u = vu[k], v = vv[k], w = vw[k];
         const F un = axis == 0 ? u : v;
         F cx = u - fU0, cy = v - fV0, c2 = cx * cx + cy * cy;

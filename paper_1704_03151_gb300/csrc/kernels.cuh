@@ -14,6 +14,7 @@ struct FaceFluxArgs {
     F* ph;                                 // [2][nf][nv] time-averaged micro flux, along +axis
     double* Fm;                            // [nf][4] macro flux
     int axis; double cfl;
+    int shock;                             // add the pressure-jump term to the interface collision time
 };
 
 void upload_series_coefficients();
@@ -26,6 +27,7 @@ struct MacroArgs {
     LevelDev L; GasDev gas; const BcDev* bc;
     double dtn_inv;                        // 1/dt_n (0 when off)
     double* flag;                          // set to 1 when a bounded device wait gave up
+    unsigned long long wait_ns;            // bound of the sweep's waits for its inputs (ns of global time)
 };
 // Gamma of every face from the frozen state Wg
 // (and the inverse diagonal of the smoother per cell)
@@ -185,6 +187,8 @@ cudaError_t launch_multi_axpy(const double* Vb, int m, size_t n, const double* h
 cudaError_t launch_mass_dot(const LevelDev& L, const VelDev& V, const double* x, double* part, cudaStream_t st);
 template <typename F> cudaError_t launch_to_double(const F* a, double* b, size_t n, cudaStream_t st);
 cudaError_t launch_to_float(const double* a, float* b, size_t n, cudaStream_t st);
+// zero the entries of cells in bodies of a 2 x nc x nv vector
+cudaError_t launch_zero_solid(const LevelDev& L, int nv, double* x, cudaStream_t st);
 cudaError_t launch_inv_tau(const GasDev& gas, const double* W, int nc, double* it, cudaStream_t st);
 cudaError_t launch_adjoint_invD(const LevelDev& L, const VelDev& V, const double* it, double* invD, cudaStream_t st);
 // m_c = (dr_c/dW~_c)^T y_c (micro residual w.r.t. the predicted state, heat flux held)

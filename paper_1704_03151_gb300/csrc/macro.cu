@@ -258,6 +258,13 @@ __global__ void k_macro_jacT(MacroArgs a, const double* __restrict__ W, const do
     const LevelDev& L = a.L;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= L.nc) return;
+    if (L.solid[c]) {             // a cell in a body has no equation: a zero row and a zero inverse block
+        if (x)
+            for (int q = 0; q < 4; ++q) y[4 * (size_t)c + q] = 0.0;
+        if (binv)
+            for (int q = 0; q < 16; ++q) binv[16 * (size_t)c + q] = 0.0;
+        return;
+    }
     const int nx = L.nx, i = c % nx, j = c / nx;
     const double* Wc = W + 4 * (size_t)c;
     const double Vc = L.dx[i] * L.dy[j];
@@ -597,7 +604,7 @@ k_macro_sgs(MacroArgs a, double* __restrict__ W, F* __restrict__ rec, double* __
             if (prod) {
                 if (issuer && dd + kMacroRing - 1 < nd) issue(issued = g + kMacroRing - 1);
             } else {
-                got = mbar_wait(&rb[g % kMacroRing], (g / kMacroRing) & 1);
+                got = mbar_wait(&rb[g % kMacroRing], (g / kMacroRing) & 1, a.wait_ns);
                 const int ilo = diag_lo(d, ny), ncell = diag_len(d, nx, ny);
                 const bool on = gs0 + ls < ncell;
                 F rc[kRec];                              // this lane's record
@@ -653,7 +660,7 @@ k_macro_sgs(MacroArgs a, double* __restrict__ W, F* __restrict__ rec, double* __
     if (active && issuer) {
         if (ok) {                                        // the halo of the last step
             issue(issued = nsteps);
-            if (!mbar_wait(&rb[nsteps % kMacroRing], (nsteps / kMacroRing) & 1)) ok = false;
+            if (!mbar_wait(&rb[nsteps % kMacroRing], (nsteps / kMacroRing) & 1, a.wait_ns)) ok = false;
         }
         if (!ok) {
             // after a timeout: the latest armed phase of every slot, so that no bulk copy

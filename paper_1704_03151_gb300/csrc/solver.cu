@@ -76,6 +76,8 @@ struct miugks_solver {
     std::vector<unsigned char> adapt_log = std::vector<unsigned char>(4096);
     double* nrm = nullptr;                      // device: 128 partial sums and the total
     int sweep_split = 0;                        // evolution sweep: 0 by size, 1 split by coupling class, 2 never
+    bool shock = false;                         // pressure-jump collision time at interior faces
+    unsigned long long wait_ns = 200000000ull;  // bound of the prediction sweep's device waits
     // timing mode: the finest level's wavefront and line-class sweep launches; totals since the last read
     SweepTimer sweep_timer;
     double t_sweepk[2] = {0, 0}, u_sweepk[2] = {0, 0};
@@ -437,7 +439,7 @@ miugks_status build_sweep_plan(miugks_solver* s, HLevel& Lv)
 
 MacroArgs macro_args(miugks_solver* s, int l, double dtn_inv)
 {
-    return MacroArgs{s->lev[l].dev, s->gas, s->bc, dtn_inv, s->rms_out + 5};
+    return MacroArgs{s->lev[l].dev, s->gas, s->bc, dtn_inv, s->rms_out + 5, s->wait_ns};
 }
 
 double dtn_inv(miugks_solver* s)
@@ -614,7 +616,8 @@ template <typename F>
 miugks_status flux_stage_t(miugks_solver* s)
 {
     HLevel& L0 = s->lev[0];
-    FaceFluxArgs<F> fa{L0.dev, s->vel, s->gas, s->bc, s->Cw, (const F*)s->f, s->W, (F*)s->phx, s->Fx, 0, s->opts.cfl};
+    FaceFluxArgs<F> fa{L0.dev, s->vel, s->gas, s->bc, s->Cw, (const F*)s->f, s->W, (F*)s->phx, s->Fx, 0, s->opts.cfl,
+                       s->shock ? 1 : 0};
     CK(launch_face_flux<F>(fa, s->st));
     fa.axis = 1; fa.ph = (F*)s->phy; fa.Fm = s->Fy;
     CK(launch_face_flux<F>(fa, s->st));
@@ -1295,6 +1298,35 @@ miugks_status miugks_set_sweep_split(miugks_solver* s, int mode)
     return MIUGKS_OK;
 }
 
+miugks_status miugks_set_wait_limit(miugks_solver* s, double seconds)
+{
+    if (!s) return MIUGKS_EINVAL;
+    if (!(seconds >= 0.0 && seconds <= 10.0)) return fail(s, MIUGKS_EINVAL, "wait limit %g s: 0 to 10", seconds);
+    s->wait_ns = (unsigned long long)(seconds * 1e9);   // a kernel argument: a captured iteration is re-captured
+    if (s->gexec) {
+        CK(cudaStreamSynchronize(s->st));
+        cudaGraphExecDestroy(s->gexec);
+        if (s->graph) cudaGraphDestroy(s->graph);
+        s->gexec = nullptr;
+        s->graph = nullptr;
+    }
+    return MIUGKS_OK;
+}
+
+miugks_status miugks_set_shock_capturing(miugks_solver* s, int on)
+{
+    if (!s) return MIUGKS_EINVAL;
+    s->shock = on != 0;            // a kernel argument: a captured iteration is re-captured
+    if (s->gexec) {
+        CK(cudaStreamSynchronize(s->st));
+        cudaGraphExecDestroy(s->gexec);
+        if (s->graph) cudaGraphDestroy(s->graph);
+        s->gexec = nullptr;
+        s->graph = nullptr;
+    }
+    return MIUGKS_OK;
+}
+
 miugks_status miugks_set_adaptive_ratio(miugks_solver* s, double ratio)
 {
     if (!s) return MIUGKS_EINVAL;
@@ -1552,7 +1584,7 @@ miugks_status refresh_invD(miugks_solver* s);
 miugks_status adj_prepare(miugks_solver* s, int m)
 {
     HLevel& L0 = s->lev[0];
-    if (L0.nfluid != L0.nc) return fail(s, MIUGKS_EINVAL, "adjoint: meshes with bodies (solid cells) are not supported");
+    if (s->shock) return fail(s, MIUGKS_EINVAL, "adjoint: the pressure-jump collision time is not differentiated");
     const size_t n = 2 * (size_t)L0.nc * s->nv;
     auto& A = s->adj;
     if (!A.alloc) {
@@ -1853,7 +1885,7 @@ miugks_status apply_B(miugks_solver* s, const double* v, double* out, double mm)
 // the residual), so P = M (I - (dr/dW~) J^{-1} Pi) and
 //   P^T z = y - Pi^T J^{-T} (dr/dW~)^T y,   y = M^T z.
 // The inner solve with J^T is inexact, so the outer Krylov method is flexible GMRES.
-miugks_status apply_PT(miugks_solver* s, const double* r, double* out)
+miugks_status apply_PT_cycle(miugks_solver* s, const double* r, double* out)
 {
     ST(cs_T(s, 0, r, out));
     if (!s->adj.macro) return MIUGKS_OK;
@@ -1873,6 +1905,17 @@ miugks_status apply_PT(miugks_solver* s, const double* r, double* out)
         CK(launch_macro_null_sub(L0.dev, wn / nn, w, s->st));
     }
     CK(launch_adjoint_macro_spread(L0.dev, s->vel, w, out, s->st));
+    return MIUGKS_OK;
+}
+
+// On a mesh with bodies the transposed cycle keeps the ghost couplings of the domain edge only (the
+// wall coupling at a body's faces is left out: the preconditioner is then an approximation, which
+// the Krylov solve corrects), and its values in the cells of bodies, which hold no state, are zeroed.
+miugks_status apply_PT(miugks_solver* s, const double* r, double* out)
+{
+    ST(apply_PT_cycle(s, r, out));
+    HLevel& L0 = s->lev[0];
+    if (L0.nfluid != L0.nc) CK(launch_zero_solid(L0.dev, s->nv, out, s->st));
     return MIUGKS_OK;
 }
 

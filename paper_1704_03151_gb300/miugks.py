@@ -95,7 +95,8 @@ def load():
         "miugks_set_adjoint_options": [vp, _i], "miugks_stage_macro_jacobian_transposed": [vp, vp, vp, vp],
         "miugks_set_adaptive_ratio": [vp, _d], "miugks_adaptive_decisions": [vp, vp, _i],
         "miugks_set_sweep_split": [vp, _i], "miugks_sweep_kernel_times": [vp, vp],
-        "miugks_copy_state": [vp, vp],
+        "miugks_copy_state": [vp, vp], "miugks_set_shock_capturing": [vp, _i],
+        "miugks_set_wait_limit": [vp, _d],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -122,7 +123,7 @@ def exported_symbols():
             "miugks_macro_sweep_times", "miugks_set_cycle", "miugks_init_from_coarse",
             "miugks_set_adjoint_options", "miugks_stage_macro_jacobian_transposed", "miugks_set_adaptive_ratio",
             "miugks_adaptive_decisions", "miugks_set_sweep_split", "miugks_sweep_kernel_times",
-            "miugks_copy_state"]
+            "miugks_copy_state", "miugks_set_shock_capturing", "miugks_set_wait_limit"]
 
 
 def _ptr(a):
@@ -280,6 +281,14 @@ class Solver:
     def set_cycle(self, cycle):
         """Multigrid cycle type of both cycles: "V", "W", "F" or "A" (adaptive)."""
         self._check(self._lib.miugks_set_cycle(self.h, {"V": 0, "W": 1, "F": 2, "A": 3}[cycle]))
+
+    def set_wait_limit(self, seconds):
+        """Bound of the prediction sweep's device waits (0.2 s by default)."""
+        self._check(self._lib.miugks_set_wait_limit(self.h, float(seconds)))
+
+    def set_shock_capturing(self, on):
+        """Pressure-jump term of the interface collision time (off by default)."""
+        self._check(self._lib.miugks_set_shock_capturing(self.h, 1 if on else 0))
 
     def set_sweep_split(self, mode):
         """Evolution-sweep layout: "auto" (by level size), "split" or "wave" (same results)."""

@@ -162,10 +162,6 @@ def test_body_layouts_the_sweeps_cannot_take_are_refused(lib):
     misaligned = box_with_bodies(12, 12, [(3, 6, 4, 8)], levels=2)
     with pytest.raises(lib.MiugksError, match="coarse"):
         lib.Solver(misaligned)
-    s = lib.Solver(CASES["single_grid"])
-    s.init_uniform(1.0, 0.0, 0.0, 1.0)
-    with pytest.raises(lib.MiugksError, match="bodies"):
-        s.adjoint(0, 2, 1, tol=1e-6, max_iter=2)
 
 
 def test_mixed_form_at_ma5_with_the_full_velocity_grid(lib):

@@ -57,3 +57,29 @@ def test_unphysical_state_reports_ediverged(lib, precision, kind, levels):
         t.step(3)
     assert np.array_equal(a.get_f(), b.get_f())
     s.close()
+
+
+def test_bounded_wait_gives_up_and_reports_etimeout(lib):
+    """The prediction smoother's cluster sweep waits (bounded) for each
+    diagonal's inputs and its neighbours' values.  With the bound at zero
+    every such wait gives up (the inputs are normally complete at the first
+    test, so only that setting reaches the path): the kernel drains its copies
+    in flight with bounded waits, returns, and the host reads MIUGKS_ETIMEOUT.
+    No fault, no hang: the solver is destroyed cleanly and a new one on the
+    same device iterates as a fresh one does."""
+    case = wl.cavity(n=64, nvel=8, kn=0.5, lid=0.2, levels=2)
+    s = lib.Solver(case)
+    s.init_uniform(1.0, 0.0, 0.0, 1.0)
+    s.step(1)
+    s.set_wait_limit(0.0)
+    with pytest.raises(lib.MiugksError) as e:
+        s.step(1)
+    assert e.value.status == lib.MIUGKS_ETIMEOUT, str(e.value)
+    s.close()
+    a, b = lib.Solver(case), lib.Solver(case)
+    for t in (a, b):
+        t.init_uniform(1.0, 0.0, 0.0, 1.0)
+        t.step(3)
+    assert np.array_equal(a.get_f(), b.get_f())
+    with pytest.raises(lib.MiugksError):
+        a.set_wait_limit(-1.0)
