@@ -2127,8 +2127,11 @@ static void interior_face_adj(oracle_solver *s, int axis, int cLL, int cL, int c
             if (cLL >= 0) {
                 double s1 = (fL - FIX(s, cp, cLL, k)) / dLLL, s2 = (fR - fL) / dLR;
                 if (s1 * s2 > 0.0) {
-                    double d = (s1 + s2) * (s1 + s2);
-                    double s1b = sLb * 2.0 * s2 * s2 / d, s2b = sLb * 2.0 * s1 * s1 / d;
+                    /* derivatives of 2 s1 s2 / (s1 + s2): 2 (s2 / (s1 + s2))^2 and 2 (s1 / (s1 + s2))^2,
+                       written with the quotients so that they stay finite when the slopes are near
+                       the underflow threshold (the far tails of the velocity grid) */
+                    double q1 = s1 / (s1 + s2), q2 = s2 / (s1 + s2);
+                    double s1b = sLb * 2.0 * q2 * q2, s2b = sLb * 2.0 * q1 * q1;
                     fLb += s1b / dLLL - s2b / dLR;
                     OUTA(out, cp, cLL, k) -= s1b / dLLL;
                     fRb += s2b / dLR;
@@ -2137,8 +2140,8 @@ static void interior_face_adj(oracle_solver *s, int axis, int cLL, int cL, int c
             if (cRR >= 0) {
                 double s2 = (fR - fL) / dLR, s3 = (FIX(s, cp, cRR, k) - fR) / dRRR;
                 if (s2 * s3 > 0.0) {
-                    double d = (s2 + s3) * (s2 + s3);
-                    double s2b = sRb * 2.0 * s3 * s3 / d, s3b = sRb * 2.0 * s2 * s2 / d;
+                    double q2 = s2 / (s2 + s3), q3 = s3 / (s2 + s3);
+                    double s2b = sRb * 2.0 * q3 * q3, s3b = sRb * 2.0 * q2 * q2;
                     fRb += s2b / dLR - s3b / dRRR;
                     fLb -= s2b / dLR;
                     OUTA(out, cp, cRR, k) += s3b / dRRR;

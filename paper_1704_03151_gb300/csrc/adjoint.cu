@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(256) k_adj_face(AdjDev A, int axis, const doub
     const LevelDev& L = A.L;
     const VelDev& Vg = A.V;
     const int nv = Vg.nv, tid = threadIdx.x, bs = blockDim.x, fi = blockIdx.x;
-    const int nx = L.nx, ny = L.ny;
+    const int nx = L.nx;
     const size_t nc = L.nc, snv = nv;
     const double* fG = A.f;
     const double* fH = A.f + nc * snv;
@@ -609,8 +609,10 @@ __device__ __forceinline__ void face_contrib(const AdjDev& A, const double* mu, 
         if (g.cLL >= 0 && sLb != 0.0) {
             double s1 = (fL - fc[g.cLL * snv + k]) * g.rLLL, s2 = (fR - fL) * g.rLR;
             if (s1 * s2 > 0.0) {
-                double dd = 2.0 * sLb / ((s1 + s2) * (s1 + s2));
-                double s1b = dd * s2 * s2, s2b = dd * s1 * s1;
+                // d/ds1 of 2 s1 s2/(s1 + s2) is 2 (s2/(s1 + s2))^2: quotients in (0, 1), so the
+                // derivative stays finite for slopes near the underflow threshold (far velocity tails)
+                const double q1 = s1 / (s1 + s2), q2 = s2 / (s1 + s2);
+                double s1b = 2.0 * sLb * q2 * q2, s2b = 2.0 * sLb * q1 * q1;
                 if (pos == 0) res -= s1b * g.rLLL;
                 else if (pos == 1) res += s1b * g.rLLL - s2b * g.rLR;
                 else if (pos == 2) res += s2b * g.rLR;
@@ -619,8 +621,8 @@ __device__ __forceinline__ void face_contrib(const AdjDev& A, const double* mu, 
         if (g.cRR >= 0 && sRb != 0.0) {
             double s2 = (fR - fL) * g.rLR, s3 = (fc[g.cRR * snv + k] - fR) * g.rRRR;
             if (s2 * s3 > 0.0) {
-                double dd = 2.0 * sRb / ((s2 + s3) * (s2 + s3));
-                double s2b = dd * s3 * s3, s3b = dd * s2 * s2;
+                const double q2 = s2 / (s2 + s3), q3 = s3 / (s2 + s3);
+                double s2b = 2.0 * sRb * q3 * q3, s3b = 2.0 * sRb * q2 * q2;
                 if (pos == 1) res -= s2b * g.rLR;
                 else if (pos == 2) res += s2b * g.rLR - s3b * g.rRRR;
                 else if (pos == 3) res += s3b * g.rRRR;
@@ -1107,7 +1109,7 @@ __global__ void __launch_bounds__(256) k_adj_objective(AdjDev A, int obj, int bc
     __shared__ double red[kRed * 8];
     const LevelDev& L = A.L;
     const VelDev& Vg = A.V;
-    const int nv = Vg.nv, tid = threadIdx.x, bs = blockDim.x, nx = L.nx, ny = L.ny;
+    const int nv = Vg.nv, tid = threadIdx.x, bs = blockDim.x, nx = L.nx;
     const size_t nc = L.nc, snv = nv;
     const int code = faces[blockIdx.x], axis = code >> 30, fi = code & ((1 << 30) - 1);
     int outsign, c;
@@ -1185,7 +1187,7 @@ __global__ void __launch_bounds__(256) k_adj_dtheta(AdjDev A, int bcid, const in
     __shared__ double red[kRed * 4];
     const LevelDev& L = A.L;
     const VelDev& Vg = A.V;
-    const int nv = Vg.nv, tid = threadIdx.x, bs = blockDim.x, nx = L.nx, ny = L.ny;
+    const int nv = Vg.nv, tid = threadIdx.x, bs = blockDim.x, nx = L.nx;
     const size_t nc = L.nc, snv = nv;
     const int code = faces[blockIdx.x], axis = code >> 30, fi = code & ((1 << 30) - 1);
     int outsign, c;

@@ -133,8 +133,8 @@ __device__ __forceinline__ double vl_limited(double s1, double s2)
 }
 __device__ __forceinline__ float vl_limited(float s1, float s2)
 {
-    float p = s1 * s2;
-    return p > 0.0f ? 2.0f * p / (s1 + s2) : 0.0f;
+    float p = s1 * s2;   // s1 + s2 has no cancellation here; the fast quotient is within 2 ulp
+    return p > 0.0f ? __fdividef(2.0f * p, s1 + s2) : 0.0f;
 }
 
 // (a . psi) g split into the reduced components: b gM + a4 hM and b hM + a4 <xi^4>/4 gM
@@ -256,24 +256,11 @@ __global__ void __launch_bounds__(256, sizeof(F) == 4 ? 4 : 2) k_face_flux(FaceF
         if (j - 1 > 0 && L.fby[fi - nx] < 0) cLL = cL - nx;
         if (j + 1 < ny && L.fby[fi + nx] < 0) cRR = cR + nx;
     }
-    if (tid == 0) {
-        double dLLL = 1, dLR, dRRR = 1, hL, hR, wL, wR;
-        if (axis == 0) {
-            if (cLL >= 0) dLLL = L.xc[i - 1] - L.xc[i - 2];
-            if (cRR >= 0) dRRR = L.xc[i + 1] - L.xc[i];
-            dLR = L.xc[i] - L.xc[i - 1];
-            hL = L.xn[i] - L.xc[i - 1]; hR = L.xc[i] - L.xn[i];
-            wL = L.dx[i - 1]; wR = L.dx[i];
-        } else {
-            if (cLL >= 0) dLLL = L.yc[j - 1] - L.yc[j - 2];
-            if (cRR >= 0) dRRR = L.yc[j + 1] - L.yc[j];
-            dLR = L.yc[j] - L.yc[j - 1];
-            hL = L.yn[j] - L.yc[j - 1]; hR = L.yc[j] - L.yn[j];
-            wL = L.dy[j - 1]; wR = L.dy[j];
-        }
-        pf[0] = (F)(1.0 / dLLL); pf[1] = (F)(1.0 / dLR); pf[2] = (F)(1.0 / dRRR);
-        pf[3] = (F)hL; pf[4] = (F)hR;
-        par[26] = hL; par[27] = hR; par[28] = wL; par[29] = wR;
+    // the face's mesh constants (kFluxGeo): par[32..40] in FP64, the first five also in F
+    if (tid < kFluxGeo - 1) {
+        const double gv = A.geo[(size_t)fi * kFluxGeo + tid];
+        par[32 + tid] = gv;
+        if (tid < 5) pf[tid] = (F)gv;
     }
     __syncthreads();
     const F r1 = pf[0], r2 = pf[1], r3 = pf[2], fhL = pf[3], fhR = pf[4];
@@ -303,7 +290,9 @@ __global__ void __launch_bounds__(256, sizeof(F) == 4 ? 4 : 2) k_face_flux(FaceF
     };
 
     // pass 1: reconstruction, upwinding, interface conservative variables
+    // (unrolled so that the loads of the next velocity are in flight with this one's arithmetic)
     Acc<F> W0a[4];
+    #pragma unroll 2
     for (int k = kb + tid; k < ke; k += bs) {
         F f0[2], sg[2];
         recon(k, f0, sg);
@@ -329,7 +318,7 @@ __global__ void __launch_bounds__(256, sizeof(F) == 4 ? 4 : 2) k_face_flux(FaceF
             par[0] = rho; par[1] = U; par[2] = V; par[3] = lam;
             if constexpr (sizeof(F) == 8) par[4] = tau_of(A.gas, rho, lam);
             else par[4] = (double)tau_of_f(A.gas, (float)rho, (float)lam);
-            par[5] = A.cfl * fmin(par[28], par[29]) / (axis == 0 ? Vg.umax : Vg.vmax);
+            par[5] = par[37];
             if (A.shock) {
                 double rl, ul, vl, ll, rr, ur, vr, lr;
                 prim4(A.W + 4 * (size_t)cL, rl, ul, vl, ll);
@@ -339,7 +328,9 @@ __global__ void __launch_bounds__(256, sizeof(F) == 4 ? 4 : 2) k_face_flux(FaceF
             }
         } else {
             const double* Wc = A.W + 4 * (size_t)(tid == 1 ? cL : cR);
-            double hf = (tid == 1 ? 1.0 : -1.0) * ir * rcp64(tid == 1 ? par[26] : par[27]), dw[4];
+            double hf, dw[4];
+            if constexpr (sizeof(F) == 8) hf = (tid == 1 ? 1.0 : -1.0) * ir * rcp64(tid == 1 ? par[35] : par[36]);
+            else hf = (tid == 1 ? 1.0 : -1.0) * ir * (tid == 1 ? par[39] : par[40]);
             for (int m = 0; m < 4; ++m) dw[m] = (W0[m] - Wc[m]) * hf;
             if constexpr (sizeof(F) == 8) {
                 micro_slope(dw, U, V, lam, par + (tid == 1 ? 8 : 12));
@@ -359,17 +350,28 @@ __global__ void __launch_bounds__(256, sizeof(F) == 4 ? 4 : 2) k_face_flux(FaceF
             if (tid < 8) val = (F)par[8 + tid];          // aL, aR
             else if (tid == 8) val = (F)U0;
             else if (tid == 9) val = (F)V0;
-            else if (tid == 10) val = (F)(rho0 * lam0 / kPi);
-            else if (tid == 11) val = (F)(kKint / (4.0 * lam0));
-            else if (tid == 12) val = (F)(kKint * (kKint + 2.0) / (16.0 * lam0 * lam0));
+            else if constexpr (sizeof(F) == 8) {
+                if (tid == 10) val = rho0 * lam0 / kPi;
+                else if (tid == 11) val = kKint / (4.0 * lam0);
+                else if (tid == 12) val = kKint * (kKint + 2.0) / (16.0 * lam0 * lam0);
+            } else {                                      // FP32 constants need no FP64 division
+                const float fl = (float)lam0;
+                if (tid == 10) val = (float)rho0 * fl * (float)(1.0 / kPi);
+                else if (tid == 11) val = (float)(kKint / 4.0) / fl;
+                else if (tid == 12) val = (float)(kKint * (kKint + 2.0) / 16.0) / (fl * fl);
+            }
             if (tid < 13) pf[8 + tid] = val;
         } else {
             for (int e = tid - 32; e < Vg.nu + Vg.nvv; e += bs - 32) {
                 const bool isu = e < Vg.nu;
                 const double d = isu ? Vg.ua[e] - U0 : Vg.vb[e - Vg.nu] - V0;
                 F ex;
-                if constexpr (sizeof(F) == 8) ex = exp(-lam0 * d * d);
-                else ex = expf((float)(-lam0 * d * d));
+                if constexpr (sizeof(F) == 8) {
+                    ex = exp(-lam0 * d * d);
+                } else {
+                    const float df = (float)d;
+                    ex = expf(-(float)lam0 * df * df);
+                }
                 (isu ? Eu[e] : Ev[e - Vg.nu]) = ex;
             }
         }
@@ -430,8 +432,11 @@ __global__ void __launch_bounds__(256, sizeof(F) == 4 ? 4 : 2) k_face_flux(FaceF
         const double rho0 = par[0], lam0 = par[3];
         F val = F(0);
         if (tid < 4) val = (F)par[16 + tid];             // A
-        else if (tid < 9) val = (F)(par[20 + tid - 4] * (1.0 / par[5]));   // q_i / dt
-        else if (tid == 9) val = (F)((1.0 - A.gas.pr) * 4.0 * lam0 * lam0 / (5.0 * rho0));
+        else if (tid < 9) val = (F)(par[20 + tid - 4] * par[38]);   // q_i / dt
+        else if (tid == 9) {
+            if constexpr (sizeof(F) == 8) val = (1.0 - A.gas.pr) * 4.0 * lam0 * lam0 / (5.0 * rho0);
+            else val = (float)((1.0 - A.gas.pr) * 0.8) * ((float)lam0 * (float)lam0) / (float)rho0;
+        }
         else if (tid == 10) val = (F)par[6];
         else if (tid == 11) val = (F)par[7];
         else if (tid == 12) val = (F)(2.0 * lam0);

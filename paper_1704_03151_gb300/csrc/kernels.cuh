@@ -15,7 +15,13 @@ struct FaceFluxArgs {
     double* Fm;                            // [nf][4] macro flux
     int axis; double cfl;
     int shock;                             // add the pressure-jump term to the interface collision time
+    const double* geo;                     // [nf][kFluxGeo] constants of each interior face of this axis
 };
+// Per interior face: 1/(x_{i-1} - x_{i-2}), 1/(x_i - x_{i-1}), 1/(x_{i+1} - x_i)
+// (1 where the outer cell does not exist), the face-to-centre distances h_L,
+// h_R, the time step dt = CFL min(dx_L, dx_R) / max|u|, 1/dt, 1/h_L, 1/h_R.
+// They depend only on the mesh, so they are computed once on the host.
+constexpr int kFluxGeo = 10;
 
 void upload_series_coefficients();
 template <typename F> cudaError_t launch_face_flux(const FaceFluxArgs<F>& a, cudaStream_t st);

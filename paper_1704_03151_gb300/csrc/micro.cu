@@ -1418,10 +1418,18 @@ __global__ void __launch_bounds__(256) k_micro_renew(MicroArgs M, const double* 
                     st4(acc + id, aa);
                 }
         } else {
+            // four velocities a block apart per thread: coalesced, eight loads in flight
+            const int bs = blockDim.x;
             for (int cp = 0; cp < 2; ++cp)
-                for (int k = threadIdx.x; k < nv; k += blockDim.x) {
-                    size_t id = (cp * nc + c) * nv + k;
-                    acc[id] = acc[id] + x[id];
+                for (int k0 = threadIdx.x; k0 < nv; k0 += 4 * bs) {
+                    const size_t id0 = (cp * nc + c) * nv + k0;
+                    F xa[4], aa[4];
+                    #pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (k0 + q * bs < nv) { xa[q] = x[id0 + q * bs]; aa[q] = acc[id0 + q * bs]; }
+                    #pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (k0 + q * bs < nv) acc[id0 + q * bs] = aa[q] + xa[q];
                 }
         }
     }
@@ -1495,6 +1503,42 @@ __global__ void __launch_bounds__(256) k_micro_renew(MicroArgs M, const double* 
         }
         return;
     }
+    if (nb == 0) {
+        // interior cell, any velocity count: four velocities a block apart per thread, so
+        // that every access is coalesced and 24 loads are in flight per thread (one
+        // velocity at a time leaves the cell's two DRAM streams latency-bound)
+        const int bs = blockDim.x;
+        for (int cp = 0; cp < 2; ++cp) {
+            const F* xb = x + cp * nc * nv;
+            F* rb = r + cp * nc * nv;
+            for (int k0 = threadIdx.x; k0 < nv; k0 += 4 * bs) {
+                F xc[4], xw[4], xe[4], xs[4], xn[4], rr[4];
+                #pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int k = k0 + q * bs;
+                    if (k < nv) {
+                        const size_t id = (size_t)c * nv + k;
+                        xc[q] = xb[id]; xw[q] = xb[id - nv]; xe[q] = xb[id + nv];
+                        xs[q] = xb[id - (size_t)nx * nv]; xn[q] = xb[id + (size_t)nx * nv]; rr[q] = rb[id];
+                    }
+                }
+                #pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int k = k0 + q * bs;
+                    if (k < nv) {
+                        const F u = vu[k], v = vv[k];
+                        F a = (itau + geomD_r<F>(rdxi, rdyj, u, v)) * xc[q];
+                        a += Dface<F>(0, -1, rdxi, u, v) * xw[q];
+                        a += Dface<F>(0, 1, rdxi, u, v) * xe[q];
+                        a += Dface<F>(1, -1, rdyj, u, v) * xs[q];
+                        a += Dface<F>(1, 1, rdyj, u, v) * xn[q];
+                        rb[(size_t)c * nv + k] = rr[q] - a;
+                    }
+                }
+            }
+        }
+        return;
+    }
     // interior neighbours (faces without a BC id)
     const bool hw = L.fbx[j * (nx + 1) + i] < 0, he = L.fbx[j * (nx + 1) + i + 1] < 0;
     const bool hs = L.fby[j * nx + i] < 0, hn = L.fby[(j + 1) * nx + i] < 0;
@@ -1556,16 +1600,32 @@ __global__ void __launch_bounds__(256) k_update_moments(LevelDev L, VelDev Vg, F
     const F* __restrict__ vv = VelT<F>::v(Vg);
     const F* __restrict__ vw = VelT<F>::w(Vg);
     __shared__ int sok;
+    // Each thread takes four velocities a block apart per round and issues all their
+    // loads before the arithmetic (the summation order is that of k = tid, tid + bs, ...).
+    const int bs = blockDim.x;
     Acc<F> sa[4];
-    for (int k = threadIdx.x; k < nv; k += blockDim.x) {
-        F g = fG[k], h = fH[k];
-        if (df) {
-            g = g + df[(size_t)c * nv + k];
-            h = h + df[(nc + c) * (size_t)nv + k];
+    for (int k0 = threadIdx.x; k0 < nv; k0 += 4 * bs) {
+        F g[4], h[4];
+        #pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int k = k0 + q * bs;
+            if (k < nv) {
+                g[q] = fG[k]; h[q] = fH[k];
+                if (df) {
+                    g[q] = g[q] + df[(size_t)c * nv + k];
+                    h[q] = h[q] + df[(nc + c) * (size_t)nv + k];
+                }
+            }
         }
-        const F u = vu[k], v = vv[k], w = vw[k];
-        sa[0].add(w * g); sa[1].add(w * u * g); sa[2].add(w * v * g);
-        sa[3].add(w * (F(0.5) * (u * u + v * v) * g + h));
+        #pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int k = k0 + q * bs;
+            if (k < nv) {
+                const F u = vu[k], v = vv[k], w = vw[k];
+                sa[0].add(w * g[q]); sa[1].add(w * u * g[q]); sa[2].add(w * v * g[q]);
+                sa[3].add(w * (F(0.5) * (u * u + v * v) * g[q] + h[q]));
+            }
+        }
     }
     double s[4];
     block_total<4>(sa, red, s);
@@ -1575,9 +1635,21 @@ __global__ void __launch_bounds__(256) k_update_moments(LevelDev L, VelDev Vg, F
         if (threadIdx.x == 0) sok = s[0] > 0.0 && s[3] * s[0] - 0.5 * (s[1] * s[1] + s[2] * s[2]) > 0.0;
         __syncthreads();
         if (sok) {
-            for (int k = threadIdx.x; k < nv; k += blockDim.x) {
-                fG[k] = fG[k] + df[(size_t)c * nv + k];
-                fH[k] = fH[k] + df[(nc + c) * (size_t)nv + k];
+            for (int k0 = threadIdx.x; k0 < nv; k0 += 4 * bs) {
+                F g[4], h[4], dg[4], dh[4];
+                #pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int k = k0 + q * bs;
+                    if (k < nv) {
+                        g[q] = fG[k]; h[q] = fH[k];
+                        dg[q] = df[(size_t)c * nv + k]; dh[q] = df[(nc + c) * (size_t)nv + k];
+                    }
+                }
+                #pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int k = k0 + q * bs;
+                    if (k < nv) { fG[k] = g[q] + dg[q]; fH[k] = h[q] + dh[q]; }
+                }
             }
         } else {
             Acc<F> sb[4];
@@ -1598,11 +1670,21 @@ __global__ void __launch_bounds__(256) k_update_moments(LevelDev L, VelDev Vg, F
     __syncthreads();
     const F fU = sUV[0], fV = sUV[1];
     Acc<F> ta[2];
-    for (int k = threadIdx.x; k < nv; k += blockDim.x) {
-        F cx = vu[k] - fU, cy = vv[k] - fV;
-        F e = F(0.5) * (cx * cx + cy * cy) * fG[k] + fH[k];
-        ta[0].add(vw[k] * cx * e);
-        ta[1].add(vw[k] * cy * e);
+    for (int k0 = threadIdx.x; k0 < nv; k0 += 4 * bs) {
+        F g[4], h[4];
+        #pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (k0 + q * bs < nv) { g[q] = fG[k0 + q * bs]; h[q] = fH[k0 + q * bs]; }
+        #pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int k = k0 + q * bs;
+            if (k < nv) {
+                F cx = vu[k] - fU, cy = vv[k] - fV;
+                F e = F(0.5) * (cx * cx + cy * cy) * g[q] + h[q];
+                ta[0].add(vw[k] * cx * e);
+                ta[1].add(vw[k] * cy * e);
+            }
+        }
     }
     double t[2];
     block_total<2>(ta, red, t);

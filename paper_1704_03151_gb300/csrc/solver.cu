@@ -64,6 +64,7 @@ struct miugks_solver {
     bool mixed = false;
     size_t fsz = sizeof(double);
     void *f = nullptr, *phx = nullptr, *phy = nullptr, *xcorner = nullptr;
+    double* fgeo[2] = {nullptr, nullptr};   // finest level: mesh constants of the interface flux per face
     double *W = nullptr, *q = nullptr, *R = nullptr, *Fx = nullptr, *Fy = nullptr;
     double *rms_part = nullptr, *rms_out = nullptr;
     double dtp_min = 0;
@@ -164,6 +165,35 @@ miugks_status dalloc(miugks_solver* s, T** p, size_t count)
     s->allocs.push_back(ptr);
     *p = (T*)ptr;
     return MIUGKS_OK;
+}
+
+// Mesh constants of every interior face of one axis of a level for the interface
+// flux (layout kFluxGeo), with the arithmetic the flux would otherwise repeat
+// per face and iteration: reconstruction distances, face-to-centre distances,
+// the local time step dt = CFL min(w_L, w_R) / cmax and reciprocals.
+std::vector<double> flux_face_geometry(const HLevel& L, int axis, double cfl, double cmax)
+{
+    const int nf = axis == 0 ? L.nfx : L.nfy;
+    std::vector<double> t((size_t)nf * kFluxGeo, 0.0);
+    const int n = axis == 0 ? L.nx : L.ny;                 // cells along the axis
+    const std::vector<double>& c = axis == 0 ? L.xc : L.yc;
+    const std::vector<double>& e = axis == 0 ? L.xn : L.yn;
+    const std::vector<double>& w = axis == 0 ? L.dx : L.dy;
+    for (int fi = 0; fi < nf; ++fi) {
+        const int p = axis == 0 ? fi % (L.nx + 1) : fi / L.nx;   // face index along the axis
+        if (p < 1 || p >= n) continue;
+        double* g = &t[(size_t)fi * kFluxGeo];
+        g[0] = p >= 2 ? 1.0 / (c[p - 1] - c[p - 2]) : 1.0;
+        g[1] = 1.0 / (c[p] - c[p - 1]);
+        g[2] = p + 1 < n ? 1.0 / (c[p + 1] - c[p]) : 1.0;
+        g[3] = e[p] - c[p - 1];
+        g[4] = c[p] - e[p];
+        g[5] = cfl * std::fmin(w[p - 1], w[p]) / cmax;
+        g[6] = 1.0 / g[5];
+        g[7] = 1.0 / g[3];
+        g[8] = 1.0 / g[4];
+    }
+    return t;
 }
 
 // per-velocity array of count elements of the solver's storage type
@@ -617,9 +647,9 @@ miugks_status flux_stage_t(miugks_solver* s)
 {
     HLevel& L0 = s->lev[0];
     FaceFluxArgs<F> fa{L0.dev, s->vel, s->gas, s->bc, s->Cw, (const F*)s->f, s->W, (F*)s->phx, s->Fx, 0, s->opts.cfl,
-                       s->shock ? 1 : 0};
+                       s->shock ? 1 : 0, s->fgeo[0]};
     CK(launch_face_flux<F>(fa, s->st));
-    fa.axis = 1; fa.ph = (F*)s->phy; fa.Fm = s->Fy;
+    fa.axis = 1; fa.ph = (F*)s->phy; fa.Fm = s->Fy; fa.geo = s->fgeo[1];
     CK(launch_face_flux<F>(fa, s->st));
     CK(launch_cell_residual(L0.dev, s->Fx, s->Fy, s->R, s->st));
     return MIUGKS_OK;
@@ -953,6 +983,8 @@ miugks_status miugks_create(const miugks_mesh* mesh, const miugks_vgrid* vg, con
         if ((st = dalloc(s, &s->R, 4 * nc)) != MIUGKS_OK) break;
         if ((st = falloc(s, &s->phx, 2 * (size_t)L0.nfx * nv)) != MIUGKS_OK) break;
         if ((st = falloc(s, &s->phy, 2 * (size_t)L0.nfy * nv)) != MIUGKS_OK) break;
+        if ((st = upload(s, &s->fgeo[0], flux_face_geometry(L0, 0, opts->cfl, s->umax))) != MIUGKS_OK) break;
+        if ((st = upload(s, &s->fgeo[1], flux_face_geometry(L0, 1, opts->cfl, s->vmax))) != MIUGKS_OK) break;
         if ((st = dalloc(s, &s->Fx, 4 * (size_t)L0.nfx)) != MIUGKS_OK) break;
         if ((st = dalloc(s, &s->Fy, 4 * (size_t)L0.nfy)) != MIUGKS_OK) break;
         if ((st = dalloc(s, &s->rms_part, 64 * 5)) != MIUGKS_OK) break;

@@ -82,6 +82,25 @@ def test_adjoint_residual_matches_oracle(lib, name):
         assert rel(g.adjoint_residual(mu), o.adjoint_residual(mu)) < TOL, name
 
 
+def test_adjoint_residual_with_slopes_near_underflow_matches_oracle(lib):
+    """One velocity at values of 1e-158 (van Leer slopes whose product is
+    subnormal, as in the far tails of the 89^2 grid at Ma 5): the limiter's
+    derivative stays finite and matches the oracle."""
+    o, g, rng = _pair(lib, _stretched_cavity(), 13)
+    f = o.get_f()
+    nvv = int(round(np.sqrt(o.nv)))
+    k0 = (nvv - 1) * nvv + nvv // 2                 # the largest u > 0
+    ix = np.arange(o.nc) % o.nx
+    for cp in range(2):
+        f[cp, :, k0] = 1e-158 * (1.0 + 0.2 * ix) * (1 + cp)
+    o.set_f(f)
+    g.set_f(f)
+    mu = rng.normal(size=(2, o.nc, o.nv))
+    out = g.adjoint_residual(mu)
+    assert np.all(np.isfinite(out))
+    assert rel(out, o.adjoint_residual(mu)) < TOL
+
+
 def _dense_sgs(o, inv_tau):
     n = 2 * o.nc * o.nv
     S = np.zeros((n, n))

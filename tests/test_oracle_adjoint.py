@@ -104,6 +104,41 @@ def test_adjoint_residual_dot_product(make):
     assert checked >= 6
 
 
+def _tiny_velocity(o, f, scale):
+    """f with one velocity (the largest u > 0: k = a nv_y + b with a the last
+    u node) replaced in every cell by scale x a profile that grows along x, so
+    that its van Leer slopes at the x-faces all have one sign and are of the
+    order of scale (both components)."""
+    nvv = int(round(np.sqrt(o.nv)))
+    k0 = (nvv - 1) * nvv + nvv // 2
+    g = f.copy()
+    ix = np.arange(o.nc) % o.nx
+    for cp in range(2):
+        g[cp, :, k0] = scale * (1.0 + 0.2 * ix) * (1 + cp)
+    return g
+
+
+def test_adjoint_residual_stays_finite_for_slopes_near_underflow():
+    """The derivative of the van Leer slope 2 s1 s2 / (s1 + s2) is
+    2 (s2 / (s1 + s2))^2 (and symmetrically): it depends on the slopes' ratio
+    only.  So a velocity whose values (and slopes) sit near the underflow
+    threshold of FP64, as in the far tails of a wide velocity grid at Ma 5,
+    gives the same transposed Jacobian as the same profile scaled to 1e-150
+    (where nothing underflows), to the 1e-150 change of the moments, and no
+    Inf or NaN."""
+    case = _stretched_cavity()
+    o = oracle.Oracle(case)
+    o.init_fields(*wl.random_fields(case, 5, amp=0.1))
+    f = o.get_f()
+    mu = np.random.default_rng(2).normal(size=f.shape)
+    outs = []
+    for scale in (1e-150, 1e-158):
+        o.set_f(_tiny_velocity(o, f, scale))
+        outs.append(o.adjoint_residual(mu))
+    assert np.all(np.isfinite(outs[1]))
+    assert np.max(np.abs(outs[1] - outs[0])) <= 1e-12 * np.max(np.abs(outs[0]))
+
+
 def test_objective_and_parameter_derivatives():
     case = _stretched_cavity()
     o = oracle.Oracle(case)
