@@ -408,7 +408,9 @@ SWEEP_VALUES_PER_CV = 5
 # kernels (mixed), from the ncu captures summarised in
 # profiles/k_sgs_plate128x96_v48_mixed.md (forward and backward launches)
 SWEEP_TRAFFIC_PER_CV = {"lines": 30.2, "wave": 29.8}
-FLUX_TRAFFIC_PLATE_MIXED = None
+# DRAM bytes (read + written) of one launch of the flat plate's face-flux kernel
+# (mixed, x-faces), from the ncu capture in profiles/k_face_flux_plate128x96_v48_mixed.md
+FLUX_TRAFFIC_PLATE_MIXED = 417.3e6
 
 
 def sweep_roofline(sk, precision):
@@ -579,7 +581,7 @@ def run_square_adjoint(args):
     adjoint gradient of the heat flux into the square (the sum over its wall
     faces of face length x heat flux, BC 0) with respect to its wall
     temperature: flexible GMRES(--restart) to --adj-tol, preconditioned by the
-    transposed multigrid cycle (approximate at the body's faces).  With --fd,
+    transposed multigrid cycle, body faces included.  With --fd,
     also central differences of two more converged solves (T_w = 1 +- 5e-3)."""
     import torch
     from paper_1704_03151_gb300 import build, miugks, refine, workloads
@@ -626,6 +628,25 @@ def run_plate_iter(args):
     res = s.step(args.steps)
     torch.cuda.synchronize()
     print(json.dumps({"workload": "flat_plate_%dx%d_v48x48_kn0.1_4level_%s" % (c["nx"], c["ny"], args.precision),
+                      "iterations": args.steps, "residual": [float(x) for x in res]}))
+    return 0
+
+
+def run_square_iter(args):
+    """--workload square_iter: --steps outer iterations (mixed form unless
+    --precision fp64) of the square cylinder at half size per axis (80x60
+    cells, 16x12-cell square, 89x89 velocities, 3 levels; a few GB on the
+    device) from its initial state, eagerly launched after the first; a
+    small profiling target with the full-size case's velocity grid."""
+    import torch
+    from paper_1704_03151_gb300 import build, miugks, workloads
+    build.build()
+    c = workloads.square_cylinder(levels=3, nx_side=32, nx_sq=16, ny_side=24, ny_sq=12)
+    s = miugks.Solver(c, precision=args.precision)
+    s.init_fields(*workloads.initial_fields(c))
+    res = s.step(args.steps)
+    torch.cuda.synchronize()
+    print(json.dumps({"workload": "square_cylinder_%dx%d_v89x89_3level_%s" % (c["nx"], c["ny"], args.precision),
                       "iterations": args.steps, "residual": [float(x) for x in res]}))
     return 0
 
@@ -679,7 +700,7 @@ def main():
     ap.add_argument("--no-square", action="store_true", help="skip the full-size square-cylinder throughput line")
     ap.add_argument("--workload", default="cavity64",
                     choices=["cavity64", "kn_sweep", "adjoint", "cycles", "plate_adjoint", "square", "plate_iter",
-                             "square_adjoint"])
+                             "square_adjoint", "square_iter"])
     ap.add_argument("--count", type=int, default=32, help="cavities of the Kn sweep")
     ap.add_argument("--restart", type=int, default=20, help="GMRES restart length of --workload square_adjoint")
     ap.add_argument("--adj-tol", type=float, default=1e-6, help="adjoint GMRES tolerance of --workload square_adjoint")
@@ -703,6 +724,8 @@ def main():
         return run_plate_iter(args)
     if args.workload == "square_adjoint":
         return run_square_adjoint(args)
+    if args.workload == "square_iter":
+        return run_square_iter(args)
     if args.workload == "square":
         return run_square(args)
     args.warmup = max(args.warmup, 3)

@@ -250,8 +250,10 @@ miugks_status miugks_stage_prolong(miugks_solver *s, int lev, int m, const doubl
  * FP64 copy (checkpoint) of the current f, whatever the solver's precision.
  * On a mesh with bodies a body's faces are wall faces of the fluid cells beside
  * them and a cell in a body holds no state (N = -f there); the transposed-cycle
- * preconditioner keeps the ghost couplings of the domain edge only (it is an
- * approximation at a body's faces, which the Krylov solve corrects).
+ * preconditioner carries the wall coupling of a body's faces as of the domain
+ * edge's (a cell with two wall faces on one sweep side, at a concave body
+ * corner, keeps the plain wavefront value there, which the Krylov solve
+ * corrects).
  *
  *  stage_adjoint_residual: out = (dN/df)^T mu at the current f, host arrays
  *        of 2 x nc x nv ([comp][cell][k]).

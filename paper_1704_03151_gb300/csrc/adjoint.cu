@@ -18,6 +18,7 @@
 //                cell's own collision term contribute to that entry.
 // Everything runs in FP64 on an FP64 copy (checkpoint) of f.
 #include "kernels.cuh"
+#include <climits>
 
 namespace miugks {
 
@@ -951,11 +952,13 @@ __global__ void __launch_bounds__(512) k_adjT_chain(AdjSweepArgs S, int pass, in
     }
 }
 
-// Every other cell of a pass has no boundary face on its side: a plain
+// Every other cell of a pass has no domain-edge face on its side: a plain
 // triangular solve along anti-diagonals, independent per velocity.  Each CTA
-// owns kAdjKc consecutive velocities and sweeps all those cells diagonal by
-// diagonal with only block barriers between diagonals.
-__global__ void __launch_bounds__(256) k_adjT_wave(AdjSweepArgs S, int pass)
+// owns kAdjKc consecutive velocities and sweeps the cells of wavefront steps
+// [t0, t1) diagonal by diagonal with only block barriers between diagonals.
+// A body's faces carry no neighbour term here; their within-cell wall
+// coupling is added by k_adjT_body between the steps.
+__global__ void __launch_bounds__(256) k_adjT_wave(AdjSweepArgs S, int pass, int t0, int t1)
 {
     const LevelDev& L = S.L;
     const VelDev& Vg = S.V;
@@ -966,7 +969,7 @@ __global__ void __launch_bounds__(256) k_adjT_wave(AdjSweepArgs S, int pass)
     const int mx = nx - 1, my = ny - 1;                 // its extent
     if (mx <= 0 || my <= 0) return;
     const int nd = mx + my - 1;
-    for (int t = 0; t < nd; ++t) {
+    for (int t = t0; t < min(t1, nd); ++t) {
         const int dd = pass == 0 ? t : nd - 1 - t;      // diagonal within the block
         const int ilo = dd - (my - 1) > 0 ? dd - (my - 1) : 0, ihi = dd < mx - 1 ? dd : mx - 1;
         const int m = ihi - ilo + 1;
@@ -992,6 +995,38 @@ __global__ void __launch_bounds__(256) k_adjT_wave(AdjSweepArgs S, int pass)
             }
         }
         __syncthreads();
+    }
+}
+
+// The wall coupling of a body face in a transposed pass, for one cell per CTA
+// (entries cell * 4 + face), after the wavefront has computed the cell's rows
+// without it: the incoming rows (u_o < 0 at the face) are final, and each
+// outgoing G row gains w u_o s / Z times its inverse diagonal, with
+// s = sum over incoming velocities of Db C (y_G + K T_w / 4 y_H) the
+// transposed wall-density sum (as in adjT_cell with one wall face).
+__global__ void __launch_bounds__(256) k_adjT_body(AdjSweepArgs S, int pass, const int* __restrict__ ent)
+{
+    __shared__ double red[kRed];
+    const LevelDev& L = S.L;
+    const VelDev& Vg = S.V;
+    const int e = ent[blockIdx.x], c = e >> 2, face = e & 3, nx = L.nx, nv = Vg.nv, i = c % nx, j = c / nx;
+    const size_t nc = L.nc, snv = nv;
+    const int axis = face >> 1, os = (face & 1) ? 1 : -1;
+    const int bid = axis == 0 ? L.fbx[j * (nx + 1) + i + (os > 0)] : L.fby[(j + (os > 0)) * nx + i];
+    const double bS = axis == 0 ? L.rdx[i] : L.rdy[j];
+    const double Z = S.Zw[bid * 4 + axis * 2 + (os > 0)];
+    const double Hf = kKint * S.bc[bid].t / 4.0;
+    double* dst = pass == 0 ? S.y : S.x;
+    double acc[1] = {0.0};
+    for (int k = threadIdx.x; k < nv; k += blockDim.x) {
+        const double uo = os * (axis == 0 ? Vg.u[k] : Vg.v[k]);
+        if (uo < 0) acc[0] += uo * bS * S.Cw[(size_t)bid * nv + k] * (dst[c * snv + k] + Hf * dst[(nc + c) * snv + k]);
+    }
+    red_sum<1>(acc, red);                    // ends with a barrier: the incoming rows are read before any write
+    const double sZ = acc[0] / Z;
+    for (int k = threadIdx.x; k < nv; k += blockDim.x) {
+        const double uo = os * (axis == 0 ? Vg.u[k] : Vg.v[k]);
+        if (uo > 0) dst[c * snv + k] += Vg.w[k] * uo * sZ * S.invD[c * snv + k];
     }
 }
 
@@ -1027,6 +1062,12 @@ __global__ void __launch_bounds__(256) k_adjT_apply(AdjSweepArgs S, const double
     if (j == 0) addb(1, -1, L.fby[i], rdy);
     if (i == nx - 1) addb(0, 1, L.fbx[j * (nx + 1) + nx], rdx);
     if (j == ny - 1) addb(1, 1, L.fby[ny * nx + i], rdy);
+    if (!L.solid[c]) {                          // a body's faces (BC ids inside the domain)
+        if (i > 0 && L.fbx[j * (nx + 1) + i] >= 0) addb(0, -1, L.fbx[j * (nx + 1) + i], rdx);
+        if (j > 0 && L.fby[j * nx + i] >= 0) addb(1, -1, L.fby[j * nx + i], rdy);
+        if (i < nx - 1 && L.fbx[j * (nx + 1) + i + 1] >= 0) addb(0, 1, L.fbx[j * (nx + 1) + i + 1], rdx);
+        if (j < ny - 1 && L.fby[(j + 1) * nx + i] >= 0) addb(1, 1, L.fby[(j + 1) * nx + i], rdy);
+    }
     auto Db = [&](int b, int k) -> double {
         double uo = bos[b] * (bax[b] == 0 ? Vg.u[k] : Vg.v[k]);
         return uo < 0 ? uo * bS[b] : 0.0;
@@ -1446,7 +1487,7 @@ cudaError_t launch_adjoint_residual(const AdjDev& A, const double* mu, double* r
     return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint_sgs(const AdjSweepArgs& S, cudaStream_t st)
+cudaError_t launch_adjoint_sgs(const AdjSweepArgs& S, const AdjBodyPlan& P, cudaStream_t st)
 {
     const size_t smem = 2 * (size_t)S.V.nv * sizeof(double);
     if (S.V.nv > kMaxAdjNv) return cudaErrorInvalidValue;
@@ -1455,7 +1496,14 @@ cudaError_t launch_adjoint_sgs(const AdjSweepArgs& S, cudaStream_t st)
     if (e != cudaSuccess) return e;
     const int nblk = (S.V.nv + kAdjKc - 1) / kAdjKc;
     for (int pass = 0; pass < 2; ++pass) {
-        k_adjT_wave<<<nblk, 256, 0, st>>>(S, pass);
+        int t = 0;
+        for (int g = 0; g < P.ngroups[pass]; ++g) {     // stop after each step that reaches a body face
+            const int ts = P.step[pass][g], n = P.off[pass][g + 1] - P.off[pass][g];
+            k_adjT_wave<<<nblk, 256, 0, st>>>(S, pass, t, ts + 1);
+            k_adjT_body<<<n, 256, 0, st>>>(S, pass, P.cells[pass] + P.off[pass][g]);
+            t = ts + 1;
+        }
+        k_adjT_wave<<<nblk, 256, 0, st>>>(S, pass, t, INT_MAX);
         k_adjT_chain<<<2, 512, smem, st>>>(S, pass, 0);
         k_adjT_chain<<<1, 512, smem, st>>>(S, pass, 1);
     }

@@ -170,8 +170,19 @@ struct AdjSweepArgs {
 // out = (dN/df)^T mu (+ pen * dM/df, M the total mass); rec*: per-face / per-cell scratch
 cudaError_t launch_adjoint_residual(const AdjDev& A, const double* mu, double* recx, double* recy, double* crec,
                                     double pen, double* out, cudaStream_t st);
-// x = P^T r, P one LU-SGS pass of the evolution smoother on level 0
-cudaError_t launch_adjoint_sgs(const AdjSweepArgs& S, cudaStream_t st);
+// Cells of a level with one wall face of a body on a transposed pass's side
+// (pass 0 east or north, pass 1 west or south), grouped by the wavefront step
+// of the transposed sweep that reaches them.  The sweep stops after each such
+// step and adds the within-cell wall coupling of those cells (the outgoing
+// rows take the transposed reflection of the incoming ones) before it goes on.
+struct AdjBodyPlan {
+    const int* cells[2];      // device, per pass: entries cell * 4 + face (0 west, 1 east, 2 south, 3 north)
+    const int* step[2];       // host, per pass: the wavefront step of each group, ascending
+    const int* off[2];        // host, per pass: first entry of group g is off[g], its end off[g + 1]
+    int ngroups[2];
+};
+// x = P^T r, P one LU-SGS pass of the evolution smoother of the level
+cudaError_t launch_adjoint_sgs(const AdjSweepArgs& S, const AdjBodyPlan& P, cudaStream_t st);
 // y = A^T x with the evolution operator of one level (all neighbours and ghosts)
 cudaError_t launch_adjoint_apply(const AdjSweepArgs& S, const double* x, double* y, cudaStream_t st);
 // fine = R^T coarse (volume-weighted restriction transposed), coarse = P^T fine (bilinear

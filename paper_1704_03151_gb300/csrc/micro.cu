@@ -802,10 +802,37 @@ __device__ __forceinline__ void cp_async_k4(F* sdst, const F* gsrc, int nk)
         cp_async16(sdst, gsrc);
         if constexpr (sizeof(F) == 8)
             if (nk > 2) cp_async16(sdst + 2, gsrc + 2);
+    } else if (sizeof(F) == 4 && nk == kInteriorKc && (reinterpret_cast<uintptr_t>(gsrc) & 7) == 0) {
+        // FP32 with a velocity count that is not a multiple of four: the run of four
+        // values still starts on an 8- or 16-byte boundary for half of the cells
+        // (sdst is 16-byte aligned)
+        if ((reinterpret_cast<uintptr_t>(gsrc) & 15) == 0) {
+            cp_async16(sdst, gsrc);
+        } else {
+            const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gsrc) : "memory");
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa + 8), "l"(gsrc + 2) : "memory");
+        }
     } else {
         #pragma unroll
         for (int q = 0; q < kInteriorKc; ++q)
             if (q < nk) cp_async_elem(sdst + q, gsrc + q);
+    }
+}
+
+// store a run of four FP32 values with the widest accesses its address allows
+__device__ __forceinline__ void st4_any(float* p, const float (&v)[4])
+{
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    if ((a & 15) == 0) {
+        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    } else if ((a & 7) == 0) {
+        *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+        *reinterpret_cast<float2*>(p + 2) = make_float2(v[2], v[3]);
+    } else {
+        p[0] = v[0];
+        *reinterpret_cast<float2*>(p + 1) = make_float2(v[1], v[2]);
+        p[3] = v[3];
     }
 }
 
@@ -944,7 +971,10 @@ __global__ void __launch_bounds__(512) k_sgs_wave(MicroArgs M, const F* __restri
     };
     if constexpr (R > 1)
         for (int dd = dd0; dd < dd0 + R - 1; ++dd) issue(dd, code_of(dd));
-    int cd_next = code_of(dd0 + R - 1);                 // for the issue of the first sweep step
+    // cell codes of the next four issues, loaded four sweep steps before they are used
+    // (one step is shorter than a global load)
+    int cd_next = code_of(dd0 + R - 1), cd_n1 = code_of(dd0 + R), cd_n2 = code_of(dd0 + R + 1),
+        cd_n3 = code_of(dd0 + R + 2);
     // prologue: diagonal buffers (the previous segment's last diagonal from x) and spacings
     for (int q = tid; q < 2 * nx * W; q += B) sx[q] = F(0);
     __syncthreads();
@@ -1032,6 +1062,14 @@ __global__ void __launch_bounds__(512) k_sgs_wave(MicroArgs M, const F* __restri
                         xd[0] = res[cp][0];
                         xd[1] = res[cp][1];
                     }
+                } else if constexpr (sizeof(F) == 4) {
+                    if (nk == K) {
+                        st4_any(xd, res[cp]);
+                    } else {
+                        #pragma unroll
+                        for (int kk = 0; kk < K; ++kk)
+                            if (kk < nk) xd[kk] = res[cp][kk];
+                    }
                 } else {
                     #pragma unroll
                     for (int kk = 0; kk < K; ++kk)
@@ -1041,7 +1079,10 @@ __global__ void __launch_bounds__(512) k_sgs_wave(MicroArgs M, const F* __restri
         }
         if constexpr (R > 1) {
             issue(dd + R - 1, cd_next);
-            cd_next = code_of(dd + R);                  // consumed after the next step's work
+            cd_next = cd_n1;
+            cd_n1 = cd_n2;
+            cd_n2 = cd_n3;
+            cd_n3 = code_of(dd + R + 3);                // consumed four steps later
         }
         __syncthreads();
     }

@@ -27,6 +27,10 @@ struct HLevel {
     SweepPlanDev plan{};                // sweep order tables (device)
     std::vector<SweepBreak> brk[2];     // body-line walks between wavefront segments
     int nlines = 0;                     // body lines (larger pass)
+    // transposed sweep (adjoint preconditioner): the cells with one wall face of a body on
+    // a pass's side, cell * 4 + face, grouped by wavefront step (AdjBodyPlan)
+    int* adjb[2] = {nullptr, nullptr};
+    std::vector<int> adjstep[2], adjoff[2];
     int* pidx = nullptr;      // prolongation stencil from the next coarser level
     double* pw = nullptr;
     int* sidx = nullptr;      // the same for a state (cells in bodies take their coarse cell's value)
@@ -464,6 +468,45 @@ miugks_status build_sweep_plan(miugks_solver* s, HLevel& Lv)
     }
     Lv.plan.nl_max = nl_max;
     Lv.plan.bodies = Lv.nfluid != Lv.nc;
+    // The transposed sweep's wavefront covers pass 0 the cells i <= nx - 2, j <= ny - 2 in
+    // steps t = i + j, pass 1 the cells i >= 1, j >= 1 in steps t = nd' - 1 - (i - 1 + j - 1),
+    // nd' = nx + ny - 3.  A fluid cell there with exactly one wall face of a body on the
+    // pass's side (pass 0 east or north, pass 1 west or south) gets its wall coupling after
+    // its step; a cell with two such faces (a concave body corner) keeps the wavefront's
+    // value (the Krylov solve corrects what the preconditioner leaves out).
+    for (int p = 0; p < 2; ++p) {
+        Lv.adjstep[p].clear();
+        Lv.adjoff[p].assign(1, 0);
+        if (nx < 2 || ny < 2 || Lv.nfluid == nc) continue;
+        const int ndT = nx + ny - 3;
+        std::vector<std::pair<int, int>> ent;   // (step, cell * 4 + face)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const int c = j * nx + i;
+                if (Lv.solid[c]) continue;
+                if (p == 0 ? (i > nx - 2 || j > ny - 2) : (i < 1 || j < 1)) continue;
+                const int fx = Lv.fbx[j * (nx + 1) + i + (p == 0 ? 1 : 0)];
+                const int fy = Lv.fby[(j + (p == 0 ? 1 : 0)) * nx + i];
+                const bool wx = fx >= 0 && s->bch[fx].type == BC_WALL, wy = fy >= 0 && s->bch[fy].type == BC_WALL;
+                if (wx == wy) continue;
+                const int t = p == 0 ? i + j : ndT - 1 - (i - 1 + j - 1);
+                ent.emplace_back(t, c * 4 + (wx ? (p == 0 ? 1 : 0) : (p == 0 ? 3 : 2)));
+            }
+        std::stable_sort(ent.begin(), ent.end(),
+                         [](const std::pair<int, int>& a, const std::pair<int, int>& b) { return a.first < b.first; });
+        std::vector<int> cells(ent.size());
+        for (size_t e = 0; e < ent.size(); ++e) {
+            cells[e] = ent[e].second;
+            if (e == 0 || ent[e].first != ent[e - 1].first) {
+                if (e > 0) Lv.adjoff[p].push_back((int)e);
+                Lv.adjstep[p].push_back(ent[e].first);
+            }
+        }
+        if (!ent.empty()) {
+            Lv.adjoff[p].push_back((int)ent.size());
+            ST(upload(s, &Lv.adjb[p], cells));
+        }
+    }
     return MIUGKS_OK;
 }
 
@@ -1716,7 +1759,15 @@ AdjSweepArgs lvl_args(miugks_solver* s, int l, const double* r, double* out)
 // out = S^T r and y = A^T x on level l
 miugks_status sweep_T(miugks_solver* s, int l, const double* r, double* out)
 {
-    CK(launch_adjoint_sgs(lvl_args(s, l, r, out), s->st));
+    const HLevel& Lv = s->lev[l];
+    AdjBodyPlan P{};
+    for (int p = 0; p < 2; ++p) {
+        P.cells[p] = Lv.adjb[p];
+        P.step[p] = Lv.adjstep[p].data();
+        P.off[p] = Lv.adjoff[p].data();
+        P.ngroups[p] = (int)Lv.adjstep[p].size();
+    }
+    CK(launch_adjoint_sgs(lvl_args(s, l, r, out), P, s->st));
     return MIUGKS_OK;
 }
 miugks_status apply_AT(miugks_solver* s, int l, const double* x, double* y)
@@ -1940,9 +1991,9 @@ miugks_status apply_PT_cycle(miugks_solver* s, const double* r, double* out)
     return MIUGKS_OK;
 }
 
-// On a mesh with bodies the transposed cycle keeps the ghost couplings of the domain edge only (the
-// wall coupling at a body's faces is left out: the preconditioner is then an approximation, which
-// the Krylov solve corrects), and its values in the cells of bodies, which hold no state, are zeroed.
+// On a mesh with bodies the transposed cycle carries the wall coupling of the bodies' faces (the
+// sweep adds it after the wavefront step that reaches each such cell; AdjBodyPlan), and its
+// values in the cells of bodies, which hold no state, are zeroed.
 miugks_status apply_PT(miugks_solver* s, const double* r, double* out)
 {
     ST(apply_PT_cycle(s, r, out));
