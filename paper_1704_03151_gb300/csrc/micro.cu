@@ -27,6 +27,7 @@
 #include "kernels.cuh"
 #include "async.cuh"
 #include <algorithm>
+#include <climits>
 
 namespace cg = cooperative_groups;
 
@@ -1328,7 +1329,36 @@ cudaError_t launch_micro_sgs(const MicroArgs& m, const SweepPlanHost& plan, cons
     constexpr size_t kSmemMax = 227 * 1024;
     if (fixed + slot > kSmemMax) return cudaErrorInvalidValue;
     const size_t rfit = (kSmemMax - fixed) / slot;
-    const int R = rfit >= 8 ? 8 : rfit >= 4 ? 4 : rfit >= 2 ? 2 : 1;
+    // On a large level the wavefront kernel takes only the blocks of velocities coupled in
+    // both directions and the line-class kernel the rest; on a small one the wavefront's
+    // dependency chain, not its traffic, sets the time and one wavefront launch over every
+    // block is faster than two launches.
+    const bool split = plan.split == 1 || (plan.split == 0 && (size_t)m.L.nc * m.V.nv >= kSweepSplitMinCv);
+    // Ring depth: the deepest of 8, 4, 2 stages whose shared memory lets the launch's CTAs
+    // be resident in the fewest rounds (a CTA's time is the dependency chain of its steps,
+    // so a second round of CTAs doubles the launch).
+    int R = rfit >= 8 ? 8 : rfit >= 4 ? 4 : rfit >= 2 ? 2 : 1;
+    {
+        static int nsm = 0, smem_sm = 0, resv = 0;
+        if (nsm == 0) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+            cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+            cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+        }
+        const long grid = split ? std::max(m.V.nwblk[0], m.V.nwblk[1]) : nblk;
+        auto rounds = [&](int r) -> long {
+            const long per = std::min<long>((long)smem_sm / (long)(fixed + slot * r + resv), 2048 / nthr);
+            return per > 0 ? (grid + per * nsm - 1) / (per * nsm) : LONG_MAX;
+        };
+        if (nsm > 0 && smem_sm > 0 && R >= 2) {
+            int best = R;
+            for (int r = R / 2; r >= 2; r /= 2)
+                if (rounds(r) < rounds(best)) best = r;
+            R = best;
+        }
+    }
     void (*wave)(MicroArgs, const F*, const F*, F*, const F*, int, int, int, int);
     if (m.P.bodies) {
         if (vec) wave = R == 8 ? k_sgs_wave<F, 8, true, true> : R == 4 ? k_sgs_wave<F, 4, true, true> : R == 2 ? k_sgs_wave<F, 2, true, true> : k_sgs_wave<F, 1, true, true>;
@@ -1344,11 +1374,7 @@ cudaError_t launch_micro_sgs(const MicroArgs& m, const SweepPlanHost& plan, cons
     }
     void (*lines)(MicroArgs, const F*, const F*, F*, const F*, int, int, int, int, int, int) =
         m.P.bodies ? k_sgs_lines<F, true> : k_sgs_lines<F, false>;
-    // one segment.  On a large level the wavefront kernel takes only the blocks of
-    // velocities coupled in both directions and the line-class kernel the rest; on a
-    // small one the wavefront's dependency chain, not its traffic, sets the time and
-    // one wavefront launch over every block is faster than two launches.
-    const bool split = plan.split == 1 || (plan.split == 0 && (size_t)m.L.nc * m.V.nv >= kSweepSplitMinCv);
+    // one segment (split: see above)
     // timing mode: an event pair around a launch, with the cell-velocity pairs it sweeps
     auto timed = [&](int kind, double units, auto&& launch) {
         SweepTimer* T = plan.timer;
