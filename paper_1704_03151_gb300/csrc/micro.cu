@@ -1824,22 +1824,40 @@ template cudaError_t launch_state_fallback<float>(const LevelDev&, const VelDev&
                                                   cudaStream_t);
 
 template <typename F>
+// The Maxwellian of velocity k = a nv_y + b factors into rho lam/pi e^{-lam (u_a - U)^2}
+// times e^{-lam (v_b - V)^2}: nu + nv_y exponentials per cell (in FP64, tabled in shared
+// memory), then two FP64 products per velocity.
 __global__ void k_init_maxwell(LevelDev L, VelDev Vg, const double* __restrict__ prim, F* __restrict__ f)
 {
-    const int c = blockIdx.x, nv = Vg.nv;
+    extern __shared__ double etab[];      // [nu] rho lam/pi e^{-lam (u_a - U)^2}, [nvv] e^{-lam (v_b - V)^2}
+    const int c = blockIdx.x, nv = Vg.nv, nu = Vg.nu, nvv = Vg.nvv, tid = threadIdx.x, bs = blockDim.x;
     const size_t nc = L.nc;
-    double rho = prim[4 * c], U = prim[4 * c + 1], V = prim[4 * c + 2], lam = 1.0 / prim[4 * c + 3];
-    for (int k = threadIdx.x; k < nv; k += blockDim.x) {
-        double du = Vg.u[k] - U, dv = Vg.v[k] - V;
-        double g = rho * (lam / kPi) * exp(-lam * (du * du + dv * dv));
+    const double rho = prim[4 * c], U = prim[4 * c + 1], V = prim[4 * c + 2], lam = 1.0 / prim[4 * c + 3];
+    const double hfac = kKint / (4.0 * lam);
+    for (int e = tid; e < nu + nvv; e += bs) {
+        if (e < nu) {
+            const double d = Vg.ua[e] - U;
+            etab[e] = rho * (lam / kPi) * exp(-lam * d * d);
+        } else {
+            const double d = Vg.vb[e - nu] - V;
+            etab[e] = exp(-lam * d * d);
+        }
+    }
+    __syncthreads();
+    // velocity k = a * nvv + b of this thread, stepped by the block size without a division
+    const int sa = bs / nvv, sb = bs - sa * nvv;
+    int a = tid / nvv, b = tid - a * nvv;
+    for (int k = tid; k < nv; k += bs, a += sa, b += sb) {
+        if (b >= nvv) { b -= nvv; ++a; }
+        const double g = etab[a] * etab[nu + b];
         f[(size_t)c * nv + k] = (F)g;
-        f[(nc + c) * (size_t)nv + k] = (F)(g * kKint / (4.0 * lam));
+        f[(nc + c) * (size_t)nv + k] = (F)(g * hfac);
     }
 }
 template <typename F>
 cudaError_t launch_init_maxwell(const LevelDev& L, const VelDev& V, const double* prim, F* f, cudaStream_t st)
 {
-    k_init_maxwell<F><<<L.nc, 128, 0, st>>>(L, V, prim, f);
+    k_init_maxwell<F><<<L.nc, V.nv >= 256 ? 256 : 128, (V.nu + V.nvv) * sizeof(double), st>>>(L, V, prim, f);
     return cudaGetLastError();
 }
 template cudaError_t launch_init_maxwell<double>(const LevelDev&, const VelDev&, const double*, double*, cudaStream_t);

@@ -15,7 +15,7 @@ import time
 from . import miugks, workloads
 
 
-def _iterate(s, tol, max_iter, chunk, floor_rtol):
+def _iterate(s, tol, max_iter, chunk, floor_rtol, hist):
     iters, prev, stop, res = 0, None, "max_iter", None
     while iters < max_iter:
         try:
@@ -23,6 +23,7 @@ def _iterate(s, tol, max_iter, chunk, floor_rtol):
         except miugks.MiugksError as e:
             return iters, res, "unphysical state (%s)" % str(e).split(": ", 1)[-1]
         iters += chunk
+        hist.append(float(max(res)))
         if max(res) < tol:
             stop = "tolerance"
             break
@@ -33,29 +34,41 @@ def _iterate(s, tol, max_iter, chunk, floor_rtol):
     return iters, res, stop
 
 
-def run(case, tol=1e-6, max_iter=3000, chunk=5, floor_rtol=1e-3, stream=None):
+def run(case, tol=1e-6, max_iter=3000, chunk=5, floor_rtol=1e-3, switch_rtol=1e-3, stream=None):
     """Solve `case` from its initial state to RMS residual `tol`: the mixed
     form first, then FP64 from the mixed form's state if the mixed form
-    stopped at its floor.  Returns the final solver and the iterations,
-    seconds and stopping reason of each phase."""
+    stopped at its floor.  The mixed form counts as at its floor once its
+    largest residual component changes by less than `switch_rtol` (relative)
+    over `chunk` iterations.  Near the floor the FP32 rounding makes the
+    residual wander by about a per cent: on a strongly stretched mesh the
+    mixed iterations still remove slow error modes there that the residual
+    does not show (switch late: 1e-3), on a mesh of similar cells they add
+    nothing that the FP64 phase has to repeat (switch early: 2e-2).  The FP64
+    phase stops at `tol` or when it changes by less than `floor_rtol`.
+    Returns the final solver and the iterations, seconds, stopping reason and
+    residual history (the largest component after every `chunk` iterations)
+    of each phase."""
     import torch
     s = miugks.Solver(case, precision="mixed", stream=stream)
     s.init_fields(*workloads.initial_fields(case))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    it1, res1, stop1 = _iterate(s, tol, max_iter, chunk, floor_rtol)
+    h1 = []
+    it1, res1, stop1 = _iterate(s, tol, max_iter, chunk, switch_rtol, h1)
     t1 = time.perf_counter()
     phases = [{"precision": "mixed", "iterations": it1, "seconds": t1 - t0, "stopped_at": stop1,
-               "residual": None if res1 is None else [float(x) for x in res1]}]
+               "residual": None if res1 is None else [float(x) for x in res1], "history": h1}]
     if stop1 == "floor":
         d = miugks.Solver(case, precision="fp64", stream=stream)
         d.copy_state(s)
         s.close()
         s = d
-        it2, res2, stop2 = _iterate(s, tol, max_iter - it1, chunk, floor_rtol)
+        h2 = []
+        it2, res2, stop2 = _iterate(s, tol, max_iter - it1, chunk, floor_rtol, h2)
         torch.cuda.synchronize()
         phases.append({"precision": "fp64", "iterations": it2, "seconds": time.perf_counter() - t1,
-                       "stopped_at": stop2, "residual": None if res2 is None else [float(x) for x in res2]})
+                       "stopped_at": stop2, "residual": None if res2 is None else [float(x) for x in res2],
+                       "history": h2})
     torch.cuda.synchronize()
     last = phases[-1]
     return s, {"seconds": time.perf_counter() - t0, "iterations": sum(p["iterations"] for p in phases),
