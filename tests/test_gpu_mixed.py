@@ -104,3 +104,25 @@ def test_copy_state_converts_precision(lib):
     assert np.array_equal(back.get_f(), d.get_f().astype(np.float32).astype(np.float64))
     with pytest.raises(lib.MiugksError):
         lib.Solver(wl.cavity(n=16, nvel=10, kn=0.5, lid=0.2, levels=2)).copy_state(m)
+
+
+def test_polish_reaches_the_fp64_steady_state(lib):
+    """refine.polish: FP64 iterations from a state converged in the mixed form
+    reach the FP64 form's own steady state (the state the adjoint is
+    linearised at), up to the total mass, which the mixed iterations carry
+    with FP32 rounding (a closed cavity's steady states differ by their
+    mass)."""
+    from paper_1704_03151_gb300 import refine
+    case = wl.cavity(n=16, nvel=16, kn=1.0, lid=0.2, levels=2, vmax=5.0)
+    m = lib.Solver(case, precision="mixed")
+    m.init_uniform(1.0, 0.0, 0.0, 1.0)
+    m.run(1e-6, 400)
+    d, info = refine.polish(m, case, tol=1e-11, max_iter=400)
+    assert info["stopped_at"] in ("tolerance", "floor"), info
+    ref = lib.Solver(case, precision="fp64")
+    ref.init_uniform(1.0, 0.0, 0.0, 1.0)
+    ref.run(1e-11, 800)
+    md, mr = d.macro(), ref.macro()
+    assert info["residual"] is not None and max(info["residual"]) < 1e-9
+    for k in ("rho", "u", "v", "t"):
+        assert rel(md[k], mr[k]) < 1e-6, k
