@@ -247,7 +247,10 @@ miugks_status miugks_stage_prolong(miugks_solver *s, int lev, int m, const doubl
  * (param 0), x-velocity (1) or y-velocity (2) of one wall BC.  Objectives of a
  * wall BC: obj 0 = sum over its faces of face length x shear stress, 1 = heat
  * flux, 2 = pressure (the quantities of miugks_get_wall).  All in FP64 on an
- * FP64 copy (checkpoint) of the current f, whatever the solver's precision.
+ * FP64 copy (checkpoint) of the current f, whatever the solver's precision
+ * (a state converged in the mixed form keeps its FP32 rounding there; a few
+ * FP64 iterations from it, through miugks_copy_state, make the Krylov solve
+ * converge several times faster).
  * On a mesh with bodies a body's faces are wall faces of the fluid cells beside
  * them and a cell in a body holds no state (N = -f there); the transposed-cycle
  * preconditioner carries the wall coupling of a body's faces as of the domain

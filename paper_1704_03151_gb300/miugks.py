@@ -430,7 +430,10 @@ class Solver:
 
     def adjoint(self, obj, bc, param, tol=1e-10, max_iter=2000, restart=30):
         """dJ/dtheta at the current (converged) state by the adjoint solve;
-        returns (gradient, {"J", "iterations", "residual"})."""
+        returns (gradient, {"J", "iterations", "residual"}).  At a state
+        converged in the mixed form, polish it in FP64 first
+        (refine.polish): the Krylov solve then needs several times fewer
+        iterations."""
         g = np.zeros(1)
         info = np.zeros(3)
         st = self._lib.miugks_adjoint(self.h, obj, bc, param, tol, max_iter, restart, _ptr(g), _ptr(info))
