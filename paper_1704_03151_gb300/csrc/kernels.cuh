@@ -150,7 +150,7 @@ cudaError_t launch_wall_quantities(const LevelDev& L, const VelDev& V, const BcD
 // ---- differentiation form: adjoint of the steady equations (FP64) ----
 constexpr int kFaceRec = 28;              // doubles per face record of the adjoint residual
 constexpr int kCellRec = 9;               // doubles per cell record
-constexpr int kMaxAdjNv = 8192;           // velocities per cell of the transposed sweep (shared memory)
+constexpr int kMaxAdjNv = 12288;          // velocities per cell of the transposed sweep (2 x 8 B each in shared memory)
 struct AdjDev {
     LevelDev L; VelDev V; GasDev gas;
     const BcDev* bc; const double* Cw;
