@@ -411,6 +411,10 @@ SWEEP_TRAFFIC_PER_CV = {"lines": 30.2, "wave": 29.8}
 # DRAM bytes (read + written) of one launch of the flat plate's face-flux kernel
 # (mixed, x-faces), from the ncu capture in profiles/k_face_flux_plate128x96_v48_mixed.md
 FLUX_TRAFFIC_PLATE_MIXED = 417.3e6
+# the same for one launch of the square cylinder's face flux (mixed, x-faces): the ncu capture of the half-size
+# case (80x60 cells, 4,860 x-faces, 580.9 MB; profiles/k_face_flux_square80x60_v89_mixed.md) scaled by the
+# faces of the full case (19,320), since each face reads its cells' rows and writes its own fluxes
+FLUX_TRAFFIC_SQUARE_MIXED = 580.9e6 * 19320 / 4860
 
 
 def sweep_roofline(sk, precision):
@@ -468,7 +472,8 @@ def measure_square(steps, warmup, precision="mixed"):
     return {"workload": "square_cylinder_%dx%d_v89x89_ma5_kn0.1_4level_%s" % (c["nx"], c["ny"], precision),
             "steps": steps, "value": cv / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
             "stage_ms_per_step": {"flux": flux_ms / 2, "evolution_cs": sweep_ms / 2, "total": total_ms / 2},
-            "roofline_flux": flux_roofline(stage, precision, c["nx"], c["ny"], c["vgrid"]["nu"] * c["vgrid"]["nv"]),
+            "roofline_flux": flux_roofline(stage, precision, c["nx"], c["ny"], c["vgrid"]["nu"] * c["vgrid"]["nv"],
+                                           traffic=FLUX_TRAFFIC_SQUARE_MIXED if precision == "mixed" else None),
             "residual_last": [float(x) for x in res],
             "step_hbm": {"bytes_per_step": b, "achieved": b / (ms * 1e-3) / 1e9, "peak": hpeak, "unit": "GB/s",
                          "frac": b / (ms * 1e-3) / 1e9 / hpeak, "peak_source": hsrc}}

@@ -496,7 +496,11 @@ cudaError_t launch_face_flux(const FaceFluxArgs<F>& a, cudaStream_t st)
     constexpr size_t kCacheMax = 64 * 1024;
     int ncl = 1;
     while (ncl < 8 && face_flux_smem<F>(a.V, true, ncl) > kCacheMax) ncl *= 2;
-    const bool cache = face_flux_smem<F>(a.V, true, ncl) <= kCacheMax;
+    // In FP32 a face that needs a cluster for its cache (the 89^2 grid) runs faster as one CTA
+    // that recomputes the reconstruction in each pass (square cylinder: 8.7 against 11.8 ms of flux
+    // per iteration); with one CTA per face the cache wins (64^2 cavity 0.34 against 0.42 ms, flat
+    // plate 1.48 against 2.08 ms).  FP64 keeps the cluster split: recomputing costs FP64 issue.
+    const bool cache = face_flux_smem<F>(a.V, true, ncl) <= kCacheMax && (sizeof(F) == 8 || ncl == 1);
     if (!cache) ncl = 1;
     const size_t smem = face_flux_smem<F>(a.V, cache, ncl);
     if (smem > kSmemMax) return cudaErrorInvalidValue;

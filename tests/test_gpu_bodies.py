@@ -166,7 +166,8 @@ def test_body_layouts_the_sweeps_cannot_take_are_refused(lib):
 
 def test_mixed_form_at_ma5_with_the_full_velocity_grid(lib):
     """The mixed form on the Ma 5 start with 89x89 velocities (its face flux
-    splits each face over a 4-CTA cluster) against the oracle: measured error
+    runs one CTA per face that recomputes the reconstruction in each pass,
+    where FP64 splits a face over an 8-CTA cluster) against the oracle: measured error
     of the macroscopic fields after five iterations (measured on GB300: at most
     1.3e-7 relative, in the temperature)."""
     case = CASES["square_ma5"]
