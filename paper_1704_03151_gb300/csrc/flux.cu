@@ -514,7 +514,11 @@ cudaError_t launch_face_flux(const FaceFluxArgs<F>& a, cudaStream_t st)
         attr_set = true;
     }
     int nf = a.axis == 0 ? a.L.nfx : a.L.nfy;
-    int threads = a.V.nv / ncl >= 256 ? 256 : 128;
+    // FP32 with a small velocity grid: 128 threads, so that more faces (CTAs) overlap their serial
+    // scalar phases on an SM (64^2 cavity, 32^2 velocities: 0.27 against 0.34 ms of flux per
+    // iteration); with 48^2 or more velocities 256 threads are faster (flat plate 1.48 against
+    // 1.72 ms, square cylinder 8.7 against 9.6 ms)
+    int threads = (a.V.nv / ncl < 256 || (sizeof(F) == 4 && a.V.nv / ncl <= 1536)) ? 128 : 256;
     if (!cache) {
         k_face_flux<F, false><<<nf, threads, smem, st>>>(a);
         return cudaGetLastError();
